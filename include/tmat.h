@@ -1,0 +1,239 @@
+/*
+ * tmat.h - C ABI of the B300 (sm_103a) T-matrix multiple-scattering library.
+ *
+ * The library solves the collective-scattering problem of arXiv 2107.09879,
+ * App. I: N scatterers, each with a T-matrix in a vector-spherical-wave basis
+ * truncated at multipole order nmax, coupled by translation coefficients, solved
+ * matrix-free by GMRES, plus the adjoint gradient of App. IV and the sub-region
+ * decomposition of the main text. Spheres on a plane are supported (all z equal).
+ *
+ * Conventions (used by every call)
+ * --------------------------------
+ *  - Wave number k = 2 pi n_bg / wavelength. Lengths in the caller's unit.
+ *  - Coefficient index of one scatterer (App. I-B, Eq. def_tmatrix):
+ *        n(l, m) = l(l+1) + m - 1 in [0, L),  L = nmax(nmax+2),
+ *        flat    = p * L + n(l, m),   p = 0 (grad phi x r waves), p = 1 (curl of those),
+ *    so one scatterer holds P = 2 L complex coefficients (P = 2 lmax(lmax+2), App. I-B).
+ *  - Complex numbers are interleaved (re, im): tmat_c128 = two doubles.
+ *  - Multi-RHS arrays are [R][N][P] (RHS-major, scatterer, coefficient).
+ *  - Positions are [N][3] doubles.
+ *
+ * Memory and streams
+ * ------------------
+ *  - Array arguments may be device pointers or host pointers; the library asks
+ *    the CUDA driver which one it got (cudaPointerGetAttributes). Host arrays are
+ *    copied to library-owned device buffers on the context stream and results are
+ *    copied back before the call returns. Device arrays are used in place.
+ *  - The caller owns every array it passes. The library allocates only scratch
+ *    (Krylov bases, tables, neighbour lists) from the context and frees it in
+ *    tmat_ctx_destroy or tmat_solution_free.
+ *  - All work is issued on the context stream. Calls that return status or
+ *    iteration info synchronise that stream before returning.
+ *  - A context is not thread-safe: one host thread at a time per context.
+ *
+ * Errors
+ * ------
+ *  Every call returns 0 (TMAT_OK) or a negative TMAT_E* code; tmat_last_error()
+ *  gives a one-line message for the last failing call on that context. On error
+ *  no output array is guaranteed to be written, except TMAT_ENOCONV, where the
+ *  outputs hold the best iterate and the info struct says how far it got.
+ */
+#ifndef TMAT_H
+#define TMAT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TMAT_OK 0
+#define TMAT_EINVAL (-1)     /* bad size, nmax outside 1..6, NaN input, non-coplanar positions */
+#define TMAT_ENOMEM (-3)     /* device allocation failed */
+#define TMAT_ENOCONV (-4)    /* iteration cap reached; outputs hold the best iterate */
+#define TMAT_EBREAKDOWN (-5) /* GMRES breakdown with a non-zero residual */
+#define TMAT_ECUDA (-6)      /* a CUDA runtime call failed */
+#define TMAT_ENOTSUP (-7)    /* valid request this build does not implement */
+
+#define TMAT_NMAX_MAX 6
+#define TMAT_MAX_RHS 16
+
+typedef struct { double re, im; } tmat_c128;
+typedef struct { float re, im; } tmat_c64;
+
+typedef struct tmat_ctx tmat_ctx;
+typedef struct tmat_solution tmat_solution;
+
+/* One spherical meta-atom: radius and complex refractive index of the sphere. */
+typedef struct {
+  double radius;
+  double n_re;
+  double n_im;
+} tmat_atom;
+
+/* Arithmetic of the iterated operator. */
+enum {
+  TMAT_PREC_FP64 = 0,  /* complex128 apply, vectors and Arnoldi */
+  TMAT_PREC_MIXED = 1, /* complex64 apply and vectors inside GMRES; fp64 Arnoldi/Givens;
+                          fp64-accurate refinement residual (iterative refinement) */
+};
+
+/* Which kernel applies the operator. */
+enum {
+  TMAT_PATH_AUTO = 0,      /* lattice path when opts.lattice_nx > 0, else neighbour path */
+  TMAT_PATH_NEIGHBOUR = 1, /* neighbour-list (CSR) apply, blocks generated per pair */
+  TMAT_PATH_LATTICE = 2,   /* rectangular lattice: one block per lattice offset, reused */
+};
+
+/* Options of tmat_solve. Zero-initialise, then set what you need. */
+typedef struct {
+  double tol;          /* stop when ||b - K x|| / ||b|| <= tol (true residual, fp64). 0 -> 1e-6 */
+  int restart;         /* GMRES restart length m. 0 -> 40 */
+  int max_iter;        /* cap on GMRES iterations in total (all restarts, all refinements). 0 -> 2000 */
+  double cutoff;       /* interaction cutoff (inclusive, |x_i - x_j| <= cutoff); <= 0: every pair */
+  int precision;       /* TMAT_PREC_* */
+  double inner_tol;    /* mixed: relative tolerance of each inner fp32 solve. 0 -> 1e-4 */
+  int path;            /* TMAT_PATH_* */
+  int lattice_nx;      /* lattice path: sites per row; positions must be the row-major lattice */
+  int lattice_ny;      /*   x = x0 + ix*pitch, y = y0 + iy*pitch, z = z0 */
+  double lattice_pitch;
+} tmat_solve_opts;
+
+/* Per-call result summary (host struct). */
+typedef struct {
+  int iterations;            /* GMRES iterations (applications of K), all RHS together */
+  int refinements;           /* mixed: outer refinement steps */
+  int converged;             /* 1 if every RHS met tol */
+  int n_rhs;
+  double rel_residual[TMAT_MAX_RHS]; /* final true ||b - K x|| / ||b|| per RHS (fp64) */
+  double seconds;            /* wall time of the call */
+} tmat_solve_info;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on `device`, issuing work on `cuda_stream` (a cudaStream_t;
+ * NULL = the legacy default stream). */
+int tmat_ctx_create(int device, void* cuda_stream, tmat_ctx** out);
+int tmat_ctx_set_stream(tmat_ctx* ctx, void* cuda_stream);
+int tmat_ctx_destroy(tmat_ctx* ctx);
+const char* tmat_last_error(const tmat_ctx* ctx);
+/* Number of kernels this context has launched so far (for launch accounting). */
+int64_t tmat_ctx_launch_count(const tmat_ctx* ctx);
+
+/* ---- geometry (integer, bit-exact) -------------------------------------- */
+
+/* Interaction neighbour lists (a cutoff is this library's parameter; the paper
+ * couples every pair, App. I-D). Source j is a neighbour of target i when j != i
+ * and d2 <= cutoff*cutoff, with d2 = dx*dx + dy*dy + dz*dz evaluated in fp64 left
+ * to right with every product and sum rounded (no fused multiply-add).
+ * cutoff <= 0 couples every pair. Output CSR: row_ptr[N+1] (int64), col[nnz]
+ * (int32, ascending within a row). Two passes: call with col == NULL to get
+ * row_ptr and *nnz_out, allocate col, call again with the same row_ptr. */
+int tmat_neighbors(tmat_ctx* ctx, const double* pos, int64_t N, double cutoff,
+                   int64_t* row_ptr, int32_t* col, int64_t* nnz_out);
+
+/* Sub-region index sets (main text: jinc-source groups with a padding region;
+ * Fig. 3 caption). On an nx x ny lattice (site index iy*nx + ix), sub-region
+ * a = ay*nax + ax (nax = ceil(nx/cx)) has core sites ix in [ax*cx, (ax+1)*cx),
+ * iy in [ay*cy, (ay+1)*cy) (clipped), and simulated sites = core grown by `buf`
+ * on every side (clipped). Outputs: core_ptr[n_sub+1], core_idx[nx*ny],
+ * sim_ptr[n_sub+1], sim_idx[sim_ptr[n_sub]] (int64, ascending per set). Pass
+ * core_idx == sim_idx == NULL first to get the pointers and *sim_total_out. */
+int tmat_subregions(tmat_ctx* ctx, int64_t nx, int64_t ny, int64_t cx, int64_t cy, int64_t buf,
+                    int64_t* core_ptr, int64_t* core_idx, int64_t* sim_ptr, int64_t* sim_idx,
+                    int64_t* n_sub_out, int64_t* sim_total_out);
+
+/* ---- per-scatterer T-matrices (App. I-B; spheres: Lorenz-Mie) ---------- */
+
+/* T_diag_out[N][P]: the diagonal of each sphere's T-matrix,
+ * t_{l,p=0} = -b_l, t_{l,p=1} = -a_l (Bohren & Huffman Mie coefficients, relative
+ * index n_sphere / n_bg, size parameter k r). dTdr_out (nullable): d t / d radius. */
+int tmat_build(tmat_ctx* ctx, const tmat_atom* atoms, int64_t N, double wavelength, double n_bg,
+               int nmax, tmat_c128* T_diag_out, tmat_c128* dTdr_out);
+
+/* ---- incident field (App. II-A) ----------------------------------------- */
+
+/* Plane waves A_r exp(i k khat_r . x), khat = (sin b cos a, sin b sin a, cos b),
+ * dirs[R][2] = (b, a) in radians, pol[R][3] complex polarisation (transverse).
+ * a0_out[R][N][P] = exp(i k khat_r . x_i) a_lmp(b, a) (App. II-A, explicit forms). */
+int tmat_incident_planewave(tmat_ctx* ctx, const double* pos, int64_t N, double wavelength,
+                            double n_bg, int nmax, const double* dirs, const tmat_c128* pol,
+                            int R, tmat_c128* a0_out);
+
+/* ---- translation coefficients (App. I-C, Eqs. tran_coeff) --------------- */
+
+/* xi_out[M][P][P]: the outgoing-to-regular translation matrix xi(k d_m) for each
+ * displacement d_m = disp[m] (any direction), rows (l,m,p), columns (l',m',p'):
+ * Phi_{lmp}(k(x - x_a)) = sum xi_{lmp;l'm'p'}(k (x_b - x_a)) RPhi_{l'm'p'}(k(x - x_b)). */
+int tmat_translation(tmat_ctx* ctx, int nmax, double k, const double* disp, int64_t M,
+                     tmat_c128* xi_out);
+
+/* ---- the operator (App. I-C/D) ------------------------------------------ */
+
+enum {
+  TMAT_OP_FORWARD = 0, /* y = x - T (A x)      : K = M Omega of App. I-C with M = diag(T) */
+  TMAT_OP_ADJOINT = 1, /* y = x - A^T (T x)    : the transposed operator of App. IV */
+  TMAT_OP_COUPLE = 2,  /* y = A x              : field incident from the other scatterers */
+};
+
+/* One application of the operator to R vectors x[R][N][P] -> y[R][N][P], with
+ * A_ij = xi(k(x_i - x_j))^T for j in the CSR row of i (row_ptr/col from
+ * tmat_neighbors). precision: TMAT_PREC_FP64 (complex128 arithmetic) or
+ * TMAT_PREC_MIXED (complex64 arithmetic; x and y are still complex128 here).
+ * Positions must be coplanar. */
+int tmat_apply(tmat_ctx* ctx, int op, int precision, const double* pos, int64_t N, double k,
+               int nmax, const tmat_c128* T_diag, const int64_t* row_ptr, const int32_t* col,
+               const tmat_c128* x, int R, tmat_c128* y);
+
+/* ---- solve (App. I-C/D) -------------------------------------------------- */
+
+/* Solve (I - T A) s = T a0 for R <= TMAT_MAX_RHS right-hand sides by restarted
+ * GMRES, x0 = 0. T_diag[N][P] from tmat_build; a0[R][N][P]; s_out[R][N][P]. With
+ * TMAT_PREC_MIXED the solve is iterative refinement: fp64-accurate residual,
+ * inner GMRES with a complex64 operator to opts.inner_tol. `keep` (nullable)
+ * receives an opaque solution object that holds what tmat_adjoint needs
+ * (positions, T, a0, s, neighbour lists); free it with tmat_solution_free.
+ * info (nullable, host). */
+int tmat_solve(tmat_ctx* ctx, const double* pos, int64_t N, double wavelength, double n_bg,
+               int nmax, const tmat_c128* T_diag, const tmat_c128* a0, int R,
+               const tmat_solve_opts* opts, tmat_c128* s_out, tmat_solution** keep,
+               tmat_solve_info* info);
+int tmat_solution_free(tmat_solution* sol);
+
+/* ---- fields (App. I-C, Eq. sca_fld_concise) ------------------------------ */
+
+/* E_out[M][3] = sum_i s_i^T Phi(k(x - x_i)) at the points pts[M][3] (scattered
+ * field of coefficients s[N][P]). Points must not coincide with a centre. */
+int tmat_field(tmat_ctx* ctx, const double* pos, int64_t N, double wavelength, double n_bg,
+               int nmax, const tmat_c128* s, const double* pts, int64_t M, tmat_c128* E_out);
+
+/* Far-field amplitude F(rhat) with E_sca(r rhat) -> e^{ikr}/(kr) F(rhat),
+ * dirs[M][2] = (theta, phi). */
+int tmat_farfield(tmat_ctx* ctx, const double* pos, int64_t N, double wavelength, double n_bg,
+                  int nmax, const tmat_c128* s, const double* dirs, int64_t M, tmat_c128* F_out);
+
+/* ---- adjoint (App. IV) ---------------------------------------------------- */
+
+/* Point figure of merit FoM = sum_c |E_inc,c(x_f) + E_sca,c(x_f)|^2 (App. IV,
+ * Eq. performance_metric with a point detector and f = |.|^2) and its adjoint
+ * source v[N][P] = dFoM/ds in the sense dFoM = 2 Re(v^T ds),
+ * v_i = sum_c conj(E_c) Phi_c(k(x_f - x_i)). E_inc_f: the incident field at x_f
+ * (3 complex). fom_out: host double. v_out nullable. */
+int tmat_point_fom(tmat_ctx* ctx, const double* pos, int64_t N, double wavelength, double n_bg,
+                   int nmax, const tmat_c128* s, const double* x_f, const tmat_c128* E_inc_f,
+                   double* fom_out, tmat_c128* v_out);
+
+/* Radius gradient of a figure of merit whose adjoint source is v[N][P] (App. IV,
+ * Eq. grad_geometry_overlap): solves (I - A^T T) mu = v with the operator,
+ * precision and tolerance of the forward solve kept in `sol`, then
+ * grad_out[i] = 2 Re sum_n mu_{i,n} dTdr_{i,n} e_{i,n}, e = a0 + A s (RHS 0 of sol).
+ * dTdr[N][P] from tmat_build. mu_out (nullable) receives mu. */
+int tmat_adjoint(tmat_ctx* ctx, const tmat_solution* sol, const tmat_c128* v,
+                 const tmat_c128* dTdr, double* grad_out, tmat_c128* mu_out,
+                 tmat_solve_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TMAT_H */

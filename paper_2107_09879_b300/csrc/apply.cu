@@ -1,0 +1,327 @@
+// Neighbour-list apply of the preconditioned Maxwell operator (App. I-C/I-D),
+// translation blocks generated per pair on the fly and discarded (App. I-D).
+//
+// Coplanar scatterers: the block of pair (i, j) splits into two classes
+// c = (l+m+p) mod 2. Inside class c, with d = x_i - x_j, rho = |d|, phi its angle:
+//   forward (A x)_i[u]   = e^{-i m_u phi} sum_q h_q(k rho) sum_{u'} G_fwd[u,u',q] e^{+i m_u' phi} x_j[u']
+//   adjoint (A^T x)_i[u] = e^{+i m_u phi} sum_q h_q(k rho) sum_{u'} G_adj[u,u',q] e^{-i m_u' phi} x_j[u']
+// where G holds a5/b5 x Pbar_q^{|mu|}(0) (real for alpha, imaginary for beta).
+// Summing over u' inside the sum over q costs one real x complex FMA pair per
+// table entry plus one complex FMA per (u, q): fewer than forming the block.
+//
+// Mapping: one warp per (target i, class c); lanes own outputs u = lane, lane+32;
+// all lanes of the warp walk the target's neighbour row together.
+#include "apply.h"
+#include "dev.cuh"
+#include "internal.h"
+
+namespace tmat {
+
+constexpr int MAXR = 4;
+constexpr int WARPS_PER_BLOCK = 4;
+
+template <typename R, int NMAX, int OP>
+__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
+apply_nbr_kernel(const double* __restrict__ pos, int64_t N, double k, const C<R>* __restrict__ T,
+                 const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                 const C<R>* __restrict__ x, C<R>* __restrict__ y, int nrhs, int64_t rhs_stride,
+                 const int* __restrict__ seg, const int* __restrict__ tri_idx, const R* __restrict__ tri_val,
+                 const int* __restrict__ mval) {
+  constexpr int L = NMAX * (NMAX + 2), P = 2 * L, Q = 2 * NMAX + 1;
+  constexpr int NU = (L + 31) / 32;
+  __shared__ C<R> xs_all[WARPS_PER_BLOCK][MAXR][L];
+  __shared__ C<R> hs_all[WARPS_PER_BLOCK][Q];
+  __shared__ C<R> ps_all[WARPS_PER_BLOCK][2 * NMAX + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * WARPS_PER_BLOCK + warp;
+  if (gw >= 2 * N) return;
+  const int64_t i = gw >> 1;
+  const int c = (int)(gw & 1);
+  C<R>(&xs)[MAXR][L] = xs_all[warp];
+  C<R>(&hs)[Q] = hs_all[warp];
+  C<R>(&ps)[2 * NMAX + 1] = ps_all[warp];
+
+  int mu_out[NU];
+  C<R> acc[MAXR][NU];
+#pragma unroll
+  for (int s = 0; s < NU; ++s) {
+    int u = lane + 32 * s;
+    mu_out[s] = (u < L) ? mval[c * L + u] : 0;
+#pragma unroll
+    for (int r = 0; r < MAXR; ++r) acc[r][s] = mk<R>(0, 0);
+  }
+  const double xi0 = pos[3 * i], yi0 = pos[3 * i + 1];
+  const int64_t jb = row_ptr[i], je = row_ptr[i + 1];
+  for (int64_t e = jb; e < je; ++e) {
+    const int64_t j = col[e];
+    const double dx = xi0 - pos[3 * j], dy = yi0 - pos[3 * j + 1];
+    const double rho = sqrt(dx * dx + dy * dy);
+    const R cp = (R)(dx / rho), sp = (R)(dy / rho);
+    {
+      C<R> h[Q];
+      hankel_up<R, Q>(k * rho, h);
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        if (lane == q) hs[q] = h[q];
+    }
+    if (lane < 2 * NMAX + 1) {  // e^{i mu phi}, mu = lane - NMAX
+      int mu = lane - NMAX;
+      C<R> e1 = mk<R>(cp, mu < 0 ? -sp : sp), z = mk<R>(1, 0);
+      for (int t = 0; t < (mu < 0 ? -mu : mu); ++t) z = cmul(z, e1);
+      ps[lane] = z;
+    }
+    __syncwarp();
+    for (int u = lane; u < L; u += 32) {
+      const int m = mval[c * L + u];
+      const C<R> ph = ps[NMAX + (OP == 1 ? -m : m)];
+      C<R> tj = mk<R>(1, 0);
+      if (OP == 1) tj = T[j * P + c * L + u];
+      for (int r = 0; r < nrhs; ++r) {
+        C<R> xv = x[r * rhs_stride + j * P + c * L + u];
+        if (OP == 1) xv = cmul(xv, tj);
+        xs[r][u] = cmul(ph, xv);
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < NU; ++s) {
+      const int u = lane + 32 * s;
+      if (u < L) {
+        C<R> pr[MAXR];
+#pragma unroll
+        for (int r = 0; r < MAXR; ++r) pr[r] = mk<R>(0, 0);
+        const int* sg = seg + (c * L + u) * (Q + 1);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const int t0 = sg[q], t1 = sg[q + 1];
+          if (t0 == t1) continue;
+          C<R> w[MAXR];
+#pragma unroll
+          for (int r = 0; r < MAXR; ++r) w[r] = mk<R>(0, 0);
+          for (int t = t0; t < t1; ++t) {
+            const int id = __ldg(tri_idx + t);
+            const R v = __ldg(tri_val + t);
+            const int up = id & 0x7fff;
+            const bool im = (id >> 15) & 1;
+#pragma unroll
+            for (int r = 0; r < MAXR; ++r) {
+              if (r < nrhs) {
+                const C<R> xv = xs[r][up];
+                const R a = im ? -xv.y : xv.x, b = im ? xv.x : xv.y;
+                w[r].x = fma(v, a, w[r].x);
+                w[r].y = fma(v, b, w[r].y);
+              }
+            }
+          }
+          const C<R> hq = hs[q];
+#pragma unroll
+          for (int r = 0; r < MAXR; ++r) cfma(pr[r], hq, w[r]);
+        }
+        const C<R> po = ps[NMAX + (OP == 1 ? mu_out[s] : -mu_out[s])];
+#pragma unroll
+        for (int r = 0; r < MAXR; ++r) cfma(acc[r][s], po, pr[r]);
+      }
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int s = 0; s < NU; ++s) {
+    const int u = lane + 32 * s;
+    if (u < L) {
+      const int64_t o = i * P + c * L + u;
+      for (int r = 0; r < nrhs; ++r) {
+        const C<R> a = acc[r][s];
+        C<R> out;
+        if (OP == 2) {
+          out = a;
+        } else if (OP == 0) {
+          out = csub(x[r * rhs_stride + o], cmul(T[o], a));
+        } else {
+          out = csub(x[r * rhs_stride + o], a);
+        }
+        y[r * rhs_stride + o] = out;
+      }
+    }
+  }
+}
+
+template <typename R, int NMAX, int OP>
+static void launch_one(cudaStream_t st, const NbrOp& a, const void* x, void* y, int nrhs, int64_t stride) {
+  const int64_t warps = 2 * a.N;
+  unsigned grid = (unsigned)cdiv(warps, WARPS_PER_BLOCK);
+  const int op = OP == 1 ? 1 : 0;
+  const R* tv = sizeof(R) == 4 ? (const R*)a.tab->d_tri_f32[op] : (const R*)a.tab->d_tri_f64[op];
+  apply_nbr_kernel<R, NMAX, OP><<<grid, WARPS_PER_BLOCK * 32, 0, st>>>(
+      a.pos, a.N, a.k, (const C<R>*)a.T, a.row_ptr, a.col, (const C<R>*)x, (C<R>*)y, nrhs, stride,
+      a.tab->d_seg[op], a.tab->d_tri_idx[op], tv, a.tab->d_mval);
+}
+
+template <typename R, int OP>
+static int dispatch_nmax(tmat_ctx* ctx, const NbrOp& a, const void* x, void* y, int nrhs, int64_t stride) {
+  switch (a.nmax) {
+    case 1: launch_one<R, 1, OP>(ctx->stream, a, x, y, nrhs, stride); break;
+    case 2: launch_one<R, 2, OP>(ctx->stream, a, x, y, nrhs, stride); break;
+    case 3: launch_one<R, 3, OP>(ctx->stream, a, x, y, nrhs, stride); break;
+    case 4: launch_one<R, 4, OP>(ctx->stream, a, x, y, nrhs, stride); break;
+    case 5: launch_one<R, 5, OP>(ctx->stream, a, x, y, nrhs, stride); break;
+    case 6: launch_one<R, 6, OP>(ctx->stream, a, x, y, nrhs, stride); break;
+    default: return set_error(ctx, TMAT_EINVAL, "nmax %d unsupported", a.nmax);
+  }
+  TM_LAUNCHED(ctx);
+  return TMAT_OK;
+}
+
+// x, y: internal layout [R][N][P] in precision a.fp32 ? complex64 : complex128
+int nbr_apply(tmat_ctx* ctx, const NbrOp& a, int op, const void* x, void* y, int R_) {
+  if (a.N == 0) return TMAT_OK;
+  const int64_t stride = a.N * num_coeffs(a.nmax);
+  const size_t esz = a.fp32 ? sizeof(float2) : sizeof(double2);
+  for (int r0 = 0; r0 < R_; r0 += MAXR) {
+    int nr = R_ - r0 < MAXR ? R_ - r0 : MAXR;
+    const char* xp = (const char*)x + esz * stride * r0;
+    char* yp = (char*)y + esz * stride * r0;
+    int rc;
+    if (a.fp32) {
+      if (op == TMAT_OP_FORWARD) rc = dispatch_nmax<float, 0>(ctx, a, xp, yp, nr, stride);
+      else if (op == TMAT_OP_ADJOINT) rc = dispatch_nmax<float, 1>(ctx, a, xp, yp, nr, stride);
+      else rc = dispatch_nmax<float, 2>(ctx, a, xp, yp, nr, stride);
+    } else {
+      if (op == TMAT_OP_FORWARD) rc = dispatch_nmax<double, 0>(ctx, a, xp, yp, nr, stride);
+      else if (op == TMAT_OP_ADJOINT) rc = dispatch_nmax<double, 1>(ctx, a, xp, yp, nr, stride);
+      else rc = dispatch_nmax<double, 2>(ctx, a, xp, yp, nr, stride);
+    }
+    if (rc) return rc;
+  }
+  return TMAT_OK;
+}
+
+// ---- layout conversion ------------------------------------------------------
+
+template <typename R>
+__global__ void to_internal_kernel(const double2* __restrict__ api, C<R>* __restrict__ out, const int* __restrict__ perm,
+                                   int P, int64_t rows) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * P) return;
+  int64_t row = t / P;
+  int u = (int)(t % P);
+  double2 v = api[row * P + perm[u]];
+  out[t] = mk<R>((R)v.x, (R)v.y);
+}
+
+template <typename R>
+__global__ void from_internal_kernel(const C<R>* __restrict__ in, double2* __restrict__ api, const int* __restrict__ perm,
+                                     int P, int64_t rows) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * P) return;
+  int64_t row = t / P;
+  int u = (int)(t % P);
+  C<R> v = in[t];
+  api[row * P + perm[u]] = make_double2((double)v.x, (double)v.y);
+}
+
+int to_internal(tmat_ctx* ctx, const Tables* t, const double2* api, void* internal, bool fp32, int64_t rows) {
+  int64_t tot = rows * t->P;
+  if (tot == 0) return TMAT_OK;
+  unsigned g = (unsigned)cdiv(tot, 256);
+  if (fp32) to_internal_kernel<float><<<g, 256, 0, ctx->stream>>>(api, (float2*)internal, t->d_perm, t->P, rows);
+  else to_internal_kernel<double><<<g, 256, 0, ctx->stream>>>(api, (double2*)internal, t->d_perm, t->P, rows);
+  TM_LAUNCHED(ctx);
+  return TMAT_OK;
+}
+
+int from_internal(tmat_ctx* ctx, const Tables* t, const void* internal, bool fp32, double2* api, int64_t rows) {
+  int64_t tot = rows * t->P;
+  if (tot == 0) return TMAT_OK;
+  unsigned g = (unsigned)cdiv(tot, 256);
+  if (fp32) from_internal_kernel<float><<<g, 256, 0, ctx->stream>>>((const float2*)internal, api, t->d_perm, t->P, rows);
+  else from_internal_kernel<double><<<g, 256, 0, ctx->stream>>>((const double2*)internal, api, t->d_perm, t->P, rows);
+  TM_LAUNCHED(ctx);
+  return TMAT_OK;
+}
+
+__global__ void coplanar_kernel(const double* __restrict__ pos, int64_t N, int* __restrict__ bad) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+  if (z != pos[2] || x != x || y != y || z != z) atomicOr(bad, 1);
+}
+
+int check_coplanar(tmat_ctx* ctx, const double* d_pos, int64_t N, int* ok) {
+  *ok = 1;
+  if (N == 0) return TMAT_OK;
+  int* flag;
+  TM_TRY(scratch(ctx, "coplanar_flag", sizeof(int), (void**)&flag));
+  TM_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+  coplanar_kernel<<<(unsigned)cdiv(N, 256), 256, 0, ctx->stream>>>(d_pos, N, flag);
+  TM_LAUNCHED(ctx);
+  int* pin = (int*)ctx->pinned;
+  TM_CUDA(ctx, cudaMemcpyAsync(pin, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  *ok = pin[0] ? 0 : 1;
+  return TMAT_OK;
+}
+
+// T diagonal (API layout, complex128) -> internal layout in the kernel precision
+int prepare_T(tmat_ctx* ctx, const Tables* t, const double2* T_api, int64_t N, bool fp32, const char* name, void** out) {
+  size_t esz = fp32 ? sizeof(float2) : sizeof(double2);
+  TM_TRY(scratch(ctx, name, esz * N * t->P, out));
+  return to_internal(ctx, t, T_api, *out, fp32, N);
+}
+
+}  // namespace tmat
+
+using namespace tmat;
+
+extern "C" int tmat_apply(tmat_ctx* ctx, int op, int precision, const double* pos, int64_t N, double k, int nmax,
+                          const tmat_c128* T_diag, const int64_t* row_ptr, const int32_t* col, const tmat_c128* x,
+                          int R, tmat_c128* y) {
+  if (!ctx) return TMAT_EINVAL;
+  if (N < 0 || R < 1 || !(k > 0) || (N > 0 && (!pos || !row_ptr || !col || !x || !y)) ||
+      (op != TMAT_OP_COUPLE && N > 0 && !T_diag) || op < 0 || op > 2 ||
+      (precision != TMAT_PREC_FP64 && precision != TMAT_PREC_MIXED))
+    return set_error(ctx, TMAT_EINVAL, "tmat_apply: bad arguments");
+  Tables* t;
+  TM_TRY(get_tables(ctx, nmax, &t));
+  TM_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (N == 0) return TMAT_OK;
+  const int P = t->P;
+  Staged sp, sT, sr, sc, sx, sy;
+  TM_TRY(stage_in(ctx, "st_pos", pos, sizeof(double) * 3 * N, &sp));
+  int ok;
+  TM_TRY(check_coplanar(ctx, (const double*)sp.dev, N, &ok));
+  if (!ok) return set_error(ctx, TMAT_EINVAL, "tmat_apply: positions must be coplanar (equal z) and finite");
+  TM_TRY(stage_in(ctx, "st_T", T_diag, sizeof(double2) * N * P, &sT));
+  TM_TRY(stage_in(ctx, "st_rowptr", row_ptr, sizeof(int64_t) * (N + 1), &sr));
+  int64_t nnz = 0;
+  {
+    int64_t* pin = (int64_t*)ctx->pinned;
+    TM_CUDA(ctx, cudaMemcpyAsync(pin, (const int64_t*)sr.dev + N, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    nnz = pin[0];
+  }
+  TM_TRY(stage_in(ctx, "st_col", col, sizeof(int32_t) * nnz, &sc));
+  TM_TRY(stage_in(ctx, "st_x", x, sizeof(double2) * R * N * P, &sx));
+  TM_TRY(stage_out(ctx, "st_y", y, sizeof(double2) * R * N * P, &sy));
+  const bool fp32 = precision == TMAT_PREC_MIXED;
+  const size_t esz = fp32 ? sizeof(float2) : sizeof(double2);
+  void *xi, *yi, *Ti = nullptr;
+  TM_TRY(scratch(ctx, "ap_x", esz * R * N * P, &xi));
+  TM_TRY(scratch(ctx, "ap_y", esz * R * N * P, &yi));
+  if (op != TMAT_OP_COUPLE) TM_TRY(prepare_T(ctx, t, (const double2*)sT.dev, N, fp32, "ap_T", &Ti));
+  TM_TRY(to_internal(ctx, t, (const double2*)sx.dev, xi, fp32, (int64_t)R * N));
+  NbrOp a;
+  a.pos = (const double*)sp.dev;
+  a.N = N;
+  a.k = k;
+  a.nmax = nmax;
+  a.fp32 = fp32;
+  a.T = Ti;
+  a.row_ptr = (const int64_t*)sr.dev;
+  a.col = (const int32_t*)sc.dev;
+  a.tab = t;
+  TM_TRY(nbr_apply(ctx, a, op, xi, yi, R));
+  TM_TRY(from_internal(ctx, t, yi, fp32, (double2*)sy.dev, (int64_t)R * N));
+  TM_TRY(finish_out(ctx, &sy));
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return TMAT_OK;
+}

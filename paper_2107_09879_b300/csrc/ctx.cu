@@ -1,0 +1,127 @@
+// Context, error reporting, scratch buffers and host/device staging.
+#include <cstring>
+
+#include "internal.h"
+
+namespace tmat {
+
+int set_error(tmat_ctx* ctx, int code, const char* fmt, ...) {
+  if (ctx) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+int cuda_fail(tmat_ctx* ctx, cudaError_t e, const char* what, const char* file, int line) {
+  int code = (e == cudaErrorMemoryAllocation) ? TMAT_ENOMEM : TMAT_ECUDA;
+  if (e == cudaErrorMemoryAllocation) cudaGetLastError();  // not sticky: clear it
+  return set_error(ctx, code, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+int scratch(tmat_ctx* ctx, const char* name, size_t bytes, void** out) {
+  DevBuf& b = ctx->bufs[name];
+  if (bytes == 0) bytes = 16;
+  if (b.bytes < bytes) {
+    if (b.p) {
+      TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      TM_CUDA(ctx, cudaFree(b.p));
+      b.p = nullptr;
+      b.bytes = 0;
+    }
+    size_t want = bytes + bytes / 8;
+    TM_CUDA(ctx, cudaMalloc(&b.p, want));
+    b.bytes = want;
+  }
+  *out = b.p;
+  return TMAT_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int stage_in(tmat_ctx* ctx, const char* name, const void* user, size_t bytes, Staged* s) {
+  s->user = user;
+  s->bytes = bytes;
+  s->host = false;
+  s->dev = const_cast<void*>(user);
+  if (!user) return TMAT_OK;
+  if (is_device_ptr(user)) return TMAT_OK;
+  s->host = true;
+  TM_TRY(scratch(ctx, name, bytes, &s->dev));
+  if (bytes) TM_CUDA(ctx, cudaMemcpyAsync(s->dev, user, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  return TMAT_OK;
+}
+
+int stage_out(tmat_ctx* ctx, const char* name, void* user, size_t bytes, Staged* s) {
+  s->user = user;
+  s->bytes = bytes;
+  s->host = false;
+  s->dev = user;
+  if (!user) return TMAT_OK;
+  if (is_device_ptr(user)) return TMAT_OK;
+  s->host = true;
+  return scratch(ctx, name, bytes, &s->dev);
+}
+
+int finish_out(tmat_ctx* ctx, Staged* s) {
+  if (s->user && s->host && s->bytes) {
+    TM_CUDA(ctx, cudaMemcpyAsync(const_cast<void*>(s->user), s->dev, s->bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  return TMAT_OK;
+}
+
+}  // namespace tmat
+
+using namespace tmat;
+
+extern "C" int tmat_ctx_create(int device, void* cuda_stream, tmat_ctx** out) {
+  if (!out) return TMAT_EINVAL;
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return TMAT_ECUDA;
+  }
+  tmat_ctx* c = new tmat_ctx();
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMallocHost(&c->pinned, 4096) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return TMAT_ENOMEM;
+  }
+  *out = c;
+  return TMAT_OK;
+}
+
+extern "C" int tmat_ctx_set_stream(tmat_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return TMAT_EINVAL;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  return TMAT_OK;
+}
+
+extern "C" int tmat_ctx_destroy(tmat_ctx* ctx) {
+  if (!ctx) return TMAT_OK;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->bufs) cudaFree(kv.second.p);
+  for (auto& kv : ctx->tables) free_tables(kv.second);
+  cudaFreeHost(ctx->pinned);
+  delete ctx;
+  return TMAT_OK;
+}
+
+extern "C" const char* tmat_last_error(const tmat_ctx* ctx) { return ctx ? ctx->err : "null context"; }
+
+extern "C" int64_t tmat_ctx_launch_count(const tmat_ctx* ctx) { return ctx ? ctx->launches : 0; }

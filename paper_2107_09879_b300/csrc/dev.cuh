@@ -1,0 +1,58 @@
+// Device-side helpers: complex arithmetic on float2/double2 and the outgoing
+// spherical Hankel functions by upward recurrence.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace tmat {
+
+template <typename R> struct cplx;
+template <> struct cplx<float> { using t = float2; };
+template <> struct cplx<double> { using t = double2; };
+template <typename R> using C = typename cplx<R>::t;
+
+template <typename R> __host__ __device__ __forceinline__ C<R> mk(R a, R b) { C<R> z; z.x = a; z.y = b; return z; }
+template <typename T> __host__ __device__ __forceinline__ T cadd(T a, T b) { a.x += b.x; a.y += b.y; return a; }
+template <typename T> __host__ __device__ __forceinline__ T csub(T a, T b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename T> __host__ __device__ __forceinline__ T cmul(T a, T b) {
+  T z; z.x = a.x * b.x - a.y * b.y; z.y = a.x * b.y + a.y * b.x; return z;
+}
+template <typename T> __host__ __device__ __forceinline__ T cconj(T a) { a.y = -a.y; return a; }
+template <typename T, typename R> __host__ __device__ __forceinline__ T cscale(T a, R s) { a.x *= s; a.y *= s; return a; }
+// acc += a * b
+template <typename T> __host__ __device__ __forceinline__ void cfma(T& acc, T a, T b) {
+  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+}
+__host__ __device__ __forceinline__ float2 to_c64(double2 a) { return make_float2((float)a.x, (float)a.y); }
+__host__ __device__ __forceinline__ double2 to_c128(float2 a) { return make_double2(a.x, a.y); }
+
+// h_q^(1)(x), q = 0..Q-1 for real x > 0, by upward recurrence
+// h_{q+1} = (2q+1)/x h_q - h_{q-1}, which is stable for the outgoing Hankel
+// function (it is dominated by y_q). e^{ix} is taken from an fp64 argument
+// reduced modulo 2 pi, so the fp32 version keeps the phase of large k d.
+template <typename R, int Q>
+__device__ __forceinline__ void hankel_up(double x, C<R> (&h)[Q]) {
+  const double twopi = 6.283185307179586476925286766559;
+  double xr = x - twopi * rint(x * (1.0 / twopi));
+  R s, c;
+  if constexpr (sizeof(R) == 4) {
+    sincosf((float)xr, &s, &c);
+  } else {
+    sincos(xr, &s, &c);
+  }
+  R xf = (R)x;
+  R ix = (R)1 / xf;
+  // h0 = -i e^{ix}/x ; h1 = -e^{ix}(x + i)/x^2 = e^{ix}(-1/x - i/x^2)
+  h[0] = mk<R>(s * ix, -c * ix);
+  if (Q > 1) {
+    R a = -ix, b = -ix * ix;  // (a + ib) e^{ix}
+    h[1] = mk<R>(a * c - b * s, a * s + b * c);
+  }
+#pragma unroll
+  for (int q = 1; q + 1 < Q; ++q) {
+    R f = (R)(2 * q + 1) * ix;
+    h[q + 1] = mk<R>(f * h[q].x - h[q - 1].x, f * h[q].y - h[q - 1].y);
+  }
+}
+
+}  // namespace tmat

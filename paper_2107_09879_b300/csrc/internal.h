@@ -1,0 +1,117 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/tmat.h"
+
+namespace tmat {
+
+// Constant tables of one multipole order (built on the host once per nmax).
+//
+// Planar tables: for coplanar scatterers the translation blocks split exactly
+// into two classes c = (l + m + p) mod 2 (entries linking different classes
+// vanish because Pbar_q^{|mu|}(0) = 0 for q + mu odd and (l l' q; 0 0 0) = 0 for
+// l + l' + q odd). Inside a class, output u couples to input u' through
+//    B[u,u'] = sum_q G[u,u',q] h_q(k d),
+// with G real for equal polarisations (alpha part) and imaginary for different
+// ones (beta part); the azimuthal phases are applied to the vectors.
+struct Tables {
+  int nmax = 0, L = 0, P = 0, Q = 0;  // Q = 2 nmax + 1 Hankel orders
+  // class-split order: member u of class c is flat index perm[c*L + u]
+  std::vector<int> perm;  // [2L] internal -> flat
+  std::vector<int> mval;  // [2L] azimuthal m of each internal index
+  int* d_perm = nullptr;
+  int* d_mval = nullptr;
+  // planar coupling triples, per op (0 = forward, 1 = adjoint):
+  //   seg[op][(c*L+u)*(Q+1) + q] .. [.. + 1] index the triples of output (c,u), order q
+  //   tri_idx: input index u' | (imag << 15); tri_f32/f64: the real factor
+  int* d_seg[2] = {nullptr, nullptr};
+  int* d_tri_idx[2] = {nullptr, nullptr};
+  float* d_tri_f32[2] = {nullptr, nullptr};
+  double* d_tri_f64[2] = {nullptr, nullptr};
+  int n_tri[2] = {0, 0};
+  // host copies of the planar triples (used to build dense lattice blocks)
+  std::vector<int> seg[2], tri_idx[2];
+  std::vector<double> tri_val[2];
+  // full (3-D) coupling constants a5/b5 as complex [L][L][Q] (zero where absent)
+  double2* d_a5 = nullptr;
+  double2* d_b5 = nullptr;
+};
+
+// A device buffer the context owns and grows on demand.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace tmat
+
+struct tmat_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  char err[512] = {0};
+  int64_t launches = 0;
+  std::map<int, tmat::Tables*> tables;
+  std::map<std::string, tmat::DevBuf> bufs;
+  int num_sms = 148;
+  void* pinned = nullptr;  // small pinned host staging area (status words)
+};
+
+namespace tmat {
+
+int set_error(tmat_ctx* ctx, int code, const char* fmt, ...);
+int cuda_fail(tmat_ctx* ctx, cudaError_t e, const char* what, const char* file, int line);
+#define TM_CUDA(ctx, call)                                                                   \
+  do {                                                                                       \
+    cudaError_t _e = (call);                                                                 \
+    if (_e != cudaSuccess) return ::tmat::cuda_fail((ctx), _e, #call, __FILE__, __LINE__); \
+  } while (0)
+// after a kernel launch: check the launch itself and count it
+#define TM_LAUNCHED(ctx)                                                                                 \
+  do {                                                                                                   \
+    (ctx)->launches++;                                                                                   \
+    cudaError_t _e = cudaGetLastError();                                                                 \
+    if (_e != cudaSuccess) return ::tmat::cuda_fail((ctx), _e, "kernel launch", __FILE__, __LINE__); \
+  } while (0)
+#define TM_TRY(x)                   \
+  do {                              \
+    int _rc = (x);                  \
+    if (_rc != TMAT_OK) return _rc; \
+  } while (0)
+
+// Grow-only scratch owned by the context, keyed by name.
+int scratch(tmat_ctx* ctx, const char* name, size_t bytes, void** out);
+// Tables of order nmax (built and uploaded on first use).
+int get_tables(tmat_ctx* ctx, int nmax, Tables** out);
+void free_tables(Tables* t);
+
+// Host/device pointer staging. An input that is host memory is copied to a
+// scratch buffer; an output that is host memory gets a scratch buffer and is
+// copied back by finish_out().
+bool is_device_ptr(const void* p);
+struct Staged {
+  const void* user = nullptr;
+  void* dev = nullptr;
+  size_t bytes = 0;
+  bool host = false;
+};
+int stage_in(tmat_ctx* ctx, const char* name, const void* user, size_t bytes, Staged* s);
+int stage_out(tmat_ctx* ctx, const char* name, void* user, size_t bytes, Staged* s);
+int finish_out(tmat_ctx* ctx, Staged* s);
+
+inline int num_coeffs(int nmax) { return 2 * nmax * (nmax + 2); }
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Host-side constant generators (tables.cpp).
+double wigner3j_host(int j1, int j2, int j3, int m1, int m2, int m3);
+void coupling_a5b5(int l, int m, int lp, int mp, int q, double2* a, double2* b);
+double pbar_at_zero(int q, int mu);  // normalised Legendre Pbar_q^mu(0), mu >= 0
+
+}  // namespace tmat
