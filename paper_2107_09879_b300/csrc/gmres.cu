@@ -1,0 +1,499 @@
+// Restarted GMRES(m) (Saad, Iterative Methods, Alg. 6.9/6.11) for R right-hand
+// sides at once, all state resident on the device: the paper solves its system
+// with GMRES using only matrix-vector products (App. I, I-D). Arnoldi uses
+// classical Gram-Schmidt applied twice (CGS2) with fp64 dot products and fp64
+// Hessenberg / Givens / least-squares work; basis vectors are complex64 or
+// complex128. Reductions are two-stage with a fixed order (deterministic).
+#include <chrono>
+#include <cmath>
+
+#include "dev.cuh"
+#include "solver.h"
+
+namespace tmat {
+
+constexpr int DOT_CHUNK = 8;
+constexpr int RED_THREADS = 256;
+
+__device__ __forceinline__ double2 shfl_down2(double2 v, int o) {
+  v.x = __shfl_down_sync(0xffffffffu, v.x, o);
+  v.y = __shfl_down_sync(0xffffffffu, v.y, o);
+  return v;
+}
+
+// part[(r*nb + b)*maxv + k] = partial sum_i conj(V_k[r][i]) w[r][i], k < nvec
+template <typename VR>
+__global__ void __launch_bounds__(RED_THREADS)
+dots_kernel(const C<VR>* __restrict__ V, int64_t vstride, int nvec, const C<VR>* __restrict__ w, int64_t n,
+            int64_t rstride, double2* __restrict__ part, int maxv, const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  __shared__ double2 red[RED_THREADS / 32][DOT_CHUNK];
+  const int nb = gridDim.x, b = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const C<VR>* wr = w + r * rstride;
+  for (int k0 = 0; k0 < nvec; k0 += DOT_CHUNK) {
+    double2 acc[DOT_CHUNK];
+#pragma unroll
+    for (int c = 0; c < DOT_CHUNK; ++c) acc[c] = make_double2(0, 0);
+    for (int64_t i = (int64_t)b * blockDim.x + threadIdx.x; i < n; i += (int64_t)nb * blockDim.x) {
+      C<VR> wv = wr[i];
+      double wx = wv.x, wy = wv.y;
+#pragma unroll
+      for (int c = 0; c < DOT_CHUNK; ++c) {
+        if (k0 + c < nvec) {
+          C<VR> v = V[(int64_t)(k0 + c) * vstride + r * rstride + i];
+          double vx = v.x, vy = v.y;
+          acc[c].x = fma(vx, wx, fma(vy, wy, acc[c].x));   // conj(v) w
+          acc[c].y = fma(vx, wy, fma(-vy, wx, acc[c].y));
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < DOT_CHUNK; ++c) {
+      double2 v = acc[c];
+      for (int o = 16; o > 0; o >>= 1) {
+        double2 t = shfl_down2(v, o);
+        v.x += t.x;
+        v.y += t.y;
+      }
+      if (lane == 0) red[warp][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < DOT_CHUNK && k0 + threadIdx.x < nvec) {
+      double2 s = make_double2(0, 0);
+      for (int q = 0; q < RED_THREADS / 32; ++q) {
+        s.x += red[q][threadIdx.x].x;
+        s.y += red[q][threadIdx.x].y;
+      }
+      part[((int64_t)r * nb + b) * maxv + k0 + threadIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// out[r*maxv + k] = sum_b part[...] (fixed order); if add_to, out += that
+__global__ void reduce_kernel(const double2* __restrict__ part, int nb, int nvec, int maxv, double2* __restrict__ out,
+                              const int* __restrict__ active) {
+  const int r = blockIdx.x, k = threadIdx.x;
+  if (k >= nvec) return;
+  if (active && !active[r]) return;
+  double2 s = make_double2(0, 0);
+  for (int b = 0; b < nb; ++b) {
+    double2 v = part[((int64_t)r * nb + b) * maxv + k];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  out[r * maxv + k] = s;
+}
+
+// out[r][i] += sign * sum_k V_k[r][i] coef[r][k]
+template <typename VR, typename XR>
+__global__ void update_kernel(const C<VR>* __restrict__ V, int64_t vstride, int nvec, const double2* __restrict__ coef,
+                              int maxv, double sign, C<XR>* __restrict__ out, int64_t n, int64_t rstride,
+                              const int* __restrict__ active, const int* __restrict__ ncols) {
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  const int nv = ncols ? min(nvec, ncols[r]) : nvec;  // only the columns this RHS built
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double sx = 0, sy = 0;
+    for (int k = 0; k < nv; ++k) {
+      C<VR> v = V[(int64_t)k * vstride + r * rstride + i];
+      double2 c = coef[r * maxv + k];
+      sx += (double)v.x * c.x - (double)v.y * c.y;
+      sy += (double)v.x * c.y + (double)v.y * c.x;
+    }
+    C<XR> o = out[r * rstride + i];
+    o.x = (XR)((double)o.x + sign * sx);
+    o.y = (XR)((double)o.y + sign * sy);
+    out[r * rstride + i] = o;
+  }
+}
+
+// y[r] = scale[r] * x[r] (scale from a device vector: 1/norm, or 0 if norm == 0)
+template <typename XR, typename YR>
+__global__ void scale_kernel(const C<XR>* __restrict__ x, C<YR>* __restrict__ y, int64_t n, int64_t rstride,
+                             const double* __restrict__ norm, int inv, const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  double s = norm ? norm[r] : 1.0;
+  if (inv) s = (s > 0) ? 1.0 / s : 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    C<XR> v = x[r * rstride + i];
+    C<YR> o;
+    o.x = (YR)((double)v.x * s);
+    o.y = (YR)((double)v.y * s);
+    y[r * rstride + i] = o;
+  }
+}
+
+// out[r] = b[r] - y[r] in the type of out
+template <typename BR, typename YR>
+__global__ void residual_kernel(const C<BR>* __restrict__ b, const C<YR>* __restrict__ y, C<BR>* __restrict__ out,
+                                int64_t total) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    C<BR> bv = b[i];
+    C<YR> yv = y[i];
+    out[i] = mk<BR>((BR)((double)bv.x - (double)yv.x), (BR)((double)bv.y - (double)yv.y));
+  }
+}
+
+template <typename XR, typename YR>
+__global__ void convert_kernel(const C<XR>* __restrict__ x, C<YR>* __restrict__ y, int64_t total) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = mk<YR>((YR)x[i].x, (YR)x[i].y);
+}
+
+// x[r] += alpha[r] * d[r]
+__global__ void axpy_scaled_kernel(double2* __restrict__ x, const double2* __restrict__ d, const double* __restrict__ alpha,
+                                   int64_t n, int64_t rstride) {
+  const int r = blockIdx.y;
+  const double a = alpha[r];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double2 v = x[r * rstride + i], w = d[r * rstride + i];
+    v.x += a * w.x;
+    v.y += a * w.y;
+    x[r * rstride + i] = v;
+  }
+}
+
+// Small per-RHS state of one GMRES run (device)
+struct GState {
+  double2 *hA, *hB;      // [R][maxv] CGS coefficients of pass 1 and 2
+  double2 *H;            // [R][maxv][m] rotated Hessenberg (upper triangle used)
+  double2 *cs, *sn, *g;  // rotations [R][m], rhs [R][maxv]
+  double2 *y;            // [R][maxv] least-squares solution
+  double *nrm;           // [R] norm of the new vector / residual
+  double *tol_abs;       // [R]
+  int *active, *ncols, *flags;
+};
+
+__global__ void cycle_init_kernel(GState s, int R, int maxv, const double* __restrict__ rnorm, const int* __restrict__ want) {
+  int r = threadIdx.x;
+  if (r >= R) return;
+  for (int k = 0; k < maxv; ++k) s.g[r * maxv + k] = make_double2(0, 0);
+  double rn = rnorm[r];
+  s.g[r * maxv] = make_double2(rn, 0);
+  s.ncols[r] = 0;
+  s.active[r] = (want[r] && rn > 0 && isfinite(rn)) ? 1 : 0;
+}
+
+__global__ void norm_from_dots_kernel(const double2* __restrict__ d, int maxv, double* __restrict__ nrm, int R,
+                                      const int* __restrict__ active) {
+  int r = threadIdx.x;
+  if (r >= R) return;
+  if (active && !active[r]) return;
+  nrm[r] = sqrt(fmax(d[r * maxv].x, 0.0));
+}
+
+__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+// Givens step for column j (one thread per RHS)
+__global__ void givens_kernel(GState s, int R, int j, int m, int maxv) {
+  int r = threadIdx.x;
+  if (r >= R || !s.active[r]) return;
+  double2 h[65];
+  for (int i = 0; i <= j; ++i) {
+    double2 a = s.hA[r * maxv + i], b = s.hB[r * maxv + i];
+    h[i] = make_double2(a.x + b.x, a.y + b.y);
+  }
+  double hn = s.nrm[r];
+  h[j + 1] = make_double2(hn, 0);
+  // rotation G_i = [[conj(c_i), conj(s_i)], [-s_i, c_i]]
+  for (int i = 0; i < j; ++i) {
+    double2 c = s.cs[r * m + i], sn = s.sn[r * m + i];
+    double2 t0 = h[i], t1 = h[i + 1];
+    h[i] = make_double2(c.x * t0.x + c.y * t0.y + sn.x * t1.x + sn.y * t1.y,
+                        c.x * t0.y - c.y * t0.x + sn.x * t1.y - sn.y * t1.x);
+    h[i + 1] = make_double2(-(sn.x * t0.x - sn.y * t0.y) + (c.x * t1.x - c.y * t1.y),
+                            -(sn.x * t0.y + sn.y * t0.x) + (c.x * t1.y + c.y * t1.x));
+  }
+  double den = sqrt(cabs2(h[j]) + cabs2(h[j + 1]));
+  double2 c = make_double2(1, 0), sn = make_double2(0, 0);
+  if (den > 0) {
+    c = make_double2(h[j].x / den, h[j].y / den);
+    sn = make_double2(h[j + 1].x / den, h[j + 1].y / den);
+  }
+  s.cs[r * m + j] = c;
+  s.sn[r * m + j] = sn;
+  h[j] = make_double2(den, 0);
+  double2 gj = s.g[r * maxv + j];
+  s.g[r * maxv + j + 1] = make_double2(-(sn.x * gj.x - sn.y * gj.y), -(sn.x * gj.y + sn.y * gj.x));
+  s.g[r * maxv + j] = make_double2(c.x * gj.x + c.y * gj.y, c.x * gj.y - c.y * gj.x);
+  for (int i = 0; i <= j; ++i) s.H[((int64_t)r * maxv + i) * m + j] = h[i];
+  s.ncols[r] = j + 1;
+  double res = sqrt(cabs2(s.g[r * maxv + j + 1]));
+  if (!isfinite(res) || !isfinite(hn)) {
+    s.flags[r] |= 1;  // NaN / Inf
+    s.active[r] = 0;
+  } else if (res <= s.tol_abs[r] || hn == 0.0) {
+    s.active[r] = 0;
+  }
+}
+
+// back substitution y = H^{-1} g over the first ncols columns
+__global__ void lsq_kernel(GState s, int R, int m, int maxv) {
+  int r = threadIdx.x;
+  if (r >= R) return;
+  int nc = s.ncols[r];
+  for (int k = 0; k < maxv; ++k) s.y[r * maxv + k] = make_double2(0, 0);
+  for (int k = nc - 1; k >= 0; --k) {
+    double2 acc = s.g[r * maxv + k];
+    for (int l = k + 1; l < nc; ++l) {
+      double2 hk = s.H[((int64_t)r * maxv + k) * m + l], yl = s.y[r * maxv + l];
+      acc.x -= hk.x * yl.x - hk.y * yl.y;
+      acc.y -= hk.x * yl.y + hk.y * yl.x;
+    }
+    double2 d = s.H[((int64_t)r * maxv + k) * m + k];
+    double den = cabs2(d);
+    s.y[r * maxv + k] = den > 0 ? make_double2((acc.x * d.x + acc.y * d.y) / den, (acc.y * d.x - acc.x * d.y) / den)
+                                : make_double2(0, 0);
+  }
+}
+
+static unsigned grid_for(tmat_ctx* ctx, int64_t n) {
+  int64_t g = cdiv(n, 256);
+  int64_t cap = (int64_t)ctx->num_sms * 8;
+  return (unsigned)(g < cap ? (g < 1 ? 1 : g) : cap);
+}
+
+// norms of R vectors (rstride apart) into nrm[r] (device); uses dots
+template <typename VR>
+static int vec_norms(tmat_ctx* ctx, const C<VR>* v, int64_t n, int64_t rstride, int R, double2* part, int nb,
+                     double2* tmp, int maxv, double* nrm, const int* active) {
+  dots_kernel<VR><<<dim3(nb, R), RED_THREADS, 0, ctx->stream>>>(v, 0, 1, v, n, rstride, part, maxv, active);
+  TM_LAUNCHED(ctx);
+  reduce_kernel<<<R, 32, 0, ctx->stream>>>(part, nb, 1, maxv, tmp, active);
+  TM_LAUNCHED(ctx);
+  norm_from_dots_kernel<<<1, 32, 0, ctx->stream>>>(tmp, maxv, nrm, R, active);
+  TM_LAUNCHED(ctx);
+  return TMAT_OK;
+}
+
+// Restarted GMRES on vectors of type VR. b (VR, internal layout, R x n) and the
+// solution x (complex128, zero on entry) both device. Convergence when the true
+// residual ||b - K x|| <= tol ||b|| per RHS.
+template <typename VR>
+static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b, double2* x, int R, int64_t n,
+                     const GmresParams& p, GmresStats* st) {
+  const int m = p.restart;
+  const int maxv = m + 1;
+  const int64_t rs = n;  // RHS stride
+  const int nb = (int)std::min<int64_t>(cdiv(n, RED_THREADS), (int64_t)ctx->num_sms * 2);
+  C<VR>* V;
+  TM_TRY(scratch(ctx, sizeof(VR) == 4 ? "g_V32" : "g_V64", sizeof(C<VR>) * (size_t)maxv * R * n, (void**)&V));
+  C<VR>* xv;  // x in operator precision (for the true residual)
+  TM_TRY(scratch(ctx, sizeof(VR) == 4 ? "g_xv32" : "g_xv64", sizeof(C<VR>) * (size_t)R * n, (void**)&xv));
+  double2* part;
+  TM_TRY(scratch(ctx, "g_part", sizeof(double2) * (size_t)R * nb * maxv, (void**)&part));
+  GState s;
+  char* small;
+  const size_t R_ = R;
+  size_t sz = sizeof(double2) * R_ * maxv * 4 + sizeof(double2) * R_ * maxv * m + sizeof(double2) * R_ * m * 2 +
+              sizeof(double) * R_ * 4 + sizeof(int) * R_ * 4 + 1024;
+  TM_TRY(scratch(ctx, "g_small", sz, (void**)&small));
+  {
+    char* q = small;
+    auto take = [&](size_t bytes) { char* o = q; q += (bytes + 255) / 256 * 256; return (void*)o; };
+    s.hA = (double2*)take(sizeof(double2) * R_ * maxv);
+    s.hB = (double2*)take(sizeof(double2) * R_ * maxv);
+    s.g = (double2*)take(sizeof(double2) * R_ * maxv);
+    s.y = (double2*)take(sizeof(double2) * R_ * maxv);
+    s.H = (double2*)take(sizeof(double2) * R_ * maxv * m);
+    s.cs = (double2*)take(sizeof(double2) * R_ * m);
+    s.sn = (double2*)take(sizeof(double2) * R_ * m);
+    s.nrm = (double*)take(sizeof(double) * R_);
+    s.tol_abs = (double*)take(sizeof(double) * R_);
+    double* bnorm = (double*)take(sizeof(double) * R_);
+    double* rnorm = (double*)take(sizeof(double) * R_);
+    s.active = (int*)take(sizeof(int) * R_);
+    s.ncols = (int*)take(sizeof(int) * R_);
+    s.flags = (int*)take(sizeof(int) * R_);
+    int* want = (int*)take(sizeof(int) * R_);
+    if ((size_t)(q - small) > sz) return set_error(ctx, TMAT_ECUDA, "gmres: state layout overflow");
+    TM_CUDA(ctx, cudaMemsetAsync(s.flags, 0, sizeof(int) * R_, ctx->stream));
+    const unsigned g1 = grid_for(ctx, n);
+    // ||b||
+    TM_TRY(vec_norms<VR>(ctx, b, n, rs, R, part, nb, s.hA, maxv, bnorm, nullptr));
+    double* pin = (double*)ctx->pinned;
+    TM_CUDA(ctx, cudaMemcpyAsync(pin, bnorm, sizeof(double) * R, cudaMemcpyDeviceToHost, ctx->stream));
+    TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    double hb[TMAT_MAX_RHS], tolabs[TMAT_MAX_RHS];
+    int hwant[TMAT_MAX_RHS];
+    for (int r = 0; r < R; ++r) {
+      hb[r] = pin[r];
+      tolabs[r] = 0.9 * p.tol * hb[r];
+      hwant[r] = hb[r] > 0 ? 1 : 0;
+      st->rel_res[r] = hb[r] > 0 ? 1.0 : 0.0;
+    }
+    TM_CUDA(ctx, cudaMemcpyAsync(s.tol_abs, tolabs, sizeof(double) * R, cudaMemcpyHostToDevice, ctx->stream));
+    TM_CUDA(ctx, cudaMemsetAsync(x, 0, sizeof(double2) * R_ * n, ctx->stream));
+    // first residual = b
+    TM_CUDA(ctx, cudaMemcpyAsync(rnorm, bnorm, sizeof(double) * R, cudaMemcpyDeviceToDevice, ctx->stream));
+    const C<VR>* rsrc = b;
+    bool all_done = true;
+    for (int r = 0; r < R; ++r) all_done = all_done && !hwant[r];
+    st->converged = all_done;
+    while (!all_done) {
+      TM_CUDA(ctx, cudaMemcpyAsync(want, hwant, sizeof(int) * R, cudaMemcpyHostToDevice, ctx->stream));
+      cycle_init_kernel<<<1, 32, 0, ctx->stream>>>(s, R, maxv, rnorm, want);
+      TM_LAUNCHED(ctx);
+      scale_kernel<VR, VR><<<dim3(g1, R), 256, 0, ctx->stream>>>(rsrc, V, n, rs, rnorm, 1, nullptr);
+      TM_LAUNCHED(ctx);
+      int j = 0;
+      for (; j < m && st->iterations < p.max_iter; ++j) {
+        C<VR>* vj = V + (int64_t)j * R * n;
+        C<VR>* w = V + (int64_t)(j + 1) * R * n;
+        TM_TRY(op_apply(ctx, A, mode, vj, w, R));
+        for (int pass = 0; pass < 2; ++pass) {
+          double2* hc = pass == 0 ? s.hA : s.hB;
+          dots_kernel<VR><<<dim3(nb, R), RED_THREADS, 0, ctx->stream>>>(V, (int64_t)R * n, j + 1, w, n, rs, part,
+                                                                         maxv, s.active);
+          TM_LAUNCHED(ctx);
+          reduce_kernel<<<R, 64, 0, ctx->stream>>>(part, nb, j + 1, maxv, hc, s.active);
+          TM_LAUNCHED(ctx);
+          update_kernel<VR, VR><<<dim3(g1, R), 256, 0, ctx->stream>>>(V, (int64_t)R * n, j + 1, hc, maxv, -1.0, w, n,
+                                                                      rs, s.active, nullptr);
+          TM_LAUNCHED(ctx);
+        }
+        TM_TRY(vec_norms<VR>(ctx, w, n, rs, R, part, nb, s.y, maxv, s.nrm, s.active));
+        scale_kernel<VR, VR><<<dim3(g1, R), 256, 0, ctx->stream>>>(w, w, n, rs, s.nrm, 1, s.active);
+        TM_LAUNCHED(ctx);
+        givens_kernel<<<1, 32, 0, ctx->stream>>>(s, R, j, m, maxv);
+        TM_LAUNCHED(ctx);
+        st->iterations++;
+        int* ipin = (int*)ctx->pinned;
+        TM_CUDA(ctx, cudaMemcpyAsync(ipin, s.active, sizeof(int) * R, cudaMemcpyDeviceToHost, ctx->stream));
+        TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        bool any = false;
+        for (int r = 0; r < R; ++r) any = any || ipin[r];
+        if (!any) {
+          ++j;
+          break;
+        }
+      }
+      // x += V y over the columns each RHS built in this cycle (ncols[r] <= j)
+      lsq_kernel<<<1, 32, 0, ctx->stream>>>(s, R, m, maxv);
+      TM_LAUNCHED(ctx);
+      update_kernel<VR, double><<<dim3(g1, R), 256, 0, ctx->stream>>>(V, (int64_t)R * n, j, s.y, maxv, 1.0, x, n, rs,
+                                                                      nullptr, s.ncols);
+      TM_LAUNCHED(ctx);
+      // true residual r = b - K x (in the operator precision)
+      convert_kernel<double, VR><<<g1, 256, 0, ctx->stream>>>(x, xv, (int64_t)R * n);
+      TM_LAUNCHED(ctx);
+      C<VR>* w = V + (int64_t)R * n;  // V[1] as scratch, V[0] receives the new start vector
+      TM_TRY(op_apply(ctx, A, mode, xv, w, R));
+      residual_kernel<VR, VR><<<g1, 256, 0, ctx->stream>>>(b, w, w, (int64_t)R * n);
+      TM_LAUNCHED(ctx);
+      TM_TRY(vec_norms<VR>(ctx, w, n, rs, R, part, nb, s.y, maxv, rnorm, nullptr));
+      TM_CUDA(ctx, cudaMemcpyAsync(pin, rnorm, sizeof(double) * R, cudaMemcpyDeviceToHost, ctx->stream));
+      int* fl = (int*)(pin + TMAT_MAX_RHS);
+      TM_CUDA(ctx, cudaMemcpyAsync(fl, s.flags, sizeof(int) * R, cudaMemcpyDeviceToHost, ctx->stream));
+      TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      all_done = true;
+      bool conv = true;
+      for (int r = 0; r < R; ++r) {
+        double rel = hb[r] > 0 ? pin[r] / hb[r] : 0.0;
+        st->rel_res[r] = rel;
+        bool ok = hb[r] == 0 || rel <= p.tol;
+        if (fl[r] & 1) st->breakdown = true;
+        hwant[r] = (!ok && !(fl[r] & 1)) ? 1 : 0;
+        conv = conv && ok;
+        all_done = all_done && !hwant[r];
+      }
+      st->converged = conv;
+      if (st->iterations >= p.max_iter) break;
+      rsrc = w;
+      // the new start vector goes to V[0] = w / ||w|| (scale reads w = V[1], writes V[0])
+    }
+  }
+  return TMAT_OK;
+}
+
+static unsigned g_for(tmat_ctx* ctx, int64_t n) { return grid_for(ctx, n); }
+
+int solve_system(tmat_ctx* ctx, const Operator& A64, const Operator* A32, int mode, const double2* b, double2* x, int R,
+                 const SolveParams& p, SolveStats* st) {
+  const int64_t n = A64.N() * num_coeffs(A64.nmax());
+  GmresParams gp;
+  gp.restart = std::max(2, std::min(p.restart, 64));
+  gp.max_iter = p.max_iter;
+  if (p.precision == TMAT_PREC_FP64 || !A32) {
+    gp.tol = p.tol;
+    GmresStats gs;
+    TM_TRY(gmres_run<double>(ctx, A64, mode, b, x, R, n, gp, &gs));
+    st->iterations = gs.iterations;
+    st->converged = gs.converged;
+    for (int r = 0; r < R; ++r) st->rel_res[r] = gs.rel_res[r];
+    if (gs.breakdown && !gs.converged) return set_error(ctx, TMAT_EBREAKDOWN, "GMRES produced a non-finite value");
+    return TMAT_OK;
+  }
+  // mixed: iterative refinement with an fp64 residual around fp32 inner GMRES
+  double2 *r64, *d64, *y64;
+  float2* r32;
+  TM_TRY(scratch(ctx, "mx_r64", sizeof(double2) * R * n, (void**)&r64));
+  TM_TRY(scratch(ctx, "mx_d64", sizeof(double2) * R * n, (void**)&d64));
+  TM_TRY(scratch(ctx, "mx_y64", sizeof(double2) * R * n, (void**)&y64));
+  TM_TRY(scratch(ctx, "mx_r32", sizeof(float2) * R * n, (void**)&r32));
+  const int nb = (int)std::min<int64_t>(cdiv(n, RED_THREADS), (int64_t)ctx->num_sms * 2);
+  double2 *part, *tmp;
+  double *rn, *bn, *alpha;
+  TM_TRY(scratch(ctx, "mx_part", sizeof(double2) * R * nb, (void**)&part));
+  TM_TRY(scratch(ctx, "mx_tmp", sizeof(double2) * R + sizeof(double) * 3 * R + 1024, (void**)&tmp));
+  rn = (double*)(tmp + R);
+  bn = rn + R;
+  alpha = bn + R;
+  const unsigned g1 = g_for(ctx, n);
+  TM_CUDA(ctx, cudaMemsetAsync(x, 0, sizeof(double2) * R * n, ctx->stream));
+  TM_TRY(vec_norms<double>(ctx, b, n, n, R, part, nb, tmp, 1, bn, nullptr));
+  TM_CUDA(ctx, cudaMemcpyAsync(r64, b, sizeof(double2) * R * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  double* pin = (double*)ctx->pinned;
+  TM_CUDA(ctx, cudaMemcpyAsync(pin, bn, sizeof(double) * R, cudaMemcpyDeviceToHost, ctx->stream));
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  double hb[TMAT_MAX_RHS], hr[TMAT_MAX_RHS];
+  for (int r = 0; r < R; ++r) hb[r] = hr[r] = pin[r];
+  st->iterations = 0;
+  st->refinements = 0;
+  for (int outer = 0; outer < 50; ++outer) {
+    bool done = true;
+    double halpha[TMAT_MAX_RHS];
+    for (int r = 0; r < R; ++r) {
+      double rel = hb[r] > 0 ? hr[r] / hb[r] : 0.0;
+      st->rel_res[r] = rel;
+      bool ok = hb[r] == 0 || rel <= p.tol;
+      done = done && ok;
+      halpha[r] = ok ? 0.0 : hr[r];  // scale of the correction; 0 freezes a converged RHS
+    }
+    st->converged = done;
+    if (done || st->iterations >= p.max_iter) break;
+    // r32 = r64 / ||r|| (zero for converged RHS)
+    TM_CUDA(ctx, cudaMemcpyAsync(alpha, halpha, sizeof(double) * R, cudaMemcpyHostToDevice, ctx->stream));
+    scale_kernel<double, float><<<dim3(g1, R), 256, 0, ctx->stream>>>(r64, r32, n, n, alpha, 1, nullptr);
+    TM_LAUNCHED(ctx);
+    GmresParams ip = gp;
+    ip.tol = p.inner_tol;
+    ip.max_iter = p.max_iter - st->iterations;
+    GmresStats gs;
+    TM_TRY(gmres_run<float>(ctx, *A32, mode, r32, d64, R, n, ip, &gs));
+    st->iterations += gs.iterations;
+    // x += ||r|| d
+    axpy_scaled_kernel<<<dim3(g1, R), 256, 0, ctx->stream>>>(x, d64, alpha, n, n);
+    TM_LAUNCHED(ctx);
+    // r = b - K x in fp64
+    TM_TRY(op_apply(ctx, A64, mode, x, y64, R));
+    residual_kernel<double, double><<<g1, 256, 0, ctx->stream>>>(b, y64, r64, (int64_t)R * n);
+    TM_LAUNCHED(ctx);
+    TM_TRY(vec_norms<double>(ctx, r64, n, n, R, part, nb, tmp, 1, rn, nullptr));
+    TM_CUDA(ctx, cudaMemcpyAsync(pin, rn, sizeof(double) * R, cudaMemcpyDeviceToHost, ctx->stream));
+    TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int r = 0; r < R; ++r) {
+      if (!std::isfinite(pin[r])) return set_error(ctx, TMAT_EBREAKDOWN, "refinement residual is not finite");
+      hr[r] = pin[r];
+    }
+    st->refinements++;
+  }
+  for (int r = 0; r < R; ++r) st->rel_res[r] = hb[r] > 0 ? hr[r] / hb[r] : 0.0;
+  return TMAT_OK;
+}
+
+}  // namespace tmat

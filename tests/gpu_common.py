@@ -1,0 +1,36 @@
+"""Helpers for the GPU parity tests: a shared library context and seeded inputs."""
+import math
+
+import numpy as np
+
+from paper_2107_09879_b300 import workloads as W
+
+K0 = 2 * math.pi
+
+
+def ctx():
+    from paper_2107_09879_b300 import _lib
+    if not hasattr(ctx, "_c"):
+        ctx._c = _lib.Context(0)
+    return ctx._c
+
+
+def atoms(radii, n_re=2.0, n_im=0.0):
+    a = np.zeros((len(radii), 3))
+    a[:, 0] = radii
+    a[:, 1] = n_re
+    a[:, 2] = n_im
+    return a
+
+
+def rel_l2(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def rand_c(shape, seed):
+    g = W.SplitMix64(seed)
+    n = int(np.prod(shape))
+    u = g.uniforms(2 * n)
+    return ((u[:n] - 0.5) + 1j * (u[n:] - 0.5)).reshape(shape)
