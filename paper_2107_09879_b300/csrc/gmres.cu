@@ -289,8 +289,9 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
   GState s;
   char* small;
   const size_t R_ = R;
-  size_t sz = sizeof(double2) * R_ * maxv * 4 + sizeof(double2) * R_ * maxv * m + sizeof(double2) * R_ * m * 2 +
-              sizeof(double) * R_ * 4 + sizeof(int) * R_ * 4 + 1024;
+  auto rup = [](size_t b) { return (b + 255) / 256 * 256; };
+  size_t sz = rup(sizeof(double2) * R_ * maxv) * 4 + rup(sizeof(double2) * R_ * maxv * m) +
+              rup(sizeof(double2) * R_ * m) * 2 + rup(sizeof(double) * R_) * 4 + rup(sizeof(int) * R_) * 4;
   TM_TRY(scratch(ctx, "g_small", sz, (void**)&small));
   {
     char* q = small;

@@ -40,6 +40,8 @@ struct Tables {
   // host copies of the planar triples (used to build dense lattice blocks)
   std::vector<int> seg[2], tri_idx[2];
   std::vector<double> tri_val[2];
+  // dense planar forward coefficients G[c][u][u'][q] as complex (alpha real, beta imaginary)
+  double2* d_gdense = nullptr;
   // full (3-D) coupling constants a5/b5 as complex [L][L][Q] (zero where absent)
   double2* d_a5 = nullptr;
   double2* d_b5 = nullptr;
@@ -106,7 +108,7 @@ int stage_in(tmat_ctx* ctx, const char* name, const void* user, size_t bytes, St
 int stage_out(tmat_ctx* ctx, const char* name, void* user, size_t bytes, Staged* s);
 int finish_out(tmat_ctx* ctx, Staged* s);
 
-inline int num_coeffs(int nmax) { return 2 * nmax * (nmax + 2); }
+__host__ __device__ inline int num_coeffs(int nmax) { return 2 * nmax * (nmax + 2); }
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // Host-side constant generators (tables.cpp).

@@ -5,8 +5,21 @@
 
 namespace tmat {
 
+// Lattice operator: row-major nx x ny lattice, one translation block per
+// lattice offset o = (dx, dy) (source site = target site + o), stored transposed
+// per class: BT[o][c][u'][u] = A_o[c][u][u'] (row stride LP complex).
+struct LatOp {
+  int64_t N = 0;
+  int nx = 0, ny = 0;
+  int nmax = 0, L = 0, P = 0, LP = 0;
+  bool fp32 = false;
+  int K = 0;                   // number of offsets
+  const int2* off = nullptr;   // [K] (dx, dy)
+  const int* neg = nullptr;    // [K] index of -o
+  const void* BT = nullptr;    // [K][2][L][LP] complex64 or complex128
+  const void* T = nullptr;     // [N][P] internal layout, kernel precision
+};
 // An operator instance in one precision. kind 0: neighbour list; kind 1: lattice.
-struct LatOp;
 struct Operator {
   int kind = 0;
   NbrOp nbr;
@@ -49,4 +62,21 @@ int solve_system(tmat_ctx* ctx, const Operator& A64, const Operator* A32, int mo
 
 int prepare_T(tmat_ctx* ctx, const Tables* t, const double2* T_api, int64_t N, bool fp32, const char* name, void** out);
 
+}  // namespace tmat
+
+namespace tmat {
+int build_neighbors(tmat_ctx* ctx, const double* d_pos, int64_t N, double cutoff, int64_t* d_row_ptr, int32_t* d_col,
+                    int64_t* nnz_out);
+int lattice_apply(tmat_ctx* ctx, const LatOp& L, int mode, const void* x, void* y, int R);
+inline int64_t lattice_N(const LatOp& L) { return L.N; }
+inline int lattice_nmax(const LatOp& L) { return L.nmax; }
+inline bool lattice_fp32(const LatOp& L) { return L.fp32; }
+// Operators (fp64 and, for mixed, fp32) for one solve.
+struct OpPair {
+  Operator A64, A32;
+  bool have32 = false;
+  LatOp lat64, lat32;
+};
+int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_t N, double k, int nx, int ny,
+                     double pitch, double cutoff, const double2* T64, const float2* T32, bool mixed, OpPair* ops);
 }  // namespace tmat

@@ -218,6 +218,19 @@ int get_tables(tmat_ctx* ctx, int nmax, Tables** out) {
       if ((rc = upload(ctx, t->tri_val[op], &t->d_tri_f64[op]))) break;
     }
     if (rc) break;
+    {
+      std::vector<double2> gd((size_t)t->P * t->L * t->Q, make_double2(0, 0));
+      const int L = t->L, Q = t->Q;
+      for (int cu = 0; cu < t->P; ++cu)
+        for (int q = 0; q < Q; ++q)
+          for (int e = t->seg[0][(size_t)cu * (Q + 1) + q]; e < t->seg[0][(size_t)cu * (Q + 1) + q + 1]; ++e) {
+            int up = t->tri_idx[0][e] & 0x7fff;
+            bool im = (t->tri_idx[0][e] >> 15) & 1;
+            double v = t->tri_val[0][e];
+            gd[((size_t)cu * L + up) * Q + q] = im ? make_double2(0, v) : make_double2(v, 0);
+          }
+      if ((rc = upload(ctx, gd, &t->d_gdense))) break;
+    }
     if ((rc = upload(ctx, a5, &t->d_a5))) break;
     if ((rc = upload(ctx, b5, &t->d_b5))) break;
   } while (0);
@@ -240,6 +253,7 @@ void free_tables(Tables* t) {
     cudaFree(t->d_tri_f32[op]);
     cudaFree(t->d_tri_f64[op]);
   }
+  cudaFree(t->d_gdense);
   cudaFree(t->d_a5);
   cudaFree(t->d_b5);
   delete t;

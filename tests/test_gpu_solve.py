@@ -1,0 +1,147 @@
+"""GPU parity of the solve, fields and adjoint (through the C-ABI) against the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_common import K0, atoms, ctx, rand_c, rel_l2
+from oracle import adjoint, field, incident, mie, system
+from paper_2107_09879_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem(nx, ny, nmax, seed, angles=(0.0,), lo=0.08, hi=0.24, const_r=None):
+    pos = W.lattice_positions(nx, ny)
+    r = np.full(nx * ny, const_r) if const_r else W.uniform_radii(nx * ny, lo, hi, seed)
+    T = ctx().tmat_build(atoms(r), 1.0, 1.0, nmax)
+    dirs = np.array([[math.radians(a), 0.0] for a in angles])
+    pols = np.array([incident.beta_hat(d[0], 0.0).astype(complex) for d in dirs])
+    a0 = ctx().tmat_incident_planewave(pos, 1.0, 1.0, nmax, dirs, pols)
+    return pos, r, T, a0, dirs, pols
+
+
+def _oracle_solve(nmax, pos, r, a0, cutoff):
+    To = np.array([mie.tmatrix_diag(nmax, K0, x, 2.0) for x in r])
+    return np.array([system.solve_dense(nmax, K0, pos, To, a0[q], cutoff) for q in range(a0.shape[0])])
+
+
+def _opts(**kw):
+    from paper_2107_09879_b300 import _lib
+    return _lib.make_opts(**kw)
+
+
+def test_dense_8x8_fp64_vs_oracle_lu():
+    """64 identical spheres r = 0.2, nmax = 3, every pair, tol 1e-10: rel. L2 <= 1e-9."""
+    pos, r, T, a0, _, _ = _problem(8, 8, 3, 0, const_r=0.2)
+    s, info, _, rc = ctx().tmat_solve(pos, 1.0, 1.0, 3, T, a0, _opts(tol=1e-10, cutoff=0.0, precision=0))
+    assert rc == 0 and info.converged and info.rel_residual[0] <= 1e-10
+    ref = _oracle_solve(3, pos, r, a0, 0.0)
+    assert rel_l2(s, ref) <= 1e-9
+
+
+@pytest.mark.parametrize("nmax,nx,ny,cutoff", [(3, 5, 4, 0.0), (4, 9, 7, 1.6), (5, 4, 3, 1.1)])
+def test_fp64_and_mixed_vs_oracle(nmax, nx, ny, cutoff):
+    pos, r, T, a0, _, _ = _problem(nx, ny, nmax, 10 + nmax, angles=(0.0, 10.0))
+    ref = _oracle_solve(nmax, pos, r, a0, cutoff)
+    s64, i64, _, rc = ctx().tmat_solve(pos, 1.0, 1.0, nmax, T, a0, _opts(tol=1e-11, cutoff=cutoff, precision=0))
+    assert rc == 0 and rel_l2(s64, ref) <= 1e-9
+    smx, imx, _, rc = ctx().tmat_solve(pos, 1.0, 1.0, nmax, T, a0,
+                                       _opts(tol=1e-8, cutoff=cutoff, precision=1, inner_tol=1e-4))
+    assert rc == 0 and imx.converged and imx.refinements >= 1
+    for q in range(2):
+        assert rel_l2(smx[q], ref[q]) <= 1e-6
+
+
+def test_restart_and_many_rhs():
+    pos, r, T, a0, _, _ = _problem(6, 5, 3, 77, angles=(0.0, 3.0, 6.0, 9.0, 12.0))
+    ref = _oracle_solve(3, pos, r, a0, 1.2)
+    s, info, _, rc = ctx().tmat_solve(pos, 1.0, 1.0, 3, T, a0, _opts(tol=1e-11, cutoff=1.2, restart=4))
+    assert rc == 0 and rel_l2(s, ref) <= 1e-9
+
+
+def test_iteration_cap_reports_enoconv():
+    from paper_2107_09879_b300 import _lib
+    pos, r, T, a0, _, _ = _problem(6, 6, 3, 5)
+    s, info, _, rc = ctx().tmat_solve(pos, 1.0, 1.0, 3, T, a0, _opts(tol=1e-12, cutoff=0.0, max_iter=3))
+    assert rc == _lib.ENOCONV and not info.converged and info.iterations == 3
+    assert 0 < info.rel_residual[0] < 1
+
+
+def test_zero_rhs_and_single_scatterer():
+    pos = np.zeros((1, 3))
+    T = ctx().tmat_build(atoms([0.2]), 1.0, 1.0, 4)
+    a0 = np.zeros((1, 1, 48), complex)
+    s, info, _, rc = ctx().tmat_solve(pos, 1.0, 1.0, 4, T, a0, _opts(tol=1e-10))
+    assert rc == 0 and np.all(s == 0)
+    a0 = ctx().tmat_incident_planewave(pos, 1.0, 1.0, 4, np.array([[0.3, 0.2]]),
+                                       np.array([incident.beta_hat(0.3, 0.2).astype(complex)]))
+    s, info, _, rc = ctx().tmat_solve(pos, 1.0, 1.0, 4, T, a0, _opts(tol=1e-12))
+    assert rc == 0 and np.max(np.abs(s[0] - T * a0[0])) <= 1e-14
+
+
+def test_field_and_farfield_vs_oracle():
+    pos, r, T, a0, _, _ = _problem(3, 3, 4, 21)
+    s = rand_c((9, 48), 4)
+    pts = np.array([[0.3, 0.4, 1.5], [5.0, -2.0, 0.7], [0.5, 0.5, -2.0], [0.25, 0.25, 0.0]])
+    E = ctx().tmat_field(pos, 1.0, 1.0, 4, s, pts)
+    Eo = field.scattered_field(4, K0, pos, s, pts)
+    assert rel_l2(E, Eo) <= 1e-12
+    dirs = np.array([[0.0, 0.0], [0.4, 1.0], [math.pi / 2, 2.0], [2.9, -1.0]])
+    F = ctx().tmat_farfield(pos, 1.0, 1.0, 4, s, dirs)
+    Fo = field.far_field(4, K0, pos, s, [tuple(d) for d in dirs])
+    assert rel_l2(F, Fo) <= 1e-12
+
+
+def test_energy_conservation_on_gpu():
+    """Lossless array, every pair coupled: extinction from the GPU coefficients
+    equals the scattered power from quadrature of the GPU far field."""
+    pos, r, T, a0, _, _ = _problem(4, 3, 3, 8, angles=(10.0,))
+    s, info, _, rc = ctx().tmat_solve(pos, 1.0, 1.0, 3, T, a0, _opts(tol=1e-12, cutoff=0.0))
+    pext = -np.real(np.vdot(a0[0], s[0])) * math.pi / K0 ** 2
+    xg, wg = np.polynomial.legendre.leggauss(40)
+    nph = 80
+    dirs = np.array([[math.acos(x), 2 * math.pi * j / nph] for x in xg for j in range(nph)])
+    F = ctx().tmat_farfield(pos, 1.0, 1.0, 3, s[0], dirs)
+    psca = np.sum(np.repeat(wg, nph) * 2 * math.pi / nph * np.sum(np.abs(F) ** 2, axis=1)) / K0 ** 2
+    assert abs(pext - psca) <= 1e-10 * psca
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_adjoint_gradient_vs_oracle_and_fd(precision):
+    nmax, cutoff = 3, 0.8
+    pos = W.lattice_positions(3, 2)
+    r = W.uniform_radii(6, 0.1, 0.22, 7)
+    xf = np.array([0.5, 0.25, 3.0])
+    A = np.array([1.0, 0.0, 0.0], dtype=complex)
+    Einc = incident.planewave_field(K0, 0.0, 0.0, A, xf[None])[0]
+    dirs = np.array([[0.0, 0.0]])
+    a0 = ctx().tmat_incident_planewave(pos, 1.0, 1.0, nmax, dirs, A[None])
+    tol = 1e-12 if precision == 0 else 1e-9
+    opts = _opts(tol=tol, cutoff=cutoff, precision=precision)
+
+    def fwd(rr, keep=False):
+        T, dT = ctx().tmat_build(atoms(rr), 1.0, 1.0, nmax, with_dr=True)
+        s, info, sol, rc = ctx().tmat_solve(pos, 1.0, 1.0, nmax, T, a0, opts, keep=keep)
+        assert rc == 0
+        return T, dT, s, sol
+
+    T, dT, s, sol = fwd(r, keep=True)
+    fom, v = ctx().tmat_point_fom(pos, 1.0, 1.0, nmax, s[0], xf, Einc)
+    To = np.array([mie.tmatrix_diag(nmax, K0, x, 2.0) for x in r])
+    so = system.solve_dense(nmax, K0, pos, To, a0[0], cutoff)
+    assert abs(fom - adjoint.fom(nmax, K0, pos, so, xf, Einc)) <= 1e-9 * fom
+    vo = adjoint.adjoint_source(nmax, K0, pos, so, xf, Einc)
+    assert rel_l2(v, vo) <= (1e-9 if precision == 0 else 1e-6)
+    grad, mu, info = ctx().tmat_adjoint(sol, v, dT, want_mu=True)
+    dTo = np.array([mie.tmatrix_diag_dr(nmax, K0, x, 2.0) for x in r])
+    go, muo = adjoint.radius_gradient(nmax, K0, pos, To, dTo, a0[0], so, vo, cutoff=cutoff)
+    assert rel_l2(grad, go) <= (1e-9 if precision == 0 else 1e-6)
+    h = 1e-5
+    for i in range(6):
+        rp, rm = r.copy(), r.copy()
+        rp[i] += h
+        rm[i] -= h
+        fp = ctx().tmat_point_fom(pos, 1.0, 1.0, nmax, fwd(rp)[2][0], xf, Einc)[0]
+        fm = ctx().tmat_point_fom(pos, 1.0, 1.0, nmax, fwd(rm)[2][0], xf, Einc)[0]
+        assert abs(grad[i] - (fp - fm) / (2 * h)) <= 1e-4 * np.max(np.abs(grad))
