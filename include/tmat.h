@@ -97,6 +97,9 @@ typedef struct {
   int lattice_nx;      /* lattice path: sites per row; positions must be the row-major lattice */
   int lattice_ny;      /*   x = x0 + ix*pitch, y = y0 + iy*pitch, z = z0 */
   double lattice_pitch;
+  double taper;        /* width of a raised-cosine fall-off of the coupling that ends at the cutoff:
+                          pair weight 1 for d <= cutoff - taper, 0.5(1 + cos(pi (d - cutoff + taper)/taper))
+                          up to the cutoff. 0: hard cutoff. Must be <= cutoff. */
 } tmat_solve_opts;
 
 /* Per-call result summary (host struct). */
@@ -119,6 +122,14 @@ int tmat_ctx_destroy(tmat_ctx* ctx);
 const char* tmat_last_error(const tmat_ctx* ctx);
 /* Number of kernels this context has launched so far (for launch accounting). */
 int64_t tmat_ctx_launch_count(const tmat_ctx* ctx);
+
+/* Kernel timing for measurement: when enabled, CUDA events are recorded on the
+ * context stream around every operator-apply launch. tmat_ctx_kernel_time
+ * synchronises and returns the launch count and summed duration of one kernel
+ * kind since timing was (re)enabled: "lattice_apply_fp32", "lattice_apply_fp64",
+ * "nbr_apply_fp32", "nbr_apply_fp64". Enabling again resets the record. */
+int tmat_ctx_set_timing(tmat_ctx* ctx, int enable);
+int tmat_ctx_kernel_time(tmat_ctx* ctx, const char* kind, int64_t* launches, double* total_ms);
 
 /* ---- geometry (integer, bit-exact) -------------------------------------- */
 
@@ -177,13 +188,24 @@ enum {
 };
 
 /* One application of the operator to R vectors x[R][N][P] -> y[R][N][P], with
- * A_ij = xi(k(x_i - x_j))^T for j in the CSR row of i (row_ptr/col from
- * tmat_neighbors). precision: TMAT_PREC_FP64 (complex128 arithmetic) or
+ * A_ij = w(|x_i - x_j|) xi(k(x_i - x_j))^T for j in the CSR row of i (row_ptr/col
+ * from tmat_neighbors), w the coupling window of tmat_solve_opts (cutoff, taper;
+ * taper 0 gives w = 1). precision: TMAT_PREC_FP64 (complex128 arithmetic) or
  * TMAT_PREC_MIXED (complex64 arithmetic; x and y are still complex128 here).
  * Positions must be coplanar. */
 int tmat_apply(tmat_ctx* ctx, int op, int precision, const double* pos, int64_t N, double k,
                int nmax, const tmat_c128* T_diag, const int64_t* row_ptr, const int32_t* col,
-               const tmat_c128* x, int R, tmat_c128* y);
+               double cutoff, double taper, const tmat_c128* x, int R, tmat_c128* y);
+
+/* The same operator on a row-major nx x ny lattice with spacing `pitch`
+ * (site index iy*nx + ix, all z equal): one translation block per lattice
+ * offset inside the cutoff (offset test (dx*pitch)^2 + (dy*pitch)^2 <= cutoff^2,
+ * cutoff <= 0: every pair; `taper` as in tmat_solve_opts), reused by all pairs
+ * with that offset. Same modes,
+ * precisions and layouts as tmat_apply. */
+int tmat_apply_lattice(tmat_ctx* ctx, int op, int precision, int nx, int ny, double pitch, double cutoff,
+                       double taper, double k, int nmax, const tmat_c128* T_diag, const tmat_c128* x, int R,
+                       tmat_c128* y);
 
 /* ---- solve (App. I-C/D) -------------------------------------------------- */
 

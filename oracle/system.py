@@ -11,15 +11,56 @@ preconditioner M = diag(T_i) gives the system that is iterated:
 The adjoint operator (App. IV, Omega^T) in the same preconditioned form is
 K^T-like: (I - A^T T) mu = v with (A^T)_ij = (A_ji)^T = xi(k(x_j - x_i)).
 Interactions are restricted to the neighbour list (all pairs when cutoff <= 0).
+
+Optional coupling window (a parameter of this implementation, not of the
+paper): window = (cutoff, taper) multiplies the block of a pair at distance d
+by w(d) = 1 for d <= cutoff - taper and 0.5 (1 + cos(pi (d - cutoff + taper) /
+taper)) up to the cutoff; window = None (or taper = 0) is the hard cutoff.
 """
+import math
+
 import numpy as np
 
 from .geometry import neighbours
 from .translation import xi_matrix
 
+_WINDOW = [None]  # (cutoff, taper) in force for _block, set by the callers below
+
+
+def coupling_weight(d, cutoff, taper):
+    """Raised-cosine window of the pair coupling (1 inside cutoff - taper)."""
+    if not taper or cutoff <= 0:
+        return 1.0
+    d0 = cutoff - taper
+    if d <= d0:
+        return 1.0
+    if d >= cutoff:
+        return 0.0
+    return 0.5 * (1.0 + math.cos(math.pi * (d - d0) / taper))
+
 
 def _block(nmax, k, xt, xs):
-    return xi_matrix(nmax, nmax, k, np.asarray(xt) - np.asarray(xs)).T
+    d = np.asarray(xt, dtype=np.float64) - np.asarray(xs, dtype=np.float64)
+    B = xi_matrix(nmax, nmax, k, d).T
+    if _WINDOW[0] is not None:
+        B = B * coupling_weight(float(np.linalg.norm(d)), *_WINDOW[0])
+    return B
+
+
+class window:
+    """Context manager: `with window(cutoff, taper): ...` applies the coupling
+    window inside the block."""
+
+    def __init__(self, cutoff, taper):
+        self.w = (cutoff, taper) if taper else None
+
+    def __enter__(self):
+        self.prev = _WINDOW[0]
+        _WINDOW[0] = self.w
+        return self
+
+    def __exit__(self, *a):
+        _WINDOW[0] = self.prev
 
 
 def apply_A(nmax, k, pos, x, nbr):

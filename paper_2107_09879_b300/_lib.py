@@ -27,7 +27,8 @@ MAX_RHS = 16
 class SolveOpts(ct.Structure):
     _fields_ = [("tol", ct.c_double), ("restart", ct.c_int), ("max_iter", ct.c_int), ("cutoff", ct.c_double),
                 ("precision", ct.c_int), ("inner_tol", ct.c_double), ("path", ct.c_int),
-                ("lattice_nx", ct.c_int), ("lattice_ny", ct.c_int), ("lattice_pitch", ct.c_double)]
+                ("lattice_nx", ct.c_int), ("lattice_ny", ct.c_int), ("lattice_pitch", ct.c_double),
+                ("taper", ct.c_double)]
 
 
 class SolveInfo(ct.Structure):
@@ -50,12 +51,15 @@ _SIGS = {
     "tmat_ctx_destroy": [_vp],
     "tmat_last_error": [_vp],
     "tmat_ctx_launch_count": [_vp],
+    "tmat_ctx_set_timing": [_vp, _int],
+    "tmat_ctx_kernel_time": [_vp, ct.c_char_p, ct.POINTER(_i64), ct.POINTER(_d)],
     "tmat_neighbors": [_vp, _vp, _i64, _d, _vp, _vp, ct.POINTER(_i64)],
     "tmat_subregions": [_vp, _i64, _i64, _i64, _i64, _i64, _vp, _vp, _vp, _vp, ct.POINTER(_i64), ct.POINTER(_i64)],
     "tmat_build": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp],
     "tmat_incident_planewave": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _int, _vp],
     "tmat_translation": [_vp, _int, _d, _vp, _i64, _vp],
-    "tmat_apply": [_vp, _int, _int, _vp, _i64, _d, _int, _vp, _vp, _vp, _vp, _int, _vp],
+    "tmat_apply": [_vp, _int, _int, _vp, _i64, _d, _int, _vp, _vp, _vp, _d, _d, _vp, _int, _vp],
+    "tmat_apply_lattice": [_vp, _int, _int, _int, _int, _d, _d, _d, _d, _int, _vp, _vp, _int, _vp],
     "tmat_solve": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _int, ct.POINTER(SolveOpts), _vp, ct.POINTER(_vp),
                    ct.POINTER(SolveInfo)],
     "tmat_solution_free": [_vp],
@@ -129,6 +133,14 @@ class Context:
     def launches(self):
         return lib.tmat_ctx_launch_count(self.h)
 
+    def set_timing(self, on):
+        self.check(lib.tmat_ctx_set_timing(self.h, 1 if on else 0))
+
+    def kernel_time(self, kind):
+        n, ms = ct.c_int64(), ct.c_double()
+        self.check(lib.tmat_ctx_kernel_time(self.h, kind.encode(), ct.byref(n), ct.byref(ms)))
+        return n.value, ms.value
+
     def close(self):
         if getattr(self, "h", None):
             lib.tmat_ctx_destroy(self.h)
@@ -188,11 +200,18 @@ class Context:
         self.check(lib.tmat_translation(self.h, nmax, k, ptr(disp), M, ptr(xi)))
         return xi
 
-    def tmat_apply(self, op, precision, pos, k, nmax, T, row_ptr, col, x):
+    def tmat_apply(self, op, precision, pos, k, nmax, T, row_ptr, col, x, cutoff=0.0, taper=0.0):
         R, N, P = x.shape
         y = empty_like_space(x, (R, N, P), np.complex128)
         self.check(lib.tmat_apply(self.h, op, precision, ptr(pos), N, k, nmax, ptr(T), ptr(row_ptr), ptr(col),
-                                  ptr(x), R, ptr(y)))
+                                  cutoff, taper, ptr(x), R, ptr(y)))
+        return y
+
+    def tmat_apply_lattice(self, op, precision, nx, ny, pitch, cutoff, k, nmax, T, x, taper=0.0):
+        R, N, P = x.shape
+        y = empty_like_space(x, (R, N, P), np.complex128)
+        self.check(lib.tmat_apply_lattice(self.h, op, precision, nx, ny, pitch, cutoff, taper, k, nmax, ptr(T), ptr(x),
+                                          R, ptr(y)))
         return y
 
     def tmat_solve(self, pos, wavelength, n_bg, nmax, T, a0, opts, keep=False, s_out=None):

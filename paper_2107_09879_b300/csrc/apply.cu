@@ -26,7 +26,7 @@ apply_nbr_kernel(const double* __restrict__ pos, int64_t N, double k, const C<R>
                  const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                  const C<R>* __restrict__ x, C<R>* __restrict__ y, int nrhs, int64_t rhs_stride,
                  const int* __restrict__ seg, const int* __restrict__ tri_idx, const R* __restrict__ tri_val,
-                 const int* __restrict__ mval) {
+                 const int* __restrict__ mval, double cutoff, double taper) {
   constexpr int L = NMAX * (NMAX + 2), P = 2 * L, Q = 2 * NMAX + 1;
   constexpr int NU = (L + 31) / 32;
   __shared__ C<R> xs_all[WARPS_PER_BLOCK][MAXR][L];
@@ -60,9 +60,17 @@ apply_nbr_kernel(const double* __restrict__ pos, int64_t N, double k, const C<R>
     {
       C<R> h[Q];
       hankel_up<R, Q>(k * rho, h);
+      R wgt = (R)1;
+      if (taper > 0) {
+        const double d0 = cutoff - taper;
+        if (rho > d0) {
+          if constexpr (sizeof(R) == 4) wgt = 0.5f * (1.0f + cospif((float)((rho - d0) / taper)));
+          else wgt = 0.5 * (1.0 + cospi((rho - d0) / taper));
+        }
+      }
 #pragma unroll
       for (int q = 0; q < Q; ++q)
-        if (lane == q) hs[q] = h[q];
+        if (lane == q) hs[q] = cscale(h[q], wgt);
     }
     if (lane < 2 * NMAX + 1) {  // e^{i mu phi}, mu = lane - NMAX
       int mu = lane - NMAX;
@@ -153,11 +161,12 @@ static void launch_one(cudaStream_t st, const NbrOp& a, const void* x, void* y, 
   const R* tv = sizeof(R) == 4 ? (const R*)a.tab->d_tri_f32[op] : (const R*)a.tab->d_tri_f64[op];
   apply_nbr_kernel<R, NMAX, OP><<<grid, WARPS_PER_BLOCK * 32, 0, st>>>(
       a.pos, a.N, a.k, (const C<R>*)a.T, a.row_ptr, a.col, (const C<R>*)x, (C<R>*)y, nrhs, stride,
-      a.tab->d_seg[op], a.tab->d_tri_idx[op], tv, a.tab->d_mval);
+      a.tab->d_seg[op], a.tab->d_tri_idx[op], tv, a.tab->d_mval, a.cutoff, a.taper);
 }
 
 template <typename R, int OP>
 static int dispatch_nmax(tmat_ctx* ctx, const NbrOp& a, const void* x, void* y, int nrhs, int64_t stride) {
+  cudaEvent_t ev = timing_begin(ctx);
   switch (a.nmax) {
     case 1: launch_one<R, 1, OP>(ctx->stream, a, x, y, nrhs, stride); break;
     case 2: launch_one<R, 2, OP>(ctx->stream, a, x, y, nrhs, stride); break;
@@ -168,6 +177,7 @@ static int dispatch_nmax(tmat_ctx* ctx, const NbrOp& a, const void* x, void* y, 
     default: return set_error(ctx, TMAT_EINVAL, "nmax %d unsupported", a.nmax);
   }
   TM_LAUNCHED(ctx);
+  timing_end(ctx, sizeof(R) == 4 ? "nbr_apply_fp32" : "nbr_apply_fp64", ev);
   return TMAT_OK;
 }
 
@@ -273,10 +283,10 @@ int prepare_T(tmat_ctx* ctx, const Tables* t, const double2* T_api, int64_t N, b
 using namespace tmat;
 
 extern "C" int tmat_apply(tmat_ctx* ctx, int op, int precision, const double* pos, int64_t N, double k, int nmax,
-                          const tmat_c128* T_diag, const int64_t* row_ptr, const int32_t* col, const tmat_c128* x,
-                          int R, tmat_c128* y) {
+                          const tmat_c128* T_diag, const int64_t* row_ptr, const int32_t* col, double cutoff,
+                          double taper, const tmat_c128* x, int R, tmat_c128* y) {
   if (!ctx) return TMAT_EINVAL;
-  if (N < 0 || R < 1 || !(k > 0) || (N > 0 && (!pos || !row_ptr || !col || !x || !y)) ||
+  if (N < 0 || R < 1 || !(k > 0) || !(taper >= 0) || (taper > 0 && !(taper <= cutoff)) || (N > 0 && (!pos || !row_ptr || !col || !x || !y)) ||
       (op != TMAT_OP_COUPLE && N > 0 && !T_diag) || op < 0 || op > 2 ||
       (precision != TMAT_PREC_FP64 && precision != TMAT_PREC_MIXED))
     return set_error(ctx, TMAT_EINVAL, "tmat_apply: bad arguments");
@@ -319,6 +329,8 @@ extern "C" int tmat_apply(tmat_ctx* ctx, int op, int precision, const double* po
   a.row_ptr = (const int64_t*)sr.dev;
   a.col = (const int32_t*)sc.dev;
   a.tab = t;
+  a.cutoff = cutoff;
+  a.taper = taper;
   TM_TRY(nbr_apply(ctx, a, op, xi, yi, R));
   TM_TRY(from_internal(ctx, t, yi, fp32, (double2*)sy.dev, (int64_t)R * N));
   TM_TRY(finish_out(ctx, &sy));

@@ -15,6 +15,7 @@ struct NbrOp {
   const int64_t* row_ptr = nullptr;
   const int32_t* col = nullptr;
   const Tables* tab = nullptr;
+  double cutoff = 0, taper = 0;  // coupling window (taper 0: hard cutoff)
 };
 
 int nbr_apply(tmat_ctx* ctx, const NbrOp& a, int op, const void* x, void* y, int R);

@@ -39,6 +39,22 @@ int scratch(tmat_ctx* ctx, const char* name, size_t bytes, void** out) {
   return TMAT_OK;
 }
 
+cudaEvent_t timing_begin(tmat_ctx* ctx) {
+  if (!ctx->timing) return nullptr;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  cudaEventRecord(e, ctx->stream);
+  return e;
+}
+
+void timing_end(tmat_ctx* ctx, const char* kind, cudaEvent_t start) {
+  if (!start) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, ctx->stream);
+  ctx->timed[kind].push_back({start, e});
+}
+
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -85,6 +101,16 @@ int finish_out(tmat_ctx* ctx, Staged* s) {
 
 using namespace tmat;
 
+static void drop_events(tmat_ctx* ctx) {
+  for (auto& kv : ctx->timed)
+    for (auto& pr : kv.second) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  ctx->timed.clear();
+}
+
+
 extern "C" int tmat_ctx_create(int device, void* cuda_stream, tmat_ctx** out) {
   if (!out) return TMAT_EINVAL;
   *out = nullptr;
@@ -117,6 +143,7 @@ extern "C" int tmat_ctx_destroy(tmat_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (auto& kv : ctx->bufs) cudaFree(kv.second.p);
   for (auto& kv : ctx->tables) free_tables(kv.second);
+  drop_events(ctx);
   cudaFreeHost(ctx->pinned);
   delete ctx;
   return TMAT_OK;
@@ -125,3 +152,29 @@ extern "C" int tmat_ctx_destroy(tmat_ctx* ctx) {
 extern "C" const char* tmat_last_error(const tmat_ctx* ctx) { return ctx ? ctx->err : "null context"; }
 
 extern "C" int64_t tmat_ctx_launch_count(const tmat_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" int tmat_ctx_set_timing(tmat_ctx* ctx, int enable) {
+  if (!ctx) return TMAT_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  drop_events(ctx);
+  ctx->timing = enable != 0;
+  return TMAT_OK;
+}
+
+extern "C" int tmat_ctx_kernel_time(tmat_ctx* ctx, const char* kind, int64_t* launches, double* total_ms) {
+  if (!ctx || !kind || !launches || !total_ms) return TMAT_EINVAL;
+  TM_CUDA(ctx, cudaSetDevice(ctx->device));
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  *launches = 0;
+  *total_ms = 0.0;
+  auto it = ctx->timed.find(kind);
+  if (it == ctx->timed.end()) return TMAT_OK;
+  for (auto& pr : it->second) {
+    float ms = 0;
+    TM_CUDA(ctx, cudaEventElapsedTime(&ms, pr.first, pr.second));
+    *total_ms += ms;
+    *launches += 1;
+  }
+  return TMAT_OK;
+}

@@ -55,4 +55,16 @@ __device__ __forceinline__ void hankel_up(double x, C<R> (&h)[Q]) {
   }
 }
 
+// Interaction weight of a pair at distance d: 1 inside cutoff - taper, a
+// raised-cosine fall-off 0.5 (1 + cos(pi (d - (cutoff - taper)) / taper)) over
+// the last `taper` before the cutoff, 1 everywhere when taper == 0 (hard
+// cutoff) or cutoff <= 0 (every pair). Pairs beyond the cutoff are not coupled.
+__host__ __device__ __forceinline__ double taper_weight(double d, double cutoff, double taper) {
+  if (!(taper > 0) || !(cutoff > 0)) return 1.0;
+  double d0 = cutoff - taper;
+  if (d <= d0) return 1.0;
+  if (d >= cutoff) return 0.0;
+  return 0.5 * (1.0 + cos(3.14159265358979323846 * (d - d0) / taper));
+}
+
 }  // namespace tmat

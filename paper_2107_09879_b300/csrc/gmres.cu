@@ -75,7 +75,7 @@ dots_kernel(const C<VR>* __restrict__ V, int64_t vstride, int nvec, const C<VR>*
 // out[r*maxv + k] = sum_b part[...] (fixed order); if add_to, out += that
 __global__ void reduce_kernel(const double2* __restrict__ part, int nb, int nvec, int maxv, double2* __restrict__ out,
                               const int* __restrict__ active) {
-  const int r = blockIdx.x, k = threadIdx.x;
+  const int r = blockIdx.x, k = blockIdx.y * blockDim.x + threadIdx.x;
   if (k >= nvec) return;
   if (active && !active[r]) return;
   double2 s = make_double2(0, 0);
@@ -188,39 +188,41 @@ __global__ void norm_from_dots_kernel(const double2* __restrict__ d, int maxv, d
 
 __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 
-// Givens step for column j (one thread per RHS)
+// Givens step for column j (one thread per RHS); the column is worked on in
+// place in H[r][.][j] (global memory), so the restart length is not bounded by
+// registers.
 __global__ void givens_kernel(GState s, int R, int j, int m, int maxv) {
   int r = threadIdx.x;
   if (r >= R || !s.active[r]) return;
-  double2 h[65];
+  double2* col = s.H + (int64_t)r * maxv * m + j;  // element i at col[i * m]
   for (int i = 0; i <= j; ++i) {
     double2 a = s.hA[r * maxv + i], b = s.hB[r * maxv + i];
-    h[i] = make_double2(a.x + b.x, a.y + b.y);
+    col[(int64_t)i * m] = make_double2(a.x + b.x, a.y + b.y);
   }
-  double hn = s.nrm[r];
-  h[j + 1] = make_double2(hn, 0);
+  const double hn = s.nrm[r];
+  double2 hj1 = make_double2(hn, 0);  // H[j+1][j], never stored
   // rotation G_i = [[conj(c_i), conj(s_i)], [-s_i, c_i]]
   for (int i = 0; i < j; ++i) {
     double2 c = s.cs[r * m + i], sn = s.sn[r * m + i];
-    double2 t0 = h[i], t1 = h[i + 1];
-    h[i] = make_double2(c.x * t0.x + c.y * t0.y + sn.x * t1.x + sn.y * t1.y,
-                        c.x * t0.y - c.y * t0.x + sn.x * t1.y - sn.y * t1.x);
-    h[i + 1] = make_double2(-(sn.x * t0.x - sn.y * t0.y) + (c.x * t1.x - c.y * t1.y),
-                            -(sn.x * t0.y + sn.y * t0.x) + (c.x * t1.y + c.y * t1.x));
+    double2 t0 = col[(int64_t)i * m], t1 = col[(int64_t)(i + 1) * m];
+    col[(int64_t)i * m] = make_double2(c.x * t0.x + c.y * t0.y + sn.x * t1.x + sn.y * t1.y,
+                                       c.x * t0.y - c.y * t0.x + sn.x * t1.y - sn.y * t1.x);
+    col[(int64_t)(i + 1) * m] = make_double2(-(sn.x * t0.x - sn.y * t0.y) + (c.x * t1.x - c.y * t1.y),
+                                             -(sn.x * t0.y + sn.y * t0.x) + (c.x * t1.y + c.y * t1.x));
   }
-  double den = sqrt(cabs2(h[j]) + cabs2(h[j + 1]));
+  double2 hjj = col[(int64_t)j * m];
+  double den = sqrt(cabs2(hjj) + cabs2(hj1));
   double2 c = make_double2(1, 0), sn = make_double2(0, 0);
   if (den > 0) {
-    c = make_double2(h[j].x / den, h[j].y / den);
-    sn = make_double2(h[j + 1].x / den, h[j + 1].y / den);
+    c = make_double2(hjj.x / den, hjj.y / den);
+    sn = make_double2(hj1.x / den, hj1.y / den);
   }
   s.cs[r * m + j] = c;
   s.sn[r * m + j] = sn;
-  h[j] = make_double2(den, 0);
+  col[(int64_t)j * m] = make_double2(den, 0);
   double2 gj = s.g[r * maxv + j];
   s.g[r * maxv + j + 1] = make_double2(-(sn.x * gj.x - sn.y * gj.y), -(sn.x * gj.y + sn.y * gj.x));
   s.g[r * maxv + j] = make_double2(c.x * gj.x + c.y * gj.y, c.x * gj.y - c.y * gj.x);
-  for (int i = 0; i <= j; ++i) s.H[((int64_t)r * maxv + i) * m + j] = h[i];
   s.ncols[r] = j + 1;
   double res = sqrt(cabs2(s.g[r * maxv + j + 1]));
   if (!isfinite(res) || !isfinite(hn)) {
@@ -263,7 +265,7 @@ static int vec_norms(tmat_ctx* ctx, const C<VR>* v, int64_t n, int64_t rstride, 
                      double2* tmp, int maxv, double* nrm, const int* active) {
   dots_kernel<VR><<<dim3(nb, R), RED_THREADS, 0, ctx->stream>>>(v, 0, 1, v, n, rstride, part, maxv, active);
   TM_LAUNCHED(ctx);
-  reduce_kernel<<<R, 32, 0, ctx->stream>>>(part, nb, 1, maxv, tmp, active);
+  reduce_kernel<<<dim3(R, 1), 32, 0, ctx->stream>>>(part, nb, 1, maxv, tmp, active);
   TM_LAUNCHED(ctx);
   norm_from_dots_kernel<<<1, 32, 0, ctx->stream>>>(tmp, maxv, nrm, R, active);
   TM_LAUNCHED(ctx);
@@ -351,7 +353,7 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
           dots_kernel<VR><<<dim3(nb, R), RED_THREADS, 0, ctx->stream>>>(V, (int64_t)R * n, j + 1, w, n, rs, part,
                                                                          maxv, s.active);
           TM_LAUNCHED(ctx);
-          reduce_kernel<<<R, 64, 0, ctx->stream>>>(part, nb, j + 1, maxv, hc, s.active);
+          reduce_kernel<<<dim3(R, (unsigned)cdiv(j + 1, 128)), 128, 0, ctx->stream>>>(part, nb, j + 1, maxv, hc, s.active);
           TM_LAUNCHED(ctx);
           update_kernel<VR, VR><<<dim3(g1, R), 256, 0, ctx->stream>>>(V, (int64_t)R * n, j + 1, hc, maxv, -1.0, w, n,
                                                                       rs, s.active, nullptr);
@@ -417,7 +419,7 @@ int solve_system(tmat_ctx* ctx, const Operator& A64, const Operator* A32, int mo
                  const SolveParams& p, SolveStats* st) {
   const int64_t n = A64.N() * num_coeffs(A64.nmax());
   GmresParams gp;
-  gp.restart = std::max(2, std::min(p.restart, 64));
+  gp.restart = std::max(2, std::min(p.restart, 1024));
   gp.max_iter = p.max_iter;
   if (p.precision == TMAT_PREC_FP64 || !A32) {
     gp.tol = p.tol;

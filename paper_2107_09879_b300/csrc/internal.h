@@ -56,6 +56,9 @@ struct DevBuf {
 }  // namespace tmat
 
 struct tmat_ctx {
+  // kernel timing (off by default): event pairs recorded around operator launches
+  bool timing = false;
+  std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> timed;
   int device = 0;
   cudaStream_t stream = nullptr;
   char err[512] = {0};
@@ -87,6 +90,11 @@ int cuda_fail(tmat_ctx* ctx, cudaError_t e, const char* what, const char* file, 
     int _rc = (x);                  \
     if (_rc != TMAT_OK) return _rc; \
   } while (0)
+
+// Kernel timing: returns a start event (or nullptr when timing is off) and
+// records the matching stop event after the launch.
+cudaEvent_t timing_begin(tmat_ctx* ctx);
+void timing_end(tmat_ctx* ctx, const char* kind, cudaEvent_t start);
 
 // Grow-only scratch owned by the context, keyed by name.
 int scratch(tmat_ctx* ctx, const char* name, size_t bytes, void** out);

@@ -24,9 +24,9 @@ namespace tmat {
 // BT[k][c][u'][u] = e^{i(m_u' - m_u) phi} sum_q G[c][u][u'][q] h_q(k rho), with
 // d = x_target - x_source = -(dx, dy) * pitch, rho = |d|, phi = angle of d.
 template <int NMAX>
-__global__ void lattice_blocks_kernel(const int2* __restrict__ off, int K, double pitch, double k,
-                                      const double2* __restrict__ G, const int* __restrict__ mval, int LP,
-                                      double2* __restrict__ B64, float2* __restrict__ B32) {
+__global__ void lattice_blocks_kernel(const int2* __restrict__ off, int K, double pitch, double k, double cutoff,
+                                      double taper, const double2* __restrict__ G, const int* __restrict__ mval,
+                                      int LP, double2* __restrict__ B64, float2* __restrict__ B32) {
   constexpr int L = NMAX * (NMAX + 2), Q = 2 * NMAX + 1;
   __shared__ double2 h[Q];
   __shared__ double2 eph[2 * (2 * NMAX) + 1];  // e^{i mu phi}, mu = -2NMAX..2NMAX
@@ -46,6 +46,7 @@ __global__ void lattice_blocks_kernel(const int2* __restrict__ off, int K, doubl
     }
   }
   __syncthreads();
+  const double wgt = taper_weight(rho, cutoff, taper);
   for (int e = threadIdx.x; e < 2 * L * L; e += blockDim.x) {
     const int c = e / (L * L), u = (e / L) % L, up = e % L;
     const double2* g = G + ((size_t)(c * L + u) * L + up) * Q;
@@ -53,7 +54,7 @@ __global__ void lattice_blocks_kernel(const int2* __restrict__ off, int K, doubl
 #pragma unroll
     for (int q = 0; q < Q; ++q) cfma(acc, g[q], h[q]);
     const int mu = mval[c * L + up] - mval[c * L + u];
-    acc = cmul(acc, eph[2 * NMAX + mu]);
+    acc = cscale(cmul(acc, eph[2 * NMAX + mu]), wgt);
     const size_t o = (((size_t)kk * 2 + c) * L + up) * LP + u;
     B64[o] = acc;
     if (B32) B32[o] = to_c64(acc);
@@ -167,9 +168,11 @@ static int launch_lat(tmat_ctx* ctx, const LatOp& a, const void* x, void* y, int
   if (smem > 48 * 1024) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
+  cudaEvent_t ev = timing_begin(ctx);
   kern<<<grid, LAT_THREADS, smem, ctx->stream>>>(a.off, a.neg, a.K, a.nx, a.ny, a.N, (const C<R>*)a.BT, a.LP,
                                                   (const C<R>*)a.T, (const C<R>*)x, (C<R>*)y, rstride);
   TM_LAUNCHED(ctx);
+  timing_end(ctx, sizeof(R) == 4 ? "lattice_apply_fp32" : "lattice_apply_fp64", ev);
   return TMAT_OK;
 }
 
@@ -219,7 +222,8 @@ __global__ void lattice_check_kernel(const double* __restrict__ pos, int64_t N, 
 }
 
 int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_t N, double k, int nx, int ny,
-                     double pitch, double cutoff, const double2* T64, const float2* T32, bool mixed, OpPair* ops) {
+                     double pitch, double cutoff, double taper, const double2* T64, const float2* T32, bool mixed,
+                     OpPair* ops) {
   if (nx <= 0 || ny <= 0 || (int64_t)nx * ny != N || !(pitch > 0))
     return set_error(ctx, TMAT_EINVAL, "lattice path: need lattice_nx * lattice_ny == N and pitch > 0");
   {
@@ -267,7 +271,7 @@ int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_
     if (B32) TM_CUDA(ctx, cudaMemsetAsync(B32, 0, sizeof(float2) * (size_t)K * 2 * L * LP, ctx->stream));
     switch (t->nmax) {
 #define LB(NM) \
-  case NM: lattice_blocks_kernel<NM><<<K, 256, 0, ctx->stream>>>(d_off, K, pitch, k, t->d_gdense, t->d_mval, LP, B64, B32); break;
+  case NM: lattice_blocks_kernel<NM><<<K, 256, 0, ctx->stream>>>(d_off, K, pitch, k, cutoff, taper, t->d_gdense, t->d_mval, LP, B64, B32); break;
       LB(1) LB(2) LB(3) LB(4) LB(5) LB(6)
 #undef LB
     }
@@ -305,3 +309,53 @@ int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_
 }
 
 }  // namespace tmat
+
+using namespace tmat;
+
+extern "C" int tmat_apply_lattice(tmat_ctx* ctx, int op, int precision, int nx, int ny, double pitch, double cutoff,
+                                  double taper, double k, int nmax, const tmat_c128* T_diag, const tmat_c128* x, int R,
+                                  tmat_c128* y) {
+  if (!ctx) return TMAT_EINVAL;
+  const int64_t N = (int64_t)nx * ny;
+  if (nx < 0 || ny < 0 || R < 1 || !(k > 0) || !(pitch > 0) || !(taper >= 0) || (taper > 0 && !(taper <= cutoff)) || (N > 0 && (!x || !y)) || op < 0 || op > 2 ||
+      (op != TMAT_OP_COUPLE && N > 0 && !T_diag) || (precision != TMAT_PREC_FP64 && precision != TMAT_PREC_MIXED))
+    return set_error(ctx, TMAT_EINVAL, "tmat_apply_lattice: bad arguments");
+  Tables* t;
+  TM_TRY(get_tables(ctx, nmax, &t));
+  TM_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (N == 0) return TMAT_OK;
+  const int P = t->P;
+  const bool fp32 = precision == TMAT_PREC_MIXED;
+  Staged sT, sx, sy;
+  TM_TRY(stage_in(ctx, "st_T", T_diag, sizeof(double2) * N * P, &sT));
+  TM_TRY(stage_in(ctx, "st_x", x, sizeof(double2) * R * N * P, &sx));
+  TM_TRY(stage_out(ctx, "st_y", y, sizeof(double2) * R * N * P, &sy));
+  // implied positions (origin 0) for the lattice check
+  std::vector<double> hpos(3 * N);
+  for (int64_t i = 0; i < N; ++i) {
+    hpos[3 * i] = (double)(i % nx) * pitch;
+    hpos[3 * i + 1] = (double)(i / nx) * pitch;
+    hpos[3 * i + 2] = 0.0;
+  }
+  double* dpos;
+  TM_TRY(scratch(ctx, "al_pos", sizeof(double) * 3 * N, (void**)&dpos));
+  TM_CUDA(ctx, cudaMemcpyAsync(dpos, hpos.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice, ctx->stream));
+  void *T64 = nullptr, *T32 = nullptr;
+  if (T_diag) {
+    TM_TRY(prepare_T(ctx, t, (const double2*)sT.dev, N, false, "al_T64", &T64));
+    if (fp32) TM_TRY(prepare_T(ctx, t, (const double2*)sT.dev, N, true, "al_T32", &T32));
+  }
+  OpPair ops;
+  TM_TRY(make_lattice_ops(ctx, t, dpos, N, k, nx, ny, pitch, cutoff, taper, (const double2*)T64, (const float2*)T32, fp32,
+                          &ops));
+  const size_t esz = fp32 ? sizeof(float2) : sizeof(double2);
+  void *xi, *yi;
+  TM_TRY(scratch(ctx, "ap_x", esz * R * N * P, &xi));
+  TM_TRY(scratch(ctx, "ap_y", esz * R * N * P, &yi));
+  TM_TRY(to_internal(ctx, t, (const double2*)sx.dev, xi, fp32, (int64_t)R * N));
+  TM_TRY(op_apply(ctx, fp32 ? ops.A32 : ops.A64, op, xi, yi, R));
+  TM_TRY(from_internal(ctx, t, yi, fp32, (double2*)sy.dev, (int64_t)R * N));
+  TM_TRY(finish_out(ctx, &sy));
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return TMAT_OK;
+}

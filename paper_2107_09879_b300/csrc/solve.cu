@@ -14,6 +14,7 @@ struct tmat_solution {
   tmat::SolveParams params;
   int path = TMAT_PATH_NEIGHBOUR;
   double cutoff = 0;
+  double taper = 0;
   int lattice_nx = 0, lattice_ny = 0;
   double lattice_pitch = 0;
   // owned device copies (internal layout where coefficients)
@@ -80,8 +81,11 @@ static void free_solution(tmat_solution* s) {
 
 
 static int make_nbr_ops(const Tables* t, const double* d_pos, int64_t N, double k, int nmax, const int64_t* rp,
-                        const int32_t* col, const double2* T64, const float2* T32, bool mixed, OpPair* ops) {
+                        const int32_t* col, double cutoff, double taper, const double2* T64, const float2* T32,
+                        bool mixed, OpPair* ops) {
   NbrOp a;
+  a.cutoff = cutoff;
+  a.taper = taper;
   a.pos = d_pos;
   a.N = N;
   a.k = k;
@@ -121,6 +125,8 @@ extern "C" int tmat_solve(tmat_ctx* ctx, const double* pos, int64_t N, double wa
   if (N < 0 || R < 1 || R > TMAT_MAX_RHS || !opts || !(wavelength > 0) || !(n_bg > 0) ||
       (N > 0 && (!pos || !T_diag || !a0 || !s_out)))
     return set_error(ctx, TMAT_EINVAL, "tmat_solve: bad arguments (R must be 1..%d)", TMAT_MAX_RHS);
+  if (!(opts->taper >= 0) || (opts->taper > 0 && !(opts->taper <= opts->cutoff)))
+    return set_error(ctx, TMAT_EINVAL, "tmat_solve: taper must be in [0, cutoff]");
   if (opts->precision != TMAT_PREC_FP64 && opts->precision != TMAT_PREC_MIXED)
     return set_error(ctx, TMAT_EINVAL, "tmat_solve: unknown precision %d", opts->precision);
   Tables* t;
@@ -167,11 +173,11 @@ extern "C" int tmat_solve(tmat_ctx* ctx, const double* pos, int64_t N, double wa
     TM_TRY(build_neighbors(ctx, (const double*)spos.dev, N, opts->cutoff, rp, nullptr, &nnz));
     TM_TRY(scratch(ctx, "sv_col", sizeof(int32_t) * (nnz + 1), (void**)&col));
     TM_TRY(build_neighbors(ctx, (const double*)spos.dev, N, opts->cutoff, rp, col, &nnz));
-    TM_TRY(make_nbr_ops(t, (const double*)spos.dev, N, k, nmax, rp, col, (const double2*)T64, (const float2*)T32,
-                        mixed, &ops));
+    TM_TRY(make_nbr_ops(t, (const double*)spos.dev, N, k, nmax, rp, col, opts->cutoff, opts->taper,
+                        (const double2*)T64, (const float2*)T32, mixed, &ops));
   } else {
     TM_TRY(make_lattice_ops(ctx, t, (const double*)spos.dev, N, k, opts->lattice_nx, opts->lattice_ny,
-                            opts->lattice_pitch, opts->cutoff, (const double2*)T64, (const float2*)T32, mixed, &ops));
+                            opts->lattice_pitch, opts->cutoff, opts->taper, (const double2*)T64, (const float2*)T32, mixed, &ops));
   }
   // b = T a0 (internal layout)
   double2 *a0i, *b, *x;
@@ -195,6 +201,7 @@ extern "C" int tmat_solve(tmat_ctx* ctx, const double* pos, int64_t N, double wa
     so->params = sp;
     so->path = path;
     so->cutoff = opts->cutoff;
+    so->taper = opts->taper;
     so->lattice_nx = opts->lattice_nx;
     so->lattice_ny = opts->lattice_ny;
     so->lattice_pitch = opts->lattice_pitch;
@@ -252,10 +259,11 @@ extern "C" int tmat_adjoint(tmat_ctx* ctx, const tmat_solution* sol, const tmat_
   const bool mixed = sol->params.precision == TMAT_PREC_MIXED;
   OpPair ops;
   if (sol->path == TMAT_PATH_NEIGHBOUR) {
-    TM_TRY(make_nbr_ops(t, sol->pos, N, sol->k, sol->nmax, sol->row_ptr, sol->col, sol->T64, sol->T32, mixed, &ops));
+    TM_TRY(make_nbr_ops(t, sol->pos, N, sol->k, sol->nmax, sol->row_ptr, sol->col, sol->cutoff, sol->taper, sol->T64,
+                        sol->T32, mixed, &ops));
   } else {
     TM_TRY(make_lattice_ops(ctx, t, sol->pos, N, sol->k, sol->lattice_nx, sol->lattice_ny, sol->lattice_pitch,
-                            sol->cutoff, sol->T64, sol->T32, mixed, &ops));
+                            sol->cutoff, sol->taper, sol->T64, sol->T32, mixed, &ops));
   }
   double2 *vi, *mu, *dTi, *As;
   TM_TRY(scratch(ctx, "adj_v", sizeof(double2) * N * P, (void**)&vi));

@@ -78,5 +78,6 @@ struct OpPair {
   LatOp lat64, lat32;
 };
 int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_t N, double k, int nx, int ny,
-                     double pitch, double cutoff, const double2* T64, const float2* T32, bool mixed, OpPair* ops);
+                     double pitch, double cutoff, double taper, const double2* T64, const float2* T32, bool mixed,
+                     OpPair* ops);
 }  // namespace tmat

@@ -1,0 +1,94 @@
+"""GPU parity of the lattice (one block per lattice offset) path against the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_common import K0, atoms, ctx, rand_c, rel_l2
+from oracle import geometry, mie, system
+from paper_2107_09879_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("nmax,nx,ny,cutoff,R", [(3, 13, 11, 1.6, 1), (4, 9, 7, 1.2, 2), (2, 6, 5, 0.0, 3),
+                                                 (5, 5, 4, 1.1, 5), (6, 4, 3, 0.8, 2), (1, 17, 9, 2.0, 1)])
+@pytest.mark.parametrize("op", [0, 1, 2])
+def test_lattice_apply_vs_oracle(nmax, nx, ny, cutoff, R, op):
+    pos = W.lattice_positions(nx, ny)
+    r = W.uniform_radii(nx * ny, 0.08, 0.24, 40 + nmax)
+    T = np.array([mie.tmatrix_diag(nmax, K0, x, 2.0) for x in r])
+    x = rand_c((R, nx * ny, T.shape[1]), 50 + nmax)
+    nbr = geometry.neighbours(pos, cutoff)
+    f = [system.apply_K, system.apply_KT, lambda nm, k, p, t, v, nb: system.apply_A(nm, k, p, v, nb)][op]
+    ref = np.array([f(nmax, K0, pos, T, x[q], nbr) for q in range(R)])
+    y64 = ctx().tmat_apply_lattice(op, 0, nx, ny, 0.5, cutoff, K0, nmax, T, x)
+    y32 = ctx().tmat_apply_lattice(op, 1, nx, ny, 0.5, cutoff, K0, nmax, T, x)
+    assert rel_l2(y64, ref) <= 1e-12
+    assert rel_l2(y32, ref) <= 2e-6
+
+
+def test_lattice_matches_neighbour_path_bitwise_structure():
+    """Same interaction set as the neighbour list on a lattice: both paths agree to rounding."""
+    nx, ny, nmax, cutoff = 20, 17, 4, 3.0
+    pos = W.lattice_positions(nx, ny)
+    r = W.uniform_radii(nx * ny, 0.08, 0.24, 3)
+    T = ctx().tmat_build(atoms(r), 1.0, 1.0, nmax)
+    x = rand_c((2, nx * ny, 48), 9)
+    rp, col = ctx().tmat_neighbors(pos, cutoff)
+    for op in range(3):
+        a = ctx().tmat_apply(op, 0, pos, K0, nmax, T, rp, col, x)
+        b = ctx().tmat_apply_lattice(op, 0, nx, ny, 0.5, cutoff, K0, nmax, T, x)
+        assert rel_l2(b, a) <= 1e-13
+
+
+@pytest.mark.parametrize("precision,tol,bound", [(0, 1e-11, 1e-9), (1, 1e-8, 1e-6)])
+def test_lattice_solve_vs_oracle(precision, tol, bound):
+    from paper_2107_09879_b300 import _lib
+    nx, ny, nmax, cutoff = 8, 7, 4, 1.6
+    pos = W.lattice_positions(nx, ny)
+    r = W.uniform_radii(nx * ny, 0.08, 0.24, 12)
+    T = ctx().tmat_build(atoms(r), 1.0, 1.0, nmax)
+    dirs = np.array([[0.0, 0.0], [math.radians(10), 0.0]])
+    pols = np.array([[1, 0, 0], [math.cos(math.radians(10)), 0, -math.sin(math.radians(10))]], dtype=complex)
+    a0 = ctx().tmat_incident_planewave(pos, 1.0, 1.0, nmax, dirs, pols)
+    opts = _lib.make_opts(tol=tol, cutoff=cutoff, precision=precision, path=2, lattice_nx=nx, lattice_ny=ny,
+                          lattice_pitch=0.5)
+    s, info, _, rc = ctx().tmat_solve(pos, 1.0, 1.0, nmax, T, a0, opts)
+    assert rc == 0 and info.converged
+    To = np.array([mie.tmatrix_diag(nmax, K0, x, 2.0) for x in r])
+    for q in range(2):
+        ref = system.solve_dense(nmax, K0, pos, To, a0[q], cutoff)
+        assert rel_l2(s[q], ref) <= bound
+
+
+def test_lattice_adjoint_matches_neighbour_adjoint():
+    from paper_2107_09879_b300 import _lib
+    nx, ny, nmax, cutoff = 7, 6, 3, 1.3
+    pos = W.lattice_positions(nx, ny)
+    r = W.uniform_radii(nx * ny, 0.1, 0.22, 17)
+    T, dT = ctx().tmat_build(atoms(r), 1.0, 1.0, nmax, with_dr=True)
+    A = np.array([[1, 0, 0]], dtype=complex)
+    a0 = ctx().tmat_incident_planewave(pos, 1.0, 1.0, nmax, np.array([[0.0, 0.0]]), A)
+    xf = np.array([1.5, 1.25, 4.0])
+    grads = []
+    for path in (1, 2):
+        opts = _lib.make_opts(tol=1e-12, cutoff=cutoff, precision=0, path=path, lattice_nx=nx, lattice_ny=ny,
+                              lattice_pitch=0.5)
+        s, info, sol, rc = ctx().tmat_solve(pos, 1.0, 1.0, nmax, T, a0, opts, keep=True)
+        fom, v = ctx().tmat_point_fom(pos, 1.0, 1.0, nmax, s[0], xf, np.exp(1j * 2 * np.pi * 4.0) * A[0])
+        g, mu, info = ctx().tmat_adjoint(sol, v, dT)
+        grads.append(g)
+    assert rel_l2(grads[1], grads[0]) <= 1e-10
+
+
+def test_lattice_rejects_non_lattice_positions():
+    from paper_2107_09879_b300 import _lib
+    pos = W.lattice_positions(4, 4).copy()
+    pos[5, 0] += 0.01
+    T = ctx().tmat_build(atoms(np.full(16, 0.1)), 1.0, 1.0, 2)
+    a0 = np.ones((1, 16, 16), complex)
+    opts = _lib.make_opts(tol=1e-8, path=2, lattice_nx=4, lattice_ny=4, lattice_pitch=0.5)
+    with pytest.raises(_lib.TMatError) as e:
+        ctx().tmat_solve(pos, 1.0, 1.0, 2, T, a0, opts)
+    assert e.value.code == _lib.EINVAL

@@ -163,3 +163,17 @@ def test_subregions_partition():
         assert np.all(np.isin(core, sim))
     # interior sub-region: (6 + 4) x (5 + 4) sites
     assert len(sets[1 * 4 + 1][1]) == 10 * 9
+
+
+def test_coupling_window_definition():
+    """The window is 1 inside cutoff - taper, 1/2 at the taper midpoint, 0 at the
+    cutoff, and scales every block of a pair by the same factor."""
+    w = system.coupling_weight
+    assert w(1.0, 8.0, 2.0) == 1.0 and w(8.0, 8.0, 2.0) == 0.0
+    assert abs(w(7.0, 8.0, 2.0) - 0.5) < 1e-15 and w(3.0, 8.0, 0.0) == 1.0
+    assert abs(w(4.0, 8.0, 8.0) - 0.5) < 1e-15
+    pos = W.lattice_positions(3, 1)
+    B0 = system._block(3, K0, pos[0], pos[2])
+    with system.window(2.0, 2.0):
+        B1 = system._block(3, K0, pos[0], pos[2])
+    assert np.allclose(B1, B0 * 0.5 * (1 + math.cos(math.pi * 1.0 / 2.0)), rtol=0, atol=1e-15)
