@@ -254,6 +254,37 @@ int tmat_adjoint(tmat_ctx* ctx, const tmat_solution* sol, const tmat_c128* v,
                  const tmat_c128* dTdr, double* grad_out, tmat_c128* mu_out,
                  tmat_solve_info* info);
 
+/* ---- allocation-free variant (no counterpart in the paper) ------------------ */
+
+/* Capacity of the fixed device scratch of tmat_field_noalloc, in complex
+ * partial sums; a call needs 3 * M of them, so M <= TMAT_NOALLOC_FIELD_SLOTS / 3. */
+#define TMAT_NOALLOC_FIELD_SLOTS 65536
+
+/* Scattered field like tmat_field, for callers that must not allocate device
+ * memory during a call: code that runs inside another framework's fixed device
+ * memory budget, or in a loop where a cudaMalloc/cudaFree (which may
+ * synchronise the whole device and stall work on other streams) is not
+ * acceptable. It takes no context, allocates nothing (no cudaMalloc, cudaFree
+ * or pinned host memory) and uses a fixed 1 MiB scratch array that lives in the
+ * library's device image (every GPU that loads the library keeps it until the
+ * process exits).
+ *  - All array arguments must be device pointers on the current device; host
+ *    pointers are rejected with TMAT_EINVAL. Work is issued on `cuda_stream`
+ *    (a cudaStream_t of the current device, NULL = legacy default stream); the
+ *    call does not synchronise.
+ *  - M above TMAT_NOALLOC_FIELD_SLOTS / 3 points, N < 0, nmax outside
+ *    1..TMAT_NMAX_MAX or a bad pointer returns TMAT_EINVAL before any work is
+ *    issued (there is no context, so there is no error message).
+ *  - The first call on each device looks up the scratch array's device address
+ *    (a one-time set-up per device); make that first call before any stream
+ *    capture begins.
+ *  - All calls on one device share its scratch array: two calls whose work
+ *    overlaps on that GPU (for example on two streams) race and give wrong
+ *    results; order them (one stream, or events). Every scratch slot a call
+ *    reads is written earlier in the same call, so nothing needs clearing. */
+int tmat_field_noalloc(void* cuda_stream, const double* pos, int64_t N, double wavelength, double n_bg,
+                       int nmax, const tmat_c128* s, const double* pts, int64_t M, tmat_c128* E_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,7 @@ _SIGS = {
     "tmat_field": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _i64, _vp],
     "tmat_farfield": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _i64, _vp],
     "tmat_point_fom": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _vp, ct.POINTER(_d), _vp],
+    "tmat_field_noalloc": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _i64, _vp],
     "tmat_adjoint": [_vp, _vp, _vp, _vp, _vp, _vp, ct.POINTER(SolveInfo)],
 }
 EXPORTED = []
@@ -76,6 +77,7 @@ for _name, _args in _SIGS.items():
         f.restype = ct.c_int
         EXPORTED.append(_name)
 lib.tmat_last_error.restype = ct.c_char_p
+NOALLOC_FIELD_SLOTS = 65536
 lib.tmat_ctx_launch_count.restype = ct.c_int64
 
 

@@ -273,3 +273,65 @@ extern "C" int tmat_point_fom(tmat_ctx* ctx, const double* pos, int64_t N, doubl
   *fom_out = f;
   return TMAT_OK;
 }
+
+// ---- allocation-free variant ------------------------------------------------------
+// The partial sums of field_kernel live in this fixed array instead of context
+// scratch. Host code must not pass `g_field_noalloc_part` itself to a kernel
+// (on the host it names a stand-in, not the device memory): the device address
+// is looked up once per device with cudaGetSymbolAddress.
+#include <mutex>
+
+static __device__ __align__(256) double2 g_field_noalloc_part[TMAT_NOALLOC_FIELD_SLOTS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double2* g_noalloc_addr[kMaxDevices] = {nullptr};
+
+// device address of the scratch array on the current device (one-time set-up)
+int noalloc_scratch(int dev, double2** out) {
+  if (dev < 0 || dev >= kMaxDevices) return TMAT_EINVAL;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_field_noalloc_part);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return TMAT_ECUDA;
+    }
+    g_noalloc_addr[dev] = (double2*)p;
+  }
+  *out = g_noalloc_addr[dev];
+  return TMAT_OK;
+}
+}  // namespace
+
+extern "C" int tmat_field_noalloc(void* cuda_stream, const double* pos, int64_t N, double wavelength, double n_bg,
+                                  int nmax, const tmat_c128* s, const double* pts, int64_t M, tmat_c128* E_out) {
+  if (N < 0 || M < 0 || M > TMAT_NOALLOC_FIELD_SLOTS / 3 || nmax < 1 || nmax > TMAT_NMAX_MAX ||
+      !(wavelength > 0) || !(n_bg > 0))
+    return TMAT_EINVAL;
+  if (M == 0) return TMAT_OK;
+  if (!is_device_ptr(pts) || !is_device_ptr(E_out) || (N > 0 && (!is_device_ptr(pos) || !is_device_ptr(s))))
+    return TMAT_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return TMAT_ECUDA;
+  }
+  double2* part = nullptr;
+  int rc = noalloc_scratch(dev, &part);
+  if (rc != TMAT_OK) return rc;
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t nchunk = std::min<int64_t>(cdiv(N, 128), std::max<int64_t>(1, 4 * sms / M));
+  nchunk = std::min<int64_t>(nchunk, TMAT_NOALLOC_FIELD_SLOTS / (3 * M));
+  nchunk = std::max<int64_t>(1, std::min<int64_t>(nchunk, 65535));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const double k = 2.0 * M_PI * n_bg / wavelength;
+  field_kernel<<<dim3((unsigned)M, (unsigned)nchunk), 128, 0, st>>>(pos, N, k, nmax, (const double2*)s, pts, M, 0,
+                                                                     part);
+  field_reduce_kernel<<<(unsigned)cdiv(M * 3, 128), 128, 0, st>>>(part, M, (int)nchunk, (double2*)E_out);
+  if (cudaGetLastError() != cudaSuccess) return TMAT_ECUDA;
+  return TMAT_OK;
+}
