@@ -263,6 +263,33 @@ def run_ours(args, rank, world):
     return out
 
 
+def run_kernel_only(args):
+    """The dominant kernel alone, in the launch configuration the solve uses
+    (complex64 lattice apply, both incidences per launch): for ncu captures and
+    kernel tuning. Holds well under 1 GB on the device."""
+    import torch
+    from paper_2107_09879_b300 import _lib
+    ctx = _lib.Context(0, None)
+    wl = workload()
+    w = wl["w"]
+    N, P, R = len(wl["pos"]), 48, 2
+    T = ctx.tmat_build(torch.from_numpy(wl["atoms"]).cuda(), 1.0, 1.0, w["nmax"])
+    g = torch.Generator(device="cpu").manual_seed(0)
+    x = (torch.randn(R, N, P, dtype=torch.complex128, generator=g) * 0.1).cuda()
+    ctx.set_timing(True)
+    for k in range(args.warmup + args.steps):
+        if k == args.warmup:
+            ctx.set_timing(True)
+        y = ctx.tmat_apply_lattice(_lib.OP_FORWARD, args.kernel_precision, 200, 200, PITCH, w["cutoff"], 2 * math.pi,
+                                   w["nmax"], T, x, taper=w["cutoff"])
+    kind = "lattice_apply_fp32" if args.kernel_precision == _lib.PREC_MIXED else "lattice_apply_fp64"
+    n, ms = ctx.kernel_time(kind)
+    pairs = pairs_within(200, 200, int(round(w["cutoff"] / PITCH)))
+    flop = 8.0 * (P * P / 2) * pairs * R
+    return {"kernel": kind, "launches": n, "avg_ms": ms / max(n, 1), "tflops": flop / (ms / max(n, 1) * 1e-3) / 1e12,
+            "flop_per_launch": flop, "y_norm": float(torch.linalg.vector_norm(y).item())}
+
+
 def run_reference(args, rank, world):
     """The reference arm: the oracle (plain fp64 CPU), timed on the host cores."""
     if rank != 0:
@@ -290,10 +317,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-matvecs", type=int, default=60, help="operator applications per solve for the oracle arm")
+    ap.add_argument("--ref-matvecs", type=int, default=276, help="operator applications per solve for the oracle arm")
+    ap.add_argument("--kernel-only", action="store_true", help="time the dominant kernel alone (for ncu captures)")
+    ap.add_argument("--kernel-precision", type=int, default=1, help="1: complex64 apply, 0: complex128 apply")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.kernel_only:
+        print(json.dumps(run_kernel_only(args)))
+        return
     if args.impl == "reference":
         if world > 1 and rank != 0:
             return
