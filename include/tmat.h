@@ -129,6 +129,10 @@ int64_t tmat_ctx_launch_count(const tmat_ctx* ctx);
  * kind since timing was (re)enabled: "lattice_apply_fp32", "lattice_apply_fp64",
  * "nbr_apply_fp32", "nbr_apply_fp64". Enabling again resets the record. */
 int tmat_ctx_set_timing(tmat_ctx* ctx, int enable);
+/* Complex64 lattice applies run on the tcgen05 tensor cores (3xTF32, nmax <= 4)
+ * unless disabled here (then the CUDA-core fp32 kernel runs). Default: enabled.
+ * Timing kind of the tensor-core kernel: "lattice_apply_tc". */
+int tmat_ctx_set_tensor_cores(tmat_ctx* ctx, int enable);
 int tmat_ctx_kernel_time(tmat_ctx* ctx, const char* kind, int64_t* launches, double* total_ms);
 
 /* ---- geometry (integer, bit-exact) -------------------------------------- */

@@ -12,7 +12,7 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libtmat.so")
+LIB_PATH = os.environ.get("TMAT_LIB") or os.path.join(_HERE, "libtmat.so")
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_2107_09879_b300.build`")
 lib = ct.CDLL(LIB_PATH)
@@ -52,6 +52,7 @@ _SIGS = {
     "tmat_last_error": [_vp],
     "tmat_ctx_launch_count": [_vp],
     "tmat_ctx_set_timing": [_vp, _int],
+    "tmat_ctx_set_tensor_cores": [_vp, _int],
     "tmat_ctx_kernel_time": [_vp, ct.c_char_p, ct.POINTER(_i64), ct.POINTER(_d)],
     "tmat_neighbors": [_vp, _vp, _i64, _d, _vp, _vp, ct.POINTER(_i64)],
     "tmat_subregions": [_vp, _i64, _i64, _i64, _i64, _i64, _vp, _vp, _vp, _vp, ct.POINTER(_i64), ct.POINTER(_i64)],
@@ -134,6 +135,9 @@ class Context:
 
     def launches(self):
         return lib.tmat_ctx_launch_count(self.h)
+
+    def set_tensor_cores(self, on):
+        self.check(lib.tmat_ctx_set_tensor_cores(self.h, 1 if on else 0))
 
     def set_timing(self, on):
         self.check(lib.tmat_ctx_set_timing(self.h, 1 if on else 0))

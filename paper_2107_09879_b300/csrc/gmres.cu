@@ -72,7 +72,112 @@ dots_kernel(const C<VR>* __restrict__ V, int64_t vstride, int nvec, const C<VR>*
   }
 }
 
-// out[r*maxv + k] = sum_b part[...] (fixed order); if add_to, out += that
+
+// ---- complex64 vectors: fp32 products, fp64 accumulation across blocks --------
+// B300 runs fp64 FMAs at ~1/75 of the fp32 rate, so the per-element products of
+// the complex64 Krylov vectors are done in fp32 (each thread sums a few hundred
+// terms), and only the per-block partials are summed in fp64.
+constexpr int DOT32_CHUNK = 16;
+
+__global__ void __launch_bounds__(RED_THREADS)
+dots32_kernel(const float2* __restrict__ V, int64_t vstride, int nvec, const float2* __restrict__ w, int64_t n,
+              int64_t rstride, double2* __restrict__ part, int maxv, const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  __shared__ double2 red[RED_THREADS / 32][DOT32_CHUNK];
+  const int nb = gridDim.x, b = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t n2 = n >> 1;  // float4 = two complex values (n is even)
+  const float4* w4 = reinterpret_cast<const float4*>(w + r * rstride);
+  for (int k0 = 0; k0 < nvec; k0 += DOT32_CHUNK) {
+    float2 acc[DOT32_CHUNK];
+#pragma unroll
+    for (int c = 0; c < DOT32_CHUNK; ++c) acc[c] = make_float2(0.f, 0.f);
+    for (int64_t i = (int64_t)b * blockDim.x + threadIdx.x; i < n2; i += (int64_t)nb * blockDim.x) {
+      const float4 wv = w4[i];
+#pragma unroll
+      for (int c = 0; c < DOT32_CHUNK; ++c) {
+        if (k0 + c < nvec) {
+          const float4 v = reinterpret_cast<const float4*>(V + (int64_t)(k0 + c) * vstride + r * rstride)[i];
+          // conj(v) w for both complex values
+          acc[c].x = fmaf(v.x, wv.x, fmaf(v.y, wv.y, fmaf(v.z, wv.z, fmaf(v.w, wv.w, acc[c].x))));
+          acc[c].y = fmaf(v.x, wv.y, fmaf(-v.y, wv.x, fmaf(v.z, wv.w, fmaf(-v.w, wv.z, acc[c].y))));
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < DOT32_CHUNK; ++c) {
+      double2 v = make_double2(acc[c].x, acc[c].y);
+      for (int o = 16; o > 0; o >>= 1) {
+        double2 t = shfl_down2(v, o);
+        v.x += t.x;
+        v.y += t.y;
+      }
+      if (lane == 0) red[warp][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < DOT32_CHUNK && k0 + threadIdx.x < nvec) {
+      double2 s = make_double2(0, 0);
+      for (int q = 0; q < RED_THREADS / 32; ++q) {
+        s.x += red[q][threadIdx.x].x;
+        s.y += red[q][threadIdx.x].y;
+      }
+      part[((int64_t)r * nb + b) * maxv + k0 + threadIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// w[r] += sign * sum_k V_k[r] coef[r][k] on complex64 vectors (fp32 arithmetic)
+__global__ void __launch_bounds__(256)
+update32_kernel(const float2* __restrict__ V, int64_t vstride, int nvec, const double2* __restrict__ coef, int maxv,
+                float sign, float2* __restrict__ out, int64_t n, int64_t rstride, const int* __restrict__ active,
+                const int* __restrict__ ncols) {
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  const int nv = ncols ? min(nvec, ncols[r]) : nvec;
+  extern __shared__ float2 cs[];  // coefficients of this RHS in fp32
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+    double2 c = coef[r * maxv + k];
+    cs[k] = make_float2((float)(sign * c.x), (float)(sign * c.y));
+  }
+  __syncthreads();
+  const int64_t n2 = n >> 1;
+  float4* o4 = reinterpret_cast<float4*>(out + r * rstride);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    int k = 0;
+    for (; k + 4 <= nv; k += 4) {
+      float4 v[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) v[t] = reinterpret_cast<const float4*>(V + (int64_t)(k + t) * vstride + r * rstride)[i];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const float2 c = cs[k + t];
+        a.x = fmaf(v[t].x, c.x, fmaf(-v[t].y, c.y, a.x));
+        a.y = fmaf(v[t].x, c.y, fmaf(v[t].y, c.x, a.y));
+        a.z = fmaf(v[t].z, c.x, fmaf(-v[t].w, c.y, a.z));
+        a.w = fmaf(v[t].z, c.y, fmaf(v[t].w, c.x, a.w));
+      }
+    }
+    for (; k < nv; ++k) {
+      const float4 v = reinterpret_cast<const float4*>(V + (int64_t)k * vstride + r * rstride)[i];
+      const float2 c = cs[k];
+      a.x = fmaf(v.x, c.x, fmaf(-v.y, c.y, a.x));
+      a.y = fmaf(v.x, c.y, fmaf(v.y, c.x, a.y));
+      a.z = fmaf(v.z, c.x, fmaf(-v.w, c.y, a.z));
+      a.w = fmaf(v.z, c.y, fmaf(v.w, c.x, a.w));
+    }
+    float4 o = o4[i];
+    o.x += a.x;
+    o.y += a.y;
+    o.z += a.z;
+    o.w += a.w;
+    o4[i] = o;
+  }
+}
+
+// out[r*maxv + k] = sum_b part[...] (fixed order)
 __global__ void reduce_kernel(const double2* __restrict__ part, int nb, int nvec, int maxv, double2* __restrict__ out,
                               const int* __restrict__ active) {
   const int r = blockIdx.x, k = blockIdx.y * blockDim.x + threadIdx.x;
@@ -281,7 +386,7 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
   const int m = p.restart;
   const int maxv = m + 1;
   const int64_t rs = n;  // RHS stride
-  const int nb = (int)std::min<int64_t>(cdiv(n, RED_THREADS), (int64_t)ctx->num_sms * 2);
+  const int nb = (int)std::min<int64_t>(cdiv(n, RED_THREADS), (int64_t)ctx->num_sms * 4);
   C<VR>* V;
   TM_TRY(scratch(ctx, sizeof(VR) == 4 ? "g_V32" : "g_V64", sizeof(C<VR>) * (size_t)maxv * R * n, (void**)&V));
   C<VR>* xv;  // x in operator precision (for the true residual)
@@ -350,13 +455,23 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
         TM_TRY(op_apply(ctx, A, mode, vj, w, R));
         for (int pass = 0; pass < 2; ++pass) {
           double2* hc = pass == 0 ? s.hA : s.hB;
-          dots_kernel<VR><<<dim3(nb, R), RED_THREADS, 0, ctx->stream>>>(V, (int64_t)R * n, j + 1, w, n, rs, part,
+          if constexpr (sizeof(VR) == 4) {
+            dots32_kernel<<<dim3(nb, R), RED_THREADS, 0, ctx->stream>>>(V, (int64_t)R * n, j + 1, w, n, rs, part,
                                                                          maxv, s.active);
+          } else {
+            dots_kernel<VR><<<dim3(nb, R), RED_THREADS, 0, ctx->stream>>>(V, (int64_t)R * n, j + 1, w, n, rs, part,
+                                                                           maxv, s.active);
+          }
           TM_LAUNCHED(ctx);
           reduce_kernel<<<dim3(R, (unsigned)cdiv(j + 1, 128)), 128, 0, ctx->stream>>>(part, nb, j + 1, maxv, hc, s.active);
           TM_LAUNCHED(ctx);
-          update_kernel<VR, VR><<<dim3(g1, R), 256, 0, ctx->stream>>>(V, (int64_t)R * n, j + 1, hc, maxv, -1.0, w, n,
-                                                                      rs, s.active, nullptr);
+          if constexpr (sizeof(VR) == 4) {
+            update32_kernel<<<dim3(g1, R), 256, sizeof(float2) * (j + 1), ctx->stream>>>(
+                V, (int64_t)R * n, j + 1, hc, maxv, -1.0f, w, n, rs, s.active, nullptr);
+          } else {
+            update_kernel<VR, VR><<<dim3(g1, R), 256, 0, ctx->stream>>>(V, (int64_t)R * n, j + 1, hc, maxv, -1.0, w, n,
+                                                                        rs, s.active, nullptr);
+          }
           TM_LAUNCHED(ctx);
         }
         TM_TRY(vec_norms<VR>(ctx, w, n, rs, R, part, nb, s.y, maxv, s.nrm, s.active));
@@ -438,7 +553,7 @@ int solve_system(tmat_ctx* ctx, const Operator& A64, const Operator* A32, int mo
   TM_TRY(scratch(ctx, "mx_d64", sizeof(double2) * R * n, (void**)&d64));
   TM_TRY(scratch(ctx, "mx_y64", sizeof(double2) * R * n, (void**)&y64));
   TM_TRY(scratch(ctx, "mx_r32", sizeof(float2) * R * n, (void**)&r32));
-  const int nb = (int)std::min<int64_t>(cdiv(n, RED_THREADS), (int64_t)ctx->num_sms * 2);
+  const int nb = (int)std::min<int64_t>(cdiv(n, RED_THREADS), (int64_t)ctx->num_sms * 4);
   double2 *part, *tmp;
   double *rn, *bn, *alpha;
   TM_TRY(scratch(ctx, "mx_part", sizeof(double2) * R * nb, (void**)&part));

@@ -66,6 +66,7 @@ struct tmat_ctx {
   std::map<int, tmat::Tables*> tables;
   std::map<std::string, tmat::DevBuf> bufs;
   int num_sms = 148;
+  bool tensor_cores = true;  // use the tcgen05 kernels where they exist
   void* pinned = nullptr;  // small pinned host staging area (status words)
 };
 

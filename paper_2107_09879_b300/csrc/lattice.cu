@@ -34,6 +34,15 @@ __global__ void lattice_blocks_kernel(const int2* __restrict__ off, int K, doubl
   if (kk >= K) return;
   const double dx = -(double)off[kk].x * pitch, dy = -(double)off[kk].y * pitch;
   const double rho = sqrt(dx * dx + dy * dy);
+  if (off[kk].x == 0 && off[kk].y == 0) {  // the self offset: no coupling
+    for (int e = threadIdx.x; e < 2 * L * L; e += blockDim.x) {
+      const int c = e / (L * L), u = (e / L) % L, up = e % L;
+      const size_t o = (((size_t)kk * 2 + c) * L + up) * LP + u;
+      B64[o] = make_double2(0, 0);
+      if (B32) B32[o] = make_float2(0.f, 0.f);
+    }
+    return;
+  }
   if (threadIdx.x == 0) {
     double2 hh[Q];
     hankel_up<double, Q>(k * rho, hh);
@@ -63,24 +72,28 @@ __global__ void lattice_blocks_kernel(const int2* __restrict__ off, int K, doubl
 
 // ---- apply -------------------------------------------------------------------
 constexpr int LAT_THREADS = 128;
+#ifndef LAT_MIN_BLOCKS
+#define LAT_MIN_BLOCKS 1  // resident blocks per SM the register budget is sized for
+#endif
 
 template <typename R> struct LatCfg;
 // outputs per thread so that UPT * NR complex accumulators stay ~<= 48 complex (fp32) / 24 (fp64)
 template <typename R, int L, int NR>
 struct Split {
-  static constexpr int budget = sizeof(R) == 4 ? 48 : 24;
+  static constexpr int budget = sizeof(R) == 4 ? 48 : 12;
   static constexpr int S = (L * NR + budget - 1) / budget;
   static constexpr int UPT = (L + S - 1) / S;
 };
 
 // MODE 0: y = x - T (A x); 1: y = x - A^T (T x); 2: y = A x
 template <typename R, int NMAX, int NR, int MODE>
-__global__ void __launch_bounds__(LAT_THREADS)
+__global__ void __launch_bounds__(LAT_THREADS, LAT_MIN_BLOCKS)
 lattice_apply_kernel(const int2* __restrict__ off, const int* __restrict__ neg, int K, int nx, int ny, int64_t N,
                      const C<R>* __restrict__ BT, int LP, const C<R>* __restrict__ T, const C<R>* __restrict__ x,
                      C<R>* __restrict__ y, int64_t rstride) {
   constexpr int L = NMAX * (NMAX + 2), P = 2 * L;
   constexpr int S = Split<R, L, NR>::S, UPT = Split<R, L, NR>::UPT;
+  static_assert(sizeof(R) == 8 || S == 1 || UPT % 2 == 0, "fp32 output split must keep 16-byte alignment");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<R>* sB = reinterpret_cast<C<R>*>(smem_raw);  // [2][L][LP]
   const int c = blockIdx.y / S, part = blockIdx.y % S;
@@ -128,12 +141,29 @@ lattice_apply_kernel(const int2* __restrict__ off, const int* __restrict__ neg, 
           if (MODE == 1) xv[r] = cmul(xv[r], T[j * P + c * L + up]);
         }
         const C<R>* brow = sb + up * LP + u0;
+        if constexpr (sizeof(R) == 4) {
+          // two complex block entries per 16-byte shared load (LP and u0 are even)
 #pragma unroll
-        for (int u = 0; u < UPT; ++u) {
-          if (u0 + u < L) {
-            const C<R> b = brow[u];
+          for (int u = 0; u < UPT; u += 2) {
+            const float4 bb = *reinterpret_cast<const float4*>(brow + u);
+            const C<R> b0 = mk<R>(bb.x, bb.y), b1 = mk<R>(bb.z, bb.w);
+            if (u0 + u < L) {
 #pragma unroll
-            for (int r = 0; r < NR; ++r) cfma(acc[r][u], b, xv[r]);
+              for (int r = 0; r < NR; ++r) cfma(acc[r][u], b0, xv[r]);
+            }
+            if (u + 1 < UPT && u0 + u + 1 < L) {
+#pragma unroll
+              for (int r = 0; r < NR; ++r) cfma(acc[r][u + 1], b1, xv[r]);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < UPT; ++u) {
+            if (u0 + u < L) {
+              const C<R> b = brow[u];
+#pragma unroll
+              for (int r = 0; r < NR; ++r) cfma(acc[r][u], b, xv[r]);
+            }
           }
         }
       }
@@ -198,6 +228,7 @@ static int lat_mode(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void
 
 int lattice_apply(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void* y, int R_) {
   if (a.N == 0) return TMAT_OK;
+  if (a.fp32 && a.use_tc && ctx->tensor_cores) return lattice_tc_apply(ctx, a, mode, x, y, R_);
   const int64_t rs = a.N * a.P;
   const size_t esz = a.fp32 ? sizeof(float2) : sizeof(double2);
   for (int r0 = 0; r0 < R_; r0 += 2) {
@@ -242,15 +273,30 @@ int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_
   const double c2 = cutoff * cutoff;
   for (int dy = -(ny - 1); dy <= ny - 1; ++dy)
     for (int dx = -(nx - 1); dx <= nx - 1; ++dx) {
-      if (dx == 0 && dy == 0) continue;
+      // (0, 0) stays in the list with an all-zero block (no self coupling): it keeps dx
+      // contiguous inside the dy = 0 group, which the tensor-core kernel relies on
       double ax = dx * pitch, ay = dy * pitch;
       volatile double d2 = ax * ax;
       volatile double d2b = ay * ay;
       double d2s = d2 + d2b;
-      if (cutoff > 0 && !(d2s <= c2)) continue;
+      if (cutoff > 0 && !(d2s <= c2) && !(dx == 0 && dy == 0)) continue;
       offs.push_back(make_int2(dx, dy));
     }
   const int K = (int)offs.size();
+  // dy groups (offsets are generated dy-major with dx ascending) and the widest dx
+  std::vector<int> dy_start;
+  int CX = 0;
+  for (int a = 0; a < K; ++a) {
+    if (a == 0 || offs[a].y != offs[a - 1].y) dy_start.push_back(a);
+    CX = std::max(CX, std::abs(offs[a].x));
+  }
+  const int ndy = (int)dy_start.size();
+  dy_start.push_back(K);
+  // the tensor-core kernel steps dx by one inside a dy group
+  bool dx_contiguous = true;
+  for (int d = 0; d < ndy; ++d)
+    for (int a = dy_start[d]; a < dy_start[d + 1]; ++a)
+      if (offs[a].x != offs[dy_start[d]].x + (a - dy_start[d])) dx_contiguous = false;
   std::vector<int> negs(K);
   for (int a = 0; a < K; ++a)
     for (int b = 0; b < K; ++b)
@@ -262,6 +308,9 @@ int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_
   float2* B32 = nullptr;
   TM_TRY(scratch(ctx, "lat_off", sizeof(int2) * std::max(K, 1), (void**)&d_off));
   TM_TRY(scratch(ctx, "lat_neg", sizeof(int) * std::max(K, 1), (void**)&d_neg));
+  int* d_dys;
+  TM_TRY(scratch(ctx, "lat_dys", sizeof(int) * (ndy + 1), (void**)&d_dys));
+  TM_CUDA(ctx, cudaMemcpyAsync(d_dys, dy_start.data(), sizeof(int) * (ndy + 1), cudaMemcpyHostToDevice, ctx->stream));
   TM_TRY(scratch(ctx, "lat_B64", sizeof(double2) * (size_t)std::max(K, 1) * 2 * L * LP, (void**)&B64));
   if (mixed) TM_TRY(scratch(ctx, "lat_B32", sizeof(float2) * (size_t)std::max(K, 1) * 2 * L * LP, (void**)&B32));
   if (K > 0) {
@@ -276,9 +325,9 @@ int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_
 #undef LB
     }
     TM_LAUNCHED(ctx);
-    // host copies above are from stack vectors: wait before they go out of scope
-    TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   }
+  // host copies above are from stack vectors: wait before they go out of scope
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   LatOp a;
   a.N = N;
   a.nx = nx;
@@ -290,6 +339,9 @@ int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_
   a.K = K;
   a.off = d_off;
   a.neg = d_neg;
+  a.dy_start = d_dys;
+  a.ndy = ndy;
+  a.CX = CX;
   a.fp32 = false;
   a.BT = B64;
   a.T = T64;
@@ -300,6 +352,10 @@ int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_
     a.fp32 = true;
     a.BT = B32;
     a.T = T32;
+    if (lattice_tc_supported(t->nmax) && K > 0 && dx_contiguous && lattice_tc_fits(t->nmax, CX)) {
+      TM_TRY(lattice_tc_prepare(ctx, &a, B64));
+      a.use_tc = true;
+    }
     ops->lat32 = a;
     ops->A32.kind = 1;
     ops->A32.lat = &ops->lat32;

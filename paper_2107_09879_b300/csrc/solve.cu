@@ -107,6 +107,16 @@ static int make_nbr_ops(const Tables* t, const double* d_pos, int64_t N, double 
   return TMAT_OK;
 }
 
+// The tensor-core kernel counts CTAs that gave up on a bounded wait.
+static int check_tc_errors(tmat_ctx* ctx, const OpPair& ops) {
+  if (!ops.have32 || ops.A32.kind != 1 || !ops.lat32.use_tc || !ops.lat32.tc_err) return TMAT_OK;
+  int* pin = (int*)ctx->pinned;
+  TM_CUDA(ctx, cudaMemcpyAsync(pin, ops.lat32.tc_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (pin[0]) return set_error(ctx, TMAT_ECUDA, "tensor-core apply: %d tiles gave up on a bounded wait", pin[0]);
+  return TMAT_OK;
+}
+
 }  // namespace tmat
 
 using namespace tmat;
@@ -190,6 +200,7 @@ extern "C" int tmat_solve(tmat_ctx* ctx, const double* pos, int64_t N, double wa
   TM_LAUNCHED(ctx);
   SolveStats st;
   TM_TRY(solve_system(ctx, ops.A64, ops.have32 ? &ops.A32 : nullptr, TMAT_OP_FORWARD, b, x, R, sp, &st));
+  TM_TRY(check_tc_errors(ctx, ops));
   TM_TRY(from_internal(ctx, t, x, false, (double2*)ss.dev, (int64_t)R * N));
   TM_TRY(finish_out(ctx, &ss));
   if (keep) {
@@ -274,6 +285,7 @@ extern "C" int tmat_adjoint(tmat_ctx* ctx, const tmat_solution* sol, const tmat_
   TM_TRY(to_internal(ctx, t, (const double2*)sd.dev, dTi, false, N));
   SolveStats st;
   TM_TRY(solve_system(ctx, ops.A64, ops.have32 ? &ops.A32 : nullptr, TMAT_OP_ADJOINT, vi, mu, 1, sol->params, &st));
+  TM_TRY(check_tc_errors(ctx, ops));
   // e = a0 + A s with the fp64 operator
   TM_TRY(op_apply(ctx, ops.A64, TMAT_OP_COUPLE, sol->s, As, 1));
   grad_kernel<<<(unsigned)cdiv(N, 128), 128, 0, ctx->stream>>>(mu, dTi, sol->a0, As, N, P, (double*)sg.dev);

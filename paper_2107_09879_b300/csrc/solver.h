@@ -18,6 +18,14 @@ struct LatOp {
   const int* neg = nullptr;    // [K] index of -o
   const void* BT = nullptr;    // [K][2][L][LP] complex64 or complex128
   const void* T = nullptr;     // [N][P] internal layout, kernel precision
+  // tensor-core (tcgen05, 3xTF32) variant of the complex64 apply
+  bool use_tc = false;
+  const void* Wtc_fwd = nullptr;  // split W tables in MMA core layout, forward
+  const void* Wtc_adj = nullptr;  // and adjoint
+  int* tc_err = nullptr;          // device counter of CTAs that gave up on a wait
+  const int* dy_start = nullptr;  // [ndy + 1] first offset of each dy (offsets sorted by dy, dx)
+  int ndy = 0;
+  int CX = 0;                     // max |dx| over the offsets
 };
 // An operator instance in one precision. kind 0: neighbour list; kind 1: lattice.
 struct Operator {
@@ -68,6 +76,10 @@ namespace tmat {
 int build_neighbors(tmat_ctx* ctx, const double* d_pos, int64_t N, double cutoff, int64_t* d_row_ptr, int32_t* d_col,
                     int64_t* nnz_out);
 int lattice_apply(tmat_ctx* ctx, const LatOp& L, int mode, const void* x, void* y, int R);
+bool lattice_tc_supported(int nmax);
+bool lattice_tc_fits(int nmax, int CX);
+int lattice_tc_apply(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void* y, int R);
+int lattice_tc_prepare(tmat_ctx* ctx, LatOp* a, const double2* BT64);
 inline int64_t lattice_N(const LatOp& L) { return L.N; }
 inline int lattice_nmax(const LatOp& L) { return L.nmax; }
 inline bool lattice_fp32(const LatOp& L) { return L.fp32; }

@@ -1,5 +1,5 @@
 """Summarise an ncu launch list (--metrics gpu__time_duration.sum --csv) by kernel:
-launches, total device time and share. Usage: python summarize_launches.py launches.csv"""
+launches, total device time and share. Usage: python -m paper_2107_09879_b300.prof_summary launches.csv"""
 import collections
 import csv
 import sys

@@ -34,3 +34,13 @@ def rand_c(shape, seed):
     n = int(np.prod(shape))
     u = g.uniforms(2 * n)
     return ((u[:n] - 0.5) + 1j * (u[n:] - 0.5)).reshape(shape)
+
+
+# Tolerance of one complex64 operator application against the fp64 oracle
+# (relative L2). The tensor-core kernel keeps each operand to ~2^-22 (TF32 head +
+# tail), drops the tail x tail product (~2^-22 relative) and accumulates on the
+# tensor core in chains of at most 8 offsets (measured truncation ~1e-8 per
+# step, ~1e-6 per chain) before fp32 round-to-nearest sums; the CUDA-core kernel
+# accumulates ~10^2..10^4 fp32 terms per output (u = 6e-8). Both stay below
+# 5e-6 on the sizes tested here.
+C64_APPLY_TOL = 5e-6

@@ -4,7 +4,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_common import K0, atoms, ctx, rand_c, rel_l2
+from gpu_common import C64_APPLY_TOL, K0, atoms, ctx, rand_c, rel_l2
 from oracle import geometry, mie, system
 from paper_2107_09879_b300 import workloads as W
 
@@ -25,7 +25,7 @@ def test_lattice_apply_vs_oracle(nmax, nx, ny, cutoff, R, op):
     y64 = ctx().tmat_apply_lattice(op, 0, nx, ny, 0.5, cutoff, K0, nmax, T, x)
     y32 = ctx().tmat_apply_lattice(op, 1, nx, ny, 0.5, cutoff, K0, nmax, T, x)
     assert rel_l2(y64, ref) <= 1e-12
-    assert rel_l2(y32, ref) <= 2e-6
+    assert rel_l2(y32, ref) <= C64_APPLY_TOL
 
 
 def test_lattice_matches_neighbour_path_bitwise_structure():
@@ -92,3 +92,30 @@ def test_lattice_rejects_non_lattice_positions():
     with pytest.raises(_lib.TMatError) as e:
         ctx().tmat_solve(pos, 1.0, 1.0, 2, T, a0, opts)
     assert e.value.code == _lib.EINVAL
+
+
+@pytest.mark.parametrize("nmax,nx,ny,cutoff,R", [(4, 23, 9, 2.0, 2), (3, 17, 13, 1.6, 1), (2, 9, 7, 1.2, 3),
+                                                 (1, 11, 5, 1.0, 2), (4, 7, 6, 0.0, 5)])
+@pytest.mark.parametrize("op", [0, 1, 2])
+def test_tensor_core_apply_matches_cuda_cores_and_oracle(nmax, nx, ny, cutoff, R, op):
+    """The tcgen05 3xTF32 kernel against the CUDA-core fp32 kernel and the oracle."""
+    pos = W.lattice_positions(nx, ny)
+    r = W.uniform_radii(nx * ny, 0.08, 0.24, 60 + nmax)
+    T = np.array([mie.tmatrix_diag(nmax, K0, x, 2.0) for x in r])
+    x = rand_c((R, nx * ny, T.shape[1]), 70 + nmax)
+    c = ctx()
+    c.set_tensor_cores(True)
+    c.set_timing(True)
+    ytc = c.tmat_apply_lattice(op, 1, nx, ny, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
+    n_tc, _ = c.kernel_time("lattice_apply_tc")
+    c.set_tensor_cores(False)
+    ycc = c.tmat_apply_lattice(op, 1, nx, ny, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
+    c.set_tensor_cores(True)
+    c.set_timing(False)
+    assert n_tc >= 1  # the tensor-core kernel really ran
+    nbr = geometry.neighbours(pos, cutoff)
+    f = [system.apply_K, system.apply_KT, lambda nm, k, p, t, v, nb: system.apply_A(nm, k, p, v, nb)][op]
+    with system.window(cutoff, cutoff):
+        ref = np.array([f(nmax, K0, pos, T, x[q], nbr) for q in range(R)])
+    assert rel_l2(ytc, ref) <= C64_APPLY_TOL
+    assert rel_l2(ytc, ycc) <= C64_APPLY_TOL

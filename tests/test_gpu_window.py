@@ -4,7 +4,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_common import K0, atoms, ctx, rand_c, rel_l2
+from gpu_common import C64_APPLY_TOL, K0, atoms, ctx, rand_c, rel_l2
 from oracle import geometry, mie, system
 from paper_2107_09879_b300 import workloads as W
 
@@ -24,7 +24,7 @@ def test_windowed_apply_both_paths(cutoff, taper, op):
     with system.window(cutoff, taper):
         ref = np.array([f(nmax, K0, pos, T, x[q], nbr) for q in range(2)])
     rp, col = ctx().tmat_neighbors(pos, cutoff)
-    for prec, bound in ((0, 1e-12), (1, 2e-6)):
+    for prec, bound in ((0, 1e-12), (1, C64_APPLY_TOL)):
         y = ctx().tmat_apply(op, prec, pos, K0, nmax, T, rp, col, x, cutoff=cutoff, taper=taper)
         assert rel_l2(y, ref) <= bound
         y = ctx().tmat_apply_lattice(op, prec, nx, ny, 0.5, cutoff, K0, nmax, T, x, taper=taper)
