@@ -66,3 +66,68 @@ def planewave_field(k, beta, alpha, A, pts):
     pts = np.asarray(pts, dtype=np.float64)
     kvec = k * direction(beta, alpha)
     return np.exp(1j * (pts @ kvec))[:, None] * np.asarray(A, dtype=np.complex128)[None, :]
+
+
+# ----------------------------------------------------------------------------
+# Jinc sources (App. II, "Computation of jinc sources").
+#
+# Readings: the sampling kernel is the cylindrical J_1 (the Fourier form of the
+# paper integrates to J_1(k0 rho)/(k0 rho), not to the spherical j_1), and a
+# source on the lambda/2 grid carries the weight of its cell, so that for a field
+# band-limited to the disc |k^T| < k0
+#     E^T(x^T, z0) = sum_s E^T(x_s, z0) (pi/2) J_1(k0 rho_s)/(k0 rho_s),
+# i.e. each source is (1/(4 k0^2)) int_{|k^T|<k0} A_s e^{i k^T.(x^T - x_s)} d^2k^T.
+# Each plane-wave component is propagated with e^{i k_z (z - z0)} and completed
+# to a transverse vector A(k^T) = A^T - z^ (k^T.A^T)/k_z. With k^T = k0 sin b
+# (cos a, sin a), d^2k^T = k0^2 sin b cos b db da, the coefficients about a
+# sphere at x_j of a group of sources are
+#     a0_j = (1/4) int db da sin b cos b e^{i k.(x_j - z0 z^)} a_lmp(b, a; A(k^T)),
+#     A(k^T) = S^T - z^ tan b (k^T^.S^T),   S^T(k^T) = sum_s A_s e^{-i k^T.x_s}.
+# The quadrature rule is part of the definition: Gauss-Legendre in b on
+# [0, pi/2] (n_beta nodes) times the trapezoid rule in a (n_alpha nodes).
+# ----------------------------------------------------------------------------
+
+def jinc_rule(n_beta, n_alpha):
+    """Nodes and weights: (beta[nb], w_beta[nb], alpha[na], w_alpha)."""
+    xg, wg = np.polynomial.legendre.leggauss(n_beta)
+    beta = (xg + 1.0) * (math.pi / 4.0)  # map [-1, 1] -> [0, pi/2]
+    wb = wg * (math.pi / 4.0)
+    alpha = np.arange(n_alpha) * (2.0 * math.pi / n_alpha)
+    return beta, wb, alpha, 2.0 * math.pi / n_alpha
+
+
+def jinc_rule_size(k0, extent):
+    """Rule that resolves phases up to k0 * extent (extent: the largest distance
+    between a sphere and a source, transverse and along z combined)."""
+    kd = k0 * extent
+    n_beta = int(math.ceil(kd * math.pi / 4.0)) + 24
+    n_alpha = int(math.ceil(kd)) + 32
+    n_alpha += (-n_alpha) % 4
+    return n_beta, n_alpha
+
+
+def jinc_group_coeffs(nmax, k0, pos, src_xy, src_A, z0, rule):
+    """a0 (N, P) of one group of jinc sources (positions src_xy (S, 2) on the plane
+    z = z0, transverse amplitudes src_A (S, 2) complex) about every sphere."""
+    pos = np.asarray(pos, dtype=np.float64)
+    src_xy = np.asarray(src_xy, dtype=np.float64)
+    src_A = np.asarray(src_A, dtype=np.complex128)
+    beta, wb, alpha, wa = rule
+    L = nmax * (nmax + 2)
+    out = np.zeros((pos.shape[0], 2 * L), dtype=np.complex128)
+    for ib, b in enumerate(beta):
+        sb, cb = math.sin(b), math.cos(b)
+        for a in alpha:
+            ca, sa = math.cos(a), math.sin(a)
+            kx, ky, kz = k0 * sb * ca, k0 * sb * sa, k0 * cb
+            # group spectrum S^T(k^T)
+            ph = np.exp(-1j * (kx * src_xy[:, 0] + ky * src_xy[:, 1]))
+            Sx = np.sum(src_A[:, 0] * ph)
+            Sy = np.sum(src_A[:, 1] * ph)
+            kdotS = ca * Sx + sa * Sy
+            A = np.array([Sx, Sy, -math.tan(b) * kdotS])
+            coef = planewave_coeffs(nmax, b, a, A)
+            w = 0.25 * wb[ib] * wa * sb * cb
+            phase = np.exp(1j * (kx * pos[:, 0] + ky * pos[:, 1] + kz * (pos[:, 2] - z0)))
+            out += (w * phase)[:, None] * coef[None, :]
+    return out
