@@ -3,6 +3,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "../../include/tmat.h"
+
 namespace tmat {
 
 template <typename R> struct cplx;
@@ -65,6 +67,37 @@ __host__ __device__ __forceinline__ double taper_weight(double d, double cutoff,
   if (d <= d0) return 1.0;
   if (d >= cutoff) return 0.0;
   return 0.5 * (1.0 + cos(3.14159265358979323846 * (d - d0) / taper));
+}
+
+// pi_l^m(b) = Pbar_l^m(cos b)/sin b (m >= 1) and tau_l^m(b) = d Pbar_l^m / d b,
+// normalised Legendre functions without the Condon-Shortley phase.
+__device__ inline void pi_tau(int l, int m, double beta, double* pi_out, double* tau_out) {
+  double s, c;
+  sincos(beta, &s, &c);
+  int mu = m < 1 ? 1 : m;  // m = 0 needs pi^1 for tau
+  double df = 1.0, f2 = 1.0;
+  for (int t = 1; t < 2 * mu; t += 2) df *= t;
+  for (int t = 2; t <= 2 * mu; ++t) f2 *= t;
+  double p_prev = 0.0, p_cur = sqrt((2 * mu + 1) / (2.0 * f2)) * df * pow(s, (double)(mu - 1));
+  double pis[TMAT_NMAX_MAX + 2];
+  for (int t = 0; t < TMAT_NMAX_MAX + 2; ++t) pis[t] = 0.0;
+  if (mu <= l) pis[mu] = p_cur;
+  for (int ll = mu + 1; ll <= l; ++ll) {
+    double a = sqrt((4.0 * ll * ll - 1) / ((double)ll * ll - (double)mu * mu));
+    double b = sqrt(((ll - 1.0) * (ll - 1.0) - (double)mu * mu) / (4.0 * (ll - 1.0) * (ll - 1.0) - 1));
+    double pn = a * (c * p_cur - b * p_prev);
+    p_prev = p_cur;
+    p_cur = pn;
+    pis[ll] = pn;
+  }
+  if (m >= 1) {
+    *pi_out = (m <= l) ? pis[l] : 0.0;
+    double prev = (l - 1 >= m) ? pis[l - 1] : 0.0;
+    *tau_out = (m <= l) ? (l * c * pis[l] - sqrt((2.0 * l + 1) * ((double)l * l - (double)m * m) / (2.0 * l - 1)) * prev) : 0.0;
+  } else {
+    *pi_out = 0.0;
+    *tau_out = -sqrt(l * (l + 1.0)) * s * pis[l];  // -sqrt(l(l+1)) Pbar_l^1
+  }
 }
 
 }  // namespace tmat
