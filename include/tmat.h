@@ -243,6 +243,46 @@ int tmat_solve(tmat_ctx* ctx, const double* pos, int64_t N, double wavelength, d
                tmat_solve_info* info);
 int tmat_solution_free(tmat_solution* sol);
 
+/* ---- sub-region sweep (main text; Fig. 3) -------------------------------- */
+
+/* Geometry and decomposition of a large-area sweep. Sites (ix, iy) of an
+ * nx x ny lattice sit at (x0 + ix*pitch, y0 + iy*pitch, z); every site also
+ * carries one jinc source on the plane z = z0 at the site's (x, y) (the
+ * lambda/2 sampling of App. II, so pitch should not exceed wavelength/(2 n_bg)).
+ * Sub-region a = ay*nax + ax has the core [ax*core_x, (ax+1)*core_x) x
+ * [ay*core_y, ...) and simulates the core grown by `buffer` sites on every side
+ * (clipped), as tmat_subregions. Sub-regions [first, first + count) are processed
+ * (count <= 0: all), so a sweep can be split into resumable pieces. */
+typedef struct {
+  int nx, ny;
+  double pitch, x0, y0, z;
+  int core_x, core_y, buffer;
+  double z0;
+  int n_beta, n_alpha;  /* jinc rule per sub-region (<= 0: sized per sub-region) */
+  int first, count;
+} tmat_sweep_opts;
+
+typedef struct {
+  int subregions;          /* processed by this call */
+  int total_subregions;
+  int unconverged;
+  int iterations;          /* GMRES iterations summed over sub-regions */
+  int64_t scatterer_solves;/* sum of padded sub-region sizes */
+  double worst_rel_residual;
+  double seconds;
+} tmat_sweep_info;
+
+/* For every sub-region: T-matrices of the padded set (atoms[nx*ny]), jinc-group
+ * incident coefficients of the core's sources (src_A[R][nx*ny][2] transverse
+ * amplitudes, R <= 4), the solve (opts; the lattice path is forced), and the
+ * scattered field of the padded set at the detectors pts[M][3], ADDED to
+ * E_out[R][M][3] in sub-region order. The sum over all sub-regions is the
+ * decomposed scattered field of the whole array (the paper adds the sub-region
+ * fields). */
+int tmat_sweep(tmat_ctx* ctx, const tmat_sweep_opts* sw, const tmat_atom* atoms, double wavelength,
+               double n_bg, int nmax, const tmat_c128* src_A, int R, const tmat_solve_opts* opts,
+               const double* pts, int64_t M, tmat_c128* E_out, tmat_sweep_info* info);
+
 /* ---- fields (App. I-C, Eq. sca_fld_concise) ------------------------------ */
 
 /* E_out[M][3] = sum_i s_i^T Phi(k(x - x_i)) at the points pts[M][3] (scattered

@@ -40,6 +40,19 @@ class SolveInfo(ct.Structure):
                     rel_residual=[self.rel_residual[i] for i in range(self.n_rhs)], seconds=self.seconds)
 
 
+class SweepOpts(ct.Structure):
+    _fields_ = [("nx", ct.c_int), ("ny", ct.c_int), ("pitch", ct.c_double), ("x0", ct.c_double), ("y0", ct.c_double),
+                ("z", ct.c_double), ("core_x", ct.c_int), ("core_y", ct.c_int), ("buffer", ct.c_int),
+                ("z0", ct.c_double), ("n_beta", ct.c_int), ("n_alpha", ct.c_int), ("first", ct.c_int),
+                ("count", ct.c_int)]
+
+
+class SweepInfo(ct.Structure):
+    _fields_ = [("subregions", ct.c_int), ("total_subregions", ct.c_int), ("unconverged", ct.c_int),
+                ("iterations", ct.c_int), ("scatterer_solves", ct.c_int64), ("worst_rel_residual", ct.c_double),
+                ("seconds", ct.c_double)]
+
+
 class Atom(ct.Structure):
     _fields_ = [("radius", ct.c_double), ("n_re", ct.c_double), ("n_im", ct.c_double)]
 
@@ -65,6 +78,8 @@ _SIGS = {
     "tmat_solve": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _int, ct.POINTER(SolveOpts), _vp, ct.POINTER(_vp),
                    ct.POINTER(SolveInfo)],
     "tmat_solution_free": [_vp],
+    "tmat_sweep": [_vp, ct.POINTER(SweepOpts), _vp, _d, _d, _int, _vp, _int, ct.POINTER(SolveOpts), _vp, _i64, _vp,
+                   ct.POINTER(SweepInfo)],
     "tmat_field": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _i64, _vp],
     "tmat_farfield": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _i64, _vp],
     "tmat_point_fom": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _vp, ct.POINTER(_d), _vp],
@@ -243,6 +258,19 @@ class Context:
             self.check(rc)
         return s, info, (Solution(sol) if keep else None), rc
 
+    def tmat_sweep(self, sw, atoms, wavelength, n_bg, nmax, src_A, opts, pts, E=None):
+        """src_A: (R, nx*ny, 2); E (R, M, 3) is accumulated into (zeros if None)."""
+        R = src_A.shape[0]
+        M = pts.shape[0]
+        if E is None:
+            E = np.zeros((R, M, 3), dtype=np.complex128) if not _is_torch(pts) else empty_like_space(pts, (R, M, 3), np.complex128).zero_()
+        info = SweepInfo()
+        rc = lib.tmat_sweep(self.h, ct.byref(sw), ptr(atoms), wavelength, n_bg, nmax, ptr(src_A), R, ct.byref(opts),
+                            ptr(pts), M, ptr(E), ct.byref(info))
+        if rc not in (OK, ENOCONV):
+            self.check(rc)
+        return E, info, rc
+
     def tmat_field(self, pos, wavelength, n_bg, nmax, s, pts):
         M = pts.shape[0]
         E = empty_like_space(pts, (M, 3), np.complex128)
@@ -292,6 +320,13 @@ class Solution:
             self.free()
         except Exception:
             pass
+
+
+def make_sweep(**kw):
+    o = SweepOpts()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
 
 
 def make_opts(**kw):
