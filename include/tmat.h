@@ -177,9 +177,11 @@ int tmat_incident_planewave(tmat_ctx* ctx, const double* pos, int64_t N, double 
 
 /* Incident coefficients of one group of jinc sources (App. II). Sources sit on
  * the plane z = z0 at src_xy[S][2] with transverse amplitudes src_A[R][S][2]
- * (one set per right-hand side, R <= 4). Each source is the lambda/2-cell sample
- * (1/(4 k0^2)) int_{|k^T|<k0} A_s e^{i k^T.(x^T - x_s)} d^2k^T propagated along +z
- * (on z = z0 it is A_s (pi/2) J1(k0 rho)/(k0 rho)); every plane-wave component is
+ * (one set per right-hand side, R <= 4) on a grid of pitch src_pitch (<= 0: the
+ * paper's lambda/2 grid). Each source is the cell-weighted sample
+ * (a^2/(4 pi^2)) int_{|k^T|<k0} A_s e^{i k^T.(x^T - x_s)} d^2k^T propagated along +z
+ * (on z = z0 it is A_s (a^2 k0^2/(2 pi)) J1(k0 rho)/(k0 rho), = (pi/2) J1/(k0 rho) on the
+ * lambda/2 grid); every plane-wave component is
  * completed to a transverse vector and expanded about each sphere (App. II-A).
  * The integral over the disc uses Gauss-Legendre in the polar angle (n_beta nodes
  * on [0, pi/2]) times the trapezoid rule in the azimuth (n_alpha nodes); with
@@ -190,7 +192,8 @@ int tmat_incident_planewave(tmat_ctx* ctx, const double* pos, int64_t N, double 
  * tile with fp64-reduced phases, fp64 sums across tiles). a0_out[R][N][P]. */
 int tmat_incident_jinc(tmat_ctx* ctx, const double* pos, int64_t N, double wavelength, double n_bg,
                        int nmax, const double* src_xy, const tmat_c128* src_A, int64_t S, int R,
-                       double z0, int n_beta, int n_alpha, int precision, tmat_c128* a0_out);
+                       double z0, double src_pitch, int n_beta, int n_alpha, int precision,
+                       tmat_c128* a0_out);
 
 /* ---- translation coefficients (App. I-C, Eqs. tran_coeff) --------------- */
 

@@ -73,15 +73,18 @@ def planewave_field(k, beta, alpha, A, pts):
 #
 # Readings: the sampling kernel is the cylindrical J_1 (the Fourier form of the
 # paper integrates to J_1(k0 rho)/(k0 rho), not to the spherical j_1), and a
-# source on the lambda/2 grid carries the weight of its cell, so that for a field
-# band-limited to the disc |k^T| < k0
-#     E^T(x^T, z0) = sum_s E^T(x_s, z0) (pi/2) J_1(k0 rho_s)/(k0 rho_s),
-# i.e. each source is (1/(4 k0^2)) int_{|k^T|<k0} A_s e^{i k^T.(x^T - x_s)} d^2k^T.
+# source on a grid of pitch a carries the weight of its cell, a^2/(4 pi^2), so that
+# for a field band-limited to the disc |k^T| < k0 (and a small enough that no
+# other reciprocal-lattice image of the band falls in the disc)
+#     E^T(x^T, z0) = sum_s E^T(x_s, z0) (a^2 k0^2 / (2 pi)) J_1(k0 rho_s)/(k0 rho_s),
+# i.e. each source is (a^2/(4 pi^2)) int_{|k^T|<k0} A_s e^{i k^T.(x^T - x_s)} d^2k^T.
+# On the paper's lambda/2 grid (a = pi/k0) the kernel is (pi/2) J_1/(k0 rho) and the
+# weight 1/(4 k0^2).
 # Each plane-wave component is propagated with e^{i k_z (z - z0)} and completed
 # to a transverse vector A(k^T) = A^T - z^ (k^T.A^T)/k_z. With k^T = k0 sin b
 # (cos a, sin a), d^2k^T = k0^2 sin b cos b db da, the coefficients about a
 # sphere at x_j of a group of sources are
-#     a0_j = (1/4) int db da sin b cos b e^{i k.(x_j - z0 z^)} a_lmp(b, a; A(k^T)),
+#     a0_j = (a k0 / (2 pi))^2 int db da sin b cos b e^{i k.(x_j - z0 z^)} a_lmp(b, a; A(k^T)),
 #     A(k^T) = S^T - z^ tan b (k^T^.S^T),   S^T(k^T) = sum_s A_s e^{-i k^T.x_s}.
 # The quadrature rule is part of the definition: Gauss-Legendre in b on
 # [0, pi/2] (n_beta nodes) times the trapezoid rule in a (n_alpha nodes).
@@ -106,9 +109,11 @@ def jinc_rule_size(k0, extent):
     return n_beta, n_alpha
 
 
-def jinc_group_coeffs(nmax, k0, pos, src_xy, src_A, z0, rule):
+def jinc_group_coeffs(nmax, k0, pos, src_xy, src_A, z0, rule, pitch=None):
     """a0 (N, P) of one group of jinc sources (positions src_xy (S, 2) on the plane
-    z = z0, transverse amplitudes src_A (S, 2) complex) about every sphere."""
+    z = z0, transverse amplitudes src_A (S, 2) complex) about every sphere; the
+    sources lie on a grid of the given pitch (default lambda/2 = pi/k0)."""
+    cell = ((pitch if pitch else math.pi / k0) * k0 / (2.0 * math.pi)) ** 2
     pos = np.asarray(pos, dtype=np.float64)
     src_xy = np.asarray(src_xy, dtype=np.float64)
     src_A = np.asarray(src_A, dtype=np.complex128)
@@ -127,7 +132,7 @@ def jinc_group_coeffs(nmax, k0, pos, src_xy, src_A, z0, rule):
             kdotS = ca * Sx + sa * Sy
             A = np.array([Sx, Sy, -math.tan(b) * kdotS])
             coef = planewave_coeffs(nmax, b, a, A)
-            w = 0.25 * wb[ib] * wa * sb * cb
+            w = cell * wb[ib] * wa * sb * cb
             phase = np.exp(1j * (kx * pos[:, 0] + ky * pos[:, 1] + kz * (pos[:, 2] - z0)))
             out += (w * phase)[:, None] * coef[None, :]
     return out

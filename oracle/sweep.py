@@ -28,7 +28,7 @@ def sweep_fields(nmax, k0, nx, ny, pitch, z, radius, n_sphere, src_A, z0, core, 
         pos = pos_all[sim_idx]
         src_xy = pos_all[core_idx, :2]
         rule = rule_for(pos, src_xy)
-        a0 = incident.jinc_group_coeffs(nmax, k0, pos, src_xy, src_A[core_idx], z0, rule)
+        a0 = incident.jinc_group_coeffs(nmax, k0, pos, src_xy, src_A[core_idx], z0, rule, pitch=pitch)
         T = np.array([mie.tmatrix_diag(nmax, k0, radius[i], n_sphere) for i in sim_idx])
         with system.window(cutoff, taper):
             s = system.solve_dense(nmax, k0, pos, T, a0, cutoff)

@@ -71,7 +71,7 @@ _SIGS = {
     "tmat_subregions": [_vp, _i64, _i64, _i64, _i64, _i64, _vp, _vp, _vp, _vp, ct.POINTER(_i64), ct.POINTER(_i64)],
     "tmat_build": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp],
     "tmat_incident_planewave": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _int, _vp],
-    "tmat_incident_jinc": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _i64, _int, _d, _int, _int, _int, _vp],
+    "tmat_incident_jinc": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _i64, _int, _d, _d, _int, _int, _int, _vp],
     "tmat_translation": [_vp, _int, _d, _vp, _i64, _vp],
     "tmat_apply": [_vp, _int, _int, _vp, _i64, _d, _int, _vp, _vp, _vp, _d, _d, _vp, _int, _vp],
     "tmat_apply_lattice": [_vp, _int, _int, _int, _int, _d, _d, _d, _d, _int, _vp, _vp, _int, _vp],
@@ -216,14 +216,14 @@ class Context:
         return a0
 
     def tmat_incident_jinc(self, pos, wavelength, n_bg, nmax, src_xy, src_A, z0, n_beta=0, n_alpha=0,
-                           precision=PREC_FP64):
+                           precision=PREC_FP64, src_pitch=0.0):
         """src_A: (R, S, 2) complex transverse amplitudes."""
         N = pos.shape[0]
         R, S = src_A.shape[0], src_A.shape[1]
         P = 2 * nmax * (nmax + 2)
         a0 = empty_like_space(pos, (R, N, P), np.complex128)
         self.check(lib.tmat_incident_jinc(self.h, ptr(pos), N, wavelength, n_bg, nmax, ptr(src_xy), ptr(src_A), S, R,
-                                          z0, n_beta, n_alpha, precision, ptr(a0)))
+                                          z0, src_pitch, n_beta, n_alpha, precision, ptr(a0)))
         return a0
 
     def tmat_translation(self, nmax, k, disp):

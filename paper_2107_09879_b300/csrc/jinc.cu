@@ -1,10 +1,11 @@
 // Incident coefficients of a group of jinc sources (App. II).
 //
 // Each source on the plane z = z0 at x_s with transverse amplitude A_s is
-// (1/(4 k0^2)) int_{|k^T|<k0} A_s e^{i k^T.(x^T - x_s)} e^{i k_z (z - z0)} d^2k^T,
+// (a^2/(4 pi^2)) int_{|k^T|<k0} A_s e^{i k^T.(x^T - x_s)} e^{i k_z (z - z0)} d^2k^T
+// (a: pitch of the source grid; the paper's lambda/2 grid gives 1/(4 k0^2)),
 // every plane-wave component completed to A(k^T) = A^T - z^ (k^T.A^T)/k_z. About a
 // sphere at x_j the group's coefficients are
-//   a0_j = (1/4) sum_q w_q sin b cos b e^{i k_q.x_j} e^{-i k_z z0} a_lmp(b, a; A(S(k_q))),
+//   a0_j = (a k0/(2 pi))^2 sum_q w_q sin b cos b e^{i k_q.x_j} e^{-i k_z z0} a_lmp(b, a; A(S(k_q))),
 //   S(k^T) = sum_s A_s e^{-i k^T.x_s},
 // with the Gauss-Legendre (b in [0, pi/2]) x trapezoid (a) rule q = (b, a).
 #include <cmath>
@@ -18,7 +19,7 @@ namespace tmat {
 // one block per node: spectrum of the group for every RHS, then the node's coefficients
 // c[q][r][f] = (w_b w_a / 4) sin b cos b e^{-i kz z0} a_f(b, a; A(S_r))
 __global__ void jinc_node_kernel(const double* __restrict__ beta, const double* __restrict__ wbeta, int n_alpha,
-                                 int q0, int nq, double k0, double z0, const double* __restrict__ src_xy,
+                                 int q0, int nq, double k0, double z0, double cell, const double* __restrict__ src_xy,
                                  const double2* __restrict__ src_A, int64_t S, int R, int nmax,
                                  double2* __restrict__ c) {
   const int ql = blockIdx.x;
@@ -58,7 +59,7 @@ __global__ void jinc_node_kernel(const double* __restrict__ beta, const double* 
   const int L = nmax * (nmax + 2), P = 2 * L;
   double sz, cz;
   sincos(-kz * z0, &sz, &cz);
-  const double wq = 0.25 * wbeta[ib] * (2.0 * M_PI / n_alpha) * sb * cb;
+  const double wq = cell * wbeta[ib] * (2.0 * M_PI / n_alpha) * sb * cb;
   const double2 pre = make_double2(wq * cz, wq * sz);
   for (int t = threadIdx.x; t < R * P; t += blockDim.x) {
     const int r = t / P, f = t % P;
@@ -205,7 +206,8 @@ using namespace tmat;
 
 extern "C" int tmat_incident_jinc(tmat_ctx* ctx, const double* pos, int64_t N, double wavelength, double n_bg,
                                   int nmax, const double* src_xy, const tmat_c128* src_A, int64_t S, int R,
-                                  double z0, int n_beta, int n_alpha, int precision, tmat_c128* a0_out) {
+                                  double z0, double src_pitch, int n_beta, int n_alpha, int precision,
+                                  tmat_c128* a0_out) {
   if (!ctx) return TMAT_EINVAL;
   if (N < 0 || S < 0 || R < 1 || R > 4 || (N > 0 && (!pos || !a0_out)) || (S > 0 && (!src_xy || !src_A)) ||
       !(wavelength > 0) || !(n_bg > 0) || (precision != TMAT_PREC_FP64 && precision != TMAT_PREC_MIXED))
@@ -214,6 +216,8 @@ extern "C" int tmat_incident_jinc(tmat_ctx* ctx, const double* pos, int64_t N, d
   TM_CUDA(ctx, cudaSetDevice(ctx->device));
   const int P = num_coeffs(nmax);
   const double k0 = 2.0 * M_PI * n_bg / wavelength;
+  // weight of one source: its grid cell a^2/(4 pi^2) times k0^2 from the measure
+  const double cell = src_pitch > 0 ? (src_pitch * k0 / (2.0 * M_PI)) * (src_pitch * k0 / (2.0 * M_PI)) : 0.25;
   Staged sp, ss, sa, so;
   TM_TRY(stage_in(ctx, "st_pos", pos, sizeof(double) * 3 * N, &sp));
   TM_TRY(stage_in(ctx, "st_srcxy", src_xy, sizeof(double) * 2 * S, &ss));
@@ -260,7 +264,7 @@ extern "C" int tmat_incident_jinc(tmat_ctx* ctx, const double* pos, int64_t N, d
   }
   for (int64_t q0 = 0; q0 < NQ; q0 += CHUNK) {
     const int nq = (int)std::min<int64_t>(CHUNK, NQ - q0);
-    jinc_node_kernel<<<nq, 64, 0, ctx->stream>>>(dbeta, dwb, n_alpha, (int)q0, nq, k0, z0, (const double*)ss.dev,
+    jinc_node_kernel<<<nq, 64, 0, ctx->stream>>>(dbeta, dwb, n_alpha, (int)q0, nq, k0, z0, cell, (const double*)ss.dev,
                                                  (const double2*)sa.dev, S, R, nmax, c);
     TM_LAUNCHED(ctx);
     const unsigned grid = (unsigned)cdiv(N, 16);

@@ -40,6 +40,15 @@ def test_jinc_group_vs_oracle(nmax, R):
     assert rel_l2(auto, ref) <= 1e-12
 
 
+def test_jinc_coarser_grid_weight():
+    pos, src, A = _case(3, 2, 3, 2, 1, 7)
+    k0 = 2 * math.pi / 0.9
+    nb, na = incident.jinc_rule_size(k0, _extent(pos, src))
+    ref = incident.jinc_group_coeffs(3, k0, pos, src, A[0], Z0, incident.jinc_rule(nb, na), pitch=0.5)
+    a = ctx().tmat_incident_jinc(pos, 0.9, 1.0, 3, src, A, Z0, nb, na, precision=0, src_pitch=0.5)
+    assert rel_l2(a[0], ref) <= 1e-12
+
+
 def test_jinc_single_source_and_empty_group():
     pos, src, A = _case(1, 1, 3, 3, 1, 3)
     a = ctx().tmat_incident_jinc(pos, 1.0, 1.0, 3, src, A, Z0)

@@ -41,6 +41,23 @@ def test_source_plane_field_is_the_jinc_sum():
         assert np.max(np.abs(e[:2] - ref)) < 1e-11
 
 
+def test_source_plane_field_on_a_coarser_grid():
+    """Grid pitch a != lambda/2: the kernel is (a^2 k0^2 / (2 pi)) J1(k0 rho)/(k0 rho)."""
+    a = 0.45 / 0.9 * 1.0  # pitch 0.5 at wavelength 0.9 -> k0 = 2 pi / 0.9
+    k0 = 2 * math.pi / 0.9
+    src = np.array([[0.0, 0.0]])
+    A = np.array([[0.7, -0.2j]])
+    xj = np.array([0.2, 0.1, Z0])
+    rule = incident.jinc_rule(*incident.jinc_rule_size(k0, 2.0))
+    coef = incident.jinc_group_coeffs(16, k0, xj[None], src, A, Z0, rule, pitch=0.5)[0]
+    for d in ([0.05, 0.02], [-0.1, 0.08]):
+        p = xj + np.array([d[0], d[1], 0.0])
+        E = coef @ vswf.vswf(16, k0, p - xj, regular=True)
+        rho = math.hypot(p[0], p[1])
+        ref = A[0] * (0.5 ** 2 * k0 ** 2 / (2 * math.pi)) * sp.j1(k0 * rho) / (k0 * rho)
+        assert np.max(np.abs(E[:2] - ref)) < 1e-11
+
+
 def test_propagated_field_matches_direct_angular_spectrum():
     """Off the source plane: sum a RPhi equals the angular-spectrum integral of the
     source evaluated directly (no spherical-wave expansion), with a finer rule."""
