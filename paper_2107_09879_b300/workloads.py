@@ -116,3 +116,23 @@ def smooth_radius_map(nx, ny, seed, pitch=0.5):
             v += -0.01 + 0.02 * noise[iy * nx + ix]
             r[iy * nx + ix] = min(0.24, max(0.08, v))
     return r
+
+
+def served_stream(n_requests, seed, rate_per_s, k_lo=10, k_hi=60, buf=4):
+    """Request stream of sub-region solves: core k x k with k ~ U{k_lo..k_hi}, a
+    `buf`-site padding ring, radii ~ U[0.08, 0.24] over the (k + 2 buf)^2 patch,
+    wavelength ~ U[0.9, 1.1], nmax ~ U{3, 4, 5}, Poisson arrivals at `rate_per_s`
+    (exponential gaps). Returns a list of dicts, ordered by arrival time."""
+    g = SplitMix64(seed)
+    t = 0.0
+    out = []
+    for rid in range(n_requests):
+        k = k_lo + min(k_hi - k_lo, int(g.uniform() * (k_hi - k_lo + 1)))
+        side = k + 2 * buf
+        radii = 0.08 + 0.16 * g.uniforms(side * side)
+        wavelength = 0.9 + 0.2 * g.uniform()
+        nmax = 3 + min(2, int(g.uniform() * 3))
+        gap = -math.log(max(1e-300, 1.0 - g.uniform())) / rate_per_s if rate_per_s > 0 else 0.0
+        t += gap
+        out.append(dict(rid=rid, k=k, buf=buf, side=side, radii=radii, wavelength=wavelength, nmax=nmax, arrival=t))
+    return out
