@@ -177,7 +177,7 @@ def run_ours(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     ctx = _lib.Context(dev, None)
-    ctx.set_tensor_cores(not args.cuda_cores)
+    ctx.set_tensor_cores(0 if args.cuda_cores else args.tc_variant)
     wl = workload()
     w = wl["w"]
     nmax, cutoff = w["nmax"], w["cutoff"]
@@ -226,8 +226,11 @@ def run_ours(args, rank, world):
     per_step = sorted(a.elapsed_time(b) for a, b in evs)
     total_ms = sum(per_step)
     gpu_launches = ctx.launches() - launches0
-    n32, ms32 = ctx.kernel_time("lattice_apply_tc")
-    kern_name = "lattice_tc_kernel<4,2,0> (tcgen05 3xTF32)"
+    n32, ms32 = ctx.kernel_time("lattice_apply_tcv")
+    kern_name = "lattice_tc2_kernel<4,0> (tcgen05 3xTF32, window view)"
+    if n32 == 0:
+        n32, ms32 = ctx.kernel_time("lattice_apply_tc")
+        kern_name = "lattice_tc_kernel<4,2,0> (tcgen05 3xTF32, gather)"
     if n32 == 0:
         n32, ms32 = ctx.kernel_time("lattice_apply_fp32")
         kern_name = "lattice_apply_kernel<float,4,2,0> (CUDA cores)"
@@ -290,7 +293,7 @@ def run_kernel_only(args):
     import torch
     from paper_2107_09879_b300 import _lib
     ctx = _lib.Context(0, None)
-    ctx.set_tensor_cores(not args.cuda_cores)
+    ctx.set_tensor_cores(0 if args.cuda_cores else args.tc_variant)
     wl = workload()
     w = wl["w"]
     N, P, R = len(wl["pos"]), 48, 2
@@ -305,9 +308,10 @@ def run_kernel_only(args):
                                    w["nmax"], T, x, taper=w["cutoff"])
     kind = "lattice_apply_fp32" if args.kernel_precision == _lib.PREC_MIXED else "lattice_apply_fp64"
     n, ms = ctx.kernel_time(kind)
-    if args.kernel_precision == _lib.PREC_MIXED and n == 0:
-        kind = "lattice_apply_tc"
-        n, ms = ctx.kernel_time(kind)
+    for alt in ("lattice_apply_tcv", "lattice_apply_tc"):
+        if args.kernel_precision == _lib.PREC_MIXED and n == 0:
+            kind = alt
+            n, ms = ctx.kernel_time(kind)
     pairs = pairs_within(200, 200, int(round(w["cutoff"] / PITCH)))
     flop = 8.0 * (P * P / 2) * pairs * R
     return {"kernel": kind, "launches": n, "avg_ms": ms / max(n, 1), "tflops": flop / (ms / max(n, 1) * 1e-3) / 1e12,
@@ -345,6 +349,8 @@ def main():
     ap.add_argument("--kernel-only", action="store_true", help="time the dominant kernel alone (for ncu captures)")
     ap.add_argument("--kernel-precision", type=int, default=1, help="1: complex64 apply, 0: complex128 apply")
     ap.add_argument("--cuda-cores", action="store_true", help="complex64 apply on CUDA cores instead of tcgen05")
+    ap.add_argument("--tc-variant", type=int, default=1, choices=[1, 2],
+                    help="tensor-core lattice kernel: 1 window view (default), 2 gather")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

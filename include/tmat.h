@@ -130,8 +130,10 @@ int64_t tmat_ctx_launch_count(const tmat_ctx* ctx);
  * "nbr_apply_fp32", "nbr_apply_fp64". Enabling again resets the record. */
 int tmat_ctx_set_timing(tmat_ctx* ctx, int enable);
 /* Complex64 lattice applies run on the tcgen05 tensor cores (3xTF32, nmax <= 4)
- * unless disabled here (then the CUDA-core fp32 kernel runs). Default: enabled.
- * Timing kind of the tensor-core kernel: "lattice_apply_tc". */
+ * unless disabled here (enable = 0: the CUDA-core fp32 kernel runs). enable = 1
+ * (default) picks the window-view kernel where its windows fit in shared memory;
+ * enable = 2 forces the gather kernel. Timing kinds: "lattice_apply_tcv" (window view),
+ * "lattice_apply_tc" (gather). */
 int tmat_ctx_set_tensor_cores(tmat_ctx* ctx, int enable);
 int tmat_ctx_kernel_time(tmat_ctx* ctx, const char* kind, int64_t* launches, double* total_ms);
 

@@ -153,7 +153,8 @@ class Context:
         return lib.tmat_ctx_launch_count(self.h)
 
     def set_tensor_cores(self, on):
-        self.check(lib.tmat_ctx_set_tensor_cores(self.h, 1 if on else 0))
+        """0/False: CUDA cores; 1/True: tensor cores (window-view kernel where it fits); 2: gather kernel."""
+        self.check(lib.tmat_ctx_set_tensor_cores(self.h, int(on)))
 
     def set_timing(self, on):
         self.check(lib.tmat_ctx_set_timing(self.h, 1 if on else 0))

@@ -156,6 +156,7 @@ extern "C" int64_t tmat_ctx_launch_count(const tmat_ctx* ctx) { return ctx ? ctx
 extern "C" int tmat_ctx_set_tensor_cores(tmat_ctx* ctx, int enable) {
   if (!ctx) return TMAT_EINVAL;
   ctx->tensor_cores = enable != 0;
+  ctx->tc_variant = enable == 2 ? 1 : 0;
   return TMAT_OK;
 }
 

@@ -67,6 +67,7 @@ struct tmat_ctx {
   std::map<std::string, tmat::DevBuf> bufs;
   int num_sms = 148;
   bool tensor_cores = true;  // use the tcgen05 kernels where they exist
+  int tc_variant = 0;        // 0: window-view kernel where it fits, 1: gather kernel
   void* pinned = nullptr;  // small pinned host staging area (status words)
 };
 

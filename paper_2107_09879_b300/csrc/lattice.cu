@@ -228,7 +228,10 @@ static int lat_mode(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void
 
 int lattice_apply(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void* y, int R_) {
   if (a.N == 0) return TMAT_OK;
-  if (a.fp32 && a.use_tc && ctx->tensor_cores) return lattice_tc_apply(ctx, a, mode, x, y, R_);
+  if (a.fp32 && a.use_tc && ctx->tensor_cores) {
+    if (a.tc2 && ctx->tc_variant != 1) return lattice_tc2_apply(ctx, a, mode, x, y, R_);
+    return lattice_tc_apply(ctx, a, mode, x, y, R_);
+  }
   const int64_t rs = a.N * a.P;
   const size_t esz = a.fp32 ? sizeof(float2) : sizeof(double2);
   for (int r0 = 0; r0 < R_; r0 += 2) {
@@ -286,9 +289,11 @@ int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_
   // dy groups (offsets are generated dy-major with dx ascending) and the widest dx
   std::vector<int> dy_start;
   int CX = 0;
+  int CY = 0;
   for (int a = 0; a < K; ++a) {
     if (a == 0 || offs[a].y != offs[a - 1].y) dy_start.push_back(a);
     CX = std::max(CX, std::abs(offs[a].x));
+    CY = std::max(CY, std::abs(offs[a].y));
   }
   const int ndy = (int)dy_start.size();
   dy_start.push_back(K);
@@ -342,6 +347,7 @@ int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_
   a.dy_start = d_dys;
   a.ndy = ndy;
   a.CX = CX;
+  a.CY = CY;
   a.fp32 = false;
   a.BT = B64;
   a.T = T64;
@@ -355,6 +361,7 @@ int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_
     if (lattice_tc_supported(t->nmax) && K > 0 && dx_contiguous && lattice_tc_fits(t->nmax, CX)) {
       TM_TRY(lattice_tc_prepare(ctx, &a, B64));
       a.use_tc = true;
+      a.tc2 = lattice_tc2_fits(t->nmax, CX);
     }
     ops->lat32 = a;
     ops->A32.kind = 1;

@@ -26,6 +26,8 @@ struct LatOp {
   const int* dy_start = nullptr;  // [ndy + 1] first offset of each dy (offsets sorted by dy, dx)
   int ndy = 0;
   int CX = 0;                     // max |dx| over the offsets
+  int CY = 0;                     // max |dy| over the offsets
+  bool tc2 = false;               // window-view tensor-core kernel usable
 };
 // An operator instance in one precision. kind 0: neighbour list; kind 1: lattice.
 struct Operator {
@@ -78,6 +80,8 @@ int build_neighbors(tmat_ctx* ctx, const double* d_pos, int64_t N, double cutoff
 int lattice_apply(tmat_ctx* ctx, const LatOp& L, int mode, const void* x, void* y, int R);
 bool lattice_tc_supported(int nmax);
 bool lattice_tc_fits(int nmax, int CX);
+bool lattice_tc2_fits(int nmax, int CX);
+int lattice_tc2_apply(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void* y, int R);
 int lattice_tc_apply(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void* y, int R);
 int lattice_tc_prepare(tmat_ctx* ctx, LatOp* a, const double2* BT64);
 inline int64_t lattice_N(const LatOp& L) { return L.N; }

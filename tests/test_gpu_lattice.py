@@ -97,17 +97,21 @@ def test_lattice_rejects_non_lattice_positions():
 @pytest.mark.parametrize("nmax,nx,ny,cutoff,R", [(4, 23, 9, 2.0, 2), (3, 17, 13, 1.6, 1), (2, 9, 7, 1.2, 3),
                                                  (1, 11, 5, 1.0, 2), (4, 7, 6, 0.0, 5)])
 @pytest.mark.parametrize("op", [0, 1, 2])
-def test_tensor_core_apply_matches_cuda_cores_and_oracle(nmax, nx, ny, cutoff, R, op):
-    """The tcgen05 3xTF32 kernel against the CUDA-core fp32 kernel and the oracle."""
+@pytest.mark.parametrize("variant,kind", [(1, "lattice_apply_tcv"), (2, "lattice_apply_tc")])
+def test_tensor_core_apply_matches_cuda_cores_and_oracle(nmax, nx, ny, cutoff, R, op, variant, kind):
+    """Both tcgen05 3xTF32 kernels (window view, gather) against the CUDA-core fp32 kernel
+    and the oracle."""
     pos = W.lattice_positions(nx, ny)
     r = W.uniform_radii(nx * ny, 0.08, 0.24, 60 + nmax)
     T = np.array([mie.tmatrix_diag(nmax, K0, x, 2.0) for x in r])
     x = rand_c((R, nx * ny, T.shape[1]), 70 + nmax)
     c = ctx()
-    c.set_tensor_cores(True)
+    c.set_tensor_cores(variant)
     c.set_timing(True)
+    n0, _ = c.kernel_time(kind)
     ytc = c.tmat_apply_lattice(op, 1, nx, ny, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
-    n_tc, _ = c.kernel_time("lattice_apply_tc")
+    n_tc, _ = c.kernel_time(kind)
+    n_tc -= n0
     c.set_tensor_cores(False)
     ycc = c.tmat_apply_lattice(op, 1, nx, ny, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
     c.set_tensor_cores(True)
