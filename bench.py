@@ -35,6 +35,7 @@ from paper_2107_09879_b300 import workloads as W  # noqa: E402
 PITCH = 0.5
 METRIC = "solves/s + p50/p99 latency; T-matvec GFLOP/s, mixed vs FP64 at 1e-6 rel err"
 UNIT = "solves/s"
+TOL = 1e-7  # refinement stops at ||r|| / ||b|| <= 1e-7, so the solution error is <= 1e-6
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
 
 
@@ -171,6 +172,167 @@ def cpu_baseline(wl, matvecs_per_solve, budget_s=12.0):
                       f"x{matvecs_per_solve} applications per solve (the GPU run's count)"}
 
 
+def _wall(fn, sync):
+    sync()
+    t0 = time.perf_counter()
+    r = fn()
+    sync()
+    return time.perf_counter() - t0, r
+
+
+def bench_dense_fp64(ctx, torch, steps=20):
+    """8 x 8 spheres, nmax 3, every pair coupled, fp64 GMRES to 1e-10 (neighbour path)."""
+    from paper_2107_09879_b300 import _lib
+    w = W.dense_8x8()
+    a = np.zeros((64, 3))
+    a[:, 0], a[:, 1] = w["radius"], w["n_sphere"]
+    pos = torch.from_numpy(w["pos"]).cuda()
+    atoms = torch.from_numpy(a).cuda()
+    dirs = torch.zeros((1, 2), dtype=torch.float64, device="cuda")
+    pol = torch.tensor([[1.0, 0.0, 0.0]], dtype=torch.complex128, device="cuda")
+    opts = _lib.make_opts(tol=w["tol"], restart=100, max_iter=2000, cutoff=0.0, precision=_lib.PREC_FP64)
+    info = []
+
+    def one():
+        T = ctx.tmat_build(atoms, 1.0, 1.0, w["nmax"])
+        a0 = ctx.tmat_incident_planewave(pos, 1.0, 1.0, w["nmax"], dirs, pol)
+        s, inf, _, rc = ctx.tmat_solve(pos, 1.0, 1.0, w["nmax"], T, a0, opts)
+        info.append(inf)
+        return rc
+    for _ in range(3):
+        one()
+    dt, _ = _wall(lambda: [one() for _ in range(steps)], torch.cuda.synchronize)
+    return {"workload": "dense_8x8_nmax3_fp64_tol1e-10", "solves_per_s": steps / dt, "ms_per_solve": dt / steps * 1e3,
+            "iterations": info[-1].iterations, "rel_residual": info[-1].rel_residual[0],
+            "note": "one solve = Mie build + incident + GMRES; launched eagerly (no graph capture)"}
+
+
+def bench_adjoint(ctx, torch, steps=3):
+    """50 x 50 spheres, nmax 4, cutoff 10 (raised-cosine window), focal |E|^2 at 20 wavelengths:
+    forward solve + FoM + adjoint solve + gradient of all 2,500 radii, mixed precision to 1e-7."""
+    from paper_2107_09879_b300 import _lib
+    w = W.lattice_50x50_adjoint()
+    nmax, cut = w["nmax"], w["cutoff"]
+    a = np.zeros((2500, 3))
+    a[:, 0], a[:, 1] = w["radius"], w["n_sphere"]
+    pos = torch.from_numpy(w["pos"]).cuda()
+    atoms = torch.from_numpy(a).cuda()
+    dirs = torch.zeros((1, 2), dtype=torch.float64, device="cuda")
+    pol = torch.tensor([[1.0, 0.0, 0.0]], dtype=torch.complex128, device="cuda")
+    xf = w["focus"]
+    E_inc = np.array([np.exp(1j * 2 * math.pi * xf[2]), 0.0, 0.0])  # x-polarised plane wave along +z
+    opts = _lib.make_opts(tol=1e-7, restart=300, max_iter=4000, cutoff=cut, taper=cut, precision=_lib.PREC_MIXED,
+                          inner_tol=1e-4, path=_lib.PATH_LATTICE, lattice_nx=50, lattice_ny=50, lattice_pitch=PITCH)
+    rec = []
+
+    def one():
+        T, dT = ctx.tmat_build(atoms, 1.0, 1.0, nmax, with_dr=True)
+        a0 = ctx.tmat_incident_planewave(pos, 1.0, 1.0, nmax, dirs, pol)
+        s, fi, sol, rc = ctx.tmat_solve(pos, 1.0, 1.0, nmax, T, a0, opts, keep=True)
+        fom, v = ctx.tmat_point_fom(pos, 1.0, 1.0, nmax, s[0], xf, E_inc)
+        g, _, ai = ctx.tmat_adjoint(sol, v, dT)
+        sol.free()
+        rec.append((fi.iterations, ai.iterations, fi.rel_residual[0], ai.rel_residual[0]))
+        return g
+    one()
+    dt, g = _wall(lambda: [one() for _ in range(steps)][-1], torch.cuda.synchronize)
+    fi, ai, fr, ar = rec[-1]
+    return {"workload": "lattice_50x50_nmax4_cutoff10_adjoint_mixed", "gradients_per_s": steps / dt,
+            "ms_per_gradient": dt / steps * 1e3, "forward_iterations": fi, "adjoint_iterations": ai,
+            "forward_rel_residual": fr, "adjoint_rel_residual": ar, "grad_norm": float(torch.linalg.vector_norm(g)),
+            "note": "one gradient = Mie build with dT/dr + incident + forward solve + focal FoM + adjoint solve"}
+
+
+def bench_served(args, torch):
+    """Served stream of sub-region requests (k x k jinc core + 4-pitch ring, k ~ U{10..60},
+    nmax ~ U{3,4,5}, wavelength ~ U[0.9, 1.1]): Poisson arrivals at 1.5x and 0.5x of the
+    measured single-stream service rate."""
+    from paper_2107_09879_b300 import serve
+    calib = W.served_stream(8, seed=W.BASE_SEED + 3, rate_per_s=0.0)
+    srv = serve.Server(slots=1, mem_budget=64 << 30)
+    srv.run(calib[:2])  # warm-up
+    t0 = time.perf_counter()
+    srv.run(calib)
+    mu = len(calib) / (time.perf_counter() - t0)
+    srv.close()
+    out = {"workload": "served_subregions_k10-60_ring4_nmax3-5_mixed", "single_stream_solves_per_s": mu}
+    for name, factor, n in (("rate_1.5x", 1.5, args.served_requests), ("rate_0.5x", 0.5, max(8, args.served_requests // 4))):
+        reqs = W.served_stream(n, seed=W.BASE_SEED + 3, rate_per_s=factor * mu)
+        srv = serve.Server(slots=4, mem_budget=64 << 30)
+        t0 = time.perf_counter()
+        recs = srv.run(reqs)
+        wall = time.perf_counter() - t0
+        srv.close()
+        summ = serve.summarize(recs, wall)
+        summ["arrival_rate_per_s"] = factor * mu
+        summ["mem_high_water_bytes_est"] = srv.mem_high
+        out[name] = summ
+    return out
+
+
+def bench_sweep(ctx, torch):
+    """1200 x 1200 spheres (smooth radius map), nmax 3, cutoff 6, 60 x 60 cores + 8-pitch rings,
+    4 incidences as RHS, mixed: four sampled sub-regions (corner, edge, two interior),
+    extrapolated to the 400-sub-region sweep."""
+    from paper_2107_09879_b300 import _lib
+    n = 1200
+    r = W.smooth_radius_map(n, n, W.BASE_SEED + 5)
+    atoms = np.zeros((n * n, 3))
+    atoms[:, 0], atoms[:, 1] = r, 2.0
+    pos = W.lattice_positions(n, n)
+    z0 = -1.0
+    src = np.zeros((4, n * n, 2), complex)
+    for q, deg in enumerate((0.0, 5.0, 10.0, 15.0)):
+        th = math.radians(deg)
+        src[q, :, 0] = math.cos(th) * np.exp(1j * 2 * math.pi * (math.sin(th) * pos[:, 0] + math.cos(th) * z0))
+    pts = np.array([[x, 300.0, 20.0] for x in np.linspace(0.0, 600.0, 64)])
+    opts = _lib.make_opts(tol=1e-7, restart=300, max_iter=4000, cutoff=6.0, taper=6.0, precision=_lib.PREC_MIXED,
+                          inner_tol=1e-4)
+    d_atoms = torch.from_numpy(atoms).cuda()
+    d_src = torch.from_numpy(src).cuda()
+    d_pts = torch.from_numpy(pts).cuda()
+    E = torch.zeros((4, 64, 3), dtype=torch.complex128, device="cuda")
+    samples = {"corner": 0, "edge": 10, "interior_a": 210, "interior_b": 114}
+    kw = dict(nx=n, ny=n, pitch=PITCH, core_x=60, core_y=60, buffer=8, z0=z0)
+    # warm-up on the corner job
+    ctx.tmat_sweep(_lib.make_sweep(first=0, count=1, **kw), d_atoms, 1.0, 1.0, 3, d_src, opts, d_pts, E=E)
+    per = {}
+    infos = {}
+    for name, first in samples.items():
+        dt, res = _wall(lambda: ctx.tmat_sweep(_lib.make_sweep(first=first, count=1, **kw), d_atoms, 1.0, 1.0, 3,
+                                               d_src, opts, d_pts, E=E), torch.cuda.synchronize)
+        per[name] = dt
+        infos[name] = res[1]
+    mean = statistics.mean(per.values())
+    return {"workload": "sweep_1200x1200_nmax3_cutoff6_core60_ring8_4rhs_mixed",
+            "seconds_per_subregion": per, "subregions_per_s": 1.0 / mean,
+            "extrapolated_sweep_s": 400 * mean,
+            "iterations": {k: v.iterations for k, v in infos.items()},
+            "worst_rel_residual": max(v.worst_rel_residual for v in infos.values()),
+            "note": "sampled sub-regions (corner, edge, 2 interior) timed; full sweep extrapolated x400 from their mean"}
+
+
+def fp64_plain_estimate(ctx, torch, step_inputs, opts_kw, krylov_iters, iters=6):
+    """The plain complex128 GPU solve of the same workload, bounded: `iters` fp64 GMRES
+    iterations timed, scaled to the mixed run's Krylov count (an estimate, labelled so)."""
+    from paper_2107_09879_b300 import _lib
+    pos, atoms, dirs, pols = step_inputs
+    kw = dict(opts_kw)
+    kw.update(precision=_lib.PREC_FP64, max_iter=iters)
+    opts = _lib.make_opts(**kw)
+    T = ctx.tmat_build(atoms, 1.0, 1.0, 4)
+    a0 = ctx.tmat_incident_planewave(pos, 1.0, 1.0, 4, dirs, pols)
+    ctx.tmat_solve(pos, 1.0, 1.0, 4, T, a0, opts)  # warm-up (allocates the fp64 basis)
+    dt, res = _wall(lambda: ctx.tmat_solve(pos, 1.0, 1.0, 4, T, a0, opts), torch.cuda.synchronize)
+    it = res[1].iterations
+    per_it = dt / (it + 1)  # the cycle ends with one true-residual application
+    est = per_it * (krylov_iters + 1)
+    return {"ms_per_iteration": per_it * 1e3, "timed_iterations": it, "est_seconds_per_solve": est,
+            "est_solves_per_s": 1.0 / est,
+            "note": f"estimate: fp64 iteration time x {krylov_iters} iterations (the mixed run's Krylov count); "
+                    "the fp64 solve to the same tolerance needs at least that many"}
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2107_09879_b300 import _lib
@@ -184,9 +346,10 @@ def run_ours(args, rank, world):
     N, R, P = len(wl["pos"]), 2, 48
     tt = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     d_pos, d_atoms, d_dirs, d_pols, d_pts = map(tt, (wl["pos"], wl["atoms"], wl["dirs"], wl["pols"], wl["pts"]))
-    opts = _lib.make_opts(tol=1e-6, restart=300, max_iter=4000, cutoff=cutoff, taper=cutoff, precision=_lib.PREC_MIXED,
-                          inner_tol=1e-4, path=_lib.PATH_LATTICE, lattice_nx=wl["nx"], lattice_ny=wl["ny"],
-                          lattice_pitch=PITCH)
+    opts_kw = dict(tol=TOL, restart=300, max_iter=4000, cutoff=cutoff, taper=cutoff, precision=_lib.PREC_MIXED,
+                   inner_tol=1e-4, path=_lib.PATH_LATTICE, lattice_nx=wl["nx"], lattice_ny=wl["ny"],
+                   lattice_pitch=PITCH)
+    opts = _lib.make_opts(**opts_kw)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     infos = []
 
@@ -269,7 +432,7 @@ def run_ours(args, rank, world):
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64 apply / f64 refinement", "data": "synthetic",
         "config": {"workload": "lattice_200x200_nmax4_cutoff8_2rhs_mixed", "spheres": N, "nmax": nmax, "P": P,
-                   "rhs": R, "cutoff_wavelengths": cutoff, "coupling_window": "raised cosine over [0, cutoff] (taper = cutoff)", "tol": 1e-6, "restart": 300, "path": "lattice (block per offset)",
+                   "rhs": R, "cutoff_wavelengths": cutoff, "coupling_window": "raised cosine over [0, cutoff] (taper = cutoff)", "tol": TOL, "restart": 300, "path": "lattice (block per offset)",
                    "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before every step"},
         "p50_ms": per_step[len(per_step) // 2], "p99_ms": per_step[min(len(per_step) - 1, int(0.99 * len(per_step)))],
         "gmres_iterations_per_solve": statistics.mean(it), "refinements_per_solve": statistics.mean(ref),
@@ -281,6 +444,12 @@ def run_ours(args, rank, world):
         "gpu_launches": int(gpu_launches),
         "clocks": clk,
     }
+    if not args.no_extras:
+        out["fp64_plain"] = fp64_plain_estimate(ctx, torch, dev_in[:4], opts_kw, matvecs - int(round(statistics.mean(ref))))
+        out["dense_8x8_fp64"] = bench_dense_fp64(ctx, torch)
+        out["adjoint_50x50"] = bench_adjoint(ctx, torch)
+        out["served"] = bench_served(args, torch)
+        out["sweep_1200x1200"] = bench_sweep(ctx, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, matvecs)
     return out
@@ -345,6 +514,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workloads (fp64 plain estimate, 8x8 fp64, adjoint, served stream, sweep)")
+    ap.add_argument("--served-requests", type=int, default=48, help="requests in the 1.5x-rate served stream")
     ap.add_argument("--ref-matvecs", type=int, default=276, help="operator applications per solve for the oracle arm")
     ap.add_argument("--kernel-only", action="store_true", help="time the dominant kernel alone (for ncu captures)")
     ap.add_argument("--kernel-precision", type=int, default=1, help="1: complex64 apply, 0: complex128 apply")

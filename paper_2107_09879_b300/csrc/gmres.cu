@@ -530,6 +530,10 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
 
 static unsigned g_for(tmat_ctx* ctx, int64_t n) { return grid_for(ctx, n); }
 
+// Relative error of a complex64 residual b - K x (x rounded to complex64, K applied in
+// fp32/3xTF32 arithmetic), as a fraction of ||b||.
+constexpr double kFastResidualFloor = 1e-7;
+
 int solve_system(tmat_ctx* ctx, const Operator& A64, const Operator* A32, int mode, const double2* b, double2* x, int R,
                  const SolveParams& p, SolveStats* st) {
   const int64_t n = A64.N() * num_coeffs(A64.nmax());
@@ -553,6 +557,8 @@ int solve_system(tmat_ctx* ctx, const Operator& A64, const Operator* A32, int mo
   TM_TRY(scratch(ctx, "mx_d64", sizeof(double2) * R * n, (void**)&d64));
   TM_TRY(scratch(ctx, "mx_y64", sizeof(double2) * R * n, (void**)&y64));
   TM_TRY(scratch(ctx, "mx_r32", sizeof(float2) * R * n, (void**)&r32));
+  float2* y32;
+  TM_TRY(scratch(ctx, "mx_y32", sizeof(float2) * R * n, (void**)&y32));
   const int nb = (int)std::min<int64_t>(cdiv(n, RED_THREADS), (int64_t)ctx->num_sms * 4);
   double2 *part, *tmp;
   double *rn, *bn, *alpha;
@@ -597,6 +603,33 @@ int solve_system(tmat_ctx* ctx, const Operator& A64, const Operator* A32, int mo
     // x += ||r|| d
     axpy_scaled_kernel<<<dim3(g1, R), 256, 0, ctx->stream>>>(x, d64, alpha, n, n);
     TM_LAUNCHED(ctx);
+    // Fast check first, where the tolerance allows it: r = b - K x with K applied in
+    // complex64 to x rounded to complex64 has an absolute error of about
+    // kFastResidualFloor ||b||, and the next correction cannot push the true residual
+    // below that error. So it is used only for tolerances >= 10x that floor, and only
+    // while it is far above the tolerance; otherwise the fp64 residual decides.
+    if (p.tol >= 10.0 * kFastResidualFloor) {
+      convert_kernel<double, float><<<g1, 256, 0, ctx->stream>>>(x, r32, (int64_t)R * n);
+      TM_LAUNCHED(ctx);
+      TM_TRY(op_apply(ctx, *A32, mode, r32, y32, R));
+      residual_kernel<double, float><<<g1, 256, 0, ctx->stream>>>(b, y32, r64, (int64_t)R * n);
+      TM_LAUNCHED(ctx);
+      TM_TRY(vec_norms<double>(ctx, r64, n, n, R, part, nb, tmp, 1, rn, nullptr));
+      TM_CUDA(ctx, cudaMemcpyAsync(pin, rn, sizeof(double) * R, cudaMemcpyDeviceToHost, ctx->stream));
+      TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      bool far = true;
+      for (int r = 0; r < R; ++r) {
+        if (!std::isfinite(pin[r])) return set_error(ctx, TMAT_EBREAKDOWN, "refinement residual is not finite");
+        if (hb[r] == 0 || halpha[r] == 0.0) continue;  // converged or zero RHS: frozen
+        far = far && pin[r] > std::max(10.0 * p.tol, 100.0 * kFastResidualFloor) * hb[r];
+      }
+      if (far) {
+        for (int r = 0; r < R; ++r)
+          if (hb[r] != 0 && halpha[r] != 0.0) hr[r] = pin[r];
+        st->refinements++;
+        continue;
+      }
+    }
     // r = b - K x in fp64
     TM_TRY(op_apply(ctx, A64, mode, x, y64, R));
     residual_kernel<double, double><<<g1, 256, 0, ctx->stream>>>(b, y64, r64, (int64_t)R * n);

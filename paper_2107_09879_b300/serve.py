@@ -35,7 +35,7 @@ def request_bytes(side, nmax, R=1, restart=60):
 
 
 class Server:
-    def __init__(self, slots=4, mem_budget=8 << 30, device=0, tol=1e-6, cutoff=8.0, restart=60, z0=-1.0,
+    def __init__(self, slots=4, mem_budget=8 << 30, device=0, tol=1e-7, cutoff=8.0, restart=60, z0=-1.0,
                  detector_height=5.0):
         import torch
         self.slots = slots
