@@ -397,7 +397,12 @@ def run_ours(args, rank, world):
     if n32 == 0:
         n32, ms32 = ctx.kernel_time("lattice_apply_fp32")
         kern_name = "lattice_apply_kernel<float,4,2,0> (CUDA cores)"
-    n64, ms64 = ctx.kernel_time("lattice_apply_fp64")
+    n64, ms64 = ctx.kernel_time("lattice_apply_oz")
+    res_kernel = "lattice_oz_kernel<4,0> (tcgen05 bf16 slices, exact group sums, fp64-class)"
+    if n64 == 0:
+        n64, ms64 = ctx.kernel_time("lattice_apply_fp64")
+        res_kernel = "lattice_apply_kernel<double,4,2,0> (FP64 CUDA cores)"
+
     ctx.set_timing(False)
     it = [i.iterations for i in infos]
     ref = [i.refinements for i in infos]
@@ -438,7 +443,8 @@ def run_ours(args, rank, world):
         "gmres_iterations_per_solve": statistics.mean(it), "refinements_per_solve": statistics.mean(ref),
         "tmatvec_gflops": (flop_per_launch / (avg32 * 1e-3) / 1e9) if n32 else None,
         "roofline": roofline(kern_name, achieved, n32, avg32, flop_per_launch),
-        "fp64_residual_launches": n64, "fp64_residual_avg_ms": (ms64 / n64) if n64 else None,
+        "fp64_residual_kernel": res_kernel, "fp64_residual_launches": n64,
+        "fp64_residual_avg_ms": (ms64 / n64) if n64 else None,
         "e2e": {"value": world * 1e3 / statistics.median(e2e_ms), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(gpu_launches),
@@ -475,7 +481,7 @@ def run_kernel_only(args):
             ctx.set_timing(True)
         y = ctx.tmat_apply_lattice(_lib.OP_FORWARD, args.kernel_precision, 200, 200, PITCH, w["cutoff"], 2 * math.pi,
                                    w["nmax"], T, x, taper=w["cutoff"])
-    kind = "lattice_apply_fp32" if args.kernel_precision == _lib.PREC_MIXED else "lattice_apply_fp64"
+    kind = {0: "lattice_apply_fp64", 1: "lattice_apply_fp32", 2: "lattice_apply_oz"}[args.kernel_precision]
     n, ms = ctx.kernel_time(kind)
     for alt in ("lattice_apply_tcv", "lattice_apply_tc"):
         if args.kernel_precision == _lib.PREC_MIXED and n == 0:
@@ -519,7 +525,7 @@ def main():
     ap.add_argument("--served-requests", type=int, default=48, help="requests in the 1.5x-rate served stream")
     ap.add_argument("--ref-matvecs", type=int, default=276, help="operator applications per solve for the oracle arm")
     ap.add_argument("--kernel-only", action="store_true", help="time the dominant kernel alone (for ncu captures)")
-    ap.add_argument("--kernel-precision", type=int, default=1, help="1: complex64 apply, 0: complex128 apply")
+    ap.add_argument("--kernel-precision", type=int, default=1, help="1: complex64 apply, 0: complex128 apply, 2: fp64-class tensor-core apply")
     ap.add_argument("--cuda-cores", action="store_true", help="complex64 apply on CUDA cores instead of tcgen05")
     ap.add_argument("--tc-variant", type=int, default=1, choices=[1, 2],
                     help="tensor-core lattice kernel: 1 window view (default), 2 gather")

@@ -75,7 +75,13 @@ typedef struct {
 enum {
   TMAT_PREC_FP64 = 0,  /* complex128 apply, vectors and Arnoldi */
   TMAT_PREC_MIXED = 1, /* complex64 apply and vectors inside GMRES; fp64 Arnoldi/Givens;
-                          fp64-accurate refinement residual (iterative refinement) */
+                          fp64-accurate refinement residual (iterative refinement). On the
+                          lattice path with tensor cores enabled and nmax <= 4 the residual
+                          uses the TMAT_PREC_FP64_TC apply. */
+  TMAT_PREC_FP64_TC = 2, /* complex128 vectors and Arnoldi; the operator applied with fp64-class
+                            accuracy (relative error ~1e-12) as exact products of 8-bit bf16
+                            slices on the tensor cores. Lattice path, nmax <= 4 only
+                            (TMAT_ENOTSUP otherwise). */
 };
 
 /* Which kernel applies the operator. */
@@ -130,10 +136,11 @@ int64_t tmat_ctx_launch_count(const tmat_ctx* ctx);
  * "nbr_apply_fp32", "nbr_apply_fp64". Enabling again resets the record. */
 int tmat_ctx_set_timing(tmat_ctx* ctx, int enable);
 /* Complex64 lattice applies run on the tcgen05 tensor cores (3xTF32, nmax <= 4)
- * unless disabled here (enable = 0: the CUDA-core fp32 kernel runs). enable = 1
+ * unless disabled here (enable = 0: the CUDA-core fp32 kernel runs, and the mixed
+ * refinement residual uses the fp64 CUDA-core kernel). enable = 1
  * (default) picks the window-view kernel where its windows fit in shared memory;
  * enable = 2 forces the gather kernel. Timing kinds: "lattice_apply_tcv" (window view),
- * "lattice_apply_tc" (gather). */
+ * "lattice_apply_tc" (gather), "lattice_apply_oz" (TMAT_PREC_FP64_TC apply). */
 int tmat_ctx_set_tensor_cores(tmat_ctx* ctx, int enable);
 int tmat_ctx_kernel_time(tmat_ctx* ctx, const char* kind, int64_t* launches, double* total_ms);
 
@@ -217,7 +224,8 @@ enum {
  * A_ij = w(|x_i - x_j|) xi(k(x_i - x_j))^T for j in the CSR row of i (row_ptr/col
  * from tmat_neighbors), w the coupling window of tmat_solve_opts (cutoff, taper;
  * taper 0 gives w = 1). precision: TMAT_PREC_FP64 (complex128 arithmetic) or
- * TMAT_PREC_MIXED (complex64 arithmetic; x and y are still complex128 here).
+ * TMAT_PREC_MIXED (complex64 arithmetic; x and y are still complex128 here);
+ * TMAT_PREC_FP64_TC only on the lattice (tmat_apply_lattice).
  * Positions must be coplanar. */
 int tmat_apply(tmat_ctx* ctx, int op, int precision, const double* pos, int64_t N, double k,
                int nmax, const tmat_c128* T_diag, const int64_t* row_ptr, const int32_t* col,

@@ -18,7 +18,7 @@ if not os.path.exists(LIB_PATH):
 lib = ct.CDLL(LIB_PATH)
 
 OK, EINVAL, ENOMEM, ENOCONV, EBREAKDOWN, ECUDA, ENOTSUP = 0, -1, -3, -4, -5, -6, -7
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_FP64_TC = 0, 1, 2
 PATH_AUTO, PATH_NEIGHBOUR, PATH_LATTICE = 0, 1, 2
 OP_FORWARD, OP_ADJOINT, OP_COUPLE = 0, 1, 2
 MAX_RHS = 16

@@ -535,7 +535,8 @@ static unsigned g_for(tmat_ctx* ctx, int64_t n) { return grid_for(ctx, n); }
 constexpr double kFastResidualFloor = 1e-7;
 
 int solve_system(tmat_ctx* ctx, const Operator& A64, const Operator* A32, int mode, const double2* b, double2* x, int R,
-                 const SolveParams& p, SolveStats* st) {
+                 const SolveParams& p, SolveStats* st, const Operator* res64) {
+  const Operator& Ares = res64 ? *res64 : A64;
   const int64_t n = A64.N() * num_coeffs(A64.nmax());
   GmresParams gp;
   gp.restart = std::max(2, std::min(p.restart, 1024));
@@ -630,8 +631,8 @@ int solve_system(tmat_ctx* ctx, const Operator& A64, const Operator* A32, int mo
         continue;
       }
     }
-    // r = b - K x in fp64
-    TM_TRY(op_apply(ctx, A64, mode, x, y64, R));
+    // r = b - K x, fp64-accurate
+    TM_TRY(op_apply(ctx, Ares, mode, x, y64, R));
     residual_kernel<double, double><<<g1, 256, 0, ctx->stream>>>(b, y64, r64, (int64_t)R * n);
     TM_LAUNCHED(ctx);
     TM_TRY(vec_norms<double>(ctx, r64, n, n, R, part, nb, tmp, 1, rn, nullptr));

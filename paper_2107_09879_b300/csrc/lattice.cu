@@ -228,6 +228,7 @@ static int lat_mode(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void
 
 int lattice_apply(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void* y, int R_) {
   if (a.N == 0) return TMAT_OK;
+  if (!a.fp32 && a.use_oz) return lattice_oz_apply(ctx, a, mode, x, y, R_);
   if (a.fp32 && a.use_tc && ctx->tensor_cores) {
     if (a.tc2 && ctx->tc_variant != 1) return lattice_tc2_apply(ctx, a, mode, x, y, R_);
     return lattice_tc_apply(ctx, a, mode, x, y, R_);
@@ -257,7 +258,7 @@ __global__ void lattice_check_kernel(const double* __restrict__ pos, int64_t N, 
 
 int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_t N, double k, int nx, int ny,
                      double pitch, double cutoff, double taper, const double2* T64, const float2* T32, bool mixed,
-                     OpPair* ops) {
+                     OpPair* ops, bool want_oz) {
   if (nx <= 0 || ny <= 0 || (int64_t)nx * ny != N || !(pitch > 0))
     return set_error(ctx, TMAT_EINVAL, "lattice path: need lattice_nx * lattice_ny == N and pitch > 0");
   {
@@ -354,6 +355,15 @@ int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_
   ops->lat64 = a;
   ops->A64.kind = 1;
   ops->A64.lat = &ops->lat64;
+  if (want_oz && ctx->tensor_cores && t->nmax <= 4 && K > 0 && dx_contiguous && lattice_oz_fits(t->nmax, CX)) {
+    LatOp z = a;
+    TM_TRY(lattice_oz_prepare(ctx, &z, B64));
+    z.use_oz = true;
+    ops->lat64oz = z;
+    ops->R64.kind = 1;
+    ops->R64.lat = &ops->lat64oz;
+    ops->have_oz = true;
+  }
   if (mixed) {
     a.fp32 = true;
     a.BT = B32;
@@ -381,7 +391,8 @@ extern "C" int tmat_apply_lattice(tmat_ctx* ctx, int op, int precision, int nx, 
   if (!ctx) return TMAT_EINVAL;
   const int64_t N = (int64_t)nx * ny;
   if (nx < 0 || ny < 0 || R < 1 || !(k > 0) || !(pitch > 0) || !(taper >= 0) || (taper > 0 && !(taper <= cutoff)) || (N > 0 && (!x || !y)) || op < 0 || op > 2 ||
-      (op != TMAT_OP_COUPLE && N > 0 && !T_diag) || (precision != TMAT_PREC_FP64 && precision != TMAT_PREC_MIXED))
+      (op != TMAT_OP_COUPLE && N > 0 && !T_diag) ||
+      (precision != TMAT_PREC_FP64 && precision != TMAT_PREC_MIXED && precision != TMAT_PREC_FP64_TC))
     return set_error(ctx, TMAT_EINVAL, "tmat_apply_lattice: bad arguments");
   Tables* t;
   TM_TRY(get_tables(ctx, nmax, &t));
@@ -409,14 +420,23 @@ extern "C" int tmat_apply_lattice(tmat_ctx* ctx, int op, int precision, int nx, 
     if (fp32) TM_TRY(prepare_T(ctx, t, (const double2*)sT.dev, N, true, "al_T32", &T32));
   }
   OpPair ops;
+  const bool emu = precision == TMAT_PREC_FP64_TC;
   TM_TRY(make_lattice_ops(ctx, t, dpos, N, k, nx, ny, pitch, cutoff, taper, (const double2*)T64, (const float2*)T32, fp32,
-                          &ops));
+                          &ops, emu));
+  if (emu && !ops.have_oz)
+    return set_error(ctx, TMAT_ENOTSUP, "TMAT_PREC_FP64_TC needs tensor cores enabled, nmax <= 4 and a cutoff window that fits");
   const size_t esz = fp32 ? sizeof(float2) : sizeof(double2);
   void *xi, *yi;
   TM_TRY(scratch(ctx, "ap_x", esz * R * N * P, &xi));
   TM_TRY(scratch(ctx, "ap_y", esz * R * N * P, &yi));
   TM_TRY(to_internal(ctx, t, (const double2*)sx.dev, xi, fp32, (int64_t)R * N));
-  TM_TRY(op_apply(ctx, fp32 ? ops.A32 : ops.A64, op, xi, yi, R));
+  TM_TRY(op_apply(ctx, fp32 ? ops.A32 : (emu ? ops.R64 : ops.A64), op, xi, yi, R));
+  if (emu) {
+    int* pin = (int*)ctx->pinned;
+    TM_CUDA(ctx, cudaMemcpyAsync(pin, ops.lat64oz.oz_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (pin[0]) return set_error(ctx, TMAT_ECUDA, "tensor-core fp64 apply: %d tiles gave up on a bounded wait", pin[0]);
+  }
   TM_TRY(from_internal(ctx, t, yi, fp32, (double2*)sy.dev, (int64_t)R * N));
   TM_TRY(finish_out(ctx, &sy));
   TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

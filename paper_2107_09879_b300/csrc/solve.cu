@@ -109,12 +109,31 @@ static int make_nbr_ops(const Tables* t, const double* d_pos, int64_t N, double 
 
 // The tensor-core kernel counts CTAs that gave up on a bounded wait.
 static int check_tc_errors(tmat_ctx* ctx, const OpPair& ops) {
-  if (!ops.have32 || ops.A32.kind != 1 || !ops.lat32.use_tc || !ops.lat32.tc_err) return TMAT_OK;
-  int* pin = (int*)ctx->pinned;
-  TM_CUDA(ctx, cudaMemcpyAsync(pin, ops.lat32.tc_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  if (pin[0]) return set_error(ctx, TMAT_ECUDA, "tensor-core apply: %d tiles gave up on a bounded wait", pin[0]);
+  const int* counters[2] = {
+      (ops.have32 && ops.A32.kind == 1 && ops.lat32.use_tc) ? ops.lat32.tc_err : nullptr,
+      ops.have_oz ? ops.lat64oz.oz_err : nullptr};
+  for (const int* c : counters) {
+    if (!c) continue;
+    int* pin = (int*)ctx->pinned;
+    TM_CUDA(ctx, cudaMemcpyAsync(pin, c, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (pin[0]) return set_error(ctx, TMAT_ECUDA, "tensor-core apply: %d tiles gave up on a bounded wait", pin[0]);
+  }
   return TMAT_OK;
+}
+
+// The solve's operators: the iterated one (A64 or, for TMAT_PREC_FP64_TC, R64), the
+// complex64 one and the refinement residual's.
+static int solve_with(tmat_ctx* ctx, const OpPair& ops, int precision, int mode, const double2* b, double2* x, int R,
+                      const SolveParams& sp, SolveStats* st) {
+  if (precision == TMAT_PREC_FP64_TC) {
+    if (!ops.have_oz)
+      return set_error(ctx, TMAT_ENOTSUP,
+                       "TMAT_PREC_FP64_TC needs the lattice path, tensor cores enabled, nmax <= 4 and a cutoff window that fits");
+    return solve_system(ctx, ops.R64, nullptr, mode, b, x, R, sp, st);
+  }
+  return solve_system(ctx, ops.A64, ops.have32 ? &ops.A32 : nullptr, mode, b, x, R, sp, st,
+                      ops.have_oz ? &ops.R64 : nullptr);
 }
 
 }  // namespace tmat
@@ -137,7 +156,7 @@ extern "C" int tmat_solve(tmat_ctx* ctx, const double* pos, int64_t N, double wa
     return set_error(ctx, TMAT_EINVAL, "tmat_solve: bad arguments (R must be 1..%d)", TMAT_MAX_RHS);
   if (!(opts->taper >= 0) || (opts->taper > 0 && !(opts->taper <= opts->cutoff)))
     return set_error(ctx, TMAT_EINVAL, "tmat_solve: taper must be in [0, cutoff]");
-  if (opts->precision != TMAT_PREC_FP64 && opts->precision != TMAT_PREC_MIXED)
+  if (opts->precision != TMAT_PREC_FP64 && opts->precision != TMAT_PREC_MIXED && opts->precision != TMAT_PREC_FP64_TC)
     return set_error(ctx, TMAT_EINVAL, "tmat_solve: unknown precision %d", opts->precision);
   Tables* t;
   TM_TRY(get_tables(ctx, nmax, &t));
@@ -187,7 +206,8 @@ extern "C" int tmat_solve(tmat_ctx* ctx, const double* pos, int64_t N, double wa
                         (const double2*)T64, (const float2*)T32, mixed, &ops));
   } else {
     TM_TRY(make_lattice_ops(ctx, t, (const double*)spos.dev, N, k, opts->lattice_nx, opts->lattice_ny,
-                            opts->lattice_pitch, opts->cutoff, opts->taper, (const double2*)T64, (const float2*)T32, mixed, &ops));
+                            opts->lattice_pitch, opts->cutoff, opts->taper, (const double2*)T64, (const float2*)T32, mixed, &ops,
+                            sp.precision != TMAT_PREC_FP64));
   }
   // b = T a0 (internal layout)
   double2 *a0i, *b, *x;
@@ -199,7 +219,7 @@ extern "C" int tmat_solve(tmat_ctx* ctx, const double* pos, int64_t N, double wa
       (const double2*)T64, a0i, b, N * P, (int64_t)R * N * P);
   TM_LAUNCHED(ctx);
   SolveStats st;
-  TM_TRY(solve_system(ctx, ops.A64, ops.have32 ? &ops.A32 : nullptr, TMAT_OP_FORWARD, b, x, R, sp, &st));
+  TM_TRY(solve_with(ctx, ops, sp.precision, TMAT_OP_FORWARD, b, x, R, sp, &st));
   TM_TRY(check_tc_errors(ctx, ops));
   TM_TRY(from_internal(ctx, t, x, false, (double2*)ss.dev, (int64_t)R * N));
   TM_TRY(finish_out(ctx, &ss));
@@ -274,7 +294,8 @@ extern "C" int tmat_adjoint(tmat_ctx* ctx, const tmat_solution* sol, const tmat_
                         sol->T32, mixed, &ops));
   } else {
     TM_TRY(make_lattice_ops(ctx, t, sol->pos, N, sol->k, sol->lattice_nx, sol->lattice_ny, sol->lattice_pitch,
-                            sol->cutoff, sol->taper, sol->T64, sol->T32, mixed, &ops));
+                            sol->cutoff, sol->taper, sol->T64, sol->T32, mixed, &ops,
+                            sol->params.precision != TMAT_PREC_FP64));
   }
   double2 *vi, *mu, *dTi, *As;
   TM_TRY(scratch(ctx, "adj_v", sizeof(double2) * N * P, (void**)&vi));
@@ -284,10 +305,10 @@ extern "C" int tmat_adjoint(tmat_ctx* ctx, const tmat_solution* sol, const tmat_
   TM_TRY(to_internal(ctx, t, (const double2*)sv.dev, vi, false, N));
   TM_TRY(to_internal(ctx, t, (const double2*)sd.dev, dTi, false, N));
   SolveStats st;
-  TM_TRY(solve_system(ctx, ops.A64, ops.have32 ? &ops.A32 : nullptr, TMAT_OP_ADJOINT, vi, mu, 1, sol->params, &st));
+  TM_TRY(solve_with(ctx, ops, sol->params.precision, TMAT_OP_ADJOINT, vi, mu, 1, sol->params, &st));
+  // e = a0 + A s with an fp64-accurate operator
+  TM_TRY(op_apply(ctx, ops.have_oz ? ops.R64 : ops.A64, TMAT_OP_COUPLE, sol->s, As, 1));
   TM_TRY(check_tc_errors(ctx, ops));
-  // e = a0 + A s with the fp64 operator
-  TM_TRY(op_apply(ctx, ops.A64, TMAT_OP_COUPLE, sol->s, As, 1));
   grad_kernel<<<(unsigned)cdiv(N, 128), 128, 0, ctx->stream>>>(mu, dTi, sol->a0, As, N, P, (double*)sg.dev);
   TM_LAUNCHED(ctx);
   if (mu_out) TM_TRY(from_internal(ctx, t, mu, false, (double2*)sm.dev, N));

@@ -28,6 +28,9 @@ struct LatOp {
   int CX = 0;                     // max |dx| over the offsets
   int CY = 0;                     // max |dy| over the offsets
   bool tc2 = false;               // window-view tensor-core kernel usable
+  // fp64-class apply on the tensor cores (bf16 slices, exact group sums)
+  bool use_oz = false;
+  int* oz_err = nullptr;  // device counter of CTAs that gave up on a wait
 };
 // An operator instance in one precision. kind 0: neighbour list; kind 1: lattice.
 struct Operator {
@@ -67,8 +70,10 @@ struct SolveStats {
   bool converged = false;
   double rel_res[TMAT_MAX_RHS] = {0};
 };
+// res64 (nullable): operator of the mixed solve's fp64-accurate refinement residual
+// (default A64).
 int solve_system(tmat_ctx* ctx, const Operator& A64, const Operator* A32, int mode, const double2* b, double2* x,
-                 int R, const SolveParams& p, SolveStats* st);
+                 int R, const SolveParams& p, SolveStats* st, const Operator* res64 = nullptr);
 
 int prepare_T(tmat_ctx* ctx, const Tables* t, const double2* T_api, int64_t N, bool fp32, const char* name, void** out);
 
@@ -84,16 +89,21 @@ bool lattice_tc2_fits(int nmax, int CX);
 int lattice_tc2_apply(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void* y, int R);
 int lattice_tc_apply(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void* y, int R);
 int lattice_tc_prepare(tmat_ctx* ctx, LatOp* a, const double2* BT64);
+bool lattice_oz_fits(int nmax, int CX);
+int lattice_oz_prepare(tmat_ctx* ctx, LatOp* a, const double2* BT64);
+int lattice_oz_apply(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void* y, int R);
 inline int64_t lattice_N(const LatOp& L) { return L.N; }
 inline int lattice_nmax(const LatOp& L) { return L.nmax; }
 inline bool lattice_fp32(const LatOp& L) { return L.fp32; }
 // Operators (fp64 and, for mixed, fp32) for one solve.
+// R64: the fp64-class tensor-core operator (have_oz), for refinement residuals and
+// TMAT_PREC_FP64_TC solves.
 struct OpPair {
-  Operator A64, A32;
-  bool have32 = false;
-  LatOp lat64, lat32;
+  Operator A64, A32, R64;
+  bool have32 = false, have_oz = false;
+  LatOp lat64, lat32, lat64oz;
 };
 int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_t N, double k, int nx, int ny,
                      double pitch, double cutoff, double taper, const double2* T64, const float2* T32, bool mixed,
-                     OpPair* ops);
+                     OpPair* ops, bool want_oz = false);
 }  // namespace tmat

@@ -108,7 +108,8 @@ extern "C" int tmat_sweep(tmat_ctx* ctx, const tmat_sweep_opts* sw, const tmat_a
     TM_LAUNCHED(ctx);
     TM_TRY(tmat_build(ctx, sat, n, wavelength, n_bg, nmax, (tmat_c128*)T, nullptr));
     TM_TRY(tmat_incident_jinc(ctx, pos, n, wavelength, n_bg, nmax, sxy, (const tmat_c128*)sA, (int64_t)cw * ch, R,
-                              sw->z0, sw->pitch, sw->n_beta, sw->n_alpha, opts->precision, (tmat_c128*)a0));
+                              sw->z0, sw->pitch, sw->n_beta, sw->n_alpha,
+                              opts->precision == TMAT_PREC_MIXED ? TMAT_PREC_MIXED : TMAT_PREC_FP64, (tmat_c128*)a0));
     tmat_solve_opts o = *opts;
     o.path = TMAT_PATH_LATTICE;
     o.lattice_nx = w;

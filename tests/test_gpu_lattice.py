@@ -123,3 +123,54 @@ def test_tensor_core_apply_matches_cuda_cores_and_oracle(nmax, nx, ny, cutoff, R
         ref = np.array([f(nmax, K0, pos, T, x[q], nbr) for q in range(R)])
     assert rel_l2(ytc, ref) <= C64_APPLY_TOL
     assert rel_l2(ytc, ycc) <= C64_APPLY_TOL
+
+
+@pytest.mark.parametrize("nmax,nx,ny,cutoff,R", [(4, 23, 9, 2.0, 2), (3, 17, 13, 1.6, 1), (2, 9, 7, 1.2, 3),
+                                                 (1, 11, 5, 1.0, 2), (4, 7, 6, 0.0, 5)])
+@pytest.mark.parametrize("op", [0, 1, 2])
+def test_fp64_tc_apply_matches_fp64(nmax, nx, ny, cutoff, R, op):
+    """TMAT_PREC_FP64_TC (exact bf16-slice products on the tensor cores) against the fp64
+    CUDA-core apply and the oracle; sources spanning six decades of magnitude."""
+    pos = W.lattice_positions(nx, ny)
+    r = W.uniform_radii(nx * ny, 0.08, 0.24, 80 + nmax)
+    T = np.array([mie.tmatrix_diag(nmax, K0, x, 2.0) for x in r])
+    x = rand_c((R, nx * ny, T.shape[1]), 90 + nmax)
+    x *= 10.0 ** (-6.0 * W.uniform_radii(nx * ny, 0.0, 1.0, 91))[None, :, None]
+    c = ctx()
+    c.set_timing(True)
+    n0, _ = c.kernel_time("lattice_apply_oz")
+    ytc = c.tmat_apply_lattice(op, 2, nx, ny, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
+    n1, _ = c.kernel_time("lattice_apply_oz")
+    c.set_timing(False)
+    assert n1 - n0 == 1
+    y64 = c.tmat_apply_lattice(op, 0, nx, ny, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
+    nbr = geometry.neighbours(pos, cutoff)
+    f = [system.apply_K, system.apply_KT, lambda nm, k, p, t, v, nb: system.apply_A(nm, k, p, v, nb)][op]
+    with system.window(cutoff, cutoff):
+        ref = np.array([f(nmax, K0, pos, T, x[q], nbr) for q in range(R)])
+    assert rel_l2(y64, ref) <= 1e-12
+    assert rel_l2(ytc, y64) <= 1e-11
+    assert rel_l2(ytc, ref) <= 1e-11
+
+
+def test_fp64_tc_solve_vs_oracle_and_neighbour_path_refused():
+    from paper_2107_09879_b300 import _lib
+    nmax, nx, ny, cutoff = 3, 9, 7, 1.5
+    pos = W.lattice_positions(nx, ny)
+    r = W.uniform_radii(nx * ny, 0.08, 0.24, 95)
+    at = atoms(r)
+    T = ctx().tmat_build(at, 1.0, 1.0, nmax)
+    a0 = ctx().tmat_incident_planewave(pos, 1.0, 1.0, nmax, np.array([[0.0, 0.0], [0.3, 0.0]]),
+                                       np.array([[1, 0, 0], [math.cos(0.3), 0, -math.sin(0.3)]], dtype=complex))
+    opts = _lib.make_opts(tol=1e-12, restart=80, max_iter=3000, cutoff=cutoff, taper=cutoff, precision=2, path=2,
+                          lattice_nx=nx, lattice_ny=ny, lattice_pitch=0.5)
+    s, info, _, rc = ctx().tmat_solve(pos, 1.0, 1.0, nmax, T, a0, opts)
+    assert rc == 0 and info.converged
+    To = np.array([mie.tmatrix_diag(nmax, K0, x, 2.0) for x in r])
+    with system.window(cutoff, cutoff):
+        ref = np.array([system.solve_dense(nmax, K0, pos, To, a0[q], cutoff) for q in range(2)])
+    assert rel_l2(s, ref) <= 1e-9
+    opts.path = 1
+    with pytest.raises(_lib.TMatError) as e:
+        ctx().tmat_solve(pos, 1.0, 1.0, nmax, T, a0, opts)
+    assert e.value.code == _lib.ENOTSUP
