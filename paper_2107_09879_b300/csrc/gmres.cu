@@ -21,7 +21,7 @@ __device__ __forceinline__ double2 shfl_down2(double2 v, int o) {
   return v;
 }
 
-// part[(r*nb + b)*maxv + k] = partial sum_i conj(V_k[r][i]) w[r][i], k < nvec
+// part[(r*maxv + k)*nb + b] = partial sum_i conj(V_k[r][i]) w[r][i], k < nvec
 template <typename VR>
 __global__ void __launch_bounds__(RED_THREADS)
 dots_kernel(const C<VR>* __restrict__ V, int64_t vstride, int nvec, const C<VR>* __restrict__ w, int64_t n,
@@ -66,65 +66,83 @@ dots_kernel(const C<VR>* __restrict__ V, int64_t vstride, int nvec, const C<VR>*
         s.x += red[q][threadIdx.x].x;
         s.y += red[q][threadIdx.x].y;
       }
-      part[((int64_t)r * nb + b) * maxv + k0 + threadIdx.x] = s;
+      part[((int64_t)r * maxv + k0 + threadIdx.x) * nb + b] = s;
     }
     __syncthreads();
   }
 }
 
 
-// ---- complex64 vectors: fp32 products, fp64 accumulation across blocks --------
+// ---- complex64 vectors: fp32 products, fp64 accumulation across warps/blocks ----
 // B300 runs fp64 FMAs at ~1/75 of the fp32 rate, so the per-element products of
-// the complex64 Krylov vectors are done in fp32 (each thread sums a few hundred
-// terms), and only the per-block partials are summed in fp64.
-constexpr int DOT32_CHUNK = 16;
+// the complex64 Krylov vectors are done in fp32 (a lane sums the products of its
+// elements, a warp its 32 lanes), and only the per-warp partials are summed in fp64.
+// Work unit = one warp: D32_VPW basis vectors over one contiguous element range; the
+// ranges per vector group are chosen so that ~48 warps per SM stream at once, each
+// with D32_VPW + 1 independent 512-byte loads per step (the same occupancy-driven
+// pattern as the update kernel). w is re-read once per vector group (from L1/L2).
+constexpr int D32_VPW = 8;
+constexpr int D32_NBMAX = 1024;  // element ranges per group (partials per dot)
 
-__global__ void __launch_bounds__(RED_THREADS)
+struct Dots32Plan {
+  int groups, ranges, blocks;
+};
+
+static inline Dots32Plan dots32_plan(int64_t n, int nvec, int num_sms, int R) {
+  Dots32Plan p;
+  p.groups = (nvec + D32_VPW - 1) / D32_VPW;
+  const int64_t target = (int64_t)num_sms * 48 / std::max(1, R);  // warps per RHS
+  int64_t nr = cdiv(target, (int64_t)p.groups);
+  nr = std::min<int64_t>(nr, std::max<int64_t>(1, cdiv(n / 2, (int64_t)32 * 16)));
+  p.ranges = (int)std::max<int64_t>(1, std::min<int64_t>(nr, D32_NBMAX));
+  p.blocks = (int)cdiv((int64_t)p.groups * p.ranges, 8);
+  return p;
+}
+
+__global__ void __launch_bounds__(256)
 dots32_kernel(const float2* __restrict__ V, int64_t vstride, int nvec, const float2* __restrict__ w, int64_t n,
-              int64_t rstride, double2* __restrict__ part, int maxv, const int* __restrict__ active) {
+              int64_t rstride, double2* __restrict__ part, int maxv, int groups, int ranges,
+              const int* __restrict__ active) {
   const int r = blockIdx.y;
   if (active && !active[r]) return;
-  __shared__ double2 red[RED_THREADS / 32][DOT32_CHUNK];
-  const int nb = gridDim.x, b = blockIdx.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t unit = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (unit >= (int64_t)groups * ranges) return;
+  const int g = (int)(unit / ranges), b = (int)(unit % ranges);
+  const int kb = g * D32_VPW;
   const int64_t n2 = n >> 1;  // float4 = two complex values (n is even)
+  const int64_t per = ((n2 + ranges - 1) / ranges + 31) / 32 * 32;
+  const int64_t lo = (int64_t)b * per, hi = lo + per < n2 ? lo + per : n2;
   const float4* w4 = reinterpret_cast<const float4*>(w + r * rstride);
-  for (int k0 = 0; k0 < nvec; k0 += DOT32_CHUNK) {
-    float2 acc[DOT32_CHUNK];
+  const float4* v4[D32_VPW];
 #pragma unroll
-    for (int c = 0; c < DOT32_CHUNK; ++c) acc[c] = make_float2(0.f, 0.f);
-    for (int64_t i = (int64_t)b * blockDim.x + threadIdx.x; i < n2; i += (int64_t)nb * blockDim.x) {
-      const float4 wv = w4[i];
+  for (int q = 0; q < D32_VPW; ++q) {
+    const int k = kb + q < nvec ? kb + q : kb;  // out-of-range vectors read a valid one, unused
+    v4[q] = reinterpret_cast<const float4*>(V + (int64_t)k * vstride + r * rstride);
+  }
+  float2 acc[D32_VPW];
 #pragma unroll
-      for (int c = 0; c < DOT32_CHUNK; ++c) {
-        if (k0 + c < nvec) {
-          const float4 v = reinterpret_cast<const float4*>(V + (int64_t)(k0 + c) * vstride + r * rstride)[i];
-          // conj(v) w for both complex values
-          acc[c].x = fmaf(v.x, wv.x, fmaf(v.y, wv.y, fmaf(v.z, wv.z, fmaf(v.w, wv.w, acc[c].x))));
-          acc[c].y = fmaf(v.x, wv.y, fmaf(-v.y, wv.x, fmaf(v.z, wv.w, fmaf(-v.w, wv.z, acc[c].y))));
-        }
-      }
-    }
+  for (int q = 0; q < D32_VPW; ++q) acc[q] = make_float2(0.f, 0.f);
+  for (int64_t i = lo + lane; i < hi; i += 32) {
+    const float4 wv = w4[i];
+    float4 v[D32_VPW];
 #pragma unroll
-    for (int c = 0; c < DOT32_CHUNK; ++c) {
-      double2 v = make_double2(acc[c].x, acc[c].y);
-      for (int o = 16; o > 0; o >>= 1) {
-        double2 t = shfl_down2(v, o);
-        v.x += t.x;
-        v.y += t.y;
-      }
-      if (lane == 0) red[warp][c] = v;
+    for (int q = 0; q < D32_VPW; ++q) v[q] = v4[q][i];
+#pragma unroll
+    for (int q = 0; q < D32_VPW; ++q) {
+      // conj(v) w for both complex values
+      acc[q].x = fmaf(v[q].x, wv.x, fmaf(v[q].y, wv.y, fmaf(v[q].z, wv.z, fmaf(v[q].w, wv.w, acc[q].x))));
+      acc[q].y = fmaf(v[q].x, wv.y, fmaf(-v[q].y, wv.x, fmaf(v[q].z, wv.w, fmaf(-v[q].w, wv.z, acc[q].y))));
     }
-    __syncthreads();
-    if (threadIdx.x < DOT32_CHUNK && k0 + threadIdx.x < nvec) {
-      double2 s = make_double2(0, 0);
-      for (int q = 0; q < RED_THREADS / 32; ++q) {
-        s.x += red[q][threadIdx.x].x;
-        s.y += red[q][threadIdx.x].y;
-      }
-      part[((int64_t)r * nb + b) * maxv + k0 + threadIdx.x] = s;
+  }
+#pragma unroll
+  for (int q = 0; q < D32_VPW; ++q) {
+    float2 v = acc[q];
+    for (int o = 16; o > 0; o >>= 1) {
+      v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+      v.y += __shfl_down_sync(0xffffffffu, v.y, o);
     }
-    __syncthreads();
+    if (lane == 0 && kb + q < nvec) part[((int64_t)r * maxv + kb + q) * ranges + b] = make_double2(v.x, v.y);
   }
 }
 
@@ -177,19 +195,79 @@ update32_kernel(const float2* __restrict__ V, int64_t vstride, int nvec, const d
   }
 }
 
-// out[r*maxv + k] = sum_b part[...] (fixed order)
-__global__ void reduce_kernel(const double2* __restrict__ part, int nb, int nvec, int maxv, double2* __restrict__ out,
-                              const int* __restrict__ active) {
-  const int r = blockIdx.x, k = blockIdx.y * blockDim.x + threadIdx.x;
+// out[r*maxv + k] = sum_b part[(r*maxv + k)*nb + b]: one block of RED2_THREADS per
+// (r, k); each thread sums a strided subset of the block partials, then a fixed tree
+// (deterministic order).
+constexpr int RED2_THREADS = 64;
+__global__ void __launch_bounds__(RED2_THREADS)
+reduce_kernel(const double2* __restrict__ part, int nb, int nvec, int maxv, double2* __restrict__ out,
+              const int* __restrict__ active) {
+  const int r = blockIdx.x, k = blockIdx.y;
   if (k >= nvec) return;
   if (active && !active[r]) return;
+  const double2* pp = part + ((int64_t)r * maxv + k) * nb;
   double2 s = make_double2(0, 0);
-  for (int b = 0; b < nb; ++b) {
-    double2 v = part[((int64_t)r * nb + b) * maxv + k];
+  for (int b = threadIdx.x; b < nb; b += RED2_THREADS) {
+    const double2 v = pp[b];
     s.x += v.x;
     s.y += v.y;
   }
-  out[r * maxv + k] = s;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double2 t = shfl_down2(s, o);
+    s.x += t.x;
+    s.y += t.y;
+  }
+  __shared__ double2 w2[RED2_THREADS / 32];
+  if ((threadIdx.x & 31) == 0) w2[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 t = w2[0];
+    for (int q = 1; q < RED2_THREADS / 32; ++q) {
+      t.x += w2[q].x;
+      t.y += w2[q].y;
+    }
+    out[r * maxv + k] = t;
+  }
+}
+
+static inline void launch_reduce(tmat_ctx* ctx, const double2* part, int nb, int nvec, int maxv, double2* out,
+                                 const int* active, int R) {
+  reduce_kernel<<<dim3(R, nvec), RED2_THREADS, 0, ctx->stream>>>(part, nb, nvec, maxv, out, active);
+}
+
+// ||v[r]||^2 block partials of complex64 vectors into part[(r*maxv + 0)*nb + b] (as the
+// .x of a double2): float4 loads, four in flight per thread, fp32 per thread, fp64 per block
+__global__ void __launch_bounds__(256)
+norm32_kernel(const float2* __restrict__ v, int64_t n, int64_t rstride, double2* __restrict__ part, int maxv,
+              const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  const int64_t n2 = n >> 1;
+  const float4* v4 = reinterpret_cast<const float4*>(v + r * rstride);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  float acc = 0.f;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n2; i += 4 * stride) {
+    float4 a[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) a[t] = v4[i + t * stride];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) acc += a[t].x * a[t].x + a[t].y * a[t].y + a[t].z * a[t].z + a[t].w * a[t].w;
+  }
+  for (; i < n2; i += stride) {
+    const float4 a = v4[i];
+    acc += a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
+  }
+  double d = acc;
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+  __shared__ double ws[8];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += ws[q];
+    part[(int64_t)r * maxv * gridDim.x + blockIdx.x] = make_double2(t, 0.0);  // slot k = 0
+  }
 }
 
 // out[r][i] += sign * sum_k V_k[r][i] coef[r][k]
@@ -293,49 +371,64 @@ __global__ void norm_from_dots_kernel(const double2* __restrict__ d, int maxv, d
 
 __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 
-// Givens step for column j (one thread per RHS); the column is worked on in
-// place in H[r][.][j] (global memory), so the restart length is not bounded by
-// registers.
+// Givens step for column j, one block per RHS: the previous rotations and the new
+// column are staged in shared memory by the block, then one thread applies the j
+// rotations in order (the recurrence is serial) and writes the column back to
+// H[r][.][j] in global memory (so the restart length is not bounded by registers).
 __global__ void givens_kernel(GState s, int R, int j, int m, int maxv) {
-  int r = threadIdx.x;
+  const int r = blockIdx.x;
   if (r >= R || !s.active[r]) return;
-  double2* col = s.H + (int64_t)r * maxv * m + j;  // element i at col[i * m]
-  for (int i = 0; i <= j; ++i) {
-    double2 a = s.hA[r * maxv + i], b = s.hB[r * maxv + i];
-    col[(int64_t)i * m] = make_double2(a.x + b.x, a.y + b.y);
+  extern __shared__ double2 gsm[];
+  double2* cs = gsm;          // [j]
+  double2* sn = cs + m;       // [j]
+  double2* col = sn + m;      // [j + 1]
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    cs[i] = s.cs[r * m + i];
+    sn[i] = s.sn[r * m + i];
   }
-  const double hn = s.nrm[r];
-  double2 hj1 = make_double2(hn, 0);  // H[j+1][j], never stored
-  // rotation G_i = [[conj(c_i), conj(s_i)], [-s_i, c_i]]
-  for (int i = 0; i < j; ++i) {
-    double2 c = s.cs[r * m + i], sn = s.sn[r * m + i];
-    double2 t0 = col[(int64_t)i * m], t1 = col[(int64_t)(i + 1) * m];
-    col[(int64_t)i * m] = make_double2(c.x * t0.x + c.y * t0.y + sn.x * t1.x + sn.y * t1.y,
-                                       c.x * t0.y - c.y * t0.x + sn.x * t1.y - sn.y * t1.x);
-    col[(int64_t)(i + 1) * m] = make_double2(-(sn.x * t0.x - sn.y * t0.y) + (c.x * t1.x - c.y * t1.y),
-                                             -(sn.x * t0.y + sn.y * t0.x) + (c.x * t1.y + c.y * t1.x));
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    const double2 a = s.hA[r * maxv + i], b = s.hB[r * maxv + i];
+    col[i] = make_double2(a.x + b.x, a.y + b.y);
   }
-  double2 hjj = col[(int64_t)j * m];
-  double den = sqrt(cabs2(hjj) + cabs2(hj1));
-  double2 c = make_double2(1, 0), sn = make_double2(0, 0);
-  if (den > 0) {
-    c = make_double2(hjj.x / den, hjj.y / den);
-    sn = make_double2(hj1.x / den, hj1.y / den);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double hn = s.nrm[r];
+    // rotation G_i = [[conj(c_i), conj(s_i)], [-s_i, c_i]]
+    double2 t0 = col[0];
+    for (int i = 0; i < j; ++i) {
+      const double2 c = cs[i], sv = sn[i];
+      const double2 t1 = col[i + 1];
+      col[i] = make_double2(c.x * t0.x + c.y * t0.y + sv.x * t1.x + sv.y * t1.y,
+                            c.x * t0.y - c.y * t0.x + sv.x * t1.y - sv.y * t1.x);
+      t0 = make_double2(-(sv.x * t0.x - sv.y * t0.y) + (c.x * t1.x - c.y * t1.y),
+                        -(sv.x * t0.y + sv.y * t0.x) + (c.x * t1.y + c.y * t1.x));
+    }
+    const double2 hjj = t0;
+    const double2 hj1 = make_double2(hn, 0);  // H[j+1][j], never stored
+    const double den = sqrt(cabs2(hjj) + cabs2(hj1));
+    double2 c = make_double2(1, 0), sv = make_double2(0, 0);
+    if (den > 0) {
+      c = make_double2(hjj.x / den, hjj.y / den);
+      sv = make_double2(hj1.x / den, hj1.y / den);
+    }
+    s.cs[r * m + j] = c;
+    s.sn[r * m + j] = sv;
+    col[j] = make_double2(den, 0);
+    const double2 gj = s.g[r * maxv + j];
+    s.g[r * maxv + j + 1] = make_double2(-(sv.x * gj.x - sv.y * gj.y), -(sv.x * gj.y + sv.y * gj.x));
+    s.g[r * maxv + j] = make_double2(c.x * gj.x + c.y * gj.y, c.x * gj.y - c.y * gj.x);
+    s.ncols[r] = j + 1;
+    const double res = sqrt(cabs2(s.g[r * maxv + j + 1]));
+    if (!isfinite(res) || !isfinite(hn)) {
+      s.flags[r] |= 1;  // NaN / Inf
+      s.active[r] = 0;
+    } else if (res <= s.tol_abs[r] || hn == 0.0) {
+      s.active[r] = 0;
+    }
   }
-  s.cs[r * m + j] = c;
-  s.sn[r * m + j] = sn;
-  col[(int64_t)j * m] = make_double2(den, 0);
-  double2 gj = s.g[r * maxv + j];
-  s.g[r * maxv + j + 1] = make_double2(-(sn.x * gj.x - sn.y * gj.y), -(sn.x * gj.y + sn.y * gj.x));
-  s.g[r * maxv + j] = make_double2(c.x * gj.x + c.y * gj.y, c.x * gj.y - c.y * gj.x);
-  s.ncols[r] = j + 1;
-  double res = sqrt(cabs2(s.g[r * maxv + j + 1]));
-  if (!isfinite(res) || !isfinite(hn)) {
-    s.flags[r] |= 1;  // NaN / Inf
-    s.active[r] = 0;
-  } else if (res <= s.tol_abs[r] || hn == 0.0) {
-    s.active[r] = 0;
-  }
+  __syncthreads();
+  double2* hcol = s.H + (int64_t)r * maxv * m + j;  // element i at hcol[i * m]
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) hcol[(int64_t)i * m] = col[i];
 }
 
 // back substitution y = H^{-1} g over the first ncols columns
@@ -364,13 +457,25 @@ static unsigned grid_for(tmat_ctx* ctx, int64_t n) {
   return (unsigned)(g < cap ? (g < 1 ? 1 : g) : cap);
 }
 
-// norms of R vectors (rstride apart) into nrm[r] (device); uses dots
+// norms of R vectors (rstride apart) into nrm[r] (device)
 template <typename VR>
 static int vec_norms(tmat_ctx* ctx, const C<VR>* v, int64_t n, int64_t rstride, int R, double2* part, int nb,
                      double2* tmp, int maxv, double* nrm, const int* active) {
+  if constexpr (sizeof(VR) == 4) {
+    if ((n & 1) == 0) {
+      const int nbn = (int)std::max<int64_t>(1, std::min<int64_t>(nb, cdiv(n / 2, 256 * 8)));
+      norm32_kernel<<<dim3(nbn, R), 256, 0, ctx->stream>>>(v, n, rstride, part, maxv, active);
+      TM_LAUNCHED(ctx);
+      launch_reduce(ctx, part, nbn, 1, maxv, tmp, active, R);
+      TM_LAUNCHED(ctx);
+      norm_from_dots_kernel<<<1, 32, 0, ctx->stream>>>(tmp, maxv, nrm, R, active);
+      TM_LAUNCHED(ctx);
+      return TMAT_OK;
+    }
+  }
   dots_kernel<VR><<<dim3(nb, R), RED_THREADS, 0, ctx->stream>>>(v, 0, 1, v, n, rstride, part, maxv, active);
   TM_LAUNCHED(ctx);
-  reduce_kernel<<<dim3(R, 1), 32, 0, ctx->stream>>>(part, nb, 1, maxv, tmp, active);
+  launch_reduce(ctx, part, nb, 1, maxv, tmp, active, R);
   TM_LAUNCHED(ctx);
   norm_from_dots_kernel<<<1, 32, 0, ctx->stream>>>(tmp, maxv, nrm, R, active);
   TM_LAUNCHED(ctx);
@@ -392,7 +497,7 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
   C<VR>* xv;  // x in operator precision (for the true residual)
   TM_TRY(scratch(ctx, sizeof(VR) == 4 ? "g_xv32" : "g_xv64", sizeof(C<VR>) * (size_t)R * n, (void**)&xv));
   double2* part;
-  TM_TRY(scratch(ctx, "g_part", sizeof(double2) * (size_t)R * nb * maxv, (void**)&part));
+  TM_TRY(scratch(ctx, "g_part", sizeof(double2) * (size_t)R * std::max(nb, D32_NBMAX) * maxv, (void**)&part));
   GState s;
   char* small;
   const size_t R_ = R;
@@ -455,15 +560,18 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
         TM_TRY(op_apply(ctx, A, mode, vj, w, R));
         for (int pass = 0; pass < 2; ++pass) {
           double2* hc = pass == 0 ? s.hA : s.hB;
+          int nbp = nb;
           if constexpr (sizeof(VR) == 4) {
-            dots32_kernel<<<dim3(nb, R), RED_THREADS, 0, ctx->stream>>>(V, (int64_t)R * n, j + 1, w, n, rs, part,
-                                                                         maxv, s.active);
+            const Dots32Plan dp = dots32_plan(n, j + 1, ctx->num_sms, R);
+            nbp = dp.ranges;
+            dots32_kernel<<<dim3(dp.blocks, R), 256, 0, ctx->stream>>>(V, (int64_t)R * n, j + 1, w, n, rs, part, maxv,
+                                                                        dp.groups, dp.ranges, s.active);
           } else {
             dots_kernel<VR><<<dim3(nb, R), RED_THREADS, 0, ctx->stream>>>(V, (int64_t)R * n, j + 1, w, n, rs, part,
                                                                            maxv, s.active);
           }
           TM_LAUNCHED(ctx);
-          reduce_kernel<<<dim3(R, (unsigned)cdiv(j + 1, 128)), 128, 0, ctx->stream>>>(part, nb, j + 1, maxv, hc, s.active);
+          launch_reduce(ctx, part, nbp, j + 1, maxv, hc, s.active, R);
           TM_LAUNCHED(ctx);
           if constexpr (sizeof(VR) == 4) {
             update32_kernel<<<dim3(g1, R), 256, sizeof(float2) * (j + 1), ctx->stream>>>(
@@ -477,7 +585,10 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
         TM_TRY(vec_norms<VR>(ctx, w, n, rs, R, part, nb, s.y, maxv, s.nrm, s.active));
         scale_kernel<VR, VR><<<dim3(g1, R), 256, 0, ctx->stream>>>(w, w, n, rs, s.nrm, 1, s.active);
         TM_LAUNCHED(ctx);
-        givens_kernel<<<1, 32, 0, ctx->stream>>>(s, R, j, m, maxv);
+        const size_t gsm_bytes = sizeof(double2) * (2 * (size_t)m + maxv);
+        if (gsm_bytes > 48 * 1024)
+          TM_CUDA(ctx, cudaFuncSetAttribute(givens_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm_bytes));
+        givens_kernel<<<R, 64, gsm_bytes, ctx->stream>>>(s, R, j, m, maxv);
         TM_LAUNCHED(ctx);
         st->iterations++;
         int* ipin = (int*)ctx->pinned;

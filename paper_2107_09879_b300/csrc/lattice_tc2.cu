@@ -34,7 +34,8 @@ template <int NMAX> struct Tc2Shape {
   static constexpr int KR = 2 * LP2;
   static constexpr int KC = KR / 4;
   static constexpr int W_BYTES = KR * KR * 4;
-  static constexpr int TMEM_COLS = KR <= 32 ? 32 : (KR <= 64 ? 64 : 128);
+  // one accumulator set: columns [0, KR) collect A_hi W_hi + A_lo W_hi, [KR, 2 KR) A_hi W_lo
+  static constexpr int TMEM_COLS = 2 * KR <= 32 ? 32 : (2 * KR <= 64 ? 64 : 128);
 };
 
 __device__ __forceinline__ uint32_t smem_u32_2(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -156,7 +157,10 @@ lattice_tc2_kernel(const int2* __restrict__ off, int K, const int* __restrict__ 
   if (warp == 0) {
     // ---------------- window loads + MMA issue ----------------
     if (lane == 0) {
-      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(KR >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+      // kind::tf32, fp32 accumulate, K-major A and B, M = 128; N = 2 KR (the W head and
+      // tail tiles are consecutive row groups, so one B descriptor covers both) or KR
+      const uint32_t idesc_hl = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)((2 * KR) >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+      const uint32_t idesc_h = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(KR >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
       const uint32_t winbase = smem_u32_2(sWin);
       const uint32_t plane_bytes = (uint32_t)WL * 16;
       int kk = 0, committed = 0, issued_win = 0;
@@ -199,22 +203,21 @@ lattice_tc2_kernel(const int2* __restrict__ off, int K, const int* __restrict__ 
           asm volatile("tcgen05.fence::after_thread_sync;");
           const int dx = o0.x + (kk - gs);
           const uint32_t ashift = (uint32_t)(CX + dx) * 16;
-          const uint32_t wh = smem_u32_2(sW + wb * W_STAGE), wl = wh + S::W_BYTES;
+          const uint32_t wh = smem_u32_2(sW + wb * W_STAGE);
           const uint32_t dacc = tmem + (uint32_t)(a * ACC_COLS);
 #pragma unroll
           for (int s = 0; s < KR / 8; ++s) {
             const uint32_t ah = winbase + (uint32_t)(0 * KC + 2 * s) * plane_bytes + ashift;
             const uint32_t al = winbase + (uint32_t)(1 * KC + 2 * s) * plane_bytes + ashift;
             const uint64_t dAh = umma_desc2(ah, plane_bytes, 128), dAl = umma_desc2(al, plane_bytes, 128);
-            const uint64_t dWh = umma_desc2(wh + s * 256, 128, KC * 128), dWl = umma_desc2(wl + s * 256, 128, KC * 128);
+            const uint64_t dWh = umma_desc2(wh + s * 256, 128, KC * 128);
             const uint32_t acc0 = (!first_in_group || s > 0) ? 1u : 0u;
+            // A_hi [W_hi; W_lo] (N = 2 KR), then A_lo W_hi into the first KR columns
             asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                          "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-                         :: "r"(dacc), "l"(dAh), "l"(dWh), "r"(idesc), "r"(acc0));
+                         :: "r"(dacc), "l"(dAh), "l"(dWh), "r"(idesc_hl), "r"(acc0));
             asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
-                         :: "r"(dacc), "l"(dAh), "l"(dWl), "r"(idesc));
-            asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
-                         :: "r"(dacc), "l"(dAl), "l"(dWh), "r"(idesc));
+                         :: "r"(dacc), "l"(dAl), "l"(dWh), "r"(idesc_h));
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                        :: "r"(bar(WEMPTY + wb)) : "memory");
@@ -280,7 +283,7 @@ lattice_tc2_kernel(const int2* __restrict__ off, int K, const int* __restrict__ 
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-      for (int c0 = 0; c0 < KR; c0 += 16) {
+      for (int c0 = 0; c0 < 2 * KR; c0 += 16) {
         uint32_t v[16];
         const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(a * ACC_COLS + c0);
         asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -288,8 +291,9 @@ lattice_tc2_kernel(const int2* __restrict__ off, int K, const int* __restrict__ 
                        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
                      : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;");
+        const int cb = c0 < KR ? c0 : c0 - KR;  // the W-tail columns add onto the same outputs
 #pragma unroll
-        for (int e = 0; e < 16; ++e) accr[c0 + e] += __uint_as_float(v[e]);
+        for (int e = 0; e < 16; ++e) accr[cb + e] += __uint_as_float(v[e]);
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(bar(ACCEMPTY + a)) : "memory");
