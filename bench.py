@@ -114,6 +114,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands
+# (profiles/lattice_tc2_200x200_nmax4.md); set to None when the kernel changes.
+MEASURED_TRAFFIC = {"lattice_tc2_kernel<4,0>": 238.0e6 + 23.0e6}
+
+
 def roofline(kern_name, achieved, launches, avg_ms, flop_per_launch):
     extra = {}
     if "tcgen05" in kern_name:
@@ -127,8 +132,9 @@ def roofline(kern_name, achieved, launches, avg_ms, flop_per_launch):
     else:
         peak, note = FP32_PEAK_TFLOPS, "FP32 FMA issue rate: 148 SMs x 128 lanes x 2 flop x 2.032 GHz (derived)"
         bound = "alu"
+    traffic = next((v for k, v in MEASURED_TRAFFIC.items() if kern_name.startswith(k)), None)
     out = {"kernel": kern_name, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-           "frac": (achieved / peak) if achieved else None, "traffic": None, "launches": launches,
+           "frac": (achieved / peak) if achieved else None, "traffic": traffic, "launches": launches,
            "avg_launch_ms": avg_ms, "flop_per_launch": flop_per_launch, "peak_note": note}
     out.update(extra)
     return out
