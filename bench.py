@@ -37,6 +37,7 @@ METRIC = "solves/s + p50/p99 latency; T-matvec GFLOP/s, mixed vs FP64 at 1e-6 re
 UNIT = "solves/s"
 TOL = 1e-7  # refinement stops at ||r|| / ||b|| <= 1e-7, so the solution error is <= 1e-6
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
+HBM_PEAK_GBS = 6451.5  # measured copy bandwidth of the B300s (MEASURED_PEAKS.json)
 
 
 def workload():
@@ -138,6 +139,20 @@ def roofline(kern_name, achieved, launches, avg_ms, flop_per_launch):
            "avg_launch_ms": avg_ms, "flop_per_launch": flop_per_launch, "peak_note": note}
     out.update(extra)
     return out
+
+
+def roofline_fft(nmul, msmul, mul_bytes, napply, avg_apply_ms, flop_per_apply):
+    """FFT path: the dominant kernel is the per-frequency block product, which streams the
+    block spectra B^ (2 L^2 Mx My complex64) and the RHS spectra once: HBM bound."""
+    avg = msmul / nmul
+    achieved = mul_bytes / (avg * 1e-3) / 1e9
+    return {"kernel": "fft_mul_kernel<float,24,0,2> (per-frequency 24x24 block products, CUDA cores)",
+            "bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+            "frac": achieved / HBM_PEAK_GBS, "traffic": MEASURED_TRAFFIC.get("fft_mul_kernel<float,24,0,2>"),
+            "launches": nmul, "avg_launch_ms": avg, "bytes_per_launch": mul_bytes,
+            "peak_note": "STREAM-style copy bandwidth of MEASURED_PEAKS.json (of measured)",
+            "apply_avg_ms": avg_apply_ms,
+            "apply_share_of_mul": avg / avg_apply_ms if avg_apply_ms else None}
 
 
 def cpu_baseline(wl, matvecs_per_solve, budget_s=12.0):
@@ -346,6 +361,7 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     ctx = _lib.Context(dev, None)
     ctx.set_tensor_cores(0 if args.cuda_cores else args.tc_variant)
+    ctx.set_lattice_fft(not args.direct)
     wl = workload()
     w = wl["w"]
     nmax, cutoff = w["nmax"], w["cutoff"]
@@ -395,19 +411,26 @@ def run_ours(args, rank, world):
     per_step = sorted(a.elapsed_time(b) for a, b in evs)
     total_ms = sum(per_step)
     gpu_launches = ctx.launches() - launches0
-    n32, ms32 = ctx.kernel_time("lattice_apply_tcv")
-    kern_name = "lattice_tc2_kernel<4,0> (tcgen05 3xTF32, window view)"
-    if n32 == 0:
-        n32, ms32 = ctx.kernel_time("lattice_apply_tc")
-        kern_name = "lattice_tc_kernel<4,2,0> (tcgen05 3xTF32, gather)"
-    if n32 == 0:
-        n32, ms32 = ctx.kernel_time("lattice_apply_fp32")
-        kern_name = "lattice_apply_kernel<float,4,2,0> (CUDA cores)"
-    n64, ms64 = ctx.kernel_time("lattice_apply_oz")
-    res_kernel = "lattice_oz_kernel<4,0> (tcgen05 bf16 slices, exact group sums, fp64-class)"
-    if n64 == 0:
-        n64, ms64 = ctx.kernel_time("lattice_apply_fp64")
-        res_kernel = "lattice_apply_kernel<double,4,2,0> (FP64 CUDA cores)"
+    apply_kinds = [("lattice_apply_fft32", "FFT convolution, complex64 (lattice_fft.cu)"),
+                   ("lattice_apply_tcv", "lattice_tc2_kernel<4,0> (tcgen05 3xTF32, window view)"),
+                   ("lattice_apply_tc", "lattice_tc_kernel<4,2,0> (tcgen05 3xTF32, gather)"),
+                   ("lattice_apply_fp32", "lattice_apply_kernel<float,4,2,0> (CUDA cores)")]
+    n32, ms32, kern_name = 0, 0.0, None
+    for kind, name in apply_kinds:
+        n32, ms32 = ctx.kernel_time(kind)
+        kern_name = name
+        if n32:
+            break
+    nmul, msmul = ctx.kernel_time("lattice_fft_mul32")
+    res_kinds = [("lattice_apply_fft64", "FFT convolution, complex128 (lattice_fft.cu)"),
+                 ("lattice_apply_oz", "lattice_oz_kernel<4,0> (tcgen05 bf16 slices, exact group sums, fp64-class)"),
+                 ("lattice_apply_fp64", "lattice_apply_kernel<double,4,2,0> (FP64 CUDA cores)")]
+    n64, ms64, res_kernel = 0, 0.0, None
+    for kind, name in res_kinds:
+        n64, ms64 = ctx.kernel_time(kind)
+        res_kernel = name
+        if n64:
+            break
 
     ctx.set_timing(False)
     it = [i.iterations for i in infos]
@@ -437,6 +460,8 @@ def run_ours(args, rank, world):
     flop_per_launch = 8.0 * (P * P / 2) * pairs * R  # nonzero complex MACs x 8 flop, both RHS per launch
     avg32 = ms32 / max(n32, 1)
     achieved = flop_per_launch / (avg32 * 1e-3) / 1e12 if n32 else None
+    fft_grid = 256 * 256  # power-of-two grid >= 200 + 16 in each direction
+    mul_bytes = 2 * 24 * 24 * fft_grid * 8 + 2 * R * P * fft_grid * 8  # B^ read, X^ read, Y^ write
     matvecs = int(round(statistics.mean(it))) + int(round(statistics.mean(ref)))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -448,7 +473,10 @@ def run_ours(args, rank, world):
         "p50_ms": per_step[len(per_step) // 2], "p99_ms": per_step[min(len(per_step) - 1, int(0.99 * len(per_step)))],
         "gmres_iterations_per_solve": statistics.mean(it), "refinements_per_solve": statistics.mean(ref),
         "tmatvec_gflops": (flop_per_launch / (avg32 * 1e-3) / 1e9) if n32 else None,
-        "roofline": roofline(kern_name, achieved, n32, avg32, flop_per_launch),
+        "roofline": (roofline_fft(nmul, msmul, mul_bytes, n32, avg32, flop_per_launch) if nmul else
+                     roofline(kern_name, achieved, n32, avg32, flop_per_launch)),
+        "operator_apply": {"path": kern_name, "launches": n32, "avg_ms": avg32,
+                           "direct_sum_equivalent_tflops": achieved},
         "fp64_residual_kernel": res_kernel, "fp64_residual_launches": n64,
         "fp64_residual_avg_ms": (ms64 / n64) if n64 else None,
         "e2e": {"value": world * 1e3 / statistics.median(e2e_ms), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -475,6 +503,7 @@ def run_kernel_only(args):
     from paper_2107_09879_b300 import _lib
     ctx = _lib.Context(0, None)
     ctx.set_tensor_cores(0 if args.cuda_cores else args.tc_variant)
+    ctx.set_lattice_fft(not args.direct)
     wl = workload()
     w = wl["w"]
     N, P, R = len(wl["pos"]), 48, 2
@@ -489,8 +518,9 @@ def run_kernel_only(args):
                                    w["nmax"], T, x, taper=w["cutoff"])
     kind = {0: "lattice_apply_fp64", 1: "lattice_apply_fp32", 2: "lattice_apply_oz"}[args.kernel_precision]
     n, ms = ctx.kernel_time(kind)
-    for alt in ("lattice_apply_tcv", "lattice_apply_tc"):
-        if args.kernel_precision == _lib.PREC_MIXED and n == 0:
+    for alt in ({0: "lattice_apply_fft64", 1: "lattice_apply_fft32"}.get(args.kernel_precision, "none"),
+                "lattice_apply_tcv", "lattice_apply_tc"):
+        if n == 0:
             kind = alt
             n, ms = ctx.kernel_time(kind)
     pairs = pairs_within(200, 200, int(round(w["cutoff"] / PITCH)))
@@ -533,6 +563,8 @@ def main():
     ap.add_argument("--kernel-only", action="store_true", help="time the dominant kernel alone (for ncu captures)")
     ap.add_argument("--kernel-precision", type=int, default=1, help="1: complex64 apply, 0: complex128 apply, 2: fp64-class tensor-core apply")
     ap.add_argument("--cuda-cores", action="store_true", help="complex64 apply on CUDA cores instead of tcgen05")
+    ap.add_argument("--direct", action="store_true",
+                    help="lattice operator by the direct block-Toeplitz kernels instead of FFT convolution")
     ap.add_argument("--tc-variant", type=int, default=1, choices=[1, 2],
                     help="tensor-core lattice kernel: 1 window view (default), 2 gather")
     args = ap.parse_args()

@@ -135,6 +135,16 @@ int64_t tmat_ctx_launch_count(const tmat_ctx* ctx);
  * kind since timing was (re)enabled: "lattice_apply_fp32", "lattice_apply_fp64",
  * "nbr_apply_fp32", "nbr_apply_fp64". Enabling again resets the record. */
 int tmat_ctx_set_timing(tmat_ctx* ctx, int enable);
+/* Lattice operators (tmat_apply_lattice, the lattice path of tmat_solve, tmat_sweep)
+ * are applied by FFT convolution when the grid fits (nx + max|dx| <= 1024 and
+ * ny + max|dy| <= 1024): y_i = sum_o B_o x_{i+o} as a circular convolution on a
+ * zero-padded power-of-two grid, one L x L block product per frequency, in the
+ * operator's precision (complex64 or complex128 arithmetic throughout). enable = 0
+ * selects the direct block-Toeplitz kernels (tensor cores / CUDA cores). Default: 1.
+ * Timing kinds: "lattice_apply_fft32", "lattice_apply_fft64" (whole applies),
+ * "lattice_fft_mul32", "lattice_fft_mul64" (the per-frequency block products). */
+int tmat_ctx_set_lattice_fft(tmat_ctx* ctx, int enable);
+
 /* Complex64 lattice applies run on the tcgen05 tensor cores (3xTF32, nmax <= 4)
  * unless disabled here (enable = 0: the CUDA-core fp32 kernel runs, and the mixed
  * refinement residual uses the fp64 CUDA-core kernel). enable = 1

@@ -66,6 +66,7 @@ _SIGS = {
     "tmat_ctx_launch_count": [_vp],
     "tmat_ctx_set_timing": [_vp, _int],
     "tmat_ctx_set_tensor_cores": [_vp, _int],
+    "tmat_ctx_set_lattice_fft": [_vp, _int],
     "tmat_ctx_kernel_time": [_vp, ct.c_char_p, ct.POINTER(_i64), ct.POINTER(_d)],
     "tmat_neighbors": [_vp, _vp, _i64, _d, _vp, _vp, ct.POINTER(_i64)],
     "tmat_subregions": [_vp, _i64, _i64, _i64, _i64, _i64, _vp, _vp, _vp, _vp, ct.POINTER(_i64), ct.POINTER(_i64)],
@@ -155,6 +156,10 @@ class Context:
     def set_tensor_cores(self, on):
         """0/False: CUDA cores; 1/True: tensor cores (window-view kernel where it fits); 2: gather kernel."""
         self.check(lib.tmat_ctx_set_tensor_cores(self.h, int(on)))
+
+    def set_lattice_fft(self, on):
+        """1: lattice operators by FFT convolution where the grid fits (default); 0: direct kernels."""
+        self.check(lib.tmat_ctx_set_lattice_fft(self.h, 1 if on else 0))
 
     def set_timing(self, on):
         self.check(lib.tmat_ctx_set_timing(self.h, 1 if on else 0))

@@ -153,6 +153,12 @@ extern "C" const char* tmat_last_error(const tmat_ctx* ctx) { return ctx ? ctx->
 
 extern "C" int64_t tmat_ctx_launch_count(const tmat_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+extern "C" int tmat_ctx_set_lattice_fft(tmat_ctx* ctx, int enable) {
+  if (!ctx) return TMAT_EINVAL;
+  ctx->lattice_fft = enable != 0;
+  return TMAT_OK;
+}
+
 extern "C" int tmat_ctx_set_tensor_cores(tmat_ctx* ctx, int enable) {
   if (!ctx) return TMAT_EINVAL;
   ctx->tensor_cores = enable != 0;

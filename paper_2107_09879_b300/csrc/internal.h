@@ -68,6 +68,7 @@ struct tmat_ctx {
   int num_sms = 148;
   bool tensor_cores = true;  // use the tcgen05 kernels where they exist
   int tc_variant = 0;        // 0: window-view kernel where it fits, 1: gather kernel
+  bool lattice_fft = true;   // lattice operators by FFT convolution where the grid fits
   void* pinned = nullptr;  // small pinned host staging area (status words)
 };
 

@@ -228,6 +228,7 @@ static int lat_mode(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void
 
 int lattice_apply(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void* y, int R_) {
   if (a.N == 0) return TMAT_OK;
+  if (a.use_fft) return lattice_fft_apply(ctx, a, mode, x, y, R_);
   if (!a.fp32 && a.use_oz) return lattice_oz_apply(ctx, a, mode, x, y, R_);
   if (a.fp32 && a.use_tc && ctx->tensor_cores) {
     if (a.tc2 && ctx->tc_variant != 1) return lattice_tc2_apply(ctx, a, mode, x, y, R_);
@@ -258,7 +259,7 @@ __global__ void lattice_check_kernel(const double* __restrict__ pos, int64_t N, 
 
 int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_t N, double k, int nx, int ny,
                      double pitch, double cutoff, double taper, const double2* T64, const float2* T32, bool mixed,
-                     OpPair* ops, bool want_oz) {
+                     OpPair* ops, int want_oz) {
   if (nx <= 0 || ny <= 0 || (int64_t)nx * ny != N || !(pitch > 0))
     return set_error(ctx, TMAT_EINVAL, "lattice path: need lattice_nx * lattice_ny == N and pitch > 0");
   {
@@ -352,10 +353,17 @@ int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_
   a.fp32 = false;
   a.BT = B64;
   a.T = T64;
+  const bool fft = ctx->lattice_fft && K > 0 && lattice_fft_fits(nx, ny, CX, CY);
+  if (fft) TM_TRY(lattice_fft_prepare(ctx, &a));
   ops->lat64 = a;
+  a.use_fft = false;
+  a.fft_Bhat = nullptr;
   ops->A64.kind = 1;
   ops->A64.lat = &ops->lat64;
-  if (want_oz && ctx->tensor_cores && t->nmax <= 4 && K > 0 && dx_contiguous && lattice_oz_fits(t->nmax, CX)) {
+  // the fp64-class tensor-core operator: for TMAT_PREC_FP64_TC, or for the refinement
+  // residual when the fp64 operator is not already the (fp64) FFT one
+  if ((want_oz == 2 || (want_oz == 1 && !fft)) && ctx->tensor_cores && t->nmax <= 4 && K > 0 && dx_contiguous &&
+      lattice_oz_fits(t->nmax, CX)) {
     LatOp z = a;
     TM_TRY(lattice_oz_prepare(ctx, &z, B64));
     z.use_oz = true;
@@ -368,7 +376,9 @@ int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_
     a.fp32 = true;
     a.BT = B32;
     a.T = T32;
-    if (lattice_tc_supported(t->nmax) && K > 0 && dx_contiguous && lattice_tc_fits(t->nmax, CX)) {
+    if (fft) {
+      TM_TRY(lattice_fft_prepare(ctx, &a));
+    } else if (lattice_tc_supported(t->nmax) && K > 0 && dx_contiguous && lattice_tc_fits(t->nmax, CX)) {
       TM_TRY(lattice_tc_prepare(ctx, &a, B64));
       a.use_tc = true;
       a.tc2 = lattice_tc2_fits(t->nmax, CX);
@@ -422,7 +432,7 @@ extern "C" int tmat_apply_lattice(tmat_ctx* ctx, int op, int precision, int nx, 
   OpPair ops;
   const bool emu = precision == TMAT_PREC_FP64_TC;
   TM_TRY(make_lattice_ops(ctx, t, dpos, N, k, nx, ny, pitch, cutoff, taper, (const double2*)T64, (const float2*)T32, fp32,
-                          &ops, emu));
+                          &ops, emu ? 2 : 0));
   if (emu && !ops.have_oz)
     return set_error(ctx, TMAT_ENOTSUP, "TMAT_PREC_FP64_TC needs tensor cores enabled, nmax <= 4 and a cutoff window that fits");
   const size_t esz = fp32 ? sizeof(float2) : sizeof(double2);

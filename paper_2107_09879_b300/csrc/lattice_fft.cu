@@ -1,0 +1,385 @@
+// Lattice operator apply by FFT convolution.
+//
+// On a row-major nx x ny lattice the coupling sum y_i = sum_o B_o x_{i+o} (one block B_o
+// per lattice offset o inside the cutoff, the same blocks the direct kernels use) is a
+// 2-D correlation of the source field with the offset blocks. With b(p) = B(-p) it is the
+// circular convolution y = b (*) x on an Mx x My grid, exact (no wrap-around) for
+// Mx >= nx + CX and My >= ny + CY, CX/CY the largest |dx|/|dy| of the offsets, and the
+// zero-padded sources. In Fourier space it is one L x L block product per frequency and
+// class: Y(f) = B^(f) X(f). The work is O(Mx My L^2) for the products plus FFTs of the
+// 2 L components of every RHS, against O(N K L^2) for the direct sum (K offsets).
+//
+// Data flow (every array component-major, rows contiguous):
+//   embed   x[r][site][u] (times T for the adjoint)  -> Xc[r*P+u][iy][ix]      (ny x nx)
+//   F1      FFT along ix (zero-padded to Mx), write transposed -> T1[.][kx][iy]  (Mx x ny)
+//   F2      FFT along iy (zero-padded to My)               -> X^[.][kx][ky]   (Mx x My)
+//   mul     per frequency and class: Y^[u] = sum_u' B^[c][u][u'] X^[u']   (adjoint: the
+//           transposed blocks at -f, since A^T has blocks B_{-o}^T)
+//   I2      inverse FFT along ky, keep iy < ny, write transposed -> T3[.][iy][kx]
+//   I1      inverse FFT along kx, keep ix < nx               -> Yc[.][iy][ix]
+//   extract y[r][site][u] = x - T (Yc / (Mx My)), x - Yc / (Mx My) or Yc / (Mx My)
+// B^ is built once per operator by the same F1/F2 passes from the blocks scattered to
+// grid position -o. The FFT is an iterative radix-2 decimation in time in shared memory
+// (Cooley and Tukey, Math. Comp. 19 (1965)) with fp64 twiddles (cast for complex64).
+#include <cmath>
+#include <vector>
+
+#include "dev.cuh"
+#include "solver.h"
+
+namespace tmat {
+
+constexpr int FFT_MAXLEN = 1024;     // longest row transform
+constexpr int FFT_THREADS = 256;
+constexpr int FFT_SMEM_POINTS = 8192;  // complex points staged per block
+
+static int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+static int pow2_at_least(int v) { return 1 << ilog2(std::max(1, v)); }
+
+// tw[k] = exp(-2 pi i k / FFT_MAXLEN), k < FFT_MAXLEN / 2, in fp64
+static int fft_twiddles(tmat_ctx* ctx, const double2** out) {
+  double2* tw;
+  bool fresh = ctx->bufs.find("fft_tw") == ctx->bufs.end();
+  TM_TRY(scratch(ctx, "fft_tw", sizeof(double2) * (FFT_MAXLEN / 2), (void**)&tw));
+  if (fresh) {
+    std::vector<double2> h(FFT_MAXLEN / 2);
+    for (int k = 0; k < FFT_MAXLEN / 2; ++k) {
+      const double a = 2.0 * M_PI * (double)k / (double)FFT_MAXLEN;
+      h[k] = make_double2(cos(a), -sin(a));
+    }
+    TM_CUDA(ctx, cudaMemcpyAsync(tw, h.data(), sizeof(double2) * h.size(), cudaMemcpyHostToDevice, ctx->stream));
+    TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  *out = tw;
+  return TMAT_OK;
+}
+
+// Row transforms. Data [batch][rows][cols], cols contiguous with pitch in_pitch, cin
+// valid columns (zero beyond, up to the length len = 2^lg). Rows [0, nrows) of every
+// batch. Output: natural out[b][row][k] (pitch out_pitch, k < cout), or transposed
+// out[b][k][row] (pitch out_pitch over rows, k < cout). dir = -1 forward, +1 inverse
+// (unnormalised). One block handles rb = 2^lgrb rows of one batch; the rows sit in
+// shared memory with an odd pitch (len + 1) so that the transposed read-out, where
+// consecutive threads take consecutive rows, spreads over the banks; the twiddles of
+// this length are staged in shared memory too.
+template <typename R, bool TOUT>
+__global__ void __launch_bounds__(FFT_THREADS)
+fft_rows_kernel(const C<R>* __restrict__ in, int64_t in_batch_stride, int in_pitch, int cin, int nrows,
+                C<R>* __restrict__ out, int64_t out_batch_stride, int out_pitch, int cout, int lg, int lgrb, int dir,
+                const double2* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  const int len = 1 << lg, rb = 1 << lgrb, pitch = len + 1;
+  C<R>* a = reinterpret_cast<C<R>*>(fsm);
+  C<R>* ws = a + (size_t)rb * pitch;  // [len / 2]
+  const int b = blockIdx.y;
+  const int row0 = blockIdx.x << lgrb;
+  const int nr = min(rb, nrows - row0);
+  const C<R>* src = in + (int64_t)b * in_batch_stride + (int64_t)row0 * in_pitch;
+  for (int j = threadIdx.x; j < (len >> 1); j += blockDim.x) {
+    const double2 w64 = tw[j << (10 - lg)];  // exp(-2 pi i j / len); FFT_MAXLEN = 2^10
+    ws[j] = mk<R>((R)w64.x, (R)(dir < 0 ? w64.y : -w64.y));
+  }
+  // load with bit reversal (zero-padded)
+  for (int e = threadIdx.x; e < (rb << lg); e += blockDim.x) {
+    const int rr = e >> lg, cc = e & (len - 1);
+    C<R> v = mk<R>((R)0, (R)0);
+    if (rr < nr && cc < cin) v = src[(int64_t)rr * in_pitch + cc];
+    const int rev = lg ? (int)(__brev((unsigned)cc) >> (32 - lg)) : 0;
+    a[rr * pitch + rev] = v;
+  }
+  __syncthreads();
+  for (int s = 0; s < lg; ++s) {
+    const int half = 1 << s;
+    const int tsh = lg - 1 - s;  // twiddle index = j * len / (2 half)
+    for (int e = threadIdx.x; e < (rb << (lg - 1)); e += blockDim.x) {
+      const int rr = e >> (lg - 1), p = e & ((len >> 1) - 1);
+      const int j = p & (half - 1);
+      const int i0 = ((p >> s) << (s + 1)) + j, i1 = i0 + half;
+      const C<R> w = ws[j << tsh];
+      C<R>* row = a + rr * pitch;
+      const C<R> t = cmul(w, row[i1]);
+      const C<R> u = row[i0];
+      row[i0] = cadd(u, t);
+      row[i1] = csub(u, t);
+    }
+    __syncthreads();
+  }
+  C<R>* dst = out + (int64_t)b * out_batch_stride;
+  if (TOUT) {
+    // out[k][row0 + rr]: consecutive threads take consecutive rows of one k
+    const int rr = threadIdx.x & (rb - 1);
+    for (int k = threadIdx.x >> lgrb; k < cout; k += blockDim.x >> lgrb)
+      if (rr < nr) dst[(int64_t)k * out_pitch + row0 + rr] = a[rr * pitch + k];
+  } else {
+    for (int rr = 0; rr < nr; ++rr)
+      for (int k = threadIdx.x; k < cout; k += blockDim.x) dst[(int64_t)(row0 + rr) * out_pitch + k] = a[rr * pitch + k];
+  }
+}
+
+template <typename R, bool TOUT>
+static int fft_rows(tmat_ctx* ctx, const C<R>* in, int64_t in_bs, int in_pitch, int cin, int nrows, C<R>* out,
+                    int64_t out_bs, int out_pitch, int cout, int len, int64_t nbatch, int dir, const double2* tw) {
+  const int lg = ilog2(len);
+  int lgrb = ilog2(std::max(1, std::min(TOUT ? 32 : 8, FFT_SMEM_POINTS / len)));
+  const int rb = 1 << lgrb;
+  const size_t smem = sizeof(C<R>) * ((size_t)rb * (len + 1) + len / 2 + 1);
+  auto kern = fft_rows_kernel<R, TOUT>;
+  if (smem > 48 * 1024) TM_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  for (int64_t b0 = 0; b0 < nbatch; b0 += 65535) {
+    const int nb = (int)std::min<int64_t>(65535, nbatch - b0);
+    dim3 grid((unsigned)cdiv(nrows, rb), (unsigned)nb);
+    kern<<<grid, FFT_THREADS, smem, ctx->stream>>>(in + b0 * in_bs, in_bs, in_pitch, cin, nrows, out + b0 * out_bs, out_bs,
+                                                   out_pitch, cout, lg, lgrb, dir, tw);
+    TM_LAUNCHED(ctx);
+  }
+  return TMAT_OK;
+}
+
+// Xc[r*P + u][iy][ix] = x[r][iy*nx + ix][u] (MODE 1: times T[site][u]); a 32 x 32 tile
+// transpose through shared memory (sites along ix x components).
+template <typename R, int MODE>
+__global__ void fft_embed_kernel(const C<R>* __restrict__ x, const C<R>* __restrict__ T, int nx, int ny, int P, int R_,
+                                 C<R>* __restrict__ Xc) {
+  __shared__ C<R> tile[32][33];
+  const int ix0 = blockIdx.x * 32, iy = blockIdx.y;
+  const int r = blockIdx.z / ((P + 31) / 32), u0 = (blockIdx.z % ((P + 31) / 32)) * 32;
+  const int64_t N = (int64_t)nx * ny;
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int ix = ix0 + q, u = u0 + threadIdx.x;
+    C<R> v = mk<R>((R)0, (R)0);
+    if (ix < nx && u < P) {
+      const int64_t site = (int64_t)iy * nx + ix;
+      v = x[((int64_t)r * N + site) * P + u];
+      if (MODE == 1) v = cmul(T[site * P + u], v);
+    }
+    tile[q][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int u = u0 + q, ix = ix0 + threadIdx.x;
+    if (u < P && ix < nx) Xc[(((int64_t)r * P + u) * ny + iy) * nx + ix] = tile[threadIdx.x][q];
+  }
+}
+
+// y[r][site][u] from Yc[r*P + u][iy][ix] scaled by 1/(Mx My): MODE 0 y = x - T Yc',
+// MODE 1 y = x - Yc', MODE 2 y = Yc'
+template <typename R, int MODE>
+__global__ void fft_extract_kernel(const C<R>* __restrict__ Yc, const C<R>* __restrict__ x, const C<R>* __restrict__ T,
+                                   int nx, int ny, int P, R scale, C<R>* __restrict__ y) {
+  __shared__ C<R> tile[32][33];
+  const int ix0 = blockIdx.x * 32, iy = blockIdx.y;
+  const int r = blockIdx.z / ((P + 31) / 32), u0 = (blockIdx.z % ((P + 31) / 32)) * 32;
+  const int64_t N = (int64_t)nx * ny;
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int u = u0 + q, ix = ix0 + threadIdx.x;
+    C<R> v = mk<R>((R)0, (R)0);
+    if (u < P && ix < nx) v = Yc[(((int64_t)r * P + u) * ny + iy) * nx + ix];
+    tile[q][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int ix = ix0 + q, u = u0 + threadIdx.x;
+    if (ix < nx && u < P) {
+      const int64_t site = (int64_t)iy * nx + ix;
+      const int64_t o = ((int64_t)r * N + site) * P + u;
+      const C<R> a = cscale(tile[threadIdx.x][q], scale);
+      C<R> out;
+      if (MODE == 2) {
+        out = a;
+      } else if (MODE == 0) {
+        out = csub(x[o], cmul(T[site * P + u], a));
+      } else {
+        out = csub(x[o], a);
+      }
+      y[o] = out;
+    }
+  }
+}
+
+// Bgrid[(c*L + u)*L + u'][iy][ix] = B_o[c][u][u'] at (ix, iy) = (-dx mod Mx, -dy mod My);
+// BT[o][c][u'][u] holds the blocks transposed (row stride LP).
+template <typename R>
+__global__ void fft_scatter_blocks_kernel(const C<R>* __restrict__ BT, const int2* __restrict__ off, int K, int L, int LP,
+                                          int Mx, int My, C<R>* __restrict__ Bgrid) {
+  const int o = blockIdx.x;
+  if (o >= K) return;
+  const int2 d = off[o];
+  const int ix = ((-d.x) % Mx + Mx) % Mx, iy = ((-d.y) % My + My) % My;
+  const int64_t F = (int64_t)Mx * My;
+  for (int e = threadIdx.x; e < 2 * L * L; e += blockDim.x) {
+    const int c = e / (L * L), u = (e / L) % L, up = e % L;
+    Bgrid[(int64_t)e * F + (int64_t)iy * Mx + ix] = BT[(((int64_t)o * 2 + c) * L + up) * LP + u];
+  }
+}
+
+// Per frequency f and class c: Y^[r][c L + u][f] = sum_u' G[u][u'] X^[r][c L + u'][f] with
+// G = B^[c][u][u'][f] (MODE 0, 2) or B^[c][u'][u][-f] (MODE 1). RC RHS per pass share
+// the B^ loads.
+template <typename R, int L, int MODE, int RC>
+__global__ void __launch_bounds__(128)
+fft_mul_kernel(const C<R>* __restrict__ Bh, const C<R>* __restrict__ Xh, C<R>* __restrict__ Yh, int Mx, int My,
+               int R_) {
+  constexpr int P = 2 * L;
+  const int64_t F = (int64_t)Mx * My;
+  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (f >= F) return;
+  int64_t fb = f;
+  if (MODE == 1) {
+    const int kx = (int)(f / My), ky = (int)(f % My);
+    fb = (int64_t)((Mx - kx) % Mx) * My + (My - ky) % My;
+  }
+  for (int r0 = 0; r0 < R_; r0 += RC) {
+    C<R> xv[RC][L];
+#pragma unroll
+    for (int q = 0; q < RC; ++q)
+#pragma unroll
+      for (int up = 0; up < L; ++up)
+        xv[q][up] = (r0 + q < R_) ? Xh[((int64_t)(r0 + q) * P + c * L + up) * F + f] : mk<R>((R)0, (R)0);
+#pragma unroll 1
+    for (int u = 0; u < L; ++u) {
+      C<R> acc[RC];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) acc[q] = mk<R>((R)0, (R)0);
+#pragma unroll
+      for (int up = 0; up < L; ++up) {
+        const int comp = MODE == 1 ? (c * L + up) * L + u : (c * L + u) * L + up;
+        const C<R> g = Bh[(int64_t)comp * F + fb];
+#pragma unroll
+        for (int q = 0; q < RC; ++q) cfma(acc[q], g, xv[q][up]);
+      }
+#pragma unroll
+      for (int q = 0; q < RC; ++q)
+        if (r0 + q < R_) Yh[((int64_t)(r0 + q) * P + c * L + u) * F + f] = acc[q];
+    }
+  }
+}
+
+// Forward 2-D transform of nb component grids [nb][ny][nx] into [nb][Mx][My] (via tmp).
+template <typename R>
+static int fft2_forward(tmat_ctx* ctx, const C<R>* grid, int nx, int ny, int Mx, int My, int64_t nb, C<R>* tmp,
+                        C<R>* out, const double2* tw) {
+  // F1: rows iy (ny of them), FFT along ix, write transposed tmp[b][kx][iy] (pitch ny)
+  TM_TRY((fft_rows<R, true>(ctx, grid, (int64_t)ny * nx, nx, nx, ny, tmp, (int64_t)Mx * ny, ny, Mx, Mx, nb, -1, tw)));
+  // F2: rows kx (Mx), FFT along iy zero-padded to My -> out[b][kx][ky]
+  TM_TRY((fft_rows<R, false>(ctx, tmp, (int64_t)Mx * ny, ny, ny, Mx, out, (int64_t)Mx * My, My, My, My, nb, -1, tw)));
+  return TMAT_OK;
+}
+
+// Inverse: [nb][Mx][My] -> [nb][ny][nx] (unnormalised), keeping iy < ny, ix < nx.
+template <typename R>
+static int fft2_inverse(tmat_ctx* ctx, const C<R>* spec, int nx, int ny, int Mx, int My, int64_t nb, C<R>* tmp,
+                        C<R>* out, const double2* tw) {
+  // I2: rows kx, inverse along ky, keep iy < ny, transposed -> tmp[b][iy][kx] (pitch Mx)
+  TM_TRY((fft_rows<R, true>(ctx, spec, (int64_t)Mx * My, My, My, Mx, tmp, (int64_t)ny * Mx, Mx, ny, My, nb, +1, tw)));
+  // I1: rows iy, inverse along kx, keep ix < nx -> out[b][iy][ix]
+  TM_TRY((fft_rows<R, false>(ctx, tmp, (int64_t)ny * Mx, Mx, Mx, ny, out, (int64_t)ny * nx, nx, nx, Mx, nb, +1, tw)));
+  return TMAT_OK;
+}
+
+bool lattice_fft_fits(int nx, int ny, int CX, int CY) {
+  return nx + CX <= FFT_MAXLEN && ny + CY <= FFT_MAXLEN;
+}
+
+// B^ of the operator (forward blocks; the adjoint reads it transposed at -f).
+template <typename R>
+static int fft_prepare_t(tmat_ctx* ctx, LatOp* a, const char* name) {
+  const int Mx = pow2_at_least(a->nx + a->CX), My = pow2_at_least(a->ny + a->CY);
+  const int L = a->L;
+  const int64_t ncomp = 2 * (int64_t)L * L;
+  const int64_t F = (int64_t)Mx * My;
+  const double2* tw;
+  TM_TRY(fft_twiddles(ctx, &tw));
+  C<R>*Bh, *grid, *tmp;
+  TM_TRY(scratch(ctx, name, sizeof(C<R>) * ncomp * F, (void**)&Bh));
+  // staging: the scattered grids (ny x nx would lose the wrapped offsets, so the full
+  // My x Mx grid is transformed) and the transposed intermediate
+  TM_TRY(scratch(ctx, "fft_bgrid", sizeof(C<R>) * ncomp * F, (void**)&grid));
+  TM_TRY(scratch(ctx, "fft_btmp", sizeof(C<R>) * ncomp * F, (void**)&tmp));
+  TM_CUDA(ctx, cudaMemsetAsync(grid, 0, sizeof(C<R>) * ncomp * F, ctx->stream));
+  fft_scatter_blocks_kernel<R><<<a->K, 256, 0, ctx->stream>>>((const C<R>*)a->BT, a->off, a->K, L, a->LP, Mx, My, grid);
+  TM_LAUNCHED(ctx);
+  TM_TRY(fft2_forward<R>(ctx, grid, Mx, My, Mx, My, ncomp, tmp, Bh, tw));
+  a->fft_Mx = Mx;
+  a->fft_My = My;
+  a->fft_Bhat = Bh;
+  a->use_fft = true;
+  return TMAT_OK;
+}
+
+int lattice_fft_prepare(tmat_ctx* ctx, LatOp* a) {
+  if (a->K == 0 || !lattice_fft_fits(a->nx, a->ny, a->CX, a->CY)) return TMAT_OK;
+  if (a->fp32) return fft_prepare_t<float>(ctx, a, "fft_Bh32");
+  return fft_prepare_t<double>(ctx, a, "fft_Bh64");
+}
+
+template <typename R, int L, int MODE>
+static int fft_apply_t(tmat_ctx* ctx, const LatOp& a, const void* xv, void* yv, int R_) {
+  constexpr int P = 2 * L;
+  const int Mx = a.fft_Mx, My = a.fft_My, nx = a.nx, ny = a.ny;
+  const int64_t F = (int64_t)Mx * My;
+  const int64_t nb = (int64_t)R_ * P;
+  const double2* tw;
+  TM_TRY(fft_twiddles(ctx, &tw));
+  const char* s1 = sizeof(R) == 4 ? "fft_w1_32" : "fft_w1_64";
+  const char* s2 = sizeof(R) == 4 ? "fft_w2_32" : "fft_w2_64";
+  C<R>*w1, *w2;  // w1: component grids / transposed intermediates; w2: spectra
+  TM_TRY(scratch(ctx, s1, sizeof(C<R>) * nb * std::max<int64_t>((int64_t)Mx * ny, (int64_t)nx * ny), (void**)&w1));
+  TM_TRY(scratch(ctx, s2, sizeof(C<R>) * 2 * nb * F, (void**)&w2));
+  C<R>* Xh = w2;
+  C<R>* Yh = w2 + nb * F;
+  C<R>* grid = Yh;  // the input grids live in the (not yet used) output spectrum buffer
+  const C<R>* x = (const C<R>*)xv;
+  const C<R>* T = (const C<R>*)a.T;
+  cudaEvent_t ev_all = timing_begin(ctx);
+  dim3 tb(32, 8);
+  dim3 tg((unsigned)cdiv(nx, 32), (unsigned)ny, (unsigned)(R_ * cdiv(P, 32)));
+  fft_embed_kernel<R, MODE == 1 ? 1 : 0><<<tg, tb, 0, ctx->stream>>>(x, T, nx, ny, P, R_, grid);
+  TM_LAUNCHED(ctx);
+  TM_TRY(fft2_forward<R>(ctx, grid, nx, ny, Mx, My, nb, w1, Xh, tw));
+  {
+    constexpr int RC = (sizeof(R) == 4 && L <= 24) ? 2 : 1;
+    dim3 g((unsigned)cdiv(F, 128), 2);
+    cudaEvent_t ev = timing_begin(ctx);
+    fft_mul_kernel<R, L, MODE, RC><<<g, 128, 0, ctx->stream>>>((const C<R>*)a.fft_Bhat, Xh, Yh, Mx, My, R_);
+    TM_LAUNCHED(ctx);
+    timing_end(ctx, sizeof(R) == 4 ? "lattice_fft_mul32" : "lattice_fft_mul64", ev);
+  }
+  C<R>* Yc = Xh;  // X^ is no longer needed
+  TM_TRY(fft2_inverse<R>(ctx, Yh, nx, ny, Mx, My, nb, w1, Yc, tw));
+  fft_extract_kernel<R, MODE><<<tg, tb, 0, ctx->stream>>>(Yc, x, T, nx, ny, P, (R)(1.0 / (double)F), (C<R>*)yv);
+  TM_LAUNCHED(ctx);
+  timing_end(ctx, sizeof(R) == 4 ? "lattice_apply_fft32" : "lattice_apply_fft64", ev_all);
+  return TMAT_OK;
+}
+
+template <typename R, int L>
+static int fft_apply_l(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void* y, int R_) {
+  if (mode == TMAT_OP_FORWARD) return fft_apply_t<R, L, 0>(ctx, a, x, y, R_);
+  if (mode == TMAT_OP_ADJOINT) return fft_apply_t<R, L, 1>(ctx, a, x, y, R_);
+  return fft_apply_t<R, L, 2>(ctx, a, x, y, R_);
+}
+
+template <typename R>
+static int fft_apply_r(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void* y, int R_) {
+  switch (a.nmax) {
+    case 1: return fft_apply_l<R, 3>(ctx, a, mode, x, y, R_);
+    case 2: return fft_apply_l<R, 8>(ctx, a, mode, x, y, R_);
+    case 3: return fft_apply_l<R, 15>(ctx, a, mode, x, y, R_);
+    case 4: return fft_apply_l<R, 24>(ctx, a, mode, x, y, R_);
+    case 5: return fft_apply_l<R, 35>(ctx, a, mode, x, y, R_);
+    case 6: return fft_apply_l<R, 48>(ctx, a, mode, x, y, R_);
+  }
+  return set_error(ctx, TMAT_ENOTSUP, "FFT lattice apply: nmax %d", a.nmax);
+}
+
+int lattice_fft_apply(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void* y, int R_) {
+  if (a.fp32) return fft_apply_r<float>(ctx, a, mode, x, y, R_);
+  return fft_apply_r<double>(ctx, a, mode, x, y, R_);
+}
+
+}  // namespace tmat

@@ -207,7 +207,7 @@ extern "C" int tmat_solve(tmat_ctx* ctx, const double* pos, int64_t N, double wa
   } else {
     TM_TRY(make_lattice_ops(ctx, t, (const double*)spos.dev, N, k, opts->lattice_nx, opts->lattice_ny,
                             opts->lattice_pitch, opts->cutoff, opts->taper, (const double2*)T64, (const float2*)T32, mixed, &ops,
-                            sp.precision != TMAT_PREC_FP64));
+                            sp.precision == TMAT_PREC_FP64_TC ? 2 : (mixed ? 1 : 0)));
   }
   // b = T a0 (internal layout)
   double2 *a0i, *b, *x;
@@ -295,7 +295,7 @@ extern "C" int tmat_adjoint(tmat_ctx* ctx, const tmat_solution* sol, const tmat_
   } else {
     TM_TRY(make_lattice_ops(ctx, t, sol->pos, N, sol->k, sol->lattice_nx, sol->lattice_ny, sol->lattice_pitch,
                             sol->cutoff, sol->taper, sol->T64, sol->T32, mixed, &ops,
-                            sol->params.precision != TMAT_PREC_FP64));
+                            sol->params.precision == TMAT_PREC_FP64_TC ? 2 : (mixed ? 1 : 0)));
   }
   double2 *vi, *mu, *dTi, *As;
   TM_TRY(scratch(ctx, "adj_v", sizeof(double2) * N * P, (void**)&vi));

@@ -31,6 +31,10 @@ struct LatOp {
   // fp64-class apply on the tensor cores (bf16 slices, exact group sums)
   bool use_oz = false;
   int* oz_err = nullptr;  // device counter of CTAs that gave up on a wait
+  // FFT convolution (lattice_fft.cu): grid size and the block spectra B^[2 L L][Mx My]
+  bool use_fft = false;
+  int fft_Mx = 0, fft_My = 0;
+  const void* fft_Bhat = nullptr;
 };
 // An operator instance in one precision. kind 0: neighbour list; kind 1: lattice.
 struct Operator {
@@ -89,6 +93,9 @@ bool lattice_tc2_fits(int nmax, int CX);
 int lattice_tc2_apply(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void* y, int R);
 int lattice_tc_apply(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void* y, int R);
 int lattice_tc_prepare(tmat_ctx* ctx, LatOp* a, const double2* BT64);
+bool lattice_fft_fits(int nx, int ny, int CX, int CY);
+int lattice_fft_prepare(tmat_ctx* ctx, LatOp* a);
+int lattice_fft_apply(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void* y, int R);
 bool lattice_oz_fits(int nmax, int CX);
 int lattice_oz_prepare(tmat_ctx* ctx, LatOp* a, const double2* BT64);
 int lattice_oz_apply(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void* y, int R);
@@ -96,8 +103,9 @@ inline int64_t lattice_N(const LatOp& L) { return L.N; }
 inline int lattice_nmax(const LatOp& L) { return L.nmax; }
 inline bool lattice_fp32(const LatOp& L) { return L.fp32; }
 // Operators (fp64 and, for mixed, fp32) for one solve.
-// R64: the fp64-class tensor-core operator (have_oz), for refinement residuals and
-// TMAT_PREC_FP64_TC solves.
+// R64: the fp64-class tensor-core operator (have_oz), for refinement residuals (when the
+// fp64 operator is not the FFT one) and TMAT_PREC_FP64_TC solves. want_oz: 0 none,
+// 1 for a refinement residual, 2 for TMAT_PREC_FP64_TC.
 struct OpPair {
   Operator A64, A32, R64;
   bool have32 = false, have_oz = false;
@@ -105,5 +113,5 @@ struct OpPair {
 };
 int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_t N, double k, int nx, int ny,
                      double pitch, double cutoff, double taper, const double2* T64, const float2* T32, bool mixed,
-                     OpPair* ops, bool want_oz = false);
+                     OpPair* ops, int want_oz = 0);
 }  // namespace tmat

@@ -23,15 +23,22 @@ import numpy as np
 from . import _lib
 
 
-def request_bytes(side, nmax, R=1, restart=60):
-    """Device-memory estimate of one request (Krylov basis, vectors, blocks, tables)."""
+def request_bytes(side, nmax, R=1, restart=60, cutoff_sites=16):
+    """Device-memory estimate of one request (Krylov basis, vectors, blocks, the FFT
+    operator's block spectra and work grids, tables)."""
     N = side * side
     P = 2 * nmax * (nmax + 2)
+    L = P // 2
     krylov = (restart + 1) * R * N * P * 8
     vectors = 14 * R * N * P * 16
-    blocks = 800 * 2 * (P // 2) ** 2 * (16 + 8 + 2 * 8)
+    blocks = 800 * 2 * L ** 2 * (16 + 8 + 2 * 8)
+    M = 1
+    while M < side + cutoff_sites:
+        M *= 2
+    spectra = 2 * L * L * M * M * (16 * 3 + 8)  # complex128 spectra + 2 staging grids, complex64 spectra
+    work = R * P * M * M * (16 * 3 + 8 * 3)
     jinc = 8192 * R * P * 16
-    return krylov + vectors + blocks + jinc + (8 << 20)
+    return krylov + vectors + blocks + spectra + work + jinc + (8 << 20)
 
 
 class Server:

@@ -106,16 +106,20 @@ def test_tensor_core_apply_matches_cuda_cores_and_oracle(nmax, nx, ny, cutoff, R
     T = np.array([mie.tmatrix_diag(nmax, K0, x, 2.0) for x in r])
     x = rand_c((R, nx * ny, T.shape[1]), 70 + nmax)
     c = ctx()
-    c.set_tensor_cores(variant)
-    c.set_timing(True)
-    n0, _ = c.kernel_time(kind)
-    ytc = c.tmat_apply_lattice(op, 1, nx, ny, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
-    n_tc, _ = c.kernel_time(kind)
-    n_tc -= n0
-    c.set_tensor_cores(False)
-    ycc = c.tmat_apply_lattice(op, 1, nx, ny, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
-    c.set_tensor_cores(True)
-    c.set_timing(False)
+    c.set_lattice_fft(False)
+    try:
+        c.set_tensor_cores(variant)
+        c.set_timing(True)
+        n0, _ = c.kernel_time(kind)
+        ytc = c.tmat_apply_lattice(op, 1, nx, ny, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
+        n_tc, _ = c.kernel_time(kind)
+        n_tc -= n0
+        c.set_tensor_cores(False)
+        ycc = c.tmat_apply_lattice(op, 1, nx, ny, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
+    finally:
+        c.set_tensor_cores(True)
+        c.set_timing(False)
+        c.set_lattice_fft(True)
     assert n_tc >= 1  # the tensor-core kernel really ran
     nbr = geometry.neighbours(pos, cutoff)
     f = [system.apply_K, system.apply_KT, lambda nm, k, p, t, v, nb: system.apply_A(nm, k, p, v, nb)][op]
@@ -174,3 +178,38 @@ def test_fp64_tc_solve_vs_oracle_and_neighbour_path_refused():
     with pytest.raises(_lib.TMatError) as e:
         ctx().tmat_solve(pos, 1.0, 1.0, nmax, T, a0, opts)
     assert e.value.code == _lib.ENOTSUP
+
+
+@pytest.mark.parametrize("nmax,nx,ny,cutoff,R", [(4, 23, 9, 2.0, 2), (3, 17, 13, 1.6, 1), (2, 9, 7, 0.0, 3),
+                                                 (5, 11, 6, 1.4, 2), (6, 5, 4, 0.9, 1), (1, 31, 1, 3.0, 2),
+                                                 (2, 1, 12, 2.0, 1)])
+@pytest.mark.parametrize("op", [0, 1, 2])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fft_apply_matches_direct_and_oracle(nmax, nx, ny, cutoff, R, op, precision):
+    """The FFT-convolution lattice apply (default) against the direct block-Toeplitz kernels
+    and the oracle: fp64 to 1e-12, complex64 to the complex64 tolerance; ragged and
+    one-row lattices, every pair (cutoff 0), nmax 1..6, both window readings."""
+    pos = W.lattice_positions(nx, ny)
+    r = W.uniform_radii(nx * ny, 0.08, 0.24, 120 + nmax)
+    T = np.array([mie.tmatrix_diag(nmax, K0, x, 2.0) for x in r])
+    x = rand_c((R, nx * ny, T.shape[1]), 130 + nmax)
+    c = ctx()
+    kind = "lattice_apply_fft64" if precision == 0 else "lattice_apply_fft32"
+    c.set_timing(True)
+    n0, _ = c.kernel_time(kind)
+    yf = c.tmat_apply_lattice(op, precision, nx, ny, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
+    n1, _ = c.kernel_time(kind)
+    c.set_timing(False)
+    assert n1 - n0 == 1  # the FFT path ran
+    c.set_lattice_fft(False)
+    try:
+        yd = c.tmat_apply_lattice(op, precision, nx, ny, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
+    finally:
+        c.set_lattice_fft(True)
+    nbr = geometry.neighbours(pos, cutoff)
+    f = [system.apply_K, system.apply_KT, lambda nm, k, p, t, v, nb: system.apply_A(nm, k, p, v, nb)][op]
+    with system.window(cutoff, cutoff):
+        ref = np.array([f(nmax, K0, pos, T, x[q], nbr) for q in range(R)])
+    bound = 1e-12 if precision == 0 else C64_APPLY_TOL
+    assert rel_l2(yf, ref) <= bound
+    assert rel_l2(yf, yd) <= bound

@@ -30,7 +30,9 @@ def test_admission_respects_memory_budget():
     """The sum of the memory estimates of the requests in flight never exceeds the
     budget; a budget that fits one request at a time serialises the stream."""
     from paper_2107_09879_b300 import serve
-    reqs = W.served_stream(5, seed=W.BASE_SEED + 4, rate_per_s=1000.0, k_lo=6, k_hi=10)
+    reqs = W.served_stream(5, seed=W.BASE_SEED + 4, rate_per_s=1000.0, k_lo=8, k_hi=8)
+    for r in reqs:
+        r["nmax"] = 4  # equal estimates: a budget of one request admits one at a time
     est = [serve.request_bytes(r["side"], r["nmax"]) for r in reqs]
     budget = max(est)
     assert 2 * min(est) > budget  # so no two requests fit together
