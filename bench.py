@@ -117,7 +117,8 @@ class ClockSampler:
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands
 # (profiles/lattice_tc2_200x200_nmax4.md); set to None when the kernel changes.
-MEASURED_TRAFFIC = {"lattice_tc2_kernel<4,0>": 238.0e6 + 23.0e6}
+MEASURED_TRAFFIC = {"lattice_tc2_kernel<4,0>": 238.0e6 + 23.0e6,
+                    "fft_mul_kernel<float,24,0,2>": 654.4e6 + 46.5e6}  # profiles/lattice_fft_200x200_nmax4.md
 
 
 def roofline(kern_name, achieved, launches, avg_ms, flop_per_launch):
