@@ -99,10 +99,13 @@ static inline Dots32Plan dots32_plan(int64_t n, int nvec, int num_sms, int R) {
   return p;
 }
 
+// TWO: also dots against a second target w2 into part2 (one read of the basis for both).
+template <bool TWO>
 __global__ void __launch_bounds__(256)
 dots32_kernel(const float2* __restrict__ V, int64_t vstride, int nvec, const float2* __restrict__ w, int64_t n,
               int64_t rstride, double2* __restrict__ part, int maxv, int groups, int ranges,
-              const int* __restrict__ active) {
+              const int* __restrict__ active, const float2* __restrict__ w2 = nullptr,
+              double2* __restrict__ part2 = nullptr) {
   const int r = blockIdx.y;
   if (active && !active[r]) return;
   const int lane = threadIdx.x & 31;
@@ -120,11 +123,16 @@ dots32_kernel(const float2* __restrict__ V, int64_t vstride, int nvec, const flo
     const int k = kb + q < nvec ? kb + q : kb;  // out-of-range vectors read a valid one, unused
     v4[q] = reinterpret_cast<const float4*>(V + (int64_t)k * vstride + r * rstride);
   }
-  float2 acc[D32_VPW];
+  const float4* w24 = TWO ? reinterpret_cast<const float4*>(w2 + r * rstride) : nullptr;
+  float2 acc[D32_VPW], acc2[TWO ? D32_VPW : 1];
 #pragma unroll
   for (int q = 0; q < D32_VPW; ++q) acc[q] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < (TWO ? D32_VPW : 1); ++q) acc2[q] = make_float2(0.f, 0.f);
   for (int64_t i = lo + lane; i < hi; i += 32) {
     const float4 wv = w4[i];
+    float4 wv2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (TWO) wv2 = w24[i];
     float4 v[D32_VPW];
 #pragma unroll
     for (int q = 0; q < D32_VPW; ++q) v[q] = v4[q][i];
@@ -133,6 +141,10 @@ dots32_kernel(const float2* __restrict__ V, int64_t vstride, int nvec, const flo
       // conj(v) w for both complex values
       acc[q].x = fmaf(v[q].x, wv.x, fmaf(v[q].y, wv.y, fmaf(v[q].z, wv.z, fmaf(v[q].w, wv.w, acc[q].x))));
       acc[q].y = fmaf(v[q].x, wv.y, fmaf(-v[q].y, wv.x, fmaf(v[q].z, wv.w, fmaf(-v[q].w, wv.z, acc[q].y))));
+      if (TWO) {
+        acc2[q].x = fmaf(v[q].x, wv2.x, fmaf(v[q].y, wv2.y, fmaf(v[q].z, wv2.z, fmaf(v[q].w, wv2.w, acc2[q].x))));
+        acc2[q].y = fmaf(v[q].x, wv2.y, fmaf(-v[q].y, wv2.x, fmaf(v[q].z, wv2.w, fmaf(-v[q].w, wv2.z, acc2[q].y))));
+      }
     }
   }
 #pragma unroll
@@ -143,6 +155,14 @@ dots32_kernel(const float2* __restrict__ V, int64_t vstride, int nvec, const flo
       v.y += __shfl_down_sync(0xffffffffu, v.y, o);
     }
     if (lane == 0 && kb + q < nvec) part[((int64_t)r * maxv + kb + q) * ranges + b] = make_double2(v.x, v.y);
+    if (TWO) {
+      float2 v2 = acc2[q];
+      for (int o = 16; o > 0; o >>= 1) {
+        v2.x += __shfl_down_sync(0xffffffffu, v2.x, o);
+        v2.y += __shfl_down_sync(0xffffffffu, v2.y, o);
+      }
+      if (lane == 0 && kb + q < nvec) part2[((int64_t)r * maxv + kb + q) * ranges + b] = make_double2(v2.x, v2.y);
+    }
   }
 }
 
@@ -349,6 +369,12 @@ struct GState {
   double *nrm;           // [R] norm of the new vector / residual
   double *tol_abs;       // [R]
   int *active, *ncols, *flags;
+  // delayed CGS2 (complex64 vectors): unrotated Hessenberg [R][maxv][m], the dots of the
+  // basis against the pending vector (D1) and the new vector (D2) [R][maxv], and the
+  // update coefficients [R][maxv] with the self-scales [R]
+  double2 *Hu, *D1, *D2;
+  float2 *cA, *cB;
+  float *selfA, *selfB;
 };
 
 __global__ void cycle_init_kernel(GState s, int R, int maxv, const double* __restrict__ rnorm, const int* __restrict__ want) {
@@ -431,6 +457,179 @@ __global__ void givens_kernel(GState s, int R, int j, int m, int maxv) {
   for (int i = threadIdx.x; i <= j; i += blockDim.x) hcol[(int64_t)i * m] = col[i];
 }
 
+// ---- delayed CGS2 (Arnoldi with the second projection one step late) ----------------
+// Iteration j expands the pending vector u_j (slot j: first projection of A q_{j-1}
+// against q_0..q_{j-1}, not normalised; q_0 for j = 0) with w = A u_j. One pass over the
+// basis gives D1 = V^H u_j and D2 = V^H w (slots 0..j). With b1 = ||u_j||, s = D1/b1 and
+// nu = sqrt(1 - |s|^2):
+//   column j-1 (final)  H[0..j-1][j-1] += b1 s,  H[j][j-1] = b1 nu,  q_j = (u_j/b1 - Q s)/nu;
+//   column j (first projection, by the Arnoldi relation A Q = Q_{j+1} H applied to A q_j =
+//   (w/b1 - A Q s)/nu)  H[0..j][j] = ([z; zeta] - H s)/nu with z = D2/b1 and
+//   zeta = (c - s^H z)/nu, c = D2[j]/b1^2;
+//   u_{j+1} = (w/b1 - Q (z - (zeta/nu) s) - (zeta/(nu b1)) u_j)/nu.
+// One more pass writes q_j into slot j and u_{j+1} into slot j+1 (both from one read of
+// the basis): two passes over the basis per iteration instead of four. The Hessenberg
+// columns are the classical Gram-Schmidt-twice ones; the reorthogonalisation of u_j uses the
+// vector actually stored, so rounding in forming it is corrected as in CGS2.
+__global__ void dcgs2_small_kernel(GState s, int j, int m, int maxv, int R, int final_only) {
+  const int r = blockIdx.x;
+  if (r >= R || !s.active[r]) return;
+  __shared__ double2 sv[1025];
+  __shared__ double red[2][32];
+  __shared__ double2 zeta_sh;
+  __shared__ double b1_sh, nu_sh;
+  const double2* D1 = s.D1 + (int64_t)r * maxv;
+  const double2* D2 = s.D2 + (int64_t)r * maxv;
+  double2* Hu = s.Hu + (int64_t)r * maxv * m;  // Hu[i * m + c]
+  float2* cA = s.cA + (int64_t)r * maxv;
+  float2* cB = s.cB + (int64_t)r * maxv;
+  const int tid = threadIdx.x;
+  if (j == 0) {
+    if (tid == 0) {
+      const double2 z0 = D2[0];
+      Hu[0] = z0;
+      cB[0] = make_float2((float)z0.x, (float)z0.y);
+      s.selfB[r] = 1.f;
+      s.selfA[r] = 0.f;
+    }
+    return;
+  }
+  if (tid == 0) {
+    b1_sh = sqrt(fmax(D1[j].x, 0.0));
+  }
+  __syncthreads();
+  const double b1 = b1_sh;
+  // s = D1 / b1 and |s|^2
+  double ss = 0.0;
+  for (int k = tid; k < j; k += blockDim.x) {
+    const double2 v = b1 > 0 ? make_double2(D1[k].x / b1, D1[k].y / b1) : make_double2(0, 0);
+    sv[k] = v;
+    ss += v.x * v.x + v.y * v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
+  if ((tid & 31) == 0) red[0][tid >> 5] = ss;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[0][q];
+    nu_sh = b1 > 0 ? sqrt(fmax(1.0 - t, 1e-30)) : 1.0;
+  }
+  __syncthreads();
+  const double nu = nu_sh;
+  // finalise column j-1 and hand it to the Givens step (hA + hB, subdiagonal in nrm)
+  for (int k = tid; k < j; k += blockDim.x) {
+    double2 h = Hu[(int64_t)k * m + (j - 1)];
+    h.x += b1 * sv[k].x;
+    h.y += b1 * sv[k].y;
+    Hu[(int64_t)k * m + (j - 1)] = h;
+    s.hA[(int64_t)r * maxv + k] = h;
+    s.hB[(int64_t)r * maxv + k] = make_double2(0, 0);
+  }
+  if (tid == 0) {
+    Hu[(int64_t)j * m + (j - 1)] = make_double2(b1 * nu, 0.0);
+    s.nrm[r] = b1 * nu;
+  }
+  if (final_only || !(b1 > 0)) return;
+  __syncthreads();
+  // zeta = (c - s^H z)/nu with z = D2/b1, c = D2[j]/b1^2
+  double zr = 0.0, zi = 0.0;
+  for (int k = tid; k < j; k += blockDim.x) {
+    const double2 z = make_double2(D2[k].x / b1, D2[k].y / b1);
+    zr += sv[k].x * z.x + sv[k].y * z.y;  // conj(s) z
+    zi += sv[k].x * z.y - sv[k].y * z.x;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    zr += __shfl_down_sync(0xffffffffu, zr, o);
+    zi += __shfl_down_sync(0xffffffffu, zi, o);
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = zr;
+    red[1][tid >> 5] = zi;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, bq = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      a += red[0][q];
+      bq += red[1][q];
+    }
+    const double b2 = b1 * b1;
+    zeta_sh = make_double2((D2[j].x / b2 - a) / nu, (D2[j].y / b2 - bq) / nu);
+  }
+  __syncthreads();
+  const double2 zeta = zeta_sh;
+  // column j: H[i][j] = ([z; zeta]_i - (H s)_i)/nu, H s over the final columns 0..j-1
+  for (int i = tid; i <= j; i += blockDim.x) {
+    double2 t = make_double2(0, 0);
+    const int c0 = i > 0 ? i - 1 : 0;  // H is upper Hessenberg: H[i][c] = 0 for c < i - 1
+    for (int c = c0; c < j; ++c) {
+      const double2 h = Hu[(int64_t)i * m + c];
+      t.x += h.x * sv[c].x - h.y * sv[c].y;
+      t.y += h.x * sv[c].y + h.y * sv[c].x;
+    }
+    const double2 zi2 = i < j ? make_double2(D2[i].x / b1, D2[i].y / b1) : zeta;
+    Hu[(int64_t)i * m + j] = make_double2((zi2.x - t.x) / nu, (zi2.y - t.y) / nu);
+  }
+  // update coefficients
+  const double zn_r = zeta.x / nu, zn_i = zeta.y / nu;  // zeta / nu
+  for (int k = tid; k < j; k += blockDim.x) {
+    const double2 sk = sv[k];
+    const double2 z = make_double2(D2[k].x / b1, D2[k].y / b1);
+    cA[k] = make_float2((float)(sk.x / nu), (float)(sk.y / nu));
+    // (z - (zeta/nu) s)/nu
+    const double2 t = make_double2(z.x - (zn_r * sk.x - zn_i * sk.y), z.y - (zn_r * sk.y + zn_i * sk.x));
+    cB[k] = make_float2((float)(t.x / nu), (float)(t.y / nu));
+  }
+  if (tid == 0) {
+    cB[j] = make_float2((float)(zn_r / (nu * b1)), (float)(zn_i / (nu * b1)));  // zeta / (nu^2 b1)
+    s.selfA[r] = (float)(1.0 / (b1 * nu));
+    s.selfB[r] = (float)(1.0 / (b1 * nu));
+  }
+}
+
+// slot j <- selfA V_j - sum_{k<j} V_k cA_k  (if j > 0), and
+// w      <- selfB w   - sum_{k<=j} V_k cB_k, from one read of V_0..V_j (complex64)
+__global__ void __launch_bounds__(256)
+dcgs2_update_kernel(float2* __restrict__ V, int64_t vstride, int j, GState s, int maxv, float2* __restrict__ w,
+                    int64_t n, int64_t rstride) {
+  const int r = blockIdx.y;
+  if (!s.active[r]) return;
+  extern __shared__ float2 dcs[];  // cA[0..j), cB[0..j]
+  float2* cA = dcs;
+  float2* cB = dcs + j + 1;
+  for (int k = threadIdx.x; k <= j; k += blockDim.x) {
+    cA[k] = k < j ? s.cA[(int64_t)r * maxv + k] : make_float2(0.f, 0.f);
+    cB[k] = s.cB[(int64_t)r * maxv + k];
+  }
+  __syncthreads();
+  const float sA = s.selfA[r], sB = s.selfB[r];
+  const int64_t n2 = n >> 1;
+  float4* vj4 = reinterpret_cast<float4*>(V + (int64_t)j * vstride + r * rstride);
+  float4* w4 = reinterpret_cast<float4*>(w + r * rstride);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), bsum = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; k <= j; ++k) {
+      const float4 v = reinterpret_cast<const float4*>(V + (int64_t)k * vstride + r * rstride)[i];
+      const float2 cb = cB[k];
+      bsum.x = fmaf(v.x, cb.x, fmaf(-v.y, cb.y, bsum.x));
+      bsum.y = fmaf(v.x, cb.y, fmaf(v.y, cb.x, bsum.y));
+      bsum.z = fmaf(v.z, cb.x, fmaf(-v.w, cb.y, bsum.z));
+      bsum.w = fmaf(v.z, cb.y, fmaf(v.w, cb.x, bsum.w));
+      const float2 ca = cA[k];
+      a.x = fmaf(v.x, ca.x, fmaf(-v.y, ca.y, a.x));
+      a.y = fmaf(v.x, ca.y, fmaf(v.y, ca.x, a.y));
+      a.z = fmaf(v.z, ca.x, fmaf(-v.w, ca.y, a.z));
+      a.w = fmaf(v.z, ca.y, fmaf(v.w, ca.x, a.w));
+    }
+    const float4 wv = w4[i];
+    w4[i] = make_float4(sB * wv.x - bsum.x, sB * wv.y - bsum.y, sB * wv.z - bsum.z, sB * wv.w - bsum.w);
+    if (j > 0) {
+      const float4 u = vj4[i];
+      vj4[i] = make_float4(sA * u.x - a.x, sA * u.y - a.y, sA * u.z - a.z, sA * u.w - a.w);
+    }
+  }
+}
+
 // back substitution y = H^{-1} g over the first ncols columns
 __global__ void lsq_kernel(GState s, int R, int m, int maxv) {
   int r = threadIdx.x;
@@ -498,12 +697,16 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
   TM_TRY(scratch(ctx, sizeof(VR) == 4 ? "g_xv32" : "g_xv64", sizeof(C<VR>) * (size_t)R * n, (void**)&xv));
   double2* part;
   TM_TRY(scratch(ctx, "g_part", sizeof(double2) * (size_t)R * std::max(nb, D32_NBMAX) * maxv, (void**)&part));
+  double2* part2 = nullptr;
+  if (sizeof(VR) == 4)
+    TM_TRY(scratch(ctx, "g_part2", sizeof(double2) * (size_t)R * D32_NBMAX * maxv, (void**)&part2));
   GState s;
   char* small;
   const size_t R_ = R;
   auto rup = [](size_t b) { return (b + 255) / 256 * 256; };
-  size_t sz = rup(sizeof(double2) * R_ * maxv) * 4 + rup(sizeof(double2) * R_ * maxv * m) +
-              rup(sizeof(double2) * R_ * m) * 2 + rup(sizeof(double) * R_) * 4 + rup(sizeof(int) * R_) * 4;
+  size_t sz = rup(sizeof(double2) * R_ * maxv) * 6 + rup(sizeof(double2) * R_ * maxv * m) * 2 +
+              rup(sizeof(double2) * R_ * m) * 2 + rup(sizeof(double) * R_) * 4 + rup(sizeof(int) * R_) * 4 +
+              rup(sizeof(float2) * R_ * maxv) * 2 + rup(sizeof(float) * R_) * 2;
   TM_TRY(scratch(ctx, "g_small", sz, (void**)&small));
   {
     char* q = small;
@@ -523,6 +726,13 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
     s.ncols = (int*)take(sizeof(int) * R_);
     s.flags = (int*)take(sizeof(int) * R_);
     int* want = (int*)take(sizeof(int) * R_);
+    s.Hu = (double2*)take(sizeof(double2) * R_ * maxv * m);
+    s.D1 = (double2*)take(sizeof(double2) * R_ * maxv);
+    s.D2 = (double2*)take(sizeof(double2) * R_ * maxv);
+    s.cA = (float2*)take(sizeof(float2) * R_ * maxv);
+    s.cB = (float2*)take(sizeof(float2) * R_ * maxv);
+    s.selfA = (float*)take(sizeof(float) * R_);
+    s.selfB = (float*)take(sizeof(float) * R_);
     if ((size_t)(q - small) > sz) return set_error(ctx, TMAT_ECUDA, "gmres: state layout overflow");
     TM_CUDA(ctx, cudaMemsetAsync(s.flags, 0, sizeof(int) * R_, ctx->stream));
     const unsigned g1 = grid_for(ctx, n);
@@ -554,6 +764,54 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
       scale_kernel<VR, VR><<<dim3(g1, R), 256, 0, ctx->stream>>>(rsrc, V, n, rs, rnorm, 1, nullptr);
       TM_LAUNCHED(ctx);
       int j = 0;
+      if constexpr (sizeof(VR) == 4) {
+        // delayed CGS2: the Hessenberg column of iteration j is finalised at iteration j + 1
+        float2* V32 = reinterpret_cast<float2*>(V);
+        const size_t gsm_bytes = sizeof(double2) * (2 * (size_t)m + maxv);
+        if (gsm_bytes > 48 * 1024)
+          TM_CUDA(ctx, cudaFuncSetAttribute(givens_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm_bytes));
+        for (;; ++j) {
+          const bool final_only = j == m || st->iterations >= p.max_iter;
+          float2* vj = V32 + (int64_t)j * R * n;
+          float2* w = final_only ? nullptr : V32 + (int64_t)(j + 1) * R * n;
+          if (!final_only) {
+            TM_TRY(op_apply(ctx, A, mode, vj, w, R));
+            st->iterations++;
+          }
+          const Dots32Plan dp = dots32_plan(n, j + 1, ctx->num_sms, R);
+          if (final_only) {
+            dots32_kernel<false><<<dim3(dp.blocks, R), 256, 0, ctx->stream>>>(V32, (int64_t)R * n, j + 1, vj, n, rs,
+                                                                               part, maxv, dp.groups, dp.ranges, s.active);
+          } else {
+            dots32_kernel<true><<<dim3(dp.blocks, R), 256, 0, ctx->stream>>>(
+                V32, (int64_t)R * n, j + 1, vj, n, rs, part, maxv, dp.groups, dp.ranges, s.active, w, part2);
+          }
+          TM_LAUNCHED(ctx);
+          launch_reduce(ctx, part, dp.ranges, j + 1, maxv, s.D1, s.active, R);
+          TM_LAUNCHED(ctx);
+          if (!final_only) {
+            launch_reduce(ctx, part2, dp.ranges, j + 1, maxv, s.D2, s.active, R);
+            TM_LAUNCHED(ctx);
+          }
+          dcgs2_small_kernel<<<R, 256, 0, ctx->stream>>>(s, j, m, maxv, R, final_only ? 1 : 0);
+          TM_LAUNCHED(ctx);
+          bool any = true;
+          if (j >= 1) {
+            givens_kernel<<<R, 64, gsm_bytes, ctx->stream>>>(s, R, j - 1, m, maxv);
+            TM_LAUNCHED(ctx);
+            int* ipin = (int*)ctx->pinned;
+            TM_CUDA(ctx, cudaMemcpyAsync(ipin, s.active, sizeof(int) * R, cudaMemcpyDeviceToHost, ctx->stream));
+            TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            any = false;
+            for (int r = 0; r < R; ++r) any = any || ipin[r];
+          }
+          if (final_only || !any) break;
+          dcgs2_update_kernel<<<dim3(g1, R), 256, sizeof(float2) * (2 * (size_t)j + 2), ctx->stream>>>(
+              V32, (int64_t)R * n, j, s, maxv, w, n, rs);
+          TM_LAUNCHED(ctx);
+        }
+        // columns 0..j-1 are final
+      } else
       for (; j < m && st->iterations < p.max_iter; ++j) {
         C<VR>* vj = V + (int64_t)j * R * n;
         C<VR>* w = V + (int64_t)(j + 1) * R * n;
@@ -564,8 +822,8 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
           if constexpr (sizeof(VR) == 4) {
             const Dots32Plan dp = dots32_plan(n, j + 1, ctx->num_sms, R);
             nbp = dp.ranges;
-            dots32_kernel<<<dim3(dp.blocks, R), 256, 0, ctx->stream>>>(V, (int64_t)R * n, j + 1, w, n, rs, part, maxv,
-                                                                        dp.groups, dp.ranges, s.active);
+            dots32_kernel<false><<<dim3(dp.blocks, R), 256, 0, ctx->stream>>>(V, (int64_t)R * n, j + 1, w, n, rs, part,
+                                                                               maxv, dp.groups, dp.ranges, s.active);
           } else {
             dots_kernel<VR><<<dim3(nb, R), RED_THREADS, 0, ctx->stream>>>(V, (int64_t)R * n, j + 1, w, n, rs, part,
                                                                            maxv, s.active);
