@@ -203,7 +203,8 @@ def _wall(fn, sync):
 
 
 def bench_dense_fp64(ctx, torch, steps=20):
-    """8 x 8 spheres, nmax 3, every pair coupled, fp64 GMRES to 1e-10 (neighbour path)."""
+    """8 x 8 spheres, nmax 3, every pair coupled, fp64 GMRES to 1e-10: on the lattice path
+    (every offset of the 8 x 8 lattice; FFT convolution) and on the neighbour-list path."""
     from paper_2107_09879_b300 import _lib
     w = W.dense_8x8()
     a = np.zeros((64, 3))
@@ -212,21 +213,26 @@ def bench_dense_fp64(ctx, torch, steps=20):
     atoms = torch.from_numpy(a).cuda()
     dirs = torch.zeros((1, 2), dtype=torch.float64, device="cuda")
     pol = torch.tensor([[1.0, 0.0, 0.0]], dtype=torch.complex128, device="cuda")
-    opts = _lib.make_opts(tol=w["tol"], restart=100, max_iter=2000, cutoff=0.0, precision=_lib.PREC_FP64)
-    info = []
+    out = {"workload": "dense_8x8_nmax3_fp64_tol1e-10",
+           "note": "one solve = Mie build + incident + GMRES; launched eagerly (no graph capture)"}
+    for path, extra in (("lattice", dict(path=_lib.PATH_LATTICE, lattice_nx=8, lattice_ny=8, lattice_pitch=PITCH)),
+                        ("neighbour", dict(path=_lib.PATH_NEIGHBOUR))):
+        opts = _lib.make_opts(tol=w["tol"], restart=100, max_iter=2000, cutoff=0.0, precision=_lib.PREC_FP64, **extra)
+        info = []
 
-    def one():
-        T = ctx.tmat_build(atoms, 1.0, 1.0, w["nmax"])
-        a0 = ctx.tmat_incident_planewave(pos, 1.0, 1.0, w["nmax"], dirs, pol)
-        s, inf, _, rc = ctx.tmat_solve(pos, 1.0, 1.0, w["nmax"], T, a0, opts)
-        info.append(inf)
-        return rc
-    for _ in range(3):
-        one()
-    dt, _ = _wall(lambda: [one() for _ in range(steps)], torch.cuda.synchronize)
-    return {"workload": "dense_8x8_nmax3_fp64_tol1e-10", "solves_per_s": steps / dt, "ms_per_solve": dt / steps * 1e3,
-            "iterations": info[-1].iterations, "rel_residual": info[-1].rel_residual[0],
-            "note": "one solve = Mie build + incident + GMRES; launched eagerly (no graph capture)"}
+        def one():
+            T = ctx.tmat_build(atoms, 1.0, 1.0, w["nmax"])
+            a0 = ctx.tmat_incident_planewave(pos, 1.0, 1.0, w["nmax"], dirs, pol)
+            s, inf, _, rc = ctx.tmat_solve(pos, 1.0, 1.0, w["nmax"], T, a0, opts)
+            info.append(inf)
+            return rc
+        for _ in range(3):
+            one()
+        dt, _ = _wall(lambda: [one() for _ in range(steps)], torch.cuda.synchronize)
+        out[path] = {"solves_per_s": steps / dt, "ms_per_solve": dt / steps * 1e3, "iterations": info[-1].iterations,
+                     "rel_residual": info[-1].rel_residual[0]}
+    out["solves_per_s"] = out["lattice"]["solves_per_s"]
+    return out
 
 
 def bench_adjoint(ctx, torch, steps=3):

@@ -313,6 +313,34 @@ __global__ void update_kernel(const C<VR>* __restrict__ V, int64_t vstride, int 
   }
 }
 
+// x[r] += sum_{k < ncols[r]} V_k[r] y[r][k] for complex64 bases: the sum in fp32 (the
+// coefficients rounded to fp32 once, in shared memory), the addition to x in fp64
+__global__ void __launch_bounds__(256)
+xupdate32_kernel(const float2* __restrict__ V, int64_t vstride, int nvec, const double2* __restrict__ coef, int maxv,
+                 double2* __restrict__ x, int64_t n, int64_t rstride, const int* __restrict__ ncols) {
+  const int r = blockIdx.y;
+  const int nv = ncols ? min(nvec, ncols[r]) : nvec;
+  extern __shared__ float2 xcs[];
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+    const double2 c = coef[r * maxv + k];
+    xcs[k] = make_float2((float)c.x, (float)c.y);
+  }
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float sx = 0.f, sy = 0.f;
+    for (int k = 0; k < nv; ++k) {
+      const float2 v = V[(int64_t)k * vstride + r * rstride + i];
+      const float2 c = xcs[k];
+      sx = fmaf(v.x, c.x, fmaf(-v.y, c.y, sx));
+      sy = fmaf(v.x, c.y, fmaf(v.y, c.x, sy));
+    }
+    double2 o = x[r * rstride + i];
+    o.x += sx;
+    o.y += sy;
+    x[r * rstride + i] = o;
+  }
+}
+
 // y[r] = scale[r] * x[r] (scale from a device vector: 1/norm, or 0 if norm == 0)
 template <typename XR, typename YR>
 __global__ void scale_kernel(const C<XR>* __restrict__ x, C<YR>* __restrict__ y, int64_t n, int64_t rstride,
@@ -632,21 +660,36 @@ dcgs2_update_kernel(float2* __restrict__ V, int64_t vstride, int j, GState s, in
 
 // back substitution y = H^{-1} g over the first ncols columns
 __global__ void lsq_kernel(GState s, int R, int m, int maxv) {
-  int r = threadIdx.x;
+  // one block per RHS, column-oriented back substitution: y_k = b_k / H_kk, then
+  // b_i -= H_ik y_k for i < k in parallel
+  const int r = blockIdx.x;
   if (r >= R) return;
-  int nc = s.ncols[r];
-  for (int k = 0; k < maxv; ++k) s.y[r * maxv + k] = make_double2(0, 0);
+  extern __shared__ double2 lsb[];  // [maxv]
+  __shared__ double2 yk_sh;
+  const int nc = s.ncols[r];
+  for (int k = threadIdx.x; k < maxv; k += blockDim.x) {
+    s.y[r * maxv + k] = make_double2(0, 0);
+    lsb[k] = k < nc ? s.g[r * maxv + k] : make_double2(0, 0);
+  }
+  __syncthreads();
+  const double2* H = s.H + (int64_t)r * maxv * m;  // H[i * m + k]
   for (int k = nc - 1; k >= 0; --k) {
-    double2 acc = s.g[r * maxv + k];
-    for (int l = k + 1; l < nc; ++l) {
-      double2 hk = s.H[((int64_t)r * maxv + k) * m + l], yl = s.y[r * maxv + l];
-      acc.x -= hk.x * yl.x - hk.y * yl.y;
-      acc.y -= hk.x * yl.y + hk.y * yl.x;
+    if (threadIdx.x == 0) {
+      const double2 d = H[(int64_t)k * m + k], acc = lsb[k];
+      const double den = cabs2(d);
+      const double2 yk = den > 0 ? make_double2((acc.x * d.x + acc.y * d.y) / den, (acc.y * d.x - acc.x * d.y) / den)
+                                 : make_double2(0, 0);
+      s.y[r * maxv + k] = yk;
+      yk_sh = yk;
     }
-    double2 d = s.H[((int64_t)r * maxv + k) * m + k];
-    double den = cabs2(d);
-    s.y[r * maxv + k] = den > 0 ? make_double2((acc.x * d.x + acc.y * d.y) / den, (acc.y * d.x - acc.x * d.y) / den)
-                                : make_double2(0, 0);
+    __syncthreads();
+    const double2 yk = yk_sh;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+      const double2 h = H[(int64_t)i * m + k];
+      lsb[i].x -= h.x * yk.x - h.y * yk.y;
+      lsb[i].y -= h.x * yk.y + h.y * yk.x;
+    }
+    __syncthreads();
   }
 }
 
@@ -860,10 +903,15 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
         }
       }
       // x += V y over the columns each RHS built in this cycle (ncols[r] <= j)
-      lsq_kernel<<<1, 32, 0, ctx->stream>>>(s, R, m, maxv);
+      lsq_kernel<<<R, 128, sizeof(double2) * maxv, ctx->stream>>>(s, R, m, maxv);
       TM_LAUNCHED(ctx);
-      update_kernel<VR, double><<<dim3(g1, R), 256, 0, ctx->stream>>>(V, (int64_t)R * n, j, s.y, maxv, 1.0, x, n, rs,
-                                                                      nullptr, s.ncols);
+      if constexpr (sizeof(VR) == 4) {
+        xupdate32_kernel<<<dim3(g1, R), 256, sizeof(float2) * std::max(j, 1), ctx->stream>>>(
+            reinterpret_cast<const float2*>(V), (int64_t)R * n, j, s.y, maxv, x, n, rs, s.ncols);
+      } else {
+        update_kernel<VR, double><<<dim3(g1, R), 256, 0, ctx->stream>>>(V, (int64_t)R * n, j, s.y, maxv, 1.0, x, n, rs,
+                                                                        nullptr, s.ncols);
+      }
       TM_LAUNCHED(ctx);
       // true residual r = b - K x (in the operator precision)
       convert_kernel<double, VR><<<g1, 256, 0, ctx->stream>>>(x, xv, (int64_t)R * n);

@@ -92,19 +92,39 @@ fft_rows_kernel(const C<R>* __restrict__ in, int64_t in_batch_stride, int in_pit
     a[rr * pitch + rev] = v;
   }
   __syncthreads();
-  for (int s = 0; s < lg; ++s) {
-    const int half = 1 << s;
-    const int tsh = lg - 1 - s;  // twiddle index = j * len / (2 half)
+  int s = 0;
+  if (lg & 1) {  // one radix-2 stage (twiddle 1) when the length is an odd power of two
     for (int e = threadIdx.x; e < (rb << (lg - 1)); e += blockDim.x) {
       const int rr = e >> (lg - 1), p = e & ((len >> 1) - 1);
-      const int j = p & (half - 1);
-      const int i0 = ((p >> s) << (s + 1)) + j, i1 = i0 + half;
-      const C<R> w = ws[j << tsh];
       C<R>* row = a + rr * pitch;
-      const C<R> t = cmul(w, row[i1]);
-      const C<R> u = row[i0];
-      row[i0] = cadd(u, t);
-      row[i1] = csub(u, t);
+      const C<R> u = row[2 * p], t = row[2 * p + 1];
+      row[2 * p] = cadd(u, t);
+      row[2 * p + 1] = csub(u, t);
+    }
+    __syncthreads();
+    s = 1;
+  }
+  // radix-4: the radix-2 stages s and s + 1 fused in registers (twiddles W_{2h}^j for the
+  // first, W_{4h}^j and W_{4h}^{j+h} = W_{4h}^j (-/+ i) for the second)
+  for (; s + 1 < lg; s += 2) {
+    const int half = 1 << s;
+    for (int e = threadIdx.x; e < (rb << (lg - 2)); e += blockDim.x) {
+      const int rr = e >> (lg - 2), p = e & ((len >> 2) - 1);
+      const int j = p & (half - 1);
+      const int i0 = ((p >> s) << (s + 2)) + j;
+      C<R>* row = a + rr * pitch;
+      const C<R> w1 = ws[j << (lg - 1 - s)], w2 = ws[j << (lg - 2 - s)];
+      const C<R> a0 = row[i0], a1 = cmul(w1, row[i0 + half]);
+      const C<R> a2 = row[i0 + 2 * half], a3 = cmul(w1, row[i0 + 3 * half]);
+      const C<R> b0 = cadd(a0, a1), b1 = csub(a0, a1), b2 = cadd(a2, a3), b3 = csub(a2, a3);
+      const C<R> t2 = cmul(w2, b2);
+      C<R> t3 = cmul(w2, b3);
+      // times -i (forward) or +i (inverse)
+      t3 = dir < 0 ? mk<R>(t3.y, -t3.x) : mk<R>(-t3.y, t3.x);
+      row[i0] = cadd(b0, t2);
+      row[i0 + 2 * half] = csub(b0, t2);
+      row[i0 + half] = cadd(b1, t3);
+      row[i0 + 3 * half] = csub(b1, t3);
     }
     __syncthreads();
   }
