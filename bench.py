@@ -194,6 +194,22 @@ def cpu_baseline(wl, matvecs_per_solve, budget_s=12.0):
                       f"x{matvecs_per_solve} applications per solve (the GPU run's count)"}
 
 
+def max_over_ranks(value, world, device):
+    """The largest of the ranks' values (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, steps, t_max_ms):
+    """Solves per second of the whole job: every rank solves `steps` independent
+    problems (replicas, weak scaling) within the slowest rank's time."""
+    return world * steps / (t_max_ms / 1e3)
+
+
 def _wall(fn, sync):
     sync()
     t0 = time.perf_counter()
@@ -457,12 +473,8 @@ def run_ours(args, rank, world):
     h2d = sum(a.nbytes for a in h_in)
     d2h = R * N * P * 16 + E.nbytes
     # max over ranks
-    t_local = total_ms
-    if world > 1:
-        t = torch.tensor([t_local], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_local = float(t.item())
-    value = world * args.steps / (t_local / 1e3)
+    t_local = max_over_ranks(total_ms, world, "cuda")
+    value = replica_throughput(world, args.steps, t_local)
     pairs = pairs_within(200, 200, int(round(cutoff / PITCH)))
     flop_per_launch = 8.0 * (P * P / 2) * pairs * R  # nonzero complex MACs x 8 flop, both RHS per launch
     avg32 = ms32 / max(n32, 1)
