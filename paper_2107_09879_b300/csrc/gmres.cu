@@ -1013,7 +1013,13 @@ int solve_system(tmat_ctx* ctx, const Operator& A64, const Operator* A32, int mo
     scale_kernel<double, float><<<dim3(g1, R), 256, 0, ctx->stream>>>(r64, r32, n, n, alpha, 1, nullptr);
     TM_LAUNCHED(ctx);
     GmresParams ip = gp;
-    ip.tol = p.inner_tol;
+    // Do not oversolve: a correction that reduces ||r|| by rho leaves ~rho ||r||, so when
+    // the remaining factor to the tolerance is milder than inner_tol the inner solve stops
+    // at half of it (the most demanding of the RHS still refined decides).
+    double need = 1.0;
+    for (int r = 0; r < R; ++r)
+      if (halpha[r] != 0.0 && hr[r] > 0) need = std::min(need, 0.5 * p.tol * hb[r] / hr[r]);
+    ip.tol = std::max(p.inner_tol, need);
     ip.max_iter = p.max_iter - st->iterations;
     GmresStats gs;
     TM_TRY(gmres_run<float>(ctx, *A32, mode, r32, d64, R, n, ip, &gs));
