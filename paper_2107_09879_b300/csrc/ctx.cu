@@ -39,20 +39,38 @@ int scratch(tmat_ctx* ctx, const char* name, size_t bytes, void** out) {
   return TMAT_OK;
 }
 
-cudaEvent_t timing_begin(tmat_ctx* ctx) {
-  if (!ctx->timing) return nullptr;
+static cudaEvent_t pooled_event(tmat_ctx* ctx) {
+  if (!ctx->event_pool.empty()) {
+    cudaEvent_t e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return e;
+  }
   cudaEvent_t e;
   if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-  cudaEventRecord(e, ctx->stream);
+  return e;
+}
+
+cudaEvent_t timing_begin(tmat_ctx* ctx) {
+  if (!ctx->timing) return nullptr;
+  cudaEvent_t e = pooled_event(ctx);
+  if (e) cudaEventRecord(e, ctx->stream);
   return e;
 }
 
 void timing_end(tmat_ctx* ctx, const char* kind, cudaEvent_t start) {
   if (!start) return;
-  cudaEvent_t e;
-  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEvent_t e = pooled_event(ctx);
+  if (!e) return;
   cudaEventRecord(e, ctx->stream);
   ctx->timed[kind].push_back({start, e});
+}
+
+int set_smem_limit(tmat_ctx* ctx, const void* func, size_t bytes) {
+  auto it = ctx->smem_attr.find(func);
+  if (it != ctx->smem_attr.end() && it->second >= (int)bytes) return TMAT_OK;
+  TM_CUDA(ctx, cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  ctx->smem_attr[func] = (int)bytes;
+  return TMAT_OK;
 }
 
 bool is_device_ptr(const void* p) {
@@ -101,13 +119,18 @@ int finish_out(tmat_ctx* ctx, Staged* s) {
 
 using namespace tmat;
 
-static void drop_events(tmat_ctx* ctx) {
+// recorded timing events go back to the pool (destroy_all: release them, at destruction)
+static void drop_events(tmat_ctx* ctx, bool destroy_all = false) {
   for (auto& kv : ctx->timed)
     for (auto& pr : kv.second) {
-      cudaEventDestroy(pr.first);
-      cudaEventDestroy(pr.second);
+      ctx->event_pool.push_back(pr.first);
+      ctx->event_pool.push_back(pr.second);
     }
   ctx->timed.clear();
+  if (destroy_all) {
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    ctx->event_pool.clear();
+  }
 }
 
 
@@ -143,7 +166,7 @@ extern "C" int tmat_ctx_destroy(tmat_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (auto& kv : ctx->bufs) cudaFree(kv.second.p);
   for (auto& kv : ctx->tables) free_tables(kv.second);
-  drop_events(ctx);
+  drop_events(ctx, true);
   cudaFreeHost(ctx->pinned);
   delete ctx;
   return TMAT_OK;

@@ -812,7 +812,7 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
         float2* V32 = reinterpret_cast<float2*>(V);
         const size_t gsm_bytes = sizeof(double2) * (2 * (size_t)m + maxv);
         if (gsm_bytes > 48 * 1024)
-          TM_CUDA(ctx, cudaFuncSetAttribute(givens_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm_bytes));
+          TM_TRY(set_smem_limit(ctx, (const void*)givens_kernel, gsm_bytes));
         for (;; ++j) {
           const bool final_only = j == m || st->iterations >= p.max_iter;
           float2* vj = V32 + (int64_t)j * R * n;
@@ -888,7 +888,7 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
         TM_LAUNCHED(ctx);
         const size_t gsm_bytes = sizeof(double2) * (2 * (size_t)m + maxv);
         if (gsm_bytes > 48 * 1024)
-          TM_CUDA(ctx, cudaFuncSetAttribute(givens_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm_bytes));
+          TM_TRY(set_smem_limit(ctx, (const void*)givens_kernel, gsm_bytes));
         givens_kernel<<<R, 64, gsm_bytes, ctx->stream>>>(s, R, j, m, maxv);
         TM_LAUNCHED(ctx);
         st->iterations++;

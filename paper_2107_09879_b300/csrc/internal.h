@@ -59,6 +59,8 @@ struct tmat_ctx {
   // kernel timing (off by default): event pairs recorded around operator launches
   bool timing = false;
   std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> timed;
+  std::vector<cudaEvent_t> event_pool;          // recycled timing events
+  std::map<const void*, int> smem_attr;         // dynamic shared memory limit set per kernel
   int device = 0;
   cudaStream_t stream = nullptr;
   char err[512] = {0};
@@ -109,6 +111,8 @@ void free_tables(Tables* t);
 // scratch buffer; an output that is host memory gets a scratch buffer and is
 // copied back by finish_out().
 bool is_device_ptr(const void* p);
+// Raise a kernel's dynamic shared memory limit once per context (the driver call is not free).
+int set_smem_limit(tmat_ctx* ctx, const void* func, size_t bytes);
 struct Staged {
   const void* user = nullptr;
   void* dev = nullptr;

@@ -195,9 +195,7 @@ static int launch_lat(tmat_ctx* ctx, const LatOp& a, const void* x, void* y, int
   dim3 grid((unsigned)cdiv(a.N, LAT_THREADS), 2 * S);
   size_t smem = sizeof(C<R>) * 2 * L * a.LP;
   auto kern = lattice_apply_kernel<R, NMAX, NR, MODE>;
-  if (smem > 48 * 1024) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  }
+  if (smem > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, smem));
   cudaEvent_t ev = timing_begin(ctx);
   kern<<<grid, LAT_THREADS, smem, ctx->stream>>>(a.off, a.neg, a.K, a.nx, a.ny, a.N, (const C<R>*)a.BT, a.LP,
                                                   (const C<R>*)a.T, (const C<R>*)x, (C<R>*)y, rstride);

@@ -148,7 +148,7 @@ static int fft_rows(tmat_ctx* ctx, const C<R>* in, int64_t in_bs, int in_pitch, 
   const int rb = 1 << lgrb;
   const size_t smem = sizeof(C<R>) * ((size_t)rb * (len + 1) + len / 2 + 1);
   auto kern = fft_rows_kernel<R, TOUT>;
-  if (smem > 48 * 1024) TM_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (smem > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, smem));
   for (int64_t b0 = 0; b0 < nbatch; b0 += 65535) {
     const int nb = (int)std::min<int64_t>(65535, nbatch - b0);
     dim3 grid((unsigned)cdiv(nrows, rb), (unsigned)nb);

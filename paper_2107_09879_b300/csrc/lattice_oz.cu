@@ -647,7 +647,7 @@ static int run_oz(tmat_ctx* ctx, const LatOp& a, const void* x, void* y, int R_)
   }
   auto kern = lattice_oz_kernel<NMAX, MODE>;
   const size_t smem = oz_smem<NMAX>(a.CX);
-  TM_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TM_TRY(set_smem_limit(ctx, (const void*)kern, smem));
   const int64_t rows = (int64_t)a.ny * Wd;
   dim3 grid((unsigned)cdiv(rows, 128), 2, (unsigned)R_);
   cudaEvent_t ev = timing_begin(ctx);

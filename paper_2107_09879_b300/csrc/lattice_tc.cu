@@ -421,7 +421,7 @@ static int launch_tc(tmat_ctx* ctx, const LatOp& a, const float* W, const void* 
                      int64_t rs, int* err) {
   auto kern = lattice_tc_kernel<NMAX, NR, MODE>;
   const size_t smem = tc_smem<NMAX>(NR, a.CX);
-  TM_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TM_TRY(set_smem_limit(ctx, (const void*)kern, smem));
   constexpr int SITES = TC_M / NR;
   dim3 grid((unsigned)cdiv(a.N, SITES), 2);
   cudaEvent_t ev = timing_begin(ctx);

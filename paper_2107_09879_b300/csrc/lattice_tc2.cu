@@ -363,7 +363,7 @@ static int run_tc2(tmat_ctx* ctx, const LatOp& a, const float* W, const void* x,
   }
   auto kern = lattice_tc2_kernel<NMAX, MODE>;
   const size_t smem = tc2_smem<NMAX>(a.CX);
-  TM_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TM_TRY(set_smem_limit(ctx, (const void*)kern, smem));
   const int64_t rows = (int64_t)a.ny * Wd;
   dim3 grid((unsigned)cdiv(rows, 128), 2, (unsigned)R_);
   cudaEvent_t ev = timing_begin(ctx);
