@@ -586,17 +586,27 @@ __global__ void dcgs2_small_kernel(GState s, int j, int m, int maxv, int R, int 
   }
   __syncthreads();
   const double2 zeta = zeta_sh;
-  // column j: H[i][j] = ([z; zeta]_i - (H s)_i)/nu, H s over the final columns 0..j-1
-  for (int i = tid; i <= j; i += blockDim.x) {
-    double2 t = make_double2(0, 0);
-    const int c0 = i > 0 ? i - 1 : 0;  // H is upper Hessenberg: H[i][c] = 0 for c < i - 1
-    for (int c = c0; c < j; ++c) {
-      const double2 h = Hu[(int64_t)i * m + c];
-      t.x += h.x * sv[c].x - h.y * sv[c].y;
-      t.y += h.x * sv[c].y + h.y * sv[c].x;
+  // column j: H[i][j] = ([z; zeta]_i - (H s)_i)/nu, H s over the final columns 0..j-1;
+  // one warp per row, the lanes split the row (H is upper Hessenberg: H[i][c] = 0 for c < i - 1)
+  {
+    const int lane = tid & 31, nw = blockDim.x >> 5;
+    for (int i = tid >> 5; i <= j; i += nw) {
+      double tx = 0.0, ty = 0.0;
+      const int c0 = i > 0 ? i - 1 : 0;
+      for (int c = c0 + lane; c < j; c += 32) {
+        const double2 h = Hu[(int64_t)i * m + c];
+        tx += h.x * sv[c].x - h.y * sv[c].y;
+        ty += h.x * sv[c].y + h.y * sv[c].x;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        tx += __shfl_down_sync(0xffffffffu, tx, o);
+        ty += __shfl_down_sync(0xffffffffu, ty, o);
+      }
+      if (lane == 0) {
+        const double2 zi2 = i < j ? make_double2(D2[i].x / b1, D2[i].y / b1) : zeta;
+        Hu[(int64_t)i * m + j] = make_double2((zi2.x - tx) / nu, (zi2.y - ty) / nu);
+      }
     }
-    const double2 zi2 = i < j ? make_double2(D2[i].x / b1, D2[i].y / b1) : zeta;
-    Hu[(int64_t)i * m + j] = make_double2((zi2.x - t.x) / nu, (zi2.y - t.y) / nu);
   }
   // update coefficients
   const double zn_r = zeta.x / nu, zn_i = zeta.y / nu;  // zeta / nu

@@ -63,16 +63,21 @@ static int fft_twiddles(tmat_ctx* ctx, const double2** out) {
 // batch. Output: natural out[b][row][k] (pitch out_pitch, k < cout), or transposed
 // out[b][k][row] (pitch out_pitch over rows, k < cout). dir = -1 forward, +1 inverse
 // (unnormalised). One block handles rb = 2^lgrb rows of one batch; the rows sit in
-// shared memory with an odd pitch (len + 1) so that the transposed read-out, where
+// shared memory padded (one slot per 16 values, plus one per row) so that the transposed read-out, where
 // consecutive threads take consecutive rows, spreads over the banks; the twiddles of
 // this length are staged in shared memory too.
+// shared-memory position of element i of a row: one pad slot after every 16 values, so
+// the power-of-two strides of the butterflies and of the bit-reversed stores fall on
+// different banks
+__device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
+
 template <typename R, bool TOUT>
 __global__ void __launch_bounds__(FFT_THREADS)
 fft_rows_kernel(const C<R>* __restrict__ in, int64_t in_batch_stride, int in_pitch, int cin, int nrows,
                 C<R>* __restrict__ out, int64_t out_batch_stride, int out_pitch, int cout, int lg, int lgrb, int dir,
                 const double2* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char fsm[];
-  const int len = 1 << lg, rb = 1 << lgrb, pitch = len + 1;
+  const int len = 1 << lg, rb = 1 << lgrb, pitch = len + (len >> 4) + 1;
   C<R>* a = reinterpret_cast<C<R>*>(fsm);
   C<R>* ws = a + (size_t)rb * pitch;  // [len / 2]
   const int b = blockIdx.y;
@@ -89,7 +94,7 @@ fft_rows_kernel(const C<R>* __restrict__ in, int64_t in_batch_stride, int in_pit
     C<R> v = mk<R>((R)0, (R)0);
     if (rr < nr && cc < cin) v = src[(int64_t)rr * in_pitch + cc];
     const int rev = lg ? (int)(__brev((unsigned)cc) >> (32 - lg)) : 0;
-    a[rr * pitch + rev] = v;
+    a[rr * pitch + fpad(rev)] = v;
   }
   __syncthreads();
   int s = 0;
@@ -97,9 +102,10 @@ fft_rows_kernel(const C<R>* __restrict__ in, int64_t in_batch_stride, int in_pit
     for (int e = threadIdx.x; e < (rb << (lg - 1)); e += blockDim.x) {
       const int rr = e >> (lg - 1), p = e & ((len >> 1) - 1);
       C<R>* row = a + rr * pitch;
-      const C<R> u = row[2 * p], t = row[2 * p + 1];
-      row[2 * p] = cadd(u, t);
-      row[2 * p + 1] = csub(u, t);
+      const int q0 = fpad(2 * p), q1 = fpad(2 * p + 1);
+      const C<R> u = row[q0], t = row[q1];
+      row[q0] = cadd(u, t);
+      row[q1] = csub(u, t);
     }
     __syncthreads();
     s = 1;
@@ -113,18 +119,19 @@ fft_rows_kernel(const C<R>* __restrict__ in, int64_t in_batch_stride, int in_pit
       const int j = p & (half - 1);
       const int i0 = ((p >> s) << (s + 2)) + j;
       C<R>* row = a + rr * pitch;
+      const int q0 = fpad(i0), q1 = fpad(i0 + half), q2 = fpad(i0 + 2 * half), q3 = fpad(i0 + 3 * half);
       const C<R> w1 = ws[j << (lg - 1 - s)], w2 = ws[j << (lg - 2 - s)];
-      const C<R> a0 = row[i0], a1 = cmul(w1, row[i0 + half]);
-      const C<R> a2 = row[i0 + 2 * half], a3 = cmul(w1, row[i0 + 3 * half]);
+      const C<R> a0 = row[q0], a1 = cmul(w1, row[q1]);
+      const C<R> a2 = row[q2], a3 = cmul(w1, row[q3]);
       const C<R> b0 = cadd(a0, a1), b1 = csub(a0, a1), b2 = cadd(a2, a3), b3 = csub(a2, a3);
       const C<R> t2 = cmul(w2, b2);
       C<R> t3 = cmul(w2, b3);
       // times -i (forward) or +i (inverse)
       t3 = dir < 0 ? mk<R>(t3.y, -t3.x) : mk<R>(-t3.y, t3.x);
-      row[i0] = cadd(b0, t2);
-      row[i0 + 2 * half] = csub(b0, t2);
-      row[i0 + half] = cadd(b1, t3);
-      row[i0 + 3 * half] = csub(b1, t3);
+      row[q0] = cadd(b0, t2);
+      row[q2] = csub(b0, t2);
+      row[q1] = cadd(b1, t3);
+      row[q3] = csub(b1, t3);
     }
     __syncthreads();
   }
@@ -133,10 +140,10 @@ fft_rows_kernel(const C<R>* __restrict__ in, int64_t in_batch_stride, int in_pit
     // out[k][row0 + rr]: consecutive threads take consecutive rows of one k
     const int rr = threadIdx.x & (rb - 1);
     for (int k = threadIdx.x >> lgrb; k < cout; k += blockDim.x >> lgrb)
-      if (rr < nr) dst[(int64_t)k * out_pitch + row0 + rr] = a[rr * pitch + k];
+      if (rr < nr) dst[(int64_t)k * out_pitch + row0 + rr] = a[rr * pitch + fpad(k)];
   } else {
     for (int rr = 0; rr < nr; ++rr)
-      for (int k = threadIdx.x; k < cout; k += blockDim.x) dst[(int64_t)(row0 + rr) * out_pitch + k] = a[rr * pitch + k];
+      for (int k = threadIdx.x; k < cout; k += blockDim.x) dst[(int64_t)(row0 + rr) * out_pitch + k] = a[rr * pitch + fpad(k)];
   }
 }
 
@@ -146,7 +153,7 @@ static int fft_rows(tmat_ctx* ctx, const C<R>* in, int64_t in_bs, int in_pitch, 
   const int lg = ilog2(len);
   int lgrb = ilog2(std::max(1, std::min(TOUT ? 32 : 8, FFT_SMEM_POINTS / len)));
   const int rb = 1 << lgrb;
-  const size_t smem = sizeof(C<R>) * ((size_t)rb * (len + 1) + len / 2 + 1);
+  const size_t smem = sizeof(C<R>) * ((size_t)rb * (len + (len >> 4) + 1) + len / 2 + 1);
   auto kern = fft_rows_kernel<R, TOUT>;
   if (smem > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, smem));
   for (int64_t b0 = 0; b0 < nbatch; b0 += 65535) {
