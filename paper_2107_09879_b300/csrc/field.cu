@@ -6,6 +6,7 @@
 //  c_l = 1/sqrt(2 l (l+1)), (kr z_l)'/(kr) = z_{l-1} - l z_l/(kr), z = h^(1).
 // Far field: h_l(z) -> (-i)^{l+1} e^{iz}/z, so F_{lm0} = c_l (-i)^{l+1}[..], F_{lm1} = c_l (-i)^l (tau th^ + i m pi ph^) e^{imph}.
 #include <cmath>
+#include <mutex>
 
 #include "dev.cuh"
 #include "internal.h"
@@ -14,138 +15,202 @@ namespace tmat {
 
 constexpr int NM1 = TMAT_NMAX_MAX + 1;
 
-// normalised Legendre tables at cos(theta): P[l][m], pi[l][m] = P/sin, tau[l][m]
-__device__ void legendre_tables(int nmax, double ct, double st, double (*P)[NM1], double (*pi)[NM1], double (*tau)[NM1]) {
-  for (int l = 0; l <= nmax; ++l)
-    for (int m = 0; m <= nmax; ++m) P[l][m] = pi[l][m] = tau[l][m] = 0.0;
-  for (int m = 0; m <= nmax; ++m) {
+// Constants of the normalised Legendre recurrences (Doicu's normalisation, no
+// Condon-Shortley phase), l, m <= TMAT_NMAX_MAX, uploaded once per device:
+//   Pbar_m^m = base_m s^m, pi_m^m = base_m s^(m-1), base_m = sqrt((2m+1)/(2 (2m)!)) (2m-1)!!
+//   Pbar_l^m = a_lm (c Pbar_{l-1}^m - b_lm Pbar_{l-2}^m) (the same for pi),
+//   a_lm = sqrt((4l^2-1)/(l^2-m^2)), b_lm = sqrt(((l-1)^2-m^2)/(4(l-1)^2-1)),
+//   tau_l^0 = -sqrt(l(l+1)) Pbar_l^1, tau_l^m = l c pi_l^m - t_lm pi_{l-1}^m,
+//   t_lm = sqrt((2l+1)(l^2-m^2)/(2l-1)); c_l = 1/sqrt(2l(l+1)).
+struct LegConst {
+  double a[NM1][NM1], b[NM1][NM1], t[NM1][NM1], base[NM1], sq[NM1], cl[NM1];
+};
+__constant__ LegConst c_leg;
+
+// once per device (on `stream`); 0 or a CUDA error code
+static cudaError_t leg_upload(int device, cudaStream_t stream) {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  std::lock_guard<std::mutex> lock(mu);
+  if (device >= 0 && device < 64 && done[device]) return cudaSuccess;
+  LegConst h = {};
+  for (int m = 0; m < NM1; ++m) {
     double df = 1.0, f2 = 1.0;
     for (int t = 1; t < 2 * m; t += 2) df *= t;
     for (int t = 2; t <= 2 * m; ++t) f2 *= t;
-    double base = sqrt((2 * m + 1) / (2.0 * f2)) * df;  // Pbar_m^m = base s^m; pi_m^m = base s^(m-1)
-    double q_prev = 0.0, q_cur = (m >= 1) ? base * pow(st, (double)(m - 1)) : 0.0;
-    double p_prev = 0.0, p_cur = base * pow(st, (double)m);
-    P[m][m] = p_cur;
-    pi[m][m] = q_cur;
-    for (int l = m + 1; l <= nmax; ++l) {
-      double a = sqrt((4.0 * l * l - 1) / ((double)l * l - (double)m * m));
-      double b = sqrt(((l - 1.0) * (l - 1.0) - (double)m * m) / (4.0 * (l - 1.0) * (l - 1.0) - 1));
-      double pn = a * (ct * p_cur - b * p_prev);
-      double qn = a * (ct * q_cur - b * q_prev);
-      p_prev = p_cur;
-      p_cur = pn;
-      q_prev = q_cur;
-      q_cur = qn;
-      P[l][m] = pn;
-      pi[l][m] = qn;
+    h.base[m] = std::sqrt((2 * m + 1) / (2.0 * f2)) * df;
+  }
+  for (int l = 0; l < NM1; ++l) {
+    h.sq[l] = std::sqrt(l * (l + 1.0));
+    h.cl[l] = l > 0 ? 1.0 / std::sqrt(2.0 * l * (l + 1)) : 0.0;
+    for (int m = 0; m < NM1; ++m) {
+      if (l > m) {
+        h.a[l][m] = std::sqrt((4.0 * l * l - 1) / ((double)l * l - (double)m * m));
+        h.b[l][m] = std::sqrt(((l - 1.0) * (l - 1.0) - (double)m * m) / (4.0 * (l - 1.0) * (l - 1.0) - 1));
+      }
+      if (l >= 1 && m <= l) h.t[l][m] = std::sqrt((2.0 * l + 1) * ((double)l * l - (double)m * m) / (2.0 * l - 1));
     }
   }
-  for (int l = 1; l <= nmax; ++l) {
-    tau[l][0] = -sqrt(l * (l + 1.0)) * P[l][1 <= nmax ? 1 : 0];
-    for (int m = 1; m <= l; ++m) {
-      double prev = (l - 1 >= m) ? pi[l - 1][m] : 0.0;
-      tau[l][m] = l * ct * pi[l][m] - sqrt((2.0 * l + 1) * ((double)l * l - (double)m * m) / (2.0 * l - 1)) * prev;
-    }
-  }
+  cudaError_t e = cudaMemcpyToSymbolAsync(c_leg, &h, sizeof(h), 0, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e == cudaSuccess && device >= 0 && device < 64) done[device] = true;
+  return e;
+}
+
+static int upload_legendre(tmat_ctx* ctx) {
+  TM_CUDA(ctx, leg_upload(ctx->device, ctx->stream));
+  return TMAT_OK;
 }
 
 // Calls f(flat, vec[3]) for every VSWF Phi_f(k d) (outgoing), far=false, or the
-// far-field amplitude F_f(d^), far=true (|d| ignored).
-template <typename Fn>
-__device__ void for_each_wave(int nmax, double k, double dx, double dy, double dz, bool far, Fn f) {
-  const int L = nmax * (nmax + 2);
-  double r = sqrt(dx * dx + dy * dy + dz * dz);
-  double ct = dz / r, st = sqrt(fmax(0.0, 1.0 - ct * ct));
-  double rho = sqrt(dx * dx + dy * dy);
-  double cp = rho > 0 ? dx / rho : 1.0, sp = rho > 0 ? dy / rho : 0.0;
-  double P[NM1][NM1], pi[NM1][NM1], tau[NM1][NM1];
-  legendre_tables(nmax, ct, st, P, pi, tau);
-  double2 h[NM1 + 1];
-  double kr = k * r;
-  if (!far) {
-    double s, c;
-    sincos(kr, &s, &c);
-    double ix = 1.0 / kr;
-    h[0] = make_double2(s * ix, -c * ix);
-    h[1] = make_double2(-ix * c + ix * ix * s, -ix * s - ix * ix * c);
-    for (int q = 1; q < nmax; ++q) {
-      double fq = (2 * q + 1) * ix;
-      h[q + 1] = make_double2(fq * h[q].x - h[q - 1].x, fq * h[q].y - h[q - 1].y);
+// far-field amplitude F_f(d^), far=true (|d| ignored). Compile-time nmax; the waves are
+// produced m-major (the flat index carries the order), so only one Legendre recurrence
+// (over l, for the current m) is live at a time; e^{i m phi} by powers of e^{i phi}.
+template <int NMAX, typename Fn>
+__device__ __forceinline__ void waves_t(double k, double dx, double dy, double dz, bool far, Fn&& f) {
+  constexpr int L = NMAX * (NMAX + 2);
+  const double r = sqrt(dx * dx + dy * dy + dz * dz);
+  const double ct = dz / r, st = sqrt(fmax(0.0, 1.0 - ct * ct));
+  const double rho = sqrt(dx * dx + dy * dy);
+  const double cp = rho > 0 ? dx / rho : 1.0, sp = rho > 0 ? dy / rho : 0.0;
+  // radial factors c_l z_l, c_l l(l+1) z_l/(kr), c_l (z_{l-1} - l z_l/(kr)) (far: phases)
+  double2 zM[NMAX + 1], zNr[NMAX + 1], zNt[NMAX + 1];
+  {
+    const double kr = k * r;
+    double2 h[NMAX + 1];
+    if (!far) {
+      double sn, cs;
+      sincos(kr, &sn, &cs);
+      const double ix = 1.0 / kr;
+      h[0] = make_double2(sn * ix, -cs * ix);
+      h[1] = make_double2(-ix * cs + ix * ix * sn, -ix * sn - ix * ix * cs);
+#pragma unroll
+      for (int q = 1; q < NMAX; ++q) {
+        const double fq = (2 * q + 1) * ix;
+        h[q + 1] = make_double2(fq * h[q].x - h[q - 1].x, fq * h[q].y - h[q - 1].y);
+      }
+    }
+#pragma unroll
+    for (int l = 1; l <= NMAX; ++l) {
+      const double cl = c_leg.cl[l];
+      if (far) {
+        const int e = (3 * (l + 1)) & 3;  // (-i)^{l+1} = i^{3(l+1)}
+        zM[l] = make_double2(e == 0 ? cl : (e == 2 ? -cl : 0.0), e == 1 ? cl : (e == 3 ? -cl : 0.0));
+        const int e2 = (3 * l) & 3;
+        zNt[l] = make_double2(e2 == 0 ? cl : (e2 == 2 ? -cl : 0.0), e2 == 1 ? cl : (e2 == 3 ? -cl : 0.0));
+        zNr[l] = make_double2(0, 0);
+      } else {
+        zM[l] = cscale(h[l], cl);
+        zNr[l] = cscale(h[l], cl * l * (l + 1.0) / kr);
+        zNt[l] = make_double2(cl * (h[l - 1].x - l * h[l].x / kr), cl * (h[l - 1].y - l * h[l].y / kr));
+      }
     }
   }
-  double3 rh = make_double3(st * cp, st * sp, ct), th = make_double3(ct * cp, ct * sp, -st), ph = make_double3(-sp, cp, 0.0);
-  const double ir[4] = {1, 0, -1, 0}, ii[4] = {0, 1, 0, -1};
-  for (int l = 1; l <= nmax; ++l) {
-    double cl = 1.0 / sqrt(2.0 * l * (l + 1));
-    double2 zM, zNr, zNt;  // radial factors of M, of N's radial part, of N's tangential part
-    if (far) {
-      int e = (3 * (l + 1)) & 3;  // (-i)^{l+1} = i^{3(l+1)}
-      zM = make_double2(ir[e], ii[e]);
-      int e2 = (3 * l) & 3;
-      zNt = make_double2(ir[e2], ii[e2]);
-      zNr = make_double2(0, 0);
-    } else {
-      zM = h[l];
-      zNr = cscale(h[l], l * (l + 1.0) / kr);
-      zNt = make_double2(h[l - 1].x - l * h[l].x / kr, h[l - 1].y - l * h[l].y / kr);
+  const double thv[3] = {ct * cp, ct * sp, -st}, phv[3] = {-sp, cp, 0.0}, rhv[3] = {st * cp, st * sp, ct};
+  // Pbar_l^1 for tau_l^0 = -sqrt(l(l+1)) Pbar_l^1
+  double P1[NMAX + 1];
+  {
+    double pp = 0.0, pc = c_leg.base[1] * st;
+    P1[1] = pc;
+#pragma unroll
+    for (int l = 2; l <= NMAX; ++l) {
+      const double pn = c_leg.a[l][1] * (ct * pc - c_leg.b[l][1] * pp);
+      pp = pc;
+      pc = pn;
+      P1[l] = pn;
     }
-    for (int m = -l; m <= l; ++m) {
-      int am = m < 0 ? -m : m;
-      double mpi = m * pi[l][am], ta = tau[l][am], pb = P[l][am];
-      double sm, cm;
-      sincos(m * atan2(sp, cp), &sm, &cm);
-      double2 e = make_double2(cm, sm);
-      // M: c z [ i mpi th - ta ph ] e ; N: c [ zNr pb r + zNt (ta th + i mpi ph) ] e
-      double2 aM = cmul(cscale(zM, cl), e), aNr = cmul(cscale(zNr, cl * pb), e), aNt = cmul(cscale(zNt, cl), e);
-      double2 vM[3], vN[3];
-      const double thv[3] = {th.x, th.y, th.z}, phv[3] = {ph.x, ph.y, ph.z}, rhv[3] = {rh.x, rh.y, rh.z};
-      for (int c = 0; c < 3; ++c) {
-        // i*mpi*th_c - ta*ph_c   and   ta*th_c + i*mpi*ph_c
-        double2 gM = make_double2(-ta * phv[c], mpi * thv[c]);
-        double2 gN = make_double2(ta * thv[c], mpi * phv[c]);
-        vM[c] = cmul(aM, gM);
-        vN[c] = cadd(cscale(aNr, rhv[c]), cmul(aNt, gN));
+  }
+  double2 em = make_double2(1.0, 0.0);
+  double pw = 1.0, pw1 = 1.0;  // st^m and st^(m-1)
+#pragma unroll
+  for (int m = 0; m <= NMAX; ++m) {
+    const double base = c_leg.base[m];
+    double p_prev = 0.0, p_cur = base * pw;                    // Pbar_m^m
+    double q_prev = 0.0, q_cur = m >= 1 ? base * pw1 : 0.0;    // pi_m^m
+#pragma unroll
+    for (int l = (m > 1 ? m : 1); l <= NMAX; ++l) {
+      if (l > m) {
+        const double a = c_leg.a[l][m], bb = c_leg.b[l][m];
+        const double pn = a * (ct * p_cur - bb * p_prev), qn = a * (ct * q_cur - bb * q_prev);
+        p_prev = p_cur;
+        p_cur = pn;
+        q_prev = q_cur;
+        q_cur = qn;
       }
-      int n = l * (l + 1) + m - 1;
-      f(n, vM);
-      f(L + n, vN);
+      // now p_cur = Pbar_l^m, q_cur = pi_l^m, q_prev = pi_{l-1}^m (0 when l == m)
+      const double pb = p_cur;
+      const double ta = m == 0 ? -c_leg.sq[l] * P1[l] : l * ct * q_cur - c_leg.t[l][m] * (l > m ? q_prev : 0.0);
+#pragma unroll
+      for (int sg = 0; sg < (m == 0 ? 1 : 2); ++sg) {
+        const int mm = sg == 0 ? m : -m;
+        const double mpi = mm * q_cur;
+        const double2 e = sg == 0 ? em : cconj(em);
+        // M: c z [ i mpi th - ta ph ] e ; N: c [ zNr pb r + zNt (ta th + i mpi ph) ] e
+        const double2 aM = cmul(zM[l], e), aNr = cmul(cscale(zNr[l], pb), e), aNt = cmul(zNt[l], e);
+        double2 vM[3], vN[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double2 gM = make_double2(-ta * phv[c], mpi * thv[c]);
+          const double2 gN = make_double2(ta * thv[c], mpi * phv[c]);
+          vM[c] = cmul(aM, gM);
+          vN[c] = cadd(cscale(aNr, rhv[c]), cmul(aNt, gN));
+        }
+        const int n = l * (l + 1) + mm - 1;
+        f(n, vM);
+        f(L + n, vN);
+      }
     }
+    pw1 = pw;
+    pw *= st;
+    em = cmul(em, make_double2(cp, sp));
   }
 }
 
 // partial E over a chunk of scatterers: grid (M, chunks); block reduce
-__global__ void field_kernel(const double* __restrict__ pos, int64_t N, double k, int nmax, const double2* __restrict__ s,
-                             const double* __restrict__ pts, int64_t M, int far, double2* __restrict__ part) {
+template <int NMAX, bool FAR>
+__global__ void __launch_bounds__(128)
+field_kernel(const double* __restrict__ pos, int64_t N, double k, const double2* __restrict__ s,
+             const double* __restrict__ pts, int64_t M, double2* __restrict__ part) {
+  constexpr int P = 2 * NMAX * (NMAX + 2);
   const int64_t a = blockIdx.x;
-  const int P = num_coeffs(nmax);
   __shared__ double2 red[3][128];
   double2 E[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
-  double ux = 0, uy = 0, uz = 0;
-  if (far) {  // direction (theta, phi)
+  double ux = 0, uy = 0, uz = 0, px = 0, py = 0, pz = 0;
+  if (FAR) {  // direction (theta, phi)
     double s_, c_, sp_, cp_;
     sincos(pts[2 * a], &s_, &c_);
     sincos(pts[2 * a + 1], &sp_, &cp_);
     ux = s_ * cp_;
     uy = s_ * sp_;
     uz = c_;
+  } else {
+    px = pts[3 * a];
+    py = pts[3 * a + 1];
+    pz = pts[3 * a + 2];
   }
   for (int64_t i = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.y * blockDim.x) {
     const double2* si = s + i * P;
-    double2 acc[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+    double2 acc0 = make_double2(0, 0), acc1 = make_double2(0, 0), acc2 = make_double2(0, 0);
     auto fn = [&](int f, const double2* v) {
-      double2 c = si[f];
-      for (int q = 0; q < 3; ++q) acc[q] = cadd(acc[q], cmul(c, v[q]));
+      const double2 c = si[f];
+      acc0 = cadd(acc0, cmul(c, v[0]));
+      acc1 = cadd(acc1, cmul(c, v[1]));
+      acc2 = cadd(acc2, cmul(c, v[2]));
     };
-    if (far) {
-      for_each_wave(nmax, k, ux, uy, uz, true, fn);
-      double ph = -k * (ux * pos[3 * i] + uy * pos[3 * i + 1] + uz * pos[3 * i + 2]);
+    if (FAR) {
+      waves_t<NMAX>(k, ux, uy, uz, true, fn);
+      const double ph = -k * (ux * pos[3 * i] + uy * pos[3 * i + 1] + uz * pos[3 * i + 2]);
       double sn, cs;
       sincos(ph, &sn, &cs);
-      for (int q = 0; q < 3; ++q) E[q] = cadd(E[q], cmul(make_double2(cs, sn), acc[q]));
+      const double2 e = make_double2(cs, sn);
+      E[0] = cadd(E[0], cmul(e, acc0));
+      E[1] = cadd(E[1], cmul(e, acc1));
+      E[2] = cadd(E[2], cmul(e, acc2));
     } else {
-      for_each_wave(nmax, k, pts[3 * a] - pos[3 * i], pts[3 * a + 1] - pos[3 * i + 1], pts[3 * a + 2] - pos[3 * i + 2],
-                    false, fn);
-      for (int q = 0; q < 3; ++q) E[q] = cadd(E[q], acc[q]);
+      waves_t<NMAX>(k, px - pos[3 * i], py - pos[3 * i + 1], pz - pos[3 * i + 2], false, fn);
+      E[0] = cadd(E[0], acc0);
+      E[1] = cadd(E[1], acc1);
+      E[2] = cadd(E[2], acc2);
     }
   }
   for (int q = 0; q < 3; ++q) red[q][threadIdx.x] = E[q];
@@ -154,6 +219,27 @@ __global__ void field_kernel(const double* __restrict__ pos, int64_t N, double k
     double2 t = make_double2(0, 0);
     for (int b = 0; b < blockDim.x; ++b) t = cadd(t, red[threadIdx.x][b]);
     part[(a * gridDim.y + blockIdx.y) * 3 + threadIdx.x] = t;
+  }
+}
+
+template <int NMAX>
+static void launch_field(dim3 grid, cudaStream_t st, const double* pos, int64_t N, double k, const double2* s,
+                         const double* pts, int64_t M, bool far, double2* part) {
+  if (far)
+    field_kernel<NMAX, true><<<grid, 128, 0, st>>>(pos, N, k, s, pts, M, part);
+  else
+    field_kernel<NMAX, false><<<grid, 128, 0, st>>>(pos, N, k, s, pts, M, part);
+}
+
+static void launch_field_n(int nmax, dim3 grid, cudaStream_t st, const double* pos, int64_t N, double k,
+                           const double2* s, const double* pts, int64_t M, bool far, double2* part) {
+  switch (nmax) {
+    case 1: launch_field<1>(grid, st, pos, N, k, s, pts, M, far, part); break;
+    case 2: launch_field<2>(grid, st, pos, N, k, s, pts, M, far, part); break;
+    case 3: launch_field<3>(grid, st, pos, N, k, s, pts, M, far, part); break;
+    case 4: launch_field<4>(grid, st, pos, N, k, s, pts, M, far, part); break;
+    case 5: launch_field<5>(grid, st, pos, N, k, s, pts, M, far, part); break;
+    case 6: launch_field<6>(grid, st, pos, N, k, s, pts, M, far, part); break;
   }
 }
 
@@ -168,6 +254,7 @@ __global__ void field_reduce_kernel(const double2* __restrict__ part, int64_t M,
 }
 
 // v[i][f] = sum_c conj(E_c) Phi_{f,c}(k(x_f - x_i))
+template <int NMAX>
 __global__ void adjoint_source_kernel(const double* __restrict__ pos, int64_t N, double k, int nmax,
                                       const double* __restrict__ xf, const double2* __restrict__ Etot,
                                       double2* __restrict__ v) {
@@ -175,7 +262,7 @@ __global__ void adjoint_source_kernel(const double* __restrict__ pos, int64_t N,
   if (i >= N) return;
   const int P = num_coeffs(nmax);
   double2 ce[3] = {cconj(Etot[0]), cconj(Etot[1]), cconj(Etot[2])};
-  for_each_wave(nmax, k, xf[0] - pos[3 * i], xf[1] - pos[3 * i + 1], xf[2] - pos[3 * i + 2], false,
+  waves_t<NMAX>(k, xf[0] - pos[3 * i], xf[1] - pos[3 * i + 1], xf[2] - pos[3 * i + 2], false,
                 [&](int f, const double2* w) {
                   double2 acc = make_double2(0, 0);
                   for (int q = 0; q < 3; ++q) acc = cadd(acc, cmul(ce[q], w[q]));
@@ -190,12 +277,13 @@ __global__ void add3_kernel(double2* __restrict__ E, const double2* __restrict__
 
 int field_dev(tmat_ctx* ctx, const double* pos, int64_t N, double k, int nmax, const double2* s, const double* pts,
               int64_t M, bool far, double2* E) {
+  TM_TRY(upload_legendre(ctx));
   if (M == 0) return TMAT_OK;
   int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(N, 128), std::max<int64_t>(1, 4 * ctx->num_sms / std::max<int64_t>(M, 1))));
   if (nchunk > 65535) nchunk = 65535;
   double2* part;
   TM_TRY(scratch(ctx, "fld_part", sizeof(double2) * M * nchunk * 3, (void**)&part));
-  field_kernel<<<dim3((unsigned)M, nchunk), 128, 0, ctx->stream>>>(pos, N, k, nmax, s, pts, M, far ? 1 : 0, part);
+  launch_field_n(nmax, dim3((unsigned)M, nchunk), ctx->stream, pos, N, k, s, pts, M, far, part);
   TM_LAUNCHED(ctx);
   field_reduce_kernel<<<(unsigned)cdiv(M * 3, 128), 128, 0, ctx->stream>>>(part, M, nchunk, E);
   TM_LAUNCHED(ctx);
@@ -260,8 +348,11 @@ extern "C" int tmat_point_fom(tmat_ctx* ctx, const double* pos, int64_t N, doubl
   add3_kernel<<<1, 32, 0, ctx->stream>>>(E, (const double2*)se.dev);
   TM_LAUNCHED(ctx);
   if (v_out && N > 0) {
-    adjoint_source_kernel<<<(unsigned)cdiv(N, 64), 64, 0, ctx->stream>>>((const double*)sp.dev, N, k, nmax,
-                                                                         (const double*)sx.dev, E, (double2*)sv.dev);
+    switch (nmax) {
+#define AK(NM) case NM: adjoint_source_kernel<NM><<<(unsigned)cdiv(N, 64), 64, 0, ctx->stream>>>((const double*)sp.dev, N, k, nmax, (const double*)sx.dev, E, (double2*)sv.dev); break;
+      AK(1) AK(2) AK(3) AK(4) AK(5) AK(6)
+#undef AK
+    }
     TM_LAUNCHED(ctx);
   }
   double2* pin = (double2*)ctx->pinned;
@@ -322,6 +413,10 @@ extern "C" int tmat_field_noalloc(void* cuda_stream, const double* pos, int64_t 
   double2* part = nullptr;
   int rc = noalloc_scratch(dev, &part);
   if (rc != TMAT_OK) return rc;
+  if (leg_upload(dev, (cudaStream_t)cuda_stream) != cudaSuccess) {
+    cudaGetLastError();
+    return TMAT_ECUDA;
+  }
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int64_t nchunk = std::min<int64_t>(cdiv(N, 128), std::max<int64_t>(1, 4 * sms / M));
@@ -329,8 +424,7 @@ extern "C" int tmat_field_noalloc(void* cuda_stream, const double* pos, int64_t 
   nchunk = std::max<int64_t>(1, std::min<int64_t>(nchunk, 65535));
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const double k = 2.0 * M_PI * n_bg / wavelength;
-  field_kernel<<<dim3((unsigned)M, (unsigned)nchunk), 128, 0, st>>>(pos, N, k, nmax, (const double2*)s, pts, M, 0,
-                                                                     part);
+  launch_field_n(nmax, dim3((unsigned)M, (unsigned)nchunk), st, pos, N, k, (const double2*)s, pts, M, false, part);
   field_reduce_kernel<<<(unsigned)cdiv(M * 3, 128), 128, 0, st>>>(part, M, (int)nchunk, (double2*)E_out);
   if (cudaGetLastError() != cudaSuccess) return TMAT_ECUDA;
   return TMAT_OK;
