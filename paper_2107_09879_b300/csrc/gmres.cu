@@ -429,10 +429,9 @@ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.
 // column are staged in shared memory by the block, then one thread applies the j
 // rotations in order (the recurrence is serial) and writes the column back to
 // H[r][.][j] in global memory (so the restart length is not bounded by registers).
-__global__ void givens_kernel(GState s, int R, int j, int m, int maxv) {
-  const int r = blockIdx.x;
-  if (r >= R || !s.active[r]) return;
-  extern __shared__ double2 gsm[];
+// Givens step for column j of RHS r by the calling block (gsm: 2 m + maxv double2 of
+// shared memory); the caller has checked that r is active.
+__device__ void givens_block(GState& s, int r, int j, int m, int maxv, double2* gsm) {
   double2* cs = gsm;          // [j]
   double2* sn = cs + m;       // [j]
   double2* col = sn + m;      // [j + 1]
@@ -483,6 +482,14 @@ __global__ void givens_kernel(GState s, int R, int j, int m, int maxv) {
   __syncthreads();
   double2* hcol = s.H + (int64_t)r * maxv * m + j;  // element i at hcol[i * m]
   for (int i = threadIdx.x; i <= j; i += blockDim.x) hcol[(int64_t)i * m] = col[i];
+  __syncthreads();
+}
+
+__global__ void givens_kernel(GState s, int R, int j, int m, int maxv) {
+  const int r = blockIdx.x;
+  if (r >= R || !s.active[r]) return;
+  extern __shared__ double2 gsm[];
+  givens_block(s, r, j, m, maxv, gsm);
 }
 
 // ---- delayed CGS2 (Arnoldi with the second projection one step late) ----------------
@@ -557,8 +564,11 @@ __global__ void dcgs2_small_kernel(GState s, int j, int m, int maxv, int R, int 
     Hu[(int64_t)j * m + (j - 1)] = make_double2(b1 * nu, 0.0);
     s.nrm[r] = b1 * nu;
   }
-  if (final_only || !(b1 > 0)) return;
   __syncthreads();
+  // rotations of column j-1 (residual estimate, convergence flag)
+  extern __shared__ double2 dsm[];
+  givens_block(s, r, j - 1, m, maxv, dsm);
+  if (final_only || !(b1 > 0) || !s.active[r]) return;
   // zeta = (c - s^H z)/nu with z = D2/b1, c = D2[j]/b1^2
   double zr = 0.0, zi = 0.0;
   for (int k = tid; k < j; k += blockDim.x) {
@@ -821,8 +831,8 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
         // delayed CGS2: the Hessenberg column of iteration j is finalised at iteration j + 1
         float2* V32 = reinterpret_cast<float2*>(V);
         const size_t gsm_bytes = sizeof(double2) * (2 * (size_t)m + maxv);
-        if (gsm_bytes > 48 * 1024)
-          TM_TRY(set_smem_limit(ctx, (const void*)givens_kernel, gsm_bytes));
+        if (gsm_bytes + 17 * 1024 > 48 * 1024)
+          TM_TRY(set_smem_limit(ctx, (const void*)dcgs2_small_kernel, gsm_bytes));
         for (;; ++j) {
           const bool final_only = j == m || st->iterations >= p.max_iter;
           float2* vj = V32 + (int64_t)j * R * n;
@@ -846,12 +856,10 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
             launch_reduce(ctx, part2, dp.ranges, j + 1, maxv, s.D2, s.active, R);
             TM_LAUNCHED(ctx);
           }
-          dcgs2_small_kernel<<<R, 256, 0, ctx->stream>>>(s, j, m, maxv, R, final_only ? 1 : 0);
+          dcgs2_small_kernel<<<R, 256, gsm_bytes, ctx->stream>>>(s, j, m, maxv, R, final_only ? 1 : 0);
           TM_LAUNCHED(ctx);
           bool any = true;
           if (j >= 1) {
-            givens_kernel<<<R, 64, gsm_bytes, ctx->stream>>>(s, R, j - 1, m, maxv);
-            TM_LAUNCHED(ctx);
             int* ipin = (int*)ctx->pinned;
             TM_CUDA(ctx, cudaMemcpyAsync(ipin, s.active, sizeof(int) * R, cudaMemcpyDeviceToHost, ctx->stream));
             TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
