@@ -817,6 +817,10 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
     // first residual = b
     TM_CUDA(ctx, cudaMemcpyAsync(rnorm, bnorm, sizeof(double) * R, cudaMemcpyDeviceToDevice, ctx->stream));
     const C<VR>* rsrc = b;
+    // Convergence is read on the host every sync_every iterations: small systems are
+    // bound by launch and synchronisation latency, and iterations past convergence are
+    // skipped per RHS by the kernels (only the operator application still runs).
+    const int sync_every = (int64_t)R * n < (1 << 20) ? 8 : 1;
     bool all_done = true;
     for (int r = 0; r < R; ++r) all_done = all_done && !hwant[r];
     st->converged = all_done;
@@ -859,7 +863,7 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
           dcgs2_small_kernel<<<R, 256, gsm_bytes, ctx->stream>>>(s, j, m, maxv, R, final_only ? 1 : 0);
           TM_LAUNCHED(ctx);
           bool any = true;
-          if (j >= 1) {
+          if (j >= 1 && (final_only || j % sync_every == 0)) {
             int* ipin = (int*)ctx->pinned;
             TM_CUDA(ctx, cudaMemcpyAsync(ipin, s.active, sizeof(int) * R, cudaMemcpyDeviceToHost, ctx->stream));
             TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -910,6 +914,7 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
         givens_kernel<<<R, 64, gsm_bytes, ctx->stream>>>(s, R, j, m, maxv);
         TM_LAUNCHED(ctx);
         st->iterations++;
+        if ((j + 1) % sync_every != 0 && j + 1 < m && st->iterations < p.max_iter) continue;
         int* ipin = (int*)ctx->pinned;
         TM_CUDA(ctx, cudaMemcpyAsync(ipin, s.active, sizeof(int) * R, cudaMemcpyDeviceToHost, ctx->stream));
         TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
