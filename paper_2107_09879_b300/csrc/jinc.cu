@@ -18,10 +18,27 @@ namespace tmat {
 
 // one block per node: spectrum of the group for every RHS, then the node's coefficients
 // c[q][r][f] = (w_b w_a / 4) sin b cos b e^{-i kz z0} a_f(b, a; A(S_r))
+// e^{i arg}: fp64 sincos, or (FAST) the argument reduced modulo 2 pi in fp64 and sincosf
+// (|error| ~ 1e-7, the accuracy of the complex64 path)
+template <bool FAST>
+__device__ __forceinline__ double2 jinc_phase(double arg) {
+  if (FAST) {
+    const double twopi = 6.283185307179586476925286766559;
+    const float red = (float)(arg - twopi * rint(arg * (1.0 / twopi)));
+    float s, c;
+    sincosf(red, &s, &c);
+    return make_double2(c, s);
+  }
+  double s, c;
+  sincos(arg, &s, &c);
+  return make_double2(c, s);
+}
+
+template <bool FAST>
 __global__ void jinc_node_kernel(const double* __restrict__ beta, const double* __restrict__ wbeta, int n_alpha,
                                  int q0, int nq, double k0, double z0, double cell, const double* __restrict__ src_xy,
                                  const double2* __restrict__ src_A, int64_t S, int R, int nmax,
-                                 double2* __restrict__ c) {
+                                 double2* __restrict__ c, double4* __restrict__ kvec) {
   const int ql = blockIdx.x;
   if (ql >= nq) return;
   const int q = q0 + ql;
@@ -31,14 +48,13 @@ __global__ void jinc_node_kernel(const double* __restrict__ beta, const double* 
   sincos(b, &sb, &cb);
   sincos(a, &sa, &ca);
   const double kx = k0 * sb * ca, ky = k0 * sb * sa, kz = k0 * cb;
+  if (threadIdx.x == 0) kvec[ql] = make_double4(kx, ky, kz, 0.0);
   __shared__ double2 red[TMAT_MAX_RHS][2][64];
   __shared__ double2 Sv[TMAT_MAX_RHS][2];
   double2 acc[TMAT_MAX_RHS][2];
   for (int r = 0; r < R; ++r) acc[r][0] = acc[r][1] = make_double2(0, 0);
   for (int64_t s = threadIdx.x; s < S; s += blockDim.x) {
-    double sn, cs;
-    sincos(-(kx * src_xy[2 * s] + ky * src_xy[2 * s + 1]), &sn, &cs);
-    const double2 ph = make_double2(cs, sn);
+    const double2 ph = jinc_phase<FAST>(-(kx * src_xy[2 * s] + ky * src_xy[2 * s + 1]));
     for (int r = 0; r < R; ++r) {
       cfma(acc[r][0], ph, src_A[((int64_t)r * S + s) * 2]);
       cfma(acc[r][1], ph, src_A[((int64_t)r * S + s) * 2 + 1]);
@@ -95,9 +111,8 @@ __global__ void jinc_node_kernel(const double* __restrict__ beta, const double* 
 constexpr int JN_TILE = 16;
 template <typename Rl, int NT>
 __global__ void __launch_bounds__(256)
-jinc_accum_kernel(const double* __restrict__ beta, int n_alpha, int q0, int nq, double k0,
-                  const double* __restrict__ pos, int64_t N, const double2* __restrict__ c, int R, int P,
-                  double2* __restrict__ a0) {
+jinc_accum_kernel(const double4* __restrict__ kvec, int nq, const double* __restrict__ pos, int64_t N,
+                  const double2* __restrict__ c, int R, int P, double2* __restrict__ a0) {
   constexpr int FMAX = (2 * TMAT_NMAX_MAX * (TMAT_NMAX_MAX + 2) + 15) / 16;
   __shared__ C<Rl> ph[16][NT];
   extern __shared__ __align__(16) unsigned char jsm[];
@@ -120,23 +135,10 @@ jinc_accum_kernel(const double* __restrict__ beta, int n_alpha, int q0, int nq, 
         const int64_t jj = (int64_t)blockIdx.x * 16 + sj2;
         C<Rl> v = mk<Rl>(0, 0);
         if (tq2 < nt && jj < N) {
-          const int q = q0 + t0 + tq2;
-          const int ib = q / n_alpha, ia = q % n_alpha;
-          double sb, cb, sa, ca;
-          sincos(beta[ib], &sb, &cb);
-          sincospi(2.0 * ia / n_alpha, &sa, &ca);
-          const double arg = k0 * (sb * ca * pos[3 * jj] + sb * sa * pos[3 * jj + 1] + cb * pos[3 * jj + 2]);
-          if constexpr (sizeof(Rl) == 8) {
-            double s, cc;
-            sincos(arg, &s, &cc);
-            v = mk<Rl>(cc, s);
-          } else {
-            const double twopi = 6.283185307179586476925286766559;
-            const float red = (float)(arg - twopi * rint(arg * (1.0 / twopi)));
-            float s, cc;
-            sincosf(red, &s, &cc);
-            v = mk<Rl>(cc, s);
-          }
+          const double4 kq = kvec[t0 + tq2];
+          const double arg = kq.x * pos[3 * jj] + kq.y * pos[3 * jj + 1] + kq.z * pos[3 * jj + 2];
+          const double2 e = jinc_phase<sizeof(Rl) == 4>(arg);
+          v = mk<Rl>((Rl)e.x, (Rl)e.y);
         }
         ph[sj2][tq2] = v;
       }
@@ -255,6 +257,8 @@ extern "C" int tmat_incident_jinc(tmat_ctx* ctx, const double* pos, int64_t N, d
   const int CHUNK = 8192;
   double2* c;
   TM_TRY(scratch(ctx, "jn_c", sizeof(double2) * (size_t)CHUNK * R * P, (void**)&c));
+  double4* kv;
+  TM_TRY(scratch(ctx, "jn_k", sizeof(double4) * (size_t)CHUNK, (void**)&kv));
   const bool fp32 = precision == TMAT_PREC_MIXED;
   const int NT = 16;
   const size_t smem = (fp32 ? sizeof(float2) : sizeof(double2)) * (size_t)NT * R * P;
@@ -264,17 +268,21 @@ extern "C" int tmat_incident_jinc(tmat_ctx* ctx, const double* pos, int64_t N, d
   }
   for (int64_t q0 = 0; q0 < NQ; q0 += CHUNK) {
     const int nq = (int)std::min<int64_t>(CHUNK, NQ - q0);
-    jinc_node_kernel<<<nq, 64, 0, ctx->stream>>>(dbeta, dwb, n_alpha, (int)q0, nq, k0, z0, cell, (const double*)ss.dev,
-                                                 (const double2*)sa.dev, S, R, nmax, c);
+    if (fp32)
+      jinc_node_kernel<true><<<nq, 64, 0, ctx->stream>>>(dbeta, dwb, n_alpha, (int)q0, nq, k0, z0, cell,
+                                                         (const double*)ss.dev, (const double2*)sa.dev, S, R, nmax, c,
+                                                         kv);
+    else
+      jinc_node_kernel<false><<<nq, 64, 0, ctx->stream>>>(dbeta, dwb, n_alpha, (int)q0, nq, k0, z0, cell,
+                                                          (const double*)ss.dev, (const double2*)sa.dev, S, R, nmax, c,
+                                                          kv);
     TM_LAUNCHED(ctx);
     const unsigned grid = (unsigned)cdiv(N, 16);
     if (fp32)
-      jinc_accum_kernel<float, 16><<<grid, 256, smem, ctx->stream>>>(dbeta, n_alpha, (int)q0, nq, k0,
-                                                                     (const double*)sp.dev, N, c, R, P,
+      jinc_accum_kernel<float, 16><<<grid, 256, smem, ctx->stream>>>(kv, nq, (const double*)sp.dev, N, c, R, P,
                                                                      (double2*)so.dev);
     else
-      jinc_accum_kernel<double, 16><<<grid, 256, smem, ctx->stream>>>(dbeta, n_alpha, (int)q0, nq, k0,
-                                                                      (const double*)sp.dev, N, c, R, P,
+      jinc_accum_kernel<double, 16><<<grid, 256, smem, ctx->stream>>>(kv, nq, (const double*)sp.dev, N, c, R, P,
                                                                       (double2*)so.dev);
     TM_LAUNCHED(ctx);
   }
