@@ -40,9 +40,15 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 flop x
 HBM_PEAK_GBS = 6451.5  # measured copy bandwidth of the B300s (MEASURED_PEAKS.json)
 
 
-def workload():
-    w = W.lattice_200x200()
-    nx = ny = 200
+def workload(size=200):
+    """The 200 x 200 workload; `size` < 200 takes its lower-left size x size corner (smaller
+    cases of the same structure, for profiler captures)."""
+    w = dict(W.lattice_200x200())
+    nx = ny = size
+    if size != 200:
+        keep = [iy * 200 + ix for iy in range(size) for ix in range(size)]
+        w["pos"] = w["pos"][keep]
+        w["radius"] = w["radius"][keep]
     a = np.zeros((nx * ny, 3))
     a[:, 0] = w["radius"]
     a[:, 1] = w["n_sphere"]
@@ -117,6 +123,12 @@ class ClockSampler:
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands
 # (profiles/lattice_tc2_200x200_nmax4.md); set to None when the kernel changes.
+# DRAM bytes / algorithmic bytes of one captured launch of the HBM-bound kernels, scaled to
+# the timed launches by their algorithmic bytes (traffic grows with the bytes a launch
+# must move): profiles/arnoldi_dcgs2_100x100_nmax4.md, profiles/lattice_fft_200x200_nmax4.md
+TRAFFIC_RATIO = {"arnoldi_dots32": (490.18e6 + 4.41e6) / (62 * 2 * 480000 * 8),
+                 "arnoldi_update32": (468.52e6 + 13.44e6) / (63 * 2 * 480000 * 8),
+                 "lattice_fft_mul32": 700.9e6 / 704.64e6}
 MEASURED_TRAFFIC = {"lattice_tc2_kernel<4,0>": 238.0e6 + 23.0e6,
                     "fft_mul_kernel<float,24,0,2>": 654.4e6 + 46.5e6}  # profiles/lattice_fft_200x200_nmax4.md
 
@@ -140,6 +152,20 @@ def roofline(kern_name, achieved, launches, avg_ms, flop_per_launch):
            "avg_launch_ms": avg_ms, "flop_per_launch": flop_per_launch, "peak_note": note}
     out.update(extra)
     return out
+
+
+def roofline_hbm(hbm, step_total_ms):
+    """The dominant kernel (largest summed time in the timed region) of the HBM-bound ones
+    the library counts algorithmic bytes for: achieved = its bytes / its time."""
+    kind, v = max(hbm.items(), key=lambda kv: kv[1]["total_ms"])
+    achieved = v["bytes"] / (v["total_ms"] * 1e-3) / 1e9
+    ratio = TRAFFIC_RATIO.get(kind)
+    return {"kernel": v["kernel"], "bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+            "frac": achieved / HBM_PEAK_GBS,
+            "traffic": (ratio * v["bytes"] / v["launches"]) if ratio else None,
+            "launches": v["launches"], "avg_launch_ms": v["total_ms"] / v["launches"],
+            "bytes_per_launch": v["bytes"] / v["launches"], "share_of_timed_region": v["total_ms"] / step_total_ms,
+            "peak_note": "STREAM-style copy bandwidth of MEASURED_PEAKS.json (of measured)"}
 
 
 def roofline_fft(nmul, msmul, mul_bytes, napply, avg_apply_ms, flop_per_apply):
@@ -385,7 +411,7 @@ def run_ours(args, rank, world):
     ctx = _lib.Context(dev, None)
     ctx.set_tensor_cores(0 if args.cuda_cores else args.tc_variant)
     ctx.set_lattice_fft(not args.direct)
-    wl = workload()
+    wl = workload(args.size)
     w = wl["w"]
     nmax, cutoff = w["nmax"], w["cutoff"]
     N, R, P = len(wl["pos"]), 2, 48
@@ -445,6 +471,14 @@ def run_ours(args, rank, world):
         if n32:
             break
     nmul, msmul = ctx.kernel_time("lattice_fft_mul32")
+    hbm_kinds = {"arnoldi_dots32": "dots32_kernel<true> (Arnoldi dot pass, two targets)",
+                 "arnoldi_update32": "dcgs2_update_kernel (Arnoldi update pass, two outputs)",
+                 "lattice_fft_mul32": "fft_mul_kernel<float,24,0,2> (per-frequency block products)"}
+    hbm = {}
+    for kind, name in hbm_kinds.items():
+        nk, msk = ctx.kernel_time(kind)
+        if nk:
+            hbm[kind] = {"kernel": name, "launches": nk, "total_ms": msk, "bytes": ctx.kernel_bytes(kind)}
     res_kinds = [("lattice_apply_fft64", "FFT convolution, complex128 (lattice_fft.cu)"),
                  ("lattice_apply_oz", "lattice_oz_kernel<4,0> (tcgen05 bf16 slices, exact group sums, fp64-class)"),
                  ("lattice_apply_fp64", "lattice_apply_kernel<double,4,2,0> (FP64 CUDA cores)")]
@@ -475,7 +509,7 @@ def run_ours(args, rank, world):
     # max over ranks
     t_local = max_over_ranks(total_ms, world, "cuda")
     value = replica_throughput(world, args.steps, t_local)
-    pairs = pairs_within(200, 200, int(round(cutoff / PITCH)))
+    pairs = pairs_within(wl["nx"], wl["ny"], int(round(cutoff / PITCH)))
     flop_per_launch = 8.0 * (P * P / 2) * pairs * R  # nonzero complex MACs x 8 flop, both RHS per launch
     avg32 = ms32 / max(n32, 1)
     achieved = flop_per_launch / (avg32 * 1e-3) / 1e12 if n32 else None
@@ -486,14 +520,16 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64 apply / f64 refinement", "data": "synthetic",
-        "config": {"workload": "lattice_200x200_nmax4_cutoff8_2rhs_mixed", "spheres": N, "nmax": nmax, "P": P,
+        "config": {"workload": f"lattice_{wl['nx']}x{wl['ny']}_nmax4_cutoff8_2rhs_mixed", "spheres": N, "nmax": nmax, "P": P,
                    "rhs": R, "cutoff_wavelengths": cutoff, "coupling_window": "raised cosine over [0, cutoff] (taper = cutoff)", "tol": TOL, "restart": 300, "path": "lattice (block per offset)",
                    "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before every step"},
         "p50_ms": per_step[len(per_step) // 2], "p99_ms": per_step[min(len(per_step) - 1, int(0.99 * len(per_step)))],
         "gmres_iterations_per_solve": statistics.mean(it), "refinements_per_solve": statistics.mean(ref),
         "tmatvec_gflops": (flop_per_launch / (avg32 * 1e-3) / 1e9) if n32 else None,
-        "roofline": (roofline_fft(nmul, msmul, mul_bytes, n32, avg32, flop_per_launch) if nmul else
+        "roofline": (roofline_hbm(hbm, total_ms) if hbm else
                      roofline(kern_name, achieved, n32, avg32, flop_per_launch)),
+        "hbm_kernels": {k: dict(v, achieved_gbs=v["bytes"] / (v["total_ms"] * 1e-3) / 1e9,
+                                frac=v["bytes"] / (v["total_ms"] * 1e-3) / 1e9 / HBM_PEAK_GBS) for k, v in hbm.items()},
         "operator_apply": {"path": kern_name, "launches": n32, "avg_ms": avg32,
                            "direct_sum_equivalent_tflops": achieved},
         "fp64_residual_kernel": res_kernel, "fp64_residual_launches": n64,
@@ -582,6 +618,8 @@ def main():
     ap.add_argument("--kernel-only", action="store_true", help="time the dominant kernel alone (for ncu captures)")
     ap.add_argument("--kernel-precision", type=int, default=1, help="1: complex64 apply, 0: complex128 apply, 2: fp64-class tensor-core apply")
     ap.add_argument("--cuda-cores", action="store_true", help="complex64 apply on CUDA cores instead of tcgen05")
+    ap.add_argument("--size", type=int, default=200,
+                    help="lattice side (200: the benchmark; smaller: its corner, for profiler captures)")
     ap.add_argument("--direct", action="store_true",
                     help="lattice operator by the direct block-Toeplitz kernels instead of FFT convolution")
     ap.add_argument("--tc-variant", type=int, default=1, choices=[1, 2],

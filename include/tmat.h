@@ -153,6 +153,11 @@ int tmat_ctx_set_lattice_fft(tmat_ctx* ctx, int enable);
  * "lattice_apply_tc" (gather), "lattice_apply_oz" (TMAT_PREC_FP64_TC apply). */
 int tmat_ctx_set_tensor_cores(tmat_ctx* ctx, int enable);
 int tmat_ctx_kernel_time(tmat_ctx* ctx, const char* kind, int64_t* launches, double* total_ms);
+/* Algorithmic bytes (what the launches of `kind` must read and write: operands, basis
+ * vectors, spectra; not cache re-reads) summed over the timed launches. Kinds with a
+ * byte count: "arnoldi_dots32", "arnoldi_update32" (the complex64 Arnoldi passes),
+ * "lattice_fft_mul32", "lattice_fft_mul64". */
+int tmat_ctx_kernel_bytes(tmat_ctx* ctx, const char* kind, double* bytes);
 
 /* ---- geometry (integer, bit-exact) -------------------------------------- */
 

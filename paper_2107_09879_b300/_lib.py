@@ -68,6 +68,7 @@ _SIGS = {
     "tmat_ctx_set_tensor_cores": [_vp, _int],
     "tmat_ctx_set_lattice_fft": [_vp, _int],
     "tmat_ctx_kernel_time": [_vp, ct.c_char_p, ct.POINTER(_i64), ct.POINTER(_d)],
+    "tmat_ctx_kernel_bytes": [_vp, ct.c_char_p, ct.POINTER(_d)],
     "tmat_neighbors": [_vp, _vp, _i64, _d, _vp, _vp, ct.POINTER(_i64)],
     "tmat_subregions": [_vp, _i64, _i64, _i64, _i64, _i64, _vp, _vp, _vp, _vp, ct.POINTER(_i64), ct.POINTER(_i64)],
     "tmat_build": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp],
@@ -168,6 +169,11 @@ class Context:
         n, ms = ct.c_int64(), ct.c_double()
         self.check(lib.tmat_ctx_kernel_time(self.h, kind.encode(), ct.byref(n), ct.byref(ms)))
         return n.value, ms.value
+
+    def kernel_bytes(self, kind):
+        b = ct.c_double()
+        self.check(lib.tmat_ctx_kernel_bytes(self.h, kind.encode(), ct.byref(b)))
+        return b.value
 
     def close(self):
         if getattr(self, "h", None):

@@ -57,12 +57,13 @@ cudaEvent_t timing_begin(tmat_ctx* ctx) {
   return e;
 }
 
-void timing_end(tmat_ctx* ctx, const char* kind, cudaEvent_t start) {
+void timing_end(tmat_ctx* ctx, const char* kind, cudaEvent_t start, double bytes) {
   if (!start) return;
   cudaEvent_t e = pooled_event(ctx);
   if (!e) return;
   cudaEventRecord(e, ctx->stream);
   ctx->timed[kind].push_back({start, e});
+  ctx->timed_bytes[kind] += bytes;
 }
 
 int set_smem_limit(tmat_ctx* ctx, const void* func, size_t bytes) {
@@ -127,6 +128,7 @@ static void drop_events(tmat_ctx* ctx, bool destroy_all = false) {
       ctx->event_pool.push_back(pr.second);
     }
   ctx->timed.clear();
+  ctx->timed_bytes.clear();
   if (destroy_all) {
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     ctx->event_pool.clear();
@@ -195,6 +197,13 @@ extern "C" int tmat_ctx_set_timing(tmat_ctx* ctx, int enable) {
   cudaStreamSynchronize(ctx->stream);
   drop_events(ctx);
   ctx->timing = enable != 0;
+  return TMAT_OK;
+}
+
+extern "C" int tmat_ctx_kernel_bytes(tmat_ctx* ctx, const char* kind, double* bytes) {
+  if (!ctx || !kind || !bytes) return TMAT_EINVAL;
+  auto it = ctx->timed_bytes.find(kind);
+  *bytes = it == ctx->timed_bytes.end() ? 0.0 : it->second;
   return TMAT_OK;
 }
 

@@ -846,6 +846,7 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
             st->iterations++;
           }
           const Dots32Plan dp = dots32_plan(n, j + 1, ctx->num_sms, R);
+          cudaEvent_t ev_d = timing_begin(ctx);
           if (final_only) {
             dots32_kernel<false><<<dim3(dp.blocks, R), 256, 0, ctx->stream>>>(V32, (int64_t)R * n, j + 1, vj, n, rs,
                                                                                part, maxv, dp.groups, dp.ranges, s.active);
@@ -854,6 +855,8 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
                 V32, (int64_t)R * n, j + 1, vj, n, rs, part, maxv, dp.groups, dp.ranges, s.active, w, part2);
           }
           TM_LAUNCHED(ctx);
+          // reads the j + 1 basis slots (the pending vector is slot j) and w
+          timing_end(ctx, "arnoldi_dots32", ev_d, 8.0 * R * n * (j + 1 + (final_only ? 0 : 1)));
           launch_reduce(ctx, part, dp.ranges, j + 1, maxv, s.D1, s.active, R);
           TM_LAUNCHED(ctx);
           if (!final_only) {
@@ -871,9 +874,12 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
             for (int r = 0; r < R; ++r) any = any || ipin[r];
           }
           if (final_only || !any) break;
+          cudaEvent_t ev_u = timing_begin(ctx);
           dcgs2_update_kernel<<<dim3(g1, R), 256, sizeof(float2) * (2 * (size_t)j + 2), ctx->stream>>>(
               V32, (int64_t)R * n, j, s, maxv, w, n, rs);
           TM_LAUNCHED(ctx);
+          // reads slots 0..j and w, writes slot j (j > 0) and w
+          timing_end(ctx, "arnoldi_update32", ev_u, 8.0 * R * n * (j + 2 + (j > 0 ? 1 : 0) + 1));
         }
         // columns 0..j-1 are final
       } else

@@ -60,6 +60,7 @@ struct tmat_ctx {
   bool timing = false;
   std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> timed;
   std::vector<cudaEvent_t> event_pool;          // recycled timing events
+  std::map<std::string, double> timed_bytes;    // algorithmic bytes of the timed launches
   std::map<const void*, int> smem_attr;         // dynamic shared memory limit set per kernel
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -99,7 +100,8 @@ int cuda_fail(tmat_ctx* ctx, cudaError_t e, const char* what, const char* file, 
 // Kernel timing: returns a start event (or nullptr when timing is off) and
 // records the matching stop event after the launch.
 cudaEvent_t timing_begin(tmat_ctx* ctx);
-void timing_end(tmat_ctx* ctx, const char* kind, cudaEvent_t start);
+// bytes: the launch's algorithmic traffic (what it must read and write), summed per kind
+void timing_end(tmat_ctx* ctx, const char* kind, cudaEvent_t start, double bytes = 0.0);
 
 // Grow-only scratch owned by the context, keyed by name.
 int scratch(tmat_ctx* ctx, const char* name, size_t bytes, void** out);

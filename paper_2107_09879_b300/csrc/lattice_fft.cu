@@ -374,7 +374,9 @@ static int fft_apply_t(tmat_ctx* ctx, const LatOp& a, const void* xv, void* yv, 
     cudaEvent_t ev = timing_begin(ctx);
     fft_mul_kernel<R, L, MODE, RC><<<g, 128, 0, ctx->stream>>>((const C<R>*)a.fft_Bhat, Xh, Yh, Mx, My, R_);
     TM_LAUNCHED(ctx);
-    timing_end(ctx, sizeof(R) == 4 ? "lattice_fft_mul32" : "lattice_fft_mul64", ev);
+    // the block spectra once, the RHS spectra in and out
+    const double mul_bytes = (double)sizeof(C<R>) * F * (2.0 * L * L + 2.0 * nb);
+    timing_end(ctx, sizeof(R) == 4 ? "lattice_fft_mul32" : "lattice_fft_mul64", ev, mul_bytes);
   }
   C<R>* Yc = Xh;  // X^ is no longer needed
   TM_TRY(fft2_inverse<R>(ctx, Yh, nx, ny, Mx, My, nb, w1, Yc, tw));
