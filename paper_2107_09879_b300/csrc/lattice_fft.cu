@@ -18,9 +18,12 @@
 //   I2      inverse FFT along ky, keep iy < ny, write transposed -> T3[.][iy][kx]
 //   I1      inverse FFT along kx, keep ix < nx               -> Yc[.][iy][ix]
 //   extract y[r][site][u] = x - T (Yc / (Mx My)), x - Yc / (Mx My) or Yc / (Mx My)
-// B^ is built once per operator by the same F1/F2 passes from the blocks scattered to
-// grid position -o. The FFT is an iterative radix-2 decimation in time in shared memory
-// (Cooley and Tukey, Math. Comp. 19 (1965)) with fp64 twiddles (cast for complex64).
+// B^ is built once per operator by the same F1/F2 passes from the blocks scattered to a
+// compact (2 CY + 1) x (2 CX + 1) grid at (CX - dx, CY - dy), i.e. position -o shifted (the
+// shift is a phase factor, removed after the transform); only the rows that hold offsets
+// are transformed along x. The FFT is an iterative decimation in time in shared memory
+// (Cooley and Tukey, Math. Comp. 19 (1965)), radix-4 stages (one radix-2 stage for odd
+// powers of two), fp64 twiddles (cast for complex64).
 #include <cmath>
 #include <vector>
 
@@ -227,19 +230,23 @@ __global__ void fft_extract_kernel(const C<R>* __restrict__ Yc, const C<R>* __re
   }
 }
 
-// Bgrid[(c*L + u)*L + u'][iy][ix] = B_o[c][u][u'] at (ix, iy) = (-dx mod Mx, -dy mod My);
-// BT[o][c][u'][u] holds the blocks transposed (row stride LP).
+// Bgrid[(c*L + u)*L + u'][iy][ix] = B_o[c][u][u'] (BT[o][c][u'][u] holds the blocks
+// transposed, row stride LP) on compact grids: offset o goes to (CX - dx, CY - dy) of a
+// (2 CY + 1) x (2 CX + 1) grid, i.e. b(-o) shifted by (CX, CY); the transforms zero-pad it
+// to Mx x My and the shift becomes the phase e^{-2 pi i (kx CX / Mx + ky CY / My)}, which
+// the block product removes per frequency.
 template <typename R>
 __global__ void fft_scatter_blocks_kernel(const C<R>* __restrict__ BT, const int2* __restrict__ off, int K, int L, int LP,
-                                          int Mx, int My, C<R>* __restrict__ Bgrid) {
+                                          int CX, int CY, C<R>* __restrict__ Bgrid) {
   const int o = blockIdx.x;
   if (o >= K) return;
   const int2 d = off[o];
-  const int ix = ((-d.x) % Mx + Mx) % Mx, iy = ((-d.y) % My + My) % My;
-  const int64_t F = (int64_t)Mx * My;
+  const int gw = 2 * CX + 1, gh = 2 * CY + 1;
+  const int ix = CX - d.x, iy = CY - d.y;
+  const int64_t G = (int64_t)gw * gh;
   for (int e = threadIdx.x; e < 2 * L * L; e += blockDim.x) {
     const int c = e / (L * L), u = (e / L) % L, up = e % L;
-    Bgrid[(int64_t)e * F + (int64_t)iy * Mx + ix] = BT[(((int64_t)o * 2 + c) * L + up) * LP + u];
+    Bgrid[(int64_t)e * G + (int64_t)iy * gw + ix] = BT[(((int64_t)o * 2 + c) * L + up) * LP + u];
   }
 }
 
@@ -249,16 +256,27 @@ __global__ void fft_scatter_blocks_kernel(const C<R>* __restrict__ BT, const int
 template <typename R, int L, int MODE, int RC>
 __global__ void __launch_bounds__(128)
 fft_mul_kernel(const C<R>* __restrict__ Bh, const C<R>* __restrict__ Xh, C<R>* __restrict__ Yh, int Mx, int My,
-               int R_) {
+               int R_, int CX, int CY) {
   constexpr int P = 2 * L;
   const int64_t F = (int64_t)Mx * My;
   const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int c = blockIdx.y;
   if (f >= F) return;
   int64_t fb = f;
+  int kx = (int)(f / My), ky = (int)(f % My);
   if (MODE == 1) {
-    const int kx = (int)(f / My), ky = (int)(f % My);
-    fb = (int64_t)((Mx - kx) % Mx) * My + (My - ky) % My;
+    kx = (Mx - kx) % Mx;
+    ky = (My - ky) % My;
+    fb = (int64_t)kx * My + ky;
+  }
+  // the stored spectra carry e^{-2 pi i (kx CX / Mx + ky CY / My)} of the compact grids:
+  // undo it (the fraction of a turn is reduced exactly in integers)
+  C<R> ph;
+  {
+    const int64_t num = ((int64_t)kx * CX * My + (int64_t)ky * CY * Mx) % F;
+    double sn, cs;
+    sincospi(2.0 * (double)num / (double)F, &sn, &cs);
+    ph = mk<R>((R)cs, (R)sn);
   }
   for (int r0 = 0; r0 < R_; r0 += RC) {
     C<R> xv[RC][L];
@@ -281,7 +299,7 @@ fft_mul_kernel(const C<R>* __restrict__ Bh, const C<R>* __restrict__ Xh, C<R>* _
       }
 #pragma unroll
       for (int q = 0; q < RC; ++q)
-        if (r0 + q < R_) Yh[((int64_t)(r0 + q) * P + c * L + u) * F + f] = acc[q];
+        if (r0 + q < R_) Yh[((int64_t)(r0 + q) * P + c * L + u) * F + f] = cmul(acc[q], ph);
     }
   }
 }
@@ -323,14 +341,17 @@ static int fft_prepare_t(tmat_ctx* ctx, LatOp* a, const char* name) {
   TM_TRY(fft_twiddles(ctx, &tw));
   C<R>*Bh, *grid, *tmp;
   TM_TRY(scratch(ctx, name, sizeof(C<R>) * ncomp * F, (void**)&Bh));
-  // staging: the scattered grids (ny x nx would lose the wrapped offsets, so the full
-  // My x Mx grid is transformed) and the transposed intermediate
-  TM_TRY(scratch(ctx, "fft_bgrid", sizeof(C<R>) * ncomp * F, (void**)&grid));
-  TM_TRY(scratch(ctx, "fft_btmp", sizeof(C<R>) * ncomp * F, (void**)&tmp));
-  TM_CUDA(ctx, cudaMemsetAsync(grid, 0, sizeof(C<R>) * ncomp * F, ctx->stream));
-  fft_scatter_blocks_kernel<R><<<a->K, 256, 0, ctx->stream>>>((const C<R>*)a->BT, a->off, a->K, L, a->LP, Mx, My, grid);
+  // staging: the compact (2 CY + 1) x (2 CX + 1) grids of the offsets and the transposed
+  // intermediate Mx x (2 CY + 1); only these rows carry data, so only they are transformed
+  const int gw = 2 * a->CX + 1, gh = 2 * a->CY + 1;
+  TM_TRY(scratch(ctx, "fft_bgrid", sizeof(C<R>) * ncomp * gw * gh, (void**)&grid));
+  TM_TRY(scratch(ctx, "fft_btmp", sizeof(C<R>) * ncomp * Mx * gh, (void**)&tmp));
+  TM_CUDA(ctx, cudaMemsetAsync(grid, 0, sizeof(C<R>) * ncomp * gw * gh, ctx->stream));
+  fft_scatter_blocks_kernel<R><<<a->K, 256, 0, ctx->stream>>>((const C<R>*)a->BT, a->off, a->K, L, a->LP, a->CX, a->CY,
+                                                              grid);
   TM_LAUNCHED(ctx);
-  TM_TRY(fft2_forward<R>(ctx, grid, Mx, My, Mx, My, ncomp, tmp, Bh, tw));
+  // stored without the shift phase; the block product applies it per frequency
+  TM_TRY(fft2_forward<R>(ctx, grid, gw, gh, Mx, My, ncomp, tmp, Bh, tw));
   a->fft_Mx = Mx;
   a->fft_My = My;
   a->fft_Bhat = Bh;
@@ -372,7 +393,7 @@ static int fft_apply_t(tmat_ctx* ctx, const LatOp& a, const void* xv, void* yv, 
     constexpr int RC = (sizeof(R) == 4 && L <= 24) ? 2 : 1;
     dim3 g((unsigned)cdiv(F, 128), 2);
     cudaEvent_t ev = timing_begin(ctx);
-    fft_mul_kernel<R, L, MODE, RC><<<g, 128, 0, ctx->stream>>>((const C<R>*)a.fft_Bhat, Xh, Yh, Mx, My, R_);
+    fft_mul_kernel<R, L, MODE, RC><<<g, 128, 0, ctx->stream>>>((const C<R>*)a.fft_Bhat, Xh, Yh, Mx, My, R_, a.CX, a.CY);
     TM_LAUNCHED(ctx);
     // the block spectra once, the RHS spectra in and out
     const double mul_bytes = (double)sizeof(C<R>) * F * (2.0 * L * L + 2.0 * nb);
