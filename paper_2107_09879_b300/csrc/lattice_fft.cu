@@ -22,8 +22,8 @@
 // compact (2 CY + 1) x (2 CX + 1) grid at (CX - dx, CY - dy), i.e. position -o shifted (the
 // shift is a phase factor, removed after the transform); only the rows that hold offsets
 // are transformed along x. The FFT is an iterative decimation in time in shared memory
-// (Cooley and Tukey, Math. Comp. 19 (1965)), radix-4 stages (one radix-2 stage for odd
-// powers of two), fp64 twiddles (cast for complex64).
+// (Cooley and Tukey, Math. Comp. 19 (1965)): radix-16 register passes, then radix 4 (one
+// radix-2 stage first for odd powers of two), fp64 twiddles (cast for complex64).
 #include <cmath>
 #include <vector>
 
@@ -35,6 +35,7 @@ namespace tmat {
 constexpr int FFT_MAXLEN = 1024;     // longest row transform
 constexpr int FFT_THREADS = 256;
 constexpr int FFT_SMEM_POINTS = 8192;  // complex points staged per block
+constexpr int FFT_LOAD_BATCH = 8;
 
 static int ilog2(int v) {
   int l = 0;
@@ -74,35 +75,30 @@ static int fft_twiddles(tmat_ctx* ctx, const double2** out) {
 // different banks
 __device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
 
-template <typename R, bool TOUT>
-__global__ void __launch_bounds__(FFT_THREADS)
-fft_rows_kernel(const C<R>* __restrict__ in, int64_t in_batch_stride, int in_pitch, int cin, int nrows,
-                C<R>* __restrict__ out, int64_t out_batch_stride, int out_pitch, int cout, int lg, int lgrb, int dir,
-                const double2* __restrict__ tw) {
-  extern __shared__ __align__(16) unsigned char fsm[];
-  const int len = 1 << lg, rb = 1 << lgrb, pitch = len + (len >> 4) + 1;
-  C<R>* a = reinterpret_cast<C<R>*>(fsm);
-  C<R>* ws = a + (size_t)rb * pitch;  // [len / 2]
-  const int b = blockIdx.y;
-  const int row0 = blockIdx.x << lgrb;
-  const int nr = min(rb, nrows - row0);
-  const C<R>* src = in + (int64_t)b * in_batch_stride + (int64_t)row0 * in_pitch;
-  for (int j = threadIdx.x; j < (len >> 1); j += blockDim.x) {
-    const double2 w64 = tw[j << (10 - lg)];  // exp(-2 pi i j / len); FFT_MAXLEN = 2^10
-    ws[j] = mk<R>((R)w64.x, (R)(dir < 0 ? w64.y : -w64.y));
+// Twiddle table by stage: wt[2^t - 1 + j] = W_{2^(t+1)}^j (j < 2^t, t < lg; W = e^{-+2 pi i/n}
+// for dir -/+), len - 1 entries, so that the threads of one stage read consecutive entries.
+template <typename R>
+__device__ __forceinline__ void fft_stage_twiddles(C<R>* wt, int lg, int dir, const double2* __restrict__ tw) {
+  for (int e = threadIdx.x; e < (1 << lg) - 1; e += blockDim.x) {
+    const int t = 31 - __clz(e + 1), j = e + 1 - (1 << t);
+    const double2 w64 = tw[j << (9 - t)];  // exp(-2 pi i j / 2^(t+1)); FFT_MAXLEN = 2^10
+    wt[e] = mk<R>((R)w64.x, (R)(dir < 0 ? w64.y : -w64.y));
   }
-  // load with bit reversal (zero-padded)
-  for (int e = threadIdx.x; e < (rb << lg); e += blockDim.x) {
-    const int rr = e >> lg, cc = e & (len - 1);
-    C<R> v = mk<R>((R)0, (R)0);
-    if (rr < nr && cc < cin) v = src[(int64_t)rr * in_pitch + cc];
-    const int rev = lg ? (int)(__brev((unsigned)cc) >> (32 - lg)) : 0;
-    a[rr * pitch + fpad(rev)] = v;
-  }
-  __syncthreads();
+}
+
+// The butterfly passes of a decimation-in-time transform of nrows rows of length 2^lg
+// held in shared memory in bit-reversed order (row stride pitch, element i at fpad(i)),
+// stage twiddles wt of the direction dir. Stages go four at a time through registers
+// (radix 16: each thread loads 16 elements i0 + j 2^s, runs stages s..s+3 among them and
+// stores them back), then two at a time (radix 4), with one radix-2 stage first for odd
+// lg: a length-256 row makes two round trips through shared memory instead of four.
+// Ends with a block barrier.
+template <typename R>
+__device__ __forceinline__ void fft_smem_passes(C<R>* a, int pitch, int nrows, int lg, const C<R>* wt, int dir) {
+  const int len = 1 << lg;
   int s = 0;
   if (lg & 1) {  // one radix-2 stage (twiddle 1) when the length is an odd power of two
-    for (int e = threadIdx.x; e < (rb << (lg - 1)); e += blockDim.x) {
+    for (int e = threadIdx.x; e < (nrows << (lg - 1)); e += blockDim.x) {
       const int rr = e >> (lg - 1), p = e & ((len >> 1) - 1);
       C<R>* row = a + rr * pitch;
       const int q0 = fpad(2 * p), q1 = fpad(2 * p + 1);
@@ -113,17 +109,48 @@ fft_rows_kernel(const C<R>* __restrict__ in, int64_t in_batch_stride, int in_pit
     __syncthreads();
     s = 1;
   }
+  for (; s + 3 < lg; s += 4) {
+    const int lgg = lg - 4;  // groups of 16 per row
+    for (int e = threadIdx.x; e < (nrows << lgg); e += blockDim.x) {
+      const int rr = e >> lgg, g = e & ((1 << lgg) - 1);
+      const int lo = g & ((1 << s) - 1);
+      const int i0 = ((g >> s) << (s + 4)) + lo;
+      C<R>* row = a + rr * pitch;
+      C<R> v[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = row[fpad(i0 + (j << s))];
+#pragma unroll
+      for (int tt = 0; tt < 4; ++tt) {
+        const int h = 1 << tt;
+        // stage t = s + tt: element i0 + (j << s) pairs with j + h; twiddle W_{2^(t+1)}^(i mod 2^t)
+        const C<R>* wst = wt + ((1 << (s + tt)) - 1) + lo;
+#pragma unroll
+        for (int m = 0; m < h; ++m) {
+          const C<R> w = wst[m << s];
+#pragma unroll
+          for (int blk = 0; blk < 16; blk += 2 * h) {
+            const C<R> t = cmul(w, v[blk + m + h]);
+            v[blk + m + h] = csub(v[blk + m], t);
+            v[blk + m] = cadd(v[blk + m], t);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) row[fpad(i0 + (j << s))] = v[j];
+    }
+    __syncthreads();
+  }
   // radix-4: the radix-2 stages s and s + 1 fused in registers (twiddles W_{2h}^j for the
   // first, W_{4h}^j and W_{4h}^{j+h} = W_{4h}^j (-/+ i) for the second)
   for (; s + 1 < lg; s += 2) {
     const int half = 1 << s;
-    for (int e = threadIdx.x; e < (rb << (lg - 2)); e += blockDim.x) {
+    for (int e = threadIdx.x; e < (nrows << (lg - 2)); e += blockDim.x) {
       const int rr = e >> (lg - 2), p = e & ((len >> 2) - 1);
       const int j = p & (half - 1);
       const int i0 = ((p >> s) << (s + 2)) + j;
       C<R>* row = a + rr * pitch;
       const int q0 = fpad(i0), q1 = fpad(i0 + half), q2 = fpad(i0 + 2 * half), q3 = fpad(i0 + 3 * half);
-      const C<R> w1 = ws[j << (lg - 1 - s)], w2 = ws[j << (lg - 2 - s)];
+      const C<R> w1 = wt[half - 1 + j], w2 = wt[2 * half - 1 + j];
       const C<R> a0 = row[q0], a1 = cmul(w1, row[q1]);
       const C<R> a2 = row[q2], a3 = cmul(w1, row[q3]);
       const C<R> b0 = cadd(a0, a1), b1 = csub(a0, a1), b2 = cadd(a2, a3), b3 = csub(a2, a3);
@@ -138,6 +165,62 @@ fft_rows_kernel(const C<R>* __restrict__ in, int64_t in_batch_stride, int in_pit
     }
     __syncthreads();
   }
+}
+
+template <typename R, bool TOUT, bool TIN>
+__global__ void __launch_bounds__(FFT_THREADS)
+fft_rows_kernel(const C<R>* __restrict__ in, int64_t in_batch_stride, int in_pitch, int cin, int nrows,
+                C<R>* __restrict__ out, int64_t out_batch_stride, int out_pitch, int cout, int lg, int lgrb, int dir,
+                const double2* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  const int len = 1 << lg, rb = 1 << lgrb, pitch = len + (len >> 4) + 1;
+  C<R>* a = reinterpret_cast<C<R>*>(fsm);
+  C<R>* ws = a + (size_t)rb * pitch;  // [len - 1] stage twiddles
+  const int b = blockIdx.y;
+  const int row0 = blockIdx.x << lgrb;
+  const int nr = min(rb, nrows - row0);
+  fft_stage_twiddles<R>(ws, lg, dir, tw);
+  // load with bit reversal (zero-padded)
+  // FFT_LOAD_BATCH independent loads per thread are issued before their shared-memory
+  // stores, so the load latency is paid once per batch rather than once per element
+  if (TIN) {
+    // in[k][row0 + rr] (transposed input): consecutive threads take consecutive rows of one k
+    const C<R>* src = in + (int64_t)b * in_batch_stride + row0;
+    const int rr = threadIdx.x & (rb - 1), step = blockDim.x >> lgrb;
+    for (int c0 = threadIdx.x >> lgrb; c0 < len; c0 += step * FFT_LOAD_BATCH) {
+      C<R> v[FFT_LOAD_BATCH];
+#pragma unroll
+      for (int t = 0; t < FFT_LOAD_BATCH; ++t) {
+        const int cc = c0 + t * step;
+        v[t] = (rr < nr && cc < cin) ? src[(int64_t)cc * in_pitch + rr] : mk<R>((R)0, (R)0);
+      }
+#pragma unroll
+      for (int t = 0; t < FFT_LOAD_BATCH; ++t) {
+        const int cc = c0 + t * step;
+        if (cc < len) a[rr * pitch + fpad(lg ? (int)(__brev((unsigned)cc) >> (32 - lg)) : 0)] = v[t];
+      }
+    }
+  } else {
+    const C<R>* src = in + (int64_t)b * in_batch_stride + (int64_t)row0 * in_pitch;
+    const int total = rb << lg;
+    for (int e0 = threadIdx.x; e0 < total; e0 += blockDim.x * FFT_LOAD_BATCH) {
+      C<R> v[FFT_LOAD_BATCH];
+#pragma unroll
+      for (int t = 0; t < FFT_LOAD_BATCH; ++t) {
+        const int e = e0 + t * (int)blockDim.x;
+        const int rr = e >> lg, cc = e & (len - 1);
+        v[t] = (e < total && rr < nr && cc < cin) ? src[(int64_t)rr * in_pitch + cc] : mk<R>((R)0, (R)0);
+      }
+#pragma unroll
+      for (int t = 0; t < FFT_LOAD_BATCH; ++t) {
+        const int e = e0 + t * (int)blockDim.x;
+        const int rr = e >> lg, cc = e & (len - 1);
+        if (e < total) a[rr * pitch + fpad(lg ? (int)(__brev((unsigned)cc) >> (32 - lg)) : 0)] = v[t];
+      }
+    }
+  }
+  __syncthreads();
+  fft_smem_passes<R>(a, pitch, rb, lg, ws, dir);
   C<R>* dst = out + (int64_t)b * out_batch_stride;
   if (TOUT) {
     // out[k][row0 + rr]: consecutive threads take consecutive rows of one k
@@ -150,14 +233,14 @@ fft_rows_kernel(const C<R>* __restrict__ in, int64_t in_batch_stride, int in_pit
   }
 }
 
-template <typename R, bool TOUT>
+template <typename R, bool TOUT, bool TIN = false>
 static int fft_rows(tmat_ctx* ctx, const C<R>* in, int64_t in_bs, int in_pitch, int cin, int nrows, C<R>* out,
                     int64_t out_bs, int out_pitch, int cout, int len, int64_t nbatch, int dir, const double2* tw) {
   const int lg = ilog2(len);
-  int lgrb = ilog2(std::max(1, std::min(TOUT ? 32 : 8, FFT_SMEM_POINTS / len)));
+  int lgrb = ilog2(std::max(1, std::min((TOUT || TIN) ? 32 : 8, FFT_SMEM_POINTS / len)));
   const int rb = 1 << lgrb;
-  const size_t smem = sizeof(C<R>) * ((size_t)rb * (len + (len >> 4) + 1) + len / 2 + 1);
-  auto kern = fft_rows_kernel<R, TOUT>;
+  const size_t smem = sizeof(C<R>) * ((size_t)rb * (len + (len >> 4) + 1) + len);
+  auto kern = fft_rows_kernel<R, TOUT, TIN>;
   if (smem > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, smem));
   for (int64_t b0 = 0; b0 < nbatch; b0 += 65535) {
     const int nb = (int)std::min<int64_t>(65535, nbatch - b0);

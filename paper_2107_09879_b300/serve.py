@@ -43,11 +43,12 @@ def request_bytes(side, nmax, R=1, restart=60, cutoff_sites=16):
 
 class Server:
     def __init__(self, slots=4, mem_budget=8 << 30, device=0, tol=1e-7, cutoff=8.0, restart=60, z0=-1.0,
-                 detector_height=5.0):
+                 detector_height=5.0, inner_tol=1e-4):
         import torch
         self.slots = slots
         self.mem_budget = mem_budget
         self.tol, self.cutoff, self.restart, self.z0, self.det_h = tol, cutoff, restart, z0, detector_height
+        self.inner_tol = inner_tol
         self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
         self.ctxs = [_lib.Context(device, ct_stream(s)) for s in self.streams]
         self.pool = [cf.ThreadPoolExecutor(max_workers=1) for _ in range(slots)]
@@ -81,7 +82,7 @@ class Server:
         T = ctx.tmat_build(atoms, w, 1.0, nmax)
         a0 = ctx.tmat_incident_jinc(pos, w, 1.0, nmax, src, A, self.z0, precision=_lib.PREC_MIXED, src_pitch=pitch)
         opts = _lib.make_opts(tol=self.tol, restart=self.restart, max_iter=3000, cutoff=self.cutoff,
-                              taper=self.cutoff, precision=_lib.PREC_MIXED, inner_tol=1e-4, path=_lib.PATH_LATTICE,
+                              taper=self.cutoff, precision=_lib.PREC_MIXED, inner_tol=self.inner_tol, path=_lib.PATH_LATTICE,
                               lattice_nx=side, lattice_ny=side, lattice_pitch=pitch)
         s, info, _, rc = ctx.tmat_solve(pos, w, 1.0, nmax, T, a0, opts)
         c = (side - 1) * pitch / 2
