@@ -335,16 +335,20 @@ __global__ void fft_scatter_blocks_kernel(const C<R>* __restrict__ BT, const int
 
 // Per frequency f and class c: Y^[r][c L + u][f] = sum_u' G[u][u'] X^[r][c L + u'][f] with
 // G = B^[c][u][u'][f] (MODE 0, 2) or B^[c][u'][u][-f] (MODE 1). RC RHS per pass share
-// the B^ loads.
+// the B^ loads. The thread's X^ values sit in its own column of shared memory rather than
+// in registers, so that three blocks fit on an SM and more B^ loads are in flight.
+constexpr int FFT_MUL_THREADS = 128;
 template <typename R, int L, int MODE, int RC>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(FFT_MUL_THREADS, 3)
 fft_mul_kernel(const C<R>* __restrict__ Bh, const C<R>* __restrict__ Xh, C<R>* __restrict__ Yh, int Mx, int My,
                int R_, int CX, int CY) {
-  constexpr int P = 2 * L;
+  constexpr int P = 2 * L, TS = FFT_MUL_THREADS;
+  extern __shared__ __align__(16) unsigned char xsm[];
+  C<R>* xs = reinterpret_cast<C<R>*>(xsm) + threadIdx.x;  // [RC][L][TS]: this thread's column
   const int64_t F = (int64_t)Mx * My;
   const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int c = blockIdx.y;
-  if (f >= F) return;
+  if (f >= F) return;  // no block barrier below
   int64_t fb = f;
   int kx = (int)(f / My), ky = (int)(f % My);
   if (MODE == 1) {
@@ -362,12 +366,12 @@ fft_mul_kernel(const C<R>* __restrict__ Bh, const C<R>* __restrict__ Xh, C<R>* _
     ph = mk<R>((R)cs, (R)sn);
   }
   for (int r0 = 0; r0 < R_; r0 += RC) {
-    C<R> xv[RC][L];
 #pragma unroll
     for (int q = 0; q < RC; ++q)
 #pragma unroll
       for (int up = 0; up < L; ++up)
-        xv[q][up] = (r0 + q < R_) ? Xh[((int64_t)(r0 + q) * P + c * L + up) * F + f] : mk<R>((R)0, (R)0);
+        xs[(q * L + up) * TS] =
+            (r0 + q < R_) ? Xh[((int64_t)(r0 + q) * P + c * L + up) * F + f] : mk<R>((R)0, (R)0);
 #pragma unroll 1
     for (int u = 0; u < L; ++u) {
       C<R> acc[RC];
@@ -378,7 +382,8 @@ fft_mul_kernel(const C<R>* __restrict__ Bh, const C<R>* __restrict__ Xh, C<R>* _
         const int comp = MODE == 1 ? (c * L + up) * L + u : (c * L + u) * L + up;
         const C<R> g = Bh[(int64_t)comp * F + fb];
 #pragma unroll
-        for (int q = 0; q < RC; ++q) cfma(acc[q], g, xv[q][up]);
+        for (int q = 0; q < RC; ++q) cfma(acc[q], g, xs[(q * L + up) * TS]);
+        if ((up & 15) == 15) __syncwarp();  // bounds how far the compiler hoists the loads
       }
 #pragma unroll
       for (int q = 0; q < RC; ++q)
@@ -474,9 +479,12 @@ static int fft_apply_t(tmat_ctx* ctx, const LatOp& a, const void* xv, void* yv, 
   TM_TRY(fft2_forward<R>(ctx, grid, nx, ny, Mx, My, nb, w1, Xh, tw));
   {
     constexpr int RC = (sizeof(R) == 4 && L <= 24) ? 2 : 1;
-    dim3 g((unsigned)cdiv(F, 128), 2);
+    const size_t msm = sizeof(C<R>) * (size_t)RC * L * FFT_MUL_THREADS;
+    auto kern = fft_mul_kernel<R, L, MODE, RC>;
+    if (msm > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, msm));
+    dim3 g((unsigned)cdiv(F, FFT_MUL_THREADS), 2);
     cudaEvent_t ev = timing_begin(ctx);
-    fft_mul_kernel<R, L, MODE, RC><<<g, 128, 0, ctx->stream>>>((const C<R>*)a.fft_Bhat, Xh, Yh, Mx, My, R_, a.CX, a.CY);
+    kern<<<g, FFT_MUL_THREADS, msm, ctx->stream>>>((const C<R>*)a.fft_Bhat, Xh, Yh, Mx, My, R_, a.CX, a.CY);
     TM_LAUNCHED(ctx);
     // the block spectra once, the RHS spectra in and out
     const double mul_bytes = (double)sizeof(C<R>) * F * (2.0 * L * L + 2.0 * nb);
