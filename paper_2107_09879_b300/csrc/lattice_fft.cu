@@ -168,7 +168,7 @@ __device__ __forceinline__ void fft_smem_passes(C<R>* a, int pitch, int nrows, i
 }
 
 template <typename R, bool TOUT, bool TIN>
-__global__ void __launch_bounds__(FFT_THREADS)
+__global__ void __launch_bounds__(FFT_THREADS, sizeof(R) == 4 ? 4 : 1)
 fft_rows_kernel(const C<R>* __restrict__ in, int64_t in_batch_stride, int in_pitch, int cin, int nrows,
                 C<R>* __restrict__ out, int64_t out_batch_stride, int out_pitch, int cout, int lg, int lgrb, int dir,
                 const double2* __restrict__ tw) {
