@@ -237,7 +237,7 @@ template <typename R, bool TOUT, bool TIN = false>
 static int fft_rows(tmat_ctx* ctx, const C<R>* in, int64_t in_bs, int in_pitch, int cin, int nrows, C<R>* out,
                     int64_t out_bs, int out_pitch, int cout, int len, int64_t nbatch, int dir, const double2* tw) {
   const int lg = ilog2(len);
-  int lgrb = ilog2(std::max(1, std::min((TOUT || TIN) ? 32 : 8, FFT_SMEM_POINTS / len)));
+  int lgrb = ilog2(std::max(1, std::min((TOUT || TIN) ? 16 : 8, FFT_SMEM_POINTS / len)));
   const int rb = 1 << lgrb;
   const size_t smem = sizeof(C<R>) * ((size_t)rb * (len + (len >> 4) + 1) + len);
   auto kern = fft_rows_kernel<R, TOUT, TIN>;
