@@ -567,6 +567,39 @@ def run_kernel_only(args):
             "flop_per_launch": flop, "y_norm": float(torch.linalg.vector_norm(y).item())}
 
 
+def run_jinc_only(args):
+    """Incident coefficients of one jinc group in the 1200 x 1200 sweep's sub-region shape
+    (76 x 76 spheres = 60 x 60 core + 8-pitch ring, sources on the core, nmax 3, 4 RHS,
+    source plane z0 = -1), complex64 and fp64 paths: per-kernel CUDA-event times and the
+    relative difference of the two results (for kernel tuning and ncu captures)."""
+    import torch
+    from paper_2107_09879_b300 import _lib
+    ctx = _lib.Context(0, None)
+    side, core, ring, nmax, R = 76, 60, 8, 3, 4
+    pos = W.lattice_positions(side, side)
+    src = W.lattice_positions(core, core)[:, :2] + ring * PITCH
+    A = np.zeros((R, core * core, 2), complex)
+    for q, deg in enumerate((0.0, 5.0, 10.0, 15.0)):
+        th = math.radians(deg)
+        A[q, :, 0] = math.cos(th) * np.exp(1j * 2 * math.pi * (math.sin(th) * src[:, 0] - math.cos(th)))
+    out, res = {}, {}
+    kinds = ("jinc_nodes", "jinc_phase32", "jinc_gemm32", "jinc_accum64")
+    for prec in (1, 0):
+        for k in range(args.warmup + args.steps):
+            if k == args.warmup:
+                ctx.set_timing(True)
+            a = ctx.tmat_incident_jinc(pos, 1.0, 1.0, nmax, src, A, -1.0, precision=prec, src_pitch=PITCH)
+        torch.cuda.synchronize()
+        t = {kk: ctx.kernel_time(kk) for kk in kinds}
+        ctx.set_timing(False)
+        res[prec] = a
+        out["complex64" if prec == 1 else "fp64"] = {kk: v[1] / max(args.steps, 1) for kk, v in t.items() if v[0]}
+    out["workload"] = "jinc_group_76x76_core60_nmax3_4rhs"
+    out["unit"] = "ms per call"
+    out["rel_l2_c64_vs_fp64"] = float(np.linalg.norm(res[1] - res[0]) / np.linalg.norm(res[0]))
+    return out
+
+
 def run_reference(args, rank, world):
     """The reference arm: the oracle (plain fp64 CPU), timed on the host cores."""
     if rank != 0:
@@ -607,6 +640,8 @@ def main():
                     help="lattice operator by the direct block-Toeplitz kernels instead of FFT convolution")
     ap.add_argument("--tc-variant", type=int, default=1, choices=[1, 2],
                     help="tensor-core lattice kernel: 1 window view (default), 2 gather")
+    ap.add_argument("--jinc-only", action="store_true",
+                    help="time one jinc group of the sweep's sub-region shape (complex64 and fp64 paths)")
     ap.add_argument("--inner-tol", type=float, default=0.1,
                     help="relative tolerance of each complex64 inner solve of the refinement (0.1: short inner "
                          "solves, each closed by an fp64 residual; the Krylov count stays ~250 while the "
@@ -616,6 +651,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.kernel_only:
         print(json.dumps(run_kernel_only(args)))
+        return
+    if args.jinc_only:
+        print(json.dumps(run_jinc_only(args)))
         return
     if args.impl == "reference":
         if world > 1 and rank != 0:
