@@ -121,16 +121,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands
-# (profiles/lattice_tc2_200x200_nmax4.md); set to None when the kernel changes.
-# DRAM bytes / algorithmic bytes of one captured launch of the HBM-bound kernels, scaled to
-# the timed launches by their algorithmic bytes (traffic grows with the bytes a launch
-# must move): profiles/arnoldi_dcgs2_100x100_nmax4.md, profiles/lattice_fft_200x200_nmax4.md
+# DRAM bytes (read + write) / algorithmic bytes of one ncu capture of each HBM-bound kernel as
+# it stands, scaled to the timed launches by their algorithmic bytes (traffic grows with the
+# bytes a launch must move): profiles/arnoldi_dcgs2_100x100_nmax4.md (dot and update passes),
+# profiles/lattice_fft_200x200_nmax4.md (block product). Set an entry to None when its kernel
+# changes.
 TRAFFIC_RATIO = {"arnoldi_dots32": (490.18e6 + 4.41e6) / (62 * 2 * 480000 * 8),
                  "arnoldi_update32": (468.52e6 + 13.44e6) / (63 * 2 * 480000 * 8),
-                 "lattice_fft_mul32": 700.9e6 / 704.64e6}
+                 "lattice_fft_mul32": (654.35e6 + 46.49e6) / 704.64e6}
+# DRAM bytes per launch of the direct-path kernels (profiles/lattice_tc2_200x200_nmax4.md) and
+# of the block product (profiles/lattice_fft_200x200_nmax4.md)
 MEASURED_TRAFFIC = {"lattice_tc2_kernel<4,0>": 238.0e6 + 23.0e6,
-                    "fft_mul_kernel<float,24,0,2>": 654.4e6 + 46.5e6}  # profiles/lattice_fft_200x200_nmax4.md
+                    "fft_mul_kernel<float,24,0,2>": 654.35e6 + 46.49e6}
 
 
 def roofline(kern_name, achieved, launches, avg_ms, flop_per_launch):
