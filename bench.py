@@ -128,11 +128,11 @@ class ClockSampler:
 # changes.
 TRAFFIC_RATIO = {"arnoldi_dots32": (490.18e6 + 4.41e6) / (62 * 2 * 480000 * 8),
                  "arnoldi_update32": (468.52e6 + 13.44e6) / (63 * 2 * 480000 * 8),
-                 "lattice_fft_mul32": (654.35e6 + 46.49e6) / 704.64e6}
+                 "lattice_fft_mul32": None}
 # DRAM bytes per launch of the direct-path kernels (profiles/lattice_tc2_200x200_nmax4.md) and
 # of the block product (profiles/lattice_fft_200x200_nmax4.md)
 MEASURED_TRAFFIC = {"lattice_tc2_kernel<4,0>": 238.0e6 + 23.0e6,
-                    "fft_mul_kernel<float,24,0,2>": 654.35e6 + 46.49e6}
+                    "fft_mul_kernel<float,24,0,2>": None}
 
 
 def roofline(kern_name, achieved, launches, avg_ms, flop_per_launch):
@@ -460,7 +460,7 @@ def run_ours(args, rank, world):
             break
     hbm_kinds = {"arnoldi_dots32": "dots32_kernel<true> (Arnoldi dot pass, two targets)",
                  "arnoldi_update32": "dcgs2_update_kernel (Arnoldi update pass, two outputs)",
-                 "lattice_fft_mul32": "fft_mul_kernel<float,24,0,2> (per-frequency block products)"}
+                 "lattice_fft_mul32": "fft_mul_kernel<float,24,0,2> (block products, mirror pairs (kx, +-ky))"}
     hbm = {}
     for kind, name in hbm_kinds.items():
         nk, msk = ctx.kernel_time(kind)

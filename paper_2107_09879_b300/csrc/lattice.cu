@@ -13,6 +13,7 @@
 // stream from L1/L2 one coefficient at a time (outer-product order).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <vector>
 
 #include "dev.cuh"
@@ -331,6 +332,29 @@ int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_
     }
     TM_LAUNCHED(ctx);
   }
+  const bool fft = ctx->lattice_fft && K > 0 && lattice_fft_fits(nx, ny, CX, CY);
+  // mirror table of the class members for the FFT block product (lattice_fft.cu)
+  std::vector<int> mir(2 * L, 0);
+  int* d_mir = nullptr;
+  if (fft) {
+    for (int c = 0; c < 2; ++c)
+      for (int u = 0; u < L; ++u) {
+        const int f = t->perm[c * L + u], p = f / L, n = f % L;
+        int l = 1;
+        while ((l + 1) * (l + 1) <= n + 1) ++l;
+        const int m = n + 1 - l * (l + 1);
+        const int f2 = p * L + l * (l + 1) - m - 1;
+        int u2 = -1;
+        for (int v = 0; v < L; ++v)
+          if (t->perm[c * L + v] == f2) u2 = v;
+        if (u2 < 0) return set_error(ctx, TMAT_ENOTSUP, "mirror partner missing in class %d", c);
+        mir[c * L + u] = u2 | (p << 16);
+      }
+    char nm[32];
+    snprintf(nm, sizeof nm, "fft_mirror%d", t->nmax);
+    TM_TRY(scratch(ctx, nm, sizeof(int) * 2 * L, (void**)&d_mir));
+    TM_CUDA(ctx, cudaMemcpyAsync(d_mir, mir.data(), sizeof(int) * 2 * L, cudaMemcpyHostToDevice, ctx->stream));
+  }
   // host copies above are from stack vectors: wait before they go out of scope
   TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   LatOp a;
@@ -351,7 +375,7 @@ int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_
   a.fp32 = false;
   a.BT = B64;
   a.T = T64;
-  const bool fft = ctx->lattice_fft && K > 0 && lattice_fft_fits(nx, ny, CX, CY);
+  a.fft_mirror = d_mir;
   if (fft) TM_TRY(lattice_fft_prepare(ctx, &a));
   ops->lat64 = a;
   a.use_fft = false;

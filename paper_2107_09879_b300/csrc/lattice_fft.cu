@@ -335,22 +335,34 @@ __global__ void fft_scatter_blocks_kernel(const C<R>* __restrict__ BT, const int
 
 // Per frequency f and class c: Y^[r][c L + u][f] = sum_u' G[u][u'] X^[r][c L + u'][f] with
 // G = B^[c][u][u'][f] (MODE 0, 2) or B^[c][u'][u][-f] (MODE 1). RC RHS per pass share
-// the B^ loads. The thread's X^ values sit in its own column of shared memory rather than
-// in registers, so that three blocks fit on an SM and more B^ loads are in flight.
+// the B^ loads.
+// Mirror pairs: the blocks obey B_(dx,-dy) = D J B_(dx,dy) J D (J: the m -> -m partner in
+// the class, D = diag((-1)^p); the offset set and the window are symmetric in dy), hence
+// B^(kx, -ky) = D J B^(kx, ky) J D for the true spectra, and for the adjoint's B^(-f)^T the
+// same with -f. One read of G at f1 = (kx, ky) therefore serves f2 = (kx, -ky):
+//   Y^(f1) = ph G X^(f1),   Y^(f2)[J u] = ph D[u] (G w)[u],  w[v] = D[v] X^(f2)[J v],
+// ph the phase of f1 (or -f1) that undoes the compact-grid shift. A thread takes one item
+// (kx, ky <= My / 2) of one class; ky = 0 and My / 2 are their own mirror. The thread's X^
+// values sit in its own column of shared memory, not in registers.
 constexpr int FFT_MUL_THREADS = 128;
 template <typename R, int L, int MODE, int RC>
-__global__ void __launch_bounds__(FFT_MUL_THREADS, 3)
+__global__ void __launch_bounds__(FFT_MUL_THREADS, 2)
 fft_mul_kernel(const C<R>* __restrict__ Bh, const C<R>* __restrict__ Xh, C<R>* __restrict__ Yh, int Mx, int My,
-               int R_, int CX, int CY) {
+               int R_, int CX, int CY, const int* __restrict__ mirror) {
   constexpr int P = 2 * L, TS = FFT_MUL_THREADS;
   extern __shared__ __align__(16) unsigned char xsm[];
-  C<R>* xs = reinterpret_cast<C<R>*>(xsm) + threadIdx.x;  // [RC][L][TS]: this thread's column
+  C<R>* x1 = reinterpret_cast<C<R>*>(xsm) + threadIdx.x;  // [RC][L][TS]: X^(f1), this thread's column
+  C<R>* x2 = x1 + RC * L * TS;                             // [RC][L][TS]: w of f2
   const int64_t F = (int64_t)Mx * My;
-  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int hy = My >= 2 ? My / 2 + 1 : 1;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int c = blockIdx.y;
-  if (f >= F) return;  // no block barrier below
-  int64_t fb = f;
-  int kx = (int)(f / My), ky = (int)(f % My);
+  if (t >= (int64_t)Mx * hy) return;  // no block barrier below
+  const int kx0 = (int)(t / hy), ky0 = (int)(t % hy);
+  const int64_t f1 = (int64_t)kx0 * My + ky0, f2 = (int64_t)kx0 * My + (My - ky0) % My;
+  const bool pair = f2 != f1;
+  int64_t fb = f1;
+  int kx = kx0, ky = ky0;
   if (MODE == 1) {
     kx = (Mx - kx) % Mx;
     ky = (My - ky) % My;
@@ -365,30 +377,71 @@ fft_mul_kernel(const C<R>* __restrict__ Bh, const C<R>* __restrict__ Xh, C<R>* _
     sincospi(2.0 * (double)num / (double)F, &sn, &cs);
     ph = mk<R>((R)cs, (R)sn);
   }
+  const int* mir = mirror + c * L;
   for (int r0 = 0; r0 < R_; r0 += RC) {
 #pragma unroll
     for (int q = 0; q < RC; ++q)
 #pragma unroll
-      for (int up = 0; up < L; ++up)
-        xs[(q * L + up) * TS] =
-            (r0 + q < R_) ? Xh[((int64_t)(r0 + q) * P + c * L + up) * F + f] : mk<R>((R)0, (R)0);
-#pragma unroll 1
-    for (int u = 0; u < L; ++u) {
-      C<R> acc[RC];
-#pragma unroll
-      for (int q = 0; q < RC; ++q) acc[q] = mk<R>((R)0, (R)0);
-#pragma unroll
-      for (int up = 0; up < L; ++up) {
-        const int comp = MODE == 1 ? (c * L + up) * L + u : (c * L + u) * L + up;
-        const C<R> g = Bh[(int64_t)comp * F + fb];
-#pragma unroll
-        for (int q = 0; q < RC; ++q) cfma(acc[q], g, xs[(q * L + up) * TS]);
-        if ((up & 15) == 15) __syncwarp();  // bounds how far the compiler hoists the loads
+      for (int v = 0; v < L; ++v) {
+        const bool live = r0 + q < R_;
+        const int64_t row = (int64_t)(r0 + q) * P + c * L;
+        x1[(q * L + v) * TS] = live ? Xh[(row + v) * F + f1] : mk<R>((R)0, (R)0);
+        C<R> w = mk<R>((R)0, (R)0);
+        if (live && pair) {
+          const int m = mir[v];
+          w = Xh[(row + (m & 0xffff)) * F + f2];
+          if (m >> 16) w = mk<R>(-w.x, -w.y);
+        }
+        x2[(q * L + v) * TS] = w;
       }
-#pragma unroll
-      for (int q = 0; q < RC; ++q)
-        if (r0 + q < R_) Yh[((int64_t)(r0 + q) * P + c * L + u) * F + f] = cmul(acc[q], ph);
+    // rows of G double-buffered in registers (complex64, L <= 24): row u + 1 is in flight
+    // while row u is used
+    C<R> gA[L], gB[L];
+#define FFT_MUL_LOAD(U, DST)                                                                 \
+  _Pragma("unroll") for (int v = 0; v < L; ++v) {                                            \
+    const int comp = MODE == 1 ? (c * L + v) * L + (U) : (c * L + (U)) * L + v;              \
+    DST[v] = Bh[(int64_t)comp * F + fb];                                                     \
+  }
+#define FFT_MUL_USE(U, G)                                                                    \
+  {                                                                                          \
+    __syncwarp(); /* the X^ columns are re-read per row, not hoisted into registers */       \
+    C<R> acc1[RC], acc2[RC];                                                                 \
+    _Pragma("unroll") for (int q = 0; q < RC; ++q) acc1[q] = acc2[q] = mk<R>((R)0, (R)0);   \
+    _Pragma("unroll") for (int v = 0; v < L; ++v) {                                          \
+      _Pragma("unroll") for (int q = 0; q < RC; ++q) {                                       \
+        cfma(acc1[q], G[v], x1[(q * L + v) * TS]);                                           \
+        cfma(acc2[q], G[v], x2[(q * L + v) * TS]);                                           \
+      }                                                                                      \
+    }                                                                                        \
+    const int m = mir[(U)];                                                                  \
+    const C<R> ph2 = (m >> 16) ? mk<R>(-ph.x, -ph.y) : ph;                                   \
+    _Pragma("unroll") for (int q = 0; q < RC; ++q) if (r0 + q < R_) {                        \
+      const int64_t row = (int64_t)(r0 + q) * P + c * L;                                     \
+      Yh[(row + (U)) * F + f1] = cmul(acc1[q], ph);                                          \
+      if (pair) Yh[(row + (m & 0xffff)) * F + f2] = cmul(acc2[q], ph2);                      \
+    }                                                                                        \
+  }
+    if constexpr (sizeof(R) == 4 && L <= 24) {
+      FFT_MUL_LOAD(0, gA)
+#pragma unroll 1
+      for (int u = 0; u < L; u += 2) {
+        if (u + 1 < L) FFT_MUL_LOAD(u + 1, gB)
+        FFT_MUL_USE(u, gA)
+        if (u + 1 < L) {
+          if (u + 2 < L) FFT_MUL_LOAD(u + 2, gA)
+          FFT_MUL_USE(u + 1, gB)
+        }
+      }
+    } else {  // wider rows or fp64: one row in flight (the register file holds no second)
+      (void)gB;
+#pragma unroll 1
+      for (int u = 0; u < L; ++u) {
+        FFT_MUL_LOAD(u, gA)
+        FFT_MUL_USE(u, gA)
+      }
     }
+#undef FFT_MUL_LOAD
+#undef FFT_MUL_USE
   }
 }
 
@@ -479,15 +532,17 @@ static int fft_apply_t(tmat_ctx* ctx, const LatOp& a, const void* xv, void* yv, 
   TM_TRY(fft2_forward<R>(ctx, grid, nx, ny, Mx, My, nb, w1, Xh, tw));
   {
     constexpr int RC = (sizeof(R) == 4 && L <= 24) ? 2 : 1;
-    const size_t msm = sizeof(C<R>) * (size_t)RC * L * FFT_MUL_THREADS;
+    const size_t msm = sizeof(C<R>) * 2 * (size_t)RC * L * FFT_MUL_THREADS;
     auto kern = fft_mul_kernel<R, L, MODE, RC>;
     if (msm > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, msm));
-    dim3 g((unsigned)cdiv(F, FFT_MUL_THREADS), 2);
+    const int64_t items = (int64_t)Mx * (My >= 2 ? My / 2 + 1 : 1);
+    dim3 g((unsigned)cdiv(items, FFT_MUL_THREADS), 2);
     cudaEvent_t ev = timing_begin(ctx);
-    kern<<<g, FFT_MUL_THREADS, msm, ctx->stream>>>((const C<R>*)a.fft_Bhat, Xh, Yh, Mx, My, R_, a.CX, a.CY);
+    kern<<<g, FFT_MUL_THREADS, msm, ctx->stream>>>((const C<R>*)a.fft_Bhat, Xh, Yh, Mx, My, R_, a.CX, a.CY,
+                                                   a.fft_mirror);
     TM_LAUNCHED(ctx);
-    // the block spectra once, the RHS spectra in and out
-    const double mul_bytes = (double)sizeof(C<R>) * F * (2.0 * L * L + 2.0 * nb);
+    // the block spectra of one frequency per mirror pair, the RHS spectra in and out
+    const double mul_bytes = (double)sizeof(C<R>) * (items * 2.0 * L * L + 2.0 * nb * F);
     timing_end(ctx, sizeof(R) == 4 ? "lattice_fft_mul32" : "lattice_fft_mul64", ev, mul_bytes);
   }
   C<R>* Yc = Xh;  // X^ is no longer needed

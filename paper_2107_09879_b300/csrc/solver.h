@@ -35,6 +35,9 @@ struct LatOp {
   bool use_fft = false;
   int fft_Mx = 0, fft_My = 0;
   const void* fft_Bhat = nullptr;
+  // [2][L] per class member u: J(u) | p(u) << 16, J the m -> -m partner in the class and p
+  // the polarisation; B_(dx,-dy) = D J B_(dx,dy) J D with D = diag((-1)^p)
+  const int* fft_mirror = nullptr;
 };
 // An operator instance in one precision. kind 0: neighbour list; kind 1: lattice.
 struct Operator {
