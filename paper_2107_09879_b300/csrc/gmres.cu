@@ -1056,12 +1056,19 @@ int solve_system(tmat_ctx* ctx, const Operator& A64, const Operator* A32, int mo
     // x += ||r|| d
     axpy_scaled_kernel<<<dim3(g1, R), 256, 0, ctx->stream>>>(x, d64, alpha, n, n);
     TM_LAUNCHED(ctx);
-    // Fast check first, where the tolerance allows it: r = b - K x with K applied in
+    // Fast check first while the residual is large: r = b - K x with K applied in
     // complex64 to x rounded to complex64 has an absolute error of about
-    // kFastResidualFloor ||b||, and the next correction cannot push the true residual
-    // below that error. So it is used only for tolerances >= 10x that floor, and only
-    // while it is far above the tolerance; otherwise the fp64 residual decides.
-    if (p.tol >= 10.0 * kFastResidualFloor) {
+    // kFastResidualFloor ||b||, so it stands in for the fp64 residual only while it is far
+    // above that floor and above the tolerance (the next correction cannot push the true
+    // residual below its error), and only while it keeps falling (no stagnation on the
+    // error of the complex64 product); near the tolerance the fp64 residual decides, and
+    // only the fp64 residual can declare convergence. It is tried when this step is
+    // expected to leave the residual far above that threshold.
+    const double fast_thr = std::max(10.0 * p.tol, 100.0 * kFastResidualFloor);
+    bool try_fast = true;
+    for (int r = 0; r < R; ++r)
+      if (hb[r] != 0 && halpha[r] != 0.0) try_fast = try_fast && ip.tol * hr[r] > 10.0 * fast_thr * hb[r];
+    if (try_fast) {
       convert_kernel<double, float><<<g1, 256, 0, ctx->stream>>>(x, r32, (int64_t)R * n);
       TM_LAUNCHED(ctx);
       TM_TRY(op_apply(ctx, *A32, mode, r32, y32, R));
@@ -1074,7 +1081,7 @@ int solve_system(tmat_ctx* ctx, const Operator& A64, const Operator* A32, int mo
       for (int r = 0; r < R; ++r) {
         if (!std::isfinite(pin[r])) return set_error(ctx, TMAT_EBREAKDOWN, "refinement residual is not finite");
         if (hb[r] == 0 || halpha[r] == 0.0) continue;  // converged or zero RHS: frozen
-        far = far && pin[r] > std::max(10.0 * p.tol, 100.0 * kFastResidualFloor) * hb[r];
+        far = far && pin[r] > fast_thr * hb[r] && pin[r] < 0.5 * hr[r];
       }
       if (far) {
         for (int r = 0; r < R; ++r)
