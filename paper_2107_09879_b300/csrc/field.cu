@@ -279,7 +279,7 @@ int field_dev(tmat_ctx* ctx, const double* pos, int64_t N, double k, int nmax, c
               int64_t M, bool far, double2* E) {
   TM_TRY(upload_legendre(ctx));
   if (M == 0) return TMAT_OK;
-  int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(N, 128), std::max<int64_t>(1, 4 * ctx->num_sms / std::max<int64_t>(M, 1))));
+  int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(N, 128), std::max<int64_t>(1, 16 * ctx->num_sms / std::max<int64_t>(M, 1))));
   if (nchunk > 65535) nchunk = 65535;
   double2* part;
   TM_TRY(scratch(ctx, "fld_part", sizeof(double2) * M * nchunk * 3, (void**)&part));
