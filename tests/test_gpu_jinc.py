@@ -57,3 +57,25 @@ def test_jinc_single_source_and_empty_group():
     assert rel_l2(a[0], ref) <= 1e-12
     z = ctx().tmat_incident_jinc(pos, 1.0, 1.0, 3, np.zeros((0, 2)), np.zeros((1, 0, 2), complex), Z0, 10, 12)
     assert np.all(z == 0)
+
+
+@pytest.mark.parametrize("offset", [0.0, 480.0])
+def test_jinc_complex64_chunked_group(offset):
+    """The complex64 path on a group that needs several node chunks of the phase matrix and a
+    GEMM split over nodes (40 x 40 spheres, 30 x 30 sources, 26,312 rule nodes, 2 RHS):
+    against the fp64 path at every sphere (complex64 tolerance) and the fp64 path against
+    the oracle at sampled spheres. The offset (480 wavelengths) puts the phases k.x in the
+    thousands of radians, where the double-float argument and its reduction modulo 2 pi
+    must still hold the complex64 accuracy."""
+    side, core = 40, 30
+    pos = W.lattice_positions(side, side, origin=(offset, 0.7 * offset))
+    src = np.ascontiguousarray(W.lattice_positions(core, core, origin=(offset + 2.5, 0.7 * offset + 2.5))[:, :2])
+    A = rand_c((2, core * core, 2), 77)
+    a32 = ctx().tmat_incident_jinc(pos, 1.0, 1.0, 3, src, A, Z0, precision=1, src_pitch=0.5)
+    a64 = ctx().tmat_incident_jinc(pos, 1.0, 1.0, 3, src, A, Z0, precision=0, src_pitch=0.5)
+    assert rel_l2(a32, a64) <= 1e-6
+    idx = [0, 777, side * side - 1]
+    nb, na = incident.jinc_rule_size(K0, _extent(pos, src))
+    assert nb * na > 3 * 8192  # several node chunks of the complex64 path
+    ref = incident.jinc_group_coeffs(3, K0, pos[idx], src, A[1], Z0, incident.jinc_rule(nb, na), pitch=0.5)
+    assert rel_l2(a64[1][idx], ref) <= 1e-10
