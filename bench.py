@@ -128,11 +128,11 @@ class ClockSampler:
 # changes.
 TRAFFIC_RATIO = {"arnoldi_dots32": (490.18e6 + 4.41e6) / (62 * 2 * 480000 * 8),
                  "arnoldi_update32": (468.52e6 + 13.44e6) / (63 * 2 * 480000 * 8),
-                 "lattice_fft_mul32": None}
+                 "lattice_fft_mul32": (390.22e6 + 40.69e6) / 405.01e6}
 # DRAM bytes per launch of the direct-path kernels (profiles/lattice_tc2_200x200_nmax4.md) and
 # of the block product (profiles/lattice_fft_200x200_nmax4.md)
 MEASURED_TRAFFIC = {"lattice_tc2_kernel<4,0>": 238.0e6 + 23.0e6,
-                    "fft_mul_kernel<float,24,0,2>": None}
+                    "fft_mul_kernel<float,24,0,2>": 390.22e6 + 40.69e6}
 
 
 def roofline(kern_name, achieved, launches, avg_ms, flop_per_launch):
