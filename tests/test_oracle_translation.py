@@ -76,3 +76,29 @@ def test_inversion_symmetry():
     S = np.diag([(-1) ** l for (l, m) in vswf.lm_list(nmax)] + [(-1) ** (l + 1) for (l, m) in vswf.lm_list(nmax)])
     d = np.array([0.7, -0.3, 0.2])
     assert np.max(np.abs(translation.xi_matrix(nmax, nmax, K0, -d) - S @ translation.xi_matrix(nmax, nmax, K0, d) @ S)) < 1e-13
+
+
+@pytest.mark.parametrize("d", [(1.0, 0.5), (0.3, -1.7), (2.5, 1.0), (-0.8, 0.0), (0.0, 1.3)])
+def test_mirror_symmetries_of_planar_blocks(d):
+    """Mirror reflections of the plane map a coupling block to a signed permutation of itself:
+    B(-dx, dy) = Dx J B(dx, dy) J Dx with Dx = diag((-1)^(m+p)) and B(dx, -dy) = Dy J B J Dy
+    with Dy = diag((-1)^p), J the m -> -m permutation. The FFT lattice operator reads one
+    block spectrum for the pair (kx, +-ky) on the strength of the second identity."""
+    nmax = 4
+    lm = vswf.lm_list(nmax)
+    L = len(lm)
+    jn = [lm.index((l, -m)) for (l, m) in lm]
+    J = np.concatenate([jn, np.array(jn) + L])
+    m = np.array([mm for (_, mm) in lm] * 2)
+    p = np.array([0] * L + [1] * L)
+    Dx, Dy = np.diag((-1.0) ** (m + p)), np.diag((-1.0) ** p)
+    dx, dy = d
+    B = translation.coupling_block(nmax, K0, np.array([dx, dy, 0.0]), np.zeros(3))
+    Bx = translation.coupling_block(nmax, K0, np.array([-dx, dy, 0.0]), np.zeros(3))
+    By = translation.coupling_block(nmax, K0, np.array([dx, -dy, 0.0]), np.zeros(3))
+    scale = np.max(np.abs(B))
+    assert np.max(np.abs(Bx - Dx @ B[np.ix_(J, J)] @ Dx)) <= 1e-13 * scale
+    assert np.max(np.abs(By - Dy @ B[np.ix_(J, J)] @ Dy)) <= 1e-13 * scale
+    # the signs matter: without them neither identity holds (off the symmetry axes)
+    if dx != 0 and dy != 0:
+        assert np.max(np.abs(By - B[np.ix_(J, J)])) > 1e-3 * scale
