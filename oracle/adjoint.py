@@ -7,6 +7,10 @@ E = E_inc + E_sca at the focal point x_f):
 Its differential is dFoM = 2 Re[ v^T ds ] with v_i = sum_c conj(E_c) Phi_c(k(x_f - x_i))
 (the Wirtinger derivative d|z|^2/dz = conj(z); reading of f').
 
+Position gradient (App. IV with the in-plane positions as the geometry parameters):
+dFoM/d(x_i, y_i) by central differences of the figure of merit, every side a direct
+solve (`position_gradient_fd`), the derivative by its definition for small arrays.
+
 Geometry gradient (App. IV, Eq. grad_geometry_overlap): only the diagonal
 blocks of Omega depend on the radius. With the preconditioned unknowns
 s = T e, e = a0 + A s, and the adjoint solve
@@ -54,3 +58,38 @@ def radius_gradient(nmax, k, pos, tdiag, dtdiag_dr, a0, s, v, cutoff=0.0, tol=1e
         mu = mu.reshape(shape)
     e = a0 + apply_A(nmax, k, pos, s, nbr)
     return 2.0 * np.real(np.sum(mu * dtdiag_dr * e, axis=1)), mu
+
+
+def position_gradient_fd(nmax, k, pos, tdiag, a0_of, x_f, E_inc_f, h=1e-5, cutoff=0.0, taper=0.0):
+    """dFoM/d(x_i, y_i) for every scatterer by central differences of the figure of merit,
+    each side a direct (LU) solve of the system with that one position moved: the derivative
+    by its definition, for small arrays. a0_of(pos) -> (N, P) incident coefficients of the
+    moved positions (the incident field at x_f does not depend on them). Returns (N, 2)."""
+    from .system import solve_dense, window
+
+    pos = np.asarray(pos, dtype=np.float64)
+
+    def F(p):
+        with window(cutoff, taper):
+            s = solve_dense(nmax, k, p, tdiag, a0_of(p), cutoff)
+        return fom(nmax, k, p, s, x_f, E_inc_f)
+
+    g = np.zeros((pos.shape[0], 2))
+    for i in range(pos.shape[0]):
+        for d in range(2):
+            pp, pm = pos.copy(), pos.copy()
+            pp[i, d] += h
+            pm[i, d] -= h
+            g[i, d] = (F(pp) - F(pm)) / (2.0 * h)
+    return g
+
+
+def focus_gradient_fd(nmax, k, pos, s, x_f, E_inc_f, h=1e-5):
+    """dFoM/d(x_f, y_f) with s and the incident field held fixed (central differences)."""
+    g = np.zeros(2)
+    for d in range(2):
+        xp, xm = np.array(x_f, dtype=np.float64), np.array(x_f, dtype=np.float64)
+        xp[d] += h
+        xm[d] -= h
+        g[d] = (fom(nmax, k, pos, s, xp, E_inc_f) - fom(nmax, k, pos, s, xm, E_inc_f)) / (2.0 * h)
+    return g
