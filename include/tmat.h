@@ -343,6 +343,26 @@ int tmat_adjoint(tmat_ctx* ctx, const tmat_solution* sol, const tmat_c128* v,
                  const tmat_c128* dTdr, double* grad_out, tmat_c128* mu_out,
                  tmat_solve_info* info);
 
+/* Position gradient of the point figure of merit: dFoM/d(x_i, y_i) for every scatterer
+ * (App. IV, with the in-plane positions as the geometry parameters). Lattice solutions
+ * (TMAT_PATH_LATTICE) only: the derivative is taken at the lattice configuration, where
+ * the derivative blocks dF/dd of the coupling (window included) depend only on the offset.
+ *   mu[N][P]        the adjoint solution for this figure of merit (tmat_adjoint's mu_out);
+ *   da0_dx, da0_dy  [N][P] d a0_i / d x_i and d a0_i / d y_i of the incident coefficients
+ *                   (for a plane wave of wave vector k_inc: i k_inc,x a0_i and i k_inc,y a0_i);
+ *                   both NULL when the incident field does not move with the scatterers;
+ *   x_f[3], E_f[3]  the focal point and the total field there (incident + scattered);
+ *   grad_out[N][2]  dFoM/dx_i, dFoM/dy_i.
+ * grad = 2 Re[(T mu)_i . (A'_q s + da0_q)_i - (A'_q^T T mu)_i . s_i] + the explicit term
+ * 2 Re sum_c conj(E_c) s_i . d Phi_c(k(x_f - x_i)) / d q_i, the latter by a central
+ * difference of the fp64 wave functions (step 1e-4 / k, relative error ~2e-9). The two
+ * derivative operators are applied in fp64 on the CUDA cores (four applies).
+ * Errors: TMAT_EINVAL (NULL required argument, only one of da0_dx/da0_dy, wrong device),
+ * TMAT_ENOTSUP (neighbour-path solution). All arrays host or device. */
+int tmat_position_gradient(tmat_ctx* ctx, const tmat_solution* sol, const tmat_c128* mu,
+                           const tmat_c128* da0_dx, const tmat_c128* da0_dy, const double* x_f,
+                           const tmat_c128* E_f, double* grad_out);
+
 /* ---- allocation-free variant (no counterpart in the paper) ------------------ */
 
 /* Capacity of the fixed device scratch of tmat_field_noalloc, in complex

@@ -87,6 +87,7 @@ _SIGS = {
     "tmat_point_fom": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _vp, ct.POINTER(_d), _vp],
     "tmat_field_noalloc": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _i64, _vp],
     "tmat_adjoint": [_vp, _vp, _vp, _vp, _vp, _vp, ct.POINTER(SolveInfo)],
+    "tmat_position_gradient": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
 }
 EXPORTED = []
 for _name, _args in _SIGS.items():
@@ -314,6 +315,15 @@ class Context:
         if rc not in (OK, ENOCONV):
             self.check(rc)
         return grad, mu, info
+
+    def tmat_position_gradient(self, sol, mu, x_f, E_f, da0_dx=None, da0_dy=None):
+        """dFoM/d(x_i, y_i) as (N, 2) float64 for a lattice solution; mu from tmat_adjoint
+        (want_mu=True), E_f the total field at the focal point x_f."""
+        N = mu.shape[0]
+        grad = empty_like_space(mu, (N, 2), np.float64)
+        self.check(lib.tmat_position_gradient(self.h, sol.h, ptr(mu), ptr(da0_dx), ptr(da0_dy), ptr(x_f), ptr(E_f),
+                                              ptr(grad)))
+        return grad
 
 
 class Solution:

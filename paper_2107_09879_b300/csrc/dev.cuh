@@ -69,6 +69,15 @@ __host__ __device__ __forceinline__ double taper_weight(double d, double cutoff,
   return 0.5 * (1.0 + cos(3.14159265358979323846 * (d - d0) / taper));
 }
 
+// d w / d d of taper_weight (zero outside the taper, where w is constant)
+__host__ __device__ __forceinline__ double taper_dweight(double d, double cutoff, double taper) {
+  if (!(taper > 0) || !(cutoff > 0)) return 0.0;
+  double d0 = cutoff - taper;
+  if (d <= d0 || d >= cutoff) return 0.0;
+  const double pi = 3.14159265358979323846;
+  return -0.5 * (pi / taper) * sin(pi * (d - d0) / taper);
+}
+
 // pi_l^m(b) = Pbar_l^m(cos b)/sin b (m >= 1) and tau_l^m(b) = d Pbar_l^m / d b,
 // normalised Legendre functions without the Condon-Shortley phase.
 __device__ inline void pi_tau(int l, int m, double beta, double* pi_out, double* tau_out) {

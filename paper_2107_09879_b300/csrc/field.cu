@@ -290,6 +290,22 @@ int field_dev(tmat_ctx* ctx, const double* pos, int64_t N, double k, int nmax, c
   return TMAT_OK;
 }
 
+// v[i][f] = sum_c conj(E_c) Phi_{f,c}(k(x_f - x_i)) for a device focal point and field
+int adjoint_source_dev(tmat_ctx* ctx, const double* pos, int64_t N, double k, int nmax, const double* xf,
+                       const double2* E, double2* v) {
+  TM_TRY(upload_legendre(ctx));
+  if (N == 0) return TMAT_OK;
+  switch (nmax) {
+#define AK(NM) \
+  case NM: adjoint_source_kernel<NM><<<(unsigned)cdiv(N, 64), 64, 0, ctx->stream>>>(pos, N, k, nmax, xf, E, v); break;
+    AK(1) AK(2) AK(3) AK(4) AK(5) AK(6)
+#undef AK
+    default: return set_error(ctx, TMAT_EINVAL, "nmax %d outside 1..%d", nmax, TMAT_NMAX_MAX);
+  }
+  TM_LAUNCHED(ctx);
+  return TMAT_OK;
+}
+
 }  // namespace tmat
 
 using namespace tmat;

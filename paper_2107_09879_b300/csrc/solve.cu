@@ -325,3 +325,216 @@ extern "C" int tmat_adjoint(tmat_ctx* ctx, const tmat_solution* sol, const tmat_
   if (!st.converged) return set_error(ctx, TMAT_ENOCONV, "tmat_adjoint: not converged after %d iterations", st.iterations);
   return TMAT_OK;
 }
+
+// ---- position gradient (App. IV with the in-plane positions as parameters) ---------
+//
+// With s = T e, e = a0 + A s and the adjoint solution mu of (I - A^T T) mu = v (as in
+// tmat_adjoint), the variation of the figure of merit at fixed T is
+//   dFoM = 2 Re[ (T mu)^T (da0 + dA s) ] + (explicit dependence of E(x_f) on the positions).
+// A block A_jl = F(x_j - x_l) depends on both ends: for position q_i of scatterer i,
+//   (T mu)^T (dA/dq_i) s = (T mu)_i . (A'_q s)_i - (A'_q^T T mu)_i . s_i,
+// where A'_q is the lattice operator whose blocks are dF/dd_q at the lattice offsets (the
+// coupling window's derivative included). The explicit term is
+//   2 Re sum_c conj(E_c) s_i . d/dq_i Phi_c(k(x_f - x_i)),
+// taken as a central difference of the fp64 wave functions in x_f (step 1e-4 / k; error
+// ~ (k h)^2 / 6 relative).
+namespace tmat {
+
+// BX/BY[k][c][u'][u] = d/dd_x, d/dd_y of w(rho) e^{i(m_u' - m_u) phi} sum_q G[c][u][u'][q] h_q(k rho)
+// at d = -(dx, dy) pitch, the layout of the lattice blocks
+template <int NMAX>
+__global__ void lattice_dblocks_kernel(const int2* __restrict__ off, int K, double pitch, double k, double cutoff,
+                                       double taper, const double2* __restrict__ G, const int* __restrict__ mval,
+                                       int LP, double2* __restrict__ BX, double2* __restrict__ BY) {
+  constexpr int L = NMAX * (NMAX + 2), Q = 2 * NMAX + 1;
+  __shared__ double2 h[Q], hp[Q];                // h_q(k rho) and d/d rho of it
+  __shared__ double2 eph[2 * (2 * NMAX) + 1];    // e^{i mu phi}
+  const int kk = blockIdx.x;
+  if (kk >= K) return;
+  const double dx = -(double)off[kk].x * pitch, dy = -(double)off[kk].y * pitch;
+  const double rho = sqrt(dx * dx + dy * dy);
+  if (off[kk].x == 0 && off[kk].y == 0) {
+    for (int e = threadIdx.x; e < 2 * L * L; e += blockDim.x) {
+      const int c = e / (L * L), u = (e / L) % L, up = e % L;
+      const size_t o = (((size_t)kk * 2 + c) * L + up) * LP + u;
+      BX[o] = make_double2(0, 0);
+      BY[o] = make_double2(0, 0);
+    }
+    return;
+  }
+  if (threadIdx.x == 0) {
+    double2 hh[Q];
+    hankel_up<double, Q>(k * rho, hh);
+    const double z = k * rho;
+    for (int q = 0; q < Q; ++q) {
+      h[q] = hh[q];
+      // h_q'(z) = h_{q-1}(z) - (q + 1) / z h_q(z), h_0' = -h_1
+      double2 d;
+      if (q == 0) d = make_double2(-hh[1].x, -hh[1].y);
+      else d = make_double2(hh[q - 1].x - (q + 1) / z * hh[q].x, hh[q - 1].y - (q + 1) / z * hh[q].y);
+      hp[q] = make_double2(k * d.x, k * d.y);
+    }
+    double2 e1 = make_double2(dx / rho, dy / rho), e = make_double2(1, 0);
+    for (int mu = 0; mu <= 2 * NMAX; ++mu) {
+      eph[2 * NMAX + mu] = e;
+      eph[2 * NMAX - mu] = cconj(e);
+      e = cmul(e, e1);
+    }
+  }
+  __syncthreads();
+  const double w = taper_weight(rho, cutoff, taper), wp = taper_dweight(rho, cutoff, taper);
+  const double cphi = dx / rho, sphi = dy / rho;
+  for (int e = threadIdx.x; e < 2 * L * L; e += blockDim.x) {
+    const int c = e / (L * L), u = (e / L) % L, up = e % L;
+    const double2* g = G + ((size_t)(c * L + u) * L + up) * Q;
+    double2 s0 = make_double2(0, 0), s1 = make_double2(0, 0);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      cfma(s0, g[q], h[q]);
+      cfma(s1, g[q], hp[q]);
+    }
+    const int mu = mval[c * L + up] - mval[c * L + u];
+    const double2 E = eph[2 * NMAX + mu];
+    const double2 b0 = cmul(E, s0), b1 = cmul(E, s1);
+    // d rho / d dx = cos phi, d phi / d dx = -sin phi / rho; d rho / d dy = sin phi, d phi / d dy = cos phi / rho
+    const double2 imb0 = make_double2(-mu * b0.y, mu * b0.x);  // i mu b0
+    const double2 dbx = make_double2(wp * cphi * b0.x + w * (cphi * b1.x - sphi / rho * imb0.x),
+                                     wp * cphi * b0.y + w * (cphi * b1.y - sphi / rho * imb0.y));
+    const double2 dby = make_double2(wp * sphi * b0.x + w * (sphi * b1.x + cphi / rho * imb0.x),
+                                     wp * sphi * b0.y + w * (sphi * b1.y + cphi / rho * imb0.y));
+    const size_t o = (((size_t)kk * 2 + c) * L + up) * LP + u;
+    BX[o] = dbx;
+    BY[o] = dby;
+  }
+}
+
+__global__ void fill_one_kernel(double2* __restrict__ x, int64_t n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) x[t] = make_double2(1.0, 0.0);
+}
+
+// grad[i][q] = 2 Re sum_u [ tmu (ys_q) - (tmu - yz_q) s + tmu da0_q ]  (internal layout)
+//              - Re sum_f s_api (vp_q - vm_q) / h                       (API layout)
+__global__ void posgrad_kernel(const double2* __restrict__ tmu, const double2* __restrict__ s,
+                               const double2* __restrict__ ys, const double2* __restrict__ yz,
+                               const double2* __restrict__ da0, const double2* __restrict__ s_api,
+                               const double2* __restrict__ vpm, double inv_h, int64_t N, int P,
+                               double* __restrict__ grad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int64_t NP = N * P;
+  for (int q = 0; q < 2; ++q) {
+    double acc = 0.0, ex = 0.0;
+    for (int u = 0; u < P; ++u) {
+      const int64_t o = i * P + u;
+      const double2 t = tmu[o];
+      double2 g = cmul(t, ys[q * NP + o]);
+      const double2 atz = make_double2(t.x - yz[q * NP + o].x, t.y - yz[q * NP + o].y);  // (A'^T T mu)
+      g = csub(g, cmul(atz, s[o]));
+      if (da0) g = cadd(g, cmul(t, da0[q * NP + o]));
+      acc += g.x;
+      const double2 dv = csub(vpm[(2 * q) * NP + o], vpm[(2 * q + 1) * NP + o]);
+      ex += cmul(s_api[o], dv).x;
+    }
+    grad[2 * i + q] = 2.0 * acc - ex * inv_h;
+  }
+}
+
+}  // namespace tmat
+
+extern "C" int tmat_position_gradient(tmat_ctx* ctx, const tmat_solution* sol, const tmat_c128* mu,
+                                      const tmat_c128* da0_dx, const tmat_c128* da0_dy, const double* x_f,
+                                      const tmat_c128* E_f, double* grad_out) {
+  if (!ctx) return TMAT_EINVAL;
+  if (!sol || !mu || !x_f || !E_f || !grad_out || ((da0_dx == nullptr) != (da0_dy == nullptr)))
+    return set_error(ctx, TMAT_EINVAL, "tmat_position_gradient: bad arguments");
+  if (sol->device != ctx->device)
+    return set_error(ctx, TMAT_EINVAL, "tmat_position_gradient: solution is on another device");
+  if (sol->path != TMAT_PATH_LATTICE)
+    return set_error(ctx, TMAT_ENOTSUP, "tmat_position_gradient: lattice solutions only");
+  Tables* t;
+  TM_TRY(get_tables(ctx, sol->nmax, &t));
+  TM_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int64_t N = sol->N;
+  const int P = t->P, L = t->L;
+  if (N == 0) return TMAT_OK;
+  Staged smu, sdx, sdy, sxf, sef, sg;
+  TM_TRY(stage_in(ctx, "st_mu_in", mu, sizeof(double2) * N * P, &smu));
+  TM_TRY(stage_in(ctx, "st_da0x", da0_dx, da0_dx ? sizeof(double2) * N * P : 0, &sdx));
+  TM_TRY(stage_in(ctx, "st_da0y", da0_dy, da0_dy ? sizeof(double2) * N * P : 0, &sdy));
+  TM_TRY(stage_in(ctx, "st_xf", x_f, sizeof(double) * 3, &sxf));
+  TM_TRY(stage_in(ctx, "st_ef", E_f, sizeof(double2) * 3, &sef));
+  TM_TRY(stage_out(ctx, "st_pgrad", grad_out, sizeof(double) * 2 * N, &sg));
+  OpPair ops;
+  TM_TRY(make_lattice_ops(ctx, t, sol->pos, N, sol->k, sol->lattice_nx, sol->lattice_ny, sol->lattice_pitch,
+                          sol->cutoff, sol->taper, sol->T64, nullptr, false, &ops, 0));
+  const LatOp& a = ops.lat64;
+  const size_t nblk = (size_t)std::max(a.K, 1) * 2 * L * a.LP;
+  double2 *BX, *BY, *one, *mui, *tmu, *da0, *ys, *yz, *s_api, *vpm, *xf4;
+  TM_TRY(scratch(ctx, "pg_BX", sizeof(double2) * nblk, (void**)&BX));
+  TM_TRY(scratch(ctx, "pg_BY", sizeof(double2) * nblk, (void**)&BY));
+  TM_TRY(scratch(ctx, "pg_one", sizeof(double2) * N * P, (void**)&one));
+  TM_TRY(scratch(ctx, "pg_mu", sizeof(double2) * N * P, (void**)&mui));
+  TM_TRY(scratch(ctx, "pg_tmu", sizeof(double2) * N * P, (void**)&tmu));
+  TM_TRY(scratch(ctx, "pg_da0", sizeof(double2) * 2 * N * P, (void**)&da0));
+  TM_TRY(scratch(ctx, "pg_ys", sizeof(double2) * 2 * N * P, (void**)&ys));
+  TM_TRY(scratch(ctx, "pg_yz", sizeof(double2) * 2 * N * P, (void**)&yz));
+  TM_TRY(scratch(ctx, "pg_sapi", sizeof(double2) * N * P, (void**)&s_api));
+  TM_TRY(scratch(ctx, "pg_vpm", sizeof(double2) * 4 * N * P, (void**)&vpm));
+  TM_TRY(scratch(ctx, "pg_xf4", sizeof(double) * 12 + 64, (void**)&xf4));
+  if (a.K > 0) {
+    switch (sol->nmax) {
+#define DB(NM)                                                                                                    \
+  case NM:                                                                                                        \
+    lattice_dblocks_kernel<NM><<<a.K, 256, 0, ctx->stream>>>(a.off, a.K, sol->lattice_pitch, sol->k, sol->cutoff, \
+                                                             sol->taper, t->d_gdense, t->d_mval, a.LP, BX, BY);   \
+    break;
+      DB(1) DB(2) DB(3) DB(4) DB(5) DB(6)
+#undef DB
+    }
+    TM_LAUNCHED(ctx);
+  }
+  fill_one_kernel<<<(unsigned)cdiv(N * P, 256), 256, 0, ctx->stream>>>(one, N * P);
+  TM_LAUNCHED(ctx);
+  TM_TRY(to_internal(ctx, t, (const double2*)smu.dev, mui, false, N));
+  tdiag_mul_kernel<<<(unsigned)cdiv(N * P, 256), 256, 0, ctx->stream>>>(sol->T64, mui, tmu, N * P, N * P);
+  TM_LAUNCHED(ctx);
+  if (da0_dx) {
+    TM_TRY(to_internal(ctx, t, (const double2*)sdx.dev, da0, false, N));
+    TM_TRY(to_internal(ctx, t, (const double2*)sdy.dev, da0 + N * P, false, N));
+  }
+  // (A'_q s) and T mu - A'_q^T (1 . T mu) for q = x, y on the fp64 CUDA-core lattice kernel
+  for (int q = 0; q < 2; ++q) {
+    LatOp d = a;
+    d.BT = q == 0 ? BX : BY;
+    d.T = one;
+    d.use_fft = false;
+    d.use_oz = false;
+    d.use_tc = false;
+    d.fp32 = false;
+    TM_TRY(lattice_apply(ctx, d, TMAT_OP_COUPLE, sol->s, ys + q * N * P, 1));
+    TM_TRY(lattice_apply(ctx, d, TMAT_OP_ADJOINT, tmu, yz + q * N * P, 1));
+  }
+  // explicit term: v at the focal point moved by +-h along x and y, with E fixed
+  TM_TRY(from_internal(ctx, t, sol->s, false, s_api, N));
+  double hxf[3];
+  TM_CUDA(ctx, cudaMemcpyAsync(hxf, sxf.dev, sizeof(double) * 3, cudaMemcpyDeviceToHost, ctx->stream));
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const double hstep = 1e-4 / sol->k;
+  double pts[12];
+  for (int j = 0; j < 4; ++j) {
+    for (int c = 0; c < 3; ++c) pts[3 * j + c] = hxf[c];
+    pts[3 * j + j / 2] += (j % 2 == 0) ? hstep : -hstep;  // +x, -x, +y, -y
+  }
+  double* dpts = (double*)xf4;
+  TM_CUDA(ctx, cudaMemcpyAsync(dpts, pts, sizeof(pts), cudaMemcpyHostToDevice, ctx->stream));
+  for (int j = 0; j < 4; ++j)
+    TM_TRY(adjoint_source_dev(ctx, sol->pos, N, sol->k, sol->nmax, dpts + 3 * j, (const double2*)sef.dev,
+                              vpm + j * N * P));
+  posgrad_kernel<<<(unsigned)cdiv(N, 128), 128, 0, ctx->stream>>>(tmu, sol->s, ys, yz, da0_dx ? da0 : nullptr, s_api,
+                                                                   vpm, 1.0 / hstep, N, P, (double*)sg.dev);
+  TM_LAUNCHED(ctx);
+  TM_TRY(finish_out(ctx, &sg));
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // pts is a host stack array
+  return TMAT_OK;
+}

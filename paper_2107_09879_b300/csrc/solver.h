@@ -114,6 +114,8 @@ struct OpPair {
   bool have32 = false, have_oz = false;
   LatOp lat64, lat32, lat64oz;
 };
+int adjoint_source_dev(tmat_ctx* ctx, const double* pos, int64_t N, double k, int nmax, const double* xf,
+                       const double2* E, double2* v);
 int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_t N, double k, int nx, int ny,
                      double pitch, double cutoff, double taper, const double2* T64, const float2* T32, bool mixed,
                      OpPair* ops, int want_oz = 0);
