@@ -356,7 +356,8 @@ int tmat_adjoint(tmat_ctx* ctx, const tmat_solution* sol, const tmat_c128* v,
  * grad = 2 Re[(T mu)_i . (A'_q s + da0_q)_i - (A'_q^T T mu)_i . s_i] + the explicit term
  * 2 Re sum_c conj(E_c) s_i . d Phi_c(k(x_f - x_i)) / d q_i, the latter by a central
  * difference of the fp64 wave functions (step 1e-4 / k, relative error ~2e-9). The two
- * derivative operators are applied in fp64 on the CUDA cores (four applies).
+ * derivative operators are applied in fp64 (four applies), by FFT convolution with their
+ * own block spectra where the lattice grid fits, else on the CUDA cores.
  * Errors: TMAT_EINVAL (NULL required argument, only one of da0_dx/da0_dy, wrong device),
  * TMAT_ENOTSUP (neighbour-path solution). All arrays host or device. */
 int tmat_position_gradient(tmat_ctx* ctx, const tmat_solution* sol, const tmat_c128* mu,

@@ -338,7 +338,8 @@ __global__ void fft_scatter_blocks_kernel(const C<R>* __restrict__ BT, const int
 // the B^ loads.
 // Mirror pairs: the blocks obey B_(dx,-dy) = D J B_(dx,dy) J D (J: the m -> -m partner in
 // the class, D = diag((-1)^p); the offset set and the window are symmetric in dy), hence
-// B^(kx, -ky) = D J B^(kx, ky) J D for the true spectra, and for the adjoint's B^(-f)^T the
+// B^(kx, -ky) = D J B^(kx, ky) J D for the true spectra (times msign = -1 for blocks that
+// are odd in dy, such as their dy-derivatives), and for the adjoint's B^(-f)^T the
 // same with -f. One read of G at f1 = (kx, ky) therefore serves f2 = (kx, -ky):
 //   Y^(f1) = ph G X^(f1),   Y^(f2)[J u] = ph D[u] (G w)[u],  w[v] = D[v] X^(f2)[J v],
 // ph the phase of f1 (or -f1) that undoes the compact-grid shift. A thread takes one item
@@ -348,7 +349,7 @@ constexpr int FFT_MUL_THREADS = 128;
 template <typename R, int L, int MODE, int RC>
 __global__ void __launch_bounds__(FFT_MUL_THREADS, 2)
 fft_mul_kernel(const C<R>* __restrict__ Bh, const C<R>* __restrict__ Xh, C<R>* __restrict__ Yh, int Mx, int My,
-               int R_, int CX, int CY, const int* __restrict__ mirror) {
+               int R_, int CX, int CY, const int* __restrict__ mirror, int msign) {
   constexpr int P = 2 * L, TS = FFT_MUL_THREADS;
   extern __shared__ __align__(16) unsigned char xsm[];
   C<R>* x1 = reinterpret_cast<C<R>*>(xsm) + threadIdx.x;  // [RC][L][TS]: X^(f1), this thread's column
@@ -414,7 +415,7 @@ fft_mul_kernel(const C<R>* __restrict__ Bh, const C<R>* __restrict__ Xh, C<R>* _
       }                                                                                      \
     }                                                                                        \
     const int m = mir[(U)];                                                                  \
-    const C<R> ph2 = (m >> 16) ? mk<R>(-ph.x, -ph.y) : ph;                                   \
+    const C<R> ph2 = ((m >> 16) != 0) != (msign < 0) ? mk<R>(-ph.x, -ph.y) : ph;           \
     _Pragma("unroll") for (int q = 0; q < RC; ++q) if (r0 + q < R_) {                        \
       const int64_t row = (int64_t)(r0 + q) * P + c * L;                                     \
       Yh[(row + (U)) * F + f1] = cmul(acc1[q], ph);                                          \
@@ -500,10 +501,10 @@ static int fft_prepare_t(tmat_ctx* ctx, LatOp* a, const char* name) {
   return TMAT_OK;
 }
 
-int lattice_fft_prepare(tmat_ctx* ctx, LatOp* a) {
+int lattice_fft_prepare(tmat_ctx* ctx, LatOp* a, const char* name) {
   if (a->K == 0 || !lattice_fft_fits(a->nx, a->ny, a->CX, a->CY)) return TMAT_OK;
-  if (a->fp32) return fft_prepare_t<float>(ctx, a, "fft_Bh32");
-  return fft_prepare_t<double>(ctx, a, "fft_Bh64");
+  if (a->fp32) return fft_prepare_t<float>(ctx, a, name ? name : "fft_Bh32");
+  return fft_prepare_t<double>(ctx, a, name ? name : "fft_Bh64");
 }
 
 template <typename R, int L, int MODE>
@@ -539,7 +540,7 @@ static int fft_apply_t(tmat_ctx* ctx, const LatOp& a, const void* xv, void* yv, 
     dim3 g((unsigned)cdiv(items, FFT_MUL_THREADS), 2);
     cudaEvent_t ev = timing_begin(ctx);
     kern<<<g, FFT_MUL_THREADS, msm, ctx->stream>>>((const C<R>*)a.fft_Bhat, Xh, Yh, Mx, My, R_, a.CX, a.CY,
-                                                   a.fft_mirror);
+                                                   a.fft_mirror, a.fft_mirror_sign);
     TM_LAUNCHED(ctx);
     // the block spectra of one frequency per mirror pair, the RHS spectra in and out
     const double mul_bytes = (double)sizeof(C<R>) * (items * 2.0 * L * L + 2.0 * nb * F);

@@ -337,7 +337,8 @@ extern "C" int tmat_adjoint(tmat_ctx* ctx, const tmat_solution* sol, const tmat_
 // coupling window's derivative included). The explicit term is
 //   2 Re sum_c conj(E_c) s_i . d/dq_i Phi_c(k(x_f - x_i)),
 // taken as a central difference of the fp64 wave functions in x_f (step 1e-4 / k; error
-// ~ (k h)^2 / 6 relative).
+// ~ (k h)^2 / 6 relative). The derivative operators are applied in fp64, by FFT
+// convolution with their own block spectra where the operator's grid fits.
 namespace tmat {
 
 // BX/BY[k][c][u'][u] = d/dd_x, d/dd_y of w(rho) e^{i(m_u' - m_u) phi} sum_q G[c][u][u'][q] h_q(k rho)
@@ -503,15 +504,18 @@ extern "C" int tmat_position_gradient(tmat_ctx* ctx, const tmat_solution* sol, c
     TM_TRY(to_internal(ctx, t, (const double2*)sdx.dev, da0, false, N));
     TM_TRY(to_internal(ctx, t, (const double2*)sdy.dev, da0 + N * P, false, N));
   }
-  // (A'_q s) and T mu - A'_q^T (1 . T mu) for q = x, y on the fp64 CUDA-core lattice kernel
+  // (A'_q s) and T mu - A'_q^T (1 . T mu) for q = x, y: by FFT convolution with their own
+  // block spectra where the operator's grid fits (the dy-derivative blocks are odd under the
+  // y mirror), else on the fp64 CUDA-core lattice kernel
   for (int q = 0; q < 2; ++q) {
     LatOp d = a;
     d.BT = q == 0 ? BX : BY;
     d.T = one;
-    d.use_fft = false;
     d.use_oz = false;
     d.use_tc = false;
     d.fp32 = false;
+    d.fft_mirror_sign = q == 0 ? 1 : -1;
+    if (a.use_fft) TM_TRY(lattice_fft_prepare(ctx, &d, q == 0 ? "pg_Bh_x" : "pg_Bh_y"));
     TM_TRY(lattice_apply(ctx, d, TMAT_OP_COUPLE, sol->s, ys + q * N * P, 1));
     TM_TRY(lattice_apply(ctx, d, TMAT_OP_ADJOINT, tmu, yz + q * N * P, 1));
   }

@@ -38,6 +38,8 @@ struct LatOp {
   // [2][L] per class member u: J(u) | p(u) << 16, J the m -> -m partner in the class and p
   // the polarisation; B_(dx,-dy) = D J B_(dx,dy) J D with D = diag((-1)^p)
   const int* fft_mirror = nullptr;
+  // +1, or -1 for blocks odd in dy (the dy-derivative blocks): B_(dx,-dy) = -D J B J D
+  int fft_mirror_sign = 1;
 };
 // An operator instance in one precision. kind 0: neighbour list; kind 1: lattice.
 struct Operator {
@@ -97,7 +99,8 @@ int lattice_tc2_apply(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, vo
 int lattice_tc_apply(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void* y, int R);
 int lattice_tc_prepare(tmat_ctx* ctx, LatOp* a, const double2* BT64);
 bool lattice_fft_fits(int nx, int ny, int CX, int CY);
-int lattice_fft_prepare(tmat_ctx* ctx, LatOp* a);
+// name: the scratch buffer of the block spectra (default: one per precision and context)
+int lattice_fft_prepare(tmat_ctx* ctx, LatOp* a, const char* name = nullptr);
 int lattice_fft_apply(tmat_ctx* ctx, const LatOp& a, int mode, const void* x, void* y, int R);
 bool lattice_oz_fits(int nmax, int CX);
 int lattice_oz_prepare(tmat_ctx* ctx, LatOp* a, const double2* BT64);

@@ -39,13 +39,19 @@ def _grad_case(nx, ny, nmax, cutoff, taper, beta_deg, xf):
     return g, go, sol, mu, xf, Ef
 
 
+@pytest.mark.parametrize("fft", [True, False])
 @pytest.mark.parametrize("nx,ny,nmax,cutoff,taper,beta", [(4, 3, 3, 1.2, 1.2, 10.0), (3, 3, 2, 0.0, 0.0, 0.0),
                                                          (5, 2, 3, 1.6, 0.6, 20.0)])
-def test_position_gradient_vs_oracle(nx, ny, nmax, cutoff, taper, beta):
+def test_position_gradient_vs_oracle(nx, ny, nmax, cutoff, taper, beta, fft):
     """Every pair or a windowed cutoff, normal and oblique incidence (the incident term),
-    ragged lattices: the adjoint gradient against central differences of direct solves."""
+    ragged lattices, derivative operators by FFT convolution or by the direct kernel: the
+    adjoint gradient against central differences of direct solves."""
     xf = np.array([0.6, 0.3, 2.5])
-    g, go, *_ = _grad_case(nx, ny, nmax, cutoff, taper, beta, xf)
+    ctx().set_lattice_fft(fft)
+    try:
+        g, go, *_ = _grad_case(nx, ny, nmax, cutoff, taper, beta, xf)
+    finally:
+        ctx().set_lattice_fft(True)
     assert np.max(np.abs(go)) > 1e-3
     assert rel_l2(g, go) <= 1e-6
 
