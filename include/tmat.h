@@ -48,7 +48,7 @@ extern "C" {
 #endif
 
 #define TMAT_OK 0
-#define TMAT_EINVAL (-1)     /* bad size, nmax outside 1..6, NaN input, non-coplanar positions */
+#define TMAT_EINVAL (-1)     /* bad size, nmax outside 1..6, NaN input, non-coplanar lattice */
 #define TMAT_ENOMEM (-3)     /* device allocation failed */
 #define TMAT_ENOCONV (-4)    /* iteration cap reached; outputs hold the best iterate */
 #define TMAT_EBREAKDOWN (-5) /* GMRES breakdown with a non-zero residual */
@@ -241,7 +241,11 @@ enum {
  * taper 0 gives w = 1). precision: TMAT_PREC_FP64 (complex128 arithmetic) or
  * TMAT_PREC_MIXED (complex64 arithmetic; x and y are still complex128 here);
  * TMAT_PREC_FP64_TC only on the lattice (tmat_apply_lattice).
- * Positions must be coplanar. */
+ * Coplanar positions (equal z) use the parity-class split of the blocks; otherwise every
+ * block is formed in full from the 3-D coupling constants (nmax <= 5, TMAT_ENOTSUP above;
+ * blocks in fp64, vectors in the requested precision). The same holds for tmat_solve on
+ * the neighbour path (the lattice path needs a common plane: TMAT_EINVAL) and for
+ * tmat_adjoint of such a solution. Non-finite coordinates: TMAT_EINVAL. */
 int tmat_apply(tmat_ctx* ctx, int op, int precision, const double* pos, int64_t N, double k,
                int nmax, const tmat_c128* T_diag, const int64_t* row_ptr, const int32_t* col,
                double cutoff, double taper, const tmat_c128* x, int R, tmat_c128* y);

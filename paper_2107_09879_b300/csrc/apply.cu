@@ -181,6 +181,148 @@ static int dispatch_nmax(tmat_ctx* ctx, const NbrOp& a, const void* x, void* y, 
   return TMAT_OK;
 }
 
+// ---- general 3-D positions ------------------------------------------------------
+// Without a common plane the blocks do not split into parity classes. The block of pair
+// (i, j) is formed in full from the 3-D coupling constants: xi(k d) with
+//   alpha[n][n'] (= xi[n][n'] = xi[L+n][L+n']) = e^{i mu phi} sum_q a5[n][n'][q] h_q(k r) Pbar_q^{|mu|}(cos theta),
+//   beta[n][n']  (= xi[n][L+n'] = xi[L+n][n'])  the same with b5, mu = m - m',
+// and applied as (A x)_i = sum_j xi(k(x_i - x_j))^T x_j (forward) or
+// (A^T z)_i = sum_j xi(k(x_j - x_i)) z_j (adjoint). One block of threads per target;
+// block entries in fp64, vectors in the operator's precision.
+constexpr int NBR3_THREADS = 128;
+template <typename R, int NMAX, int OP>
+__global__ void __launch_bounds__(NBR3_THREADS)
+apply_nbr3d_kernel(const double* __restrict__ pos, int64_t N, double k, const C<R>* __restrict__ T,
+                   const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                   const C<R>* __restrict__ x, C<R>* __restrict__ y, int nrhs, int64_t rhs_stride,
+                   const double2* __restrict__ a5, const double2* __restrict__ b5, const int* __restrict__ perm,
+                   double cutoff, double taper) {
+  constexpr int L = NMAX * (NMAX + 2), P = 2 * L, Q = 2 * NMAX + 1;
+  static_assert(P <= NBR3_THREADS, "one output per thread");
+  __shared__ double2 al[L * L], be[L * L];
+  __shared__ double2 h[Q];
+  __shared__ double Pq[Q][Q];
+  __shared__ double2 eph[2 * Q - 1];
+  __shared__ double2 xs[MAXR][P];  // source coefficients in flat order
+  const int64_t i = blockIdx.x;
+  if (i >= N) return;
+  const int tid = threadIdx.x;
+  const int fo = tid < P ? perm[tid] : 0;  // flat index of this thread's output (internal index tid)
+  const int po = fo / L, no = fo % L;
+  double2 acc[MAXR];
+#pragma unroll
+  for (int r = 0; r < MAXR; ++r) acc[r] = make_double2(0, 0);
+  const int64_t jb = row_ptr[i], je = row_ptr[i + 1];
+  for (int64_t e = jb; e < je; ++e) {
+    const int64_t j = col[e];
+    const double sg = OP == 1 ? -1.0 : 1.0;  // adjoint: d = x_j - x_i
+    const double dx = sg * (pos[3 * i] - pos[3 * j]), dy = sg * (pos[3 * i + 1] - pos[3 * j + 1]),
+                 dz = sg * (pos[3 * i + 2] - pos[3 * j + 2]);
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    const double ct = dz / r, st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    const double rho = sqrt(dx * dx + dy * dy);
+    const double cp = rho > 0 ? dx / rho : 1.0, sp = rho > 0 ? dy / rho : 0.0;
+    const double w = taper_weight(r, cutoff, taper);
+    if (tid == 0) {
+      double2 hh[Q];
+      hankel_up<double, Q>(k * r, hh);
+      for (int q = 0; q < Q; ++q) h[q] = cscale(hh[q], w);
+      double2 ee = make_double2(1, 0), e1 = make_double2(cp, sp);
+      for (int mu = 0; mu < Q; ++mu) {
+        eph[Q - 1 + mu] = ee;
+        eph[Q - 1 - mu] = cconj(ee);
+        ee = cmul(ee, e1);
+      }
+    }
+    if (tid < Q) {  // Pbar_q^mu(cos theta), mu = tid, upward in q
+      const int mu = tid;
+      double df = 1.0, f2 = 1.0;
+      for (int t = 1; t < 2 * mu; t += 2) df *= t;
+      for (int t = 2; t <= 2 * mu; ++t) f2 *= t;
+      double pprev = 0.0, pcur = sqrt((2 * mu + 1) / (2.0 * f2)) * df * pow(st, (double)mu);
+      for (int q = 0; q < mu; ++q) Pq[q][mu] = 0.0;
+      Pq[mu][mu] = pcur;
+      for (int q = mu + 1; q < Q; ++q) {
+        const double a = sqrt((4.0 * q * q - 1) / ((double)q * q - (double)mu * mu));
+        const double b = sqrt(((q - 1.0) * (q - 1.0) - (double)mu * mu) / (4.0 * (q - 1.0) * (q - 1.0) - 1));
+        const double pn = a * (ct * pcur - b * pprev);
+        pprev = pcur;
+        pcur = pn;
+        Pq[q][mu] = pn;
+      }
+    }
+    for (int t = tid; t < nrhs * P; t += NBR3_THREADS) {
+      const int rr = t / P, u = t % P;
+      C<R> v = x[rr * rhs_stride + j * P + u];
+      if (OP == 1) v = cmul(v, T[j * P + u]);
+      xs[rr][perm[u]] = make_double2((double)v.x, (double)v.y);
+    }
+    __syncthreads();
+    for (int t = tid; t < L * L; t += NBR3_THREADS) {
+      const int n = t / L, np = t % L;
+      int l = 1, lp = 1;
+      while ((l + 1) * (l + 1) - 1 <= n) ++l;
+      while ((lp + 1) * (lp + 1) - 1 <= np) ++lp;
+      const int m = n + 1 - l * (l + 1), mp = np + 1 - lp * (lp + 1);
+      const int mu = m - mp, amu = abs(mu);
+      double2 a_ = make_double2(0, 0), b_ = make_double2(0, 0);
+      for (int q = abs(l - lp); q <= l + lp; ++q) {
+        if (amu > q) continue;
+        const double2 hp = cscale(h[q], Pq[q][amu]);
+        cfma(a_, a5[((size_t)n * L + np) * Q + q], hp);
+        cfma(b_, b5[((size_t)n * L + np) * Q + q], hp);
+      }
+      al[t] = cmul(a_, eph[Q - 1 + mu]);
+      be[t] = cmul(b_, eph[Q - 1 + mu]);
+    }
+    __syncthreads();
+    if (tid < P) {
+      for (int np = 0; np < L; ++np) {
+        // forward: xi^T, entry (f', f) of xi; adjoint: xi, entry (f, f')
+        const double2 ga = OP == 1 ? al[no * L + np] : al[np * L + no];
+        const double2 gb = OP == 1 ? be[no * L + np] : be[np * L + no];
+        for (int rr = 0; rr < nrhs; ++rr) {
+          cfma(acc[rr], ga, xs[rr][po * L + np]);
+          cfma(acc[rr], gb, xs[rr][(1 - po) * L + np]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (tid < P) {
+    const int64_t o = i * P + tid;
+    for (int rr = 0; rr < nrhs; ++rr) {
+      const C<R> a = mk<R>((R)acc[rr].x, (R)acc[rr].y);
+      C<R> out;
+      if (OP == 2) out = a;
+      else if (OP == 0) out = csub(x[rr * rhs_stride + o], cmul(T[o], a));
+      else out = csub(x[rr * rhs_stride + o], a);
+      y[rr * rhs_stride + o] = out;
+    }
+  }
+}
+
+template <typename R, int OP>
+static int dispatch3d(tmat_ctx* ctx, const NbrOp& a, const void* x, void* y, int nrhs, int64_t stride) {
+  cudaEvent_t ev = timing_begin(ctx);
+  const unsigned grid = (unsigned)a.N;
+  const Tables* t = a.tab;
+#define N3(NM)                                                                                                    \
+  case NM:                                                                                                        \
+    apply_nbr3d_kernel<R, NM, OP><<<grid, NBR3_THREADS, 0, ctx->stream>>>(                                      \
+        a.pos, a.N, a.k, (const C<R>*)a.T, a.row_ptr, a.col, (const C<R>*)x, (C<R>*)y, nrhs, stride, t->d_a5, \
+        t->d_b5, t->d_perm, a.cutoff, a.taper);                                                                  \
+    break;
+  switch (a.nmax) {
+    N3(1) N3(2) N3(3) N3(4) N3(5)
+    default: return set_error(ctx, TMAT_ENOTSUP, "non-coplanar positions: nmax %d above 5", a.nmax);
+  }
+#undef N3
+  TM_LAUNCHED(ctx);
+  timing_end(ctx, "nbr_apply3d", ev);
+  return TMAT_OK;
+}
+
 // x, y: internal layout [R][N][P] in precision a.fp32 ? complex64 : complex128
 int nbr_apply(tmat_ctx* ctx, const NbrOp& a, int op, const void* x, void* y, int R_) {
   if (a.N == 0) return TMAT_OK;
@@ -191,7 +333,17 @@ int nbr_apply(tmat_ctx* ctx, const NbrOp& a, int op, const void* x, void* y, int
     const char* xp = (const char*)x + esz * stride * r0;
     char* yp = (char*)y + esz * stride * r0;
     int rc;
-    if (a.fp32) {
+    if (a.threed) {
+      if (a.fp32) {
+        if (op == TMAT_OP_FORWARD) rc = dispatch3d<float, 0>(ctx, a, xp, yp, nr, stride);
+        else if (op == TMAT_OP_ADJOINT) rc = dispatch3d<float, 1>(ctx, a, xp, yp, nr, stride);
+        else rc = dispatch3d<float, 2>(ctx, a, xp, yp, nr, stride);
+      } else {
+        if (op == TMAT_OP_FORWARD) rc = dispatch3d<double, 0>(ctx, a, xp, yp, nr, stride);
+        else if (op == TMAT_OP_ADJOINT) rc = dispatch3d<double, 1>(ctx, a, xp, yp, nr, stride);
+        else rc = dispatch3d<double, 2>(ctx, a, xp, yp, nr, stride);
+      }
+    } else if (a.fp32) {
       if (op == TMAT_OP_FORWARD) rc = dispatch_nmax<float, 0>(ctx, a, xp, yp, nr, stride);
       else if (op == TMAT_OP_ADJOINT) rc = dispatch_nmax<float, 1>(ctx, a, xp, yp, nr, stride);
       else rc = dispatch_nmax<float, 2>(ctx, a, xp, yp, nr, stride);
@@ -249,27 +401,29 @@ int from_internal(tmat_ctx* ctx, const Tables* t, const void* internal, bool fp3
   return TMAT_OK;
 }
 
-__global__ void coplanar_kernel(const double* __restrict__ pos, int64_t N, int* __restrict__ bad) {
+__global__ void position_flags_kernel(const double* __restrict__ pos, int64_t N, int* __restrict__ flags) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
-  if (z != pos[2] || x != x || y != y || z != z) atomicOr(bad, 1);
+  if (!isfinite(x) || !isfinite(y) || !isfinite(z)) atomicOr(flags, 2);
+  else if (z != pos[2]) atomicOr(flags, 1);
 }
 
-int check_coplanar(tmat_ctx* ctx, const double* d_pos, int64_t N, int* ok) {
-  *ok = 1;
+int position_flags(tmat_ctx* ctx, const double* d_pos, int64_t N, int* flags) {
+  *flags = 0;
   if (N == 0) return TMAT_OK;
-  int* flag;
-  TM_TRY(scratch(ctx, "coplanar_flag", sizeof(int), (void**)&flag));
-  TM_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
-  coplanar_kernel<<<(unsigned)cdiv(N, 256), 256, 0, ctx->stream>>>(d_pos, N, flag);
+  int* f;
+  TM_TRY(scratch(ctx, "posflag", sizeof(int), (void**)&f));
+  TM_CUDA(ctx, cudaMemsetAsync(f, 0, sizeof(int), ctx->stream));
+  position_flags_kernel<<<(unsigned)cdiv(N, 256), 256, 0, ctx->stream>>>(d_pos, N, f);
   TM_LAUNCHED(ctx);
   int* pin = (int*)ctx->pinned;
-  TM_CUDA(ctx, cudaMemcpyAsync(pin, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  TM_CUDA(ctx, cudaMemcpyAsync(pin, f, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  *ok = pin[0] ? 0 : 1;
+  *flags = pin[0];
   return TMAT_OK;
 }
+
 
 // T diagonal (API layout, complex128) -> internal layout in the kernel precision
 int prepare_T(tmat_ctx* ctx, const Tables* t, const double2* T_api, int64_t N, bool fp32, const char* name, void** out) {
@@ -297,9 +451,9 @@ extern "C" int tmat_apply(tmat_ctx* ctx, int op, int precision, const double* po
   const int P = t->P;
   Staged sp, sT, sr, sc, sx, sy;
   TM_TRY(stage_in(ctx, "st_pos", pos, sizeof(double) * 3 * N, &sp));
-  int ok;
-  TM_TRY(check_coplanar(ctx, (const double*)sp.dev, N, &ok));
-  if (!ok) return set_error(ctx, TMAT_EINVAL, "tmat_apply: positions must be coplanar (equal z) and finite");
+  int pflags;
+  TM_TRY(position_flags(ctx, (const double*)sp.dev, N, &pflags));
+  if (pflags & 2) return set_error(ctx, TMAT_EINVAL, "tmat_apply: positions must be finite");
   TM_TRY(stage_in(ctx, "st_T", T_diag, sizeof(double2) * N * P, &sT));
   TM_TRY(stage_in(ctx, "st_rowptr", row_ptr, sizeof(int64_t) * (N + 1), &sr));
   int64_t nnz = 0;
@@ -331,6 +485,7 @@ extern "C" int tmat_apply(tmat_ctx* ctx, int op, int precision, const double* po
   a.tab = t;
   a.cutoff = cutoff;
   a.taper = taper;
+  a.threed = (pflags & 1) != 0;  // not coplanar: full 3-D blocks
   TM_TRY(nbr_apply(ctx, a, op, xi, yi, R));
   TM_TRY(from_internal(ctx, t, yi, fp32, (double2*)sy.dev, (int64_t)R * N));
   TM_TRY(finish_out(ctx, &sy));

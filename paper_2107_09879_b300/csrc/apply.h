@@ -16,6 +16,7 @@ struct NbrOp {
   const int32_t* col = nullptr;
   const Tables* tab = nullptr;
   double cutoff = 0, taper = 0;  // coupling window (taper 0: hard cutoff)
+  bool threed = false;           // positions not coplanar: full 3-D blocks (apply_nbr3d_kernel)
 };
 
 int nbr_apply(tmat_ctx* ctx, const NbrOp& a, int op, const void* x, void* y, int R);
@@ -25,7 +26,8 @@ int nbr_apply(tmat_ctx* ctx, const NbrOp& a, int op, const void* x, void* y, int
 int to_internal(tmat_ctx* ctx, const Tables* t, const double2* api, void* internal, bool fp32, int64_t rows);
 int from_internal(tmat_ctx* ctx, const Tables* t, const void* internal, bool fp32, double2* api, int64_t rows);
 
-// 1 if every z equals pos[2] and no coordinate is NaN, else 0 (synchronises)
-int check_coplanar(tmat_ctx* ctx, const double* d_pos, int64_t N, int* ok);
+// flags: bit 0 some z differs from pos[2] (not coplanar), bit 1 a non-finite coordinate
+// (synchronises)
+int position_flags(tmat_ctx* ctx, const double* d_pos, int64_t N, int* flags);
 
 }  // namespace tmat

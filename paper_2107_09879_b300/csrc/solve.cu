@@ -23,6 +23,7 @@ struct tmat_solution {
   float2* T32 = nullptr;
   int64_t* row_ptr = nullptr;
   int32_t* col = nullptr;
+  bool threed = false;    // positions not coplanar (neighbour path with full 3-D blocks)
   double2* a0 = nullptr;  // RHS 0
   double2* s = nullptr;   // RHS 0
 };
@@ -82,10 +83,11 @@ static void free_solution(tmat_solution* s) {
 
 static int make_nbr_ops(const Tables* t, const double* d_pos, int64_t N, double k, int nmax, const int64_t* rp,
                         const int32_t* col, double cutoff, double taper, const double2* T64, const float2* T32,
-                        bool mixed, OpPair* ops) {
+                        bool mixed, OpPair* ops, bool threed = false) {
   NbrOp a;
   a.cutoff = cutoff;
   a.taper = taper;
+  a.threed = threed;
   a.pos = d_pos;
   a.N = N;
   a.k = k;
@@ -183,9 +185,12 @@ extern "C" int tmat_solve(tmat_ctx* ctx, const double* pos, int64_t N, double wa
   }
   Staged spos, sT, sa, ss;
   TM_TRY(stage_in(ctx, "st_pos", pos, sizeof(double) * 3 * N, &spos));
-  int ok;
-  TM_TRY(check_coplanar(ctx, (const double*)spos.dev, N, &ok));
-  if (!ok) return set_error(ctx, TMAT_EINVAL, "tmat_solve: positions must be coplanar (equal z) and finite");
+  int pflags;
+  TM_TRY(position_flags(ctx, (const double*)spos.dev, N, &pflags));
+  if (pflags & 2) return set_error(ctx, TMAT_EINVAL, "tmat_solve: positions must be finite");
+  const bool threed = (pflags & 1) != 0;
+  if (threed && path == TMAT_PATH_LATTICE)
+    return set_error(ctx, TMAT_EINVAL, "tmat_solve: the lattice path needs coplanar positions");
   TM_TRY(stage_in(ctx, "st_T", T_diag, sizeof(double2) * N * P, &sT));
   TM_TRY(stage_in(ctx, "st_a0", a0, sizeof(double2) * R * N * P, &sa));
   TM_TRY(stage_out(ctx, "st_s", s_out, sizeof(double2) * R * N * P, &ss));
@@ -203,7 +208,7 @@ extern "C" int tmat_solve(tmat_ctx* ctx, const double* pos, int64_t N, double wa
     TM_TRY(scratch(ctx, "sv_col", sizeof(int32_t) * (nnz + 1), (void**)&col));
     TM_TRY(build_neighbors(ctx, (const double*)spos.dev, N, opts->cutoff, rp, col, &nnz));
     TM_TRY(make_nbr_ops(t, (const double*)spos.dev, N, k, nmax, rp, col, opts->cutoff, opts->taper,
-                        (const double2*)T64, (const float2*)T32, mixed, &ops));
+                        (const double2*)T64, (const float2*)T32, mixed, &ops, threed));
   } else {
     TM_TRY(make_lattice_ops(ctx, t, (const double*)spos.dev, N, k, opts->lattice_nx, opts->lattice_ny,
                             opts->lattice_pitch, opts->cutoff, opts->taper, (const double2*)T64, (const float2*)T32, mixed, &ops,
@@ -236,6 +241,7 @@ extern "C" int tmat_solve(tmat_ctx* ctx, const double* pos, int64_t N, double wa
     so->lattice_nx = opts->lattice_nx;
     so->lattice_ny = opts->lattice_ny;
     so->lattice_pitch = opts->lattice_pitch;
+    so->threed = threed;
     int rc = TMAT_OK;
     do {
       if ((rc = dmalloc_copy(ctx, &so->pos, spos.dev, sizeof(double) * 3 * N))) break;
@@ -291,7 +297,7 @@ extern "C" int tmat_adjoint(tmat_ctx* ctx, const tmat_solution* sol, const tmat_
   OpPair ops;
   if (sol->path == TMAT_PATH_NEIGHBOUR) {
     TM_TRY(make_nbr_ops(t, sol->pos, N, sol->k, sol->nmax, sol->row_ptr, sol->col, sol->cutoff, sol->taper, sol->T64,
-                        sol->T32, mixed, &ops));
+                        sol->T32, mixed, &ops, sol->threed));
   } else {
     TM_TRY(make_lattice_ops(ctx, t, sol->pos, N, sol->k, sol->lattice_nx, sol->lattice_ny, sol->lattice_pitch,
                             sol->cutoff, sol->taper, sol->T64, sol->T32, mixed, &ops,

@@ -118,12 +118,12 @@ def test_apply_neighbour_fp64_and_fp32(nmax, nx, ny, cutoff, R, op):
     assert rel_l2(y32, ref) <= C64_APPLY_TOL
 
 
-def test_apply_rejects_non_coplanar():
+def test_apply_rejects_non_finite_positions():
     from paper_2107_09879_b300 import _lib
     pos, T, x = _apply_case(3, 3, 2, 1.0, 5, 1)
-    pos = pos.copy()
-    pos[4, 2] = 0.1
     rp, col = ctx().tmat_neighbors(pos, 1.0)
+    pos = pos.copy()
+    pos[4, 2] = float("nan")
     with pytest.raises(_lib.TMatError) as e:
         ctx().tmat_apply(0, 0, pos, K0, 2, T, rp, col, x)
     assert e.value.code == _lib.EINVAL
