@@ -388,6 +388,50 @@ def bench_sweep(ctx, torch, inner_tol=0.1):
             "note": "sampled sub-regions (corner, edge, 2 interior) timed; full sweep extrapolated x400 from their mean"}
 
 
+def bench_padding(ctx, torch):
+    """Padding (buffer-ring) convergence of the sub-region decomposition, the synthetic
+    analog of the paper's padding study: an 80 x 80 array (nmax 3, smooth radius map, cutoff 6
+    with a raised-cosine window, jinc sources sampling a normally incident x-polarised plane
+    wave at z0 = -1) solved whole and as 16 sub-regions of 20 x 20 with rings of 0..16 pitches;
+    error of the summed field on a detector line 10 wavelengths above the array, and of the
+    intensity at its brightest point, against the whole-array solve (fp64 throughout)."""
+    from paper_2107_09879_b300 import _lib
+    n, nmax, z0, cut = 80, 3, -1.0, 6.0
+    r = W.smooth_radius_map(n, n, W.BASE_SEED + 6)
+    at = np.zeros((n * n, 3))
+    at[:, 0], at[:, 1] = r, 2.0
+    pos = W.lattice_positions(n, n)
+    src = np.zeros((1, n * n, 2), complex)
+    src[0, :, 0] = np.exp(1j * 2 * math.pi * z0)
+    pts = np.array([[x, 19.75, 10.0] for x in np.linspace(5.0, 35.0, 32)])
+    opts = _lib.make_opts(tol=1e-11, restart=200, max_iter=4000, cutoff=cut, taper=cut, precision=_lib.PREC_FP64,
+                          path=_lib.PATH_LATTICE, lattice_nx=n, lattice_ny=n, lattice_pitch=PITCH)
+    T = ctx.tmat_build(at, 1.0, 1.0, nmax)
+    a0 = ctx.tmat_incident_jinc(pos, 1.0, 1.0, nmax, np.ascontiguousarray(pos[:, :2]), src, z0, precision=0,
+                                src_pitch=PITCH)
+    s, info, _, rc = ctx.tmat_solve(pos, 1.0, 1.0, nmax, T, a0, opts)
+    full = ctx.tmat_field(pos, 1.0, 1.0, nmax, s[0], pts)
+    I_full = np.sum(np.abs(full) ** 2, axis=1)
+    peak = int(np.argmax(I_full))
+    sopts = _lib.make_opts(tol=1e-11, restart=200, max_iter=4000, cutoff=cut, taper=cut, precision=_lib.PREC_FP64)
+    rows = []
+    for buf in (0, 2, 4, 8, 16):
+        sw = _lib.make_sweep(nx=n, ny=n, pitch=PITCH, core_x=20, core_y=20, buffer=buf, z0=z0)
+        t0 = time.perf_counter()
+        E, sinfo, src_rc = ctx.tmat_sweep(sw, at, 1.0, 1.0, nmax, src, sopts, pts)
+        dt = time.perf_counter() - t0
+        E = E[0]
+        I = np.sum(np.abs(E) ** 2, axis=1)
+        rows.append({"buffer_pitches": buf, "buffer_wavelengths": buf * PITCH,
+                     "rel_field_error": float(np.linalg.norm(E - full) / np.linalg.norm(full)),
+                     "peak_intensity_rel_error": float(abs(I[peak] - I_full[peak]) / I_full[peak]),
+                     "seconds": dt})
+    return {"workload": "padding_80x80_nmax3_cutoff6_core20_fp64", "whole_array_iterations": info.iterations,
+            "rows": rows,
+            "note": "16 sub-regions of 20 x 20; field on 32 detector points at height 10; the whole-array "
+                    "solve (lattice path, fp64) is the reference"}
+
+
 def fp64_plain_estimate(ctx, torch, step_inputs, opts_kw, krylov_iters, iters=6):
     """The plain complex128 GPU solve of the same workload, bounded: `iters` fp64 GMRES
     iterations timed, scaled to the mixed run's Krylov count (an estimate, labelled so)."""
@@ -548,6 +592,10 @@ def run_ours(args, rank, world):
         out["adjoint_50x50"] = bench_adjoint(ctx, torch)
         out["served"] = bench_served(args, torch)
         out["sweep_1200x1200"] = bench_sweep(ctx, torch)
+        try:
+            out["padding_study"] = bench_padding(ctx, torch)
+        except Exception as exc:  # a study, not the headline: report it rather than lose the line
+            out["padding_study"] = {"error": repr(exc)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, matvecs)
     return out
