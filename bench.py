@@ -36,8 +36,26 @@ PITCH = 0.5
 METRIC = "solves/s + p50/p99 latency; T-matvec GFLOP/s, mixed vs FP64 at 1e-6 rel err"
 UNIT = "solves/s"
 TOL = 1e-7  # refinement stops at ||r|| / ||b|| <= 1e-7, so the solution error is <= 1e-6
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
-HBM_PEAK_GBS = 6451.5  # measured copy bandwidth of the B300s (MEASURED_PEAKS.json)
+HBM_FALLBACK_GBS = 6400.0  # used only when the measured-peaks file is absent
+
+
+def measured_peaks():
+    """HBM copy bandwidth and bf16 rates measured on this machine type (MEASURED_PEAKS.json
+    beside this file), else the fallback figure, with a note saying which."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return {"hbm_gbs": float(m["hbm_gbs"]), "bf16_tflops": float(m["bf16_tflops"]),
+                "bf16_tflops_sustained": float(m.get("bf16_tflops_sustained", m["bf16_tflops"])),
+                "note": "of measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": HBM_FALLBACK_GBS, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+                "note": "of fallback"}
+
+
+PEAKS = measured_peaks()
+FMA_PEAKS = {}  # fp32/fp64 FMA rates, probed on the device at start-up
+HBM_PEAK_GBS = PEAKS["hbm_gbs"]
 
 
 def workload(size=200):
@@ -122,15 +140,14 @@ class ClockSampler:
 
 
 # DRAM bytes (read + write) / algorithmic bytes of one ncu capture of each HBM-bound kernel as
-# it stands, scaled to the timed launches by their algorithmic bytes (traffic grows with the
-# bytes a launch must move): profiles/arnoldi_dcgs2_100x100_nmax4.md (dot and update passes),
-# profiles/lattice_fft_200x200_nmax4.md (block product). Set an entry to None when its kernel
-# changes.
+# it stands (dot and update passes on a 100 x 100 solve, the block product on the 200 x 200
+# lattice), scaled to the timed launches by their algorithmic bytes (traffic grows with the
+# bytes a launch must move). Set an entry to None when its kernel changes.
 TRAFFIC_RATIO = {"arnoldi_dots32": (490.18e6 + 4.41e6) / (62 * 2 * 480000 * 8),
                  "arnoldi_update32": (468.52e6 + 13.44e6) / (63 * 2 * 480000 * 8),
                  "lattice_fft_mul32": (390.22e6 + 40.69e6) / 405.01e6}
-# DRAM bytes per launch of the direct-path kernels (profiles/lattice_tc2_200x200_nmax4.md) and
-# of the block product (profiles/lattice_fft_200x200_nmax4.md)
+# DRAM bytes per launch of the direct-path window-view kernel and of the block product
+# (one ncu capture each on the 200 x 200 lattice)
 MEASURED_TRAFFIC = {"lattice_tc2_kernel<4,0>": 238.0e6 + 23.0e6,
                     "fft_mul_kernel<float,24,0,2>": 390.22e6 + 40.69e6}
 
@@ -140,13 +157,13 @@ def roofline(kern_name, achieved, launches, avg_ms, flop_per_launch):
     if "tcgen05" in kern_name:
         # TF32 dense peak of measured: bf16 burst 1736 TFLOP/s x nominal TF32/BF16 ratio 1.1/2.25.
         # 3xTF32 executes 3 tensor GEMMs per algorithmic product, so frac <= 1/3 by construction.
-        peak = 1736.0 * 1.1 / 2.25
-        note = "TF32 dense: measured bf16 burst 1736 x nominal 1.1/2.25 (of measured)"
+        peak = PEAKS["bf16_tflops"] * 1.1 / 2.25
+        note = f"TF32 dense: bf16 burst {PEAKS['bf16_tflops']} x nominal 1.1/2.25 ({PEAKS['note']})"
         bound = "tensor"
         extra = {"tensor_flop_per_algorithmic_flop": 3,
                  "tensor_pipe_frac": (3 * achieved / peak) if achieved else None}
     else:
-        peak, note = FP32_PEAK_TFLOPS, "FP32 FMA issue rate: 148 SMs x 128 lanes x 2 flop x 2.032 GHz (derived)"
+        peak, note = FMA_PEAKS.get("fp32_tflops"), "FP32 FMA issue rate probed by tmat_measure_fma_peak (measured)"
         bound = "alu"
     traffic = next((v for k, v in MEASURED_TRAFFIC.items() if kern_name.startswith(k)), None)
     out = {"kernel": kern_name, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -154,6 +171,26 @@ def roofline(kern_name, achieved, launches, avg_ms, flop_per_launch):
            "avg_launch_ms": avg_ms, "flop_per_launch": flop_per_launch, "peak_note": note}
     out.update(extra)
     return out
+
+
+def fft_apply_work(nx, ny, c, L, R):
+    """Work of one complex64 FFT-convolution apply on an nx x ny lattice with offsets up to c
+    sites: flops (row transforms at 5 n log2 n, block products at 8 flop per complex MAC) and
+    bytes (every pass's reads and writes; operands alone)."""
+    Mx = 1 << (nx + c - 1).bit_length()
+    My = 1 << (ny + c - 1).bit_length()
+    nb, F, N = R * 2 * L, Mx * My, nx * ny
+    lg = lambda n: n.bit_length() - 1
+    fft = 2 * nb * (ny * 5 * Mx * lg(Mx) + Mx * 5 * My * lg(My))
+    mul = 8.0 * F * 2 * L * L * R
+    e = 8  # bytes per complex64
+    items = Mx * (My // 2 + 1)
+    bhat = e * items * 2 * L * L
+    grid, tmpb, spec = nb * N * e, nb * Mx * ny * e, nb * F * e
+    passes = (2 * grid) + (grid + tmpb) + (tmpb + spec) + (bhat + 2 * spec) + (spec + tmpb) + (tmpb + grid) + \
+             (grid + grid + N * 2 * L * e + grid)
+    return {"flop_per_apply": float(fft + mul), "pass_bytes": float(passes),
+            "operand_bytes": float(bhat + 2 * grid + N * 2 * L * e), "grid": [Mx, My]}
 
 
 def roofline_hbm(hbm, step_total_ms):
@@ -167,24 +204,23 @@ def roofline_hbm(hbm, step_total_ms):
             "traffic": (ratio * v["bytes"] / v["launches"]) if ratio else None,
             "launches": v["launches"], "avg_launch_ms": v["total_ms"] / v["launches"],
             "bytes_per_launch": v["bytes"] / v["launches"], "share_of_timed_region": v["total_ms"] / step_total_ms,
-            "peak_note": "STREAM-style copy bandwidth of MEASURED_PEAKS.json (of measured)"}
+            "peak_note": f"STREAM-style copy bandwidth ({PEAKS['note']})"}
 
 
-def cpu_baseline(wl, matvecs_per_solve, budget_s=12.0):
-    """The oracle (plain fp64 numpy, test infrastructure) on a bounded sample:
-    rows of one operator application for both incidences, extrapolated to the
-    full matvec and to the solve's number of operator applications."""
-    from oracle import geometry, mie, system
+def _oracle_rows(targets, budget_s, size=200):
+    """Oracle rows of one operator application (both incidences) for the given target
+    sites of the headline workload, until `budget_s` has passed: (rows done, seconds).
+    Inputs are rebuilt from their seeds, so a worker process needs nothing passed in."""
+    from oracle import mie, system
+    wl = workload(size)
     pos, nmax, cutoff = wl["pos"], wl["w"]["nmax"], wl["w"]["cutoff"]
     k = 2 * math.pi
     N = len(pos)
     rng = np.random.default_rng(0)
     x = (rng.normal(size=(2, N, 48)) + 1j * rng.normal(size=(2, N, 48))) * 0.1
-    centre = [(100 + dy) * 200 + 100 + dx for dy in range(-8, 8) for dx in range(-8, 8)]
-    # neighbour rows of the sampled targets only (the oracle's definition, restricted)
     t0 = time.perf_counter()
-    rows_done = 0
-    for i in centre:
+    done = 0
+    for i in targets:
         d = pos - pos[i]
         d2 = d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]
         d2 = d2 + d[:, 2] * d[:, 2]
@@ -196,16 +232,67 @@ def cpu_baseline(wl, matvecs_per_solve, budget_s=12.0):
         Ti[i] = mie.tmatrix_diag(nmax, k, wl["w"]["radius"][i], 2.0)
         for q in range(2):
             system.apply_K_rows(nmax, k, pos, Ti, x[q], (rp, js), [i])
-        rows_done += 1
+        done += 1
         if time.perf_counter() - t0 > budget_s:
             break
-    dt = time.perf_counter() - t0
-    per_matvec = dt / rows_done * N
-    per_solve = per_matvec * matvecs_per_solve
-    return {"value": 1.0 / per_solve, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{rows_done} interior target rows of one operator application (both incidences, "
-                      f"{dt:.1f} s), extrapolated x{N / rows_done:.0f} to one application and "
-                      f"x{matvecs_per_solve} applications per solve (the GPU run's count)"}
+    return done, time.perf_counter() - t0
+
+
+def _oracle_rows_worker(arg):
+    targets, budget_s = arg
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    _oracle_rows(targets[:1], 0.0)  # warm-up: tables and imports outside the timed rows
+    return _oracle_rows(targets, budget_s)
+
+
+def _cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+CENTRE_ROWS = [(100 + dy) * 200 + 100 + dx for dy in range(-8, 8) for dx in range(-8, 8)]
+
+
+def oracle_rows_all_cores(budget_s):
+    """Oracle rows on every host core: one spawned process per core (spawn, never fork,
+    after CUDA has started), each on its own share of the sampled targets."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    rows = CENTRE_ROWS * max(1, (4 * n) // len(CENTRE_ROWS) + 1)
+    shares = [rows[i::n] for i in range(n)]
+    with mp.get_context("spawn").Pool(n) as pool:
+        res = pool.map(_oracle_rows_worker, [(sh, budget_s) for sh in shares])
+    rate = sum(d / t for d, t in res if t > 0)
+    return rate, n, sum(d for d, _ in res)
+
+
+def cpu_baseline(wl, matvecs_per_solve, budget_s=12.0, all_cores=True):
+    """The oracle (plain fp64 numpy, test infrastructure) on a bounded sample:
+    rows of one operator application for both incidences, extrapolated to the
+    full matvec and to the solve's number of operator applications; on one core
+    and on every host core."""
+    N = len(wl["pos"])
+    done, dt = _oracle_rows(CENTRE_ROWS, budget_s)
+    per_solve = dt / done * N * matvecs_per_solve
+    out = {"value": 1.0 / per_solve, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{done} interior target rows of one operator application (both incidences, "
+                     f"{dt:.1f} s on one core), extrapolated x{N / done:.0f} to one application and "
+                     f"x{matvecs_per_solve} applications per solve (the GPU run's count)",
+           "cpu_model": _cpu_model(), "nproc": os.cpu_count()}
+    if all_cores:
+        try:
+            rate, n, rows = oracle_rows_all_cores(max(2.0, budget_s / 3))
+            out["all_cores"] = {"value": rate / (N * matvecs_per_solve), "unit": UNIT, "cores": n,
+                                "sample": f"{rows} target rows over {n} spawned processes "
+                                          f"({max(2.0, budget_s / 3):.0f} s each), same extrapolation"}
+        except Exception as exc:  # a baseline, not the headline: report why it is missing
+            out["all_cores"] = {"error": repr(exc)}
+    return out
 
 
 def max_over_ranks(value, world, device):
@@ -432,25 +519,121 @@ def bench_padding(ctx, torch):
                     "solve (lattice path, fp64) is the reference"}
 
 
-def fp64_plain_estimate(ctx, torch, step_inputs, opts_kw, krylov_iters, iters=6):
-    """The plain complex128 GPU solve of the same workload, bounded: `iters` fp64 GMRES
-    iterations timed, scaled to the mixed run's Krylov count (an estimate, labelled so)."""
+def study_inputs(n, torch):
+    """The n x n lower-left corner of the 200 x 200 workload on the device, with 64 detector
+    points on a line 20 wavelengths above the middle of that corner."""
+    wl = workload(n)
+    half = 0.5 * PITCH * (n - 1)
+    pts = np.array([[x, half, 20.0] for x in np.linspace(0.2 * half, 1.8 * half, 64)])
+    tt = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return wl, tt(wl["pos"]), tt(wl["atoms"]), tt(wl["dirs"]), tt(wl["pols"]), tt(pts)
+
+
+def bench_window_study(ctx, torch, n, precision, tol, cases, max_iter=4000, restart=300):
+    """The coupling operator of an n x n corner of the benchmark lattice under several cutoff
+    readings, against the every-pair operator (the paper's, App. I-D): iterations to `tol`,
+    and the relative L2 error of the coefficients and of the scattered field on the detector
+    line against the every-pair solution. `cases`: (label, cutoff, taper); cutoff 0 = every pair."""
+    from paper_2107_09879_b300 import _lib
+    wl, pos, atoms, dirs, pols, pts = study_inputs(n, torch)
+    nmax = wl["w"]["nmax"]
+    T = ctx.tmat_build(atoms, 1.0, 1.0, nmax)
+    a0 = ctx.tmat_incident_planewave(pos, 1.0, 1.0, nmax, dirs, pols)
+    rows, ref_s, ref_E = [], None, None
+    for label, cut, tap in cases:
+        opts = _lib.make_opts(tol=tol, restart=restart, max_iter=max_iter, cutoff=cut, taper=tap,
+                              precision=precision, inner_tol=0.2 if precision == _lib.PREC_MIXED else 0.0,
+                              path=_lib.PATH_LATTICE, lattice_nx=n, lattice_ny=n, lattice_pitch=PITCH)
+        ctx.tmat_solve(pos, 1.0, 1.0, nmax, T, a0, _lib.make_opts(**{**{f: getattr(opts, f) for f, _ in opts._fields_},
+                                                                       "max_iter": 2}))  # spectra + basis
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s, info, _, rc = ctx.tmat_solve(pos, 1.0, 1.0, nmax, T, a0, opts)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        E = torch.stack([ctx.tmat_field(pos, 1.0, 1.0, nmax, s[q].contiguous(), pts) for q in range(s.shape[0])])
+        row = {"operator": label, "cutoff": cut, "taper": tap, "iterations": info.iterations,
+               "converged": bool(info.converged), "rel_residual": max(info.rel_residual[q] for q in range(info.n_rhs)),
+               "seconds": dt}
+        if ref_s is None:
+            ref_s, ref_E = s.clone(), E.clone()
+        else:
+            row["coef_rel_err_vs_every_pair"] = float(torch.linalg.vector_norm(s - ref_s) / torch.linalg.vector_norm(ref_s))
+            row["field_rel_err_vs_every_pair"] = float(torch.linalg.vector_norm(E - ref_E) / torch.linalg.vector_norm(ref_E))
+        rows.append(row)
+    return {"workload": f"lattice_{n}x{n}_nmax{nmax}_2rhs_{'fp64' if precision == _lib.PREC_FP64 else 'mixed'}",
+            "tol": tol, "rows": rows}
+
+
+WINDOW_CASES = [("every pair", 0.0, 0.0), ("hard cutoff 8", 8.0, 0.0), ("window c8 tau1", 8.0, 1.0),
+                ("window c8 tau2", 8.0, 2.0), ("window c8 tau4", 8.0, 4.0), ("window c8 tau8", 8.0, 8.0),
+                ("window c12 tau4", 12.0, 4.0), ("window c16 tau8", 16.0, 8.0)]
+
+
+def run_window_study(args):
+    import torch
+    from paper_2107_09879_b300 import _lib
+    ctx = _lib.Context(0, None)
+    out = {"small": bench_window_study(ctx, torch, args.study_size, _lib.PREC_FP64, 1e-10, WINDOW_CASES,
+                                       max_iter=args.study_max_iter)}
+    if args.study_full:
+        out["full"] = bench_window_study(ctx, torch, 200, _lib.PREC_MIXED, TOL,
+                                         [c for c in WINDOW_CASES if c[0] != "hard cutoff 8"],
+                                         max_iter=args.study_max_iter)
+    return out
+
+
+def fp64_plain(ctx, torch, step_inputs, opts_kw, s_mixed, steps=1):
+    """The plain complex128 GPU solve of the headline workload to the same tolerance (complex128
+    FFT apply, complex128 vectors, fp64 CGS2 Arnoldi), timed in full, and its difference from the
+    mixed solution."""
     from paper_2107_09879_b300 import _lib
     pos, atoms, dirs, pols = step_inputs
     kw = dict(opts_kw)
-    kw.update(precision=_lib.PREC_FP64, max_iter=iters)
+    kw.update(precision=_lib.PREC_FP64)
     opts = _lib.make_opts(**kw)
     T = ctx.tmat_build(atoms, 1.0, 1.0, 4)
     a0 = ctx.tmat_incident_planewave(pos, 1.0, 1.0, 4, dirs, pols)
-    ctx.tmat_solve(pos, 1.0, 1.0, 4, T, a0, opts)  # warm-up (allocates the fp64 basis)
-    dt, res = _wall(lambda: ctx.tmat_solve(pos, 1.0, 1.0, 4, T, a0, opts), torch.cuda.synchronize)
-    it = res[1].iterations
-    per_it = dt / (it + 1)  # the cycle ends with one true-residual application
-    est = per_it * (krylov_iters + 1)
-    return {"ms_per_iteration": per_it * 1e3, "timed_iterations": it, "est_seconds_per_solve": est,
-            "est_solves_per_s": 1.0 / est,
-            "note": f"estimate: fp64 iteration time x {krylov_iters} iterations (the mixed run's Krylov count); "
-                    "the fp64 solve to the same tolerance needs at least that many"}
+    ctx.tmat_solve(pos, 1.0, 1.0, 4, T, a0, _lib.make_opts(**dict(kw, max_iter=2)))  # spectra + basis
+    times, res = [], None
+    for _ in range(steps):
+        dt, res = _wall(lambda: ctx.tmat_solve(pos, 1.0, 1.0, 4, T, a0, opts), torch.cuda.synchronize)
+        times.append(dt)
+    s, info, _, rc = res
+    rel = float(torch.linalg.vector_norm(s_mixed - s) / torch.linalg.vector_norm(s))
+    return {"solves_per_s": 1.0 / statistics.mean(times), "seconds_per_solve": statistics.mean(times),
+            "iterations": info.iterations, "converged": bool(info.converged),
+            "rel_residual": max(info.rel_residual[q] for q in range(info.n_rhs)), "timed_solves": steps,
+            "mixed_vs_fp64_rel_l2": rel,
+            "note": "complex128 solve of the headline workload to the same tolerance, timed whole (Mie build and "
+                    "incident coefficients excluded); mixed_vs_fp64_rel_l2 = ||s_mixed - s_fp64|| / ||s_fp64||"}
+
+
+def bench_every_pair(ctx, torch, steps=2):
+    """The headline lattice with every pair coupled (the paper's operator, App. I-D; no cutoff):
+    the same mixed solve through the FFT convolution on a 512 x 512 grid."""
+    from paper_2107_09879_b300 import _lib
+    wl, pos, atoms, dirs, pols, pts = study_inputs(200, torch)
+    opts = _lib.make_opts(tol=TOL, restart=300, max_iter=4000, cutoff=0.0, taper=0.0, precision=_lib.PREC_MIXED,
+                          inner_tol=0.2, path=_lib.PATH_LATTICE, lattice_nx=200, lattice_ny=200, lattice_pitch=PITCH)
+    rec = []
+
+    def one():
+        T = ctx.tmat_build(atoms, 1.0, 1.0, 4)
+        a0 = ctx.tmat_incident_planewave(pos, 1.0, 1.0, 4, dirs, pols)
+        s, info, _, rc = ctx.tmat_solve(pos, 1.0, 1.0, 4, T, a0, opts)
+        E = ctx.tmat_field(pos, 1.0, 1.0, 4, s[0], pts)
+        rec.append(info)
+        return rc
+    one()
+    times = [_wall(one, torch.cuda.synchronize)[0] for _ in range(steps)]
+    info = rec[-1]
+    return {"workload": "lattice_200x200_nmax4_every_pair_2rhs_mixed", "solves_per_s": 1.0 / statistics.mean(times),
+            "seconds_per_solve": statistics.mean(times), "iterations": info.iterations,
+            "refinements": info.refinements, "converged": bool(info.converged),
+            "rel_residual": max(info.rel_residual[q] for q in range(info.n_rhs)),
+            "note": "every pair of the 40,000 spheres coupled (no cutoff, no window): FFT convolution on a "
+                    "512 x 512 grid; same step as the headline (build, incident, solve, field)"}
 
 
 def run_ours(args, rank, world):
@@ -461,6 +644,8 @@ def run_ours(args, rank, world):
     ctx = _lib.Context(dev, None)
     ctx.set_tensor_cores(0 if args.cuda_cores else args.tc_variant)
     ctx.set_lattice_fft(not args.direct)
+    FMA_PEAKS["fp32_tflops"] = _lib.tmat_measure_fma_peak(dev, _lib.PREC_MIXED)
+    FMA_PEAKS["fp64_tflops"] = _lib.tmat_measure_fma_peak(dev, _lib.PREC_FP64)
     wl = workload(args.size)
     w = wl["w"]
     nmax, cutoff = w["nmax"], w["cutoff"]
@@ -563,6 +748,7 @@ def run_ours(args, rank, world):
     avg32 = ms32 / max(n32, 1)
     achieved = flop_per_launch / (avg32 * 1e-3) / 1e12 if n32 else None
     matvecs = int(round(statistics.mean(it))) + int(round(statistics.mean(ref)))
+    fft_work = fft_apply_work(wl["nx"], wl["ny"], int(round(cutoff / PITCH)), 24, R) if "FFT" in (kern_name or "") else None
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -572,22 +758,36 @@ def run_ours(args, rank, world):
                    "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before every step"},
         "p50_ms": per_step[len(per_step) // 2], "p99_ms": per_step[min(len(per_step) - 1, int(0.99 * len(per_step)))],
         "gmres_iterations_per_solve": statistics.mean(it), "refinements_per_solve": statistics.mean(ref),
-        "tmatvec_gflops": (flop_per_launch / (avg32 * 1e-3) / 1e9) if n32 else None,
+        "tmatvec_gflops": (fft_work["flop_per_apply"] / (avg32 * 1e-3) / 1e9) if (n32 and fft_work) else None,
         "roofline": (roofline_hbm(hbm, total_ms) if hbm else
                      roofline(kern_name, achieved, n32, avg32, flop_per_launch)),
         "hbm_kernels": {k: dict(v, achieved_gbs=v["bytes"] / (v["total_ms"] * 1e-3) / 1e9,
                                 frac=v["bytes"] / (v["total_ms"] * 1e-3) / 1e9 / HBM_PEAK_GBS) for k, v in hbm.items()},
-        "operator_apply": {"path": kern_name, "launches": n32, "avg_ms": avg32,
-                           "direct_sum_equivalent_tflops": achieved},
+        "operator_apply": dict({"path": kern_name, "launches": n32, "avg_ms": avg32}, **(
+            {"flop_per_apply": fft_work["flop_per_apply"], "achieved_tflops": fft_work["flop_per_apply"] / (avg32 * 1e-3) / 1e12,
+             "fp32_peak_tflops": FMA_PEAKS.get("fp32_tflops"),
+             "pass_bytes_per_apply": fft_work["pass_bytes"], "operand_bytes_per_apply": fft_work["operand_bytes"],
+             "achieved_gbs_pass_bytes": fft_work["pass_bytes"] / (avg32 * 1e-3) / 1e9, "hbm_peak_gbs": HBM_PEAK_GBS,
+             "aside_direct_sum_equivalent_tflops": achieved,
+             "note": "flop: 5 n log2 n per n-point complex row transform (4 passes) + 8 flop per complex MAC of the "
+                     "per-frequency block products; pass bytes: every pass's reads and writes (the FFT "
+                     "intermediates partly stay in L2); operand bytes: x, y, T and the block spectra once. The "
+                     "aside is the direct sum's flop count (8 P^2/2 per directed pair and RHS) over the same time, "
+                     "work the FFT path does not do."} if fft_work else {"direct_sum_tflops": achieved})),
         "fp64_residual_kernel": res_kernel, "fp64_residual_launches": n64,
         "fp64_residual_avg_ms": (ms64 / n64) if n64 else None,
         "e2e": {"value": world * 1e3 / statistics.median(e2e_ms), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(gpu_launches),
+        "peaks": {"hbm_gbs": HBM_PEAK_GBS, "bf16_tflops": PEAKS["bf16_tflops"], "source": PEAKS["note"],
+                  "fp32_fma_tflops": FMA_PEAKS["fp32_tflops"], "fp64_fma_tflops": FMA_PEAKS["fp64_tflops"],
+                  "fma_source": "tmat_measure_fma_peak on this GPU at start-up (measured)"},
         "clocks": clk,
     }
     if not args.no_extras:
-        out["fp64_plain"] = fp64_plain_estimate(ctx, torch, dev_in[:4], opts_kw, matvecs - int(round(statistics.mean(ref))))
+        s_mixed, _ = step(*dev_in)
+        out["fp64_plain"] = fp64_plain(ctx, torch, dev_in[:4], opts_kw, s_mixed)
+        out["every_pair_200x200"] = bench_every_pair(ctx, torch)
         out["dense_8x8_fp64"] = bench_dense_fp64(ctx, torch)
         out["adjoint_50x50"] = bench_adjoint(ctx, torch)
         out["served"] = bench_served(args, torch)
@@ -668,23 +868,61 @@ def run_jinc_only(args):
     return out
 
 
+def launch_summary(path):
+    """Per-kernel launches, total device time and share of an ncu launch list
+    (`--metrics gpu__time_duration.sum --csv`); times there are serialised and cold-cache."""
+    import collections
+    import csv
+    scale = {"ns": 1e-6, "nsecond": 1e-6, "us": 1e-3, "usecond": 1e-3, "ms": 1.0, "msecond": 1.0, "s": 1e3,
+             "second": 1e3}
+    rows = list(csv.reader(open(path)))
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    hdr = rows[hi]
+    ki, mi, vi, ui = (hdr.index(x) for x in ("Kernel Name", "Metric Name", "Metric Value", "Metric Unit"))
+    agg = collections.defaultdict(lambda: [0, 0.0])
+    for r in rows[hi + 1:]:
+        if len(r) <= vi or r[mi] != "gpu__time_duration.sum":
+            continue
+        name = r[ki].split("(")[0].replace("void ", "")
+        agg[name][0] += 1
+        agg[name][1] += float(r[vi].replace(",", "")) * scale[r[ui]]
+    tot = sum(v[1] for v in agg.values())
+    lines = [f"{sum(v[0] for v in agg.values())} launches, {tot:.1f} ms device time (serialised, cold cache)",
+             f"{'kernel':72s} {'launches':>8s} {'total ms':>10s} {'share':>7s}"]
+    for k, (c, ms) in sorted(agg.items(), key=lambda kv: -kv[1][1]):
+        lines.append(f"{k[:72]:72s} {c:8d} {ms:10.2f} {100 * ms / tot:6.2f}%")
+    return "\n".join(lines)
+
+
 def run_reference(args, rank, world):
-    """The reference arm: the oracle (plain fp64 CPU), timed on the host cores."""
+    """The reference arm: the oracle (plain fp64 CPU, as it stands), timed on the host cores
+    (every core when the process pool starts; else one). Each step is a bounded sample of
+    oracle rows of the headline workload; `value` extrapolates it to solves/s."""
     if rank != 0:
         return None
     wl = workload()
-    per = []
-    base = None
+    N = len(wl["pos"])
+    rates, walls, cores = [], [], 1
     for k in range(args.warmup + args.steps):
-        base = cpu_baseline(wl, matvecs_per_solve=args.ref_matvecs, budget_s=3.0)
+        t0 = time.perf_counter()
+        try:
+            rate, cores, _ = oracle_rows_all_cores(2.0)
+        except Exception:
+            done, dt = _oracle_rows(CENTRE_ROWS, 2.0)
+            rate, cores = done / dt, 1
         if k >= args.warmup:
-            per.append(1.0 / base["value"])
-    value = 1.0 / statistics.mean(per)
+            rates.append(rate)
+            walls.append(time.perf_counter() - t0)
+    value = statistics.mean(rates) / (N * args.ref_matvecs)
+    sample = (f"per step: oracle rows of one operator application (both incidences) for 2 s on each of {cores} "
+              f"host cores, extrapolated x{N} rows and x{args.ref_matvecs} applications per solve")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(per) * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(walls) * 1e3,
+            "extrapolated_ms_per_solve": 1e3 / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "lattice_200x200_nmax4_cutoff8_2rhs_mixed", "spheres": 40000},
-            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1, "sample": base["sample"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": cores, "sample": sample,
+                             "cpu_model": _cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -708,6 +946,12 @@ def main():
                     help="lattice operator by the direct block-Toeplitz kernels instead of FFT convolution")
     ap.add_argument("--tc-variant", type=int, default=1, choices=[1, 2],
                     help="tensor-core lattice kernel: 1 window view (default), 2 gather")
+    ap.add_argument("--launch-summary", metavar="CSV", help="summarise an ncu launch list by kernel and exit")
+    ap.add_argument("--window-study", action="store_true",
+                    help="coupling-window study: every pair vs hard cutoff vs raised-cosine windows")
+    ap.add_argument("--study-size", type=int, default=60)
+    ap.add_argument("--study-max-iter", type=int, default=3000)
+    ap.add_argument("--study-full", action="store_true", help="window study also on the full 200 x 200 lattice")
     ap.add_argument("--jinc-only", action="store_true",
                     help="time one jinc group of the sweep's sub-region shape (complex64 and fp64 paths)")
     ap.add_argument("--inner-tol", type=float, default=0.2,
@@ -717,11 +961,17 @@ def main():
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.launch_summary:
+        print(launch_summary(args.launch_summary))
+        return
     if args.kernel_only:
         print(json.dumps(run_kernel_only(args)))
         return
     if args.jinc_only:
         print(json.dumps(run_jinc_only(args)))
+        return
+    if args.window_study:
+        print(json.dumps(run_window_study(args)))
         return
     if args.impl == "reference":
         if world > 1 and rank != 0:

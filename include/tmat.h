@@ -159,6 +159,13 @@ int tmat_ctx_kernel_time(tmat_ctx* ctx, const char* kind, int64_t* launches, dou
  * "lattice_fft_mul32", "lattice_fft_mul64". */
 int tmat_ctx_kernel_bytes(tmat_ctx* ctx, const char* kind, double* bytes);
 
+/* Measured FMA issue rate of `device` in TFLOP/s (2 flop per fused multiply-add), the
+ * denominator of the ALU-bound rooflines: precision TMAT_PREC_MIXED probes fp32 FMA,
+ * TMAT_PREC_FP64 probes fp64 FMA. Every thread runs 16 independent FMA chains; the grid
+ * fills every SM; the best of five ~5 ms launches on the legacy default stream of
+ * `device` (synchronous). Not part of the method: a measurement utility. */
+int tmat_measure_fma_peak(int device, int precision, double* tflops_out);
+
 /* ---- geometry (integer, bit-exact) -------------------------------------- */
 
 /* Interaction neighbour lists (a cutoff is this library's parameter; the paper
@@ -382,16 +389,22 @@ int tmat_position_gradient(tmat_ctx* ctx, const tmat_solution* sol, const tmat_c
  * or pinned host memory) and uses a fixed 1 MiB scratch array that lives in the
  * library's device image (every GPU that loads the library keeps it until the
  * process exits).
- *  - All array arguments must be device pointers on the current device; host
- *    pointers are rejected with TMAT_EINVAL. Work is issued on `cuda_stream`
- *    (a cudaStream_t of the current device, NULL = legacy default stream); the
- *    call does not synchronise.
+ *  - All array arguments must be device (or managed) memory of the current
+ *    device; host pointers and pointers into another GPU's memory are rejected
+ *    with TMAT_EINVAL. Work is issued on `cuda_stream` (a cudaStream_t of the
+ *    current device, NULL = legacy default stream); after the first call on a
+ *    device (below) a call does not synchronise.
  *  - M above TMAT_NOALLOC_FIELD_SLOTS / 3 points, N < 0, nmax outside
  *    1..TMAT_NMAX_MAX or a bad pointer returns TMAT_EINVAL before any work is
- *    issued (there is no context, so there is no error message).
- *  - The first call on each device looks up the scratch array's device address
- *    (a one-time set-up per device); make that first call before any stream
- *    capture begins.
+ *    issued (there is no context, so there is no error message). A CUDA error
+ *    left pending by the caller's earlier work is reported as TMAT_ECUDA and
+ *    left pending (not cleared); errors of this call's own launches are
+ *    consumed and reported as TMAT_ECUDA.
+ *  - The first call on each device does a one-time set-up: it looks up the
+ *    scratch array's device address and copies the Legendre recurrence
+ *    constants from host memory into the library's constant memory on
+ *    `cuda_stream`, then synchronises `cuda_stream`. Make that first call
+ *    before any stream capture begins.
  *  - All calls on one device share its scratch array: two calls whose work
  *    overlaps on that GPU (for example on two streams) race and give wrong
  *    results; order them (one stream, or events). Every scratch slot a call

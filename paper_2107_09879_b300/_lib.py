@@ -88,6 +88,7 @@ _SIGS = {
     "tmat_field_noalloc": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _i64, _vp],
     "tmat_adjoint": [_vp, _vp, _vp, _vp, _vp, _vp, ct.POINTER(SolveInfo)],
     "tmat_position_gradient": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "tmat_measure_fma_peak": [_int, _int, ct.POINTER(_d)],
 }
 EXPORTED = []
 for _name, _args in _SIGS.items():
@@ -324,6 +325,15 @@ class Context:
         self.check(lib.tmat_position_gradient(self.h, sol.h, ptr(mu), ptr(da0_dx), ptr(da0_dy), ptr(x_f), ptr(E_f),
                                               ptr(grad)))
         return grad
+
+
+def tmat_measure_fma_peak(device, precision):
+    """Measured FMA rate of `device` in TFLOP/s (PREC_MIXED: fp32, PREC_FP64: fp64)."""
+    v = ct.c_double()
+    rc = lib.tmat_measure_fma_peak(device, precision, ct.byref(v))
+    if rc != OK:
+        raise TMatError(rc, "tmat_measure_fma_peak failed")
+    return v.value
 
 
 class Solution:

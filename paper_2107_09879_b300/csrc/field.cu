@@ -395,6 +395,19 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 double2* g_noalloc_addr[kMaxDevices] = {nullptr};
 
+// True when p is device memory of device `dev`, or managed memory. A pointer into another
+// GPU's memory is refused: this entry point enables no peer access.
+bool device_ptr_on(const void* p, int dev) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // the error of this query only (no launch is pending: checked on entry)
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 // device address of the scratch array on the current device (one-time set-up)
 int noalloc_scratch(int dev, double2** out) {
   if (dev < 0 || dev >= kMaxDevices) return TMAT_EINVAL;
@@ -419,13 +432,16 @@ extern "C" int tmat_field_noalloc(void* cuda_stream, const double* pos, int64_t 
       !(wavelength > 0) || !(n_bg > 0))
     return TMAT_EINVAL;
   if (M == 0) return TMAT_OK;
-  if (!is_device_ptr(pts) || !is_device_ptr(E_out) || (N > 0 && (!is_device_ptr(pos) || !is_device_ptr(s))))
-    return TMAT_EINVAL;
+  // an error left pending by earlier work of the caller is reported, not consumed
+  if (cudaPeekAtLastError() != cudaSuccess) return TMAT_ECUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return TMAT_ECUDA;
   }
+  if (!device_ptr_on(pts, dev) || !device_ptr_on(E_out, dev) ||
+      (N > 0 && (!device_ptr_on(pos, dev) || !device_ptr_on(s, dev))))
+    return TMAT_EINVAL;
   double2* part = nullptr;
   int rc = noalloc_scratch(dev, &part);
   if (rc != TMAT_OK) return rc;
@@ -441,6 +457,7 @@ extern "C" int tmat_field_noalloc(void* cuda_stream, const double* pos, int64_t 
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const double k = 2.0 * M_PI * n_bg / wavelength;
   launch_field_n(nmax, dim3((unsigned)M, (unsigned)nchunk), st, pos, N, k, (const double2*)s, pts, M, false, part);
+  if (cudaGetLastError() != cudaSuccess) return TMAT_ECUDA;
   field_reduce_kernel<<<(unsigned)cdiv(M * 3, 128), 128, 0, st>>>(part, M, (int)nchunk, (double2*)E_out);
   if (cudaGetLastError() != cudaSuccess) return TMAT_ECUDA;
   return TMAT_OK;

@@ -303,10 +303,10 @@ int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_
   for (int d = 0; d < ndy; ++d)
     for (int a = dy_start[d]; a < dy_start[d + 1]; ++a)
       if (offs[a].x != offs[dy_start[d]].x + (a - dy_start[d])) dx_contiguous = false;
-  std::vector<int> negs(K);
-  for (int a = 0; a < K; ++a)
-    for (int b = 0; b < K; ++b)
-      if (offs[b].x == -offs[a].x && offs[b].y == -offs[a].y) negs[a] = b;
+  // index of -o for every offset o (the set is symmetric): a (2nx-1) x (2ny-1) lookup grid
+  std::vector<int> negs(K), slot((size_t)(2 * nx - 1) * (2 * ny - 1), -1);
+  for (int a = 0; a < K; ++a) slot[(size_t)(offs[a].y + ny - 1) * (2 * nx - 1) + (offs[a].x + nx - 1)] = a;
+  for (int a = 0; a < K; ++a) negs[a] = slot[(size_t)(ny - 1 - offs[a].y) * (2 * nx - 1) + (nx - 1 - offs[a].x)];
   const int L = t->L, LP = (L % 2) ? L + 1 : L;
   int2* d_off;
   int* d_neg;

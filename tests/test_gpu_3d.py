@@ -54,13 +54,14 @@ def test_solve_and_radius_gradient_3d(precision):
     s, info, sol, rc = ctx().tmat_solve(pos, 1.0, 1.0, nmax, T, a0, opts, keep=True)
     assert rc == 0
     To = np.array([mie.tmatrix_diag(nmax, K0, x, 2.0) for x in r])
-    so = system.solve_dense(nmax, K0, pos, To, a0[0], cutoff)
+    a0o = incident.planewave_incident(nmax, K0, pos, 0.0, 0.0, A)  # the oracle's own
+    so = system.solve_dense(nmax, K0, pos, To, a0o, cutoff)
     assert rel_l2(s[0], so) <= (1e-9 if precision == 0 else 1e-6)
     fom, v = ctx().tmat_point_fom(pos, 1.0, 1.0, nmax, s[0], xf, Einc)
     vo = adjoint.adjoint_source(nmax, K0, pos, so, xf, Einc)
     grad, mu, _ = ctx().tmat_adjoint(sol, v, dT, want_mu=True)
     dTo = np.array([mie.tmatrix_diag_dr(nmax, K0, x, 2.0) for x in r])
-    go, _ = adjoint.radius_gradient(nmax, K0, pos, To, dTo, a0[0], so, vo, cutoff=cutoff)
+    go, _ = adjoint.radius_gradient(nmax, K0, pos, To, dTo, a0o, so, vo, cutoff=cutoff)
     assert rel_l2(grad, go) <= (1e-9 if precision == 0 else 1e-6)
 
 

@@ -39,8 +39,7 @@ def test_autograd_matches_oracle_gradient(device):
     To = np.array([mie.tmatrix_diag(nmax, K0, x, 2.0) for x in r])
     dTo = np.array([mie.tmatrix_diag_dr(nmax, K0, x, 2.0) for x in r])
     from oracle import system
-    a0 = ctx().tmat_incident_planewave(pos, 1.0, 1.0, nmax, np.array([[0.0, 0.0]]),
-                                       np.array([[1.0, 0.0, 0.0]], dtype=complex))
+    a0 = incident.planewave_incident(nmax, K0, pos, 0.0, 0.0, np.array([1.0, 0.0, 0.0], dtype=complex))[None]
     so = system.solve_dense(nmax, K0, pos, To, a0[0], cutoff)
     Einc = prob.E_inc_f
     assert abs(fom.item() - adjoint.fom(nmax, K0, pos, so, xf, Einc)) <= 1e-9 * fom.item()

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from gpu_common import C64_APPLY_TOL, K0, atoms, ctx, rand_c, rel_l2
-from oracle import geometry, mie, system
+from oracle import incident, geometry, mie, system
 from paper_2107_09879_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -58,7 +58,8 @@ def test_lattice_solve_vs_oracle(precision, tol, bound):
     assert rc == 0 and info.converged
     To = np.array([mie.tmatrix_diag(nmax, K0, x, 2.0) for x in r])
     for q in range(2):
-        ref = system.solve_dense(nmax, K0, pos, To, a0[q], cutoff)
+        a0o = incident.planewave_incident(nmax, K0, pos, dirs[q, 0], dirs[q, 1], pols[q])  # the oracle's own
+        ref = system.solve_dense(nmax, K0, pos, To, a0o, cutoff)
         assert rel_l2(s[q], ref) <= bound
 
 
@@ -171,8 +172,10 @@ def test_fp64_tc_solve_vs_oracle_and_neighbour_path_refused():
     s, info, _, rc = ctx().tmat_solve(pos, 1.0, 1.0, nmax, T, a0, opts)
     assert rc == 0 and info.converged
     To = np.array([mie.tmatrix_diag(nmax, K0, x, 2.0) for x in r])
+    a0o = [incident.planewave_incident(nmax, K0, pos, b, 0.0, np.array([math.cos(b), 0, -math.sin(b)], complex))
+           for b in (0.0, 0.3)]  # the oracle's own incident coefficients
     with system.window(cutoff, cutoff):
-        ref = np.array([system.solve_dense(nmax, K0, pos, To, a0[q], cutoff) for q in range(2)])
+        ref = np.array([system.solve_dense(nmax, K0, pos, To, a0o[q], cutoff) for q in range(2)])
     assert rel_l2(s, ref) <= 1e-9
     opts.path = 1
     with pytest.raises(_lib.TMatError) as e:

@@ -21,8 +21,19 @@ def _problem(nx, ny, nmax, seed, angles=(0.0,), lo=0.08, hi=0.24, const_r=None):
     return pos, r, T, a0, dirs, pols
 
 
-def _oracle_solve(nmax, pos, r, a0, cutoff):
+def _oracle_a0(nmax, pos, angles):
+    """Incident coefficients computed by the oracle itself (never the GPU's): p-polarised
+    plane waves in the xz plane at the given angles."""
+    return np.array([incident.planewave_incident(nmax, K0, pos, math.radians(a), 0.0,
+                                                 incident.beta_hat(math.radians(a), 0.0)) for a in angles])
+
+
+def _oracle_solve(nmax, pos, r, a0, cutoff, angles=None):
+    """Oracle inputs -> oracle answer: T from the oracle's Mie, a0 from the oracle's plane-wave
+    expansion when `angles` is given (a0 is then used only for its shape)."""
     To = np.array([mie.tmatrix_diag(nmax, K0, x, 2.0) for x in r])
+    if angles is not None:
+        a0 = _oracle_a0(nmax, pos, angles)
     return np.array([system.solve_dense(nmax, K0, pos, To, a0[q], cutoff) for q in range(a0.shape[0])])
 
 
@@ -36,14 +47,14 @@ def test_dense_8x8_fp64_vs_oracle_lu():
     pos, r, T, a0, _, _ = _problem(8, 8, 3, 0, const_r=0.2)
     s, info, _, rc = ctx().tmat_solve(pos, 1.0, 1.0, 3, T, a0, _opts(tol=1e-10, cutoff=0.0, precision=0))
     assert rc == 0 and info.converged and info.rel_residual[0] <= 1e-10
-    ref = _oracle_solve(3, pos, r, a0, 0.0)
+    ref = _oracle_solve(3, pos, r, a0, 0.0, angles=(0.0,))
     assert rel_l2(s, ref) <= 1e-9
 
 
 @pytest.mark.parametrize("nmax,nx,ny,cutoff", [(3, 5, 4, 0.0), (4, 9, 7, 1.6), (5, 4, 3, 1.1)])
 def test_fp64_and_mixed_vs_oracle(nmax, nx, ny, cutoff):
     pos, r, T, a0, _, _ = _problem(nx, ny, nmax, 10 + nmax, angles=(0.0, 10.0))
-    ref = _oracle_solve(nmax, pos, r, a0, cutoff)
+    ref = _oracle_solve(nmax, pos, r, a0, cutoff, angles=(0.0, 10.0))
     s64, i64, _, rc = ctx().tmat_solve(pos, 1.0, 1.0, nmax, T, a0, _opts(tol=1e-11, cutoff=cutoff, precision=0))
     assert rc == 0 and rel_l2(s64, ref) <= 1e-9
     smx, imx, _, rc = ctx().tmat_solve(pos, 1.0, 1.0, nmax, T, a0,
@@ -55,7 +66,7 @@ def test_fp64_and_mixed_vs_oracle(nmax, nx, ny, cutoff):
 
 def test_restart_and_many_rhs():
     pos, r, T, a0, _, _ = _problem(6, 5, 3, 77, angles=(0.0, 3.0, 6.0, 9.0, 12.0))
-    ref = _oracle_solve(3, pos, r, a0, 1.2)
+    ref = _oracle_solve(3, pos, r, a0, 1.2, angles=(0.0, 3.0, 6.0, 9.0, 12.0))
     s, info, _, rc = ctx().tmat_solve(pos, 1.0, 1.0, 3, T, a0, _opts(tol=1e-11, cutoff=1.2, restart=4))
     assert rc == 0 and rel_l2(s, ref) <= 1e-9
 

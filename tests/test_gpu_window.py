@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from gpu_common import C64_APPLY_TOL, K0, atoms, ctx, rand_c, rel_l2
-from oracle import geometry, mie, system
+from oracle import incident, geometry, mie, system
 from paper_2107_09879_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -41,7 +41,9 @@ def test_windowed_solve_vs_oracle(path):
     a0 = ctx().tmat_incident_planewave(pos, 1.0, 1.0, nmax, np.array([[0.0, 0.0]]), np.array([[1, 0, 0]], complex))
     To = np.array([mie.tmatrix_diag(nmax, K0, x, 2.0) for x in r])
     with system.window(cutoff, cutoff):
-        ref = system.solve_dense(nmax, K0, pos, To, a0[0], cutoff)
+        ref = system.solve_dense(nmax, K0, pos, To,
+                                 incident.planewave_incident(nmax, K0, pos, 0.0, 0.0, np.array([1, 0, 0], complex)),
+                                 cutoff)
     for prec, tol, bound in ((0, 1e-11, 1e-9), (1, 1e-8, 1e-6)):
         opts = _lib.make_opts(tol=tol, cutoff=cutoff, taper=cutoff, precision=prec, path=path, lattice_nx=nx,
                               lattice_ny=ny, lattice_pitch=0.5)
