@@ -145,11 +145,10 @@ class ClockSampler:
 # bytes a launch must move). Set an entry to None when its kernel changes.
 TRAFFIC_RATIO = {"arnoldi_dots32": (490.18e6 + 4.41e6) / (62 * 2 * 480000 * 8),
                  "arnoldi_update32": (468.52e6 + 13.44e6) / (63 * 2 * 480000 * 8),
-                 "lattice_fft_mul32": (390.22e6 + 40.69e6) / 405.01e6}
+                 "lattice_fft_mul32": None}
 # DRAM bytes per launch of the direct-path window-view kernel and of the block product
 # (one ncu capture each on the 200 x 200 lattice)
-MEASURED_TRAFFIC = {"lattice_tc2_kernel<4,0>": 238.0e6 + 23.0e6,
-                    "fft_mul_kernel<float,24,0,2>": 390.22e6 + 40.69e6}
+MEASURED_TRAFFIC = {"lattice_tc2_kernel<4,0>": 238.0e6 + 23.0e6}
 
 
 def roofline(kern_name, achieved, launches, avg_ms, flop_per_launch):
@@ -643,7 +642,7 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     ctx = _lib.Context(dev, None)
     ctx.set_tensor_cores(0 if args.cuda_cores else args.tc_variant)
-    ctx.set_lattice_fft(not args.direct)
+    ctx.set_lattice_fft(0 if args.direct else args.fft_mode)
     FMA_PEAKS["fp32_tflops"] = _lib.tmat_measure_fma_peak(dev, _lib.PREC_MIXED)
     FMA_PEAKS["fp64_tflops"] = _lib.tmat_measure_fma_peak(dev, _lib.PREC_FP64)
     wl = workload(args.size)
@@ -707,7 +706,9 @@ def run_ours(args, rank, world):
             break
     hbm_kinds = {"arnoldi_dots32": "dots32_kernel<true> (Arnoldi dot pass, two targets)",
                  "arnoldi_update32": "dcgs2_update_kernel (Arnoldi update pass, two outputs)",
-                 "lattice_fft_mul32": "fft_mul_kernel<float,24,0,2> (block products, mirror pairs (kx, +-ky))"}
+                 "lattice_fft_mul32": ("fft_mul4_kernel<24,0> (block products, quad-mirror form: one symmetric matrix per "
+                                       "(+-kx, +-ky))" if args.fft_mode == 1 else
+                                       "fft_mul_kernel<float,24,0,2> (block products, mirror pairs (kx, +-ky))")}
     hbm = {}
     for kind, name in hbm_kinds.items():
         nk, msk = ctx.kernel_time(kind)
@@ -809,7 +810,7 @@ def run_kernel_only(args):
     from paper_2107_09879_b300 import _lib
     ctx = _lib.Context(0, None)
     ctx.set_tensor_cores(0 if args.cuda_cores else args.tc_variant)
-    ctx.set_lattice_fft(not args.direct)
+    ctx.set_lattice_fft(0 if args.direct else args.fft_mode)
     wl = workload()
     w = wl["w"]
     N, P, R = len(wl["pos"]), 48, 2
@@ -944,6 +945,8 @@ def main():
                     help="lattice side (200: the benchmark; smaller: its corner, for profiler captures)")
     ap.add_argument("--direct", action="store_true",
                     help="lattice operator by the direct block-Toeplitz kernels instead of FFT convolution")
+    ap.add_argument("--fft-mode", type=int, default=1, choices=[1, 2],
+                    help="FFT block products: 1 quad-mirror form (default), 2 mirror pairs")
     ap.add_argument("--tc-variant", type=int, default=1, choices=[1, 2],
                     help="tensor-core lattice kernel: 1 window view (default), 2 gather")
     ap.add_argument("--launch-summary", metavar="CSV", help="summarise an ncu launch list by kernel and exit")

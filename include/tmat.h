@@ -140,7 +140,10 @@ int tmat_ctx_set_timing(tmat_ctx* ctx, int enable);
  * ny + max|dy| <= 1024): y_i = sum_o B_o x_{i+o} as a circular convolution on a
  * zero-padded power-of-two grid, one L x L block product per frequency, in the
  * operator's precision (complex64 or complex128 arithmetic throughout). enable = 0
- * selects the direct block-Toeplitz kernels (tensor cores / CUDA cores). Default: 1.
+ * selects the direct block-Toeplitz kernels (tensor cores / CUDA cores). Default: 1,
+ * where the complex64 block products use the quad-mirror form (one symmetric matrix per
+ * frequency quadruple (+-kx, +-ky), a quarter of the spectra read per apply); enable = 2
+ * keeps the FFT with the mirror-pair products (one spectrum per pair (kx, +-ky)).
  * Timing kinds: "lattice_apply_fft32", "lattice_apply_fft64" (whole applies),
  * "lattice_fft_mul32", "lattice_fft_mul64" (the per-frequency block products). */
 int tmat_ctx_set_lattice_fft(tmat_ctx* ctx, int enable);

@@ -19,6 +19,7 @@ Modules
 specfun      spherical Bessel/Hankel, normalised Legendre, pi/tau, Wigner-3j
 vswf         vector spherical wave functions Phi, RPhi (App. I-A)
 mie          sphere T-matrix (closed-form special case of App. I-B) and dT/dr
+nullfield    null-field T-matrix of a scatterer bounded by a surface (App. I-B): cylinders
 translation  addition-theorem coefficients xi = alpha/beta (App. I-C)
 incident     plane-wave and jinc-source expansion coefficients (App. II)
 system       Maxwell operator (I - T A), dense assembly, LU, GMRES (App. I-C/D)

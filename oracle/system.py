@@ -213,3 +213,39 @@ def solve_gmres(nmax, k, pos, tdiag, a0, cutoff=0.0, tol=1e-13, restart=50, maxi
 
     x, its, rr = gmres(mv, b, tol=tol, restart=restart, maxiter=maxiter)
     return x.reshape(shape), its, rr
+
+
+# ----------------------------------------------------------------------------
+# Full per-scatterer T-blocks (App. I-B, Eq. def_tmatrix: s_i = T_i a_i with T_i a
+# P x P matrix, e.g. a null-field cylinder). The same system with block-diagonal
+# T = diag(T_1 .. T_N) instead of a diagonal:
+#     K = I - T A,  b = T a0;  adjoint (transpose) K^T = I - A^T T^T.
+# Tb has shape (N, P, P), rows = outgoing index, columns = incident index.
+# ----------------------------------------------------------------------------
+
+def apply_K_blocks(nmax, k, pos, Tb, x, nbr):
+    """y_i = x_i - T_i (A x)_i."""
+    Ax = apply_A(nmax, k, pos, x, nbr)
+    return x - np.einsum("nab,nb->na", Tb, Ax)
+
+
+def apply_KT_blocks(nmax, k, pos, Tb, x, nbr):
+    """y = x - A^T (T^T x), the transpose of apply_K_blocks."""
+    return x - apply_AT(nmax, k, pos, np.einsum("nba,nb->na", Tb, x), nbr)
+
+
+def dense_K_blocks(nmax, k, pos, Tb, nbr):
+    A = dense_A(nmax, k, pos, nbr)
+    N, P, _ = Tb.shape
+    Tfull = np.zeros((N * P, N * P), dtype=np.complex128)
+    for i in range(N):
+        Tfull[i * P:(i + 1) * P, i * P:(i + 1) * P] = Tb[i]
+    return np.eye(N * P, dtype=np.complex128) - Tfull @ A
+
+
+def solve_dense_blocks(nmax, k, pos, Tb, a0, cutoff=0.0):
+    """Direct solve of (I - T A) s = T a0 with full T-blocks (LU, the library step)."""
+    nbr = neighbours(pos, cutoff)
+    K = dense_K_blocks(nmax, k, pos, Tb, nbr)
+    b = np.einsum("nab,nb->na", Tb, a0).reshape(-1)
+    return np.linalg.solve(K, b).reshape(a0.shape)

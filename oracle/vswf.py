@@ -45,8 +45,9 @@ def _sph_to_cart(th, ph):
 
 def vswf(nmax, k, x, regular=False):
     """Phi (regular=False) or RPhi (regular=True) at the point x (3-vector,
-    relative to the expansion centre), wave number k. Returns complex array
-    of shape (P, 3): row p*L + n(l,m) holds the Cartesian vector."""
+    relative to the expansion centre), wave number k (complex allowed for RPhi:
+    the field inside a lossy scatterer). Returns complex array of shape (P, 3):
+    row p*L + n(l,m) holds the Cartesian vector."""
     x = np.asarray(x, dtype=np.float64)
     r = float(np.linalg.norm(x))
     if r == 0.0:
@@ -55,9 +56,14 @@ def vswf(nmax, k, x, regular=False):
     ph = math.atan2(x[1], x[0])
     rho = k * r
     if regular:
-        z = sph_jn_all(nmax, rho).real.astype(np.complex128)
+        # a complex wave number (lossy medium, inside a scatterer) keeps complex j_l
+        z = sph_jn_all(nmax, rho)
+        if np.imag(k) == 0:
+            z = z.real.astype(np.complex128)
     else:
-        z = sph_h1_all(nmax, rho)
+        if np.imag(k) != 0:
+            raise ValueError("outgoing waves need a real wave number")
+        z = sph_h1_all(nmax, float(np.real(rho)))
     # (rho z_l)'/rho = z_{l-1} - l z_l / rho
     P, pi, tau = legendre_norm(nmax, th)
     rhat, thhat, phhat = _sph_to_cart(th, ph)

@@ -161,8 +161,10 @@ class Context:
         self.check(lib.tmat_ctx_set_tensor_cores(self.h, int(on)))
 
     def set_lattice_fft(self, on):
-        """1: lattice operators by FFT convolution where the grid fits (default); 0: direct kernels."""
-        self.check(lib.tmat_ctx_set_lattice_fft(self.h, 1 if on else 0))
+        """1/True: lattice operators by FFT convolution where the grid fits, quad-mirror complex64 block
+        products (default); 2: FFT with the mirror-pair block products; 0/False: direct kernels."""
+        self.check(lib.tmat_ctx_set_lattice_fft(self.h, on if isinstance(on, int) and not isinstance(on, bool)
+                                                else (1 if on else 0)))
 
     def set_timing(self, on):
         self.check(lib.tmat_ctx_set_timing(self.h, 1 if on else 0))

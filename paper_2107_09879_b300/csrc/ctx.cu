@@ -180,7 +180,9 @@ extern "C" int64_t tmat_ctx_launch_count(const tmat_ctx* ctx) { return ctx ? ctx
 
 extern "C" int tmat_ctx_set_lattice_fft(tmat_ctx* ctx, int enable) {
   if (!ctx) return TMAT_EINVAL;
+  if (enable < 0 || enable > 2) return set_error(ctx, TMAT_EINVAL, "tmat_ctx_set_lattice_fft: enable must be 0, 1 or 2");
   ctx->lattice_fft = enable != 0;
+  ctx->fft_quad = enable == 1;
   return TMAT_OK;
 }
 

@@ -72,6 +72,7 @@ struct tmat_ctx {
   bool tensor_cores = true;  // use the tcgen05 kernels where they exist
   int tc_variant = 0;        // 0: window-view kernel where it fits, 1: gather kernel
   bool lattice_fft = true;   // lattice operators by FFT convolution where the grid fits
+  bool fft_quad = true;      // complex64 FFT block products in the quad-mirror form
   void* pinned = nullptr;  // small pinned host staging area (status words)
 };
 

@@ -334,8 +334,9 @@ int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_
   }
   const bool fft = ctx->lattice_fft && K > 0 && lattice_fft_fits(nx, ny, CX, CY);
   // mirror table of the class members for the FFT block product (lattice_fft.cu)
-  std::vector<int> mir(2 * L, 0);
+  std::vector<int> mir(2 * L, 0), sym(2 * L, 0);
   int* d_mir = nullptr;
+  int* d_sym = nullptr;
   if (fft) {
     for (int c = 0; c < 2; ++c)
       for (int u = 0; u < L; ++u) {
@@ -349,11 +350,15 @@ int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_
           if (t->perm[c * L + v] == f2) u2 = v;
         if (u2 < 0) return set_error(ctx, TMAT_ENOTSUP, "mirror partner missing in class %d", c);
         mir[c * L + u] = u2 | (p << 16);
+        sym[c * L + u] = u2 | ((m & 1) << 16) | (p << 17);
       }
     char nm[32];
     snprintf(nm, sizeof nm, "fft_mirror%d", t->nmax);
     TM_TRY(scratch(ctx, nm, sizeof(int) * 2 * L, (void**)&d_mir));
     TM_CUDA(ctx, cudaMemcpyAsync(d_mir, mir.data(), sizeof(int) * 2 * L, cudaMemcpyHostToDevice, ctx->stream));
+    snprintf(nm, sizeof nm, "fft_sym%d", t->nmax);
+    TM_TRY(scratch(ctx, nm, sizeof(int) * 2 * L, (void**)&d_sym));
+    TM_CUDA(ctx, cudaMemcpyAsync(d_sym, sym.data(), sizeof(int) * 2 * L, cudaMemcpyHostToDevice, ctx->stream));
   }
   // host copies above are from stack vectors: wait before they go out of scope
   TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -376,6 +381,7 @@ int make_lattice_ops(tmat_ctx* ctx, const Tables* t, const double* d_pos, int64_
   a.BT = B64;
   a.T = T64;
   a.fft_mirror = d_mir;
+  a.fft_sym = d_sym;
   if (fft) TM_TRY(lattice_fft_prepare(ctx, &a));
   ops->lat64 = a;
   a.use_fft = false;

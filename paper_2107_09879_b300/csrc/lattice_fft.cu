@@ -25,6 +25,7 @@
 // (Cooley and Tukey, Math. Comp. 19 (1965)): radix-16 register passes, then radix 4 (one
 // radix-2 stage first for odd powers of two), fp64 twiddles (cast for complex64).
 #include <cmath>
+#include <string>
 #include <vector>
 
 #include "dev.cuh"
@@ -446,6 +447,181 @@ fft_mul_kernel(const C<R>* __restrict__ Bh, const C<R>* __restrict__ Xh, C<R>* _
   }
 }
 
+// ---- quad-mirror block product (complex64) ---------------------------------------------
+// Besides the two mirror identities the blocks obey reciprocity, B_(-o) = J B_o^T J, and the
+// full inversion B_(-o) = Dm B_o Dm with Dm = diag((-1)^m); together B_o^T = S B_o S with
+// S = J Dm (an involution), so C_o = B_o S is symmetric. All of this is linear in the
+// blocks, so with the true spectra B^(f) (shift phase removed) and an item (kx, ky),
+// 0 <= kx <= Mx/2, 0 <= ky <= My/2, the one symmetric matrix C = B^(kx, ky) S gives the
+// products at all four frequencies f1 = (kx, ky), f2 = (kx, -ky), f3 = (-kx, ky),
+// f4 = (-kx, -ky), for the forward operator and its transpose:
+//   forward  Y(f1) = C (S X)         Y(f2) = Dy J C (Dx X)   Y(f3) = Dx J C (Dy X)   Y(f4) = Dm C (J X)
+//   adjoint  Y(f1) = J C (Dm X)      Y(f2) = Dy C (J Dx X)   Y(f3) = Dx C (J Dy X)   Y(f4) = J Dm C X
+// (adjoint: Y(f) = B^(-f)^T X(f)), with Dx = diag((-1)^(m+p)), Dy = diag((-1)^p). Every
+// input and output map is a signed permutation (J or identity, times one of the diagonal
+// signs, all J-invariant), so one read of C (one quarter of the full spectra) serves four
+// frequencies and both directions. C is staged per tile of NI consecutive ky by one bulk
+// copy into shared memory; thread (item, class, u) forms row u of Z = C W for the 4 x RC
+// columns W (the transformed inputs), reading C[v][u] = C[u][v] (consecutive u: no bank
+// conflicts) and the column values by broadcast.
+constexpr uint32_t FFT4_WAIT_LIMIT = 1u << 22;  // polls of a bounded mbarrier wait
+
+template <int L>
+struct Fft4Cfg {
+  static constexpr int NI = L <= 24 ? 4 : 2;  // items (consecutive ky) per tile
+  static constexpr int THREADS = NI * 2 * L;
+  static constexpr int RC = 2;                // RHS per pass
+  static constexpr int NCOL = 4 * RC;
+  static constexpr size_t C_BYTES = (size_t)NI * 2 * L * L * sizeof(float2);
+  static constexpr size_t W_BYTES = (size_t)NI * 2 * L * NCOL * sizeof(float2);
+  static constexpr size_t SMEM = C_BYTES + W_BYTES + 16;
+  static constexpr int MIN_BLOCKS = L <= 24 ? 4 : 2;  // resident CTAs per SM the registers allow
+};
+
+// sign selector: 0 none, 1 Dx = (-1)^(m+p), 2 Dy = (-1)^p, 3 Dm = (-1)^m
+__device__ __forceinline__ bool fft4_neg(int sel, int mpar, int p) {
+  return sel == 1 ? ((mpar ^ p) != 0) : sel == 2 ? (p != 0) : sel == 3 ? (mpar != 0) : false;
+}
+
+__device__ __forceinline__ bool fft4_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (uint32_t it = 0; it < FFT4_WAIT_LIMIT; ++it) {
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+template <int L, int MODE>
+__global__ void __launch_bounds__(Fft4Cfg<L>::THREADS, Fft4Cfg<L>::MIN_BLOCKS)
+fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, float2* __restrict__ Yh, int Mx, int My,
+                int R_, const int* __restrict__ sym, int* __restrict__ err) {
+  using Cfg = Fft4Cfg<L>;
+  constexpr int NI = Cfg::NI, RC = Cfg::RC, NCOL = Cfg::NCOL, P = 2 * L;
+  // per column k (frequency f1..f4): input permutation / sign, output permutation / sign
+  constexpr int IN_J[2][4] = {{1, 0, 0, 1}, {0, 1, 1, 0}};
+  constexpr int IN_S[2][4] = {{3, 1, 2, 0}, {3, 1, 2, 0}};
+  constexpr int OUT_J[2][4] = {{0, 1, 1, 0}, {1, 0, 0, 1}};
+  constexpr int OUT_S[2][4] = {{0, 2, 1, 3}, {0, 2, 1, 3}};
+  constexpr int D = MODE == 1 ? 1 : 0;
+  extern __shared__ __align__(128) unsigned char fsm4[];
+  float2* Cs = reinterpret_cast<float2*>(fsm4);                      // [NI][2][L][L]
+  float2* Ws = reinterpret_cast<float2*>(fsm4 + Cfg::C_BYTES);       // [NI][2][L][NCOL]
+  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(fsm4 + Cfg::C_BYTES + Cfg::W_BYTES);
+  const uint32_t cs_addr = (uint32_t)__cvta_generic_to_shared(Cs);
+  const int t = threadIdx.x;
+  const int it = t / (2 * L), c = (t / L) & 1, u = t % L;
+  const int64_t F = (int64_t)Mx * My;
+  const int hx = Mx >= 2 ? Mx / 2 + 1 : 1, hy = My >= 2 ? My / 2 + 1 : 1;
+  const int tpr = (hy + NI - 1) / NI;
+  const int64_t ntiles = (int64_t)hx * tpr;
+  const int su = sym[c * L + u];
+  const int Ju = su & 0xffff, mpar = (su >> 16) & 1, pp = (su >> 17) & 1;
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int kx = (int)(tile / tpr), ky0 = (int)(tile % tpr) * NI;
+    const int ni = min(NI, hy - ky0);
+    if (t == 0) {
+      const uint32_t bytes = (uint32_t)(ni * 2 * L * L * sizeof(float2));
+      const float2* src = Cq + ((int64_t)kx * hy + ky0) * 2 * L * L;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                   :: "r"(cs_addr), "l"(src), "r"(bytes), "r"(bar) : "memory");
+    }
+    const bool live = it < ni;
+    const int ky = ky0 + it;
+    const int kxm = (Mx - kx) % Mx, kym = (My - ky) % My;
+    // the four frequencies (column k) as (row, column) of the Mx x My grid; bit k of vmask:
+    // column k is a distinct frequency of a live item
+    const bool dy = kym != ky, dx = kxm != kx;
+    const unsigned vmask = live ? (1u | (dy ? 2u : 0u) | (dx ? 4u : 0u) | (dx && dy ? 8u : 0u)) : 0u;
+    auto freq = [&](int k) -> int64_t {
+      return (int64_t)((k & 2) ? kxm : kx) * My + ((k & 1) ? kym : ky);
+    };
+    float2* wrow = Ws + ((it * 2 + c) * L + u) * NCOL;
+    for (int r0 = 0; r0 < R_; r0 += RC) {
+      // this thread's row of the transformed inputs, all columns
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int q = 0; q < RC; ++q) {
+          float2 w = make_float2(0.f, 0.f);
+          if (((vmask >> k) & 1u) && r0 + q < R_) {
+            const int comp = IN_J[D][k] ? Ju : u;
+            w = Xh[((int64_t)(r0 + q) * P + c * L + comp) * F + freq(k)];
+            if (fft4_neg(IN_S[D][k], mpar, pp)) w = make_float2(-w.x, -w.y);
+          }
+          wrow[k * RC + q] = w;
+        }
+      int bad = 0;
+      if (r0 == 0) bad = !fft4_wait(bar, phase);
+      bad = __syncthreads_or(bad);
+      if (bad) {
+        if (t == 0) {
+          atomicAdd(err, 1);
+          fft4_wait(bar, phase);  // let the copy in flight land before the CTA leaves
+        }
+        return;
+      }
+      float2 acc[NCOL];
+#pragma unroll
+      for (int j = 0; j < NCOL; ++j) acc[j] = make_float2(0.f, 0.f);
+      const float2* Ci = Cs + (it * 2 + c) * L * L + u;
+      const float4* Wi = reinterpret_cast<const float4*>(Ws + (it * 2 + c) * L * NCOL);
+#pragma unroll 4
+      for (int v = 0; v < L; ++v) {
+        const float2 g = Ci[v * L];
+#pragma unroll
+        for (int j = 0; j < NCOL / 2; ++j) {
+          const float4 w2 = Wi[v * (NCOL / 2) + j];
+          cfma(acc[2 * j], g, make_float2(w2.x, w2.y));
+          cfma(acc[2 * j + 1], g, make_float2(w2.z, w2.w));
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int q = 0; q < RC; ++q)
+          if (((vmask >> k) & 1u) && r0 + q < R_) {
+            const int comp = OUT_J[D][k] ? Ju : u;
+            float2 z = acc[k * RC + q];
+            if (fft4_neg(OUT_S[D][k], mpar, pp)) z = make_float2(-z.x, -z.y);
+            Yh[((int64_t)(r0 + q) * P + c * L + comp) * F + freq(k)] = z;
+          }
+      __syncthreads();  // Ws (next RHS pass) and Cs (next tile) are overwritten next
+    }
+    phase ^= 1u;
+  }
+}
+
+// C[item][c][u][v] = ph(f1) Bs[(c L + u) L + J(v)][f1] (-1)^(m_v) from the stored spectra
+// (component-major, with the compact-grid shift phase, undone here); item = kx * hy + ky.
+__global__ void fft_pack_quad_kernel(const float2* __restrict__ Bs, int Mx, int My, int L, int CX, int CY,
+                                     const int* __restrict__ sym, float2* __restrict__ Cq) {
+  const int hy = My >= 2 ? My / 2 + 1 : 1, hx = Mx >= 2 ? Mx / 2 + 1 : 1;
+  const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int e = blockIdx.y;  // (c, u, v)
+  if (item >= (int64_t)hx * hy) return;
+  const int c = e / (L * L), u = (e / L) % L, v = e % L;
+  const int kx = (int)(item / hy), ky = (int)(item % hy);
+  const int64_t F = (int64_t)Mx * My, f1 = (int64_t)kx * My + ky;
+  const int64_t num = ((int64_t)kx * CX * My + (int64_t)ky * CY * Mx) % F;
+  double sn, cs;
+  sincospi(2.0 * (double)num / (double)F, &sn, &cs);
+  const int sv = sym[c * L + v];
+  const float2 b = Bs[((int64_t)(c * L + u) * L + (sv & 0xffff)) * F + f1];
+  float2 z = cmul(make_float2((float)cs, (float)sn), b);
+  if ((sv >> 16) & 1) z = make_float2(-z.x, -z.y);
+  Cq[(item * 2 + c) * L * L + u * L + v] = z;
+}
+
 // Forward 2-D transform of nb component grids [nb][ny][nx] into [nb][Mx][My] (via tmp).
 template <typename R>
 static int fft2_forward(tmat_ctx* ctx, const C<R>* grid, int nx, int ny, int Mx, int My, int64_t nb, C<R>* tmp,
@@ -498,6 +674,22 @@ static int fft_prepare_t(tmat_ctx* ctx, LatOp* a, const char* name) {
   a->fft_My = My;
   a->fft_Bhat = Bh;
   a->use_fft = true;
+  a->fft_C = nullptr;
+  if (sizeof(R) == 4 && a->fft_mirror_sign == 1 && a->fft_sym && ctx->fft_quad) {
+    const int hx = Mx >= 2 ? Mx / 2 + 1 : 1, hy = My >= 2 ? My / 2 + 1 : 1;
+    const int64_t items = (int64_t)hx * hy;
+    std::string cn = std::string(name) + "_quad";
+    float2* Cq;
+    int* err;
+    TM_TRY(scratch(ctx, cn.c_str(), sizeof(float2) * items * 2 * L * L, (void**)&Cq));
+    TM_TRY(scratch(ctx, "fft_quad_err", sizeof(int), (void**)&err));
+    TM_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+    dim3 g((unsigned)cdiv(items, 128), (unsigned)(2 * L * L));
+    fft_pack_quad_kernel<<<g, 128, 0, ctx->stream>>>((const float2*)Bh, Mx, My, L, a->CX, a->CY, a->fft_sym, Cq);
+    TM_LAUNCHED(ctx);
+    a->fft_C = Cq;
+    a->fft_err = err;
+  }
   return TMAT_OK;
 }
 
@@ -531,7 +723,28 @@ static int fft_apply_t(tmat_ctx* ctx, const LatOp& a, const void* xv, void* yv, 
   fft_embed_kernel<R, MODE == 1 ? 1 : 0><<<tg, tb, 0, ctx->stream>>>(x, T, nx, ny, P, R_, grid);
   TM_LAUNCHED(ctx);
   TM_TRY(fft2_forward<R>(ctx, grid, nx, ny, Mx, My, nb, w1, Xh, tw));
-  {
+  bool quad_done = false;
+  if constexpr (sizeof(R) == 4) {
+    if (a.fft_C) {
+      using Cfg = Fft4Cfg<L>;
+      auto kern = fft_mul4_kernel<L, MODE == 1 ? 1 : 0>;
+      if (Cfg::SMEM > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, Cfg::SMEM));
+      const int hx = Mx >= 2 ? Mx / 2 + 1 : 1, hy = My >= 2 ? My / 2 + 1 : 1;
+      const int64_t ntiles = (int64_t)hx * cdiv(hy, Cfg::NI);
+      int per_sm = 0;
+      TM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::THREADS, Cfg::SMEM));
+      const int64_t grid = std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * std::max(1, per_sm));
+      cudaEvent_t ev = timing_begin(ctx);
+      kern<<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, ctx->stream>>>((const float2*)a.fft_C, (const float2*)Xh,
+                                                                     (float2*)Yh, Mx, My, R_, a.fft_sym, a.fft_err);
+      TM_LAUNCHED(ctx);
+      // the quad-form spectra once, the RHS spectra in and out
+      const double mul_bytes = (double)sizeof(float2) * ((double)hx * hy * 2.0 * L * L + 2.0 * nb * F);
+      timing_end(ctx, "lattice_fft_mul32", ev, mul_bytes);
+      quad_done = true;
+    }
+  }
+  if (!quad_done) {
     constexpr int RC = (sizeof(R) == 4 && L <= 24) ? 2 : 1;
     const size_t msm = sizeof(C<R>) * 2 * (size_t)RC * L * FFT_MUL_THREADS;
     auto kern = fft_mul_kernel<R, L, MODE, RC>;

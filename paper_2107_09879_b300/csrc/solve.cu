@@ -111,9 +111,10 @@ static int make_nbr_ops(const Tables* t, const double* d_pos, int64_t N, double 
 
 // The tensor-core kernel counts CTAs that gave up on a bounded wait.
 static int check_tc_errors(tmat_ctx* ctx, const OpPair& ops) {
-  const int* counters[2] = {
+  const int* counters[3] = {
       (ops.have32 && ops.A32.kind == 1 && ops.lat32.use_tc) ? ops.lat32.tc_err : nullptr,
-      ops.have_oz ? ops.lat64oz.oz_err : nullptr};
+      ops.have_oz ? ops.lat64oz.oz_err : nullptr,
+      (ops.have32 && ops.A32.kind == 1 && ops.lat32.use_fft && ops.lat32.fft_C) ? ops.lat32.fft_err : nullptr};
   for (const int* c : counters) {
     if (!c) continue;
     int* pin = (int*)ctx->pinned;

@@ -40,6 +40,12 @@ struct LatOp {
   const int* fft_mirror = nullptr;
   // +1, or -1 for blocks odd in dy (the dy-derivative blocks): B_(dx,-dy) = -D J B J D
   int fft_mirror_sign = 1;
+  // [2][L] per class member u: J(u) | (m mod 2) << 16 | p << 17 (quad-mirror block product)
+  const int* fft_sym = nullptr;
+  // complex64 quad-mirror form of the spectra: per item (kx <= Mx/2, ky <= My/2) and class
+  // the symmetric matrix C = B^(kx, ky) S, S = J diag((-1)^m), item-major [items][2][L][L]
+  const void* fft_C = nullptr;
+  int* fft_err = nullptr;  // device counter of CTAs that gave up on a bounded wait
 };
 // An operator instance in one precision. kind 0: neighbour list; kind 1: lattice.
 struct Operator {

@@ -216,3 +216,27 @@ def test_fft_apply_matches_direct_and_oracle(nmax, nx, ny, cutoff, R, op, precis
     bound = 1e-12 if precision == 0 else C64_APPLY_TOL
     assert rel_l2(yf, ref) <= bound
     assert rel_l2(yf, yd) <= bound
+
+
+@pytest.mark.parametrize("nmax,nx,ny,cutoff,R", [(4, 37, 29, 3.0, 5), (3, 40, 3, 0.0, 2), (5, 13, 21, 2.2, 3),
+                                                 (6, 7, 9, 1.1, 1), (1, 6, 50, 4.0, 4)])
+@pytest.mark.parametrize("op", [0, 1, 2])
+def test_fft_quad_product_matches_mirror_pair_product(nmax, nx, ny, cutoff, R, op):
+    """The complex64 quad-mirror block product (one symmetric matrix per frequency quadruple,
+    default) against the mirror-pair product (tmat_ctx_set_lattice_fft(ctx, 2)) and the
+    oracle: odd RHS counts (a half-empty last RHS pass), partial ky tiles, every pair, one
+    grid dimension much longer than the other, nmax 1..6."""
+    from paper_2107_09879_b300 import _lib
+    pos = W.lattice_positions(nx, ny)
+    r = W.uniform_radii(nx * ny, 0.08, 0.24, 140 + nmax)
+    T = np.array([mie.tmatrix_diag(nmax, K0, x, 2.0) for x in r])
+    x = rand_c((R, nx * ny, T.shape[1]), 150 + nmax)
+    c = _lib.Context(0)
+    yq = c.tmat_apply_lattice(op, 1, nx, ny, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
+    c.set_lattice_fft(2)
+    yp = c.tmat_apply_lattice(op, 1, nx, ny, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
+    c.close()
+    y64 = ctx().tmat_apply_lattice(op, 0, nx, ny, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
+    assert rel_l2(yq, y64) <= C64_APPLY_TOL
+    assert rel_l2(yp, y64) <= C64_APPLY_TOL
+    assert rel_l2(yq, yp) <= 2 * C64_APPLY_TOL
