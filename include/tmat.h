@@ -200,6 +200,32 @@ int tmat_subregions(tmat_ctx* ctx, int64_t nx, int64_t ny, int64_t cx, int64_t c
 int tmat_build(tmat_ctx* ctx, const tmat_atom* atoms, int64_t N, double wavelength, double n_bg,
                int nmax, tmat_c128* T_diag_out, tmat_c128* dTdr_out);
 
+/* ---- null-field T-matrices of cylinders (App. I-B) ------------------------ */
+
+/* An upright circular cylinder (axis along z, centred on its position) of complex
+ * refractive index n_re + i n_im; its enclosing sphere has radius
+ * sqrt(radius^2 + (height/2)^2). */
+typedef struct {
+  double radius;
+  double height;
+  double n_re;
+  double n_im;
+} tmat_cylinder;
+
+/* Full T-matrices of n cylinders by the null-field method (App. I-B, the P and Q surface
+ * integrals over the scatterer surface and T = -Q P^-1; the two terms of the integrand are
+ * added): T_out[n][P][P] complex128, rows the outgoing (scattered) index, columns the
+ * incident index, flat coefficient order. The body of revolution makes the azimuthal
+ * integral exact (T couples m = m' only), and the profile integral uses n_quad Gauss-Legendre
+ * nodes on each face (bottom disc, side, top disc; 0 -> 48; at most 512). A cylinder
+ * centred on its position is z-mirror symmetric, so T preserves the class (l + m + p) mod 2.
+ * dTdr_out (nullable): d T / d radius by a central difference of the same build (step
+ * 1e-5 wavelengths in the background medium; relative error ~1e-9). n <= 65535 per call;
+ * radius, height > 0, n_re > 0, n_im >= 0 (TMAT_EINVAL otherwise). Host or device arrays;
+ * synchronises the context stream. */
+int tmat_build_cylinder(tmat_ctx* ctx, const tmat_cylinder* cyl, int64_t n, double wavelength, double n_bg,
+                        int nmax, int n_quad, tmat_c128* T_out, tmat_c128* dTdr_out);
+
 /* ---- incident field (App. II-A) ----------------------------------------- */
 
 /* Plane waves A_r exp(i k khat_r . x), khat = (sin b cos a, sin b sin a, cos b),
@@ -285,6 +311,23 @@ int tmat_solve(tmat_ctx* ctx, const double* pos, int64_t N, double wavelength, d
                tmat_solve_info* info);
 int tmat_solution_free(tmat_solution* sol);
 
+/* The same solve with full per-scatterer T-blocks (App. I-B, Eq. def_tmatrix: s_i = T_i a_i
+ * with T_i a P x P matrix, e.g. from tmat_build_cylinder): (I - T A) s = T a0 with
+ * T = diag(T_1 .. T_N).
+ *   T_blocks[n_types][P][P]  complex128, rows outgoing index, columns incident index;
+ *   type[N]                  int32 index into T_blocks per scatterer (nullable: scatterer i
+ *                            uses block i, n_types must equal N); an index outside
+ *                            [0, n_types) returns TMAT_EINVAL.
+ * A block may couple every index (no class or m structure is assumed). The operator applies
+ * A (forward: coupling only) and then the blocks per scatterer; the transposed operator
+ * applies T^T first. Paths, precisions (TMAT_PREC_FP64 or TMAT_PREC_MIXED; TMAT_PREC_FP64_TC
+ * returns TMAT_ENOTSUP), options, layouts and errors as tmat_solve. `keep` receives a solution
+ * for tmat_adjoint_tblocks. */
+int tmat_solve_tblocks(tmat_ctx* ctx, const double* pos, int64_t N, double wavelength, double n_bg, int nmax,
+                       const tmat_c128* T_blocks, const int32_t* type, int64_t n_types, const tmat_c128* a0,
+                       int R, const tmat_solve_opts* opts, tmat_c128* s_out, tmat_solution** keep,
+                       tmat_solve_info* info);
+
 /* ---- sub-region sweep (main text; Fig. 3) -------------------------------- */
 
 /* Geometry and decomposition of a large-area sweep. Sites (ix, iy) of an
@@ -356,6 +399,15 @@ int tmat_point_fom(tmat_ctx* ctx, const double* pos, int64_t N, double wavelengt
 int tmat_adjoint(tmat_ctx* ctx, const tmat_solution* sol, const tmat_c128* v,
                  const tmat_c128* dTdr, double* grad_out, tmat_c128* mu_out,
                  tmat_solve_info* info);
+
+/* Parameter gradient of a figure of merit for a T-block solution of tmat_solve_tblocks
+ * (App. IV): solves (I - A^T T^T) mu = v and returns
+ * grad_out[i] = 2 Re mu_i^T (dT_{type_i} e_i),  e = a0 + A s (RHS 0 of sol),
+ * with dT_blocks[n_types][P][P] the derivative of each T-block with respect to its
+ * scatterer's parameter (e.g. dTdr_out of tmat_build_cylinder), indexed by the solve's types.
+ * mu_out (nullable) receives mu. TMAT_EINVAL for a solution of tmat_solve. */
+int tmat_adjoint_tblocks(tmat_ctx* ctx, const tmat_solution* sol, const tmat_c128* v, const tmat_c128* dT_blocks,
+                         double* grad_out, tmat_c128* mu_out, tmat_solve_info* info);
 
 /* Position gradient of the point figure of merit: dFoM/d(x_i, y_i) for every scatterer
  * (App. IV, with the in-plane positions as the geometry parameters). Lattice solutions

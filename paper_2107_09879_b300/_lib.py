@@ -89,6 +89,10 @@ _SIGS = {
     "tmat_adjoint": [_vp, _vp, _vp, _vp, _vp, _vp, ct.POINTER(SolveInfo)],
     "tmat_position_gradient": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "tmat_measure_fma_peak": [_int, _int, ct.POINTER(_d)],
+    "tmat_build_cylinder": [_vp, _vp, _i64, _d, _d, _int, _int, _vp, _vp],
+    "tmat_solve_tblocks": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _i64, _vp, _int, ct.POINTER(SolveOpts), _vp,
+                           ct.POINTER(_vp), ct.POINTER(SolveInfo)],
+    "tmat_adjoint_tblocks": [_vp, _vp, _vp, _vp, _vp, _vp, ct.POINTER(SolveInfo)],
 }
 EXPORTED = []
 for _name, _args in _SIGS.items():
@@ -286,6 +290,38 @@ class Context:
         if rc not in (OK, ENOCONV):
             self.check(rc)
         return E, info, rc
+
+    def tmat_build_cylinder(self, cyl, wavelength, n_bg, nmax, n_quad=0, with_dr=False):
+        """cyl: (n, 4) float64 [radius, height, n_re, n_im]; returns T (n, P, P) [and dT/dradius]."""
+        n = cyl.shape[0]
+        P = 2 * nmax * (nmax + 2)
+        T = empty_like_space(cyl, (n, P, P), np.complex128)
+        dT = empty_like_space(cyl, (n, P, P), np.complex128) if with_dr else None
+        self.check(lib.tmat_build_cylinder(self.h, ptr(cyl), n, wavelength, n_bg, nmax, n_quad, ptr(T), ptr(dT)))
+        return (T, dT) if with_dr else T
+
+    def tmat_solve_tblocks(self, pos, wavelength, n_bg, nmax, T_blocks, a0, opts, types=None, keep=False):
+        """T_blocks (n_types, P, P); types (N,) int32 or None (block i for scatterer i)."""
+        R, N, P = a0.shape
+        s = empty_like_space(a0, (R, N, P), np.complex128)
+        info = SolveInfo()
+        sol = ct.c_void_p()
+        rc = lib.tmat_solve_tblocks(self.h, ptr(pos), N, wavelength, n_bg, nmax, ptr(T_blocks), ptr(types),
+                                    T_blocks.shape[0], ptr(a0), R, ct.byref(opts), ptr(s),
+                                    ct.byref(sol) if keep else None, ct.byref(info))
+        if rc not in (OK, ENOCONV):
+            self.check(rc)
+        return s, info, (Solution(sol) if keep else None), rc
+
+    def tmat_adjoint_tblocks(self, sol, v, dT_blocks, want_mu=False):
+        N = v.shape[0]
+        grad = empty_like_space(v, (N,), np.float64)
+        mu = empty_like_space(v, v.shape, np.complex128) if want_mu else None
+        info = SolveInfo()
+        rc = lib.tmat_adjoint_tblocks(self.h, sol.h, ptr(v), ptr(dT_blocks), ptr(grad), ptr(mu), ct.byref(info))
+        if rc not in (OK, ENOCONV):
+            self.check(rc)
+        return grad, mu, info
 
     def tmat_field(self, pos, wavelength, n_bg, nmax, s, pts):
         M = pts.shape[0]

@@ -471,9 +471,17 @@ struct Fft4Cfg {
   static constexpr int NI = L <= 24 ? 4 : 2;  // items (consecutive ky) per tile
   static constexpr int THREADS = NI * 2 * L;
   static constexpr int RC = 2;                // RHS per pass
-  static constexpr int NCOL = 4 * RC;
-  static constexpr size_t C_BYTES = (size_t)NI * 2 * L * L * sizeof(float2);
-  static constexpr size_t W_BYTES = (size_t)NI * 2 * L * NCOL * sizeof(float2);
+  static constexpr int NCOL = 4 * RC;         // columns: 4 frequencies x RC RHS
+  // stride of one class block of C in complex values: >= L^2 and = 8 (mod 16), so that the
+  // two class blocks of an item start 16 banks apart (a warp spanning both reads C without
+  // bank conflicts); kept in the global layout too, so one bulk copy moves a whole tile
+  static constexpr int SC = ((L * L + 7) / 16) * 16 + 8;
+  // stride of one (item, class) block of the transformed inputs in complex values: two
+  // values past a multiple of 64 bytes, so the class-0 and class-1 lanes of a warp (two
+  // broadcast addresses per 16-byte load) fall on different banks
+  static constexpr int SW = L * NCOL + 2;
+  static constexpr size_t C_BYTES = (size_t)NI * 2 * SC * sizeof(float2);
+  static constexpr size_t W_BYTES = (size_t)NI * 2 * SW * sizeof(float2);
   static constexpr size_t SMEM = C_BYTES + W_BYTES + 16;
   static constexpr int MIN_BLOCKS = L <= 24 ? 4 : 2;  // resident CTAs per SM the registers allow
 };
@@ -493,76 +501,108 @@ __device__ __forceinline__ bool fft4_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
+// per column k (frequency f1..f4) and direction D (0 forward / coupling, 1 transposed):
+// input permutation and sign, output permutation and sign (see the block comment above)
+__device__ __constant__ int c_fft4_in_j[2][4] = {{1, 0, 0, 1}, {0, 1, 1, 0}};
+__device__ __constant__ int c_fft4_in_s[2][4] = {{3, 1, 2, 0}, {3, 1, 2, 0}};
+
 template <int L, int MODE>
 __global__ void __launch_bounds__(Fft4Cfg<L>::THREADS, Fft4Cfg<L>::MIN_BLOCKS)
 fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, float2* __restrict__ Yh, int Mx, int My,
                 int R_, const int* __restrict__ sym, int* __restrict__ err) {
   using Cfg = Fft4Cfg<L>;
-  constexpr int NI = Cfg::NI, RC = Cfg::RC, NCOL = Cfg::NCOL, P = 2 * L;
-  // per column k (frequency f1..f4): input permutation / sign, output permutation / sign
-  constexpr int IN_J[2][4] = {{1, 0, 0, 1}, {0, 1, 1, 0}};
-  constexpr int IN_S[2][4] = {{3, 1, 2, 0}, {3, 1, 2, 0}};
+  constexpr int NI = Cfg::NI, RC = Cfg::RC, NCOL = Cfg::NCOL, P = 2 * L, SC = Cfg::SC, SW = Cfg::SW,
+                NT = Cfg::THREADS;
   constexpr int OUT_J[2][4] = {{0, 1, 1, 0}, {1, 0, 0, 1}};
   constexpr int OUT_S[2][4] = {{0, 2, 1, 3}, {0, 2, 1, 3}};
   constexpr int D = MODE == 1 ? 1 : 0;
   extern __shared__ __align__(128) unsigned char fsm4[];
-  float2* Cs = reinterpret_cast<float2*>(fsm4);                      // [NI][2][L][L]
-  float2* Ws = reinterpret_cast<float2*>(fsm4 + Cfg::C_BYTES);       // [NI][2][L][NCOL]
+  float2* Cs = reinterpret_cast<float2*>(fsm4);                  // [NI][2][SC]
+  float2* Ws = reinterpret_cast<float2*>(fsm4 + Cfg::C_BYTES);   // [NI][2][SW >= L * NCOL]
   const uint32_t bar = (uint32_t)__cvta_generic_to_shared(fsm4 + Cfg::C_BYTES + Cfg::W_BYTES);
   const uint32_t cs_addr = (uint32_t)__cvta_generic_to_shared(Cs);
   const int t = threadIdx.x;
-  const int it = t / (2 * L), c = (t / L) & 1, u = t % L;
+  const int it = t / (2 * L), c = (t / L) & 1, u = t % L;  // compute role: row u of item it, class c
   const int64_t F = (int64_t)Mx * My;
   const int hx = Mx >= 2 ? Mx / 2 + 1 : 1, hy = My >= 2 ? My / 2 + 1 : 1;
   const int tpr = (hy + NI - 1) / NI;
   const int64_t ntiles = (int64_t)hx * tpr;
   const int su = sym[c * L + u];
   const int Ju = su & 0xffff, mpar = (su >> 16) & 1, pp = (su >> 17) & 1;
+  if ((int64_t)blockIdx.x >= ntiles) return;  // uniform over the CTA
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   __syncthreads();
-  uint32_t phase = 0;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int kx = (int)(tile / tpr), ky0 = (int)(tile % tpr) * NI;
-    const int ni = min(NI, hy - ky0);
-    if (t == 0) {
-      const uint32_t bytes = (uint32_t)(ni * 2 * L * L * sizeof(float2));
-      const float2* src = Cq + ((int64_t)kx * hy + ky0) * 2 * L * L;
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
-      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                   :: "r"(cs_addr), "l"(src), "r"(bytes), "r"(bar) : "memory");
+
+  // the tile's four frequencies of item i (kx fixed per tile) and which are distinct
+  auto tile_of = [&](int64_t tl, int& kx, int& ky0, int& ni) {
+    kx = (int)(tl / tpr);
+    ky0 = (int)(tl % tpr) * NI;
+    ni = min(NI, hy - ky0);
+  };
+  auto issue_c = [&](int64_t tl) {
+    int kx, ky0, ni;
+    tile_of(tl, kx, ky0, ni);
+    const uint32_t bytes = (uint32_t)(ni * 2 * SC * sizeof(float2));
+    const float2* src = Cq + ((int64_t)kx * hy + ky0) * 2 * SC;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(cs_addr), "l"(src), "r"(bytes), "r"(bar) : "memory");
+  };
+  // load role: value e = t + j NT of the tile's transformed inputs, item fastest (the NI
+  // items of a tile are consecutive frequencies: one 32-byte sector per plane for NI = 4)
+  float2 wv[NCOL];
+  auto load_w = [&](int64_t tl, int r0) {
+    int kx, ky0, ni;
+    tile_of(tl, kx, ky0, ni);
+    const int kxm = (Mx - kx) % Mx;
+#pragma unroll
+    for (int j = 0; j < NCOL; ++j) {
+      const int e = t + j * NT;
+      const int item = e % NI, rest = e / NI;
+      const int col = rest % NCOL, row = rest / NCOL;
+      const int cc = row / L, v = row % L, k = col / RC, q = col % RC;
+      const int ky = ky0 + item, kym = (My - ky) % My;
+      const bool ok = item < ni && r0 + q < R_ && ((k & 1) == 0 || kym != ky) && ((k & 2) == 0 || kxm != kx);
+      float2 w = make_float2(0.f, 0.f);
+      if (ok) {
+        const int sv = sym[cc * L + v];
+        const int comp = c_fft4_in_j[D][k] ? (sv & 0xffff) : v;
+        const int64_t f = (int64_t)((k & 2) ? kxm : kx) * My + ((k & 1) ? kym : ky);
+        w = Xh[((int64_t)(r0 + q) * P + cc * L + comp) * F + f];
+        if (fft4_neg(c_fft4_in_s[D][k], (sv >> 16) & 1, (sv >> 17) & 1)) w = make_float2(-w.x, -w.y);
+      }
+      wv[j] = w;
     }
-    const bool live = it < ni;
-    const int ky = ky0 + it;
-    const int kxm = (Mx - kx) % Mx, kym = (My - ky) % My;
-    // the four frequencies (column k) as (row, column) of the Mx x My grid; bit k of vmask:
-    // column k is a distinct frequency of a live item
+  };
+  auto store_w = [&]() {
+#pragma unroll
+    for (int j = 0; j < NCOL; ++j) {
+      const int e = t + j * NT;
+      const int item = e % NI, rest = e / NI;
+      const int col = rest % NCOL, row = rest / NCOL;
+      Ws[(item * 2 + row / L) * SW + (row % L) * NCOL + col] = wv[j];
+    }
+  };
+
+  int64_t tile = blockIdx.x;
+  uint32_t phase = 0;
+  if (t == 0) issue_c(tile);
+  load_w(tile, 0);
+  store_w();
+  for (;;) {
+    int kx, ky0, ni;
+    tile_of(tile, kx, ky0, ni);
+    const int ky = ky0 + it, kxm = (Mx - kx) % Mx, kym = (My - ky) % My;
     const bool dy = kym != ky, dx = kxm != kx;
-    const unsigned vmask = live ? (1u | (dy ? 2u : 0u) | (dx ? 4u : 0u) | (dx && dy ? 8u : 0u)) : 0u;
-    auto freq = [&](int k) -> int64_t {
-      return (int64_t)((k & 2) ? kxm : kx) * My + ((k & 1) ? kym : ky);
-    };
-    float2* wrow = Ws + ((it * 2 + c) * L + u) * NCOL;
+    const unsigned vmask = it < ni ? (1u | (dy ? 2u : 0u) | (dx ? 4u : 0u) | (dx && dy ? 8u : 0u)) : 0u;
     for (int r0 = 0; r0 < R_; r0 += RC) {
-      // this thread's row of the transformed inputs, all columns
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int q = 0; q < RC; ++q) {
-          float2 w = make_float2(0.f, 0.f);
-          if (((vmask >> k) & 1u) && r0 + q < R_) {
-            const int comp = IN_J[D][k] ? Ju : u;
-            w = Xh[((int64_t)(r0 + q) * P + c * L + comp) * F + freq(k)];
-            if (fft4_neg(IN_S[D][k], mpar, pp)) w = make_float2(-w.x, -w.y);
-          }
-          wrow[k * RC + q] = w;
-        }
       int bad = 0;
       if (r0 == 0) bad = !fft4_wait(bar, phase);
-      bad = __syncthreads_or(bad);
+      bad = __syncthreads_or(bad);  // also makes this stage's Ws visible
       if (bad) {
         if (t == 0) {
           atomicAdd(err, 1);
@@ -573,8 +613,8 @@ fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, fl
       float2 acc[NCOL];
 #pragma unroll
       for (int j = 0; j < NCOL; ++j) acc[j] = make_float2(0.f, 0.f);
-      const float2* Ci = Cs + (it * 2 + c) * L * L + u;
-      const float4* Wi = reinterpret_cast<const float4*>(Ws + (it * 2 + c) * L * NCOL);
+      const float2* Ci = Cs + (it * 2 + c) * SC + u;
+      const float4* Wi = reinterpret_cast<const float4*>(Ws + (it * 2 + c) * SW);
 #pragma unroll 4
       for (int v = 0; v < L; ++v) {
         const float2 g = Ci[v * L];
@@ -585,6 +625,16 @@ fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, fl
           cfma(acc[2 * j + 1], g, make_float2(w2.z, w2.w));
         }
       }
+      __syncthreads();  // every read of Cs and Ws of this stage is done
+      // next stage: its C copy (new tile) and its input loads go out before this stage's
+      // outputs are written
+      const bool more_rhs = r0 + RC < R_;
+      const int64_t ntile = more_rhs ? tile : tile + gridDim.x;
+      const bool have_next = ntile < ntiles;
+      if (have_next) {
+        if (!more_rhs && t == 0) issue_c(ntile);
+        load_w(ntile, more_rhs ? r0 + RC : 0);
+      }
 #pragma unroll
       for (int k = 0; k < 4; ++k)
 #pragma unroll
@@ -593,17 +643,21 @@ fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, fl
             const int comp = OUT_J[D][k] ? Ju : u;
             float2 z = acc[k * RC + q];
             if (fft4_neg(OUT_S[D][k], mpar, pp)) z = make_float2(-z.x, -z.y);
-            Yh[((int64_t)(r0 + q) * P + c * L + comp) * F + freq(k)] = z;
+            const int64_t f = (int64_t)((k & 2) ? kxm : kx) * My + ((k & 1) ? kym : ky);
+            Yh[((int64_t)(r0 + q) * P + c * L + comp) * F + f] = z;
           }
-      __syncthreads();  // Ws (next RHS pass) and Cs (next tile) are overwritten next
+      if (have_next) store_w();
     }
+    tile += gridDim.x;
+    if (tile >= ntiles) break;
     phase ^= 1u;
   }
 }
 
 // C[item][c][u][v] = ph(f1) Bs[(c L + u) L + J(v)][f1] (-1)^(m_v) from the stored spectra
-// (component-major, with the compact-grid shift phase, undone here); item = kx * hy + ky.
-__global__ void fft_pack_quad_kernel(const float2* __restrict__ Bs, int Mx, int My, int L, int CX, int CY,
+// (component-major, with the compact-grid shift phase, undone here); item = kx * hy + ky,
+// class blocks SC complex values apart (the padding is left zero).
+__global__ void fft_pack_quad_kernel(const float2* __restrict__ Bs, int Mx, int My, int L, int SC, int CX, int CY,
                                      const int* __restrict__ sym, float2* __restrict__ Cq) {
   const int hy = My >= 2 ? My / 2 + 1 : 1, hx = Mx >= 2 ? Mx / 2 + 1 : 1;
   const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -619,7 +673,7 @@ __global__ void fft_pack_quad_kernel(const float2* __restrict__ Bs, int Mx, int 
   const float2 b = Bs[((int64_t)(c * L + u) * L + (sv & 0xffff)) * F + f1];
   float2 z = cmul(make_float2((float)cs, (float)sn), b);
   if ((sv >> 16) & 1) z = make_float2(-z.x, -z.y);
-  Cq[(item * 2 + c) * L * L + u * L + v] = z;
+  Cq[(item * 2 + c) * SC + u * L + v] = z;
 }
 
 // Forward 2-D transform of nb component grids [nb][ny][nx] into [nb][Mx][My] (via tmp).
@@ -678,14 +732,16 @@ static int fft_prepare_t(tmat_ctx* ctx, LatOp* a, const char* name) {
   if (sizeof(R) == 4 && a->fft_mirror_sign == 1 && a->fft_sym && ctx->fft_quad) {
     const int hx = Mx >= 2 ? Mx / 2 + 1 : 1, hy = My >= 2 ? My / 2 + 1 : 1;
     const int64_t items = (int64_t)hx * hy;
+    const int SC = ((L * L + 7) / 16) * 16 + 8;  // Fft4Cfg<L>::SC
     std::string cn = std::string(name) + "_quad";
     float2* Cq;
     int* err;
-    TM_TRY(scratch(ctx, cn.c_str(), sizeof(float2) * items * 2 * L * L, (void**)&Cq));
+    TM_TRY(scratch(ctx, cn.c_str(), sizeof(float2) * items * 2 * SC, (void**)&Cq));
     TM_TRY(scratch(ctx, "fft_quad_err", sizeof(int), (void**)&err));
     TM_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+    TM_CUDA(ctx, cudaMemsetAsync(Cq, 0, sizeof(float2) * items * 2 * SC, ctx->stream));
     dim3 g((unsigned)cdiv(items, 128), (unsigned)(2 * L * L));
-    fft_pack_quad_kernel<<<g, 128, 0, ctx->stream>>>((const float2*)Bh, Mx, My, L, a->CX, a->CY, a->fft_sym, Cq);
+    fft_pack_quad_kernel<<<g, 128, 0, ctx->stream>>>((const float2*)Bh, Mx, My, L, SC, a->CX, a->CY, a->fft_sym, Cq);
     TM_LAUNCHED(ctx);
     a->fft_C = Cq;
     a->fft_err = err;
@@ -739,7 +795,7 @@ static int fft_apply_t(tmat_ctx* ctx, const LatOp& a, const void* xv, void* yv, 
                                                                      (float2*)Yh, Mx, My, R_, a.fft_sym, a.fft_err);
       TM_LAUNCHED(ctx);
       // the quad-form spectra once, the RHS spectra in and out
-      const double mul_bytes = (double)sizeof(float2) * ((double)hx * hy * 2.0 * L * L + 2.0 * nb * F);
+      const double mul_bytes = (double)sizeof(float2) * ((double)hx * hy * 2.0 * Cfg::SC + 2.0 * nb * F);
       timing_end(ctx, "lattice_fft_mul32", ev, mul_bytes);
       quad_done = true;
     }

@@ -26,6 +26,12 @@ struct tmat_solution {
   bool threed = false;    // positions not coplanar (neighbour path with full 3-D blocks)
   double2* a0 = nullptr;  // RHS 0
   double2* s = nullptr;   // RHS 0
+  // T-block solutions (tmat_solve_tblocks): blocks in internal order, both storages
+  bool tblocks = false;
+  int64_t n_types = 0;
+  double2 *tb64c = nullptr, *tb64r = nullptr;
+  float2 *tb32c = nullptr, *tb32r = nullptr;
+  int32_t* ttype = nullptr;  // null: scatterer i uses block i
 };
 
 namespace tmat {
@@ -34,9 +40,73 @@ bool Operator::fp32() const { return kind == 0 ? nbr.fp32 : lattice_fp32(*lat); 
 int64_t Operator::N() const { return kind == 0 ? nbr.N : lattice_N(*lat); }
 int Operator::nmax() const { return kind == 0 ? nbr.nmax : lattice_nmax(*lat); }
 
-int op_apply(tmat_ctx* ctx, const Operator& A, int mode, const void* x, void* y, int R) {
+static int op_apply_inner(tmat_ctx* ctx, const Operator& A, int mode, const void* x, void* y, int R) {
   if (A.kind == 0) return nbr_apply(ctx, A.nbr, mode, x, y, R);
   return lattice_apply(ctx, *A.lat, mode, x, y, R);
+}
+
+// y = x - t + w (the transposed T-block operator from t = T^T x and w = t - A^T t)
+template <typename R>
+__global__ void tb_combine_kernel(const C<R>* __restrict__ x, const C<R>* __restrict__ t, const C<R>* __restrict__ w,
+                                  C<R>* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = cadd(csub(x[i], t[i]), w[i]);
+}
+
+int op_apply(tmat_ctx* ctx, const Operator& A, int mode, const void* x, void* y, int R) {
+  if (!A.tbc || mode == TMAT_OP_COUPLE) return op_apply_inner(ctx, A, mode, x, y, R);
+  const bool f32 = A.fp32();
+  const int64_t N = A.N();
+  const int P = num_coeffs(A.nmax());
+  const size_t bytes = (f32 ? sizeof(float2) : sizeof(double2)) * (size_t)R * N * P;
+  void *z, *w;
+  TM_TRY(scratch(ctx, f32 ? "tb_z32" : "tb_z64", bytes, &z));
+  if (mode == TMAT_OP_FORWARD) {
+    TM_TRY(op_apply_inner(ctx, A, TMAT_OP_COUPLE, x, z, R));
+    return tblock_mul(ctx, A.tbc, A.ttype, z, x, y, N, P, R, f32);
+  }
+  TM_TRY(scratch(ctx, f32 ? "tb_w32" : "tb_w64", bytes, &w));
+  TM_TRY(tblock_mul(ctx, A.tbr, A.ttype, x, nullptr, z, N, P, R, f32));  // t = T^T x
+  TM_TRY(op_apply_inner(ctx, A, TMAT_OP_ADJOINT, z, w, R));             // w = t - A^T t (inner T = 1)
+  const int64_t n = (int64_t)R * N * P;
+  const unsigned g = (unsigned)std::min<int64_t>(cdiv(n, 256), 8192);
+  if (f32) tb_combine_kernel<float><<<g, 256, 0, ctx->stream>>>((const float2*)x, (const float2*)z, (const float2*)w, (float2*)y, n);
+  else tb_combine_kernel<double><<<g, 256, 0, ctx->stream>>>((const double2*)x, (const double2*)z, (const double2*)w, (double2*)y, n);
+  TM_LAUNCHED(ctx);
+  return TMAT_OK;
+}
+
+// out[r][i][a] = sum_c Tm[(type_i P + c) P + a] in[r][i][c] (minus that from xsub when given);
+// one thread per (scatterer, a), the scatterer's input read by broadcast
+template <typename R>
+__global__ void tblock_mul_kernel(const C<R>* __restrict__ Tm, const int32_t* __restrict__ type, const C<R>* __restrict__ in,
+                                  const C<R>* __restrict__ xsub, C<R>* __restrict__ out, int64_t N, int P, int R_, int SB) {
+  const int loc = threadIdx.x / P, a = threadIdx.x % P;
+  const int64_t i = (int64_t)blockIdx.x * SB + loc;
+  if (loc >= SB || i >= N) return;
+  const C<R>* Tt = Tm + (int64_t)(type ? type[i] : i) * P * P + a;
+  for (int r = 0; r < R_; ++r) {
+    const C<R>* v = in + ((int64_t)r * N + i) * P;
+    C<R> acc = mk<R>((R)0, (R)0);
+    for (int c = 0; c < P; ++c) cfma(acc, Tt[(int64_t)c * P], v[c]);
+    const int64_t o = ((int64_t)r * N + i) * P + a;
+    out[o] = xsub ? csub(xsub[o], acc) : acc;
+  }
+}
+
+int tblock_mul(tmat_ctx* ctx, const void* Tm, const int32_t* type, const void* in, const void* xsub, void* out,
+               int64_t N, int P, int R, bool fp32) {
+  if (N == 0) return TMAT_OK;
+  const int SB = std::max(1, 256 / P);
+  const unsigned g = (unsigned)cdiv(N, SB);
+  if (fp32)
+    tblock_mul_kernel<float><<<g, SB * P, 0, ctx->stream>>>((const float2*)Tm, type, (const float2*)in,
+                                                            (const float2*)xsub, (float2*)out, N, P, R, SB);
+  else
+    tblock_mul_kernel<double><<<g, SB * P, 0, ctx->stream>>>((const double2*)Tm, type, (const double2*)in,
+                                                             (const double2*)xsub, (double2*)out, N, P, R, SB);
+  TM_LAUNCHED(ctx);
+  return TMAT_OK;
 }
 
 // b[r][i][u] = T[i][u] a[r][i][u]   (internal layout, complex128)
@@ -77,6 +147,11 @@ static void free_solution(tmat_solution* s) {
   cudaFree(s->col);
   cudaFree(s->a0);
   cudaFree(s->s);
+  cudaFree(s->tb64c);
+  cudaFree(s->tb64r);
+  cudaFree(s->tb32c);
+  cudaFree(s->tb32r);
+  cudaFree(s->ttype);
   delete s;
 }
 
@@ -148,15 +223,116 @@ extern "C" int tmat_solution_free(tmat_solution* sol) {
   return TMAT_OK;
 }
 
-extern "C" int tmat_solve(tmat_ctx* ctx, const double* pos, int64_t N, double wavelength, double n_bg, int nmax,
-                          const tmat_c128* T_diag, const tmat_c128* a0, int R, const tmat_solve_opts* opts,
-                          tmat_c128* s_out, tmat_solution** keep, tmat_solve_info* info) {
+namespace tmat {
+// T-blocks of a tmat_solve_tblocks call (API order, host or device)
+struct TBlockArgs {
+  const tmat_c128* blocks = nullptr;
+  const int32_t* type = nullptr;
+  int64_t n_types = 0;
+};
+}  // namespace tmat
+
+// kept by the solution object of a T-block solve
+struct TBlockDev {
+  double2 *c64 = nullptr, *r64 = nullptr;
+  float2 *c32 = nullptr, *r32 = nullptr;
+  const int32_t* type = nullptr;
+};
+
+template <typename R>
+__global__ void unit_kernel(C<R>* out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = mk<R>((R)1, (R)0);
+}
+
+// an all-ones diagonal T (internal layout) for operators whose blocks are applied around them
+static int unit_T(tmat_ctx* ctx, int64_t n, bool fp32, const char* name, void** out) {
+  TM_TRY(scratch(ctx, name, (fp32 ? sizeof(float2) : sizeof(double2)) * n, out));
+  const unsigned g = (unsigned)std::min<int64_t>(cdiv(n, 256), 8192);
+  if (fp32) unit_kernel<float><<<g, 256, 0, ctx->stream>>>((float2*)*out, n);
+  else unit_kernel<double><<<g, 256, 0, ctx->stream>>>((double2*)*out, n);
+  TM_LAUNCHED(ctx);
+  return TMAT_OK;
+}
+
+static void attach_tblocks(OpPair* ops, const TBlockDev& d) {
+  ops->A64.tbc = d.c64;
+  ops->A64.tbr = d.r64;
+  ops->A64.ttype = d.type;
+  if (ops->have32) {
+    ops->A32.tbc = d.c32;
+    ops->A32.tbr = d.r32;
+    ops->A32.ttype = d.type;
+  }
+}
+
+// blocks in internal order: c[(ty P + c) P + a] = T[a][c], r[(ty P + c) P + a] = T[c][a]
+// (internal indices; T flat is [ty][perm[a]][perm[c]])
+template <typename R>
+__global__ void tblock_internal_kernel(const double2* __restrict__ Tf, const int* __restrict__ perm, int64_t n, int P,
+                                       C<R>* __restrict__ oc, C<R>* __restrict__ orw) {
+  const int64_t PP = (int64_t)P * P;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * PP; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ty = e / PP;
+    const int c = (int)((e % PP) / P), a = (int)(e % P);
+    const double2 tac = Tf[ty * PP + (int64_t)perm[a] * P + perm[c]];
+    const double2 tca = Tf[ty * PP + (int64_t)perm[c] * P + perm[a]];
+    oc[e] = mk<R>((R)tac.x, (R)tac.y);
+    orw[e] = mk<R>((R)tca.x, (R)tca.y);
+  }
+}
+
+__global__ void type_check_kernel(const int32_t* __restrict__ type, int64_t N, int64_t n_types, int* __restrict__ bad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    if (type[i] < 0 || type[i] >= n_types) atomicOr(bad, 1);
+}
+
+static int prepare_tblocks(tmat_ctx* ctx, const Tables* t, const TBlockArgs& tb, int64_t N, bool mixed, TBlockDev* d) {
+  const int P = t->P;
+  const int64_t n = tb.n_types, PP = (int64_t)P * P;
+  Staged sb, st;
+  TM_TRY(stage_in(ctx, "st_tblk", tb.blocks, sizeof(double2) * n * PP, &sb));
+  if (tb.type) {
+    TM_TRY(stage_in(ctx, "st_ttype", tb.type, sizeof(int32_t) * N, &st));
+    int* flag;
+    TM_TRY(scratch(ctx, "tb_flag", sizeof(int), (void**)&flag));
+    TM_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+    type_check_kernel<<<(unsigned)std::min<int64_t>(cdiv(N, 256), 4096), 256, 0, ctx->stream>>>(
+        (const int32_t*)st.dev, N, n, flag);
+    TM_LAUNCHED(ctx);
+    int* pin = (int*)ctx->pinned;
+    TM_CUDA(ctx, cudaMemcpyAsync(pin, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (pin[0]) return set_error(ctx, TMAT_EINVAL, "tmat_solve_tblocks: a type index is outside [0, %lld)", (long long)n);
+    d->type = (const int32_t*)st.dev;
+  }
+  TM_TRY(scratch(ctx, "tb_c64", sizeof(double2) * n * PP, (void**)&d->c64));
+  TM_TRY(scratch(ctx, "tb_r64", sizeof(double2) * n * PP, (void**)&d->r64));
+  const unsigned g = (unsigned)std::min<int64_t>(cdiv(n * PP, 256), 16384);
+  tblock_internal_kernel<double><<<g, 256, 0, ctx->stream>>>((const double2*)sb.dev, t->d_perm, n, P, d->c64, d->r64);
+  TM_LAUNCHED(ctx);
+  if (mixed) {
+    TM_TRY(scratch(ctx, "tb_c32", sizeof(float2) * n * PP, (void**)&d->c32));
+    TM_TRY(scratch(ctx, "tb_r32", sizeof(float2) * n * PP, (void**)&d->r32));
+    tblock_internal_kernel<float><<<g, 256, 0, ctx->stream>>>((const double2*)sb.dev, t->d_perm, n, P, d->c32, d->r32);
+    TM_LAUNCHED(ctx);
+  }
+  return TMAT_OK;
+}
+
+static int solve_impl(tmat_ctx* ctx, const double* pos, int64_t N, double wavelength, double n_bg, int nmax,
+                      const tmat_c128* T_diag, const TBlockArgs* tb, const tmat_c128* a0, int R,
+                      const tmat_solve_opts* opts, tmat_c128* s_out, tmat_solution** keep, tmat_solve_info* info) {
   auto t_start = std::chrono::steady_clock::now();
   if (!ctx) return TMAT_EINVAL;
   if (keep) *keep = nullptr;
   if (N < 0 || R < 1 || R > TMAT_MAX_RHS || !opts || !(wavelength > 0) || !(n_bg > 0) ||
-      (N > 0 && (!pos || !T_diag || !a0 || !s_out)))
+      (N > 0 && (!pos || (!T_diag && !tb) || !a0 || !s_out)))
     return set_error(ctx, TMAT_EINVAL, "tmat_solve: bad arguments (R must be 1..%d)", TMAT_MAX_RHS);
+  if (tb && (!tb->blocks || tb->n_types < 1 || (!tb->type && tb->n_types != N)))
+    return set_error(ctx, TMAT_EINVAL, "tmat_solve_tblocks: need blocks, n_types >= 1 and a type array unless n_types == N");
+  if (tb && opts->precision == TMAT_PREC_FP64_TC)
+    return set_error(ctx, TMAT_ENOTSUP, "tmat_solve_tblocks: TMAT_PREC_FP64_TC is not supported with T-blocks");
   if (!(opts->taper >= 0) || (opts->taper > 0 && !(opts->taper <= opts->cutoff)))
     return set_error(ctx, TMAT_EINVAL, "tmat_solve: taper must be in [0, cutoff]");
   if (opts->precision != TMAT_PREC_FP64 && opts->precision != TMAT_PREC_MIXED && opts->precision != TMAT_PREC_FP64_TC)
@@ -192,13 +368,21 @@ extern "C" int tmat_solve(tmat_ctx* ctx, const double* pos, int64_t N, double wa
   const bool threed = (pflags & 1) != 0;
   if (threed && path == TMAT_PATH_LATTICE)
     return set_error(ctx, TMAT_EINVAL, "tmat_solve: the lattice path needs coplanar positions");
-  TM_TRY(stage_in(ctx, "st_T", T_diag, sizeof(double2) * N * P, &sT));
+  if (!tb) TM_TRY(stage_in(ctx, "st_T", T_diag, sizeof(double2) * N * P, &sT));
   TM_TRY(stage_in(ctx, "st_a0", a0, sizeof(double2) * R * N * P, &sa));
   TM_TRY(stage_out(ctx, "st_s", s_out, sizeof(double2) * R * N * P, &ss));
   const bool mixed = sp.precision == TMAT_PREC_MIXED;
   void *T64, *T32 = nullptr;
-  TM_TRY(prepare_T(ctx, t, (const double2*)sT.dev, N, false, "sv_T64", &T64));
-  if (mixed) TM_TRY(prepare_T(ctx, t, (const double2*)sT.dev, N, true, "sv_T32", &T32));
+  TBlockDev tbd;
+  if (tb) {
+    // the operators carry T = 1; the blocks are applied around them (op_apply)
+    TM_TRY(prepare_tblocks(ctx, t, *tb, N, mixed, &tbd));
+    TM_TRY(unit_T(ctx, N * P, false, "sv_one64", &T64));
+    if (mixed) TM_TRY(unit_T(ctx, N * P, true, "sv_one32", &T32));
+  } else {
+    TM_TRY(prepare_T(ctx, t, (const double2*)sT.dev, N, false, "sv_T64", &T64));
+    if (mixed) TM_TRY(prepare_T(ctx, t, (const double2*)sT.dev, N, true, "sv_T32", &T32));
+  }
   OpPair ops;
   int64_t* rp = nullptr;
   int32_t* col = nullptr;
@@ -213,17 +397,22 @@ extern "C" int tmat_solve(tmat_ctx* ctx, const double* pos, int64_t N, double wa
   } else {
     TM_TRY(make_lattice_ops(ctx, t, (const double*)spos.dev, N, k, opts->lattice_nx, opts->lattice_ny,
                             opts->lattice_pitch, opts->cutoff, opts->taper, (const double2*)T64, (const float2*)T32, mixed, &ops,
-                            sp.precision == TMAT_PREC_FP64_TC ? 2 : (mixed ? 1 : 0)));
+                            sp.precision == TMAT_PREC_FP64_TC ? 2 : (mixed && !tb ? 1 : 0)));
   }
+  if (tb) attach_tblocks(&ops, tbd);
   // b = T a0 (internal layout)
   double2 *a0i, *b, *x;
   TM_TRY(scratch(ctx, "sv_a0", sizeof(double2) * R * N * P, (void**)&a0i));
   TM_TRY(scratch(ctx, "sv_b", sizeof(double2) * R * N * P, (void**)&b));
   TM_TRY(scratch(ctx, "sv_x", sizeof(double2) * R * N * P, (void**)&x));
   TM_TRY(to_internal(ctx, t, (const double2*)sa.dev, a0i, false, (int64_t)R * N));
-  tdiag_mul_kernel<<<(unsigned)std::min<int64_t>(cdiv((int64_t)R * N * P, 256), 65535), 256, 0, ctx->stream>>>(
-      (const double2*)T64, a0i, b, N * P, (int64_t)R * N * P);
-  TM_LAUNCHED(ctx);
+  if (tb) {
+    TM_TRY(tblock_mul(ctx, tbd.c64, tbd.type, a0i, nullptr, b, N, P, R, false));
+  } else {
+    tdiag_mul_kernel<<<(unsigned)std::min<int64_t>(cdiv((int64_t)R * N * P, 256), 65535), 256, 0, ctx->stream>>>(
+        (const double2*)T64, a0i, b, N * P, (int64_t)R * N * P);
+    TM_LAUNCHED(ctx);
+  }
   SolveStats st;
   TM_TRY(solve_with(ctx, ops, sp.precision, TMAT_OP_FORWARD, b, x, R, sp, &st));
   TM_TRY(check_tc_errors(ctx, ops));
@@ -254,6 +443,16 @@ extern "C" int tmat_solve(tmat_ctx* ctx, const double* pos, int64_t N, double wa
       }
       if ((rc = dmalloc_copy(ctx, &so->a0, a0i, sizeof(double2) * N * P))) break;
       if ((rc = dmalloc_copy(ctx, &so->s, x, sizeof(double2) * N * P))) break;
+      if (tb) {
+        const size_t nb = sizeof(double2) * tb->n_types * P * P;
+        so->tblocks = true;
+        so->n_types = tb->n_types;
+        if ((rc = dmalloc_copy(ctx, &so->tb64c, tbd.c64, nb))) break;
+        if ((rc = dmalloc_copy(ctx, &so->tb64r, tbd.r64, nb))) break;
+        if (mixed && (rc = dmalloc_copy(ctx, &so->tb32c, tbd.c32, nb / 2))) break;
+        if (mixed && (rc = dmalloc_copy(ctx, &so->tb32r, tbd.r32, nb / 2))) break;
+        if (tbd.type && (rc = dmalloc_copy(ctx, &so->ttype, tbd.type, sizeof(int32_t) * N))) break;
+      }
     } while (0);
     if (rc) {
       free_solution(so);
@@ -274,12 +473,30 @@ extern "C" int tmat_solve(tmat_ctx* ctx, const double* pos, int64_t N, double wa
   return TMAT_OK;
 }
 
+extern "C" int tmat_solve(tmat_ctx* ctx, const double* pos, int64_t N, double wavelength, double n_bg, int nmax,
+                          const tmat_c128* T_diag, const tmat_c128* a0, int R, const tmat_solve_opts* opts,
+                          tmat_c128* s_out, tmat_solution** keep, tmat_solve_info* info) {
+  return solve_impl(ctx, pos, N, wavelength, n_bg, nmax, T_diag, nullptr, a0, R, opts, s_out, keep, info);
+}
+
+extern "C" int tmat_solve_tblocks(tmat_ctx* ctx, const double* pos, int64_t N, double wavelength, double n_bg, int nmax,
+                                  const tmat_c128* T_blocks, const int32_t* type, int64_t n_types, const tmat_c128* a0,
+                                  int R, const tmat_solve_opts* opts, tmat_c128* s_out, tmat_solution** keep,
+                                  tmat_solve_info* info) {
+  TBlockArgs tb;
+  tb.blocks = T_blocks;
+  tb.type = type;
+  tb.n_types = n_types;
+  return solve_impl(ctx, pos, N, wavelength, n_bg, nmax, nullptr, &tb, a0, R, opts, s_out, keep, info);
+}
+
 extern "C" int tmat_adjoint(tmat_ctx* ctx, const tmat_solution* sol, const tmat_c128* v, const tmat_c128* dTdr,
                             double* grad_out, tmat_c128* mu_out, tmat_solve_info* info) {
   auto t_start = std::chrono::steady_clock::now();
   if (!ctx) return TMAT_EINVAL;
   if (!sol || !v || !dTdr || !grad_out) return set_error(ctx, TMAT_EINVAL, "tmat_adjoint: bad arguments");
   if (sol->device != ctx->device) return set_error(ctx, TMAT_EINVAL, "tmat_adjoint: solution is on another device");
+  if (sol->tblocks) return set_error(ctx, TMAT_EINVAL, "tmat_adjoint: a T-block solution needs tmat_adjoint_tblocks");
   Tables* t;
   TM_TRY(get_tables(ctx, sol->nmax, &t));
   TM_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -330,6 +547,100 @@ extern "C" int tmat_adjoint(tmat_ctx* ctx, const tmat_solution* sol, const tmat_
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   }
   if (!st.converged) return set_error(ctx, TMAT_ENOCONV, "tmat_adjoint: not converged after %d iterations", st.iterations);
+  return TMAT_OK;
+}
+
+// grad[i] = 2 Re sum_a mu[i][a] sum_c dT[type_i][a][c] e[i][c], e = a0 + A s; dTc in the
+// column storage dTc[(ty P + c) P + a] = dT[a][c]
+__global__ void grad_blocks_kernel(const double2* __restrict__ mu, const double2* __restrict__ dTc,
+                                   const int32_t* __restrict__ type, const double2* __restrict__ a0,
+                                   const double2* __restrict__ As, int64_t N, int P, double* __restrict__ grad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double2* D = dTc + (int64_t)(type ? type[i] : i) * P * P;
+  double acc = 0;
+  for (int c = 0; c < P; ++c) {
+    const int64_t oc = i * P + c;
+    const double2 e = make_double2(a0[oc].x + As[oc].x, a0[oc].y + As[oc].y);
+    double2 row = make_double2(0.0, 0.0);  // sum_a mu[a] dT[a][c]
+    for (int a = 0; a < P; ++a) row = cadd(row, cmul(mu[i * P + a], D[(int64_t)c * P + a]));
+    acc += cmul(row, e).x;
+  }
+  grad[i] = 2.0 * acc;
+}
+
+extern "C" int tmat_adjoint_tblocks(tmat_ctx* ctx, const tmat_solution* sol, const tmat_c128* v,
+                                    const tmat_c128* dT_blocks, double* grad_out, tmat_c128* mu_out,
+                                    tmat_solve_info* info) {
+  auto t_start = std::chrono::steady_clock::now();
+  if (!ctx) return TMAT_EINVAL;
+  if (!sol || !v || !dT_blocks || !grad_out) return set_error(ctx, TMAT_EINVAL, "tmat_adjoint_tblocks: bad arguments");
+  if (sol->device != ctx->device) return set_error(ctx, TMAT_EINVAL, "tmat_adjoint_tblocks: solution is on another device");
+  if (!sol->tblocks) return set_error(ctx, TMAT_EINVAL, "tmat_adjoint_tblocks: not a T-block solution (use tmat_adjoint)");
+  Tables* t;
+  TM_TRY(get_tables(ctx, sol->nmax, &t));
+  TM_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int64_t N = sol->N;
+  const int P = t->P;
+  if (info) {
+    *info = tmat_solve_info();
+    info->n_rhs = 1;
+  }
+  const bool mixed = sol->params.precision == TMAT_PREC_MIXED;
+  Staged sv, sd, sg, sm;
+  TM_TRY(stage_in(ctx, "st_v", v, sizeof(double2) * N * P, &sv));
+  TM_TRY(stage_in(ctx, "st_dTb", dT_blocks, sizeof(double2) * sol->n_types * P * P, &sd));
+  TM_TRY(stage_out(ctx, "st_grad", grad_out, sizeof(double) * N, &sg));
+  TM_TRY(stage_out(ctx, "st_mu", mu_out, sizeof(double2) * N * P, &sm));
+  void *one64, *one32 = nullptr;
+  TM_TRY(unit_T(ctx, N * P, false, "sv_one64", &one64));
+  if (mixed) TM_TRY(unit_T(ctx, N * P, true, "sv_one32", &one32));
+  OpPair ops;
+  if (sol->path == TMAT_PATH_NEIGHBOUR) {
+    TM_TRY(make_nbr_ops(t, sol->pos, N, sol->k, sol->nmax, sol->row_ptr, sol->col, sol->cutoff, sol->taper,
+                        (const double2*)one64, (const float2*)one32, mixed, &ops, sol->threed));
+  } else {
+    TM_TRY(make_lattice_ops(ctx, t, sol->pos, N, sol->k, sol->lattice_nx, sol->lattice_ny, sol->lattice_pitch,
+                            sol->cutoff, sol->taper, (const double2*)one64, (const float2*)one32, mixed, &ops, 0));
+  }
+  TBlockDev d;
+  d.c64 = sol->tb64c;
+  d.r64 = sol->tb64r;
+  d.c32 = sol->tb32c;
+  d.r32 = sol->tb32r;
+  d.type = sol->ttype;
+  attach_tblocks(&ops, d);
+  // derivative blocks in the column storage (the row storage is not needed)
+  double2 *dTc, *dTr, *vi, *mu, *As;
+  TM_TRY(scratch(ctx, "adjb_dTc", sizeof(double2) * sol->n_types * P * P, (void**)&dTc));
+  TM_TRY(scratch(ctx, "adjb_dTr", sizeof(double2) * sol->n_types * P * P, (void**)&dTr));
+  tblock_internal_kernel<double><<<(unsigned)std::min<int64_t>(cdiv(sol->n_types * P * P, 256), 16384), 256, 0,
+                                   ctx->stream>>>((const double2*)sd.dev, t->d_perm, sol->n_types, P, dTc, dTr);
+  TM_LAUNCHED(ctx);
+  TM_TRY(scratch(ctx, "adj_v", sizeof(double2) * N * P, (void**)&vi));
+  TM_TRY(scratch(ctx, "adj_mu", sizeof(double2) * N * P, (void**)&mu));
+  TM_TRY(scratch(ctx, "adj_As", sizeof(double2) * N * P, (void**)&As));
+  TM_TRY(to_internal(ctx, t, (const double2*)sv.dev, vi, false, N));
+  SolveStats st;
+  TM_TRY(solve_with(ctx, ops, sol->params.precision, TMAT_OP_ADJOINT, vi, mu, 1, sol->params, &st));
+  TM_TRY(op_apply(ctx, ops.A64, TMAT_OP_COUPLE, sol->s, As, 1));  // e = a0 + A s (fp64)
+  TM_TRY(check_tc_errors(ctx, ops));
+  grad_blocks_kernel<<<(unsigned)cdiv(N, 128), 128, 0, ctx->stream>>>(mu, dTc, sol->ttype, sol->a0, As, N, P,
+                                                                       (double*)sg.dev);
+  TM_LAUNCHED(ctx);
+  if (mu_out) TM_TRY(from_internal(ctx, t, mu, false, (double2*)sm.dev, N));
+  TM_TRY(finish_out(ctx, &sg));
+  TM_TRY(finish_out(ctx, &sm));
+  TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (info) {
+    info->iterations = st.iterations;
+    info->refinements = st.refinements;
+    info->converged = st.converged ? 1 : 0;
+    info->rel_residual[0] = st.rel_res[0];
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  }
+  if (!st.converged)
+    return set_error(ctx, TMAT_ENOCONV, "tmat_adjoint_tblocks: not converged after %d iterations", st.iterations);
   return TMAT_OK;
 }
 
@@ -458,8 +769,8 @@ extern "C" int tmat_position_gradient(tmat_ctx* ctx, const tmat_solution* sol, c
     return set_error(ctx, TMAT_EINVAL, "tmat_position_gradient: bad arguments");
   if (sol->device != ctx->device)
     return set_error(ctx, TMAT_EINVAL, "tmat_position_gradient: solution is on another device");
-  if (sol->path != TMAT_PATH_LATTICE)
-    return set_error(ctx, TMAT_ENOTSUP, "tmat_position_gradient: lattice solutions only");
+  if (sol->path != TMAT_PATH_LATTICE || sol->tblocks)
+    return set_error(ctx, TMAT_ENOTSUP, "tmat_position_gradient: lattice solutions with diagonal T only");
   Tables* t;
   TM_TRY(get_tables(ctx, sol->nmax, &t));
   TM_CUDA(ctx, cudaSetDevice(ctx->device));

@@ -52,6 +52,13 @@ struct Operator {
   int kind = 0;
   NbrOp nbr;
   const LatOp* lat = nullptr;
+  // full per-scatterer T-blocks (internal index order, the operator's precision). When set,
+  // the operator above carries T = 1 and op_apply multiplies by the blocks:
+  //   forward y = x - T (A x); transposed y = x - A^T (T^T x); coupling y = A x.
+  // tbc[(type P + c) P + a] = T[a][c] (for T z), tbr[(type P + c) P + a] = T[c][a] (for T^T x)
+  const void* tbc = nullptr;
+  const void* tbr = nullptr;
+  const int32_t* ttype = nullptr;  // [N] block of each scatterer
   bool fp32() const;
   int64_t N() const;
   int nmax() const;
@@ -91,6 +98,9 @@ int solve_system(tmat_ctx* ctx, const Operator& A64, const Operator* A32, int mo
                  int R, const SolveParams& p, SolveStats* st, const Operator* res64 = nullptr);
 
 int prepare_T(tmat_ctx* ctx, const Tables* t, const double2* T_api, int64_t N, bool fp32, const char* name, void** out);
+// out[r][i][a] = sum_c Tm[(type_i P + c) P + a] in[r][i][c]; with xsub: xsub - that
+int tblock_mul(tmat_ctx* ctx, const void* Tm, const int32_t* type, const void* in, const void* xsub, void* out,
+               int64_t N, int P, int R, bool fp32);
 
 }  // namespace tmat
 
