@@ -49,6 +49,7 @@ extern "C" {
 
 #define TMAT_OK 0
 #define TMAT_EINVAL (-1)     /* bad size, nmax outside 1..6, NaN input, non-coplanar lattice */
+#define TMAT_EOVERLAP (-2)   /* the enclosing spheres of two scatterers intersect (App. I-C) */
 #define TMAT_ENOMEM (-3)     /* device allocation failed */
 #define TMAT_ENOCONV (-4)    /* iteration cap reached; outputs hold the best iterate */
 #define TMAT_EBREAKDOWN (-5) /* GMRES breakdown with a non-zero residual */
@@ -106,6 +107,10 @@ typedef struct {
   double taper;        /* width of a raised-cosine fall-off of the coupling that ends at the cutoff:
                           pair weight 1 for d <= cutoff - taper, 0.5(1 + cos(pi (d - cutoff + taper)/taper))
                           up to the cutoff. 0: hard cutoff. Must be <= cutoff. */
+  const double* enclosing_radii; /* nullable [N] (host or device): radius of each scatterer's enclosing
+                          sphere; when given, the solve first checks that no two enclosing spheres
+                          intersect (|x_i - x_j| < r_i + r_j; touching is allowed) and returns
+                          TMAT_EOVERLAP naming the first such pair (App. I-C assumes none). */
 } tmat_solve_opts;
 
 /* Per-call result summary (host struct). */
@@ -180,6 +185,13 @@ int tmat_measure_fma_peak(int device, int precision, double* tflops_out);
  * row_ptr and *nnz_out, allocate col, call again with the same row_ptr. */
 int tmat_neighbors(tmat_ctx* ctx, const double* pos, int64_t N, double cutoff,
                    int64_t* row_ptr, int32_t* col, int64_t* nnz_out);
+
+/* Enclosing-sphere overlap check (App. I-C: the method assumes that the enclosing spheres of
+ * the scatterers do not intersect): returns TMAT_EOVERLAP when |x_i - x_j| < r_i + r_j for
+ * some pair (fp64, every product and sum rounded; touching spheres pass), with the first
+ * such pair (smallest i, then j) in pair_out[2] (nullable, host), else TMAT_OK. radii[N]
+ * >= 0. Cell-binned: O(N) work. Host or device arrays; synchronises. */
+int tmat_check_overlap(tmat_ctx* ctx, const double* pos, int64_t N, const double* radii, int64_t* pair_out);
 
 /* Sub-region index sets (main text: jinc-source groups with a padding region;
  * Fig. 3 caption). On an nx x ny lattice (site index iy*nx + ix), sub-region

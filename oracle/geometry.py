@@ -54,3 +54,21 @@ def subregion_sets(nx, ny, cx, cy, buf):
             sim = [iy * nx + ix for iy in range(py0, py1) for ix in range(px0, px1)]
             out.append((np.array(core, dtype=np.int64), np.array(sim, dtype=np.int64)))
     return out
+
+
+def first_overlap(pos, radii):
+    """The enclosing-sphere condition of App. I-C (the method assumes no two enclosing
+    spheres intersect): the first pair (i < j, smallest i, then j) with
+    d2 < (r_i + r_j)^2, d2 = dx*dx + dy*dy + dz*dz evaluated left to right, or None.
+    Brute force over all pairs."""
+    pos = np.asarray(pos, dtype=np.float64)
+    n = len(pos)
+    for i in range(n):
+        for j in range(i + 1, n):
+            d = pos[i] - pos[j]
+            d2 = float(d[0]) * float(d[0]) + float(d[1]) * float(d[1])
+            d2 = d2 + float(d[2]) * float(d[2])
+            s = float(radii[i]) + float(radii[j])
+            if d2 < s * s:
+                return i, j
+    return None

@@ -17,7 +17,7 @@ if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_2107_09879_b300.build`")
 lib = ct.CDLL(LIB_PATH)
 
-OK, EINVAL, ENOMEM, ENOCONV, EBREAKDOWN, ECUDA, ENOTSUP = 0, -1, -3, -4, -5, -6, -7
+OK, EINVAL, EOVERLAP, ENOMEM, ENOCONV, EBREAKDOWN, ECUDA, ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
 PREC_FP64, PREC_MIXED, PREC_FP64_TC = 0, 1, 2
 PATH_AUTO, PATH_NEIGHBOUR, PATH_LATTICE = 0, 1, 2
 OP_FORWARD, OP_ADJOINT, OP_COUPLE = 0, 1, 2
@@ -28,7 +28,7 @@ class SolveOpts(ct.Structure):
     _fields_ = [("tol", ct.c_double), ("restart", ct.c_int), ("max_iter", ct.c_int), ("cutoff", ct.c_double),
                 ("precision", ct.c_int), ("inner_tol", ct.c_double), ("path", ct.c_int),
                 ("lattice_nx", ct.c_int), ("lattice_ny", ct.c_int), ("lattice_pitch", ct.c_double),
-                ("taper", ct.c_double)]
+                ("taper", ct.c_double), ("enclosing_radii", ct.c_void_p)]
 
 
 class SolveInfo(ct.Structure):
@@ -89,6 +89,7 @@ _SIGS = {
     "tmat_adjoint": [_vp, _vp, _vp, _vp, _vp, _vp, ct.POINTER(SolveInfo)],
     "tmat_position_gradient": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "tmat_measure_fma_peak": [_int, _int, ct.POINTER(_d)],
+    "tmat_check_overlap": [_vp, _vp, _i64, _vp, _vp],
     "tmat_build_cylinder": [_vp, _vp, _i64, _d, _d, _int, _int, _vp, _vp],
     "tmat_solve_tblocks": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _i64, _vp, _int, ct.POINTER(SolveOpts), _vp,
                            ct.POINTER(_vp), ct.POINTER(SolveInfo)],
@@ -291,6 +292,15 @@ class Context:
             self.check(rc)
         return E, info, rc
 
+    def tmat_check_overlap(self, pos, radii):
+        """None when no two enclosing spheres intersect, else the first pair (i, j)."""
+        pair = np.zeros(2, np.int64)
+        rc = lib.tmat_check_overlap(self.h, ptr(pos), pos.shape[0], ptr(radii), ptr(pair))
+        if rc == EOVERLAP:
+            return int(pair[0]), int(pair[1])
+        self.check(rc)
+        return None
+
     def tmat_build_cylinder(self, cyl, wavelength, n_bg, nmax, n_quad=0, with_dr=False):
         """cyl: (n, 4) float64 [radius, height, n_re, n_im]; returns T (n, P, P) [and dT/dradius]."""
         n = cyl.shape[0]
@@ -402,5 +412,8 @@ def make_sweep(**kw):
 def make_opts(**kw):
     o = SolveOpts()
     for k, v in kw.items():
+        if k == "enclosing_radii" and v is not None:
+            o._radii = v  # keep the array alive as long as the options
+            v = ptr(v)
         setattr(o, k, v)
     return o

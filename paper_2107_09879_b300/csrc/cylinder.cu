@@ -34,25 +34,30 @@ struct CylGeom {
   double2 m_rel;  // refractive index relative to the background
 };
 
-__device__ __forceinline__ double2 cd_div(double2 a, double2 b) {
-  const double s = 1.0 / (b.x * b.x + b.y * b.y);
-  return make_double2((a.x * b.x + a.y * b.y) * s, (a.y * b.x - a.x * b.y) * s);
+// a / b by Smith's method (no squared magnitudes, so no overflow or underflow of |b|^2)
+__host__ __device__ __forceinline__ double2 cd_div(double2 a, double2 b) {
+  if (fabs(b.x) >= fabs(b.y)) {
+    const double r = b.y / b.x, d = b.x + b.y * r;
+    return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+  }
+  const double r = b.x / b.y, d = b.y + b.x * r;
+  return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
 }
-__device__ __forceinline__ double2 cd_sin(double2 z) {
+__host__ __device__ __forceinline__ double2 cd_sin(double2 z) {
   return make_double2(sin(z.x) * cosh(z.y), cos(z.x) * sinh(z.y));
 }
-__device__ __forceinline__ double2 cd_cos(double2 z) {
+__host__ __device__ __forceinline__ double2 cd_cos(double2 z) {
   return make_double2(cos(z.x) * cosh(z.y), -sin(z.x) * sinh(z.y));
 }
-__device__ __forceinline__ double cd_abs2(double2 z) { return z.x * z.x + z.y * z.y; }
+__host__ __device__ __forceinline__ double cd_abs2(double2 z) { return z.x * z.x + z.y * z.y; }
 
 // j_0 .. j_n (n <= CYL_NL) of a complex argument by Miller's downward recurrence
 // j_{l-1} = (2l + 1)/z j_l - j_{l+1}, started far above n and normalised with whichever of
 // j_0 = sin z / z and j_1 = sin z / z^2 - cos z / z is larger (their zeros interlace).
-__device__ void sph_j_complex(double2 z, int n, double2* out) {
+__host__ __device__ void sph_j_complex(double2 z, int n, double2* out) {
   const double az = sqrt(cd_abs2(z));
   const int start = n + 24 + (int)az;
-  double2 jp1 = make_double2(0.0, 0.0), jc = make_double2(1e-280, 0.0);
+  double2 jp1 = make_double2(0.0, 0.0), jc = make_double2(1e-30, 0.0);  // the scale is arbitrary
   double2 keep[CYL_NL + 2];
   for (int l = 0; l <= CYL_NL + 1; ++l) keep[l] = make_double2(0.0, 0.0);
   const double2 iz = cd_div(make_double2(1.0, 0.0), z);
@@ -76,7 +81,7 @@ __device__ void sph_j_complex(double2 z, int n, double2* out) {
 
 // normalised Legendre functions (no Condon-Shortley phase) at cos(theta) = ct, sin = st:
 // Pbar_l^am, pi_l^am = Pbar_l^am / sin (am >= 1) and tau_l^am = d Pbar_l^am / d theta, l <= nmax
-__device__ void legendre_row(int nmax, int am, double ct, double st, double* Pb, double* pi, double* tau) {
+__host__ __device__ void legendre_row(int nmax, int am, double ct, double st, double* Pb, double* pi, double* tau) {
   // Pbar_l^mu for mu = am and, for tau at am = 0, mu = 1
   auto rowP = [&](int mu, double* out, bool over_sin) {
     for (int l = 0; l <= nmax; ++l) out[l] = 0.0;
@@ -121,7 +126,7 @@ struct ProfilePoint {
   double r, ct, st, nr, nt, w;
 };
 
-__device__ ProfilePoint profile_point(const CylGeom& g, int q, int nq, const double* __restrict__ gx,
+__host__ __device__ ProfilePoint profile_point(const CylGeom& g, int q, int nq, const double* __restrict__ gx,
                                       const double* __restrict__ gw) {
   const int face = q / nq, j = q % nq;
   const double a = g.radius, h = g.height;

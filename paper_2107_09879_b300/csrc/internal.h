@@ -106,6 +106,9 @@ void timing_end(tmat_ctx* ctx, const char* kind, cudaEvent_t start, double bytes
 
 // Grow-only scratch owned by the context, keyed by name.
 int scratch(tmat_ctx* ctx, const char* name, size_t bytes, void** out);
+// Enclosing-sphere overlap check of N scatterers (device arrays): TMAT_OK or TMAT_EOVERLAP
+// with the first intersecting pair in pair_out[2] (nullable); synchronises.
+int check_overlap(tmat_ctx* ctx, const double* d_pos, const double* d_rad, int64_t N, int64_t* pair_out);
 // Tables of order nmax (built and uploaded on first use).
 int get_tables(tmat_ctx* ctx, int nmax, Tables** out);
 void free_tables(Tables* t);

@@ -366,6 +366,11 @@ static int solve_impl(tmat_ctx* ctx, const double* pos, int64_t N, double wavele
   TM_TRY(position_flags(ctx, (const double*)spos.dev, N, &pflags));
   if (pflags & 2) return set_error(ctx, TMAT_EINVAL, "tmat_solve: positions must be finite");
   const bool threed = (pflags & 1) != 0;
+  if (opts->enclosing_radii) {
+    Staged srad;
+    TM_TRY(stage_in(ctx, "st_rad", opts->enclosing_radii, sizeof(double) * N, &srad));
+    TM_TRY(check_overlap(ctx, (const double*)spos.dev, (const double*)srad.dev, N, nullptr));
+  }
   if (threed && path == TMAT_PATH_LATTICE)
     return set_error(ctx, TMAT_EINVAL, "tmat_solve: the lattice path needs coplanar positions");
   if (!tb) TM_TRY(stage_in(ctx, "st_T", T_diag, sizeof(double2) * N * P, &sT));

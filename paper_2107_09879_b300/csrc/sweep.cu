@@ -26,6 +26,18 @@ __global__ void sweep_gather_kernel(int nx, double pitch, double x0, double y0, 
   sub_atoms[t] = atoms[(int64_t)iy * nx + ix];
 }
 
+// every site's position and sphere radius (for the overlap check)
+__global__ void sweep_sites_kernel(int nx, int nsites, double pitch, double x0, double y0, double z,
+                                   const tmat_atom* __restrict__ atoms, double* __restrict__ pos,
+                                   double* __restrict__ rad) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nsites) return;
+  pos[3 * t] = x0 + (t % nx) * pitch;
+  pos[3 * t + 1] = y0 + (t / nx) * pitch;
+  pos[3 * t + 2] = z;
+  rad[t] = atoms[t].radius;
+}
+
 __global__ void sweep_sources_kernel(int nx, int nsites, double pitch, double x0, double y0, int cx0, int cy0, int w,
                                      int h, int R, const double2* __restrict__ src_A, double* __restrict__ sxy,
                                      double2* __restrict__ sA) {
@@ -91,6 +103,16 @@ extern "C" int tmat_sweep(tmat_ctx* ctx, const tmat_sweep_opts* sw, const tmat_a
   TM_TRY(scratch(ctx, "sw_Ea", sizeof(double2) * 3 * (size_t)std::max<int64_t>(M, 1), (void**)&Ea));
   TM_TRY(scratch(ctx, "sw_sxy", sizeof(double) * 2 * (size_t)sw->core_x * sw->core_y, (void**)&sxy));
   TM_TRY(scratch(ctx, "sw_sA", sizeof(double2) * 2 * (size_t)R * sw->core_x * sw->core_y, (void**)&sA));
+  {
+    // the spheres of the whole array must not intersect (App. I-C); checked once per call
+    double *pall, *rall;
+    TM_TRY(scratch(ctx, "sw_pos_all", sizeof(double) * 3 * (size_t)nsites, (void**)&pall));
+    TM_TRY(scratch(ctx, "sw_rad_all", sizeof(double) * (size_t)nsites, (void**)&rall));
+    sweep_sites_kernel<<<(unsigned)cdiv(nsites, 256), 256, 0, ctx->stream>>>(
+        nx, nsites, sw->pitch, sw->x0, sw->y0, sw->z, (const tmat_atom*)sa.dev, pall, rall);
+    TM_LAUNCHED(ctx);
+    TM_TRY(check_overlap(ctx, pall, rall, nsites, nullptr));
+  }
   tmat_sweep_info inf = tmat_sweep_info();
   for (int a = first; a < last; ++a) {
     const int ax = a % nax, ay = a / nax;
@@ -111,6 +133,7 @@ extern "C" int tmat_sweep(tmat_ctx* ctx, const tmat_sweep_opts* sw, const tmat_a
                               sw->z0, sw->pitch, sw->n_beta, sw->n_alpha,
                               opts->precision == TMAT_PREC_MIXED ? TMAT_PREC_MIXED : TMAT_PREC_FP64, (tmat_c128*)a0));
     tmat_solve_opts o = *opts;
+    o.enclosing_radii = nullptr;  // checked for the whole array above
     o.path = TMAT_PATH_LATTICE;
     o.lattice_nx = w;
     o.lattice_ny = h;
