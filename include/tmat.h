@@ -340,6 +340,36 @@ int tmat_solve_tblocks(tmat_ctx* ctx, const double* pos, int64_t N, double wavel
                        int R, const tmat_solve_opts* opts, tmat_c128* s_out, tmat_solution** keep,
                        tmat_solve_info* info);
 
+/* ---- batched independent problems (served sub-region jobs) --------------- */
+
+/* One lattice problem of a batch: an nx x ny row-major lattice (site iy*nx + ix at
+ * (ix*pitch, iy*pitch, 0)), its own wavelength, T_diag[nx*ny][P] (tmat_build at that
+ * wavelength), one incident set a0[nx*ny][P] and the output s_out[nx*ny][P]. */
+typedef struct {
+  int nx, ny;
+  double wavelength;
+  const tmat_c128* T_diag;
+  const tmat_c128* a0;
+  tmat_c128* s_out;
+} tmat_batch_problem;
+
+/* Solve n <= TMAT_MAX_RHS independent lattice problems of one nmax (the sub-region jobs of
+ * the main text) together: each is placed at the origin of a canvas_nx x canvas_ny canvas
+ * lattice (0: the largest problem's size) with T = 0 and a0 = 0 on the sites it does not
+ * own, which leaves its solution unchanged, and the problems become the right-hand sides of
+ * one batched operator on the FFT lattice path: every kernel launch of the apply (with each
+ * problem's own block spectra and T) and of GMRES covers the whole batch, and a problem
+ * that has converged leaves the Arnoldi work. A problem's result depends only on its own
+ * data and the canvas size (fix the canvas per size class to make results independent of
+ * the rest of the batch). opts: tol, restart, max_iter, cutoff, taper, inner_tol and
+ * precision (TMAT_PREC_FP64 or TMAT_PREC_MIXED) as tmat_solve; the path is the lattice.
+ * infos[n] (nullable, host): per problem (iterations and refinements are the batch's).
+ * TMAT_ENOTSUP when the canvas does not fit the FFT operator; TMAT_ENOCONV when some
+ * problem did not converge (every output holds its best iterate). Host or device arrays;
+ * synchronises. */
+int tmat_solve_batch(tmat_ctx* ctx, const tmat_batch_problem* probs, int n, double n_bg, int nmax, double pitch,
+                     int canvas_nx, int canvas_ny, const tmat_solve_opts* opts, tmat_solve_info* infos);
+
 /* ---- sub-region sweep (main text; Fig. 3) -------------------------------- */
 
 /* Geometry and decomposition of a large-area sweep. Sites (ix, iy) of an

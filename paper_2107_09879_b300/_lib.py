@@ -53,6 +53,11 @@ class SweepInfo(ct.Structure):
                 ("seconds", ct.c_double)]
 
 
+class BatchProblem(ct.Structure):
+    _fields_ = [("nx", ct.c_int), ("ny", ct.c_int), ("wavelength", ct.c_double), ("T_diag", ct.c_void_p),
+                ("a0", ct.c_void_p), ("s_out", ct.c_void_p)]
+
+
 class Atom(ct.Structure):
     _fields_ = [("radius", ct.c_double), ("n_re", ct.c_double), ("n_im", ct.c_double)]
 
@@ -90,6 +95,7 @@ _SIGS = {
     "tmat_position_gradient": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "tmat_measure_fma_peak": [_int, _int, ct.POINTER(_d)],
     "tmat_check_overlap": [_vp, _vp, _i64, _vp, _vp],
+    "tmat_solve_batch": [_vp, _vp, _int, _d, _int, _d, _int, _int, ct.POINTER(SolveOpts), _vp],
     "tmat_build_cylinder": [_vp, _vp, _i64, _d, _d, _int, _int, _vp, _vp],
     "tmat_solve_tblocks": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _i64, _vp, _int, ct.POINTER(SolveOpts), _vp,
                            ct.POINTER(_vp), ct.POINTER(SolveInfo)],
@@ -291,6 +297,23 @@ class Context:
         if rc not in (OK, ENOCONV):
             self.check(rc)
         return E, info, rc
+
+    def tmat_solve_batch(self, problems, n_bg, nmax, pitch, opts, canvas=(0, 0)):
+        """problems: list of dicts nx, ny, wavelength, T (nx*ny, P), a0 (nx*ny, P) complex128 (numpy
+        or torch). Returns (list of s (nx*ny, P), list of SolveInfo, rc)."""
+        n = len(problems)
+        arr = (BatchProblem * n)()
+        outs = []
+        for i, p in enumerate(problems):
+            s = empty_like_space(p["a0"], p["a0"].shape, np.complex128)
+            outs.append(s)
+            arr[i].nx, arr[i].ny, arr[i].wavelength = p["nx"], p["ny"], p["wavelength"]
+            arr[i].T_diag, arr[i].a0, arr[i].s_out = ptr(p["T"]).value, ptr(p["a0"]).value, ptr(s).value
+        infos = (SolveInfo * n)()
+        rc = lib.tmat_solve_batch(self.h, arr, n, n_bg, nmax, pitch, canvas[0], canvas[1], ct.byref(opts), infos)
+        if rc not in (OK, ENOCONV):
+            self.check(rc)
+        return outs, list(infos), rc
 
     def tmat_check_overlap(self, pos, radii):
         """None when no two enclosing spheres intersect, else the first pair (i, j)."""

@@ -257,7 +257,7 @@ static int fft_rows(tmat_ctx* ctx, const C<R>* in, int64_t in_bs, int in_pitch, 
 // transpose through shared memory (sites along ix x components).
 template <typename R, int MODE>
 __global__ void fft_embed_kernel(const C<R>* __restrict__ x, const C<R>* __restrict__ T, int nx, int ny, int P, int R_,
-                                 C<R>* __restrict__ Xc) {
+                                 C<R>* __restrict__ Xc, int64_t tstride) {
   __shared__ C<R> tile[32][33];
   const int ix0 = blockIdx.x * 32, iy = blockIdx.y;
   const int r = blockIdx.z / ((P + 31) / 32), u0 = (blockIdx.z % ((P + 31) / 32)) * 32;
@@ -268,7 +268,7 @@ __global__ void fft_embed_kernel(const C<R>* __restrict__ x, const C<R>* __restr
     if (ix < nx && u < P) {
       const int64_t site = (int64_t)iy * nx + ix;
       v = x[((int64_t)r * N + site) * P + u];
-      if (MODE == 1) v = cmul(T[site * P + u], v);
+      if (MODE == 1) v = cmul(T[r * tstride + site * P + u], v);
     }
     tile[q][threadIdx.x] = v;
   }
@@ -283,7 +283,7 @@ __global__ void fft_embed_kernel(const C<R>* __restrict__ x, const C<R>* __restr
 // MODE 1 y = x - Yc', MODE 2 y = Yc'
 template <typename R, int MODE>
 __global__ void fft_extract_kernel(const C<R>* __restrict__ Yc, const C<R>* __restrict__ x, const C<R>* __restrict__ T,
-                                   int nx, int ny, int P, R scale, C<R>* __restrict__ y) {
+                                   int nx, int ny, int P, R scale, C<R>* __restrict__ y, int64_t tstride) {
   __shared__ C<R> tile[32][33];
   const int ix0 = blockIdx.x * 32, iy = blockIdx.y;
   const int r = blockIdx.z / ((P + 31) / 32), u0 = (blockIdx.z % ((P + 31) / 32)) * 32;
@@ -305,7 +305,7 @@ __global__ void fft_extract_kernel(const C<R>* __restrict__ Yc, const C<R>* __re
       if (MODE == 2) {
         out = a;
       } else if (MODE == 0) {
-        out = csub(x[o], cmul(T[site * P + u], a));
+        out = csub(x[o], cmul(T[r * tstride + site * P + u], a));
       } else {
         out = csub(x[o], a);
       }
@@ -350,7 +350,7 @@ constexpr int FFT_MUL_THREADS = 128;
 template <typename R, int L, int MODE, int RC>
 __global__ void __launch_bounds__(FFT_MUL_THREADS, 2)
 fft_mul_kernel(const C<R>* __restrict__ Bh, const C<R>* __restrict__ Xh, C<R>* __restrict__ Yh, int Mx, int My,
-               int R_, int CX, int CY, const int* __restrict__ mirror, int msign) {
+               int R_, int CX, int CY, const int* __restrict__ mirror, int msign, int64_t bstride) {
   constexpr int P = 2 * L, TS = FFT_MUL_THREADS;
   extern __shared__ __align__(16) unsigned char xsm[];
   C<R>* x1 = reinterpret_cast<C<R>*>(xsm) + threadIdx.x;  // [RC][L][TS]: X^(f1), this thread's column
@@ -402,7 +402,7 @@ fft_mul_kernel(const C<R>* __restrict__ Bh, const C<R>* __restrict__ Xh, C<R>* _
 #define FFT_MUL_LOAD(U, DST)                                                                 \
   _Pragma("unroll") for (int v = 0; v < L; ++v) {                                            \
     const int comp = MODE == 1 ? (c * L + v) * L + (U) : (c * L + (U)) * L + v;              \
-    DST[v] = Bh[(int64_t)comp * F + fb];                                                     \
+    DST[v] = Bh[(int64_t)r0 * bstride + (int64_t)comp * F + fb];                             \
   }
 #define FFT_MUL_USE(U, G)                                                                    \
   {                                                                                          \
@@ -466,11 +466,11 @@ fft_mul_kernel(const C<R>* __restrict__ Bh, const C<R>* __restrict__ Xh, C<R>* _
 // conflicts) and the column values by broadcast.
 constexpr uint32_t FFT4_WAIT_LIMIT = 1u << 22;  // polls of a bounded mbarrier wait
 
-template <int L>
+template <int L, int RC_ = 2>
 struct Fft4Cfg {
   static constexpr int NI = L <= 24 ? 4 : 2;  // items (consecutive ky) per tile
   static constexpr int THREADS = NI * 2 * L;
-  static constexpr int RC = 2;                // RHS per pass
+  static constexpr int RC = RC_;              // RHS per pass (1 when every RHS has its own spectra)
   static constexpr int NCOL = 4 * RC;         // columns: 4 frequencies x RC RHS
   // stride of one class block of C in complex values: >= L^2 and = 8 (mod 16), so that the
   // two class blocks of an item start 16 banks apart (a warp spanning both reads C without
@@ -506,11 +506,13 @@ __device__ __forceinline__ bool fft4_wait(uint32_t bar, uint32_t parity) {
 __device__ __constant__ int c_fft4_in_j[2][4] = {{1, 0, 0, 1}, {0, 1, 1, 0}};
 __device__ __constant__ int c_fft4_in_s[2][4] = {{3, 1, 2, 0}, {3, 1, 2, 0}};
 
-template <int L, int MODE>
-__global__ void __launch_bounds__(Fft4Cfg<L>::THREADS, Fft4Cfg<L>::MIN_BLOCKS)
+// cstride: complex values between the spectra of consecutive RHS (0: one operator for all
+// RHS; otherwise RC = 1 and every RHS pass stages its own C)
+template <int L, int MODE, int RC_>
+__global__ void __launch_bounds__(Fft4Cfg<L, RC_>::THREADS, Fft4Cfg<L, RC_>::MIN_BLOCKS)
 fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, float2* __restrict__ Yh, int Mx, int My,
-                int R_, const int* __restrict__ sym, int* __restrict__ err) {
-  using Cfg = Fft4Cfg<L>;
+                int R_, const int* __restrict__ sym, int* __restrict__ err, int64_t cstride) {
+  using Cfg = Fft4Cfg<L, RC_>;
   constexpr int NI = Cfg::NI, RC = Cfg::RC, NCOL = Cfg::NCOL, P = 2 * L, SC = Cfg::SC, SW = Cfg::SW,
                 NT = Cfg::THREADS;
   constexpr int OUT_J[2][4] = {{0, 1, 1, 0}, {1, 0, 0, 1}};
@@ -542,11 +544,11 @@ fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, fl
     ky0 = (int)(tl % tpr) * NI;
     ni = min(NI, hy - ky0);
   };
-  auto issue_c = [&](int64_t tl) {
+  auto issue_c = [&](int64_t tl, int r0) {
     int kx, ky0, ni;
     tile_of(tl, kx, ky0, ni);
     const uint32_t bytes = (uint32_t)(ni * 2 * SC * sizeof(float2));
-    const float2* src = Cq + ((int64_t)kx * hy + ky0) * 2 * SC;
+    const float2* src = Cq + (int64_t)r0 * cstride + ((int64_t)kx * hy + ky0) * 2 * SC;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
@@ -590,7 +592,7 @@ fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, fl
 
   int64_t tile = blockIdx.x;
   uint32_t phase = 0;
-  if (t == 0) issue_c(tile);
+  if (t == 0) issue_c(tile, 0);
   load_w(tile, 0);
   store_w();
   for (;;) {
@@ -601,12 +603,16 @@ fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, fl
     const unsigned vmask = it < ni ? (1u | (dy ? 2u : 0u) | (dx ? 4u : 0u) | (dx && dy ? 8u : 0u)) : 0u;
     for (int r0 = 0; r0 < R_; r0 += RC) {
       int bad = 0;
-      if (r0 == 0) bad = !fft4_wait(bar, phase);
+      const uint32_t wphase = phase;
+      if (r0 == 0 || cstride) {
+        bad = !fft4_wait(bar, wphase);
+        if (cstride) phase ^= 1u;  // one copy per RHS pass
+      }
       bad = __syncthreads_or(bad);  // also makes this stage's Ws visible
       if (bad) {
         if (t == 0) {
           atomicAdd(err, 1);
-          fft4_wait(bar, phase);  // let the copy in flight land before the CTA leaves
+          fft4_wait(bar, wphase);  // let the copy in flight land before the CTA leaves
         }
         return;
       }
@@ -632,7 +638,7 @@ fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, fl
       const int64_t ntile = more_rhs ? tile : tile + gridDim.x;
       const bool have_next = ntile < ntiles;
       if (have_next) {
-        if (!more_rhs && t == 0) issue_c(ntile);
+        if ((!more_rhs || cstride) && t == 0) issue_c(ntile, more_rhs ? r0 + RC : 0);
         load_w(ntile, more_rhs ? r0 + RC : 0);
       }
 #pragma unroll
@@ -650,7 +656,7 @@ fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, fl
     }
     tile += gridDim.x;
     if (tile >= ntiles) break;
-    phase ^= 1u;
+    if (!cstride) phase ^= 1u;
   }
 }
 
@@ -776,48 +782,53 @@ static int fft_apply_t(tmat_ctx* ctx, const LatOp& a, const void* xv, void* yv, 
   cudaEvent_t ev_all = timing_begin(ctx);
   dim3 tb(32, 8);
   dim3 tg((unsigned)cdiv(nx, 32), (unsigned)ny, (unsigned)(R_ * cdiv(P, 32)));
-  fft_embed_kernel<R, MODE == 1 ? 1 : 0><<<tg, tb, 0, ctx->stream>>>(x, T, nx, ny, P, R_, grid);
+  fft_embed_kernel<R, MODE == 1 ? 1 : 0><<<tg, tb, 0, ctx->stream>>>(x, T, nx, ny, P, R_, grid, a.t_stride);
   TM_LAUNCHED(ctx);
   TM_TRY(fft2_forward<R>(ctx, grid, nx, ny, Mx, My, nb, w1, Xh, tw));
   bool quad_done = false;
   if constexpr (sizeof(R) == 4) {
     if (a.fft_C) {
-      using Cfg = Fft4Cfg<L>;
-      auto kern = fft_mul4_kernel<L, MODE == 1 ? 1 : 0>;
-      if (Cfg::SMEM > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, Cfg::SMEM));
+      // one RHS per pass when every RHS has its own operator
+      using Cfg = Fft4Cfg<L, 2>;
+      auto kern = a.fft_cstride ? fft_mul4_kernel<L, MODE == 1 ? 1 : 0, 1> : fft_mul4_kernel<L, MODE == 1 ? 1 : 0, 2>;
+      const size_t smem = a.fft_cstride ? Fft4Cfg<L, 1>::SMEM : Cfg::SMEM;
+      if (smem > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, smem));
       const int hx = Mx >= 2 ? Mx / 2 + 1 : 1, hy = My >= 2 ? My / 2 + 1 : 1;
       const int64_t ntiles = (int64_t)hx * cdiv(hy, Cfg::NI);
       int per_sm = 0;
-      TM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::THREADS, Cfg::SMEM));
+      TM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::THREADS, smem));
       const int64_t grid = std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * std::max(1, per_sm));
       cudaEvent_t ev = timing_begin(ctx);
-      kern<<<(unsigned)grid, Cfg::THREADS, Cfg::SMEM, ctx->stream>>>((const float2*)a.fft_C, (const float2*)Xh,
-                                                                     (float2*)Yh, Mx, My, R_, a.fft_sym, a.fft_err);
+      kern<<<(unsigned)grid, Cfg::THREADS, smem, ctx->stream>>>((const float2*)a.fft_C, (const float2*)Xh, (float2*)Yh,
+                                                                Mx, My, R_, a.fft_sym, a.fft_err, a.fft_cstride);
       TM_LAUNCHED(ctx);
       // the quad-form spectra once, the RHS spectra in and out
-      const double mul_bytes = (double)sizeof(float2) * ((double)hx * hy * 2.0 * Cfg::SC + 2.0 * nb * F);
+      const double mul_bytes =
+          (double)sizeof(float2) * ((double)hx * hy * 2.0 * Cfg::SC * (a.fft_cstride ? R_ : 1) + 2.0 * nb * F);
       timing_end(ctx, "lattice_fft_mul32", ev, mul_bytes);
       quad_done = true;
     }
   }
   if (!quad_done) {
-    constexpr int RC = (sizeof(R) == 4 && L <= 24) ? 2 : 1;
+    constexpr int RC2 = (sizeof(R) == 4 && L <= 24) ? 2 : 1;
+    const int RC = a.fft_bstride ? 1 : RC2;  // one RHS per pass when every RHS has its own spectra
     const size_t msm = sizeof(C<R>) * 2 * (size_t)RC * L * FFT_MUL_THREADS;
-    auto kern = fft_mul_kernel<R, L, MODE, RC>;
+    auto kern = RC == 1 ? fft_mul_kernel<R, L, MODE, 1> : fft_mul_kernel<R, L, MODE, RC2>;
     if (msm > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, msm));
     const int64_t items = (int64_t)Mx * (My >= 2 ? My / 2 + 1 : 1);
     dim3 g((unsigned)cdiv(items, FFT_MUL_THREADS), 2);
     cudaEvent_t ev = timing_begin(ctx);
     kern<<<g, FFT_MUL_THREADS, msm, ctx->stream>>>((const C<R>*)a.fft_Bhat, Xh, Yh, Mx, My, R_, a.CX, a.CY,
-                                                   a.fft_mirror, a.fft_mirror_sign);
+                                                   a.fft_mirror, a.fft_mirror_sign, a.fft_bstride);
     TM_LAUNCHED(ctx);
     // the block spectra of one frequency per mirror pair, the RHS spectra in and out
-    const double mul_bytes = (double)sizeof(C<R>) * (items * 2.0 * L * L + 2.0 * nb * F);
+    const double mul_bytes = (double)sizeof(C<R>) * (items * 2.0 * L * L * (a.fft_bstride ? R_ : 1) + 2.0 * nb * F);
     timing_end(ctx, sizeof(R) == 4 ? "lattice_fft_mul32" : "lattice_fft_mul64", ev, mul_bytes);
   }
   C<R>* Yc = Xh;  // X^ is no longer needed
   TM_TRY(fft2_inverse<R>(ctx, Yh, nx, ny, Mx, My, nb, w1, Yc, tw));
-  fft_extract_kernel<R, MODE><<<tg, tb, 0, ctx->stream>>>(Yc, x, T, nx, ny, P, (R)(1.0 / (double)F), (C<R>*)yv);
+  fft_extract_kernel<R, MODE><<<tg, tb, 0, ctx->stream>>>(Yc, x, T, nx, ny, P, (R)(1.0 / (double)F), (C<R>*)yv,
+                                                          a.t_stride);
   TM_LAUNCHED(ctx);
   timing_end(ctx, sizeof(R) == 4 ? "lattice_apply_fft32" : "lattice_apply_fft64", ev_all);
   return TMAT_OK;

@@ -46,6 +46,10 @@ struct LatOp {
   // the symmetric matrix C = B^(kx, ky) S, S = J diag((-1)^m), item-major [items][2][L][L]
   const void* fft_C = nullptr;
   int* fft_err = nullptr;  // device counter of CTAs that gave up on a bounded wait
+  // batched operators (one independent problem per RHS, FFT path): per-RHS strides, in
+  // complex values, of T ([R][N][P]), of the block spectra and of the quad-form spectra;
+  // 0 = one operator shared by every RHS
+  int64_t t_stride = 0, fft_bstride = 0, fft_cstride = 0;
 };
 // An operator instance in one precision. kind 0: neighbour list; kind 1: lattice.
 struct Operator {
