@@ -407,20 +407,25 @@ def bench_adjoint(ctx, torch, steps=3):
 
 def bench_served(args, torch):
     """Served stream of sub-region requests (k x k jinc core + 4-pitch ring, k ~ U{10..60},
-    nmax ~ U{3,4,5}, wavelength ~ U[0.9, 1.1]): Poisson arrivals at 1.5x and 0.5x of the
-    measured single-stream service rate."""
+    nmax ~ U{3,4,5}, wavelength ~ U[0.9, 1.1]) with continuous batching: Poisson arrivals at
+    1.5x and 0.5x of the measured single-stream service rate (one request at a time, no
+    batching), `args.served_requests` requests at 1.5x."""
     from paper_2107_09879_b300 import serve
-    calib = W.served_stream(8, seed=W.BASE_SEED + 3, rate_per_s=0.0)
-    srv = serve.Server(slots=1, mem_budget=64 << 30)
+    calib = W.served_stream(16, seed=W.BASE_SEED + 3, rate_per_s=0.0)
+    srv = serve.Server(slots=1, mem_budget=64 << 30, max_batch=1)
     srv.run(calib[:2])  # warm-up
     t0 = time.perf_counter()
     srv.run(calib)
     mu = len(calib) / (time.perf_counter() - t0)
     srv.close()
-    out = {"workload": "served_subregions_k10-60_ring4_nmax3-5_mixed", "single_stream_solves_per_s": mu}
-    for name, factor, n in (("rate_1.5x", 1.5, args.served_requests), ("rate_0.5x", 0.5, max(8, args.served_requests // 4))):
+    out = {"workload": "served_subregions_k10-60_ring4_nmax3-5_mixed_batched",
+           "single_stream_solves_per_s": mu,
+           "note": "continuous batching: up to 8 requests of one nmax and canvas class per batch, 4 slots "
+                   "(streams); latency = finish - arrival"}
+    for name, factor, n in (("rate_1.5x", 1.5, args.served_requests), ("rate_0.5x", 0.5, max(16, args.served_requests // 4))):
         reqs = W.served_stream(n, seed=W.BASE_SEED + 3, rate_per_s=factor * mu)
-        srv = serve.Server(slots=4, mem_budget=64 << 30)
+        srv = serve.Server(slots=4, mem_budget=64 << 30, max_batch=8)
+        srv.run(reqs[:4])  # warm-up of the slots' contexts
         t0 = time.perf_counter()
         recs = srv.run(reqs)
         wall = time.perf_counter() - t0
@@ -428,7 +433,18 @@ def bench_served(args, torch):
         summ = serve.summarize(recs, wall)
         summ["arrival_rate_per_s"] = factor * mu
         summ["mem_high_water_bytes_est"] = srv.mem_high
+        summ["ctx_scratch_high_water_bytes"] = srv.ctx_mem_high
         out[name] = summ
+    # saturation: every request queued at t = 0, with and without batching
+    for name, mb in (("burst_batched", 8), ("burst_unbatched", 1)):
+        reqs = W.served_stream(args.served_requests // 2, seed=W.BASE_SEED + 8, rate_per_s=0.0)
+        srv = serve.Server(slots=4, mem_budget=64 << 30, max_batch=mb)
+        srv.run(reqs[:4])
+        t0 = time.perf_counter()
+        recs = srv.run(reqs)
+        wall = time.perf_counter() - t0
+        srv.close()
+        out[name] = serve.summarize(recs, wall)
     return out
 
 
@@ -936,7 +952,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads (fp64 plain estimate, 8x8 fp64, adjoint, served stream, sweep)")
-    ap.add_argument("--served-requests", type=int, default=48, help="requests in the 1.5x-rate served stream")
+    ap.add_argument("--served-requests", type=int, default=512, help="requests in the 1.5x-rate served stream")
     ap.add_argument("--ref-matvecs", type=int, default=276, help="operator applications per solve for the oracle arm")
     ap.add_argument("--kernel-only", action="store_true", help="time the dominant kernel alone (for ncu captures)")
     ap.add_argument("--kernel-precision", type=int, default=1, help="1: complex64 apply, 0: complex128 apply, 2: fp64-class tensor-core apply")
@@ -950,6 +966,7 @@ def main():
     ap.add_argument("--tc-variant", type=int, default=1, choices=[1, 2],
                     help="tensor-core lattice kernel: 1 window view (default), 2 gather")
     ap.add_argument("--launch-summary", metavar="CSV", help="summarise an ncu launch list by kernel and exit")
+    ap.add_argument("--served-only", action="store_true", help="run only the served-stream workload")
     ap.add_argument("--window-study", action="store_true",
                     help="coupling-window study: every pair vs hard cutoff vs raised-cosine windows")
     ap.add_argument("--study-size", type=int, default=60)
@@ -975,6 +992,10 @@ def main():
         return
     if args.window_study:
         print(json.dumps(run_window_study(args)))
+        return
+    if args.served_only:
+        import torch
+        print(json.dumps(bench_served(args, torch)))
         return
     if args.impl == "reference":
         if world > 1 and rank != 0:

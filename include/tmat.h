@@ -131,6 +131,9 @@ int tmat_ctx_create(int device, void* cuda_stream, tmat_ctx** out);
 int tmat_ctx_set_stream(tmat_ctx* ctx, void* cuda_stream);
 int tmat_ctx_destroy(tmat_ctx* ctx);
 const char* tmat_last_error(const tmat_ctx* ctx);
+/* Device memory this context holds as scratch (bytes, host int64): what it has allocated
+ * for Krylov bases, block spectra, work grids and tables; freed by tmat_ctx_destroy. */
+int tmat_ctx_memory(const tmat_ctx* ctx, int64_t* bytes_out);
 /* Number of kernels this context has launched so far (for launch accounting). */
 int64_t tmat_ctx_launch_count(const tmat_ctx* ctx);
 

@@ -96,6 +96,7 @@ _SIGS = {
     "tmat_measure_fma_peak": [_int, _int, ct.POINTER(_d)],
     "tmat_check_overlap": [_vp, _vp, _i64, _vp, _vp],
     "tmat_solve_batch": [_vp, _vp, _int, _d, _int, _d, _int, _int, ct.POINTER(SolveOpts), _vp],
+    "tmat_ctx_memory": [_vp, ct.POINTER(_i64)],
     "tmat_build_cylinder": [_vp, _vp, _i64, _d, _d, _int, _int, _vp, _vp],
     "tmat_solve_tblocks": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _i64, _vp, _int, ct.POINTER(SolveOpts), _vp,
                            ct.POINTER(_vp), ct.POINTER(SolveInfo)],
@@ -163,6 +164,12 @@ class Context:
 
     def set_stream(self, stream):
         self.check(lib.tmat_ctx_set_stream(self.h, stream))
+
+    def memory(self):
+        """Device scratch held by this context, bytes."""
+        b = ct.c_int64()
+        self.check(lib.tmat_ctx_memory(self.h, ct.byref(b)))
+        return b.value
 
     def launches(self):
         return lib.tmat_ctx_launch_count(self.h)

@@ -225,3 +225,11 @@ extern "C" int tmat_ctx_kernel_time(tmat_ctx* ctx, const char* kind, int64_t* la
   }
   return TMAT_OK;
 }
+
+extern "C" int tmat_ctx_memory(const tmat_ctx* ctx, int64_t* bytes_out) {
+  if (!ctx || !bytes_out) return TMAT_EINVAL;
+  int64_t b = 0;
+  for (const auto& kv : ctx->bufs) b += (int64_t)kv.second.bytes;
+  *bytes_out = b;
+  return TMAT_OK;
+}

@@ -1,14 +1,25 @@
-"""Request loop for sub-region solves on one GPU (the paper's sub-region jobs,
-main text "Low-overhead multi-GPU simulation strategy", run as a served stream).
+"""Request loop for sub-region solves on one GPU (the paper's sub-region jobs, main text
+"Low-overhead multi-GPU simulation strategy", run as a served stream).
 
-A request is one sub-region: a k x k core of jinc sources (App. II) sampling a
-normally incident x-polarised plane wave, the core plus a padding ring of
-spheres, its own wavelength and nmax. The loop admits requests in arrival order
-when a slot is free and the request's device-memory estimate fits the budget;
-every slot owns a library context bound to its own CUDA stream, so admitted
-requests run concurrently and their kernels overlap on the device. Each request
-is solved by the same deterministic kernels whatever else runs, so its result
-does not depend on the mix.
+A request is one sub-region: a k x k core of jinc sources (App. II) sampling a normally
+incident x-polarised plane wave, the core plus a padding ring of spheres, its own
+wavelength and nmax.
+
+Continuous batching: whenever a slot is free the loop forms a batch from the requests that
+have arrived (oldest first; up to `max_batch` requests of the same nmax and canvas class),
+admits it if its device memory fits, and solves it with one tmat_solve_batch call on the
+slot's own library context and CUDA stream: the requests of a batch share every kernel
+launch (FFT applies with their own block spectra, Arnoldi and Givens passes), their Krylov
+bases stay resident on the device through all refinement steps, and batches on different
+slots overlap on the GPU. Requests that arrive while batches run wait only for the next free
+slot. A request's canvas (the lattice its problem is placed on) depends only on its own size
+class, so its result does not depend on what it was batched with (to rounding in fp64,
+within the solve tolerance in mixed precision).
+
+Admission is by device memory: a batch's estimate (request_bytes) must fit both the
+configured budget and the free memory the driver reports (cudaMemGetInfo through torch),
+and the contexts' own scratch (tmat_ctx_memory, what the library really holds) is sampled
+after every batch and reported beside the estimate.
 
 Everything numeric runs in the native library (libtmat.so) through `_lib`.
 """
@@ -22,40 +33,62 @@ import numpy as np
 
 from . import _lib
 
+CANVAS_CLASSES = (24, 32, 48, 68)  # canvas side of a request: the smallest class >= its side
+
+
+def canvas_of(side):
+    for c in CANVAS_CLASSES:
+        if side <= c:
+            return c
+    return side
+
 
 def request_bytes(side, nmax, R=1, restart=60, cutoff_sites=16):
-    """Device-memory estimate of one request (Krylov basis, vectors, blocks, the FFT
-    operator's block spectra and work grids, tables)."""
-    N = side * side
+    """Device-memory estimate of one request on its canvas (Krylov basis, vectors, blocks,
+    the FFT operator's block spectra and work grids, jinc staging)."""
+    c = canvas_of(side)
+    N = c * c
     P = 2 * nmax * (nmax + 2)
     L = P // 2
     krylov = (restart + 1) * R * N * P * 8
     vectors = 14 * R * N * P * 16
     blocks = 800 * 2 * L ** 2 * (16 + 8 + 2 * 8)
     M = 1
-    while M < side + cutoff_sites:
+    while M < c + cutoff_sites:
         M *= 2
-    spectra = 2 * L * L * M * M * (16 * 3 + 8)  # complex128 spectra + 2 staging grids, complex64 spectra
+    spectra = 2 * L * L * M * M * (16 * 2 + 8 * 2)  # complex128 + complex64 spectra, batch copies
     work = R * P * M * M * (16 * 3 + 8 * 3)
     jinc = 8192 * R * P * 16
     return krylov + vectors + blocks + spectra + work + jinc + (8 << 20)
 
 
+def ct_stream(torch_stream):
+    return torch_stream.cuda_stream
+
+
+def _device_free_bytes(device):
+    import torch
+    free, _ = torch.cuda.mem_get_info(device)
+    return free
+
+
 class Server:
     def __init__(self, slots=4, mem_budget=8 << 30, device=0, tol=1e-7, cutoff=8.0, restart=60, z0=-1.0,
-                 detector_height=5.0, inner_tol=1e-4):
+                 detector_height=5.0, inner_tol=1e-4, max_batch=8, reserve_bytes=2 << 30):
         import torch
-        self.slots = slots
-        self.mem_budget = mem_budget
+        self.slots, self.mem_budget, self.device = slots, mem_budget, device
         self.tol, self.cutoff, self.restart, self.z0, self.det_h = tol, cutoff, restart, z0, detector_height
-        self.inner_tol = inner_tol
+        self.inner_tol, self.max_batch, self.reserve = inner_tol, max_batch, reserve_bytes
         self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
         self.ctxs = [_lib.Context(device, ct_stream(s)) for s in self.streams]
         self.pool = [cf.ThreadPoolExecutor(max_workers=1) for _ in range(slots)]
         self.lock = threading.Condition()
         self.free = collections.deque(range(slots))
         self.mem_in_use = 0
-        self.mem_high = 0
+        self.mem_high = 0           # largest sum of the estimates of the batches in flight
+        self.ctx_mem_high = 0       # largest measured scratch held by the contexts
+        self.batches = []           # sizes of the batches run
+        self.slot_mem = [0] * slots  # scratch each slot's context held after its last batch
 
     def close(self):
         for p in self.pool:
@@ -63,9 +96,8 @@ class Server:
         for c in self.ctxs:
             c.close()
 
-    # ---- one request, on its slot's context -------------------------------------
-    def _solve(self, slot, req):
-        ctx = self.ctxs[slot]
+    # ---- one batch, on its slot's context ------------------------------------------
+    def _problem(self, ctx, req):
         side, k, b, nmax, w = req["side"], req["k"], req["buf"], req["nmax"], req["wavelength"]
         pitch = 0.5
         n = side * side
@@ -76,44 +108,75 @@ class Server:
         atoms = np.stack([req["radii"], np.full(n, 2.0), np.zeros(n)], axis=1)
         cy, cx = np.divmod(np.arange(k * k), k)
         src = np.stack([(cx + b) * pitch, (cy + b) * pitch], axis=1)
-        kk = 2 * math.pi / w
         A = np.zeros((1, k * k, 2), complex)
-        A[0, :, 0] = np.exp(1j * kk * self.z0)  # normally incident x-polarised plane wave at z = z0
+        A[0, :, 0] = np.exp(1j * (2 * math.pi / w) * self.z0)  # x-polarised plane wave at normal incidence, z = z0
         T = ctx.tmat_build(atoms, w, 1.0, nmax)
         a0 = ctx.tmat_incident_jinc(pos, w, 1.0, nmax, src, A, self.z0, precision=_lib.PREC_MIXED, src_pitch=pitch)
-        opts = _lib.make_opts(tol=self.tol, restart=self.restart, max_iter=3000, cutoff=self.cutoff,
-                              taper=self.cutoff, precision=_lib.PREC_MIXED, inner_tol=self.inner_tol, path=_lib.PATH_LATTICE,
-                              lattice_nx=side, lattice_ny=side, lattice_pitch=pitch)
-        s, info, _, rc = ctx.tmat_solve(pos, w, 1.0, nmax, T, a0, opts)
-        c = (side - 1) * pitch / 2
-        det = np.array([[c, c, self.det_h]])
-        E = ctx.tmat_field(pos, w, 1.0, nmax, s[0], det)
-        return s, E, info, rc
+        return dict(nx=side, ny=side, wavelength=w, T=T, a0=np.ascontiguousarray(a0[0]), pos=pos)
 
-    # ---- the loop ----------------------------------------------------------------
+    def _solve_batch(self, slot, reqs):
+        ctx = self.ctxs[slot]
+        nmax = reqs[0]["nmax"]
+        canvas = canvas_of(max(r["side"] for r in reqs))
+        probs = [self._problem(ctx, r) for r in reqs]
+        opts = _lib.make_opts(tol=self.tol, restart=self.restart, max_iter=3000, cutoff=self.cutoff,
+                              taper=self.cutoff, precision=_lib.PREC_MIXED, inner_tol=self.inner_tol)
+        outs, infos, rc = ctx.tmat_solve_batch(probs, 1.0, nmax, 0.5, opts, canvas=(canvas, canvas))
+        res = []
+        for p, s, info in zip(probs, outs, infos):
+            c = (p["nx"] - 1) * 0.5 / 2
+            E = ctx.tmat_field(p["pos"], p["wavelength"], 1.0, nmax, s, np.array([[c, c, self.det_h]]))
+            res.append((s, E, info))
+        return res, rc, ctx.memory()
+
+    # ---- batch formation -----------------------------------------------------------
+    def _take_batch(self, ready):
+        """The oldest ready request and up to max_batch - 1 more of the same nmax and canvas
+        class, as many as the memory budget left over by the running batches allows (at least
+        the oldest one)."""
+        head = ready[0]
+        key = (head["nmax"], canvas_of(head["side"]))
+        room = min(self.mem_budget - self.mem_in_use, _device_free_bytes(self.device) - self.reserve)
+        batch, est = [], 0
+        for r in ready:
+            if (r["nmax"], canvas_of(r["side"])) != key:
+                continue
+            e = request_bytes(r["side"], r["nmax"], restart=self.restart)
+            if batch and (est + e > room or len(batch) >= self.max_batch):
+                break
+            batch.append(r)
+            est += e
+        return batch, est
+
+    # ---- the loop ------------------------------------------------------------------
     def run(self, requests, keep_solutions=False):
-        """Release each request at its arrival time (seconds after the start), admit
-        by slot and memory, and return per-request records."""
+        """Release each request at its arrival time (seconds after the start), batch and admit
+        by slot and device memory, and return per-request records."""
         t0 = time.perf_counter()
         pending = collections.deque(sorted(requests, key=lambda r: r["arrival"]))
-        ready = collections.deque()
+        ready = []
         records = {}
         running = 0
 
-        def done(slot, req, est, fut):
+        def done(slot, reqs, est, fut):
             nonlocal running
             t = time.perf_counter() - t0
             with self.lock:
-                rec = records[req["rid"]]
-                rec["finish"] = t
                 try:
-                    s, E, info, rc = fut.result()
-                    rec.update(E=E, iterations=info.iterations, refinements=info.refinements,
-                               residual=max(info.rel_residual[:1]), rc=rc)
-                    if keep_solutions:
-                        rec["s"] = s
-                except Exception as e:  # recorded, not raised: one failed job does not stop the loop
-                    rec["error"] = repr(e)
+                    res, rc, ctx_mem = fut.result()
+                    # each context is read only by its own slot's thread (contexts are not
+                    # thread-safe): the slot reports its scratch with the batch's results
+                    self.slot_mem[slot] = ctx_mem
+                    self.ctx_mem_high = max(self.ctx_mem_high, sum(self.slot_mem))
+                    for req, (s, E, info) in zip(reqs, res):
+                        rec = records[req["rid"]]
+                        rec.update(finish=t, E=E, iterations=info.iterations, refinements=info.refinements,
+                                   residual=info.rel_residual[0], rc=0 if info.converged else _lib.ENOCONV)
+                        if keep_solutions:
+                            rec["s"] = s
+                except Exception as e:  # recorded, not raised: one failed batch does not stop the loop
+                    for req in reqs:
+                        records[req["rid"]].update(finish=t, error=repr(e))
                 self.mem_in_use -= est
                 self.free.append(slot)
                 running -= 1
@@ -125,29 +188,30 @@ class Server:
                 while pending and pending[0]["arrival"] <= now:
                     ready.append(pending.popleft())
                 while ready and self.free:
-                    req = ready[0]
-                    est = request_bytes(req["side"], req["nmax"], restart=self.restart)
-                    if self.mem_in_use + est > self.mem_budget and running > 0:
+                    batch, est = self._take_batch(ready)
+                    fits = (self.mem_in_use + est <= self.mem_budget and
+                            est + self.reserve <= _device_free_bytes(self.device))
+                    if not fits and running > 0:
                         break  # wait for memory to free up
-                    ready.popleft()
+                    for r in batch:
+                        ready.remove(r)
                     slot = self.free.popleft()
                     self.mem_in_use += est
                     self.mem_high = max(self.mem_high, self.mem_in_use)
+                    self.batches.append(len(batch))
                     running += 1
-                    records[req["rid"]] = dict(rid=req["rid"], arrival=req["arrival"], admit=now, slot=slot,
-                                               side=req["side"], nmax=req["nmax"], wavelength=req["wavelength"])
-                    fut = self.pool[slot].submit(self._solve, slot, req)
-                    fut.add_done_callback(lambda f, s=slot, r=req, e=est: done(s, r, e, f))
-                wait = 0.05
+                    for r in batch:
+                        records[r["rid"]] = dict(rid=r["rid"], arrival=r["arrival"], admit=now, slot=slot,
+                                                 side=r["side"], nmax=r["nmax"], wavelength=r["wavelength"],
+                                                 batch=len(batch))
+                    fut = self.pool[slot].submit(self._solve_batch, slot, batch)
+                    fut.add_done_callback(lambda f, s=slot, b=batch, e=est: done(s, b, e, f))
+                wait = 0.02
                 if pending:
                     wait = max(0.0, min(wait, pending[0]["arrival"] - (time.perf_counter() - t0)))
                 if pending or ready or running:
                     self.lock.wait(timeout=wait)
         return [records[k] for k in sorted(records)]
-
-
-def ct_stream(torch_stream):
-    return torch_stream.cuda_stream
 
 
 def summarize(records, wall_s):
@@ -156,4 +220,5 @@ def summarize(records, wall_s):
     return {"requests": len(records), "completed": sum(1 for r in records if "E" in r),
             "errors": sum(1 for r in records if "error" in r),
             "solves_per_s": len(lat) / wall_s if wall_s > 0 else None,
-            "p50_latency_s": q(0.50), "p99_latency_s": q(0.99), "wall_s": wall_s}
+            "p50_latency_s": q(0.50), "p99_latency_s": q(0.99), "wall_s": wall_s,
+            "mean_batch": (sum(r.get("batch", 1) for r in records) / len(records)) if records else None}
