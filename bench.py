@@ -450,13 +450,11 @@ def bench_served(args, torch):
 
 def bench_sweep(ctx, torch, inner_tol=0.1):
     """1200 x 1200 spheres (smooth radius map), nmax 3, cutoff 6, 60 x 60 cores + 8-pitch rings,
-    4 incidences as RHS, mixed: four sampled sub-regions (corner, edge, two interior),
-    extrapolated to the 400-sub-region sweep."""
-    from paper_2107_09879_b300 import _lib
+    4 incidences, mixed: all 400 sub-regions served through the request loop (continuous
+    batching, 4 slots), fields added in sub-region order."""
+    from paper_2107_09879_b300 import serve
     n = 1200
     r = W.smooth_radius_map(n, n, W.BASE_SEED + 5)
-    atoms = np.zeros((n * n, 3))
-    atoms[:, 0], atoms[:, 1] = r, 2.0
     pos = W.lattice_positions(n, n)
     z0 = -1.0
     src = np.zeros((4, n * n, 2), complex)
@@ -464,30 +462,25 @@ def bench_sweep(ctx, torch, inner_tol=0.1):
         th = math.radians(deg)
         src[q, :, 0] = math.cos(th) * np.exp(1j * 2 * math.pi * (math.sin(th) * pos[:, 0] + math.cos(th) * z0))
     pts = np.array([[x, 300.0, 20.0] for x in np.linspace(0.0, 600.0, 64)])
-    opts = _lib.make_opts(tol=1e-7, restart=300, max_iter=4000, cutoff=6.0, taper=6.0, precision=_lib.PREC_MIXED,
-                          inner_tol=inner_tol)
-    d_atoms = torch.from_numpy(atoms).cuda()
-    d_src = torch.from_numpy(src).cuda()
-    d_pts = torch.from_numpy(pts).cuda()
-    E = torch.zeros((4, 64, 3), dtype=torch.complex128, device="cuda")
-    samples = {"corner": 0, "edge": 10, "interior_a": 210, "interior_b": 114}
-    kw = dict(nx=n, ny=n, pitch=PITCH, core_x=60, core_y=60, buffer=8, z0=z0)
-    # warm-up on the corner job
-    ctx.tmat_sweep(_lib.make_sweep(first=0, count=1, **kw), d_atoms, 1.0, 1.0, 3, d_src, opts, d_pts, E=E)
-    per = {}
-    infos = {}
-    for name, first in samples.items():
-        dt, res = _wall(lambda: ctx.tmat_sweep(_lib.make_sweep(first=first, count=1, **kw), d_atoms, 1.0, 1.0, 3,
-                                               d_src, opts, d_pts, E=E), torch.cuda.synchronize)
-        per[name] = dt
-        infos[name] = res[1]
-    mean = statistics.mean(per.values())
-    return {"workload": "sweep_1200x1200_nmax3_cutoff6_core60_ring8_4rhs_mixed",
-            "seconds_per_subregion": per, "subregions_per_s": 1.0 / mean,
-            "extrapolated_sweep_s": 400 * mean,
-            "iterations": {k: v.iterations for k, v in infos.items()},
-            "worst_rel_residual": max(v.worst_rel_residual for v in infos.values()),
-            "note": "sampled sub-regions (corner, edge, 2 interior) timed; full sweep extrapolated x400 from their mean"}
+    reqs = serve.sweep_requests(n, n, 60, 8, PITCH, r, 2.0, src, z0, pts, 3)
+    srv = serve.Server(slots=4, mem_budget=96 << 30, max_batch=4, cutoff=6.0, tol=1e-7, restart=300,
+                       inner_tol=inner_tol)
+    srv.run(reqs[:4])  # warm-up (contexts, tables)
+    t0 = time.perf_counter()
+    recs = srv.run(reqs)
+    wall = time.perf_counter() - t0
+    srv.close()
+    E = serve.sweep_field(recs, 4, len(pts))
+    its = sorted(x["iterations"] for x in recs if "iterations" in x)
+    q = lambda f: its[min(len(its) - 1, int(f * len(its)))]
+    return {"workload": "sweep_1200x1200_nmax3_cutoff6_core60_ring8_4rhs_mixed", "subregions": len(recs),
+            "completed": sum(1 for x in recs if "E" in x), "unconverged": sum(1 for x in recs if x.get("rc")),
+            "wall_s": wall, "subregions_per_s": len(recs) / wall,
+            "iterations_per_subregion": {"min": its[0], "median": q(0.5), "max": its[-1]} if its else None,
+            "worst_rel_residual": max((x.get("residual", 0.0) for x in recs), default=None),
+            "mean_batch": statistics.mean(srv.batches), "field_norm": float(np.linalg.norm(E)),
+            "note": "every sub-region solved (4 incidences each as RHS), through the request loop; a "
+                    "sub-region's iteration count is that of its batch"}
 
 
 def bench_padding(ctx, torch):
@@ -967,6 +960,7 @@ def main():
                     help="tensor-core lattice kernel: 1 window view (default), 2 gather")
     ap.add_argument("--launch-summary", metavar="CSV", help="summarise an ncu launch list by kernel and exit")
     ap.add_argument("--served-only", action="store_true", help="run only the served-stream workload")
+    ap.add_argument("--sweep-only", action="store_true", help="run only the 1200 x 1200 sweep")
     ap.add_argument("--window-study", action="store_true",
                     help="coupling-window study: every pair vs hard cutoff vs raised-cosine windows")
     ap.add_argument("--study-size", type=int, default=60)
@@ -996,6 +990,10 @@ def main():
     if args.served_only:
         import torch
         print(json.dumps(bench_served(args, torch)))
+        return
+    if args.sweep_only:
+        import torch
+        print(json.dumps(bench_sweep(None, torch)))
         return
     if args.impl == "reference":
         if world > 1 and rank != 0:

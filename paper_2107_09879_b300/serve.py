@@ -62,6 +62,42 @@ def request_bytes(side, nmax, R=1, restart=60, cutoff_sites=16):
     return krylov + vectors + blocks + spectra + work + jinc + (8 << 20)
 
 
+def _canvas(req):
+    """Canvas side of a request: its size class (sub-region sweeps: their own side)."""
+    if "sweep" in req:
+        return max(req["w"], req["h"])
+    return canvas_of(req["side"])
+
+
+def sweep_requests(nx, ny, core, buf, pitch, radius, n_sphere, src_A, z0, pts, nmax):
+    """One request per sub-region of an nx x ny sweep (cores of core x core sites, rings of buf
+    sites, clipped at the edge): src_A (R, nx * ny, 2) transverse amplitudes of the jinc source
+    at every site, detectors pts (M, 3) in the sweep's coordinates. All arrive at t = 0."""
+    g = dict(nx=nx, ny=ny, pitch=pitch, radius=np.asarray(radius), n_sphere=n_sphere, src_A=np.asarray(src_A),
+             z0=z0, pts=np.asarray(pts, dtype=np.float64))
+    out = []
+    nax, nay = -(-nx // core), -(-ny // core)
+    for a in range(nax * nay):
+        ax, ay = a % nax, a // nax
+        cx0, cy0 = ax * core, ay * core
+        cx1, cy1 = min(nx, cx0 + core), min(ny, cy0 + core)
+        px0, py0 = max(0, cx0 - buf), max(0, cy0 - buf)
+        px1, py1 = min(nx, cx1 + buf), min(ny, cy1 + buf)
+        out.append(dict(rid=a, arrival=0.0, nmax=nmax, sweep=g, cx0=cx0, cy0=cy0, cw=cx1 - cx0, ch=cy1 - cy0,
+                        px0=px0, py0=py0, w=px1 - px0, h=py1 - py0, side=max(px1 - px0, py1 - py0),
+                        wavelength=1.0))
+    return out
+
+
+def sweep_field(records, R, M):
+    """The decomposed field of the whole array: the sub-regions' fields added in sub-region
+    order (deterministic), fp64 on the host."""
+    E = np.zeros((R, M, 3), dtype=np.complex128)
+    for rec in sorted(records, key=lambda r: r["rid"]):
+        E += rec["E"]
+    return E
+
+
 def ct_stream(torch_stream):
     return torch_stream.cuda_stream
 
@@ -114,38 +150,75 @@ class Server:
         a0 = ctx.tmat_incident_jinc(pos, w, 1.0, nmax, src, A, self.z0, precision=_lib.PREC_MIXED, src_pitch=pitch)
         return dict(nx=side, ny=side, wavelength=w, T=T, a0=np.ascontiguousarray(a0[0]), pos=pos)
 
+    def _sweep_problems(self, ctx, req):
+        """A sub-region of a large-area sweep (main text, Fig. 3): its spheres (core + ring) on
+        a lattice at the origin, the jinc sources of its core shifted by the same offset (the
+        problem is translation invariant), one problem per incidence."""
+        g = req["sweep"]
+        pitch, nx = g["pitch"], g["nx"]
+        px0, py0, w, h = req["px0"], req["py0"], req["w"], req["h"]
+        iy, ix = np.divmod(np.arange(w * h), w)
+        pos = np.zeros((w * h, 3))
+        pos[:, 0], pos[:, 1] = ix * pitch, iy * pitch
+        sites = (py0 + iy) * nx + px0 + ix
+        atoms = np.stack([g["radius"][sites], np.full(w * h, g["n_sphere"]), np.zeros(w * h)], axis=1)
+        cy, cx = np.divmod(np.arange(req["cw"] * req["ch"]), req["cw"])
+        csites = (req["cy0"] + cy) * nx + req["cx0"] + cx
+        src = np.stack([(req["cx0"] - px0 + cx) * pitch, (req["cy0"] - py0 + cy) * pitch], axis=1)
+        A = np.ascontiguousarray(g["src_A"][:, csites, :])
+        T = ctx.tmat_build(atoms, 1.0, 1.0, req["nmax"])
+        a0 = ctx.tmat_incident_jinc(pos, 1.0, 1.0, req["nmax"], src, A, g["z0"], precision=_lib.PREC_MIXED,
+                                    src_pitch=pitch)
+        return [dict(nx=w, ny=h, wavelength=1.0, T=T, a0=np.ascontiguousarray(a0[r]), pos=pos)
+                for r in range(A.shape[0])]
+
     def _solve_batch(self, slot, reqs):
         ctx = self.ctxs[slot]
         nmax = reqs[0]["nmax"]
-        canvas = canvas_of(max(r["side"] for r in reqs))
-        probs = [self._problem(ctx, r) for r in reqs]
+        canvas = max(_canvas(r) for r in reqs)
+        per_req = [self._sweep_problems(ctx, r) if "sweep" in r else [self._problem(ctx, r)] for r in reqs]
+        probs = [p for pr in per_req for p in pr]
         opts = _lib.make_opts(tol=self.tol, restart=self.restart, max_iter=3000, cutoff=self.cutoff,
                               taper=self.cutoff, precision=_lib.PREC_MIXED, inner_tol=self.inner_tol)
         outs, infos, rc = ctx.tmat_solve_batch(probs, 1.0, nmax, 0.5, opts, canvas=(canvas, canvas))
-        res = []
-        for p, s, info in zip(probs, outs, infos):
-            c = (p["nx"] - 1) * 0.5 / 2
-            E = ctx.tmat_field(p["pos"], p["wavelength"], 1.0, nmax, s, np.array([[c, c, self.det_h]]))
-            res.append((s, E, info))
+        res, q = [], 0
+        for req, pr in zip(reqs, per_req):
+            if "sweep" in req:  # field of every incidence at the sweep's detectors (shifted)
+                shift = np.array([req["px0"] * req["sweep"]["pitch"], req["py0"] * req["sweep"]["pitch"], 0.0])
+                pts = np.ascontiguousarray(req["sweep"]["pts"] - shift)
+                E = np.stack([ctx.tmat_field(p["pos"], 1.0, 1.0, nmax, outs[q + i], pts) for i, p in enumerate(pr)])
+                s = None
+            else:
+                p = pr[0]
+                c = (p["nx"] - 1) * 0.5 / 2
+                s = outs[q]
+                E = ctx.tmat_field(p["pos"], p["wavelength"], 1.0, nmax, s, np.array([[c, c, self.det_h]]))
+            res.append((s, E, infos[q]))
+            q += len(pr)
         return res, rc, ctx.memory()
 
     # ---- batch formation -----------------------------------------------------------
+    def _problems_of(self, r):
+        return r["sweep"]["src_A"].shape[0] if "sweep" in r else 1
+
     def _take_batch(self, ready):
         """The oldest ready request and up to max_batch - 1 more of the same nmax and canvas
         class, as many as the memory budget left over by the running batches allows (at least
         the oldest one)."""
         head = ready[0]
-        key = (head["nmax"], canvas_of(head["side"]))
+        key = (head["nmax"], _canvas(head))
         room = min(self.mem_budget - self.mem_in_use, _device_free_bytes(self.device) - self.reserve)
-        batch, est = [], 0
+        batch, est, nprob = [], 0, 0
         for r in ready:
-            if (r["nmax"], canvas_of(r["side"])) != key:
+            if (r["nmax"], _canvas(r)) != key:
                 continue
-            e = request_bytes(r["side"], r["nmax"], restart=self.restart)
-            if batch and (est + e > room or len(batch) >= self.max_batch):
+            e = request_bytes(_canvas(r), r["nmax"], R=self._problems_of(r), restart=self.restart)
+            k = self._problems_of(r)
+            if batch and (est + e > room or len(batch) >= self.max_batch or nprob + k > _lib.MAX_RHS):
                 break
             batch.append(r)
             est += e
+            nprob += k
         return batch, est
 
     # ---- the loop ------------------------------------------------------------------

@@ -83,3 +83,35 @@ def test_served_results_match_the_oracle():
         Eo = field.scattered_field(2, kk, pos, so, np.array([[c, c, srv.det_h]]))
         assert _rel(rec["s"], so) <= 1e-6
         assert _rel(rec["E"], Eo) <= 1e-6
+
+
+def test_sweep_through_the_request_loop_matches_tmat_sweep_and_oracle():
+    """A small large-area sweep served as sub-region requests (batched, shifted to the origin)
+    against tmat_sweep (absolute coordinates) and the oracle's sweep definition."""
+    from oracle import incident, sweep
+    from paper_2107_09879_b300 import _lib, serve
+    from gpu_common import K0, atoms, ctx
+    nx, ny, core, buf, nmax, cut, z0 = 14, 11, 5, 2, 2, 1.2, -1.0
+    r = W.smooth_radius_map(nx, ny, W.BASE_SEED + 9)
+    pos = W.lattice_positions(nx, ny)
+    src = np.zeros((2, nx * ny, 2), complex)
+    for q, deg in enumerate((0.0, 8.0)):
+        th = math.radians(deg)
+        src[q, :, 0] = math.cos(th) * np.exp(1j * K0 * (math.sin(th) * pos[:, 0] + math.cos(th) * z0))
+    pts = np.array([[1.0, 2.0, 3.0], [4.5, 2.5, 2.0], [6.0, 4.0, 5.0]])
+    reqs = serve.sweep_requests(nx, ny, core, buf, 0.5, r, 2.0, src, z0, pts, nmax)
+    srv = serve.Server(slots=2, mem_budget=16 << 30, max_batch=4, cutoff=cut, tol=1e-9, restart=100)
+    recs = srv.run(reqs)
+    srv.close()
+    assert all("E" in x and x["rc"] == 0 for x in recs)
+    E = serve.sweep_field(recs, 2, len(pts))
+    opts = _lib.make_opts(tol=1e-9, restart=100, max_iter=3000, cutoff=cut, taper=cut, precision=_lib.PREC_MIXED)
+    sw = _lib.make_sweep(nx=nx, ny=ny, pitch=0.5, core_x=core, core_y=core, buffer=buf, z0=z0)
+    Ed, info, rc = ctx().tmat_sweep(sw, atoms(r), 1.0, 1.0, nmax, src, opts, pts)
+    assert rc == 0 and _rel(E, Ed) <= 1e-6
+    xy = pos[:, :2]
+    rule_for = lambda p, s: incident.jinc_rule(*incident.jinc_rule_size(
+        K0, max(np.hypot(*(a[:2] - b)) for a in p for b in s) + abs(z0)))
+    Eo = sweep.sweep_fields(nmax, K0, nx, ny, 0.5, 0.0, r, 2.0, src[0], z0, (core, core), buf, pts, rule_for,
+                            cutoff=cut, taper=cut)
+    assert _rel(E[0], Eo) <= 1e-6
