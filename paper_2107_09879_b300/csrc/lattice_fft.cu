@@ -501,10 +501,14 @@ __device__ __forceinline__ bool fft4_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
-// per column k (frequency f1..f4) and direction D (0 forward / coupling, 1 transposed):
-// input permutation and sign, output permutation and sign (see the block comment above)
-__device__ __constant__ int c_fft4_in_j[2][4] = {{1, 0, 0, 1}, {0, 1, 1, 0}};
-__device__ __constant__ int c_fft4_in_s[2][4] = {{3, 1, 2, 0}, {3, 1, 2, 0}};
+// per column k (frequency f1..f4) and direction D (0 forward / coupling, 1 transposed), see
+// the block comment above: the input is permuted by J for k in {0, 3} (forward) or {1, 2}
+// (transposed) and the output for the other two; the input sign is (Dm, Dx, Dy, 1) and the
+// output sign (1, Dy, Dx, Dm) over k = 0..3 (selectors of fft4_neg)
+__device__ __forceinline__ bool fft4_in_j(int D, int k) { return ((k == 0 || k == 3) ? 0 : 1) == D; }
+__device__ __forceinline__ bool fft4_out_j(int D, int k) { return !fft4_in_j(D, k); }
+__device__ __forceinline__ int fft4_in_s(int k) { return k == 0 ? 3 : (k == 1 ? 1 : (k == 2 ? 2 : 0)); }
+__device__ __forceinline__ int fft4_out_s(int k) { return k == 0 ? 0 : (k == 1 ? 2 : (k == 2 ? 1 : 3)); }
 
 // cstride: complex values between the spectra of consecutive RHS (0: one operator for all
 // RHS; otherwise RC = 1 and every RHS pass stages its own C)
@@ -515,8 +519,6 @@ fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, fl
   using Cfg = Fft4Cfg<L, RC_>;
   constexpr int NI = Cfg::NI, RC = Cfg::RC, NCOL = Cfg::NCOL, P = 2 * L, SC = Cfg::SC, SW = Cfg::SW,
                 NT = Cfg::THREADS;
-  constexpr int OUT_J[2][4] = {{0, 1, 1, 0}, {1, 0, 0, 1}};
-  constexpr int OUT_S[2][4] = {{0, 2, 1, 3}, {0, 2, 1, 3}};
   constexpr int D = MODE == 1 ? 1 : 0;
   extern __shared__ __align__(128) unsigned char fsm4[];
   float2* Cs = reinterpret_cast<float2*>(fsm4);                  // [NI][2][SC]
@@ -572,10 +574,10 @@ fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, fl
       float2 w = make_float2(0.f, 0.f);
       if (ok) {
         const int sv = sym[cc * L + v];
-        const int comp = c_fft4_in_j[D][k] ? (sv & 0xffff) : v;
+        const int comp = fft4_in_j(D, k) ? (sv & 0xffff) : v;
         const int64_t f = (int64_t)((k & 2) ? kxm : kx) * My + ((k & 1) ? kym : ky);
         w = Xh[((int64_t)(r0 + q) * P + cc * L + comp) * F + f];
-        if (fft4_neg(c_fft4_in_s[D][k], (sv >> 16) & 1, (sv >> 17) & 1)) w = make_float2(-w.x, -w.y);
+        if (fft4_neg(fft4_in_s(k), (sv >> 16) & 1, (sv >> 17) & 1)) w = make_float2(-w.x, -w.y);
       }
       wv[j] = w;
     }
@@ -598,9 +600,7 @@ fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, fl
   for (;;) {
     int kx, ky0, ni;
     tile_of(tile, kx, ky0, ni);
-    const int ky = ky0 + it, kxm = (Mx - kx) % Mx, kym = (My - ky) % My;
-    const bool dy = kym != ky, dx = kxm != kx;
-    const unsigned vmask = it < ni ? (1u | (dy ? 2u : 0u) | (dx ? 4u : 0u) | (dx && dy ? 8u : 0u)) : 0u;
+    const int kxm = (Mx - kx) % Mx;
     for (int r0 = 0; r0 < R_; r0 += RC) {
       int bad = 0;
       const uint32_t wphase = phase;
@@ -632,6 +632,20 @@ fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, fl
         }
       }
       __syncthreads();  // every read of Cs and Ws of this stage is done
+      // this thread's outputs, with their output signs, into the staging area (Ws); the
+      // stores below take them item-fastest, so the NI items of a tile fill whole sectors
+      {
+        float2* zrow = Ws + (it * 2 + c) * SW + u * NCOL;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int q = 0; q < RC; ++q) {
+            float2 z = acc[k * RC + q];
+            if (fft4_neg(fft4_out_s(k), mpar, pp)) z = make_float2(-z.x, -z.y);
+            zrow[k * RC + q] = z;
+          }
+      }
+      __syncthreads();
       // next stage: its C copy (new tile) and its input loads go out before this stage's
       // outputs are written
       const bool more_rhs = r0 + RC < R_;
@@ -642,16 +656,20 @@ fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, fl
         load_w(ntile, more_rhs ? r0 + RC : 0);
       }
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int q = 0; q < RC; ++q)
-          if (((vmask >> k) & 1u) && r0 + q < R_) {
-            const int comp = OUT_J[D][k] ? Ju : u;
-            float2 z = acc[k * RC + q];
-            if (fft4_neg(OUT_S[D][k], mpar, pp)) z = make_float2(-z.x, -z.y);
-            const int64_t f = (int64_t)((k & 2) ? kxm : kx) * My + ((k & 1) ? kym : ky);
-            Yh[((int64_t)(r0 + q) * P + c * L + comp) * F + f] = z;
-          }
+      for (int j = 0; j < NCOL; ++j) {
+        const int e = t + j * NT;
+        const int item = e % NI, rest = e / NI;
+        const int col = rest % NCOL, row = rest / NCOL;
+        const int cc = row / L, v = row % L, k = col / RC, q = col % RC;
+        const int iky = ky0 + item, ikym = (My - iky) % My;
+        const bool ok = item < ni && r0 + q < R_ && ((k & 1) == 0 || ikym != iky) && ((k & 2) == 0 || kxm != kx);
+        if (ok) {
+          const int comp = fft4_out_j(D, k) ? (sym[cc * L + v] & 0xffff) : v;
+          const int64_t f = (int64_t)((k & 2) ? kxm : kx) * My + ((k & 1) ? ikym : iky);
+          Yh[((int64_t)(r0 + q) * P + cc * L + comp) * F + f] = Ws[(item * 2 + cc) * SW + v * NCOL + col];
+        }
+      }
+      __syncthreads();  // the staged outputs are read
       if (have_next) store_w();
     }
     tile += gridDim.x;
