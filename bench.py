@@ -483,6 +483,46 @@ def bench_sweep(ctx, torch, inner_tol=0.1):
                     "sub-region's iteration count is that of its batch"}
 
 
+def bench_cylinders(ctx, torch, steps=3):
+    """A metalens-like array of silicon-like cylinders (the paper's meta-atoms, App. I-B):
+    200 x 200 upright cylinders on the 0.5-wavelength lattice, 8 radii from 0.08 to 0.15
+    (height 0.3, index 3.5; every enclosing sphere inside its cell), nmax 4, cutoff 8 with the
+    raised-cosine window, normal x-polarised incidence, mixed: null-field T-blocks built on
+    the GPU, then the solve with full T-blocks (types) through the FFT lattice operator."""
+    from paper_2107_09879_b300 import _lib
+    n, nmax = 200, 4
+    kinds = np.linspace(0.08, 0.15, 8)
+    cyl = np.ascontiguousarray(np.array([[a, 0.3, 3.5, 0.0] for a in kinds]))
+    g = W.SplitMix64(W.BASE_SEED + 11)
+    types = np.array([min(7, int(8 * g.uniform())) for _ in range(n * n)], dtype=np.int32)
+    pos = torch.from_numpy(W.lattice_positions(n, n)).cuda()
+    d_types = torch.from_numpy(types).cuda()
+    d_cyl = torch.from_numpy(cyl).cuda()
+    dirs = torch.zeros((1, 2), dtype=torch.float64, device="cuda")
+    pol = torch.tensor([[1.0, 0.0, 0.0]], dtype=torch.complex128, device="cuda")
+    radii = torch.from_numpy(np.sqrt(kinds[types] ** 2 + 0.15 ** 2)).cuda()
+    opts = _lib.make_opts(tol=TOL, restart=300, max_iter=4000, cutoff=8.0, taper=8.0, precision=_lib.PREC_MIXED,
+                          inner_tol=0.2, path=_lib.PATH_LATTICE, lattice_nx=n, lattice_ny=n, lattice_pitch=PITCH,
+                          enclosing_radii=radii)
+    rec = []
+
+    def one():
+        Tb = ctx.tmat_build_cylinder(d_cyl, 1.0, 1.0, nmax, n_quad=48)
+        a0 = ctx.tmat_incident_planewave(pos, 1.0, 1.0, nmax, dirs, pol)
+        s, info, _, rc = ctx.tmat_solve_tblocks(pos, 1.0, 1.0, nmax, Tb, a0, opts, types=d_types)
+        rec.append(info)
+        return rc
+    one()
+    times = [_wall(one, torch.cuda.synchronize)[0] for _ in range(steps)]
+    tb_t = _wall(lambda: ctx.tmat_build_cylinder(d_cyl, 1.0, 1.0, nmax, n_quad=48), torch.cuda.synchronize)[0]
+    info = rec[-1]
+    return {"workload": "cylinders_200x200_8types_nmax4_cutoff8_mixed", "solves_per_s": 1.0 / statistics.mean(times),
+            "seconds_per_solve": statistics.mean(times), "iterations": info.iterations,
+            "refinements": info.refinements, "converged": bool(info.converged),
+            "rel_residual": info.rel_residual[0], "tblock_build_ms": tb_t * 1e3,
+            "note": "one solve = null-field T-blocks of the 8 cylinder types + incident + overlap check + solve"}
+
+
 def bench_padding(ctx, torch):
     """Padding (buffer-ring) convergence of the sub-region decomposition, the synthetic
     analog of the paper's padding study: an 80 x 80 array (nmax 3, smooth radius map, cutoff 6
@@ -498,14 +538,43 @@ def bench_padding(ctx, torch):
     pos = W.lattice_positions(n, n)
     src = np.zeros((1, n * n, 2), complex)
     src[0, :, 0] = np.exp(1j * 2 * math.pi * z0)
-    pts = np.array([[x, 19.75, 10.0] for x in np.linspace(5.0, 35.0, 32)])
+    line = np.array([[x, 19.75, 10.0] for x in np.linspace(5.0, 35.0, 32)])
+    # focal-plane grid for the efficiency (1/4-wavelength spacing over 16 x 16 wavelengths)
+    gx = np.linspace(11.75, 27.75, 65)
+    plane = np.array([[x, y, 10.0] for y in gx for x in gx])
+    pts = np.ascontiguousarray(np.vstack([line, plane]))
     opts = _lib.make_opts(tol=1e-11, restart=200, max_iter=4000, cutoff=cut, taper=cut, precision=_lib.PREC_FP64,
                           path=_lib.PATH_LATTICE, lattice_nx=n, lattice_ny=n, lattice_pitch=PITCH)
+    k = 2 * math.pi
+    aperture = (n * PITCH) ** 2
+
+    def efficiency(Esca):
+        """Power inside a circle of diameter 3 x FWHM around the brightest point of the plane,
+        over the incident power on the array's aperture (main text, lens efficiency): total field
+        = the scattered field + the unit x-polarised plane wave the sources sample."""
+        Et = Esca[len(line):].copy()
+        Et[:, 0] += np.exp(1j * k * 10.0)
+        I = np.sum(np.abs(Et) ** 2, axis=1).reshape(len(gx), len(gx))
+        iy, ix = np.unravel_index(int(np.argmax(I)), I.shape)
+        row = I[iy]
+        half = row[ix] / 2
+        lo, hi = ix, ix
+        while lo > 0 and row[lo] > half:
+            lo -= 1
+        while hi < len(gx) - 1 and row[hi] > half:
+            hi += 1
+        fwhm = max(gx[hi] - gx[lo], gx[1] - gx[0])
+        X, Y = np.meshgrid(gx, gx)
+        inside = (X - gx[ix]) ** 2 + (Y - gx[iy]) ** 2 <= (1.5 * fwhm) ** 2
+        dA = (gx[1] - gx[0]) ** 2
+        return float(np.sum(I[inside]) * dA / aperture), float(fwhm)
     T = ctx.tmat_build(at, 1.0, 1.0, nmax)
     a0 = ctx.tmat_incident_jinc(pos, 1.0, 1.0, nmax, np.ascontiguousarray(pos[:, :2]), src, z0, precision=0,
                                 src_pitch=PITCH)
     s, info, _, rc = ctx.tmat_solve(pos, 1.0, 1.0, nmax, T, a0, opts)
-    full = ctx.tmat_field(pos, 1.0, 1.0, nmax, s[0], pts)
+    fullp = ctx.tmat_field(pos, 1.0, 1.0, nmax, s[0], pts)
+    eff_full, fwhm_full = efficiency(fullp)
+    full = fullp[:len(line)]
     I_full = np.sum(np.abs(full) ** 2, axis=1)
     peak = int(np.argmax(I_full))
     sopts = _lib.make_opts(tol=1e-11, restart=200, max_iter=4000, cutoff=cut, taper=cut, precision=_lib.PREC_FP64)
@@ -515,16 +584,19 @@ def bench_padding(ctx, torch):
         t0 = time.perf_counter()
         E, sinfo, src_rc = ctx.tmat_sweep(sw, at, 1.0, 1.0, nmax, src, sopts, pts)
         dt = time.perf_counter() - t0
-        E = E[0]
+        eff, _ = efficiency(E[0])
+        E = E[0][:len(line)]
         I = np.sum(np.abs(E) ** 2, axis=1)
         rows.append({"buffer_pitches": buf, "buffer_wavelengths": buf * PITCH,
                      "rel_field_error": float(np.linalg.norm(E - full) / np.linalg.norm(full)),
                      "peak_intensity_rel_error": float(abs(I[peak] - I_full[peak]) / I_full[peak]),
-                     "seconds": dt})
+                     "efficiency": eff, "efficiency_abs_error": abs(eff - eff_full), "seconds": dt})
     return {"workload": "padding_80x80_nmax3_cutoff6_core20_fp64", "whole_array_iterations": info.iterations,
-            "rows": rows,
-            "note": "16 sub-regions of 20 x 20; field on 32 detector points at height 10; the whole-array "
-                    "solve (lattice path, fp64) is the reference"}
+            "whole_array_efficiency": eff_full, "whole_array_fwhm": fwhm_full, "rows": rows,
+            "note": "16 sub-regions of 20 x 20; field on 32 detector points at height 10 and on a 65 x 65 "
+                    "focal-plane grid (efficiency: power within 3 x FWHM of the brightest point over the "
+                    "incident power on the aperture); the whole-array solve (lattice path, fp64) is the "
+                    "reference"}
 
 
 def study_inputs(n, torch):
@@ -652,6 +724,7 @@ def run_ours(args, rank, world):
     ctx = _lib.Context(dev, None)
     ctx.set_tensor_cores(0 if args.cuda_cores else args.tc_variant)
     ctx.set_lattice_fft(0 if args.direct else args.fft_mode)
+    ctx.set_field_precision(_lib.PREC_MIXED)  # the field of a mixed solve: fp32 waves, fp64 phases
     FMA_PEAKS["fp32_tflops"] = _lib.tmat_measure_fma_peak(dev, _lib.PREC_MIXED)
     FMA_PEAKS["fp64_tflops"] = _lib.tmat_measure_fma_peak(dev, _lib.PREC_FP64)
     wl = workload(args.size)
@@ -764,7 +837,7 @@ def run_ours(args, rank, world):
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64 apply / f64 refinement", "data": "synthetic",
         "config": {"workload": f"lattice_{wl['nx']}x{wl['ny']}_nmax4_cutoff8_2rhs_mixed", "spheres": N, "nmax": nmax, "P": P,
-                   "rhs": R, "cutoff_wavelengths": cutoff, "coupling_window": "raised cosine over [0, cutoff] (taper = cutoff)", "tol": TOL, "restart": 300, "path": "lattice (block per offset)",
+                   "rhs": R, "cutoff_wavelengths": cutoff, "coupling_window": "raised cosine over [0, cutoff] (taper = cutoff)", "field": "mixed (fp32 waves, fp64 phases)", "tol": TOL, "restart": 300, "path": "lattice (block per offset)",
                    "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) before every step"},
         "p50_ms": per_step[len(per_step) // 2], "p99_ms": per_step[min(len(per_step) - 1, int(0.99 * len(per_step)))],
         "gmres_iterations_per_solve": statistics.mean(it), "refinements_per_solve": statistics.mean(ref),
@@ -802,6 +875,7 @@ def run_ours(args, rank, world):
         out["adjoint_50x50"] = bench_adjoint(ctx, torch)
         out["served"] = bench_served(args, torch)
         out["sweep_1200x1200"] = bench_sweep(ctx, torch)
+        out["cylinders_200x200"] = bench_cylinders(ctx, torch)
         try:
             out["padding_study"] = bench_padding(ctx, torch)
         except Exception as exc:  # a study, not the headline: report it rather than lose the line

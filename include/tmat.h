@@ -156,6 +156,14 @@ int tmat_ctx_set_timing(tmat_ctx* ctx, int enable);
  * "lattice_fft_mul32", "lattice_fft_mul64" (the per-frequency block products). */
 int tmat_ctx_set_lattice_fft(tmat_ctx* ctx, int enable);
 
+/* Precision of near-field evaluations (tmat_field, tmat_point_fom, tmat_sweep's fields):
+ * TMAT_PREC_FP64 (default) or TMAT_PREC_MIXED, where the distance, k|d| and its reduction
+ * modulo 2 pi stay fp64 and the rest of each wave (sin/cos of the reduced phase, Hankel and
+ * Legendre recurrences, products with complex64 copies of the coefficients) is fp32, summed in
+ * fp64 across scatterers: relative error ~1e-7, for results of a mixed solve (1e-6 target).
+ * Far-field amplitudes stay fp64. Timing kinds: "field64", "field32", "farfield". */
+int tmat_ctx_set_field_precision(tmat_ctx* ctx, int precision);
+
 /* Complex64 lattice applies run on the tcgen05 tensor cores (3xTF32, nmax <= 4)
  * unless disabled here (enable = 0: the CUDA-core fp32 kernel runs, and the mixed
  * refinement residual uses the fp64 CUDA-core kernel). enable = 1

@@ -233,3 +233,11 @@ extern "C" int tmat_ctx_memory(const tmat_ctx* ctx, int64_t* bytes_out) {
   *bytes_out = b;
   return TMAT_OK;
 }
+
+extern "C" int tmat_ctx_set_field_precision(tmat_ctx* ctx, int precision) {
+  if (!ctx) return TMAT_EINVAL;
+  if (precision != TMAT_PREC_FP64 && precision != TMAT_PREC_MIXED)
+    return set_error(ctx, TMAT_EINVAL, "tmat_ctx_set_field_precision: TMAT_PREC_FP64 or TMAT_PREC_MIXED");
+  ctx->field_mixed = precision == TMAT_PREC_MIXED;
+  return TMAT_OK;
+}

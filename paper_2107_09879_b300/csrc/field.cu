@@ -26,6 +26,11 @@ struct LegConst {
   double a[NM1][NM1], b[NM1][NM1], t[NM1][NM1], base[NM1], sq[NM1], cl[NM1];
 };
 __constant__ LegConst c_leg;
+// the same constants in fp32 (the mixed-precision near field)
+struct LegConstF {
+  float a[NM1][NM1], b[NM1][NM1], t[NM1][NM1], base[NM1], sq[NM1], cl[NM1];
+};
+__constant__ LegConstF c_legf;
 
 // once per device (on `stream`); 0 or a CUDA error code
 static cudaError_t leg_upload(int device, cudaStream_t stream) {
@@ -51,7 +56,19 @@ static cudaError_t leg_upload(int device, cudaStream_t stream) {
       if (l >= 1 && m <= l) h.t[l][m] = std::sqrt((2.0 * l + 1) * ((double)l * l - (double)m * m) / (2.0 * l - 1));
     }
   }
+  LegConstF hf;
+  for (int i = 0; i < NM1; ++i) {
+    hf.base[i] = (float)h.base[i];
+    hf.sq[i] = (float)h.sq[i];
+    hf.cl[i] = (float)h.cl[i];
+    for (int j = 0; j < NM1; ++j) {
+      hf.a[i][j] = (float)h.a[i][j];
+      hf.b[i][j] = (float)h.b[i][j];
+      hf.t[i][j] = (float)h.t[i][j];
+    }
+  }
   cudaError_t e = cudaMemcpyToSymbolAsync(c_leg, &h, sizeof(h), 0, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_legf, &hf, sizeof(hf), 0, cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e == cudaSuccess && device >= 0 && device < 64) done[device] = true;
   return e;
@@ -164,6 +181,144 @@ __device__ __forceinline__ void waves_t(double k, double dx, double dy, double d
     pw *= st;
     em = cmul(em, make_double2(cp, sp));
   }
+}
+
+// Mixed-precision near field: the outgoing waves Phi_f(k d) with the distance, k|d| and its
+// reduction modulo 2 pi in fp64 (so the phase of a wave hundreds of wavelengths away keeps
+// ~1e-7 accuracy), everything else (sin/cos of the reduced phase, the Hankel recurrence, the
+// Legendre recurrences, the vector components) in fp32. Same formulas as waves_t.
+template <int NMAX, typename Fn>
+__device__ __forceinline__ void waves32_near(double k, double dx, double dy, double dz, Fn&& f) {
+  constexpr int L = NMAX * (NMAX + 2);
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  // 1/sqrt(r2): fp32 estimate, one Newton step in fp64 (relative error ~1e-14)
+  double y = (double)rsqrtf((float)r2);
+  y = y * (1.5 - 0.5 * r2 * y * y);
+  const double r = r2 * y;
+  const double kr = k * r;
+  const double twopi = 6.283185307179586476925286766559;
+  const float ang = (float)(kr - twopi * rint(kr * (1.0 / twopi)));
+  const float fy = (float)y;
+  const float fdx = (float)dx, fdy = (float)dy;
+  const float rho = sqrtf(fdx * fdx + fdy * fdy);
+  // sin(theta) from the transverse distance, not sqrt(1 - cos^2) (which loses every digit
+  // in fp32 for points nearly straight above a scatterer)
+  const float ct = (float)dz * fy, st = rho * fy;
+  const float cp = rho > 0.f ? fdx / rho : 1.f, sp = rho > 0.f ? fdy / rho : 0.f;
+  float2 zM[NMAX + 1], zNr[NMAX + 1], zNt[NMAX + 1];
+  {
+    float sn, cs;
+    sincosf(ang, &sn, &cs);
+    const float ix = (float)(1.0 / kr);
+    float2 h[NMAX + 1];
+    h[0] = make_float2(sn * ix, -cs * ix);
+    h[1] = make_float2(-ix * cs + ix * ix * sn, -ix * sn - ix * ix * cs);
+#pragma unroll
+    for (int q = 1; q < NMAX; ++q) {
+      const float fq = (2 * q + 1) * ix;
+      h[q + 1] = make_float2(fq * h[q].x - h[q - 1].x, fq * h[q].y - h[q - 1].y);
+    }
+#pragma unroll
+    for (int l = 1; l <= NMAX; ++l) {
+      const float cl = c_legf.cl[l];
+      zM[l] = cscale(h[l], cl);
+      zNr[l] = cscale(h[l], cl * l * (l + 1.f) * ix);
+      zNt[l] = make_float2(cl * (h[l - 1].x - l * h[l].x * ix), cl * (h[l - 1].y - l * h[l].y * ix));
+    }
+  }
+  const float thv[3] = {ct * cp, ct * sp, -st}, phv[3] = {-sp, cp, 0.f}, rhv[3] = {st * cp, st * sp, ct};
+  float P1[NMAX + 1];
+  {
+    float pp = 0.f, pc = c_legf.base[1] * st;
+    P1[1] = pc;
+#pragma unroll
+    for (int l = 2; l <= NMAX; ++l) {
+      const float pn = c_legf.a[l][1] * (ct * pc - c_legf.b[l][1] * pp);
+      pp = pc;
+      pc = pn;
+      P1[l] = pn;
+    }
+  }
+  float2 em = make_float2(1.f, 0.f);
+  float pw = 1.f, pw1 = 1.f;
+#pragma unroll
+  for (int m = 0; m <= NMAX; ++m) {
+    const float base = c_legf.base[m];
+    float p_prev = 0.f, p_cur = base * pw;
+    float q_prev = 0.f, q_cur = m >= 1 ? base * pw1 : 0.f;
+#pragma unroll
+    for (int l = (m > 1 ? m : 1); l <= NMAX; ++l) {
+      if (l > m) {
+        const float a = c_legf.a[l][m], bb = c_legf.b[l][m];
+        const float pn = a * (ct * p_cur - bb * p_prev), qn = a * (ct * q_cur - bb * q_prev);
+        p_prev = p_cur;
+        p_cur = pn;
+        q_prev = q_cur;
+        q_cur = qn;
+      }
+      const float pb = p_cur;
+      const float ta = m == 0 ? -c_legf.sq[l] * P1[l] : l * ct * q_cur - c_legf.t[l][m] * (l > m ? q_prev : 0.f);
+#pragma unroll
+      for (int sg = 0; sg < (m == 0 ? 1 : 2); ++sg) {
+        const int mm = sg == 0 ? m : -m;
+        const float mpi = mm * q_cur;
+        const float2 e = sg == 0 ? em : cconj(em);
+        const float2 aM = cmul(zM[l], e), aNr = cmul(cscale(zNr[l], pb), e), aNt = cmul(zNt[l], e);
+        float2 vM[3], vN[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float2 gM = make_float2(-ta * phv[c], mpi * thv[c]);
+          const float2 gN = make_float2(ta * thv[c], mpi * phv[c]);
+          vM[c] = cmul(aM, gM);
+          vN[c] = cadd(cscale(aNr, rhv[c]), cmul(aNt, gN));
+        }
+        const int n = l * (l + 1) + mm - 1;
+        f(n, vM);
+        f(L + n, vN);
+      }
+    }
+    pw1 = pw;
+    pw *= st;
+    em = cmul(em, make_float2(cp, sp));
+  }
+}
+
+// mixed-precision partial near field over a chunk of scatterers (coefficients s32 in
+// complex64): fp32 products per scatterer, fp64 sums across scatterers and threads
+template <int NMAX>
+__global__ void __launch_bounds__(128)
+field32_kernel(const double* __restrict__ pos, int64_t N, double k, const float2* __restrict__ s32,
+               const double* __restrict__ pts, double2* __restrict__ part) {
+  constexpr int P = 2 * NMAX * (NMAX + 2);
+  const int64_t a = blockIdx.x;
+  __shared__ double2 red[3][128];
+  double2 E[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+  const double px = pts[3 * a], py = pts[3 * a + 1], pz = pts[3 * a + 2];
+  for (int64_t i = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.y * blockDim.x) {
+    const float2* si = s32 + i * P;
+    float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f), acc2 = make_float2(0.f, 0.f);
+    waves32_near<NMAX>(k, px - pos[3 * i], py - pos[3 * i + 1], pz - pos[3 * i + 2], [&](int fidx, const float2* v) {
+      const float2 c = si[fidx];
+      acc0 = cadd(acc0, cmul(c, v[0]));
+      acc1 = cadd(acc1, cmul(c, v[1]));
+      acc2 = cadd(acc2, cmul(c, v[2]));
+    });
+    E[0] = cadd(E[0], to_c128(acc0));
+    E[1] = cadd(E[1], to_c128(acc1));
+    E[2] = cadd(E[2], to_c128(acc2));
+  }
+  for (int q = 0; q < 3; ++q) red[q][threadIdx.x] = E[q];
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double2 t = make_double2(0, 0);
+    for (int b = 0; b < blockDim.x; ++b) t = cadd(t, red[threadIdx.x][b]);
+    part[(a * gridDim.y + blockIdx.y) * 3 + threadIdx.x] = t;
+  }
+}
+
+__global__ void to_c64_kernel(const double2* __restrict__ in, float2* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = to_c64(in[i]);
 }
 
 // partial E over a chunk of scatterers: grid (M, chunks); block reduce
@@ -283,8 +438,25 @@ int field_dev(tmat_ctx* ctx, const double* pos, int64_t N, double k, int nmax, c
   if (nchunk > 65535) nchunk = 65535;
   double2* part;
   TM_TRY(scratch(ctx, "fld_part", sizeof(double2) * M * nchunk * 3, (void**)&part));
-  launch_field_n(nmax, dim3((unsigned)M, nchunk), ctx->stream, pos, N, k, s, pts, M, far, part);
+  cudaEvent_t ev = timing_begin(ctx);
+  if (!far && ctx->field_mixed) {
+    const int P = num_coeffs(nmax);
+    float2* s32;
+    TM_TRY(scratch(ctx, "fld_s32", sizeof(float2) * N * P, (void**)&s32));
+    to_c64_kernel<<<(unsigned)std::min<int64_t>(cdiv(N * P, 256), 4096), 256, 0, ctx->stream>>>(s, s32, N * P);
+    TM_LAUNCHED(ctx);
+    const dim3 g((unsigned)M, nchunk);
+    switch (nmax) {
+#define F32(NM) \
+  case NM: field32_kernel<NM><<<g, 128, 0, ctx->stream>>>(pos, N, k, s32, pts, part); break;
+      F32(1) F32(2) F32(3) F32(4) F32(5) F32(6)
+#undef F32
+    }
+  } else {
+    launch_field_n(nmax, dim3((unsigned)M, nchunk), ctx->stream, pos, N, k, s, pts, M, far, part);
+  }
   TM_LAUNCHED(ctx);
+  timing_end(ctx, far ? "farfield" : (ctx->field_mixed ? "field32" : "field64"), ev);
   field_reduce_kernel<<<(unsigned)cdiv(M * 3, 128), 128, 0, ctx->stream>>>(part, M, nchunk, E);
   TM_LAUNCHED(ctx);
   return TMAT_OK;

@@ -73,6 +73,7 @@ struct tmat_ctx {
   int tc_variant = 0;        // 0: window-view kernel where it fits, 1: gather kernel
   bool lattice_fft = true;   // lattice operators by FFT convolution where the grid fits
   bool fft_quad = true;      // complex64 FFT block products in the quad-mirror form
+  bool field_mixed = false;  // near fields in fp32 with fp64 phases (tmat_ctx_set_field_precision)
   void* pinned = nullptr;  // small pinned host staging area (status words)
 };
 

@@ -156,3 +156,24 @@ def test_adjoint_gradient_vs_oracle_and_fd(precision):
         fp = ctx().tmat_point_fom(pos, 1.0, 1.0, nmax, fwd(rp)[2][0], xf, Einc)[0]
         fm = ctx().tmat_point_fom(pos, 1.0, 1.0, nmax, fwd(rm)[2][0], xf, Einc)[0]
         assert abs(grad[i] - (fp - fm) / (2 * h)) <= 1e-4 * np.max(np.abs(grad))
+
+
+@pytest.mark.parametrize("nmax,height", [(2, 3.0), (4, 20.0), (5, 150.0)])
+def test_mixed_precision_near_field(nmax, height):
+    """tmat_ctx_set_field_precision(MIXED): fp32 waves with fp64 phases against the oracle's
+    field (detectors up to 150 wavelengths away: the phase reduction matters) to 1e-6."""
+    from paper_2107_09879_b300 import _lib
+    nx, ny = 9, 7
+    pos = W.lattice_positions(nx, ny)
+    P = 2 * nmax * (nmax + 2)
+    s = rand_c((nx * ny, P), 700 + nmax)
+    g = W.SplitMix64(710 + nmax)
+    pts = np.stack([g.uniforms(16) * 6 - 1, g.uniforms(16) * 5 - 1, height + g.uniforms(16)], axis=1)
+    c = _lib.Context(0)
+    c.set_field_precision(_lib.PREC_MIXED)
+    E32 = c.tmat_field(pos, 1.0, 1.0, nmax, s, pts)
+    c.close()
+    ref = field.scattered_field(nmax, K0, pos, s, pts)
+    assert rel_l2(E32, ref) <= 1e-6
+    E64 = ctx().tmat_field(pos, 1.0, 1.0, nmax, s, pts)
+    assert rel_l2(E64, ref) <= 1e-12
