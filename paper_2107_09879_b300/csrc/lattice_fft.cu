@@ -76,6 +76,99 @@ static int fft_twiddles(tmat_ctx* ctx, const double2** out) {
 // different banks
 __device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
 
+// ---- double-float arithmetic for the fp64-accurate transforms --------------------------
+// The B300 issues fp64 at 1/63 of its fp32 rate, so the complex128 transforms (refinement
+// residuals, fp64 operators) compute in double-float: every real is an unevaluated sum
+// hi + lo of two fp32 values (~48-bit significand), with Knuth's two-sum for additions and
+// the FMA-based exact product for multiplications (Dekker's product, FMA form). Inputs and
+// outputs stay complex128 in global memory; only the butterflies use the pairs.
+struct DF {};
+struct dfc {
+  float rh, rl, ih, il;
+};
+template <> struct cplx<DF> { using t = dfc; };
+// global element type of a transform's compute type (double-float reads/writes complex128)
+template <typename R> struct gtype { using t = C<R>; };
+template <> struct gtype<DF> { using t = double2; };
+template <typename R> using G = typename gtype<R>::t;
+
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void df_norm(float& h, float& l) {  // quick two-sum, |h| >= |l|
+  const float s = h + l;
+  l = l - (s - h);
+  h = s;
+}
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& h, float& l) {
+  float s, e;
+  df_two_sum(ah, bh, s, e);
+  e += al + bl;
+  h = s;
+  l = e;
+  df_norm(h, l);
+}
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& h, float& l) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, fmaf(al, bh, e));
+  h = p;
+  l = e;
+  df_norm(h, l);
+}
+__device__ __forceinline__ dfc cadd(dfc a, dfc b) {
+  dfc z;
+  df_add(a.rh, a.rl, b.rh, b.rl, z.rh, z.rl);
+  df_add(a.ih, a.il, b.ih, b.il, z.ih, z.il);
+  return z;
+}
+__device__ __forceinline__ dfc csub(dfc a, dfc b) {
+  dfc z;
+  df_add(a.rh, a.rl, -b.rh, -b.rl, z.rh, z.rl);
+  df_add(a.ih, a.il, -b.ih, -b.il, z.ih, z.il);
+  return z;
+}
+__device__ __forceinline__ dfc cmul(dfc a, dfc b) {
+  float p1h, p1l, p2h, p2l, p3h, p3l, p4h, p4l;
+  df_mul(a.rh, a.rl, b.rh, b.rl, p1h, p1l);
+  df_mul(a.ih, a.il, b.ih, b.il, p2h, p2l);
+  df_mul(a.rh, a.rl, b.ih, b.il, p3h, p3l);
+  df_mul(a.ih, a.il, b.rh, b.rl, p4h, p4l);
+  dfc z;
+  df_add(p1h, p1l, -p2h, -p2l, z.rh, z.rl);
+  df_add(p3h, p3l, p4h, p4l, z.ih, z.il);
+  return z;
+}
+
+template <typename R> __device__ __forceinline__ C<R> czero() { return mk<R>((R)0, (R)0); }
+template <> __device__ __forceinline__ dfc czero<DF>() { return dfc{0.f, 0.f, 0.f, 0.f}; }
+__device__ __forceinline__ void df_split(double v, float& h, float& l) {
+  h = (float)v;
+  l = (float)(v - (double)h);
+}
+template <typename R> __device__ __forceinline__ C<R> cfrom64(double re, double im) { return mk<R>((R)re, (R)im); }
+template <> __device__ __forceinline__ dfc cfrom64<DF>(double re, double im) {
+  dfc z;
+  df_split(re, z.rh, z.rl);
+  df_split(im, z.ih, z.il);
+  return z;
+}
+template <typename R> __device__ __forceinline__ C<R> gload(G<R> v) { return v; }
+template <> __device__ __forceinline__ dfc gload<DF>(double2 v) { return cfrom64<DF>(v.x, v.y); }
+template <typename R> __device__ __forceinline__ G<R> gstore(C<R> v) { return v; }
+template <> __device__ __forceinline__ double2 gstore<DF>(dfc v) {
+  return make_double2((double)v.rh + (double)v.rl, (double)v.ih + (double)v.il);
+}
+// times -i (dir < 0) or +i (dir > 0): exact
+template <typename R> __device__ __forceinline__ C<R> crot(C<R> t, int dir) {
+  return dir < 0 ? mk<R>(t.y, -t.x) : mk<R>(-t.y, t.x);
+}
+template <> __device__ __forceinline__ dfc crot<DF>(dfc t, int dir) {
+  return dir < 0 ? dfc{t.ih, t.il, -t.rh, -t.rl} : dfc{-t.ih, -t.il, t.rh, t.rl};
+}
+
 // Twiddle table by stage: wt[2^t - 1 + j] = W_{2^(t+1)}^j (j < 2^t, t < lg; W = e^{-+2 pi i/n}
 // for dir -/+), len - 1 entries, so that the threads of one stage read consecutive entries.
 template <typename R>
@@ -83,7 +176,7 @@ __device__ __forceinline__ void fft_stage_twiddles(C<R>* wt, int lg, int dir, co
   for (int e = threadIdx.x; e < (1 << lg) - 1; e += blockDim.x) {
     const int t = 31 - __clz(e + 1), j = e + 1 - (1 << t);
     const double2 w64 = tw[j << (9 - t)];  // exp(-2 pi i j / 2^(t+1)); FFT_MAXLEN = 2^10
-    wt[e] = mk<R>((R)w64.x, (R)(dir < 0 ? w64.y : -w64.y));
+    wt[e] = cfrom64<R>(w64.x, dir < 0 ? w64.y : -w64.y);
   }
 }
 
@@ -157,8 +250,7 @@ __device__ __forceinline__ void fft_smem_passes(C<R>* a, int pitch, int nrows, i
       const C<R> b0 = cadd(a0, a1), b1 = csub(a0, a1), b2 = cadd(a2, a3), b3 = csub(a2, a3);
       const C<R> t2 = cmul(w2, b2);
       C<R> t3 = cmul(w2, b3);
-      // times -i (forward) or +i (inverse)
-      t3 = dir < 0 ? mk<R>(t3.y, -t3.x) : mk<R>(-t3.y, t3.x);
+      t3 = crot<R>(t3, dir);  // times -i (forward) or +i (inverse)
       row[q0] = cadd(b0, t2);
       row[q2] = csub(b0, t2);
       row[q1] = cadd(b1, t3);
@@ -169,9 +261,9 @@ __device__ __forceinline__ void fft_smem_passes(C<R>* a, int pitch, int nrows, i
 }
 
 template <typename R, bool TOUT, bool TIN>
-__global__ void __launch_bounds__(FFT_THREADS, sizeof(R) == 4 ? 4 : 1)
-fft_rows_kernel(const C<R>* __restrict__ in, int64_t in_batch_stride, int in_pitch, int cin, int nrows,
-                C<R>* __restrict__ out, int64_t out_batch_stride, int out_pitch, int cout, int lg, int lgrb, int dir,
+__global__ void __launch_bounds__(FFT_THREADS, sizeof(C<R>) == 8 ? 4 : 2)
+fft_rows_kernel(const G<R>* __restrict__ in, int64_t in_batch_stride, int in_pitch, int cin, int nrows,
+                G<R>* __restrict__ out, int64_t out_batch_stride, int out_pitch, int cout, int lg, int lgrb, int dir,
                 const double2* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int len = 1 << lg, rb = 1 << lgrb, pitch = len + (len >> 4) + 1;
@@ -186,14 +278,14 @@ fft_rows_kernel(const C<R>* __restrict__ in, int64_t in_batch_stride, int in_pit
   // stores, so the load latency is paid once per batch rather than once per element
   if (TIN) {
     // in[k][row0 + rr] (transposed input): consecutive threads take consecutive rows of one k
-    const C<R>* src = in + (int64_t)b * in_batch_stride + row0;
+    const G<R>* src = in + (int64_t)b * in_batch_stride + row0;
     const int rr = threadIdx.x & (rb - 1), step = blockDim.x >> lgrb;
     for (int c0 = threadIdx.x >> lgrb; c0 < len; c0 += step * FFT_LOAD_BATCH) {
       C<R> v[FFT_LOAD_BATCH];
 #pragma unroll
       for (int t = 0; t < FFT_LOAD_BATCH; ++t) {
         const int cc = c0 + t * step;
-        v[t] = (rr < nr && cc < cin) ? src[(int64_t)cc * in_pitch + rr] : mk<R>((R)0, (R)0);
+        v[t] = (rr < nr && cc < cin) ? gload<R>(src[(int64_t)cc * in_pitch + rr]) : czero<R>();
       }
 #pragma unroll
       for (int t = 0; t < FFT_LOAD_BATCH; ++t) {
@@ -202,7 +294,7 @@ fft_rows_kernel(const C<R>* __restrict__ in, int64_t in_batch_stride, int in_pit
       }
     }
   } else {
-    const C<R>* src = in + (int64_t)b * in_batch_stride + (int64_t)row0 * in_pitch;
+    const G<R>* src = in + (int64_t)b * in_batch_stride + (int64_t)row0 * in_pitch;
     const int total = rb << lg;
     for (int e0 = threadIdx.x; e0 < total; e0 += blockDim.x * FFT_LOAD_BATCH) {
       C<R> v[FFT_LOAD_BATCH];
@@ -210,7 +302,7 @@ fft_rows_kernel(const C<R>* __restrict__ in, int64_t in_batch_stride, int in_pit
       for (int t = 0; t < FFT_LOAD_BATCH; ++t) {
         const int e = e0 + t * (int)blockDim.x;
         const int rr = e >> lg, cc = e & (len - 1);
-        v[t] = (e < total && rr < nr && cc < cin) ? src[(int64_t)rr * in_pitch + cc] : mk<R>((R)0, (R)0);
+        v[t] = (e < total && rr < nr && cc < cin) ? gload<R>(src[(int64_t)rr * in_pitch + cc]) : czero<R>();
       }
 #pragma unroll
       for (int t = 0; t < FFT_LOAD_BATCH; ++t) {
@@ -222,32 +314,40 @@ fft_rows_kernel(const C<R>* __restrict__ in, int64_t in_batch_stride, int in_pit
   }
   __syncthreads();
   fft_smem_passes<R>(a, pitch, rb, lg, ws, dir);
-  C<R>* dst = out + (int64_t)b * out_batch_stride;
+  G<R>* dst = out + (int64_t)b * out_batch_stride;
   if (TOUT) {
     // out[k][row0 + rr]: consecutive threads take consecutive rows of one k
     const int rr = threadIdx.x & (rb - 1);
     for (int k = threadIdx.x >> lgrb; k < cout; k += blockDim.x >> lgrb)
-      if (rr < nr) dst[(int64_t)k * out_pitch + row0 + rr] = a[rr * pitch + fpad(k)];
+      if (rr < nr) dst[(int64_t)k * out_pitch + row0 + rr] = gstore<R>(a[rr * pitch + fpad(k)]);
   } else {
     for (int rr = 0; rr < nr; ++rr)
-      for (int k = threadIdx.x; k < cout; k += blockDim.x) dst[(int64_t)(row0 + rr) * out_pitch + k] = a[rr * pitch + fpad(k)];
+      for (int k = threadIdx.x; k < cout; k += blockDim.x)
+        dst[(int64_t)(row0 + rr) * out_pitch + k] = gstore<R>(a[rr * pitch + fpad(k)]);
   }
 }
+
+// complex64 transforms compute in fp32; complex128 ones in double-float (see above)
+template <typename R> struct fft_compute { using t = R; };
+template <> struct fft_compute<double> { using t = DF; };
 
 template <typename R, bool TOUT, bool TIN = false>
 static int fft_rows(tmat_ctx* ctx, const C<R>* in, int64_t in_bs, int in_pitch, int cin, int nrows, C<R>* out,
                     int64_t out_bs, int out_pitch, int cout, int len, int64_t nbatch, int dir, const double2* tw) {
+  using CR = typename fft_compute<R>::t;
+  static_assert(sizeof(G<CR>) == sizeof(C<R>), "global element type");
   const int lg = ilog2(len);
   int lgrb = ilog2(std::max(1, std::min((TOUT || TIN) ? 16 : 8, FFT_SMEM_POINTS / len)));
   const int rb = 1 << lgrb;
-  const size_t smem = sizeof(C<R>) * ((size_t)rb * (len + (len >> 4) + 1) + len);
-  auto kern = fft_rows_kernel<R, TOUT, TIN>;
+  const size_t smem = sizeof(C<CR>) * ((size_t)rb * (len + (len >> 4) + 1) + len);
+  auto kern = fft_rows_kernel<CR, TOUT, TIN>;
   if (smem > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, smem));
   for (int64_t b0 = 0; b0 < nbatch; b0 += 65535) {
     const int nb = (int)std::min<int64_t>(65535, nbatch - b0);
     dim3 grid((unsigned)cdiv(nrows, rb), (unsigned)nb);
-    kern<<<grid, FFT_THREADS, smem, ctx->stream>>>(in + b0 * in_bs, in_bs, in_pitch, cin, nrows, out + b0 * out_bs, out_bs,
-                                                   out_pitch, cout, lg, lgrb, dir, tw);
+    kern<<<grid, FFT_THREADS, smem, ctx->stream>>>((const G<CR>*)(in + b0 * in_bs), in_bs, in_pitch, cin, nrows,
+                                                   (G<CR>*)(out + b0 * out_bs), out_bs, out_pitch, cout, lg, lgrb, dir,
+                                                   tw);
     TM_LAUNCHED(ctx);
   }
   return TMAT_OK;
