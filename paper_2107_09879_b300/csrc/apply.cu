@@ -1,185 +1,246 @@
-// Neighbour-list apply of the preconditioned Maxwell operator (App. I-C/I-D),
-// translation blocks generated per pair on the fly and discarded (App. I-D).
+// Neighbour-list apply of the preconditioned Maxwell operator (App. I-C/I-D), with the
+// translation of every pair generated on the fly and discarded (App. I-D).
 //
-// Coplanar scatterers: the block of pair (i, j) splits into two classes
-// c = (l+m+p) mod 2. Inside class c, with d = x_i - x_j, rho = |d|, phi its angle:
-//   forward (A x)_i[u]   = e^{-i m_u phi} sum_q h_q(k rho) sum_{u'} G_fwd[u,u',q] e^{+i m_u' phi} x_j[u']
-//   adjoint (A^T x)_i[u] = e^{+i m_u phi} sum_q h_q(k rho) sum_{u'} G_adj[u,u',q] e^{-i m_u' phi} x_j[u']
-// where G holds a5/b5 x Pbar_q^{|mu|}(0) (real for alpha, imaginary for beta).
-// Summing over u' inside the sum over q costs one real x complex FMA pair per
-// table entry plus one complex FMA per (u, q): fewer than forming the block.
+// Coplanar scatterers: inside the parity classes c = (l+m+p) mod 2 the block of pair
+// (i, j), d = x_i - x_j = rho (cos phi, sin phi), is a combination of fixed sparse
+// matrices with pair-dependent scalar weights:
+//   A_ij = sum_{q, mu} H_ij[q, mu] G^(q, mu),   H_ij[q, mu] = w(rho) h_q(k rho) e^{i mu phi},
+// mu in {-q, -q+2, .., q} (Pbar_q^{|mu|}(0) vanishes otherwise; it sits in G with the
+// coupling constants a5/b5), w the coupling window. Hence
+//   (A x)_i = sum_{q, mu} G^(q, mu) Z_i[q, mu],   Z_i[q, mu] = sum_j H_ij[q, mu] x_j,
+// and a target's sum over its neighbours is one dense complex product
+//   Z_i (NQM x P) = H_i (NQM x n_i) X_i (n_i x P),   NQM = (nmax+1)(2nmax+1) combinations,
+// computed in register tiles on CUDA cores; the sparse G contraction (the same tables for
+// every target) runs once per target instead of once per pair. The adjoint uses the
+// transposed tables (mu = m - m', signs of the inverted offset) on T_j x_j.
 //
-// Mapping: one warp per (target i, class c); lanes own outputs u = lane, lane+32;
-// all lanes of the warp walk the target's neighbour row together.
+// Mapping: one thread block per (target, right-hand side). The neighbour row is taken in
+// chunks of KC pairs: one warp forms each pair's w h_q and e^{i mu phi} (distance and phase
+// reduction in fp64), the block gathers the chunk's x_j rows and builds H, then every
+// thread accumulates an A x B tile of Z.
 #include "apply.h"
 #include "dev.cuh"
 #include "internal.h"
 
 namespace tmat {
 
-constexpr int MAXR = 4;
-constexpr int WARPS_PER_BLOCK = 4;
+constexpr int PS_KC = 32;  // pairs per chunk
+
+// Tiles of the pair-sum product: A x TR rows cover the NQM combinations, B x TC columns
+// the P coefficients (B * TC == P).
+template <int NMAX, bool DBL> struct PsCfg;
+#define PS_CFG(NM, D, A_, TR_, B_, TC_)  \
+  template <> struct PsCfg<NM, D> {      \
+    static constexpr int A = A_, TR = TR_, B = B_, TC = TC_; \
+  };
+PS_CFG(1, false, 1, 6, 1, 6)
+PS_CFG(2, false, 3, 5, 2, 8)
+PS_CFG(3, false, 2, 14, 5, 6)
+PS_CFG(4, false, 3, 15, 6, 8)
+PS_CFG(5, false, 6, 11, 7, 10)
+PS_CFG(6, false, 7, 13, 6, 16)
+PS_CFG(1, true, 1, 6, 1, 6)
+PS_CFG(2, true, 3, 5, 2, 8)
+PS_CFG(3, true, 2, 14, 5, 6)
+PS_CFG(4, true, 3, 15, 6, 8)
+PS_CFG(5, true, 3, 22, 7, 10)
+PS_CFG(6, true, 7, 13, 3, 32)
+#undef PS_CFG
+
+template <typename R, int NMAX> struct PsShape {
+  using Cf = PsCfg<NMAX, sizeof(R) == 8>;
+  static constexpr int L = NMAX * (NMAX + 2), P = 2 * L, Q = 2 * NMAX + 1;
+  static constexpr int NQM = (NMAX + 1) * (2 * NMAX + 1);
+  static constexpr int NQP = Cf::A * Cf::TR;  // padded rows of H
+  static constexpr int THREADS = ((Cf::TR * Cf::TC + 31) / 32) * 32 < 64 ? 64 : ((Cf::TR * Cf::TC + 31) / 32) * 32;
+  static_assert(Cf::B * Cf::TC == P, "column tiles cover P");
+  static_assert(NQP >= NQM, "row tiles cover the combinations");
+  static_assert(THREADS >= P && THREADS >= PS_KC, "one thread per output and per chunk pair");
+  // shared memory (units of C<R>): hw[KC][Q], ep[KC][Q], then the product region
+  // {Hs[KC][NQP], Xs[KC][P]} which Z[NQM][P] reuses after the last chunk
+  static constexpr int PROD = PS_KC * (NQP + P) > NQM * P ? PS_KC * (NQP + P) : NQM * P;
+  static constexpr size_t SMEM = sizeof(C<R>) * (2 * PS_KC * Q + PROD) + sizeof(int) * PS_KC;
+};
 
 template <typename R, int NMAX, int OP>
-__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
-apply_nbr_kernel(const double* __restrict__ pos, int64_t N, double k, const C<R>* __restrict__ T,
-                 const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                 const C<R>* __restrict__ x, C<R>* __restrict__ y, int nrhs, int64_t rhs_stride,
-                 const int* __restrict__ seg, const int* __restrict__ tri_idx, const R* __restrict__ tri_val,
-                 const int* __restrict__ mval, double cutoff, double taper) {
-  constexpr int L = NMAX * (NMAX + 2), P = 2 * L, Q = 2 * NMAX + 1;
-  constexpr int NU = (L + 31) / 32;
-  __shared__ C<R> xs_all[WARPS_PER_BLOCK][MAXR][L];
-  __shared__ C<R> hs_all[WARPS_PER_BLOCK][Q];
-  __shared__ C<R> ps_all[WARPS_PER_BLOCK][2 * NMAX + 1];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t gw = (int64_t)blockIdx.x * WARPS_PER_BLOCK + warp;
-  if (gw >= 2 * N) return;
-  const int64_t i = gw >> 1;
-  const int c = (int)(gw & 1);
-  C<R>(&xs)[MAXR][L] = xs_all[warp];
-  C<R>(&hs)[Q] = hs_all[warp];
-  C<R>(&ps)[2 * NMAX + 1] = ps_all[warp];
+__global__ void __launch_bounds__(PsShape<R, NMAX>::THREADS)
+pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const C<R>* __restrict__ T,
+               const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+               const C<R>* __restrict__ x, C<R>* __restrict__ y, int64_t rhs_stride,
+               const int* __restrict__ zseg, const int* __restrict__ zidx, const R* __restrict__ zval,
+               double cutoff, double taper) {
+  using S = PsShape<R, NMAX>;
+  using Cf = typename S::Cf;
+  constexpr int P = S::P, Q = S::Q, NQM = S::NQM, NQP = S::NQP, KC = PS_KC;
+  constexpr int A = Cf::A, B = Cf::B, TC = Cf::TC, TR = Cf::TR;
+  extern __shared__ __align__(16) unsigned char ps_smem[];
+  C<R>* hw = reinterpret_cast<C<R>*>(ps_smem);  // [KC][Q] w h_q
+  C<R>* ep = hw + KC * Q;                        // [KC][Q] e^{i mu phi}, mu = 0..Q-1
+  C<R>* Hs = ep + KC * Q;                        // [KC][NQP]
+  C<R>* Xs = Hs + KC * NQP;                      // [KC][P]
+  C<R>* Z = Hs;                                  // [NQM][P] after the last chunk
+  int* js = reinterpret_cast<int*>(Hs + S::PROD);
 
-  int mu_out[NU];
-  C<R> acc[MAXR][NU];
-#pragma unroll
-  for (int s = 0; s < NU; ++s) {
-    int u = lane + 32 * s;
-    mu_out[s] = (u < L) ? mval[c * L + u] : 0;
-#pragma unroll
-    for (int r = 0; r < MAXR; ++r) acc[r][s] = mk<R>(0, 0);
-  }
+  const int64_t i = blockIdx.x;
+  const int r = blockIdx.y;
+  const int tid = threadIdx.x;
+  const int tr = tid / TC, tc = tid % TC;
+  const bool tile = tr < TR;
+  const C<R>* xr = x + r * rhs_stride;
   const double xi0 = pos[3 * i], yi0 = pos[3 * i + 1];
   const int64_t jb = row_ptr[i], je = row_ptr[i + 1];
-  for (int64_t e = jb; e < je; ++e) {
-    const int64_t j = col[e];
-    const double dx = xi0 - pos[3 * j], dy = yi0 - pos[3 * j + 1];
-    const double rho = sqrt(dx * dx + dy * dy);
-    const R cp = (R)(dx / rho), sp = (R)(dy / rho);
-    {
-      C<R> h[Q];
-      hankel_up<R, Q>(k * rho, h);
-      R wgt = (R)1;
-      if (taper > 0) {
-        const double d0 = cutoff - taper;
-        if (rho > d0) {
-          if constexpr (sizeof(R) == 4) wgt = 0.5f * (1.0f + cospif((float)((rho - d0) / taper)));
-          else wgt = 0.5 * (1.0 + cospi((rho - d0) / taper));
+
+  C<R> acc[A][B];
+#pragma unroll
+  for (int a = 0; a < A; ++a)
+#pragma unroll
+    for (int b = 0; b < B; ++b) acc[a][b] = mk<R>((R)0, (R)0);
+
+  for (int64_t c0 = jb; c0 < je; c0 += KC) {
+    if (tid < KC) {  // pair weights
+      const int64_t e = c0 + tid;
+      int jj = -1;
+      if (e < je) {
+        jj = col[e];
+        const double dx = xi0 - pos[3 * jj], dy = yi0 - pos[3 * jj + 1];
+        const double r2 = dx * dx + dy * dy;
+        double rho;
+        if constexpr (sizeof(R) == 4) {
+          const double r0 = (double)rsqrtf((float)r2);  // one Newton step to fp64 accuracy
+          rho = r2 * r0;
+          rho += 0.5 * r0 * (r2 - rho * rho);
+        } else {
+          rho = sqrt(r2);
         }
-      }
-#pragma unroll
-      for (int q = 0; q < Q; ++q)
-        if (lane == q) hs[q] = cscale(h[q], wgt);
-    }
-    if (lane < 2 * NMAX + 1) {  // e^{i mu phi}, mu = lane - NMAX
-      int mu = lane - NMAX;
-      C<R> e1 = mk<R>(cp, mu < 0 ? -sp : sp), z = mk<R>(1, 0);
-      for (int t = 0; t < (mu < 0 ? -mu : mu); ++t) z = cmul(z, e1);
-      ps[lane] = z;
-    }
-    __syncwarp();
-    for (int u = lane; u < L; u += 32) {
-      const int m = mval[c * L + u];
-      const C<R> ph = ps[NMAX + (OP == 1 ? -m : m)];
-      C<R> tj = mk<R>(1, 0);
-      if (OP == 1) tj = T[j * P + c * L + u];
-      for (int r = 0; r < nrhs; ++r) {
-        C<R> xv = x[r * rhs_stride + j * P + c * L + u];
-        if (OP == 1) xv = cmul(xv, tj);
-        xs[r][u] = cmul(ph, xv);
-      }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int s = 0; s < NU; ++s) {
-      const int u = lane + 32 * s;
-      if (u < L) {
-        C<R> pr[MAXR];
-#pragma unroll
-        for (int r = 0; r < MAXR; ++r) pr[r] = mk<R>(0, 0);
-        const int* sg = seg + (c * L + u) * (Q + 1);
+        C<R> h[Q];
+        hankel_up<R, Q>(k * rho, h);
+        R wgt = (R)1;
+        if (taper > 0) {
+          const double d0 = cutoff - taper;
+          if (rho > d0) {
+            if constexpr (sizeof(R) == 4) wgt = 0.5f * (1.0f + cospif((float)((rho - d0) / taper)));
+            else wgt = 0.5 * (1.0 + cospi((rho - d0) / taper));
+          }
+        }
+        const R ir = (R)1 / (R)rho;
+        const C<R> e1 = mk<R>((R)dx * ir, (R)dy * ir);
+        C<R> z = mk<R>((R)1, (R)0);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-          const int t0 = sg[q], t1 = sg[q + 1];
-          if (t0 == t1) continue;
-          C<R> w[MAXR];
-#pragma unroll
-          for (int r = 0; r < MAXR; ++r) w[r] = mk<R>(0, 0);
-          for (int t = t0; t < t1; ++t) {
-            const int id = __ldg(tri_idx + t);
-            const R v = __ldg(tri_val + t);
-            const int up = id & 0x7fff;
-            const bool im = (id >> 15) & 1;
-#pragma unroll
-            for (int r = 0; r < MAXR; ++r) {
-              if (r < nrhs) {
-                const C<R> xv = xs[r][up];
-                const R a = im ? -xv.y : xv.x, b = im ? xv.x : xv.y;
-                w[r].x = fma(v, a, w[r].x);
-                w[r].y = fma(v, b, w[r].y);
-              }
-            }
-          }
-          const C<R> hq = hs[q];
-#pragma unroll
-          for (int r = 0; r < MAXR; ++r) cfma(pr[r], hq, w[r]);
+          hw[tid * Q + q] = cscale(h[q], wgt);
+          ep[tid * Q + q] = z;
+          z = cmul(z, e1);
         }
-        const C<R> po = ps[NMAX + (OP == 1 ? mu_out[s] : -mu_out[s])];
+      } else {
 #pragma unroll
-        for (int r = 0; r < MAXR; ++r) cfma(acc[r][s], po, pr[r]);
+        for (int q = 0; q < Q; ++q) {
+          hw[tid * Q + q] = mk<R>((R)0, (R)0);
+          ep[tid * Q + q] = mk<R>((R)0, (R)0);
+        }
+      }
+      js[tid] = jj;
+    }
+    __syncthreads();
+    // x_j rows of the chunk (T_j x_j for the adjoint), zero for absent pairs
+    for (int idx = tid; idx < KC * P; idx += S::THREADS) {
+      const int t = idx / P, c = idx - t * P;
+      const int jj = js[t];
+      C<R> v = mk<R>((R)0, (R)0);
+      if (jj >= 0) {
+        v = xr[(int64_t)jj * P + c];
+        if (OP == 1) v = cmul(v, T[(int64_t)jj * P + c]);
+      }
+      Xs[idx] = v;
+    }
+    // H[t][a] = w h_q e^{i mu phi}, a = q(q+1)/2 + (mu+q)/2
+    for (int idx = tid; idx < KC * NQM; idx += S::THREADS) {
+      const int t = idx / NQM, a = idx - t * NQM;
+      const int q = (int)((sqrtf((float)(8 * a + 1)) - 1.0f) * 0.5f);
+      const int mu = 2 * (a - q * (q + 1) / 2) - q;
+      C<R> e = ep[t * Q + (mu < 0 ? -mu : mu)];
+      if (mu < 0) e = cconj(e);
+      Hs[t * NQP + a] = cmul(hw[t * Q + q], e);
+    }
+    __syncthreads();
+    if (tile) {
+#pragma unroll 2
+      for (int t = 0; t < KC; ++t) {
+        C<R> hv[A], xv[B];
+#pragma unroll
+        for (int a = 0; a < A; ++a) hv[a] = Hs[t * NQP + tr * A + a];
+#pragma unroll
+        for (int b = 0; b < B; ++b) xv[b] = Xs[t * P + tc * B + b];
+#pragma unroll
+        for (int a = 0; a < A; ++a)
+#pragma unroll
+          for (int b = 0; b < B; ++b) cfma(acc[a][b], hv[a], xv[b]);
       }
     }
-    __syncwarp();
+    __syncthreads();
   }
+  // Z to shared memory, then the sparse contraction per output
+  if (tile) {
 #pragma unroll
-  for (int s = 0; s < NU; ++s) {
-    const int u = lane + 32 * s;
-    if (u < L) {
-      const int64_t o = i * P + c * L + u;
-      for (int r = 0; r < nrhs; ++r) {
-        const C<R> a = acc[r][s];
-        C<R> out;
-        if (OP == 2) {
-          out = a;
-        } else if (OP == 0) {
-          out = csub(x[r * rhs_stride + o], cmul(T[o], a));
-        } else {
-          out = csub(x[r * rhs_stride + o], a);
-        }
-        y[r * rhs_stride + o] = out;
+    for (int a = 0; a < A; ++a)
+      if (tr * A + a < NQM) {
+#pragma unroll
+        for (int b = 0; b < B; ++b) Z[(tr * A + a) * P + tc * B + b] = acc[a][b];
       }
+  }
+  __syncthreads();
+  if (tid < P) {
+    const int o = tid;
+    C<R> s = mk<R>((R)0, (R)0);
+    for (int e = zseg[o]; e < zseg[o + 1]; ++e) {
+      const int pk = __ldg(zidx + e);
+      const R v = __ldg(zval + e);
+      const C<R> zv = Z[((pk >> 8) & 0xff) * P + (pk & 0xff)];
+      const bool im = (pk >> 16) & 1;
+      s.x = fma(v, im ? -zv.y : zv.x, s.x);
+      s.y = fma(v, im ? zv.x : zv.y, s.y);
     }
+    const int64_t oi = i * P + o;
+    C<R> out;
+    if (OP == 2) out = s;
+    else if (OP == 0) out = csub(xr[oi], cmul(T[oi], s));
+    else out = csub(xr[oi], s);
+    y[r * rhs_stride + oi] = out;
   }
 }
 
 template <typename R, int NMAX, int OP>
-static void launch_one(cudaStream_t st, const NbrOp& a, const void* x, void* y, int nrhs, int64_t stride) {
-  const int64_t warps = 2 * a.N;
-  unsigned grid = (unsigned)cdiv(warps, WARPS_PER_BLOCK);
+static int launch_pairsum(tmat_ctx* ctx, const NbrOp& a, const void* x, void* y, int nrhs, int64_t stride) {
+  using S = PsShape<R, NMAX>;
+  auto kern = pairsum_kernel<R, NMAX, OP>;
+  if (S::SMEM > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, S::SMEM));
   const int op = OP == 1 ? 1 : 0;
-  const R* tv = sizeof(R) == 4 ? (const R*)a.tab->d_tri_f32[op] : (const R*)a.tab->d_tri_f64[op];
-  apply_nbr_kernel<R, NMAX, OP><<<grid, WARPS_PER_BLOCK * 32, 0, st>>>(
-      a.pos, a.N, a.k, (const C<R>*)a.T, a.row_ptr, a.col, (const C<R>*)x, (C<R>*)y, nrhs, stride,
-      a.tab->d_seg[op], a.tab->d_tri_idx[op], tv, a.tab->d_mval, a.cutoff, a.taper);
+  const R* zv = sizeof(R) == 4 ? (const R*)a.tab->d_zval_f32[op] : (const R*)a.tab->d_zval_f64[op];
+  kern<<<dim3((unsigned)a.N, (unsigned)nrhs), S::THREADS, S::SMEM, ctx->stream>>>(
+      a.pos, a.N, a.k, (const C<R>*)a.T, a.row_ptr, a.col, (const C<R>*)x, (C<R>*)y, stride, a.tab->d_zseg[op],
+      a.tab->d_zidx[op], zv, a.cutoff, a.taper);
+  return TMAT_OK;
 }
 
 template <typename R, int OP>
 static int dispatch_nmax(tmat_ctx* ctx, const NbrOp& a, const void* x, void* y, int nrhs, int64_t stride) {
   cudaEvent_t ev = timing_begin(ctx);
+  int rc;
   switch (a.nmax) {
-    case 1: launch_one<R, 1, OP>(ctx->stream, a, x, y, nrhs, stride); break;
-    case 2: launch_one<R, 2, OP>(ctx->stream, a, x, y, nrhs, stride); break;
-    case 3: launch_one<R, 3, OP>(ctx->stream, a, x, y, nrhs, stride); break;
-    case 4: launch_one<R, 4, OP>(ctx->stream, a, x, y, nrhs, stride); break;
-    case 5: launch_one<R, 5, OP>(ctx->stream, a, x, y, nrhs, stride); break;
-    case 6: launch_one<R, 6, OP>(ctx->stream, a, x, y, nrhs, stride); break;
+    case 1: rc = launch_pairsum<R, 1, OP>(ctx, a, x, y, nrhs, stride); break;
+    case 2: rc = launch_pairsum<R, 2, OP>(ctx, a, x, y, nrhs, stride); break;
+    case 3: rc = launch_pairsum<R, 3, OP>(ctx, a, x, y, nrhs, stride); break;
+    case 4: rc = launch_pairsum<R, 4, OP>(ctx, a, x, y, nrhs, stride); break;
+    case 5: rc = launch_pairsum<R, 5, OP>(ctx, a, x, y, nrhs, stride); break;
+    case 6: rc = launch_pairsum<R, 6, OP>(ctx, a, x, y, nrhs, stride); break;
     default: return set_error(ctx, TMAT_EINVAL, "nmax %d unsupported", a.nmax);
   }
+  if (rc) return rc;
   TM_LAUNCHED(ctx);
   timing_end(ctx, sizeof(R) == 4 ? "nbr_apply_fp32" : "nbr_apply_fp64", ev);
   return TMAT_OK;
 }
+
+constexpr int MAXR = 4;  // right-hand sides per launch
 
 // ---- general 3-D positions ------------------------------------------------------
 // Without a common plane the blocks do not split into parity classes. The block of pair

@@ -29,17 +29,21 @@ struct Tables {
   std::vector<int> mval;  // [2L] azimuthal m of each internal index
   int* d_perm = nullptr;
   int* d_mval = nullptr;
-  // planar coupling triples, per op (0 = forward, 1 = adjoint):
+  // planar coupling triples, per op (0 = forward, 1 = adjoint), host only:
   //   seg[op][(c*L+u)*(Q+1) + q] .. [.. + 1] index the triples of output (c,u), order q
-  //   tri_idx: input index u' | (imag << 15); tri_f32/f64: the real factor
-  int* d_seg[2] = {nullptr, nullptr};
-  int* d_tri_idx[2] = {nullptr, nullptr};
-  float* d_tri_f32[2] = {nullptr, nullptr};
-  double* d_tri_f64[2] = {nullptr, nullptr};
+  //   tri_idx: input index u' | (imag << 15); tri_val: the real factor
   int n_tri[2] = {0, 0};
-  // host copies of the planar triples (used to build dense lattice blocks)
   std::vector<int> seg[2], tri_idx[2];
   std::vector<double> tri_val[2];
+  // the same triples for the pair-sum apply, per op: zseg[o] .. zseg[o+1] index the
+  // entries of internal output o; zidx = column (c*L+u') | combination a << 8 | imag << 16
+  // with a = q(q+1)/2 + (mu+q)/2; zval the real factor (times i where imag)
+  std::vector<int> zseg[2], zidx[2];
+  std::vector<double> zval[2];
+  int* d_zseg[2] = {nullptr, nullptr};
+  int* d_zidx[2] = {nullptr, nullptr};
+  float* d_zval_f32[2] = {nullptr, nullptr};
+  double* d_zval_f64[2] = {nullptr, nullptr};
   // dense planar forward coefficients G[c][u][u'][q] as complex (alpha real, beta imaginary)
   double2* d_gdense = nullptr;
   // full (3-D) coupling constants a5/b5 as complex [L][L][Q] (zero where absent)

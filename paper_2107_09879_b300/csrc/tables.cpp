@@ -185,6 +185,31 @@ static void build_host(Tables* t, int nmax, std::vector<double2>& a5, std::vecto
     seg[(size_t)P * (Q + 1)] = (int)tri_idx.size();
     t->n_tri[op] = (int)tri_idx.size();
   }
+  // pair-sum tables: the triples of output o = c*L+u regrouped by combination
+  // a = q(q+1)/2 + (mu+q)/2 of the weights H[q, mu] = w h_q e^{i mu phi}, with
+  // mu = m' - m (forward) or m - m' (adjoint) and column c*L+u' of Z
+  for (int op = 0; op < 2; ++op) {
+    std::vector<int>& zseg = t->zseg[op];
+    std::vector<int>& zidx = t->zidx[op];
+    std::vector<double>& zval = t->zval[op];
+    zseg.assign((size_t)P + 1, 0);
+    zidx.clear();
+    zval.clear();
+    for (int cu = 0; cu < P; ++cu) {
+      const int c = cu / L, u = cu % L;
+      zseg[cu] = (int)zidx.size();
+      for (int q = 0; q < Q; ++q)
+        for (int e = t->seg[op][(size_t)cu * (Q + 1) + q]; e < t->seg[op][(size_t)cu * (Q + 1) + q + 1]; ++e) {
+          const int up = t->tri_idx[op][e] & 0x7fff;
+          const int im = (t->tri_idx[op][e] >> 15) & 1;
+          const int mu = op == 0 ? t->mval[c * L + up] - t->mval[c * L + u] : t->mval[c * L + u] - t->mval[c * L + up];
+          const int a = q * (q + 1) / 2 + (mu + q) / 2;  // q + |mu| is even and |mu| <= q for every triple
+          zidx.push_back((c * L + up) | (a << 8) | (im << 16));
+          zval.push_back(t->tri_val[op][e]);
+        }
+    }
+    zseg[P] = (int)zidx.size();
+  }
 }
 
 template <typename T>
@@ -211,11 +236,11 @@ int get_tables(tmat_ctx* ctx, int nmax, Tables** out) {
     if ((rc = upload(ctx, t->perm, &t->d_perm))) break;
     if ((rc = upload(ctx, t->mval, &t->d_mval))) break;
     for (int op = 0; op < 2 && !rc; ++op) {
-      std::vector<float> vf(t->tri_val[op].begin(), t->tri_val[op].end());
-      if ((rc = upload(ctx, t->seg[op], &t->d_seg[op]))) break;
-      if ((rc = upload(ctx, t->tri_idx[op], &t->d_tri_idx[op]))) break;
-      if ((rc = upload(ctx, vf, &t->d_tri_f32[op]))) break;
-      if ((rc = upload(ctx, t->tri_val[op], &t->d_tri_f64[op]))) break;
+      std::vector<float> vf(t->zval[op].begin(), t->zval[op].end());
+      if ((rc = upload(ctx, t->zseg[op], &t->d_zseg[op]))) break;
+      if ((rc = upload(ctx, t->zidx[op], &t->d_zidx[op]))) break;
+      if ((rc = upload(ctx, vf, &t->d_zval_f32[op]))) break;
+      if ((rc = upload(ctx, t->zval[op], &t->d_zval_f64[op]))) break;
     }
     if (rc) break;
     {
@@ -248,10 +273,10 @@ void free_tables(Tables* t) {
   cudaFree(t->d_perm);
   cudaFree(t->d_mval);
   for (int op = 0; op < 2; ++op) {
-    cudaFree(t->d_seg[op]);
-    cudaFree(t->d_tri_idx[op]);
-    cudaFree(t->d_tri_f32[op]);
-    cudaFree(t->d_tri_f64[op]);
+    cudaFree(t->d_zseg[op]);
+    cudaFree(t->d_zidx[op]);
+    cudaFree(t->d_zval_f32[op]);
+    cudaFree(t->d_zval_f64[op]);
   }
   cudaFree(t->d_gdense);
   cudaFree(t->d_a5);
