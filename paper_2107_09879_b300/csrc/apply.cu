@@ -17,9 +17,14 @@
 // Mapping: one thread block per (target, right-hand side). The neighbour row is taken in
 // chunks of KC pairs: one warp forms each pair's w h_q and e^{i mu phi} (distance and phase
 // reduction in fp64), the block gathers the chunk's x_j rows and builds H, then every
-// thread accumulates an A x B tile of Z.
+// thread accumulates an A x B tile of Z. Compute types: fp32 (complex64 vectors) and
+// double-float (complex128 vectors, fp64 distances, Hankel functions and phases, the
+// products and sums in fp32 pairs: the fp64 pipe runs at 1/64 of the fp32 one).
+#include <type_traits>
+
 #include "apply.h"
 #include "dev.cuh"
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace tmat {
@@ -39,6 +44,7 @@ PS_CFG(3, false, 2, 14, 5, 6)
 PS_CFG(4, false, 3, 15, 6, 8)
 PS_CFG(5, false, 6, 11, 7, 10)
 PS_CFG(6, false, 7, 13, 6, 16)
+// complex128 / double-float tiles (16-byte elements)
 PS_CFG(1, true, 1, 6, 1, 6)
 PS_CFG(2, true, 3, 5, 2, 8)
 PS_CFG(3, true, 2, 14, 5, 6)
@@ -48,7 +54,7 @@ PS_CFG(6, true, 7, 13, 3, 32)
 #undef PS_CFG
 
 template <typename R, int NMAX> struct PsShape {
-  using Cf = PsCfg<NMAX, sizeof(R) == 8>;
+  using Cf = PsCfg<NMAX, sizeof(C<R>) == 16>;
   static constexpr int L = NMAX * (NMAX + 2), P = 2 * L, Q = 2 * NMAX + 1;
   static constexpr int NQM = (NMAX + 1) * (2 * NMAX + 1);
   static constexpr int NQP = Cf::A * Cf::TR;  // padded rows of H
@@ -62,14 +68,20 @@ template <typename R, int NMAX> struct PsShape {
   static constexpr size_t SMEM = sizeof(C<R>) * (2 * PS_KC * Q + PROD) + sizeof(int) * PS_KC;
 };
 
+// real type of the per-pair geometry, Hankel functions and phases, and of the G factors
+template <typename R> using PsReal = std::conditional_t<std::is_same_v<R, float>, float, double>;
+template <typename R> __device__ __forceinline__ C<R> ps_conv(C<PsReal<R>> v) { return v; }
+template <> __device__ __forceinline__ dfc ps_conv<DF>(double2 v) { return cfrom64<DF>(v.x, v.y); }
+
 template <typename R, int NMAX, int OP>
 __global__ void __launch_bounds__(PsShape<R, NMAX>::THREADS)
-pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const C<R>* __restrict__ T,
+pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const G<R>* __restrict__ T,
                const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-               const C<R>* __restrict__ x, C<R>* __restrict__ y, int64_t rhs_stride,
-               const int* __restrict__ zseg, const int* __restrict__ zidx, const R* __restrict__ zval,
+               const G<R>* __restrict__ x, G<R>* __restrict__ y, int64_t rhs_stride,
+               const int* __restrict__ zseg, const int* __restrict__ zidx, const PsReal<R>* __restrict__ zval,
                double cutoff, double taper) {
   using S = PsShape<R, NMAX>;
+  using RG = PsReal<R>;
   using Cf = typename S::Cf;
   constexpr int P = S::P, Q = S::Q, NQM = S::NQM, NQP = S::NQP, KC = PS_KC;
   constexpr int A = Cf::A, B = Cf::B, TC = Cf::TC, TR = Cf::TR;
@@ -86,7 +98,7 @@ pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const C<R>* 
   const int tid = threadIdx.x;
   const int tr = tid / TC, tc = tid % TC;
   const bool tile = tr < TR;
-  const C<R>* xr = x + r * rhs_stride;
+  const G<R>* xr = x + r * rhs_stride;
   const double xi0 = pos[3 * i], yi0 = pos[3 * i + 1];
   const int64_t jb = row_ptr[i], je = row_ptr[i + 1];
 
@@ -94,7 +106,7 @@ pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const C<R>* 
 #pragma unroll
   for (int a = 0; a < A; ++a)
 #pragma unroll
-    for (int b = 0; b < B; ++b) acc[a][b] = mk<R>((R)0, (R)0);
+    for (int b = 0; b < B; ++b) acc[a][b] = czero<R>();
 
   for (int64_t c0 = jb; c0 < je; c0 += KC) {
     if (tid < KC) {  // pair weights
@@ -105,37 +117,37 @@ pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const C<R>* 
         const double dx = xi0 - pos[3 * jj], dy = yi0 - pos[3 * jj + 1];
         const double r2 = dx * dx + dy * dy;
         double rho;
-        if constexpr (sizeof(R) == 4) {
+        if constexpr (std::is_same_v<R, float>) {
           const double r0 = (double)rsqrtf((float)r2);  // one Newton step to fp64 accuracy
           rho = r2 * r0;
           rho += 0.5 * r0 * (r2 - rho * rho);
         } else {
           rho = sqrt(r2);
         }
-        C<R> h[Q];
-        hankel_up<R, Q>(k * rho, h);
-        R wgt = (R)1;
+        C<RG> h[Q];
+        hankel_up<RG, Q>(k * rho, h);
+        RG wgt = (RG)1;
         if (taper > 0) {
           const double d0 = cutoff - taper;
           if (rho > d0) {
-            if constexpr (sizeof(R) == 4) wgt = 0.5f * (1.0f + cospif((float)((rho - d0) / taper)));
+            if constexpr (std::is_same_v<RG, float>) wgt = 0.5f * (1.0f + cospif((float)((rho - d0) / taper)));
             else wgt = 0.5 * (1.0 + cospi((rho - d0) / taper));
           }
         }
-        const R ir = (R)1 / (R)rho;
-        const C<R> e1 = mk<R>((R)dx * ir, (R)dy * ir);
-        C<R> z = mk<R>((R)1, (R)0);
+        const RG ir = (RG)1 / (RG)rho;
+        const C<RG> e1 = mk<RG>((RG)dx * ir, (RG)dy * ir);
+        C<RG> z = mk<RG>((RG)1, (RG)0);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-          hw[tid * Q + q] = cscale(h[q], wgt);
-          ep[tid * Q + q] = z;
+          hw[tid * Q + q] = ps_conv<R>(cscale(h[q], wgt));
+          ep[tid * Q + q] = ps_conv<R>(z);
           z = cmul(z, e1);
         }
       } else {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-          hw[tid * Q + q] = mk<R>((R)0, (R)0);
-          ep[tid * Q + q] = mk<R>((R)0, (R)0);
+          hw[tid * Q + q] = czero<R>();
+          ep[tid * Q + q] = czero<R>();
         }
       }
       js[tid] = jj;
@@ -145,10 +157,10 @@ pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const C<R>* 
     for (int idx = tid; idx < KC * P; idx += S::THREADS) {
       const int t = idx / P, c = idx - t * P;
       const int jj = js[t];
-      C<R> v = mk<R>((R)0, (R)0);
+      C<R> v = czero<R>();
       if (jj >= 0) {
-        v = xr[(int64_t)jj * P + c];
-        if (OP == 1) v = cmul(v, T[(int64_t)jj * P + c]);
+        v = gload<R>(xr[(int64_t)jj * P + c]);
+        if (OP == 1) v = cmul(v, gload<R>(T[(int64_t)jj * P + c]));
       }
       Xs[idx] = v;
     }
@@ -190,20 +202,28 @@ pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const C<R>* 
   __syncthreads();
   if (tid < P) {
     const int o = tid;
-    C<R> s = mk<R>((R)0, (R)0);
+    C<R> s = czero<R>();
     for (int e = zseg[o]; e < zseg[o + 1]; ++e) {
       const int pk = __ldg(zidx + e);
-      const R v = __ldg(zval + e);
+      const RG v = __ldg(zval + e);
       const C<R> zv = Z[((pk >> 8) & 0xff) * P + (pk & 0xff)];
       const bool im = (pk >> 16) & 1;
-      s.x = fma(v, im ? -zv.y : zv.x, s.x);
-      s.y = fma(v, im ? zv.x : zv.y, s.y);
+      if constexpr (std::is_same_v<R, DF>) {
+        float vh, vl;
+        df_split(v, vh, vl);
+        const dfc zr = im ? dfc{-zv.ih, -zv.il, zv.rh, zv.rl} : zv;  // i z where imag
+        s = cadd(s, cscale_df(zr, vh, vl));
+      } else {
+        s.x = fma(v, im ? -zv.y : zv.x, s.x);
+        s.y = fma(v, im ? zv.x : zv.y, s.y);
+      }
     }
     const int64_t oi = i * P + o;
-    C<R> out;
-    if (OP == 2) out = s;
-    else if (OP == 0) out = csub(xr[oi], cmul(T[oi], s));
-    else out = csub(xr[oi], s);
+    const G<R> sg = gstore<R>(s);
+    G<R> out;
+    if (OP == 2) out = sg;
+    else if (OP == 0) out = csub(xr[oi], cmul(T[oi], sg));
+    else out = csub(xr[oi], sg);
     y[r * rhs_stride + oi] = out;
   }
 }
@@ -214,9 +234,10 @@ static int launch_pairsum(tmat_ctx* ctx, const NbrOp& a, const void* x, void* y,
   auto kern = pairsum_kernel<R, NMAX, OP>;
   if (S::SMEM > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, S::SMEM));
   const int op = OP == 1 ? 1 : 0;
-  const R* zv = sizeof(R) == 4 ? (const R*)a.tab->d_zval_f32[op] : (const R*)a.tab->d_zval_f64[op];
+  const PsReal<R>* zv = std::is_same_v<R, float> ? (const PsReal<R>*)a.tab->d_zval_f32[op]
+                                                 : (const PsReal<R>*)a.tab->d_zval_f64[op];
   kern<<<dim3((unsigned)a.N, (unsigned)nrhs), S::THREADS, S::SMEM, ctx->stream>>>(
-      a.pos, a.N, a.k, (const C<R>*)a.T, a.row_ptr, a.col, (const C<R>*)x, (C<R>*)y, stride, a.tab->d_zseg[op],
+      a.pos, a.N, a.k, (const G<R>*)a.T, a.row_ptr, a.col, (const G<R>*)x, (G<R>*)y, stride, a.tab->d_zseg[op],
       a.tab->d_zidx[op], zv, a.cutoff, a.taper);
   return TMAT_OK;
 }
@@ -236,7 +257,7 @@ static int dispatch_nmax(tmat_ctx* ctx, const NbrOp& a, const void* x, void* y, 
   }
   if (rc) return rc;
   TM_LAUNCHED(ctx);
-  timing_end(ctx, sizeof(R) == 4 ? "nbr_apply_fp32" : "nbr_apply_fp64", ev);
+  timing_end(ctx, std::is_same_v<R, float> ? "nbr_apply_fp32" : "nbr_apply_fp64", ev);
   return TMAT_OK;
 }
 
@@ -409,9 +430,9 @@ int nbr_apply(tmat_ctx* ctx, const NbrOp& a, int op, const void* x, void* y, int
       else if (op == TMAT_OP_ADJOINT) rc = dispatch_nmax<float, 1>(ctx, a, xp, yp, nr, stride);
       else rc = dispatch_nmax<float, 2>(ctx, a, xp, yp, nr, stride);
     } else {
-      if (op == TMAT_OP_FORWARD) rc = dispatch_nmax<double, 0>(ctx, a, xp, yp, nr, stride);
-      else if (op == TMAT_OP_ADJOINT) rc = dispatch_nmax<double, 1>(ctx, a, xp, yp, nr, stride);
-      else rc = dispatch_nmax<double, 2>(ctx, a, xp, yp, nr, stride);
+      if (op == TMAT_OP_FORWARD) rc = dispatch_nmax<DF, 0>(ctx, a, xp, yp, nr, stride);
+      else if (op == TMAT_OP_ADJOINT) rc = dispatch_nmax<DF, 1>(ctx, a, xp, yp, nr, stride);
+      else rc = dispatch_nmax<DF, 2>(ctx, a, xp, yp, nr, stride);
     }
     if (rc) return rc;
   }
