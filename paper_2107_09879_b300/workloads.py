@@ -101,6 +101,16 @@ def random_positions(n, box, min_sep, seed):
     return np.array(pts, dtype=np.float64)
 
 
+def jittered_lattice(nx, ny, jitter, seed, pitch=0.5):
+    """A disordered array: the nx x ny lattice sites, each displaced in x and y by
+    U[-jitter, jitter] (splitmix64 stream, x then y per site), z = 0."""
+    g = SplitMix64(seed)
+    pos = lattice_positions(nx, ny, pitch)
+    u = g.uniforms(2 * nx * ny).reshape(nx * ny, 2)
+    pos[:, :2] += jitter * (2.0 * u - 1.0)
+    return pos
+
+
 def smooth_radius_map(nx, ny, seed, pitch=0.5):
     """Seeded smoothly varying radius map in [0.08, 0.24] plus U[-0.01, 0.01]
     noise: r = 0.16 + 0.065 sin(2 pi x/97 + p1) cos(2 pi y/131 + p2) + noise."""
