@@ -31,41 +31,52 @@ namespace tmat {
 
 constexpr int PS_KC = 32;  // pairs per chunk
 
-// Tiles of the pair-sum product: A x TR rows cover the NQM combinations, B x TC columns
-// the P coefficients (B * TC == P).
-template <int NMAX, bool DBL> struct PsCfg;
-#define PS_CFG(NM, D, A_, TR_, B_, TC_)  \
-  template <> struct PsCfg<NM, D> {      \
-    static constexpr int A = A_, TR = TR_, B = B_, TC = TC_; \
+// Tiles of the pair-sum product for NR right-hand sides per block: A x TR rows cover the
+// NQM combinations, B x TC columns the NR * P coefficients (B * TC == NR * P).
+template <int NMAX, bool DBL, int NR> struct PsCfg;
+#define PS_CFG(NM, D, NR_, A_, TR_, B_, TC_)                    \
+  template <> struct PsCfg<NM, D, NR_> {                        \
+    static constexpr int A = A_, TR = TR_, B = B_, TC = TC_;    \
   };
-PS_CFG(1, false, 1, 6, 1, 6)
-PS_CFG(2, false, 3, 5, 2, 8)
-PS_CFG(3, false, 2, 14, 5, 6)
-PS_CFG(4, false, 3, 15, 6, 8)
-PS_CFG(5, false, 6, 11, 7, 10)
-PS_CFG(6, false, 7, 13, 6, 16)
-// complex128 / double-float tiles (16-byte elements)
-PS_CFG(1, true, 1, 6, 1, 6)
-PS_CFG(2, true, 3, 5, 2, 8)
-PS_CFG(3, true, 2, 14, 5, 6)
-PS_CFG(4, true, 3, 15, 6, 8)
-PS_CFG(5, true, 3, 22, 7, 10)
-PS_CFG(6, true, 7, 13, 3, 32)
+// complex64, one right-hand side
+PS_CFG(1, false, 1, 1, 6, 1, 6)
+PS_CFG(2, false, 1, 3, 5, 2, 8)
+PS_CFG(3, false, 1, 2, 14, 5, 6)
+PS_CFG(4, false, 1, 3, 15, 6, 8)
+PS_CFG(5, false, 1, 6, 11, 7, 10)
+PS_CFG(6, false, 1, 7, 13, 6, 16)
+// complex64, two right-hand sides (the weights H shared)
+PS_CFG(1, false, 2, 1, 6, 2, 6)
+PS_CFG(2, false, 2, 3, 5, 4, 8)
+PS_CFG(3, false, 2, 2, 14, 10, 6)
+PS_CFG(4, false, 2, 3, 15, 12, 8)
+PS_CFG(5, false, 2, 3, 22, 14, 10)
+PS_CFG(6, false, 2, 7, 13, 6, 32)
+// double-float, one right-hand side (16-byte elements)
+PS_CFG(1, true, 1, 1, 6, 1, 6)
+PS_CFG(2, true, 1, 3, 5, 2, 8)
+PS_CFG(3, true, 1, 2, 14, 5, 6)
+PS_CFG(4, true, 1, 3, 15, 6, 8)
+PS_CFG(5, true, 1, 3, 22, 7, 10)
+PS_CFG(6, true, 1, 7, 13, 3, 32)
 #undef PS_CFG
 
-template <typename R, int NMAX> struct PsShape {
-  using Cf = PsCfg<NMAX, sizeof(C<R>) == 16>;
+template <typename R, int NMAX, int NR> struct PsShape {
+  using Cf = PsCfg<NMAX, sizeof(C<R>) == 16, NR>;
   static constexpr int L = NMAX * (NMAX + 2), P = 2 * L, Q = 2 * NMAX + 1;
+  static constexpr int NP = NR * P;  // columns of Z
   static constexpr int NQM = (NMAX + 1) * (2 * NMAX + 1);
-  static constexpr int NQP = Cf::A * Cf::TR;  // padded rows of H
-  static constexpr int THREADS = ((Cf::TR * Cf::TC + 31) / 32) * 32 < 64 ? 64 : ((Cf::TR * Cf::TC + 31) / 32) * 32;
-  static_assert(Cf::B * Cf::TC == P, "column tiles cover P");
+  static constexpr int NQP = Cf::A * Cf::TR;  // rows of the tiles
+  static constexpr int TT = ((Cf::TR * Cf::TC + 31) / 32) * 32;
+  static constexpr int THREADS = TT < 64 ? 64 : TT;
+  static_assert(Cf::B * Cf::TC == NP, "column tiles cover NR * P");
   static_assert(NQP >= NQM, "row tiles cover the combinations");
-  static_assert(THREADS >= P && THREADS >= PS_KC, "one thread per output and per chunk pair");
+  static_assert(THREADS >= NP && THREADS >= PS_KC, "one thread per output and per chunk pair");
   // shared memory (units of C<R>): hw[KC][Q], ep[KC][Q], then the product region
-  // {Hs[KC][NQP], Xs[KC][P]} which Z[NQM][P] reuses after the last chunk
-  static constexpr int PROD = PS_KC * (NQP + P) > NQM * P ? PS_KC * (NQP + P) : NQM * P;
-  static constexpr size_t SMEM = sizeof(C<R>) * (2 * PS_KC * Q + PROD) + sizeof(int) * PS_KC;
+  // {Hs[KC][NQP], Xs[KC][NP]} which Z[NQM][NP] reuses after the last chunk; then the
+  // chunk's source indices and the combination table (ints)
+  static constexpr int PROD = PS_KC * (NQP + NP) > NQM * NP ? PS_KC * (NQP + NP) : NQM * NP;
+  static constexpr size_t SMEM = sizeof(C<R>) * (2 * PS_KC * Q + PROD) + sizeof(int) * (PS_KC + NQM);
 };
 
 // real type of the per-pair geometry, Hankel functions and phases, and of the G factors
@@ -73,34 +84,68 @@ template <typename R> using PsReal = std::conditional_t<std::is_same_v<R, float>
 template <typename R> __device__ __forceinline__ C<R> ps_conv(C<PsReal<R>> v) { return v; }
 template <> __device__ __forceinline__ dfc ps_conv<DF>(double2 v) { return cfrom64<DF>(v.x, v.y); }
 
-template <typename R, int NMAX, int OP>
-__global__ void __launch_bounds__(PsShape<R, NMAX>::THREADS)
+// Column of tile element b of column group tc. With B even the groups interleave in pairs
+// (b/2) * 2 TC + 2 tc + b % 2, so that the 16-byte loads of the TC groups of a warp fall on
+// consecutive addresses (no shared-memory bank conflicts); otherwise tc * B + b.
+template <int B, int TC> __device__ __forceinline__ int ps_col(int tc, int b) {
+  if constexpr (B % 2 == 0) return (b >> 1) * (2 * TC) + 2 * tc + (b & 1);
+  else return tc * B + b;
+}
+
+// Two consecutive coefficients of row jj (times T_jj for the adjoint) into Xs.
+template <typename R, int OP>
+__device__ __forceinline__ void ps_gather2(C<R>* dst, const G<R>* __restrict__ xrow, const G<R>* __restrict__ trow) {
+  if constexpr (std::is_same_v<R, float>) {
+    float4 v = *reinterpret_cast<const float4*>(xrow);
+    if (OP == 1) {
+      const float4 t = *reinterpret_cast<const float4*>(trow);
+      v = make_float4(v.x * t.x - v.y * t.y, v.x * t.y + v.y * t.x, v.z * t.z - v.w * t.w, v.z * t.w + v.w * t.z);
+    }
+    *reinterpret_cast<float4*>(dst) = v;
+  } else {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      C<R> v = gload<R>(xrow[h]);
+      if (OP == 1) v = cmul(v, gload<R>(trow[h]));
+      dst[h] = v;
+    }
+  }
+}
+
+template <typename R, int NMAX, int OP, int NR>
+__global__ void __launch_bounds__(PsShape<R, NMAX, NR>::THREADS)
 pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const G<R>* __restrict__ T,
                const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                const G<R>* __restrict__ x, G<R>* __restrict__ y, int64_t rhs_stride,
                const int* __restrict__ zseg, const int* __restrict__ zidx, const PsReal<R>* __restrict__ zval,
-               double cutoff, double taper) {
-  using S = PsShape<R, NMAX>;
-  using RG = PsReal<R>;
+               double cutoff, double taper, double inv_taper) {
+  using S = PsShape<R, NMAX, NR>;
   using Cf = typename S::Cf;
-  constexpr int P = S::P, Q = S::Q, NQM = S::NQM, NQP = S::NQP, KC = PS_KC;
+  using RG = PsReal<R>;
+  constexpr int P = S::P, Q = S::Q, NQM = S::NQM, NQP = S::NQP, NP = S::NP, KC = PS_KC;
   constexpr int A = Cf::A, B = Cf::B, TC = Cf::TC, TR = Cf::TR;
   extern __shared__ __align__(16) unsigned char ps_smem[];
   C<R>* hw = reinterpret_cast<C<R>*>(ps_smem);  // [KC][Q] w h_q
   C<R>* ep = hw + KC * Q;                        // [KC][Q] e^{i mu phi}, mu = 0..Q-1
   C<R>* Hs = ep + KC * Q;                        // [KC][NQP]
-  C<R>* Xs = Hs + KC * NQP;                      // [KC][P]
-  C<R>* Z = Hs;                                  // [NQM][P] after the last chunk
+  C<R>* Xs = Hs + KC * NQP;                      // [KC][NP]
+  C<R>* Z = Hs;                                  // [NQM][NP] after the last chunk
   int* js = reinterpret_cast<int*>(Hs + S::PROD);
+  int* atab = js + KC;  // combination a -> q | |mu| << 4 | (mu < 0) << 8
 
   const int64_t i = blockIdx.x;
-  const int r = blockIdx.y;
+  const int r0 = blockIdx.y * NR;
   const int tid = threadIdx.x;
   const int tr = tid / TC, tc = tid % TC;
   const bool tile = tr < TR;
-  const G<R>* xr = x + r * rhs_stride;
   const double xi0 = pos[3 * i], yi0 = pos[3 * i + 1];
   const int64_t jb = row_ptr[i], je = row_ptr[i + 1];
+  for (int a = tid; a < NQM; a += S::THREADS) {
+    int q = 0;
+    while ((q + 1) * (q + 2) / 2 <= a) ++q;
+    const int mu = 2 * (a - q * (q + 1) / 2) - q;
+    atab[a] = q | ((mu < 0 ? -mu : mu) << 4) | ((mu < 0 ? 1 : 0) << 8);
+  }
 
   C<R> acc[A][B];
 #pragma unroll
@@ -118,9 +163,9 @@ pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const G<R>* 
         const double r2 = dx * dx + dy * dy;
         double rho;
         if constexpr (std::is_same_v<R, float>) {
-          const double r0 = (double)rsqrtf((float)r2);  // one Newton step to fp64 accuracy
-          rho = r2 * r0;
-          rho += 0.5 * r0 * (r2 - rho * rho);
+          const double r0d = (double)rsqrtf((float)r2);  // one Newton step to fp64 accuracy
+          rho = r2 * r0d;
+          rho += 0.5 * r0d * (r2 - rho * rho);
         } else {
           rho = sqrt(r2);
         }
@@ -130,8 +175,8 @@ pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const G<R>* 
         if (taper > 0) {
           const double d0 = cutoff - taper;
           if (rho > d0) {
-            if constexpr (std::is_same_v<RG, float>) wgt = 0.5f * (1.0f + cospif((float)((rho - d0) / taper)));
-            else wgt = 0.5 * (1.0 + cospi((rho - d0) / taper));
+            if constexpr (std::is_same_v<RG, float>) wgt = 0.5f * (1.0f + cospif((float)(rho - d0) * (float)inv_taper));
+            else wgt = 0.5 * (1.0 + cospi((rho - d0) * inv_taper));
           }
         }
         const RG ir = (RG)1 / (RG)rho;
@@ -153,25 +198,27 @@ pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const G<R>* 
       js[tid] = jj;
     }
     __syncthreads();
-    // x_j rows of the chunk (T_j x_j for the adjoint), zero for absent pairs
-    for (int idx = tid; idx < KC * P; idx += S::THREADS) {
-      const int t = idx / P, c = idx - t * P;
+    // x_j rows of the chunk for the NR right-hand sides (T_j x_j for the adjoint), two
+    // coefficients per step, zero for absent pairs
+    for (int idx = tid; idx < KC * NP / 2; idx += S::THREADS) {
+      const int t = idx / (NP / 2), c = 2 * (idx - t * (NP / 2));
+      const int rl = c / P, cc = c - rl * P;
       const int jj = js[t];
-      C<R> v = czero<R>();
+      C<R>* dst = Xs + t * NP + c;
       if (jj >= 0) {
-        v = gload<R>(xr[(int64_t)jj * P + c]);
-        if (OP == 1) v = cmul(v, gload<R>(T[(int64_t)jj * P + c]));
+        ps_gather2<R, OP>(dst, x + (int64_t)(r0 + rl) * rhs_stride + (int64_t)jj * P + cc, T + (int64_t)jj * P + cc);
+      } else {
+        dst[0] = czero<R>();
+        dst[1] = czero<R>();
       }
-      Xs[idx] = v;
     }
-    // H[t][a] = w h_q e^{i mu phi}, a = q(q+1)/2 + (mu+q)/2
+    // H[t][a] = w h_q e^{i mu phi}
     for (int idx = tid; idx < KC * NQM; idx += S::THREADS) {
       const int t = idx / NQM, a = idx - t * NQM;
-      const int q = (int)((sqrtf((float)(8 * a + 1)) - 1.0f) * 0.5f);
-      const int mu = 2 * (a - q * (q + 1) / 2) - q;
-      C<R> e = ep[t * Q + (mu < 0 ? -mu : mu)];
-      if (mu < 0) e = cconj(e);
-      Hs[t * NQP + a] = cmul(hw[t * Q + q], e);
+      const int pk = atab[a];
+      C<R> e = ep[t * Q + ((pk >> 4) & 15)];
+      if (pk >> 8) e = cconj(e);
+      Hs[t * NQP + a] = cmul(hw[t * Q + (pk & 15)], e);
     }
     __syncthreads();
     if (tile) {
@@ -181,7 +228,7 @@ pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const G<R>* 
 #pragma unroll
         for (int a = 0; a < A; ++a) hv[a] = Hs[t * NQP + tr * A + a];
 #pragma unroll
-        for (int b = 0; b < B; ++b) xv[b] = Xs[t * P + tc * B + b];
+        for (int b = 0; b < B; ++b) xv[b] = Xs[t * NP + ps_col<B, TC>(tc, b)];
 #pragma unroll
         for (int a = 0; a < A; ++a)
 #pragma unroll
@@ -196,17 +243,18 @@ pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const G<R>* 
     for (int a = 0; a < A; ++a)
       if (tr * A + a < NQM) {
 #pragma unroll
-        for (int b = 0; b < B; ++b) Z[(tr * A + a) * P + tc * B + b] = acc[a][b];
+        for (int b = 0; b < B; ++b) Z[(tr * A + a) * NP + ps_col<B, TC>(tc, b)] = acc[a][b];
       }
   }
   __syncthreads();
-  if (tid < P) {
-    const int o = tid;
+  if (tid < NP) {
+    const int rl = tid / P, o = tid - rl * P;
+    const C<R>* Zr = Z + rl * P;
     C<R> s = czero<R>();
     for (int e = zseg[o]; e < zseg[o + 1]; ++e) {
       const int pk = __ldg(zidx + e);
       const RG v = __ldg(zval + e);
-      const C<R> zv = Z[((pk >> 8) & 0xff) * P + (pk & 0xff)];
+      const C<R> zv = Zr[((pk >> 8) & 0xff) * NP + (pk & 0xff)];
       const bool im = (pk >> 16) & 1;
       if constexpr (std::is_same_v<R, DF>) {
         float vh, vl;
@@ -219,26 +267,40 @@ pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const G<R>* 
       }
     }
     const int64_t oi = i * P + o;
+    const G<R>* xr = x + (int64_t)(r0 + rl) * rhs_stride;
     const G<R> sg = gstore<R>(s);
     G<R> out;
     if (OP == 2) out = sg;
     else if (OP == 0) out = csub(xr[oi], cmul(T[oi], sg));
     else out = csub(xr[oi], sg);
-    y[r * rhs_stride + oi] = out;
+    y[(int64_t)(r0 + rl) * rhs_stride + oi] = out;
   }
 }
 
-template <typename R, int NMAX, int OP>
-static int launch_pairsum(tmat_ctx* ctx, const NbrOp& a, const void* x, void* y, int nrhs, int64_t stride) {
-  using S = PsShape<R, NMAX>;
-  auto kern = pairsum_kernel<R, NMAX, OP>;
+template <typename R, int NMAX, int OP, int NR>
+static int launch_pairsum(tmat_ctx* ctx, const NbrOp& a, const void* x, void* y, int ngroups, int64_t stride) {
+  using S = PsShape<R, NMAX, NR>;
+  auto kern = pairsum_kernel<R, NMAX, OP, NR>;
   if (S::SMEM > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, S::SMEM));
   const int op = OP == 1 ? 1 : 0;
   const PsReal<R>* zv = std::is_same_v<R, float> ? (const PsReal<R>*)a.tab->d_zval_f32[op]
                                                  : (const PsReal<R>*)a.tab->d_zval_f64[op];
-  kern<<<dim3((unsigned)a.N, (unsigned)nrhs), S::THREADS, S::SMEM, ctx->stream>>>(
+  kern<<<dim3((unsigned)a.N, (unsigned)ngroups), S::THREADS, S::SMEM, ctx->stream>>>(
       a.pos, a.N, a.k, (const G<R>*)a.T, a.row_ptr, a.col, (const G<R>*)x, (G<R>*)y, stride, a.tab->d_zseg[op],
-      a.tab->d_zidx[op], zv, a.cutoff, a.taper);
+      a.tab->d_zidx[op], zv, a.cutoff, a.taper, a.taper > 0 ? 1.0 / a.taper : 0.0);
+  return TMAT_OK;
+}
+
+// nrhs right-hand sides: complex64 in blocks of two (the pair weights shared), then one
+template <typename R, int NMAX, int OP>
+static int launch_rhs(tmat_ctx* ctx, const NbrOp& a, const void* x, void* y, int nrhs, int64_t stride) {
+  constexpr int NR = std::is_same_v<R, float> ? 2 : 1;
+  const int ng = nrhs / NR;
+  if (ng > 0) TM_TRY((launch_pairsum<R, NMAX, OP, NR>(ctx, a, x, y, ng, stride)));
+  if (NR == 2 && (nrhs & 1)) {
+    const size_t off = sizeof(G<R>) * (size_t)stride * (nrhs - 1);
+    TM_TRY((launch_pairsum<R, NMAX, OP, 1>(ctx, a, (const char*)x + off, (char*)y + off, 1, stride)));
+  }
   return TMAT_OK;
 }
 
@@ -247,12 +309,12 @@ static int dispatch_nmax(tmat_ctx* ctx, const NbrOp& a, const void* x, void* y, 
   cudaEvent_t ev = timing_begin(ctx);
   int rc;
   switch (a.nmax) {
-    case 1: rc = launch_pairsum<R, 1, OP>(ctx, a, x, y, nrhs, stride); break;
-    case 2: rc = launch_pairsum<R, 2, OP>(ctx, a, x, y, nrhs, stride); break;
-    case 3: rc = launch_pairsum<R, 3, OP>(ctx, a, x, y, nrhs, stride); break;
-    case 4: rc = launch_pairsum<R, 4, OP>(ctx, a, x, y, nrhs, stride); break;
-    case 5: rc = launch_pairsum<R, 5, OP>(ctx, a, x, y, nrhs, stride); break;
-    case 6: rc = launch_pairsum<R, 6, OP>(ctx, a, x, y, nrhs, stride); break;
+    case 1: rc = launch_rhs<R, 1, OP>(ctx, a, x, y, nrhs, stride); break;
+    case 2: rc = launch_rhs<R, 2, OP>(ctx, a, x, y, nrhs, stride); break;
+    case 3: rc = launch_rhs<R, 3, OP>(ctx, a, x, y, nrhs, stride); break;
+    case 4: rc = launch_rhs<R, 4, OP>(ctx, a, x, y, nrhs, stride); break;
+    case 5: rc = launch_rhs<R, 5, OP>(ctx, a, x, y, nrhs, stride); break;
+    case 6: rc = launch_rhs<R, 6, OP>(ctx, a, x, y, nrhs, stride); break;
     default: return set_error(ctx, TMAT_EINVAL, "nmax %d unsupported", a.nmax);
   }
   if (rc) return rc;
