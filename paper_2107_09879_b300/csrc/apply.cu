@@ -14,12 +14,15 @@
 // every target) runs once per target instead of once per pair. The adjoint uses the
 // transposed tables (mu = m - m', signs of the inverted offset) on T_j x_j.
 //
-// Mapping: one thread block per (target, right-hand side). The neighbour row is taken in
-// chunks of KC pairs: one warp forms each pair's w h_q and e^{i mu phi} (distance and phase
-// reduction in fp64), the block gathers the chunk's x_j rows and builds H, then every
-// thread accumulates an A x B tile of Z. Compute types: fp32 (complex64 vectors) and
+// Mapping: one thread block per (target, group of NR right-hand sides). The neighbour row
+// is taken in chunks of KC pairs, double-buffered: while the tile warps accumulate their
+// A x B tiles of Z from chunk c (each thread forming its own rows of H from the weights),
+// every thread issues the asynchronous copies of chunk c+1's x_j rows (T_j x_j for the
+// adjoint, formed beforehand) and a producer warp forms its weights (w h_q and
+// e^{i mu phi}, distance and phase reduction in fp64). Compute types: fp32 (complex64 vectors) and
 // double-float (complex128 vectors, fp64 distances, Hankel functions and phases, the
 // products and sums in fp32 pairs: the fp64 pipe runs at 1/64 of the fp32 one).
+#include <algorithm>
 #include <type_traits>
 
 #include "apply.h"
@@ -28,8 +31,6 @@
 #include "internal.h"
 
 namespace tmat {
-
-constexpr int PS_KC = 32;  // pairs per chunk
 
 // Tiles of the pair-sum product for NR right-hand sides per block: A x TR rows cover the
 // NQM combinations, B x TC columns the NR * P coefficients (B * TC == NR * P).
@@ -67,22 +68,29 @@ template <typename R, int NMAX, int NR> struct PsShape {
   static constexpr int NP = NR * P;  // columns of Z
   static constexpr int NQM = (NMAX + 1) * (2 * NMAX + 1);
   static constexpr int NQP = Cf::A * Cf::TR;  // rows of the tiles
-  static constexpr int TT = ((Cf::TR * Cf::TC + 31) / 32) * 32;
-  static constexpr int THREADS = TT < 64 ? 64 : TT;
+  static constexpr int TT = ((Cf::TR * Cf::TC + 31) / 32) * 32;  // tile threads
+  static constexpr int THREADS = TT + 32;                         // + one producer warp
+  // resident blocks per SM asked of the register allocator (the shared memory allows them)
+  static constexpr int MINB = THREADS > 160 || NMAX > 4 ? 1 : sizeof(C<R>) == 16 ? 2 : NR == 2 ? 3 : 4;
+  // pairs per chunk: 32, or 16 where two buffers of gathered rows would pass 64 KB
+  static constexpr int KC = 2 * 32 * NP * sizeof(C<R>) <= 64 * 1024 ? 32 : 16;
   static_assert(Cf::B * Cf::TC == NP, "column tiles cover NR * P");
   static_assert(NQP >= NQM, "row tiles cover the combinations");
-  static_assert(THREADS >= NP && THREADS >= PS_KC, "one thread per output and per chunk pair");
-  // shared memory (units of C<R>): hw[KC][Q], ep[KC][Q], then the product region
-  // {Hs[KC][NQP], Xs[KC][NP]} which Z[NQM][NP] reuses after the last chunk; then the
-  // chunk's source indices and the combination table (ints)
-  static constexpr int PROD = PS_KC * (NQP + NP) > NQM * NP ? PS_KC * (NQP + NP) : NQM * NP;
-  static constexpr size_t SMEM = sizeof(C<R>) * (2 * PS_KC * Q + PROD) + sizeof(int) * (PS_KC + NQM);
+  static_assert(THREADS >= NP, "one thread per output");
+  // shared memory (units of C<R>): W[2][2][KC][Q] (per buffer: w h_q, then e^{i mu phi}),
+  // then Xs[2][KC][NP] which Z[NQM][NP] reuses after the last chunk
+  static constexpr int WSZ = 2 * KC * Q;  // one buffer of weights
+  static constexpr int PROD = 2 * KC * NP > NQM * NP ? 2 * KC * NP : NQM * NP;
+  static constexpr size_t SMEM = sizeof(C<R>) * (2 * WSZ + PROD);
 };
 
 // real type of the per-pair geometry, Hankel functions and phases, and of the G factors
 template <typename R> using PsReal = std::conditional_t<std::is_same_v<R, float>, float, double>;
 template <typename R> __device__ __forceinline__ C<R> ps_conv(C<PsReal<R>> v) { return v; }
 template <> __device__ __forceinline__ dfc ps_conv<DF>(double2 v) { return cfrom64<DF>(v.x, v.y); }
+// conjugate where neg (the weights of mu < 0)
+__device__ __forceinline__ float2 ps_cond_conj(float2 e, bool neg) { return neg ? cconj(e) : e; }
+__device__ __forceinline__ dfc ps_cond_conj(dfc e, bool neg) { return neg ? cconj(e) : e; }
 
 // Column of tile element b of column group tc. With B even the groups interleave in pairs
 // (b/2) * 2 TC + 2 tc + b % 2, so that the 16-byte loads of the TC groups of a warp fall on
@@ -92,60 +100,135 @@ template <int B, int TC> __device__ __forceinline__ int ps_col(int tc, int b) {
   else return tc * B + b;
 }
 
-// Two consecutive coefficients of row jj (times T_jj for the adjoint) into Xs.
-template <typename R, int OP>
-__device__ __forceinline__ void ps_gather2(C<R>* dst, const G<R>* __restrict__ xrow, const G<R>* __restrict__ trow) {
-  if constexpr (std::is_same_v<R, float>) {
-    float4 v = *reinterpret_cast<const float4*>(xrow);
-    if (OP == 1) {
-      const float4 t = *reinterpret_cast<const float4*>(trow);
-      v = make_float4(v.x * t.x - v.y * t.y, v.x * t.y + v.y * t.x, v.z * t.z - v.w * t.w, v.z * t.w + v.w * t.z);
+__device__ __forceinline__ void ps_cp_async16(void* dst, const void* src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void ps_cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void ps_cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// The source rows of one chunk for the NR right-hand sides, in the compute format
+// (16-byte asynchronous copies by every thread of the block), zero-filled past the row's end.
+template <typename R, int NMAX, int NR>
+__device__ __forceinline__ void ps_gather_async(int tid, int nthr, int64_t c0, int64_t je,
+                                                const int32_t* __restrict__ col, const C<R>* __restrict__ xg,
+                                                int64_t rhs_stride, int r0, C<R>* Xb) {
+  using S = PsShape<R, NMAX, NR>;
+  constexpr int P = S::P, NP = S::NP, KC = S::KC;
+  constexpr int EPC = 16 / (int)sizeof(C<R>);  // elements per copy
+  constexpr int CPR = NP / EPC;                // copies per pair
+  static_assert(P % EPC == 0, "copies stay inside one right-hand side");
+  for (int idx = tid; idx < KC * CPR; idx += nthr) {
+    const int t = idx / CPR, c = (idx - t * CPR) * EPC;
+    const int rl = c / P, cc = c - rl * P;
+    const int64_t e = c0 + t;
+    const bool ok = e < je;
+    const int jj = ok ? col[e] : 0;
+    ps_cp_async16(Xb + t * NP + c, xg + (int64_t)(r0 + rl) * rhs_stride + (int64_t)jj * P + cc, ok ? 16 : 0);
+  }
+  ps_cp_async_commit();
+}
+
+// The weights of one chunk of a target's neighbour row, by the producer warp (lane = its
+// lane): per pair w h_q into W[t][q] and e^{i mu phi} into W[KC + t][mu] (fp64 distance
+// and phase reduction); zero past the row's end.
+template <typename R, int NMAX, int NR>
+__device__ __forceinline__ void ps_weights(int lane, int64_t c0, int64_t je, double xi0, double yi0,
+                                           const double* __restrict__ pos, double k, const int32_t* __restrict__ col,
+                                           double cutoff, double taper, double inv_taper, C<R>* W) {
+  using S = PsShape<R, NMAX, NR>;
+  using RG = PsReal<R>;
+  constexpr int Q = S::Q, KC = S::KC;
+  if (lane >= KC) return;
+  C<R>* hw = W + lane * Q;
+  C<R>* ep = W + (KC + lane) * Q;
+  const int64_t e = c0 + lane;
+  if (e < je) {
+    const int jj = col[e];
+    const double dx = xi0 - pos[3 * jj], dy = yi0 - pos[3 * jj + 1];
+    const double r2 = dx * dx + dy * dy;
+    double rho;
+    if constexpr (std::is_same_v<R, float>) {
+      const double r0d = (double)rsqrtf((float)r2);  // one Newton step to fp64 accuracy
+      rho = r2 * r0d;
+      rho += 0.5 * r0d * (r2 - rho * rho);
+    } else {
+      rho = sqrt(r2);
     }
-    *reinterpret_cast<float4*>(dst) = v;
+    C<RG> h[Q];
+    hankel_up<RG, Q>(k * rho, h);
+    RG wgt = (RG)1;
+    if (taper > 0) {
+      const double d0 = cutoff - taper;
+      if (rho > d0) {
+        if constexpr (std::is_same_v<RG, float>) wgt = 0.5f * (1.0f + cospif((float)(rho - d0) * (float)inv_taper));
+        else wgt = 0.5 * (1.0 + cospi((rho - d0) * inv_taper));
+      }
+    }
+    const RG ir = (RG)1 / (RG)rho;
+    const C<RG> e1 = mk<RG>((RG)dx * ir, (RG)dy * ir);
+    C<RG> z = mk<RG>((RG)1, (RG)0);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      hw[q] = ps_conv<R>(cscale(h[q], wgt));
+      ep[q] = ps_conv<R>(z);
+      z = cmul(z, e1);
+    }
   } else {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      C<R> v = gload<R>(xrow[h]);
-      if (OP == 1) v = cmul(v, gload<R>(trow[h]));
-      dst[h] = v;
+    for (int q = 0; q < Q; ++q) {
+      hw[q] = czero<R>();
+      ep[q] = czero<R>();
     }
   }
 }
 
 template <typename R, int NMAX, int OP, int NR>
-__global__ void __launch_bounds__(PsShape<R, NMAX, NR>::THREADS)
+__global__ void __launch_bounds__(PsShape<R, NMAX, NR>::THREADS, PsShape<R, NMAX, NR>::MINB)
 pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const G<R>* __restrict__ T,
                const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-               const G<R>* __restrict__ x, G<R>* __restrict__ y, int64_t rhs_stride,
+               const G<R>* __restrict__ x, const C<R>* __restrict__ xg, G<R>* __restrict__ y, int64_t rhs_stride,
                const int* __restrict__ zseg, const int* __restrict__ zidx, const PsReal<R>* __restrict__ zval,
                double cutoff, double taper, double inv_taper) {
   using S = PsShape<R, NMAX, NR>;
   using Cf = typename S::Cf;
   using RG = PsReal<R>;
-  constexpr int P = S::P, Q = S::Q, NQM = S::NQM, NQP = S::NQP, NP = S::NP, KC = PS_KC;
+  constexpr int P = S::P, Q = S::Q, NQM = S::NQM, NP = S::NP, KC = S::KC, WSZ = S::WSZ;
   constexpr int A = Cf::A, B = Cf::B, TC = Cf::TC, TR = Cf::TR;
   extern __shared__ __align__(16) unsigned char ps_smem[];
-  C<R>* hw = reinterpret_cast<C<R>*>(ps_smem);  // [KC][Q] w h_q
-  C<R>* ep = hw + KC * Q;                        // [KC][Q] e^{i mu phi}, mu = 0..Q-1
-  C<R>* Hs = ep + KC * Q;                        // [KC][NQP]
-  C<R>* Xs = Hs + KC * NQP;                      // [KC][NP]
-  C<R>* Z = Hs;                                  // [NQM][NP] after the last chunk
-  int* js = reinterpret_cast<int*>(Hs + S::PROD);
-  int* atab = js + KC;  // combination a -> q | |mu| << 4 | (mu < 0) << 8
+  C<R>* W = reinterpret_cast<C<R>*>(ps_smem);  // [2][2 KC][Q]
+  C<R>* Xs = W + 2 * WSZ;                       // [2][KC][NP]
+  C<R>* Z = Xs;                                 // [NQM][NP] after the last chunk
 
   const int64_t i = blockIdx.x;
   const int r0 = blockIdx.y * NR;
   const int tid = threadIdx.x;
+  const bool producer = tid >= S::TT;
+  const int lane = tid - S::TT;
   const int tr = tid / TC, tc = tid % TC;
-  const bool tile = tr < TR;
+  const bool tile = !producer && tr < TR;
   const double xi0 = pos[3 * i], yi0 = pos[3 * i + 1];
   const int64_t jb = row_ptr[i], je = row_ptr[i + 1];
-  for (int a = tid; a < NQM; a += S::THREADS) {
+  const int nch = (int)((je - jb + KC - 1) / KC);
+  // this thread's rows of H: a = tr A + s -> (q, |mu|, mu < 0), a = q(q+1)/2 + (mu+q)/2
+  int qa[A], ma[A];
+  bool na[A];
+#pragma unroll
+  for (int s = 0; s < A; ++s) {
+    const int a = tile ? min(tr * A + s, NQM - 1) : 0;
     int q = 0;
     while ((q + 1) * (q + 2) / 2 <= a) ++q;
     const int mu = 2 * (a - q * (q + 1) / 2) - q;
-    atab[a] = q | ((mu < 0 ? -mu : mu) << 4) | ((mu < 0 ? 1 : 0) << 8);
+    qa[s] = q;
+    ma[s] = mu < 0 ? -mu : mu;
+    na[s] = mu < 0;
   }
+  if (nch > 0) {
+    if (producer) ps_weights<R, NMAX, NR>(lane, jb, je, xi0, yi0, pos, k, col, cutoff, taper, inv_taper, W);
+    ps_gather_async<R, NMAX, NR>(tid, S::THREADS, jb, je, col, xg, rhs_stride, r0, Xs);
+  }
+  ps_cp_async_wait_all();
+  __syncthreads();
 
   C<R> acc[A][B];
 #pragma unroll
@@ -153,88 +236,33 @@ pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const G<R>* 
 #pragma unroll
     for (int b = 0; b < B; ++b) acc[a][b] = czero<R>();
 
-  for (int64_t c0 = jb; c0 < je; c0 += KC) {
-    if (tid < KC) {  // pair weights
-      const int64_t e = c0 + tid;
-      int jj = -1;
-      if (e < je) {
-        jj = col[e];
-        const double dx = xi0 - pos[3 * jj], dy = yi0 - pos[3 * jj + 1];
-        const double r2 = dx * dx + dy * dy;
-        double rho;
-        if constexpr (std::is_same_v<R, float>) {
-          const double r0d = (double)rsqrtf((float)r2);  // one Newton step to fp64 accuracy
-          rho = r2 * r0d;
-          rho += 0.5 * r0d * (r2 - rho * rho);
-        } else {
-          rho = sqrt(r2);
-        }
-        C<RG> h[Q];
-        hankel_up<RG, Q>(k * rho, h);
-        RG wgt = (RG)1;
-        if (taper > 0) {
-          const double d0 = cutoff - taper;
-          if (rho > d0) {
-            if constexpr (std::is_same_v<RG, float>) wgt = 0.5f * (1.0f + cospif((float)(rho - d0) * (float)inv_taper));
-            else wgt = 0.5 * (1.0 + cospi((rho - d0) * inv_taper));
-          }
-        }
-        const RG ir = (RG)1 / (RG)rho;
-        const C<RG> e1 = mk<RG>((RG)dx * ir, (RG)dy * ir);
-        C<RG> z = mk<RG>((RG)1, (RG)0);
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-          hw[tid * Q + q] = ps_conv<R>(cscale(h[q], wgt));
-          ep[tid * Q + q] = ps_conv<R>(z);
-          z = cmul(z, e1);
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-          hw[tid * Q + q] = czero<R>();
-          ep[tid * Q + q] = czero<R>();
-        }
-      }
-      js[tid] = jj;
+  // chunk c (buffer c & 1) is multiplied while the rows of chunk c + 1 arrive (copies
+  // issued by every thread) and the producer warp forms its weights
+  for (int c = 0; c < nch; ++c) {
+    const int buf = c & 1;
+    if (c + 1 < nch) {
+      const int64_t c1 = jb + (int64_t)(c + 1) * KC;
+      if (producer) ps_weights<R, NMAX, NR>(lane, c1, je, xi0, yi0, pos, k, col, cutoff, taper, inv_taper, W + (buf ^ 1) * WSZ);
+      ps_gather_async<R, NMAX, NR>(tid, S::THREADS, c1, je, col, xg, rhs_stride, r0, Xs + (buf ^ 1) * KC * NP);
     }
-    __syncthreads();
-    // x_j rows of the chunk for the NR right-hand sides (T_j x_j for the adjoint), two
-    // coefficients per step, zero for absent pairs
-    for (int idx = tid; idx < KC * NP / 2; idx += S::THREADS) {
-      const int t = idx / (NP / 2), c = 2 * (idx - t * (NP / 2));
-      const int rl = c / P, cc = c - rl * P;
-      const int jj = js[t];
-      C<R>* dst = Xs + t * NP + c;
-      if (jj >= 0) {
-        ps_gather2<R, OP>(dst, x + (int64_t)(r0 + rl) * rhs_stride + (int64_t)jj * P + cc, T + (int64_t)jj * P + cc);
-      } else {
-        dst[0] = czero<R>();
-        dst[1] = czero<R>();
-      }
-    }
-    // H[t][a] = w h_q e^{i mu phi}
-    for (int idx = tid; idx < KC * NQM; idx += S::THREADS) {
-      const int t = idx / NQM, a = idx - t * NQM;
-      const int pk = atab[a];
-      C<R> e = ep[t * Q + ((pk >> 4) & 15)];
-      if (pk >> 8) e = cconj(e);
-      Hs[t * NQP + a] = cmul(hw[t * Q + (pk & 15)], e);
-    }
-    __syncthreads();
     if (tile) {
+      const C<R>* hw = W + buf * WSZ;
+      const C<R>* ep = hw + KC * Q;
+      const C<R>* Xb = Xs + buf * KC * NP;
 #pragma unroll 2
       for (int t = 0; t < KC; ++t) {
         C<R> hv[A], xv[B];
 #pragma unroll
-        for (int a = 0; a < A; ++a) hv[a] = Hs[t * NQP + tr * A + a];
+        for (int s = 0; s < A; ++s) hv[s] = cmul(hw[t * Q + qa[s]], ps_cond_conj(ep[t * Q + ma[s]], na[s]));
 #pragma unroll
-        for (int b = 0; b < B; ++b) xv[b] = Xs[t * NP + ps_col<B, TC>(tc, b)];
+        for (int b = 0; b < B; ++b) xv[b] = Xb[t * NP + ps_col<B, TC>(tc, b)];
 #pragma unroll
         for (int a = 0; a < A; ++a)
 #pragma unroll
           for (int b = 0; b < B; ++b) cfma(acc[a][b], hv[a], xv[b]);
       }
     }
+    ps_cp_async_wait_all();
     __syncthreads();
   }
   // Z to shared memory, then the sparse contraction per output
@@ -278,7 +306,8 @@ pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const G<R>* 
 }
 
 template <typename R, int NMAX, int OP, int NR>
-static int launch_pairsum(tmat_ctx* ctx, const NbrOp& a, const void* x, void* y, int ngroups, int64_t stride) {
+static int launch_pairsum(tmat_ctx* ctx, const NbrOp& a, const void* x, const void* xg, void* y, int ngroups,
+                          int64_t stride) {
   using S = PsShape<R, NMAX, NR>;
   auto kern = pairsum_kernel<R, NMAX, OP, NR>;
   if (S::SMEM > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, S::SMEM));
@@ -286,35 +315,67 @@ static int launch_pairsum(tmat_ctx* ctx, const NbrOp& a, const void* x, void* y,
   const PsReal<R>* zv = std::is_same_v<R, float> ? (const PsReal<R>*)a.tab->d_zval_f32[op]
                                                  : (const PsReal<R>*)a.tab->d_zval_f64[op];
   kern<<<dim3((unsigned)a.N, (unsigned)ngroups), S::THREADS, S::SMEM, ctx->stream>>>(
-      a.pos, a.N, a.k, (const G<R>*)a.T, a.row_ptr, a.col, (const G<R>*)x, (G<R>*)y, stride, a.tab->d_zseg[op],
-      a.tab->d_zidx[op], zv, a.cutoff, a.taper, a.taper > 0 ? 1.0 / a.taper : 0.0);
+      a.pos, a.N, a.k, (const G<R>*)a.T, a.row_ptr, a.col, (const G<R>*)x, (const C<R>*)xg, (G<R>*)y, stride,
+      a.tab->d_zseg[op], a.tab->d_zidx[op], zv, a.cutoff, a.taper, a.taper > 0 ? 1.0 / a.taper : 0.0);
   return TMAT_OK;
 }
 
 // nrhs right-hand sides: complex64 in blocks of two (the pair weights shared), then one
 template <typename R, int NMAX, int OP>
-static int launch_rhs(tmat_ctx* ctx, const NbrOp& a, const void* x, void* y, int nrhs, int64_t stride) {
+static int launch_rhs(tmat_ctx* ctx, const NbrOp& a, const void* x, const void* xg, void* y, int nrhs,
+                      int64_t stride) {
   constexpr int NR = std::is_same_v<R, float> ? 2 : 1;
   const int ng = nrhs / NR;
-  if (ng > 0) TM_TRY((launch_pairsum<R, NMAX, OP, NR>(ctx, a, x, y, ng, stride)));
+  if (ng > 0) TM_TRY((launch_pairsum<R, NMAX, OP, NR>(ctx, a, x, xg, y, ng, stride)));
   if (NR == 2 && (nrhs & 1)) {
     const size_t off = sizeof(G<R>) * (size_t)stride * (nrhs - 1);
-    TM_TRY((launch_pairsum<R, NMAX, OP, 1>(ctx, a, (const char*)x + off, (char*)y + off, 1, stride)));
+    const size_t offg = sizeof(C<R>) * (size_t)stride * (nrhs - 1);
+    TM_TRY((launch_pairsum<R, NMAX, OP, 1>(ctx, a, (const char*)x + off, (const char*)xg + offg, (char*)y + off, 1,
+                                           stride)));
   }
   return TMAT_OK;
+}
+
+// The gathered sources in the compute format: xg[r] = x[r] (times T elementwise for the
+// adjoint), n = N P coefficients per right-hand side
+template <typename R, bool MULT>
+__global__ void ps_sources_kernel(const G<R>* __restrict__ x, const G<R>* __restrict__ T, C<R>* __restrict__ xg,
+                                  int64_t n, int nrhs, int64_t stride) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n * nrhs;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / n, e = idx - r * n;
+    G<R> v = x[r * stride + e];
+    if (MULT) v = cmul(v, T[e]);
+    xg[r * stride + e] = gload<R>(v);
+  }
 }
 
 template <typename R, int OP>
 static int dispatch_nmax(tmat_ctx* ctx, const NbrOp& a, const void* x, void* y, int nrhs, int64_t stride) {
   cudaEvent_t ev = timing_begin(ctx);
+  const void* xg = x;
+  if (OP == 1 || !std::is_same_v<R, float>) {  // T_j x_j for the adjoint; double-float pairs
+    void* xt = nullptr;
+    TM_TRY(scratch(ctx, "nbr_sources", sizeof(C<R>) * (size_t)stride * nrhs, &xt));
+    const int64_t n = a.N * num_coeffs(a.nmax);
+    const unsigned grid = (unsigned)std::min<int64_t>(cdiv(n * nrhs, 256), 8 * (int64_t)ctx->num_sms);
+    if (OP == 1)
+      ps_sources_kernel<R, true><<<grid, 256, 0, ctx->stream>>>((const G<R>*)x, (const G<R>*)a.T, (C<R>*)xt, n, nrhs,
+                                                                stride);
+    else
+      ps_sources_kernel<R, false><<<grid, 256, 0, ctx->stream>>>((const G<R>*)x, (const G<R>*)a.T, (C<R>*)xt, n, nrhs,
+                                                                 stride);
+    TM_LAUNCHED(ctx);
+    xg = xt;
+  }
   int rc;
   switch (a.nmax) {
-    case 1: rc = launch_rhs<R, 1, OP>(ctx, a, x, y, nrhs, stride); break;
-    case 2: rc = launch_rhs<R, 2, OP>(ctx, a, x, y, nrhs, stride); break;
-    case 3: rc = launch_rhs<R, 3, OP>(ctx, a, x, y, nrhs, stride); break;
-    case 4: rc = launch_rhs<R, 4, OP>(ctx, a, x, y, nrhs, stride); break;
-    case 5: rc = launch_rhs<R, 5, OP>(ctx, a, x, y, nrhs, stride); break;
-    case 6: rc = launch_rhs<R, 6, OP>(ctx, a, x, y, nrhs, stride); break;
+    case 1: rc = launch_rhs<R, 1, OP>(ctx, a, x, xg, y, nrhs, stride); break;
+    case 2: rc = launch_rhs<R, 2, OP>(ctx, a, x, xg, y, nrhs, stride); break;
+    case 3: rc = launch_rhs<R, 3, OP>(ctx, a, x, xg, y, nrhs, stride); break;
+    case 4: rc = launch_rhs<R, 4, OP>(ctx, a, x, xg, y, nrhs, stride); break;
+    case 5: rc = launch_rhs<R, 5, OP>(ctx, a, x, xg, y, nrhs, stride); break;
+    case 6: rc = launch_rhs<R, 6, OP>(ctx, a, x, xg, y, nrhs, stride); break;
     default: return set_error(ctx, TMAT_EINVAL, "nmax %d unsupported", a.nmax);
   }
   if (rc) return rc;
