@@ -33,40 +33,60 @@
 namespace tmat {
 
 // Tiles of the pair-sum product for NR right-hand sides per block: A x TR rows cover the
-// NQM combinations, B x TC columns the NR * P coefficients (B * TC == NR * P).
-template <int NMAX, bool DBL, int NR> struct PsCfg;
-#define PS_CFG(NM, D, NR_, A_, TR_, B_, TC_)                    \
-  template <> struct PsCfg<NM, D, NR_> {                        \
-    static constexpr int A = A_, TR = TR_, B = B_, TC = TC_;    \
+// NQM combinations, B x TC columns the NR * P coefficients (B * TC == NR * P); D3: off the
+// plane (NQM = (2 nmax + 1)^2 combinations).
+template <int NMAX, bool DBL, int NR, bool D3> struct PsCfg;
+#define PS_CFG(NM, D, NR_, D3_, A_, TR_, B_, TC_)              \
+  template <> struct PsCfg<NM, D, NR_, D3_> {                  \
+    static constexpr int A = A_, TR = TR_, B = B_, TC = TC_;   \
   };
 // complex64, one right-hand side
-PS_CFG(1, false, 1, 1, 6, 1, 6)
-PS_CFG(2, false, 1, 3, 5, 2, 8)
-PS_CFG(3, false, 1, 2, 14, 5, 6)
-PS_CFG(4, false, 1, 3, 15, 6, 8)
-PS_CFG(5, false, 1, 6, 11, 7, 10)
-PS_CFG(6, false, 1, 7, 13, 6, 16)
+PS_CFG(1, false, 1, false, 1, 6, 1, 6)
+PS_CFG(2, false, 1, false, 3, 5, 2, 8)
+PS_CFG(3, false, 1, false, 2, 14, 5, 6)
+PS_CFG(4, false, 1, false, 3, 15, 6, 8)
+PS_CFG(5, false, 1, false, 6, 11, 7, 10)
+PS_CFG(6, false, 1, false, 7, 13, 6, 16)
 // complex64, two right-hand sides (the weights H shared)
-PS_CFG(1, false, 2, 1, 6, 2, 6)
-PS_CFG(2, false, 2, 3, 5, 4, 8)
-PS_CFG(3, false, 2, 2, 14, 10, 6)
-PS_CFG(4, false, 2, 3, 15, 12, 8)
-PS_CFG(5, false, 2, 3, 22, 14, 10)
-PS_CFG(6, false, 2, 7, 13, 6, 32)
+PS_CFG(1, false, 2, false, 1, 6, 2, 6)
+PS_CFG(2, false, 2, false, 3, 5, 4, 8)
+PS_CFG(3, false, 2, false, 2, 14, 10, 6)
+PS_CFG(4, false, 2, false, 3, 15, 12, 8)
+PS_CFG(5, false, 2, false, 3, 22, 14, 10)
+PS_CFG(6, false, 2, false, 7, 13, 6, 32)
 // double-float, one right-hand side (16-byte elements)
-PS_CFG(1, true, 1, 1, 6, 1, 6)
-PS_CFG(2, true, 1, 3, 5, 2, 8)
-PS_CFG(3, true, 1, 2, 14, 5, 6)
-PS_CFG(4, true, 1, 3, 15, 6, 8)
-PS_CFG(5, true, 1, 3, 22, 7, 10)
-PS_CFG(6, true, 1, 7, 13, 3, 32)
+PS_CFG(1, true, 1, false, 1, 6, 1, 6)
+PS_CFG(2, true, 1, false, 3, 5, 2, 8)
+PS_CFG(3, true, 1, false, 2, 14, 5, 6)
+PS_CFG(4, true, 1, false, 3, 15, 6, 8)
+PS_CFG(5, true, 1, false, 3, 22, 7, 10)
+PS_CFG(6, true, 1, false, 7, 13, 3, 32)
+// off the plane (nmax <= 5): complex64 one and two right-hand sides, double-float one
+PS_CFG(1, false, 1, true, 3, 3, 1, 6)
+PS_CFG(2, false, 1, true, 5, 5, 2, 8)
+PS_CFG(3, false, 1, true, 7, 7, 5, 6)
+PS_CFG(4, false, 1, true, 3, 27, 6, 8)
+PS_CFG(5, false, 1, true, 4, 31, 7, 10)
+PS_CFG(1, false, 2, true, 3, 3, 2, 6)
+PS_CFG(2, false, 2, true, 5, 5, 4, 8)
+PS_CFG(3, false, 2, true, 7, 7, 5, 12)
+PS_CFG(4, false, 2, true, 3, 27, 12, 8)
+PS_CFG(5, false, 2, true, 4, 31, 14, 10)
+PS_CFG(1, true, 1, true, 3, 3, 1, 6)
+PS_CFG(2, true, 1, true, 5, 5, 2, 8)
+PS_CFG(3, true, 1, true, 7, 7, 5, 6)
+PS_CFG(4, true, 1, true, 3, 27, 6, 8)
+PS_CFG(5, true, 1, true, 4, 31, 7, 10)
 #undef PS_CFG
 
-template <typename R, int NMAX, int NR> struct PsShape {
-  using Cf = PsCfg<NMAX, sizeof(C<R>) == 16, NR>;
+template <typename R, int NMAX, int NR, bool D3> struct PsShape {
+  using Cf = PsCfg<NMAX, sizeof(C<R>) == 16, NR, D3>;
   static constexpr int L = NMAX * (NMAX + 2), P = 2 * L, Q = 2 * NMAX + 1;
   static constexpr int NP = NR * P;  // columns of Z
-  static constexpr int NQM = (NMAX + 1) * (2 * NMAX + 1);
+  static constexpr int NQM = D3 ? Q * Q : (NMAX + 1) * (2 * NMAX + 1);
+  // per pair: HWN radial weights (w h_q; off the plane w h_q Pbar_q^m(cos theta), m <= q)
+  // and the Q phases e^{i m phi}
+  static constexpr int HWN = D3 ? Q * (Q + 1) / 2 : Q;
   static constexpr int NQP = Cf::A * Cf::TR;  // rows of the tiles
   static constexpr int TT = ((Cf::TR * Cf::TC + 31) / 32) * 32;  // tile threads
   static constexpr int THREADS = TT + 32;                         // + one producer warp
@@ -77,9 +97,9 @@ template <typename R, int NMAX, int NR> struct PsShape {
   static_assert(Cf::B * Cf::TC == NP, "column tiles cover NR * P");
   static_assert(NQP >= NQM, "row tiles cover the combinations");
   static_assert(THREADS >= NP, "one thread per output");
-  // shared memory (units of C<R>): W[2][2][KC][Q] (per buffer: w h_q, then e^{i mu phi}),
-  // then Xs[2][KC][NP] which Z[NQM][NP] reuses after the last chunk
-  static constexpr int WSZ = 2 * KC * Q;  // one buffer of weights
+  // shared memory (units of C<R>): W[2][KC][HWN + Q] (per buffer: the radial weights, then
+  // the phases), then Xs[2][KC][NP] which Z[NQM][NP] reuses after the last chunk
+  static constexpr int WSZ = KC * (HWN + Q);  // one buffer of weights
   static constexpr int PROD = 2 * KC * NP > NQM * NP ? 2 * KC * NP : NQM * NP;
   static constexpr size_t SMEM = sizeof(C<R>) * (2 * WSZ + PROD);
 };
@@ -109,11 +129,11 @@ __device__ __forceinline__ void ps_cp_async_wait_all() { asm volatile("cp.async.
 
 // The source rows of one chunk for the NR right-hand sides, in the compute format
 // (16-byte asynchronous copies by every thread of the block), zero-filled past the row's end.
-template <typename R, int NMAX, int NR>
+template <typename R, int NMAX, int NR, bool D3>
 __device__ __forceinline__ void ps_gather_async(int tid, int nthr, int64_t c0, int64_t je,
                                                 const int32_t* __restrict__ col, const C<R>* __restrict__ xg,
                                                 int64_t rhs_stride, int r0, C<R>* Xb) {
-  using S = PsShape<R, NMAX, NR>;
+  using S = PsShape<R, NMAX, NR, D3>;
   constexpr int P = S::P, NP = S::NP, KC = S::KC;
   constexpr int EPC = 16 / (int)sizeof(C<R>);  // elements per copy
   constexpr int CPR = NP / EPC;                // copies per pair
@@ -130,73 +150,100 @@ __device__ __forceinline__ void ps_gather_async(int tid, int nthr, int64_t c0, i
 }
 
 // The weights of one chunk of a target's neighbour row, by the producer warp (lane = its
-// lane): per pair w h_q into W[t][q] and e^{i mu phi} into W[KC + t][mu] (fp64 distance
-// and phase reduction); zero past the row's end.
-template <typename R, int NMAX, int NR>
-__device__ __forceinline__ void ps_weights(int lane, int64_t c0, int64_t je, double xi0, double yi0,
+// lane): per pair the radial weights into W[t][0..HWN) (on the plane w h_q; off the plane
+// w h_q Pbar_q^m(cos theta) at q(q+1)/2 + m, m <= q) and e^{i m phi} into
+// W[KC HWN + t Q + m] (fp64 distance and phase reduction); zero past the row's end.
+template <typename R, int NMAX, int NR, bool D3>
+__device__ __forceinline__ void ps_weights(int lane, int64_t c0, int64_t je, double xi0, double yi0, double zi0,
                                            const double* __restrict__ pos, double k, const int32_t* __restrict__ col,
                                            double cutoff, double taper, double inv_taper, C<R>* W) {
-  using S = PsShape<R, NMAX, NR>;
+  using S = PsShape<R, NMAX, NR, D3>;
   using RG = PsReal<R>;
-  constexpr int Q = S::Q, KC = S::KC;
+  constexpr int Q = S::Q, KC = S::KC, HWN = S::HWN;
   if (lane >= KC) return;
-  C<R>* hw = W + lane * Q;
-  C<R>* ep = W + (KC + lane) * Q;
+  C<R>* hw = W + lane * HWN;
+  C<R>* ep = W + KC * HWN + lane * Q;
   const int64_t e = c0 + lane;
-  if (e < je) {
-    const int jj = col[e];
-    const double dx = xi0 - pos[3 * jj], dy = yi0 - pos[3 * jj + 1];
-    const double r2 = dx * dx + dy * dy;
-    double rho;
-    if constexpr (std::is_same_v<R, float>) {
-      const double r0d = (double)rsqrtf((float)r2);  // one Newton step to fp64 accuracy
-      rho = r2 * r0d;
-      rho += 0.5 * r0d * (r2 - rho * rho);
-    } else {
-      rho = sqrt(r2);
-    }
-    C<RG> h[Q];
-    hankel_up<RG, Q>(k * rho, h);
-    RG wgt = (RG)1;
-    if (taper > 0) {
-      const double d0 = cutoff - taper;
-      if (rho > d0) {
-        if constexpr (std::is_same_v<RG, float>) wgt = 0.5f * (1.0f + cospif((float)(rho - d0) * (float)inv_taper));
-        else wgt = 0.5 * (1.0 + cospi((rho - d0) * inv_taper));
-      }
-    }
-    const RG ir = (RG)1 / (RG)rho;
-    const C<RG> e1 = mk<RG>((RG)dx * ir, (RG)dy * ir);
-    C<RG> z = mk<RG>((RG)1, (RG)0);
+  if (e >= je) {
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      hw[q] = ps_conv<R>(cscale(h[q], wgt));
-      ep[q] = ps_conv<R>(z);
-      z = cmul(z, e1);
+    for (int q = 0; q < HWN; ++q) hw[q] = czero<R>();
+#pragma unroll
+    for (int q = 0; q < Q; ++q) ep[q] = czero<R>();
+    return;
+  }
+  const int jj = col[e];
+  const double dx = xi0 - pos[3 * jj], dy = yi0 - pos[3 * jj + 1];
+  const double dz = D3 ? zi0 - pos[3 * jj + 2] : 0.0;
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  double rho;
+  if constexpr (std::is_same_v<R, float>) {
+    const double r0d = (double)rsqrtf((float)r2);  // one Newton step to fp64 accuracy
+    rho = r2 * r0d;
+    rho += 0.5 * r0d * (r2 - rho * rho);
+  } else {
+    rho = sqrt(r2);
+  }
+  C<RG> h[Q];
+  hankel_up<RG, Q>(k * rho, h);
+  RG wgt = (RG)1;
+  if (taper > 0) {
+    const double d0 = cutoff - taper;
+    if (rho > d0) {
+      if constexpr (std::is_same_v<RG, float>) wgt = 0.5f * (1.0f + cospif((float)(rho - d0) * (float)inv_taper));
+      else wgt = 0.5 * (1.0 + cospi((rho - d0) * inv_taper));
+    }
+  }
+  C<RG> e1;
+  if constexpr (D3) {  // theta, phi of d; phi = 0 on the axis
+    const RG ir = (RG)1 / (RG)rho, rxy = (RG)sqrt(dx * dx + dy * dy);
+    const RG ct = (RG)dz * ir, st = rxy * ir;
+    e1 = rxy > (RG)0 ? mk<RG>((RG)dx / rxy, (RG)dy / rxy) : mk<RG>((RG)1, (RG)0);
+    // Pbar_q^m(cos theta), m = 0..Q-1, upward in q from Pbar_m^m
+    RG smm = (RG)1;  // st^m
+    for (int m = 0; m < Q; ++m) {
+      RG df = 1, f2 = 1;
+      for (int t = 1; t < 2 * m; t += 2) df *= (RG)t;
+      for (int t = 2; t <= 2 * m; ++t) f2 *= (RG)t;
+      RG pprev = 0, pcur = sqrt((RG)(2 * m + 1) / ((RG)2 * f2)) * df * smm;
+      hw[m * (m + 1) / 2 + m] = ps_conv<R>(cscale(h[m], wgt * pcur));
+      for (int q = m + 1; q < Q; ++q) {
+        const RG a = sqrt((RG)(4 * q * q - 1) / (RG)(q * q - m * m));
+        const RG b = sqrt((RG)((q - 1) * (q - 1) - m * m) / (RG)(4 * (q - 1) * (q - 1) - 1));
+        const RG pn = a * (ct * pcur - b * pprev);
+        pprev = pcur;
+        pcur = pn;
+        hw[q * (q + 1) / 2 + m] = ps_conv<R>(cscale(h[q], wgt * pcur));
+      }
+      smm *= st;
     }
   } else {
+    const RG ir = (RG)1 / (RG)rho;
+    e1 = mk<RG>((RG)dx * ir, (RG)dy * ir);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      hw[q] = czero<R>();
-      ep[q] = czero<R>();
-    }
+    for (int q = 0; q < Q; ++q) hw[q] = ps_conv<R>(cscale(h[q], wgt));
+  }
+  C<RG> z = mk<RG>((RG)1, (RG)0);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    ep[q] = ps_conv<R>(z);
+    z = cmul(z, e1);
   }
 }
 
-template <typename R, int NMAX, int OP, int NR>
-__global__ void __launch_bounds__(PsShape<R, NMAX, NR>::THREADS, PsShape<R, NMAX, NR>::MINB)
+template <typename R, int NMAX, int OP, int NR, bool D3>
+__global__ void __launch_bounds__(PsShape<R, NMAX, NR, D3>::THREADS, PsShape<R, NMAX, NR, D3>::MINB)
 pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const G<R>* __restrict__ T,
                const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                const G<R>* __restrict__ x, const C<R>* __restrict__ xg, G<R>* __restrict__ y, int64_t rhs_stride,
                const int* __restrict__ zseg, const int* __restrict__ zidx, const PsReal<R>* __restrict__ zval,
                double cutoff, double taper, double inv_taper) {
-  using S = PsShape<R, NMAX, NR>;
+  using S = PsShape<R, NMAX, NR, D3>;
   using Cf = typename S::Cf;
   using RG = PsReal<R>;
-  constexpr int P = S::P, Q = S::Q, NQM = S::NQM, NP = S::NP, KC = S::KC, WSZ = S::WSZ;
+  constexpr int P = S::P, Q = S::Q, NQM = S::NQM, NP = S::NP, KC = S::KC, WSZ = S::WSZ, HWN = S::HWN;
   constexpr int A = Cf::A, B = Cf::B, TC = Cf::TC, TR = Cf::TR;
   extern __shared__ __align__(16) unsigned char ps_smem[];
-  C<R>* W = reinterpret_cast<C<R>*>(ps_smem);  // [2][2 KC][Q]
+  C<R>* W = reinterpret_cast<C<R>*>(ps_smem);  // [2][KC][HWN + Q]
   C<R>* Xs = W + 2 * WSZ;                       // [2][KC][NP]
   C<R>* Z = Xs;                                 // [NQM][NP] after the last chunk
 
@@ -207,25 +254,32 @@ pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const G<R>* 
   const int lane = tid - S::TT;
   const int tr = tid / TC, tc = tid % TC;
   const bool tile = !producer && tr < TR;
-  const double xi0 = pos[3 * i], yi0 = pos[3 * i + 1];
+  const double xi0 = pos[3 * i], yi0 = pos[3 * i + 1], zi0 = pos[3 * i + 2];
   const int64_t jb = row_ptr[i], je = row_ptr[i + 1];
   const int nch = (int)((je - jb + KC - 1) / KC);
-  // this thread's rows of H: a = tr A + s -> (q, |mu|, mu < 0), a = q(q+1)/2 + (mu+q)/2
+  // this thread's rows of H: a = tr A + s -> (q, |mu|, mu < 0) with a = q(q+1)/2 + (mu+q)/2
+  // on the plane, a = q^2 + mu + q off it; qa: the radial weight's slot, ma = |mu|
   int qa[A], ma[A];
   bool na[A];
 #pragma unroll
   for (int s = 0; s < A; ++s) {
     const int a = tile ? min(tr * A + s, NQM - 1) : 0;
-    int q = 0;
-    while ((q + 1) * (q + 2) / 2 <= a) ++q;
-    const int mu = 2 * (a - q * (q + 1) / 2) - q;
-    qa[s] = q;
+    int q = 0, mu;
+    if constexpr (D3) {
+      while ((q + 1) * (q + 1) <= a) ++q;
+      mu = a - q * q - q;
+    } else {
+      while ((q + 1) * (q + 2) / 2 <= a) ++q;
+      mu = 2 * (a - q * (q + 1) / 2) - q;
+    }
     ma[s] = mu < 0 ? -mu : mu;
+    qa[s] = D3 ? q * (q + 1) / 2 + ma[s] : q;
     na[s] = mu < 0;
   }
   if (nch > 0) {
-    if (producer) ps_weights<R, NMAX, NR>(lane, jb, je, xi0, yi0, pos, k, col, cutoff, taper, inv_taper, W);
-    ps_gather_async<R, NMAX, NR>(tid, S::THREADS, jb, je, col, xg, rhs_stride, r0, Xs);
+    if (producer)
+      ps_weights<R, NMAX, NR, D3>(lane, jb, je, xi0, yi0, zi0, pos, k, col, cutoff, taper, inv_taper, W);
+    ps_gather_async<R, NMAX, NR, D3>(tid, S::THREADS, jb, je, col, xg, rhs_stride, r0, Xs);
   }
   ps_cp_async_wait_all();
   __syncthreads();
@@ -242,18 +296,20 @@ pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const G<R>* 
     const int buf = c & 1;
     if (c + 1 < nch) {
       const int64_t c1 = jb + (int64_t)(c + 1) * KC;
-      if (producer) ps_weights<R, NMAX, NR>(lane, c1, je, xi0, yi0, pos, k, col, cutoff, taper, inv_taper, W + (buf ^ 1) * WSZ);
-      ps_gather_async<R, NMAX, NR>(tid, S::THREADS, c1, je, col, xg, rhs_stride, r0, Xs + (buf ^ 1) * KC * NP);
+      if (producer)
+        ps_weights<R, NMAX, NR, D3>(lane, c1, je, xi0, yi0, zi0, pos, k, col, cutoff, taper, inv_taper,
+                                    W + (buf ^ 1) * WSZ);
+      ps_gather_async<R, NMAX, NR, D3>(tid, S::THREADS, c1, je, col, xg, rhs_stride, r0, Xs + (buf ^ 1) * KC * NP);
     }
     if (tile) {
       const C<R>* hw = W + buf * WSZ;
-      const C<R>* ep = hw + KC * Q;
+      const C<R>* ep = hw + KC * HWN;
       const C<R>* Xb = Xs + buf * KC * NP;
 #pragma unroll 2
       for (int t = 0; t < KC; ++t) {
         C<R> hv[A], xv[B];
 #pragma unroll
-        for (int s = 0; s < A; ++s) hv[s] = cmul(hw[t * Q + qa[s]], ps_cond_conj(ep[t * Q + ma[s]], na[s]));
+        for (int s = 0; s < A; ++s) hv[s] = cmul(hw[t * HWN + qa[s]], ps_cond_conj(ep[t * Q + ma[s]], na[s]));
 #pragma unroll
         for (int b = 0; b < B; ++b) xv[b] = Xb[t * NP + ps_col<B, TC>(tc, b)];
 #pragma unroll
@@ -305,33 +361,36 @@ pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const G<R>* 
   }
 }
 
-template <typename R, int NMAX, int OP, int NR>
+template <typename R, int NMAX, int OP, int NR, bool D3>
 static int launch_pairsum(tmat_ctx* ctx, const NbrOp& a, const void* x, const void* xg, void* y, int ngroups,
                           int64_t stride) {
-  using S = PsShape<R, NMAX, NR>;
-  auto kern = pairsum_kernel<R, NMAX, OP, NR>;
+  using S = PsShape<R, NMAX, NR, D3>;
+  auto kern = pairsum_kernel<R, NMAX, OP, NR, D3>;
   if (S::SMEM > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, S::SMEM));
   const int op = OP == 1 ? 1 : 0;
-  const PsReal<R>* zv = std::is_same_v<R, float> ? (const PsReal<R>*)a.tab->d_zval_f32[op]
-                                                 : (const PsReal<R>*)a.tab->d_zval_f64[op];
+  const Tables* t = a.tab;
+  const int* zs = D3 ? t->d_z3seg[op] : t->d_zseg[op];
+  const int* zi = D3 ? t->d_z3idx[op] : t->d_zidx[op];
+  const void* zv = std::is_same_v<R, float> ? (D3 ? (const void*)t->d_z3val_f32[op] : (const void*)t->d_zval_f32[op])
+                                            : (D3 ? (const void*)t->d_z3val_f64[op] : (const void*)t->d_zval_f64[op]);
   kern<<<dim3((unsigned)a.N, (unsigned)ngroups), S::THREADS, S::SMEM, ctx->stream>>>(
-      a.pos, a.N, a.k, (const G<R>*)a.T, a.row_ptr, a.col, (const G<R>*)x, (const C<R>*)xg, (G<R>*)y, stride,
-      a.tab->d_zseg[op], a.tab->d_zidx[op], zv, a.cutoff, a.taper, a.taper > 0 ? 1.0 / a.taper : 0.0);
+      a.pos, a.N, a.k, (const G<R>*)a.T, a.row_ptr, a.col, (const G<R>*)x, (const C<R>*)xg, (G<R>*)y, stride, zs, zi,
+      (const PsReal<R>*)zv, a.cutoff, a.taper, a.taper > 0 ? 1.0 / a.taper : 0.0);
   return TMAT_OK;
 }
 
 // nrhs right-hand sides: complex64 in blocks of two (the pair weights shared), then one
-template <typename R, int NMAX, int OP>
+template <typename R, int NMAX, int OP, bool D3>
 static int launch_rhs(tmat_ctx* ctx, const NbrOp& a, const void* x, const void* xg, void* y, int nrhs,
                       int64_t stride) {
   constexpr int NR = std::is_same_v<R, float> ? 2 : 1;
   const int ng = nrhs / NR;
-  if (ng > 0) TM_TRY((launch_pairsum<R, NMAX, OP, NR>(ctx, a, x, xg, y, ng, stride)));
+  if (ng > 0) TM_TRY((launch_pairsum<R, NMAX, OP, NR, D3>(ctx, a, x, xg, y, ng, stride)));
   if (NR == 2 && (nrhs & 1)) {
     const size_t off = sizeof(G<R>) * (size_t)stride * (nrhs - 1);
     const size_t offg = sizeof(C<R>) * (size_t)stride * (nrhs - 1);
-    TM_TRY((launch_pairsum<R, NMAX, OP, 1>(ctx, a, (const char*)x + off, (const char*)xg + offg, (char*)y + off, 1,
-                                           stride)));
+    TM_TRY((launch_pairsum<R, NMAX, OP, 1, D3>(ctx, a, (const char*)x + off, (const char*)xg + offg, (char*)y + off,
+                                               1, stride)));
   }
   return TMAT_OK;
 }
@@ -369,164 +428,33 @@ static int dispatch_nmax(tmat_ctx* ctx, const NbrOp& a, const void* x, void* y, 
     xg = xt;
   }
   int rc;
-  switch (a.nmax) {
-    case 1: rc = launch_rhs<R, 1, OP>(ctx, a, x, xg, y, nrhs, stride); break;
-    case 2: rc = launch_rhs<R, 2, OP>(ctx, a, x, xg, y, nrhs, stride); break;
-    case 3: rc = launch_rhs<R, 3, OP>(ctx, a, x, xg, y, nrhs, stride); break;
-    case 4: rc = launch_rhs<R, 4, OP>(ctx, a, x, xg, y, nrhs, stride); break;
-    case 5: rc = launch_rhs<R, 5, OP>(ctx, a, x, xg, y, nrhs, stride); break;
-    case 6: rc = launch_rhs<R, 6, OP>(ctx, a, x, xg, y, nrhs, stride); break;
-    default: return set_error(ctx, TMAT_EINVAL, "nmax %d unsupported", a.nmax);
+  if (a.threed) {
+    switch (a.nmax) {
+      case 1: rc = launch_rhs<R, 1, OP, true>(ctx, a, x, xg, y, nrhs, stride); break;
+      case 2: rc = launch_rhs<R, 2, OP, true>(ctx, a, x, xg, y, nrhs, stride); break;
+      case 3: rc = launch_rhs<R, 3, OP, true>(ctx, a, x, xg, y, nrhs, stride); break;
+      case 4: rc = launch_rhs<R, 4, OP, true>(ctx, a, x, xg, y, nrhs, stride); break;
+      case 5: rc = launch_rhs<R, 5, OP, true>(ctx, a, x, xg, y, nrhs, stride); break;
+      default: return set_error(ctx, TMAT_ENOTSUP, "non-coplanar positions: nmax %d above 5", a.nmax);
+    }
+  } else {
+    switch (a.nmax) {
+      case 1: rc = launch_rhs<R, 1, OP, false>(ctx, a, x, xg, y, nrhs, stride); break;
+      case 2: rc = launch_rhs<R, 2, OP, false>(ctx, a, x, xg, y, nrhs, stride); break;
+      case 3: rc = launch_rhs<R, 3, OP, false>(ctx, a, x, xg, y, nrhs, stride); break;
+      case 4: rc = launch_rhs<R, 4, OP, false>(ctx, a, x, xg, y, nrhs, stride); break;
+      case 5: rc = launch_rhs<R, 5, OP, false>(ctx, a, x, xg, y, nrhs, stride); break;
+      case 6: rc = launch_rhs<R, 6, OP, false>(ctx, a, x, xg, y, nrhs, stride); break;
+      default: return set_error(ctx, TMAT_EINVAL, "nmax %d unsupported", a.nmax);
+    }
   }
   if (rc) return rc;
   TM_LAUNCHED(ctx);
-  timing_end(ctx, std::is_same_v<R, float> ? "nbr_apply_fp32" : "nbr_apply_fp64", ev);
+  timing_end(ctx, a.threed ? "nbr_apply3d" : std::is_same_v<R, float> ? "nbr_apply_fp32" : "nbr_apply_fp64", ev);
   return TMAT_OK;
 }
 
 constexpr int MAXR = 4;  // right-hand sides per launch
-
-// ---- general 3-D positions ------------------------------------------------------
-// Without a common plane the blocks do not split into parity classes. The block of pair
-// (i, j) is formed in full from the 3-D coupling constants: xi(k d) with
-//   alpha[n][n'] (= xi[n][n'] = xi[L+n][L+n']) = e^{i mu phi} sum_q a5[n][n'][q] h_q(k r) Pbar_q^{|mu|}(cos theta),
-//   beta[n][n']  (= xi[n][L+n'] = xi[L+n][n'])  the same with b5, mu = m - m',
-// and applied as (A x)_i = sum_j xi(k(x_i - x_j))^T x_j (forward) or
-// (A^T z)_i = sum_j xi(k(x_j - x_i)) z_j (adjoint). One block of threads per target;
-// block entries in fp64, vectors in the operator's precision.
-constexpr int NBR3_THREADS = 128;
-template <typename R, int NMAX, int OP>
-__global__ void __launch_bounds__(NBR3_THREADS)
-apply_nbr3d_kernel(const double* __restrict__ pos, int64_t N, double k, const C<R>* __restrict__ T,
-                   const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                   const C<R>* __restrict__ x, C<R>* __restrict__ y, int nrhs, int64_t rhs_stride,
-                   const double2* __restrict__ a5, const double2* __restrict__ b5, const int* __restrict__ perm,
-                   double cutoff, double taper) {
-  constexpr int L = NMAX * (NMAX + 2), P = 2 * L, Q = 2 * NMAX + 1;
-  static_assert(P <= NBR3_THREADS, "one output per thread");
-  __shared__ double2 al[L * L], be[L * L];
-  __shared__ double2 h[Q];
-  __shared__ double Pq[Q][Q];
-  __shared__ double2 eph[2 * Q - 1];
-  __shared__ double2 xs[MAXR][P];  // source coefficients in flat order
-  const int64_t i = blockIdx.x;
-  if (i >= N) return;
-  const int tid = threadIdx.x;
-  const int fo = tid < P ? perm[tid] : 0;  // flat index of this thread's output (internal index tid)
-  const int po = fo / L, no = fo % L;
-  double2 acc[MAXR];
-#pragma unroll
-  for (int r = 0; r < MAXR; ++r) acc[r] = make_double2(0, 0);
-  const int64_t jb = row_ptr[i], je = row_ptr[i + 1];
-  for (int64_t e = jb; e < je; ++e) {
-    const int64_t j = col[e];
-    const double sg = OP == 1 ? -1.0 : 1.0;  // adjoint: d = x_j - x_i
-    const double dx = sg * (pos[3 * i] - pos[3 * j]), dy = sg * (pos[3 * i + 1] - pos[3 * j + 1]),
-                 dz = sg * (pos[3 * i + 2] - pos[3 * j + 2]);
-    const double r = sqrt(dx * dx + dy * dy + dz * dz);
-    const double ct = dz / r, st = sqrt(fmax(0.0, 1.0 - ct * ct));
-    const double rho = sqrt(dx * dx + dy * dy);
-    const double cp = rho > 0 ? dx / rho : 1.0, sp = rho > 0 ? dy / rho : 0.0;
-    const double w = taper_weight(r, cutoff, taper);
-    if (tid == 0) {
-      double2 hh[Q];
-      hankel_up<double, Q>(k * r, hh);
-      for (int q = 0; q < Q; ++q) h[q] = cscale(hh[q], w);
-      double2 ee = make_double2(1, 0), e1 = make_double2(cp, sp);
-      for (int mu = 0; mu < Q; ++mu) {
-        eph[Q - 1 + mu] = ee;
-        eph[Q - 1 - mu] = cconj(ee);
-        ee = cmul(ee, e1);
-      }
-    }
-    if (tid < Q) {  // Pbar_q^mu(cos theta), mu = tid, upward in q
-      const int mu = tid;
-      double df = 1.0, f2 = 1.0;
-      for (int t = 1; t < 2 * mu; t += 2) df *= t;
-      for (int t = 2; t <= 2 * mu; ++t) f2 *= t;
-      double pprev = 0.0, pcur = sqrt((2 * mu + 1) / (2.0 * f2)) * df * pow(st, (double)mu);
-      for (int q = 0; q < mu; ++q) Pq[q][mu] = 0.0;
-      Pq[mu][mu] = pcur;
-      for (int q = mu + 1; q < Q; ++q) {
-        const double a = sqrt((4.0 * q * q - 1) / ((double)q * q - (double)mu * mu));
-        const double b = sqrt(((q - 1.0) * (q - 1.0) - (double)mu * mu) / (4.0 * (q - 1.0) * (q - 1.0) - 1));
-        const double pn = a * (ct * pcur - b * pprev);
-        pprev = pcur;
-        pcur = pn;
-        Pq[q][mu] = pn;
-      }
-    }
-    for (int t = tid; t < nrhs * P; t += NBR3_THREADS) {
-      const int rr = t / P, u = t % P;
-      C<R> v = x[rr * rhs_stride + j * P + u];
-      if (OP == 1) v = cmul(v, T[j * P + u]);
-      xs[rr][perm[u]] = make_double2((double)v.x, (double)v.y);
-    }
-    __syncthreads();
-    for (int t = tid; t < L * L; t += NBR3_THREADS) {
-      const int n = t / L, np = t % L;
-      int l = 1, lp = 1;
-      while ((l + 1) * (l + 1) - 1 <= n) ++l;
-      while ((lp + 1) * (lp + 1) - 1 <= np) ++lp;
-      const int m = n + 1 - l * (l + 1), mp = np + 1 - lp * (lp + 1);
-      const int mu = m - mp, amu = abs(mu);
-      double2 a_ = make_double2(0, 0), b_ = make_double2(0, 0);
-      for (int q = abs(l - lp); q <= l + lp; ++q) {
-        if (amu > q) continue;
-        const double2 hp = cscale(h[q], Pq[q][amu]);
-        cfma(a_, a5[((size_t)n * L + np) * Q + q], hp);
-        cfma(b_, b5[((size_t)n * L + np) * Q + q], hp);
-      }
-      al[t] = cmul(a_, eph[Q - 1 + mu]);
-      be[t] = cmul(b_, eph[Q - 1 + mu]);
-    }
-    __syncthreads();
-    if (tid < P) {
-      for (int np = 0; np < L; ++np) {
-        // forward: xi^T, entry (f', f) of xi; adjoint: xi, entry (f, f')
-        const double2 ga = OP == 1 ? al[no * L + np] : al[np * L + no];
-        const double2 gb = OP == 1 ? be[no * L + np] : be[np * L + no];
-        for (int rr = 0; rr < nrhs; ++rr) {
-          cfma(acc[rr], ga, xs[rr][po * L + np]);
-          cfma(acc[rr], gb, xs[rr][(1 - po) * L + np]);
-        }
-      }
-    }
-    __syncthreads();
-  }
-  if (tid < P) {
-    const int64_t o = i * P + tid;
-    for (int rr = 0; rr < nrhs; ++rr) {
-      const C<R> a = mk<R>((R)acc[rr].x, (R)acc[rr].y);
-      C<R> out;
-      if (OP == 2) out = a;
-      else if (OP == 0) out = csub(x[rr * rhs_stride + o], cmul(T[o], a));
-      else out = csub(x[rr * rhs_stride + o], a);
-      y[rr * rhs_stride + o] = out;
-    }
-  }
-}
-
-template <typename R, int OP>
-static int dispatch3d(tmat_ctx* ctx, const NbrOp& a, const void* x, void* y, int nrhs, int64_t stride) {
-  cudaEvent_t ev = timing_begin(ctx);
-  const unsigned grid = (unsigned)a.N;
-  const Tables* t = a.tab;
-#define N3(NM)                                                                                                    \
-  case NM:                                                                                                        \
-    apply_nbr3d_kernel<R, NM, OP><<<grid, NBR3_THREADS, 0, ctx->stream>>>(                                      \
-        a.pos, a.N, a.k, (const C<R>*)a.T, a.row_ptr, a.col, (const C<R>*)x, (C<R>*)y, nrhs, stride, t->d_a5, \
-        t->d_b5, t->d_perm, a.cutoff, a.taper);                                                                  \
-    break;
-  switch (a.nmax) {
-    N3(1) N3(2) N3(3) N3(4) N3(5)
-    default: return set_error(ctx, TMAT_ENOTSUP, "non-coplanar positions: nmax %d above 5", a.nmax);
-  }
-#undef N3
-  TM_LAUNCHED(ctx);
-  timing_end(ctx, "nbr_apply3d", ev);
-  return TMAT_OK;
-}
 
 // x, y: internal layout [R][N][P] in precision a.fp32 ? complex64 : complex128
 int nbr_apply(tmat_ctx* ctx, const NbrOp& a, int op, const void* x, void* y, int R_) {
@@ -538,17 +466,7 @@ int nbr_apply(tmat_ctx* ctx, const NbrOp& a, int op, const void* x, void* y, int
     const char* xp = (const char*)x + esz * stride * r0;
     char* yp = (char*)y + esz * stride * r0;
     int rc;
-    if (a.threed) {
-      if (a.fp32) {
-        if (op == TMAT_OP_FORWARD) rc = dispatch3d<float, 0>(ctx, a, xp, yp, nr, stride);
-        else if (op == TMAT_OP_ADJOINT) rc = dispatch3d<float, 1>(ctx, a, xp, yp, nr, stride);
-        else rc = dispatch3d<float, 2>(ctx, a, xp, yp, nr, stride);
-      } else {
-        if (op == TMAT_OP_FORWARD) rc = dispatch3d<double, 0>(ctx, a, xp, yp, nr, stride);
-        else if (op == TMAT_OP_ADJOINT) rc = dispatch3d<double, 1>(ctx, a, xp, yp, nr, stride);
-        else rc = dispatch3d<double, 2>(ctx, a, xp, yp, nr, stride);
-      }
-    } else if (a.fp32) {
+    if (a.fp32) {
       if (op == TMAT_OP_FORWARD) rc = dispatch_nmax<float, 0>(ctx, a, xp, yp, nr, stride);
       else if (op == TMAT_OP_ADJOINT) rc = dispatch_nmax<float, 1>(ctx, a, xp, yp, nr, stride);
       else rc = dispatch_nmax<float, 2>(ctx, a, xp, yp, nr, stride);

@@ -44,6 +44,14 @@ struct Tables {
   int* d_zidx[2] = {nullptr, nullptr};
   float* d_zval_f32[2] = {nullptr, nullptr};
   double* d_zval_f64[2] = {nullptr, nullptr};
+  // the same off the plane: every (n, n') pair of the full block, combination
+  // a = q^2 + mu + q (no class split; columns in the internal order)
+  std::vector<int> z3seg[2], z3idx[2];
+  std::vector<double> z3val[2];
+  int* d_z3seg[2] = {nullptr, nullptr};
+  int* d_z3idx[2] = {nullptr, nullptr};
+  float* d_z3val_f32[2] = {nullptr, nullptr};
+  double* d_z3val_f64[2] = {nullptr, nullptr};
   // dense planar forward coefficients G[c][u][u'][q] as complex (alpha real, beta imaginary)
   double2* d_gdense = nullptr;
   // full (3-D) coupling constants a5/b5 as complex [L][L][Q] (zero where absent)

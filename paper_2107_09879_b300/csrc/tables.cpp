@@ -210,6 +210,44 @@ static void build_host(Tables* t, int nmax, std::vector<double2>& a5, std::vecto
     }
     zseg[P] = (int)zidx.size();
   }
+  // pair-sum tables off the plane (no class split): every pair (n, n') of the full block
+  // with its 3-D coupling constant, combination a = q^2 + mu + q of the weights
+  // H[q, mu] = w h_q Pbar_q^{|mu|}(cos theta) e^{i mu phi} of d = x_i - x_j, output and
+  // column in the internal order. Forward (A x)_f = sum xi_{f' f}(d) x_f': c5(n'|n|q),
+  // mu = m' - m; adjoint (A^T z)_f = sum xi_{f f'}(-d) z_f': c5(n|n'|q) (-1)^q, mu = m - m'
+  // (H(-d)[q, mu] = (-1)^q H(d)[q, mu]); c5 = a5 for equal polarisations, b5 otherwise,
+  // each a real number times a power of i.
+  for (int op = 0; op < 2; ++op) {
+    std::vector<int>& zseg = t->z3seg[op];
+    std::vector<int>& zidx = t->z3idx[op];
+    std::vector<double>& zval = t->z3val[op];
+    zseg.assign((size_t)P + 1, 0);
+    zidx.clear();
+    zval.clear();
+    for (int o = 0; o < P; ++o) {
+      zseg[o] = (int)zidx.size();
+      const int f = t->perm[o], p = fp[f], l = fl[f], m = fm[f], n = l * (l + 1) + m - 1;
+      for (int o2 = 0; o2 < P; ++o2) {
+        const int f2 = t->perm[o2], p2 = fp[f2], l2 = fl[f2], m2 = fm[f2], n2 = l2 * (l2 + 1) + m2 - 1;
+        for (int q = std::abs(l - l2); q <= l + l2; ++q) {
+          const int mu = op == 0 ? m2 - m : m - m2;
+          if (std::abs(mu) > q) continue;
+          const size_t at = op == 0 ? ((size_t)n2 * L + n) * Q + q : ((size_t)n * L + n2) * Q + q;
+          double2 v = (p == p2) ? a5[at] : b5[at];
+          if (op == 1 && (q & 1)) {
+            v.x = -v.x;
+            v.y = -v.y;
+          }
+          if (v.x == 0.0 && v.y == 0.0) continue;
+          const bool imag = v.x == 0.0;  // a real coupling constant times 1 or i (up to sign)
+          const int a = q * q + mu + q;
+          zidx.push_back(o2 | (a << 8) | ((imag ? 1 : 0) << 16));
+          zval.push_back(imag ? v.y : v.x);
+        }
+      }
+    }
+    zseg[P] = (int)zidx.size();
+  }
 }
 
 template <typename T>
@@ -241,6 +279,11 @@ int get_tables(tmat_ctx* ctx, int nmax, Tables** out) {
       if ((rc = upload(ctx, t->zidx[op], &t->d_zidx[op]))) break;
       if ((rc = upload(ctx, vf, &t->d_zval_f32[op]))) break;
       if ((rc = upload(ctx, t->zval[op], &t->d_zval_f64[op]))) break;
+      std::vector<float> vf3(t->z3val[op].begin(), t->z3val[op].end());
+      if ((rc = upload(ctx, t->z3seg[op], &t->d_z3seg[op]))) break;
+      if ((rc = upload(ctx, t->z3idx[op], &t->d_z3idx[op]))) break;
+      if ((rc = upload(ctx, vf3, &t->d_z3val_f32[op]))) break;
+      if ((rc = upload(ctx, t->z3val[op], &t->d_z3val_f64[op]))) break;
     }
     if (rc) break;
     {
@@ -277,6 +320,10 @@ void free_tables(Tables* t) {
     cudaFree(t->d_zidx[op]);
     cudaFree(t->d_zval_f32[op]);
     cudaFree(t->d_zval_f64[op]);
+    cudaFree(t->d_z3seg[op]);
+    cudaFree(t->d_z3idx[op]);
+    cudaFree(t->d_z3val_f32[op]);
+    cudaFree(t->d_z3val_f64[op]);
   }
   cudaFree(t->d_gdense);
   cudaFree(t->d_a5);
