@@ -716,15 +716,18 @@ def bench_every_pair(ctx, torch, steps=2):
                     "512 x 512 grid; same step as the headline (build, incident, solve, field)"}
 
 
-def bench_disordered(ctx, torch, steps=2):
+def bench_disordered(ctx, torch, steps=2, dz=0.0):
     """A disordered array on the neighbour-list path (no lattice, no FFT): 100 x 100 sites
     jittered by U[-0.1, 0.1] wavelengths, radii U[0.08, 0.14] (enclosing spheres apart),
     nmax 4, cutoff 8 with the raised-cosine window, two incidences (normal and 5 degrees,
     x-polarised), mixed precision to 1e-7. The apply is the pair sum: per target the dense
-    product Z = H X on CUDA cores (fp32 inner, double-float refinement residuals)."""
+    product Z = H X on CUDA cores (fp32 inner, double-float refinement residuals). dz > 0:
+    every site also lifted by U[-dz, dz] (no common plane: the 3-D weights and tables)."""
     from paper_2107_09879_b300 import _lib
     n, nmax, cut = 100, 4, 8.0
     pos_h = W.jittered_lattice(n, n, 0.1, W.BASE_SEED + 13)
+    if dz > 0:
+        pos_h[:, 2] = dz * (2.0 * W.uniform_radii(n * n, 0.0, 1.0, W.BASE_SEED + 15) - 1.0)
     a = np.zeros((n * n, 3))
     a[:, 0] = W.uniform_radii(n * n, 0.08, 0.14, W.BASE_SEED + 14)
     a[:, 1] = 2.0
@@ -744,33 +747,35 @@ def bench_disordered(ctx, torch, steps=2):
         return rc
     one()
     ctx.set_timing(True)
-    n32a, t32a = ctx.kernel_time("nbr_apply_fp32")
-    n64a, t64a = ctx.kernel_time("nbr_apply_fp64")
+    k32, k64 = ("nbr_apply3d_fp32", "nbr_apply3d_fp64") if dz > 0 else ("nbr_apply_fp32", "nbr_apply_fp64")
+    n32a, t32a = ctx.kernel_time(k32)
+    n64a, t64a = ctx.kernel_time(k64)
     times = [_wall(one, torch.cuda.synchronize)[0] for _ in range(steps)]
-    n32b, t32b = ctx.kernel_time("nbr_apply_fp32")
-    n64b, t64b = ctx.kernel_time("nbr_apply_fp64")
+    n32b, t32b = ctx.kernel_time(k32)
+    n64b, t64b = ctx.kernel_time(k64)
     rp, col = ctx.tmat_neighbors(pos, cut)
     pairs = int(col.numel())
     info = rec[-1]
     ms32 = (t32b - t32a) / max(1, n32b - n32a)
     ms64 = (t64b - t64a) / max(1, n64b - n64a)
-    nqm, P, R = 45, 48, 2
+    nqm, P, R = (81 if dz > 0 else 45), 48, 2
     flop = 8.0 * nqm * P * pairs * R  # complex MACs of Z = H X (the dominant part of the kernel)
-    return {"workload": "disordered_100x100_jitter0.1_nmax4_cutoff8_2rhs_mixed",
+    name = f"corrugated_100x100_dz{dz:g}" if dz > 0 else "disordered_100x100"
+    return {"workload": f"{name}_jitter0.1_nmax4_cutoff8_2rhs_mixed",
             "solves_per_s": 1.0 / statistics.mean(times), "seconds_per_solve": statistics.mean(times),
             "iterations": info.iterations, "refinements": info.refinements, "converged": bool(info.converged),
             "rel_residual": max(info.rel_residual[q] for q in range(info.n_rhs)), "directed_pairs": pairs,
-            "apply_fp32": {"kernel": "pairsum_kernel<float,4,0> (apply.cu)", "launches": n32b - n32a,
-                           "avg_ms": ms32, "ns_per_pair": ms32 * 1e6 / pairs,
+            "apply_fp32": {"kernel": f"pairsum_kernel<float,4,0,2,{'true' if dz > 0 else 'false'}> (apply.cu)",
+                           "launches": n32b - n32a, "avg_ms": ms32, "ns_per_pair": ms32 * 1e6 / pairs,
                            "achieved_tflops": flop / (ms32 * 1e-3) / 1e12, "bound": "alu",
                            "peak_tflops": FMA_PEAKS.get("fp32_tflops"),
                            "frac": flop / (ms32 * 1e-3) / 1e12 / FMA_PEAKS["fp32_tflops"]
                            if FMA_PEAKS.get("fp32_tflops") else None},
-            "apply_fp64": {"kernel": "pairsum_kernel<DF,4,0> (double-float)", "launches": n64b - n64a,
+            "apply_fp64": {"kernel": "pairsum_kernel<DF,...> (double-float)", "launches": n64b - n64a,
                            "avg_ms": ms64, "ns_per_pair": ms64 * 1e6 / pairs},
-            "note": "flop: 8 x 45 x 48 per directed pair and RHS (the pair-sum product Z = H X, 45 weights "
-                    "w h_q e^{i mu phi} times the 48 coefficients); peak: measured fp32 FMA rate; one solve = "
-                    "Mie build + incident + overlap check + solve"}
+            "note": f"flop: 8 x {nqm} x 48 per directed pair and RHS (the pair-sum product Z = H X, {nqm} weights "
+                    "times the 48 coefficients); peak: measured fp32 FMA rate; one solve = Mie build + incident + "
+                    "overlap check + solve"}
 
 
 def run_ours(args, rank, world):
@@ -934,6 +939,7 @@ def run_ours(args, rank, world):
         out["sweep_1200x1200"] = bench_sweep(ctx, torch)
         out["cylinders_200x200"] = bench_cylinders(ctx, torch)
         out["disordered_100x100"] = bench_disordered(ctx, torch)
+        out["corrugated_100x100"] = bench_disordered(ctx, torch, dz=0.25)
         try:
             out["padding_study"] = bench_padding(ctx, torch)
         except Exception as exc:  # a study, not the headline: report it rather than lose the line

@@ -101,7 +101,11 @@ template <typename R, int NMAX, int NR, bool D3> struct PsShape {
   // the phases), then Xs[2][KC][NP] which Z[NQM][NP] reuses after the last chunk
   static constexpr int WSZ = KC * (HWN + Q);  // one buffer of weights
   static constexpr int PROD = 2 * KC * NP > NQM * NP ? 2 * KC * NP : NQM * NP;
-  static constexpr size_t SMEM = sizeof(C<R>) * (2 * WSZ + PROD);
+  // off the plane, after these: the Legendre recurrence factors (a, b)[q][m] and the
+  // starting values' factors c[m] in the geometry's real type
+  static constexpr size_t LEG = D3 ? sizeof(std::conditional_t<std::is_same_v<R, float>, float, double>) *
+                                         (size_t)(2 * Q * Q + Q) : 0;
+  static constexpr size_t SMEM = sizeof(C<R>) * (2 * WSZ + PROD) + LEG;
 };
 
 // real type of the per-pair geometry, Hankel functions and phases, and of the G factors
@@ -149,6 +153,30 @@ __device__ __forceinline__ void ps_gather_async(int tid, int nthr, int64_t c0, i
   ps_cp_async_commit();
 }
 
+// Recurrence factors of the normalised associated Legendre functions, Q orders:
+// Pbar_q^m = a (x Pbar_{q-1}^m - b Pbar_{q-2}^m), a = sqrt((4q^2-1)/(q^2-m^2)),
+// b = sqrt(((q-1)^2-m^2)/(4(q-1)^2-1)) at [2(q Q + m)], [2(q Q + m) + 1]; and
+// Pbar_m^m = c[m] sin^m theta, c[m] = sqrt((2m+1)/(2 (2m)!)) (2m-1)!! at [2 Q Q + m].
+template <typename RG, int Q>
+__device__ __forceinline__ void ps_legendre_factors(int lane, RG* leg) {
+  for (int e = lane; e < Q * Q; e += 32) {
+    const int q = e / Q, m = e - q * Q;
+    RG a = 0, b = 0;
+    if (q > m) {
+      a = sqrt((RG)(4 * q * q - 1) / (RG)(q * q - m * m));
+      b = sqrt((RG)((q - 1) * (q - 1) - m * m) / (RG)(4 * (q - 1) * (q - 1) - 1));
+    }
+    leg[2 * e] = a;
+    leg[2 * e + 1] = b;
+  }
+  for (int m = lane; m < Q; m += 32) {
+    RG df = 1, f2 = 1;
+    for (int t = 1; t < 2 * m; t += 2) df *= (RG)t;
+    for (int t = 2; t <= 2 * m; ++t) f2 *= (RG)t;
+    leg[2 * Q * Q + m] = sqrt((RG)(2 * m + 1) / ((RG)2 * f2)) * df;
+  }
+}
+
 // The weights of one chunk of a target's neighbour row, by the producer warp (lane = its
 // lane): per pair the radial weights into W[t][0..HWN) (on the plane w h_q; off the plane
 // w h_q Pbar_q^m(cos theta) at q(q+1)/2 + m, m <= q) and e^{i m phi} into
@@ -156,7 +184,8 @@ __device__ __forceinline__ void ps_gather_async(int tid, int nthr, int64_t c0, i
 template <typename R, int NMAX, int NR, bool D3>
 __device__ __forceinline__ void ps_weights(int lane, int64_t c0, int64_t je, double xi0, double yi0, double zi0,
                                            const double* __restrict__ pos, double k, const int32_t* __restrict__ col,
-                                           double cutoff, double taper, double inv_taper, C<R>* W) {
+                                           double cutoff, double taper, double inv_taper, C<R>* W,
+                                           const PsReal<R>* leg) {
   using S = PsShape<R, NMAX, NR, D3>;
   using RG = PsReal<R>;
   constexpr int Q = S::Q, KC = S::KC, HWN = S::HWN;
@@ -198,18 +227,16 @@ __device__ __forceinline__ void ps_weights(int lane, int64_t c0, int64_t je, dou
     const RG ir = (RG)1 / (RG)rho, rxy = (RG)sqrt(dx * dx + dy * dy);
     const RG ct = (RG)dz * ir, st = rxy * ir;
     e1 = rxy > (RG)0 ? mk<RG>((RG)dx / rxy, (RG)dy / rxy) : mk<RG>((RG)1, (RG)0);
-    // Pbar_q^m(cos theta), m = 0..Q-1, upward in q from Pbar_m^m
+    // Pbar_q^m(cos theta), m = 0..Q-1, upward in q from Pbar_m^m = c[m] sin^m theta with the
+    // factors of the block's table (ps_legendre_factors)
     RG smm = (RG)1;  // st^m
+#pragma unroll
     for (int m = 0; m < Q; ++m) {
-      RG df = 1, f2 = 1;
-      for (int t = 1; t < 2 * m; t += 2) df *= (RG)t;
-      for (int t = 2; t <= 2 * m; ++t) f2 *= (RG)t;
-      RG pprev = 0, pcur = sqrt((RG)(2 * m + 1) / ((RG)2 * f2)) * df * smm;
+      RG pprev = 0, pcur = leg[2 * Q * Q + m] * smm;
       hw[m * (m + 1) / 2 + m] = ps_conv<R>(cscale(h[m], wgt * pcur));
+#pragma unroll
       for (int q = m + 1; q < Q; ++q) {
-        const RG a = sqrt((RG)(4 * q * q - 1) / (RG)(q * q - m * m));
-        const RG b = sqrt((RG)((q - 1) * (q - 1) - m * m) / (RG)(4 * (q - 1) * (q - 1) - 1));
-        const RG pn = a * (ct * pcur - b * pprev);
+        const RG pn = leg[2 * (q * Q + m)] * (ct * pcur - leg[2 * (q * Q + m) + 1] * pprev);
         pprev = pcur;
         pcur = pn;
         hw[q * (q + 1) / 2 + m] = ps_conv<R>(cscale(h[q], wgt * pcur));
@@ -246,6 +273,7 @@ pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const G<R>* 
   C<R>* W = reinterpret_cast<C<R>*>(ps_smem);  // [2][KC][HWN + Q]
   C<R>* Xs = W + 2 * WSZ;                       // [2][KC][NP]
   C<R>* Z = Xs;                                 // [NQM][NP] after the last chunk
+  PsReal<R>* leg = reinterpret_cast<PsReal<R>*>(Xs + S::PROD);  // off the plane: Legendre factors
 
   const int64_t i = blockIdx.x;
   const int r0 = blockIdx.y * NR;
@@ -276,9 +304,13 @@ pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const G<R>* 
     qa[s] = D3 ? q * (q + 1) / 2 + ma[s] : q;
     na[s] = mu < 0;
   }
+  if (D3 && producer) {
+    ps_legendre_factors<PsReal<R>, Q>(lane, leg);
+    __syncwarp();
+  }
   if (nch > 0) {
     if (producer)
-      ps_weights<R, NMAX, NR, D3>(lane, jb, je, xi0, yi0, zi0, pos, k, col, cutoff, taper, inv_taper, W);
+      ps_weights<R, NMAX, NR, D3>(lane, jb, je, xi0, yi0, zi0, pos, k, col, cutoff, taper, inv_taper, W, leg);
     ps_gather_async<R, NMAX, NR, D3>(tid, S::THREADS, jb, je, col, xg, rhs_stride, r0, Xs);
   }
   ps_cp_async_wait_all();
@@ -298,7 +330,7 @@ pairsum_kernel(const double* __restrict__ pos, int64_t N, double k, const G<R>* 
       const int64_t c1 = jb + (int64_t)(c + 1) * KC;
       if (producer)
         ps_weights<R, NMAX, NR, D3>(lane, c1, je, xi0, yi0, zi0, pos, k, col, cutoff, taper, inv_taper,
-                                    W + (buf ^ 1) * WSZ);
+                                    W + (buf ^ 1) * WSZ, leg);
       ps_gather_async<R, NMAX, NR, D3>(tid, S::THREADS, c1, je, col, xg, rhs_stride, r0, Xs + (buf ^ 1) * KC * NP);
     }
     if (tile) {
@@ -450,7 +482,9 @@ static int dispatch_nmax(tmat_ctx* ctx, const NbrOp& a, const void* x, void* y, 
   }
   if (rc) return rc;
   TM_LAUNCHED(ctx);
-  timing_end(ctx, a.threed ? "nbr_apply3d" : std::is_same_v<R, float> ? "nbr_apply_fp32" : "nbr_apply_fp64", ev);
+  constexpr bool F32 = std::is_same_v<R, float>;
+  timing_end(ctx, a.threed ? (F32 ? "nbr_apply3d_fp32" : "nbr_apply3d_fp64") : (F32 ? "nbr_apply_fp32" : "nbr_apply_fp64"),
+             ev);
   return TMAT_OK;
 }
 
