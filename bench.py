@@ -1099,6 +1099,8 @@ def main():
     ap.add_argument("--launch-summary", metavar="CSV", help="summarise an ncu launch list by kernel and exit")
     ap.add_argument("--served-only", action="store_true", help="run only the served-stream workload")
     ap.add_argument("--sweep-only", action="store_true", help="run only the 1200 x 1200 sweep")
+    ap.add_argument("--disordered-only", action="store_true",
+                    help="run only the disordered and corrugated 100 x 100 neighbour-path solves")
     ap.add_argument("--window-study", action="store_true",
                     help="coupling-window study: every pair vs hard cutoff vs raised-cosine windows")
     ap.add_argument("--study-size", type=int, default=60)
@@ -1132,6 +1134,14 @@ def main():
     if args.sweep_only:
         import torch
         print(json.dumps(bench_sweep(None, torch)))
+        return
+    if args.disordered_only:
+        import torch
+        from paper_2107_09879_b300 import _lib
+        ctx = _lib.Context(0, None)
+        FMA_PEAKS["fp32_tflops"] = _lib.tmat_measure_fma_peak(0, _lib.PREC_MIXED)
+        print(json.dumps({"disordered_100x100": bench_disordered(ctx, torch),
+                          "corrugated_100x100": bench_disordered(ctx, torch, dz=0.25)}))
         return
     if args.impl == "reference":
         if world > 1 and rank != 0:

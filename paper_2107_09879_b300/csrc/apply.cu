@@ -91,7 +91,10 @@ template <typename R, int NMAX, int NR, bool D3> struct PsShape {
   static constexpr int TT = ((Cf::TR * Cf::TC + 31) / 32) * 32;  // tile threads
   static constexpr int THREADS = TT + 32;                         // + one producer warp
   // resident blocks per SM asked of the register allocator (the shared memory allows them)
-  static constexpr int MINB = THREADS > 160 || NMAX > 4 ? 1 : sizeof(C<R>) == 16 ? 2 : NR == 2 ? 3 : 4;
+  static constexpr int MINB_F = 65536 / (THREADS * 128), MINB_D = 65536 / (THREADS * 200);
+  static constexpr int MINB = (NMAX > 4 && !D3) ? 1
+                              : sizeof(C<R>) == 16 ? (MINB_D < 1 ? 1 : MINB_D > 2 ? 2 : MINB_D)
+                                                   : (MINB_F < 1 ? 1 : MINB_F > 4 ? 4 : MINB_F);
   // pairs per chunk: 32, or 16 where two buffers of gathered rows would pass 64 KB
   static constexpr int KC = 2 * 32 * NP * sizeof(C<R>) <= 64 * 1024 ? 32 : 16;
   static_assert(Cf::B * Cf::TC == NP, "column tiles cover NR * P");
@@ -227,21 +230,28 @@ __device__ __forceinline__ void ps_weights(int lane, int64_t c0, int64_t je, dou
     const RG ir = (RG)1 / (RG)rho, rxy = (RG)sqrt(dx * dx + dy * dy);
     const RG ct = (RG)dz * ir, st = rxy * ir;
     e1 = rxy > (RG)0 ? mk<RG>((RG)dx / rxy, (RG)dy / rxy) : mk<RG>((RG)1, (RG)0);
-    // Pbar_q^m(cos theta), m = 0..Q-1, upward in q from Pbar_m^m = c[m] sin^m theta with the
-    // factors of the block's table (ps_legendre_factors)
-    RG smm = (RG)1;  // st^m
+    // Pbar_q^m(cos theta) row by row in q (all m <= q), upward from Pbar_m^m = c[m] sin^m
+    // theta with the factors of the block's table (ps_legendre_factors); every index static
+    RG p1[Q], p2[Q];  // rows q - 1 and q - 2
 #pragma unroll
-    for (int m = 0; m < Q; ++m) {
-      RG pprev = 0, pcur = leg[2 * Q * Q + m] * smm;
-      hw[m * (m + 1) / 2 + m] = ps_conv<R>(cscale(h[m], wgt * pcur));
+    for (int m = 0; m < Q; ++m) p1[m] = p2[m] = (RG)0;
+    RG sq = (RG)1;  // st^q
 #pragma unroll
-      for (int q = m + 1; q < Q; ++q) {
-        const RG pn = leg[2 * (q * Q + m)] * (ct * pcur - leg[2 * (q * Q + m) + 1] * pprev);
-        pprev = pcur;
-        pcur = pn;
-        hw[q * (q + 1) / 2 + m] = ps_conv<R>(cscale(h[q], wgt * pcur));
+    for (int q = 0; q < Q; ++q) {
+      RG cur[Q];
+#pragma unroll
+      for (int m = 0; m < Q; ++m) {
+        if (m > q) continue;
+        cur[m] = m == q ? leg[2 * Q * Q + q] * sq
+                        : leg[2 * (q * Q + m)] * (ct * p1[m] - leg[2 * (q * Q + m) + 1] * p2[m]);
+        hw[q * (q + 1) / 2 + m] = ps_conv<R>(cscale(h[q], wgt * cur[m]));
       }
-      smm *= st;
+#pragma unroll
+      for (int m = 0; m < Q; ++m) {
+        p2[m] = p1[m];
+        p1[m] = m <= q ? cur[m] : (RG)0;
+      }
+      sq *= st;
     }
   } else {
     const RG ir = (RG)1 / (RG)rho;
