@@ -540,7 +540,7 @@ fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, fl
   const int tpr = (hy + NI - 1) / NI;
   const int64_t ntiles = (int64_t)hx * tpr;
   const int su = sym[c * L + u];
-  const int Ju = su & 0xffff, mpar = (su >> 16) & 1, pp = (su >> 17) & 1;
+  const int mpar = (su >> 16) & 1, pp = (su >> 17) & 1;
   if ((int64_t)blockIdx.x >= ntiles) return;  // uniform over the CTA
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar));
