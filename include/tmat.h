@@ -421,6 +421,23 @@ int tmat_sweep(tmat_ctx* ctx, const tmat_sweep_opts* sw, const tmat_atom* atoms,
                double n_bg, int nmax, const tmat_c128* src_A, int R, const tmat_solve_opts* opts,
                const double* pts, int64_t M, tmat_c128* E_out, tmat_sweep_info* info);
 
+/* ---- one forward simulation in a single call (App. I) -------------------- */
+
+/* The whole forward step of App. I for spheres: Lorenz-Mie T-matrices of atoms[N]
+ * (tmat_build), plane-wave incident coefficients of the R <= TMAT_MAX_RHS incidences
+ * dirs[R][2] = (beta, alpha) with polarisations pol[R][3] (tmat_incident_planewave),
+ * the solve (I - T A) s = T a0 with opts (tmat_solve; the mixed and fp64 paths, the
+ * lattice path when opts asks for it), and the scattered field of every incidence at
+ * pts[M][3] (tmat_field). Each pointer may be host or device memory; T, a0 and s stay
+ * on the device (context scratch) between the steps, host inputs are copied in and host
+ * outputs copied back. s_out[R][N][P] (nullable: not returned), E_out[R][M][3] (nullable
+ * when M = 0), info (nullable, host). Returns what tmat_solve returns (TMAT_ENOCONV: the
+ * outputs hold the best iterate and its field); argument errors as the four calls. */
+int tmat_forward(tmat_ctx* ctx, const double* pos, int64_t N, const tmat_atom* atoms, double wavelength,
+                 double n_bg, int nmax, const double* dirs, const tmat_c128* pol, int R,
+                 const tmat_solve_opts* opts, const double* pts, int64_t M, tmat_c128* s_out,
+                 tmat_c128* E_out, tmat_solve_info* info);
+
 /* ---- fields (App. I-C, Eq. sca_fld_concise) ------------------------------ */
 
 /* E_out[M][3] = sum_i s_i^T Phi(k(x - x_i)) at the points pts[M][3] (scattered

@@ -88,6 +88,8 @@ _SIGS = {
     "tmat_sweep": [_vp, ct.POINTER(SweepOpts), _vp, _d, _d, _int, _vp, _int, ct.POINTER(SolveOpts), _vp, _i64, _vp,
                    ct.POINTER(SweepInfo)],
     "tmat_field": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _i64, _vp],
+    "tmat_forward": [_vp, _vp, _i64, _vp, _d, _d, _int, _vp, _vp, _int, ct.POINTER(SolveOpts), _vp, _i64, _vp, _vp,
+                     ct.POINTER(SolveInfo)],
     "tmat_farfield": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _i64, _vp],
     "tmat_point_fom": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _vp, ct.POINTER(_d), _vp],
     "tmat_field_noalloc": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _i64, _vp],
@@ -296,6 +298,22 @@ class Context:
         if rc not in (OK, ENOCONV):
             self.check(rc)
         return s, info, (Solution(sol) if keep else None), rc
+
+    def tmat_forward(self, pos, atoms, wavelength, n_bg, nmax, dirs, pol, opts, pts, want_s=True, s_out=None,
+                     E_out=None):
+        """Build + incident + solve + field of every incidence in one call; returns (s or None,
+        E [R][M][3], info, rc). Outputs go to s_out / E_out when given (e.g. pinned host arrays),
+        else to new arrays in the memory space of pos."""
+        N, R, M = pos.shape[0], dirs.shape[0], pts.shape[0]
+        P = 2 * nmax * (nmax + 2)
+        s = s_out if s_out is not None else (empty_like_space(pos, (R, N, P), np.complex128) if want_s else None)
+        E = E_out if E_out is not None else empty_like_space(pos, (R, M, 3), np.complex128)
+        info = SolveInfo()
+        rc = lib.tmat_forward(self.h, ptr(pos), N, ptr(atoms), wavelength, n_bg, nmax, ptr(dirs), ptr(pol), R,
+                              ct.byref(opts), ptr(pts), M, ptr(s) if s is not None else None, ptr(E), ct.byref(info))
+        if rc not in (OK, ENOCONV):
+            self.check(rc)
+        return s, E, info, rc
 
     def tmat_sweep(self, sw, atoms, wavelength, n_bg, nmax, src_A, opts, pts, E=None):
         """src_A: (R, nx*ny, 2); E (R, M, 3) is accumulated into (zeros if None)."""

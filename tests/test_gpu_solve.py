@@ -178,3 +178,47 @@ def test_mixed_precision_near_field(nmax, height):
     E64 = ctx().tmat_field(pos, 1.0, 1.0, nmax, s, pts)
     assert rel_l2(E64, ref) <= 1e-8  # the fp64 field (pinned at 1e-12 near the array elsewhere)
     assert rel_l2(E32, E64) <= 1e-6
+
+
+@pytest.mark.parametrize("space", ["host", "device"])
+def test_forward_call_matches_the_separate_calls(space):
+    """tmat_forward (build + incident + solve + fields in one call) against the four calls, on
+    host arrays and on device tensors, and its field against the oracle's field of the
+    oracle's solution."""
+    import torch
+    from paper_2107_09879_b300 import _lib
+    nmax, cut, n = 3, 2.0, 7
+    pos = W.lattice_positions(n, 5)
+    r = W.uniform_radii(n * 5, 0.08, 0.22, 77)
+    b = math.radians(8.0)
+    dirs = np.array([[0.0, 0.0], [b, 0.0]])
+    pol = np.array([[1, 0, 0], [math.cos(b), 0, -math.sin(b)]], complex)
+    pts = np.array([[1.0, 0.7, 2.0], [2.2, 1.1, 4.0], [0.3, 2.0, 9.0]])
+    opts = _lib.make_opts(tol=1e-11, restart=80, max_iter=2000, cutoff=cut, taper=cut, precision=_lib.PREC_FP64)
+    args = [pos, atoms(r), dirs, pol, pts]
+    if space == "device":
+        args = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in args]
+    s, E, info, rc = ctx().tmat_forward(args[0], args[1], 1.0, 1.0, nmax, args[2], args[3], opts, args[4])
+    assert rc == 0 and info.converged
+    if space == "device":
+        s, E = s.cpu().numpy(), E.cpu().numpy()
+    T = ctx().tmat_build(atoms(r), 1.0, 1.0, nmax)
+    a0 = ctx().tmat_incident_planewave(pos, 1.0, 1.0, nmax, dirs, pol)
+    s2, _, _, rc2 = ctx().tmat_solve(pos, 1.0, 1.0, nmax, T, a0, opts)
+    assert rc2 == 0 and rel_l2(s, s2) <= 1e-12
+    for q in range(2):
+        assert rel_l2(E[q], ctx().tmat_field(pos, 1.0, 1.0, nmax, s2[q], pts)) <= 1e-12
+    To = np.array([mie.tmatrix_diag(nmax, K0, x, 2.0) for x in r])
+    a0o = incident.planewave_incident(nmax, K0, pos, b, 0.0, incident.beta_hat(b, 0.0))
+    with system.window(cut, cut):
+        so = system.solve_dense(nmax, K0, pos, To, a0o, cut)
+    assert rel_l2(E[1], field.scattered_field(nmax, K0, pos, so, pts)) <= 1e-9
+
+
+def test_forward_call_argument_errors():
+    from paper_2107_09879_b300 import _lib
+    pos = W.lattice_positions(2, 2)
+    opts = _lib.make_opts(tol=1e-8, precision=_lib.PREC_FP64)
+    with pytest.raises(_lib.TMatError):
+        ctx().tmat_forward(pos, atoms(np.full(4, 0.1)), 1.0, 1.0, 9, np.zeros((1, 2)), np.ones((1, 3), complex), opts,
+                           np.ones((1, 3)))
