@@ -164,6 +164,12 @@ int tmat_ctx_set_lattice_fft(tmat_ctx* ctx, int enable);
  * Far-field amplitudes stay fp64. Timing kinds: "field64", "field32", "farfield". */
 int tmat_ctx_set_field_precision(tmat_ctx* ctx, int precision);
 
+/* Mixed-precision solves: inner complex64 GMRES solves whose tolerance is >= 1e-2 keep
+ * their final Krylov vectors as fp16 pairs scaled by sqrt(n) (half the basis traffic; the
+ * arithmetic stays fp32 and every refinement step is closed by the fp64-accurate residual),
+ * enable = 1 (default); 0 keeps every basis in complex64. */
+int tmat_ctx_set_compressed_basis(tmat_ctx* ctx, int enable);
+
 /* Complex64 lattice applies run on the tcgen05 tensor cores (3xTF32, nmax <= 4)
  * unless disabled here (enable = 0: the CUDA-core fp32 kernel runs, and the mixed
  * refinement residual uses the fp64 CUDA-core kernel). enable = 1

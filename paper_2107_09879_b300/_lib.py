@@ -100,6 +100,7 @@ _SIGS = {
     "tmat_solve_batch": [_vp, _vp, _int, _d, _int, _d, _int, _int, ct.POINTER(SolveOpts), _vp],
     "tmat_ctx_memory": [_vp, ct.POINTER(_i64)],
     "tmat_ctx_set_field_precision": [_vp, _int],
+    "tmat_ctx_set_compressed_basis": [_vp, _int],
     "tmat_build_cylinder": [_vp, _vp, _i64, _d, _d, _int, _int, _vp, _vp],
     "tmat_solve_tblocks": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp, _i64, _vp, _int, ct.POINTER(SolveOpts), _vp,
                            ct.POINTER(_vp), ct.POINTER(SolveInfo)],
@@ -167,6 +168,10 @@ class Context:
 
     def set_stream(self, stream):
         self.check(lib.tmat_ctx_set_stream(self.h, stream))
+
+    def set_compressed_basis(self, on):
+        """Loose inner solves (tolerance >= 1e-2) keep their final Krylov vectors in scaled fp16."""
+        self.check(lib.tmat_ctx_set_compressed_basis(self.h, 1 if on else 0))
 
     def set_field_precision(self, precision):
         """PREC_FP64 (default) or PREC_MIXED: near fields in fp32 with fp64 phases."""

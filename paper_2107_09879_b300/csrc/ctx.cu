@@ -234,6 +234,12 @@ extern "C" int tmat_ctx_memory(const tmat_ctx* ctx, int64_t* bytes_out) {
   return TMAT_OK;
 }
 
+extern "C" int tmat_ctx_set_compressed_basis(tmat_ctx* ctx, int enable) {
+  if (!ctx) return TMAT_EINVAL;
+  ctx->compress_basis = enable != 0;
+  return TMAT_OK;
+}
+
 extern "C" int tmat_ctx_set_field_precision(tmat_ctx* ctx, int precision) {
   if (!ctx) return TMAT_EINVAL;
   if (precision != TMAT_PREC_FP64 && precision != TMAT_PREC_MIXED)

@@ -7,6 +7,8 @@
 #include <chrono>
 #include <cmath>
 
+#include <cuda_fp16.h>
+
 #include "dev.cuh"
 #include "solver.h"
 
@@ -678,6 +680,213 @@ dcgs2_update_kernel(float2* __restrict__ V, int64_t vstride, int j, GState s, in
   }
 }
 
+
+// ---- compressed basis: final vectors stored as scaled fp16 --------------------------
+// For loose inner solves (tolerance >= 1e-2; every refinement step is closed by an
+// fp64-accurate residual) the final basis vectors v_0..v_{j-1} are stored as fp16 pairs
+// of sqrt(n) v (unit vectors: every scaled element stays below sqrt(n) < 65504, the
+// rounding is ~5e-4 relative), halving the basis traffic of the Arnoldi passes; the
+// pending vector and the operator's output stay in two fp32 slots, the arithmetic in fp32
+// (the compressed-basis GMRES of Aliaga, Anzt et al., Concurr. Comput. 2022). The scale
+// 1/sqrt(n) is folded into the dot products and into the update coefficients.
+__device__ __forceinline__ float4 h16_load2(const uint2* __restrict__ p, int64_t i) {
+  const uint2 u = p[i];
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ uint2 h16_pack2(float4 v) {
+  const __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+  uint2 u;
+  u.x = *reinterpret_cast<const unsigned*>(&a);
+  u.y = *reinterpret_cast<const unsigned*>(&b);
+  return u;
+}
+
+// Dot-pass shape on the compressed basis (measured on a B300 for 2 RHS of 1.92 M values and
+// j = 2..30: two vectors per warp, four blocks per SM, the element loop unrolled by two and
+// ~64 warps per SM in all reach 3.2-4.7 TB/s, against 1.3-2.9 TB/s for eight vectors per
+// warp at two blocks per SM): short warps with few streams keep more loads in flight.
+constexpr int D16_VPW = 2;
+struct Dots16Plan {
+  int ranges, blocks;
+};
+static inline Dots16Plan dots16_plan(int64_t n, int gh, int num_sms, int R) {
+  Dots16Plan p;
+  const int64_t target = (int64_t)num_sms * 64 / std::max(1, R);  // warps per RHS
+  int64_t nr = cdiv(target, (int64_t)gh + 1);
+  nr = std::min<int64_t>(nr, std::max<int64_t>(1, cdiv(n / 2, (int64_t)32 * 16)));
+  p.ranges = (int)std::max<int64_t>(1, std::min<int64_t>(nr, D32_NBMAX));
+  p.blocks = (int)cdiv(((int64_t)gh + 1) * p.ranges, 8);
+  return p;
+}
+
+// Dot pass of iteration j on the compressed basis: units of D16_VPW fp16 vectors of
+// Vh[0..nh) (groups gh) and one unit group for the pending fp32 vector u (index nh),
+// against the targets u and (TWO) w; partials as dots32_kernel, scaled back by inv_sc.
+template <bool TWO>
+__global__ void __launch_bounds__(256, 4)
+dots16_kernel(const uint2* __restrict__ Vh, int64_t hstride, int nh, const float2* __restrict__ u, int64_t n,
+              int64_t rstride, double2* __restrict__ part, int maxv, int gh, int ranges, const int* __restrict__ active,
+              float inv_sc, const float2* __restrict__ w2 = nullptr, double2* __restrict__ part2 = nullptr) {
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t unit = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (unit >= (int64_t)(gh + 1) * ranges) return;
+  const int g = (int)(unit / ranges), b = (int)(unit % ranges);
+  const bool pend = g == gh;  // the pending fp32 vector
+  const int kb = pend ? nh : g * D16_VPW;
+  const int nq = pend ? 1 : min(D16_VPW, nh - kb);
+  const int64_t n2 = n >> 1;
+  const int64_t per = ((n2 + ranges - 1) / ranges + 31) / 32 * 32;
+  const int64_t lo = (int64_t)b * per, hi = lo + per < n2 ? lo + per : n2;
+  const float4* u4 = reinterpret_cast<const float4*>(u + r * rstride);
+  const float4* w24 = TWO ? reinterpret_cast<const float4*>(w2 + r * rstride) : nullptr;
+  const uint2* h4[D16_VPW];
+#pragma unroll
+  for (int q = 0; q < D16_VPW; ++q) {
+    const int k = q < nq ? kb + q : kb;  // unused slots read a valid vector
+    h4[q] = reinterpret_cast<const uint2*>(Vh + ((int64_t)(pend ? 0 : k) * hstride + r * rstride) / 2);
+  }
+  float2 acc[D16_VPW], acc2[TWO ? D16_VPW : 1];
+#pragma unroll
+  for (int q = 0; q < D16_VPW; ++q) acc[q] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < (TWO ? D16_VPW : 1); ++q) acc2[q] = make_float2(0.f, 0.f);
+#pragma unroll 2
+  for (int64_t i = lo + lane; i < hi; i += 32) {
+    const float4 wv = u4[i];
+    float4 wv2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (TWO) wv2 = w24[i];
+    float4 v[D16_VPW];
+    if (pend) {
+      v[0] = wv;
+#pragma unroll
+      for (int q = 1; q < D16_VPW; ++q) v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+#pragma unroll
+      for (int q = 0; q < D16_VPW; ++q) v[q] = h16_load2(h4[q], i);
+    }
+#pragma unroll
+    for (int q = 0; q < D16_VPW; ++q) {
+      acc[q].x = fmaf(v[q].x, wv.x, fmaf(v[q].y, wv.y, fmaf(v[q].z, wv.z, fmaf(v[q].w, wv.w, acc[q].x))));
+      acc[q].y = fmaf(v[q].x, wv.y, fmaf(-v[q].y, wv.x, fmaf(v[q].z, wv.w, fmaf(-v[q].w, wv.z, acc[q].y))));
+      if (TWO) {
+        acc2[q].x = fmaf(v[q].x, wv2.x, fmaf(v[q].y, wv2.y, fmaf(v[q].z, wv2.z, fmaf(v[q].w, wv2.w, acc2[q].x))));
+        acc2[q].y = fmaf(v[q].x, wv2.y, fmaf(-v[q].y, wv2.x, fmaf(v[q].z, wv2.w, fmaf(-v[q].w, wv2.z, acc2[q].y))));
+      }
+    }
+  }
+  const float sc = pend ? 1.0f : inv_sc;
+#pragma unroll
+  for (int q = 0; q < D16_VPW; ++q) {
+    float2 v = acc[q];
+    for (int o = 16; o > 0; o >>= 1) {
+      v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+      v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+    }
+    if (lane == 0 && q < nq) part[((int64_t)r * maxv + kb + q) * ranges + b] = make_double2(sc * v.x, sc * v.y);
+    if (TWO) {
+      float2 v2 = acc2[q];
+      for (int o = 16; o > 0; o >>= 1) {
+        v2.x += __shfl_down_sync(0xffffffffu, v2.x, o);
+        v2.y += __shfl_down_sync(0xffffffffu, v2.y, o);
+      }
+      if (lane == 0 && q < nq) part2[((int64_t)r * maxv + kb + q) * ranges + b] = make_double2(sc * v2.x, sc * v2.y);
+    }
+  }
+}
+
+// Update pass of iteration j on the compressed basis (see dcgs2_update_kernel): the final
+// v_j = selfA u - sum_{k<j} V_k cA_k (j = 0: v_0 = u) goes to Vh[j] as fp16 of sc v_j, and
+// w <- selfB w - sum_{k<j} V_k cB_k - u cB_j, with V_k = Vh_k / sc.
+__global__ void __launch_bounds__(256)
+dcgs2_update16_kernel(uint2* __restrict__ Vh, int64_t hstride, int j, GState s, int maxv,
+                      const float2* __restrict__ u, float2* __restrict__ w, int64_t n, int64_t rstride, float sc) {
+  const int r = blockIdx.y;
+  if (!s.active[r]) return;
+  extern __shared__ float2 dcs[];  // cA[0..j) / sc, cB[0..j) / sc, cB[j]
+  float2* cA = dcs;
+  float2* cB = dcs + j + 1;
+  const float inv_sc = 1.0f / sc;
+  for (int k = threadIdx.x; k <= j; k += blockDim.x) {
+    const float2 a = k < j ? s.cA[(int64_t)r * maxv + k] : make_float2(0.f, 0.f);
+    const float2 c = s.cB[(int64_t)r * maxv + k];
+    const float f = k < j ? inv_sc : 1.0f;
+    cA[k] = make_float2(a.x * inv_sc, a.y * inv_sc);
+    cB[k] = make_float2(c.x * f, c.y * f);
+  }
+  __syncthreads();
+  const float sA = s.selfA[r], sB = s.selfB[r];
+  const int64_t n2 = n >> 1;
+  const float4* u4 = reinterpret_cast<const float4*>(u + r * rstride);
+  float4* w4 = reinterpret_cast<float4*>(w + r * rstride);
+  uint2* vj = Vh + ((int64_t)j * hstride + r * rstride) / 2;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), bsum = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; k < j; ++k) {
+      const float4 v = h16_load2(Vh + ((int64_t)k * hstride + r * rstride) / 2, i);
+      const float2 cb = cB[k];
+      bsum.x = fmaf(v.x, cb.x, fmaf(-v.y, cb.y, bsum.x));
+      bsum.y = fmaf(v.x, cb.y, fmaf(v.y, cb.x, bsum.y));
+      bsum.z = fmaf(v.z, cb.x, fmaf(-v.w, cb.y, bsum.z));
+      bsum.w = fmaf(v.z, cb.y, fmaf(v.w, cb.x, bsum.w));
+      const float2 ca = cA[k];
+      a.x = fmaf(v.x, ca.x, fmaf(-v.y, ca.y, a.x));
+      a.y = fmaf(v.x, ca.y, fmaf(v.y, ca.x, a.y));
+      a.z = fmaf(v.z, ca.x, fmaf(-v.w, ca.y, a.z));
+      a.w = fmaf(v.z, ca.y, fmaf(v.w, ca.x, a.w));
+    }
+    const float4 uv = u4[i];
+    {
+      const float2 cb = cB[j];
+      bsum.x = fmaf(uv.x, cb.x, fmaf(-uv.y, cb.y, bsum.x));
+      bsum.y = fmaf(uv.x, cb.y, fmaf(uv.y, cb.x, bsum.y));
+      bsum.z = fmaf(uv.z, cb.x, fmaf(-uv.w, cb.y, bsum.z));
+      bsum.w = fmaf(uv.z, cb.y, fmaf(uv.w, cb.x, bsum.w));
+    }
+    const float4 wv = w4[i];
+    w4[i] = make_float4(sB * wv.x - bsum.x, sB * wv.y - bsum.y, sB * wv.z - bsum.z, sB * wv.w - bsum.w);
+    const float4 fin = j > 0 ? make_float4(sA * uv.x - a.x, sA * uv.y - a.y, sA * uv.z - a.z, sA * uv.w - a.w) : uv;
+    vj[i] = h16_pack2(make_float4(sc * fin.x, sc * fin.y, sc * fin.z, sc * fin.w));
+  }
+}
+
+// x[r] += sum_{k < ncols[r]} V_k coef[r][k] on the compressed basis (V_k = Vh_k / sc)
+__global__ void __launch_bounds__(256)
+xupdate16_kernel(const uint2* __restrict__ Vh, int64_t hstride, int nvec, const double2* __restrict__ coef, int maxv,
+                 double2* __restrict__ x, int64_t n, int64_t rstride, const int* __restrict__ ncols, float inv_sc) {
+  const int r = blockIdx.y;
+  const int nv = ncols ? min(nvec, ncols[r]) : nvec;
+  extern __shared__ float2 xcs[];
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+    const double2 c = coef[r * maxv + k];
+    xcs[k] = make_float2((float)c.x * inv_sc, (float)c.y * inv_sc);
+  }
+  __syncthreads();
+  const int64_t n2 = n >> 1;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; k < nv; ++k) {
+      const float4 v = h16_load2(Vh + ((int64_t)k * hstride + r * rstride) / 2, i);
+      const float2 c = xcs[k];
+      a.x = fmaf(v.x, c.x, fmaf(-v.y, c.y, a.x));
+      a.y = fmaf(v.x, c.y, fmaf(v.y, c.x, a.y));
+      a.z = fmaf(v.z, c.x, fmaf(-v.w, c.y, a.z));
+      a.w = fmaf(v.z, c.y, fmaf(v.w, c.x, a.w));
+    }
+    double2* xo = x + r * rstride + 2 * i;
+    double2 o0 = xo[0], o1 = xo[1];
+    o0.x += a.x;
+    o0.y += a.y;
+    o1.x += a.z;
+    o1.y += a.w;
+    xo[0] = o0;
+    xo[1] = o1;
+  }
+}
+
 // back substitution y = H^{-1} g over the first ncols columns
 __global__ void lsq_kernel(GState s, int R, int m, int maxv) {
   // one block per RHS, column-oriented back substitution: y_k = b_k / H_kk, then
@@ -754,8 +963,15 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
   const int maxv = m + 1;
   const int64_t rs = n;  // RHS stride
   const int nb = (int)std::min<int64_t>(cdiv(n, RED_THREADS), (int64_t)ctx->num_sms * 4);
+  // compressed basis (complex64 operator, loose tolerance): two fp32 slots (the pending
+  // vector and the operator's output) and maxv fp16 slots for the final vectors
+  const bool h16 = sizeof(VR) == 4 && p.compress_basis;
   C<VR>* V;
-  TM_TRY(scratch(ctx, sizeof(VR) == 4 ? "g_V32" : "g_V64", sizeof(C<VR>) * (size_t)maxv * R * n, (void**)&V));
+  TM_TRY(scratch(ctx, sizeof(VR) == 4 ? "g_V32" : "g_V64", sizeof(C<VR>) * (size_t)(h16 ? 2 : maxv) * R * n,
+                 (void**)&V));
+  uint2* Vh = nullptr;
+  if (h16) TM_TRY(scratch(ctx, "g_V16", sizeof(uint2) / 2 * (size_t)maxv * R * n, (void**)&Vh));
+  const float h16_sc = (float)std::sqrt((double)n), h16_inv = 1.0f / h16_sc;
   C<VR>* xv;  // x in operator precision (for the true residual)
   TM_TRY(scratch(ctx, sizeof(VR) == 4 ? "g_xv32" : "g_xv64", sizeof(C<VR>) * (size_t)R * n, (void**)&xv));
   double2* part;
@@ -839,15 +1055,28 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
           TM_TRY(set_smem_limit(ctx, (const void*)dcgs2_small_kernel, gsm_bytes));
         for (;; ++j) {
           const bool final_only = j == m || st->iterations >= p.max_iter;
-          float2* vj = V32 + (int64_t)j * R * n;
-          float2* w = final_only ? nullptr : V32 + (int64_t)(j + 1) * R * n;
+          float2* vj = V32 + (int64_t)(h16 ? (j & 1) : j) * R * n;
+          float2* w = final_only ? nullptr : V32 + (int64_t)(h16 ? ((j + 1) & 1) : j + 1) * R * n;
           if (!final_only) {
             TM_TRY(op_apply(ctx, A, mode, vj, w, R));
             st->iterations++;
           }
-          const Dots32Plan dp = dots32_plan(n, j + 1, ctx->num_sms, R);
+          const int gh = (j + D16_VPW - 1) / D16_VPW;  // fp16 vector groups (compressed basis)
+          Dots32Plan dp = dots32_plan(n, j + 1, ctx->num_sms, R);
+          if (h16) {
+            const Dots16Plan hp = dots16_plan(n, gh, ctx->num_sms, R);
+            dp.ranges = hp.ranges;
+            dp.blocks = hp.blocks;
+          }
           cudaEvent_t ev_d = timing_begin(ctx);
-          if (final_only) {
+          if (h16) {
+            if (final_only)
+              dots16_kernel<false><<<dim3(dp.blocks, R), 256, 0, ctx->stream>>>(
+                  Vh, (int64_t)R * n, j, vj, n, rs, part, maxv, gh, dp.ranges, s.active, h16_inv);
+            else
+              dots16_kernel<true><<<dim3(dp.blocks, R), 256, 0, ctx->stream>>>(
+                  Vh, (int64_t)R * n, j, vj, n, rs, part, maxv, gh, dp.ranges, s.active, h16_inv, w, part2);
+          } else if (final_only) {
             dots32_kernel<false><<<dim3(dp.blocks, R), 256, 0, ctx->stream>>>(V32, (int64_t)R * n, j + 1, vj, n, rs,
                                                                                part, maxv, dp.groups, dp.ranges, s.active);
           } else {
@@ -856,7 +1085,9 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
           }
           TM_LAUNCHED(ctx);
           // reads the j + 1 basis slots (the pending vector is slot j) and w
-          timing_end(ctx, "arnoldi_dots32", ev_d, 8.0 * R * n * (j + 1 + (final_only ? 0 : 1)));
+          timing_end(ctx, "arnoldi_dots32", ev_d,
+                     h16 ? 4.0 * R * n * j + 8.0 * R * n * (1 + (final_only ? 0 : 1))
+                         : 8.0 * R * n * (j + 1 + (final_only ? 0 : 1)));
           launch_reduce(ctx, part, dp.ranges, j + 1, maxv, s.D1, s.active, R);
           TM_LAUNCHED(ctx);
           if (!final_only) {
@@ -875,11 +1106,18 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
           }
           if (final_only || !any) break;
           cudaEvent_t ev_u = timing_begin(ctx);
-          dcgs2_update_kernel<<<dim3(g1, R), 256, sizeof(float2) * (2 * (size_t)j + 2), ctx->stream>>>(
-              V32, (int64_t)R * n, j, s, maxv, w, n, rs);
+          if (h16) {
+            dcgs2_update16_kernel<<<dim3(g1, R), 256, sizeof(float2) * (2 * (size_t)j + 2), ctx->stream>>>(
+                Vh, (int64_t)R * n, j, s, maxv, vj, w, n, rs, h16_sc);
+          } else {
+            dcgs2_update_kernel<<<dim3(g1, R), 256, sizeof(float2) * (2 * (size_t)j + 2), ctx->stream>>>(
+                V32, (int64_t)R * n, j, s, maxv, w, n, rs);
+          }
           TM_LAUNCHED(ctx);
-          // reads slots 0..j and w, writes slot j (j > 0) and w
-          timing_end(ctx, "arnoldi_update32", ev_u, 8.0 * R * n * (j + 2 + (j > 0 ? 1 : 0) + 1));
+          // reads slots 0..j and w, writes slot j (j > 0) and w (compressed: fp16 slots 0..j-1,
+          // the fp32 pending vector and w; writes fp16 slot j and w)
+          timing_end(ctx, "arnoldi_update32", ev_u,
+                     h16 ? 4.0 * R * n * (j + 1) + 8.0 * R * n * 3 : 8.0 * R * n * (j + 2 + (j > 0 ? 1 : 0) + 1));
         }
         // columns 0..j-1 are final
       } else
@@ -935,8 +1173,12 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
       lsq_kernel<<<R, 128, sizeof(double2) * maxv, ctx->stream>>>(s, R, m, maxv);
       TM_LAUNCHED(ctx);
       if constexpr (sizeof(VR) == 4) {
-        xupdate32_kernel<<<dim3(g1, R), 256, sizeof(float2) * std::max(j, 1), ctx->stream>>>(
-            reinterpret_cast<const float2*>(V), (int64_t)R * n, j, s.y, maxv, x, n, rs, s.ncols);
+        if (h16)
+          xupdate16_kernel<<<dim3(g1, R), 256, sizeof(float2) * std::max(j, 1), ctx->stream>>>(
+              Vh, (int64_t)R * n, j, s.y, maxv, x, n, rs, s.ncols, h16_inv);
+        else
+          xupdate32_kernel<<<dim3(g1, R), 256, sizeof(float2) * std::max(j, 1), ctx->stream>>>(
+              reinterpret_cast<const float2*>(V), (int64_t)R * n, j, s.y, maxv, x, n, rs, s.ncols);
       } else {
         update_kernel<VR, double><<<dim3(g1, R), 256, 0, ctx->stream>>>(V, (int64_t)R * n, j, s.y, maxv, 1.0, x, n, rs,
                                                                         nullptr, s.ncols);
@@ -1050,6 +1292,9 @@ int solve_system(tmat_ctx* ctx, const Operator& A64, const Operator* A32, int mo
       if (halpha[r] != 0.0 && hr[r] > 0) need = std::min(need, 0.5 * p.tol * hb[r] / hr[r]);
     ip.tol = std::max(p.inner_tol, need);
     ip.max_iter = p.max_iter - st->iterations;
+    // loose inner solves keep their final basis vectors in fp16 (the fp64-accurate outer
+    // residual closes every step); tight ones in fp32
+    ip.compress_basis = ctx->compress_basis && ip.tol >= 1e-2;
     GmresStats gs;
     TM_TRY(gmres_run<float>(ctx, *A32, mode, r32, d64, R, n, ip, &gs));
     st->iterations += gs.iterations;

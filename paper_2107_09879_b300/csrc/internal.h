@@ -68,6 +68,9 @@ struct DevBuf {
 }  // namespace tmat
 
 struct tmat_ctx {
+  // mixed solves: inner solves with tolerance >= 1e-2 store the final Krylov vectors as
+  // scaled fp16 (tmat_ctx_set_compressed_basis)
+  bool compress_basis = true;
   // kernel timing (off by default): event pairs recorded around operator launches
   bool timing = false;
   std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> timed;

@@ -73,6 +73,7 @@ struct GmresParams {
   double tol = 1e-6;
   int restart = 40;
   int max_iter = 2000;
+  bool compress_basis = false;  // complex64 operator: final basis vectors stored as scaled fp16
 };
 struct GmresStats {
   int iterations = 0;

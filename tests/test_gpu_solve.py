@@ -222,3 +222,33 @@ def test_forward_call_argument_errors():
     with pytest.raises(_lib.TMatError):
         ctx().tmat_forward(pos, atoms(np.full(4, 0.1)), 1.0, 1.0, 9, np.zeros((1, 2)), np.ones((1, 3), complex), opts,
                            np.ones((1, 3)))
+
+
+def test_compressed_basis_solve_matches_the_complex64_basis_and_fp64():
+    """Inner solves with a loose tolerance keep their final Krylov vectors in scaled fp16:
+    the refined solution meets the same tolerance and agrees with the complex64-basis and
+    the fp64 solves within the mixed path's bound."""
+    from paper_2107_09879_b300 import _lib
+    nmax, cut, n = 4, 4.0, 30
+    pos = W.lattice_positions(n, n)
+    r = W.uniform_radii(n * n, 0.08, 0.24, 91)
+    T = ctx().tmat_build(atoms(r), 1.0, 1.0, nmax)
+    b = math.radians(10.0)
+    a0 = ctx().tmat_incident_planewave(pos, 1.0, 1.0, nmax, np.array([[0.0, 0.0], [b, 0.0]]),
+                                       np.array([[1, 0, 0], [math.cos(b), 0, -math.sin(b)]], complex))
+    kw = dict(restart=200, max_iter=4000, cutoff=cut, taper=cut, path=_lib.PATH_LATTICE, lattice_nx=n, lattice_ny=n,
+              lattice_pitch=0.5)
+    o_mix = _lib.make_opts(tol=1e-7, precision=_lib.PREC_MIXED, inner_tol=0.2, **kw)
+    s16, i16, _, rc = ctx().tmat_solve(pos, 1.0, 1.0, nmax, T, a0, o_mix)
+    assert rc == 0 and i16.converged and max(i16.rel_residual[q] for q in range(2)) <= 1e-7
+    ctx().set_compressed_basis(False)
+    try:
+        s32, i32, _, rc = ctx().tmat_solve(pos, 1.0, 1.0, nmax, T, a0, o_mix)
+    finally:
+        ctx().set_compressed_basis(True)
+    assert rc == 0
+    s64, _, _, rc = ctx().tmat_solve(pos, 1.0, 1.0, nmax, T, a0,
+                                     _lib.make_opts(tol=1e-10, precision=_lib.PREC_FP64, **kw))
+    assert rc == 0
+    assert rel_l2(s16, s64) <= 1e-6 and rel_l2(s32, s64) <= 1e-6
+    assert i16.iterations <= 1.3 * i32.iterations + 10
