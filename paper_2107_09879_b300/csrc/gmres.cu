@@ -257,6 +257,39 @@ static inline void launch_reduce(tmat_ctx* ctx, const double2* part, int nb, int
   reduce_kernel<<<dim3(R, nvec), RED2_THREADS, 0, ctx->stream>>>(part, nb, nvec, maxv, out, active);
 }
 
+// both dot targets of a DCGS2 pass in one launch: blockIdx.z = 0 reduces part into out,
+// 1 part2 into out2 (the same fixed order as reduce_kernel)
+__global__ void __launch_bounds__(RED2_THREADS)
+reduce_pair_kernel(const double2* __restrict__ part, const double2* __restrict__ part2, int nb, int nvec, int maxv,
+                   double2* __restrict__ out, double2* __restrict__ out2, const int* __restrict__ active) {
+  const int r = blockIdx.x, k = blockIdx.y;
+  if (k >= nvec) return;
+  if (active && !active[r]) return;
+  const double2* pp = (blockIdx.z ? part2 : part) + ((int64_t)r * maxv + k) * nb;
+  double2 s = make_double2(0, 0);
+  for (int b = threadIdx.x; b < nb; b += RED2_THREADS) {
+    const double2 v = pp[b];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double2 t = shfl_down2(s, o);
+    s.x += t.x;
+    s.y += t.y;
+  }
+  __shared__ double2 w2[RED2_THREADS / 32];
+  if ((threadIdx.x & 31) == 0) w2[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 t = w2[0];
+    for (int q = 1; q < RED2_THREADS / 32; ++q) {
+      t.x += w2[q].x;
+      t.y += w2[q].y;
+    }
+    (blockIdx.z ? out2 : out)[r * maxv + k] = t;
+  }
+}
+
 // ||v[r]||^2 block partials of complex64 vectors into part[(r*maxv + 0)*nb + b] (as the
 // .x of a double2): float4 loads, four in flight per thread, fp32 per thread, fp64 per block
 __global__ void __launch_bounds__(256)
@@ -514,7 +547,7 @@ __global__ void dcgs2_small_kernel(GState s, int j, int m, int maxv, int R, int 
   __shared__ double2 sv[1025];
   __shared__ double red[2][32];
   __shared__ double2 zeta_sh;
-  __shared__ double b1_sh, nu_sh;
+  __shared__ double b1_sh, nu_sh, ib1_sh, inu_sh;
   const double2* D1 = s.D1 + (int64_t)r * maxv;
   const double2* D2 = s.D2 + (int64_t)r * maxv;
   double2* Hu = s.Hu + (int64_t)r * maxv * m;  // Hu[i * m + c]
@@ -533,13 +566,14 @@ __global__ void dcgs2_small_kernel(GState s, int j, int m, int maxv, int R, int 
   }
   if (tid == 0) {
     b1_sh = sqrt(fmax(D1[j].x, 0.0));
+    ib1_sh = b1_sh > 0 ? 1.0 / b1_sh : 0.0;
   }
   __syncthreads();
-  const double b1 = b1_sh;
+  const double b1 = b1_sh, ib1 = ib1_sh;  // divisions by b1 and nu as products with reciprocals
   // s = D1 / b1 and |s|^2
   double ss = 0.0;
   for (int k = tid; k < j; k += blockDim.x) {
-    const double2 v = b1 > 0 ? make_double2(D1[k].x / b1, D1[k].y / b1) : make_double2(0, 0);
+    const double2 v = make_double2(D1[k].x * ib1, D1[k].y * ib1);
     sv[k] = v;
     ss += v.x * v.x + v.y * v.y;
   }
@@ -550,9 +584,10 @@ __global__ void dcgs2_small_kernel(GState s, int j, int m, int maxv, int R, int 
     double t = 0.0;
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[0][q];
     nu_sh = b1 > 0 ? sqrt(fmax(1.0 - t, 1e-30)) : 1.0;
+    inu_sh = 1.0 / nu_sh;
   }
   __syncthreads();
-  const double nu = nu_sh;
+  const double nu = nu_sh, inu = inu_sh;
   // finalise column j-1 and hand it to the Givens step (hA + hB, subdiagonal in nrm)
   for (int k = tid; k < j; k += blockDim.x) {
     double2 h = Hu[(int64_t)k * m + (j - 1)];
@@ -574,7 +609,7 @@ __global__ void dcgs2_small_kernel(GState s, int j, int m, int maxv, int R, int 
   // zeta = (c - s^H z)/nu with z = D2/b1, c = D2[j]/b1^2
   double zr = 0.0, zi = 0.0;
   for (int k = tid; k < j; k += blockDim.x) {
-    const double2 z = make_double2(D2[k].x / b1, D2[k].y / b1);
+    const double2 z = make_double2(D2[k].x * ib1, D2[k].y * ib1);
     zr += sv[k].x * z.x + sv[k].y * z.y;  // conj(s) z
     zi += sv[k].x * z.y - sv[k].y * z.x;
   }
@@ -593,8 +628,8 @@ __global__ void dcgs2_small_kernel(GState s, int j, int m, int maxv, int R, int 
       a += red[0][q];
       bq += red[1][q];
     }
-    const double b2 = b1 * b1;
-    zeta_sh = make_double2((D2[j].x / b2 - a) / nu, (D2[j].y / b2 - bq) / nu);
+    const double ib2 = ib1 * ib1;
+    zeta_sh = make_double2((D2[j].x * ib2 - a) * inu, (D2[j].y * ib2 - bq) * inu);
   }
   __syncthreads();
   const double2 zeta = zeta_sh;
@@ -615,25 +650,25 @@ __global__ void dcgs2_small_kernel(GState s, int j, int m, int maxv, int R, int 
         ty += __shfl_down_sync(0xffffffffu, ty, o);
       }
       if (lane == 0) {
-        const double2 zi2 = i < j ? make_double2(D2[i].x / b1, D2[i].y / b1) : zeta;
-        Hu[(int64_t)i * m + j] = make_double2((zi2.x - tx) / nu, (zi2.y - ty) / nu);
+        const double2 zi2 = i < j ? make_double2(D2[i].x * ib1, D2[i].y * ib1) : zeta;
+        Hu[(int64_t)i * m + j] = make_double2((zi2.x - tx) * inu, (zi2.y - ty) * inu);
       }
     }
   }
   // update coefficients
-  const double zn_r = zeta.x / nu, zn_i = zeta.y / nu;  // zeta / nu
+  const double zn_r = zeta.x * inu, zn_i = zeta.y * inu;  // zeta / nu
   for (int k = tid; k < j; k += blockDim.x) {
     const double2 sk = sv[k];
-    const double2 z = make_double2(D2[k].x / b1, D2[k].y / b1);
-    cA[k] = make_float2((float)(sk.x / nu), (float)(sk.y / nu));
+    const double2 z = make_double2(D2[k].x * ib1, D2[k].y * ib1);
+    cA[k] = make_float2((float)(sk.x * inu), (float)(sk.y * inu));
     // (z - (zeta/nu) s)/nu
     const double2 t = make_double2(z.x - (zn_r * sk.x - zn_i * sk.y), z.y - (zn_r * sk.y + zn_i * sk.x));
-    cB[k] = make_float2((float)(t.x / nu), (float)(t.y / nu));
+    cB[k] = make_float2((float)(t.x * inu), (float)(t.y * inu));
   }
   if (tid == 0) {
-    cB[j] = make_float2((float)(zn_r / (nu * b1)), (float)(zn_i / (nu * b1)));  // zeta / (nu^2 b1)
-    s.selfA[r] = (float)(1.0 / (b1 * nu));
-    s.selfB[r] = (float)(1.0 / (b1 * nu));
+    cB[j] = make_float2((float)(zn_r * inu * ib1), (float)(zn_i * inu * ib1));  // zeta / (nu^2 b1)
+    s.selfA[r] = (float)(ib1 * inu);
+    s.selfB[r] = (float)(ib1 * inu);
   }
 }
 
@@ -1091,12 +1126,13 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
           timing_end(ctx, "arnoldi_dots32", ev_d,
                      h16 ? 4.0 * R * n * j + 8.0 * R * n * (1 + (final_only ? 0 : 1))
                          : 8.0 * R * n * (j + 1 + (final_only ? 0 : 1)));
-          launch_reduce(ctx, part, dp.ranges, j + 1, maxv, s.D1, s.active, R);
-          TM_LAUNCHED(ctx);
-          if (!final_only) {
-            launch_reduce(ctx, part2, dp.ranges, j + 1, maxv, s.D2, s.active, R);
-            TM_LAUNCHED(ctx);
+          if (final_only) {
+            launch_reduce(ctx, part, dp.ranges, j + 1, maxv, s.D1, s.active, R);
+          } else {
+            reduce_pair_kernel<<<dim3(R, j + 1, 2), RED2_THREADS, 0, ctx->stream>>>(part, part2, dp.ranges, j + 1, maxv,
+                                                                                   s.D1, s.D2, s.active);
           }
+          TM_LAUNCHED(ctx);
           dcgs2_small_kernel<<<R, 256, gsm_bytes, ctx->stream>>>(s, j, m, maxv, R, final_only ? 1 : 0);
           TM_LAUNCHED(ctx);
           bool any = true;
