@@ -25,6 +25,7 @@
 // (Cooley and Tukey, Math. Comp. 19 (1965)): radix-16 register passes, then radix 4 (one
 // radix-2 stage first for odd powers of two), fp64 twiddles (cast for complex64).
 #include <cmath>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -168,10 +169,32 @@ __device__ __forceinline__ void fft_smem_passes(C<R>* a, int pitch, int nrows, i
   }
 }
 
-template <typename R, bool TOUT, bool TIN>
+// Element formats of a transform's global arrays: complex64 transforms read and write
+// float2; double-float ones read complex128 (double2, split on load) or double-float pairs
+// (dfc, the format of their intermediates and spectra: no conversion) and write either.
+template <typename R, typename GT> struct FftIo;
+template <> struct FftIo<float, float2> {
+  static __device__ __forceinline__ float2 ld(float2 v) { return v; }
+  static __device__ __forceinline__ float2 st(float2 v) { return v; }
+};
+template <> struct FftIo<DF, double2> {
+  static __device__ __forceinline__ dfc ld(double2 v) { return gload<DF>(v); }
+  static __device__ __forceinline__ double2 st(dfc v) { return gstore<DF>(v); }
+};
+template <> struct FftIo<DF, dfc> {
+  static __device__ __forceinline__ dfc ld(dfc v) { return v; }
+  static __device__ __forceinline__ dfc st(dfc v) { return v; }
+};
+// the double-float storage format of a compute type (complex64 transforms: float2)
+template <typename R> struct fft_store { using t = C<R>; };
+
+template <typename T> __device__ __forceinline__ T cneg(T a) { a.x = -a.x; a.y = -a.y; return a; }
+__device__ __forceinline__ dfc cneg(dfc a) { return dfc{-a.rh, -a.rl, -a.ih, -a.il}; }
+
+template <typename R, bool TOUT, bool TIN, typename GI = G<R>, typename GO = G<R>>
 __global__ void __launch_bounds__(FFT_THREADS, sizeof(C<R>) == 8 ? 4 : 2)
-fft_rows_kernel(const G<R>* __restrict__ in, int64_t in_batch_stride, int in_pitch, int cin, int nrows,
-                G<R>* __restrict__ out, int64_t out_batch_stride, int out_pitch, int cout, int lg, int lgrb, int dir,
+fft_rows_kernel(const GI* __restrict__ in, int64_t in_batch_stride, int in_pitch, int cin, int nrows,
+                GO* __restrict__ out, int64_t out_batch_stride, int out_pitch, int cout, int lg, int lgrb, int dir,
                 const double2* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int len = 1 << lg, rb = 1 << lgrb, pitch = len + (len >> 4) + 1;
@@ -186,14 +209,14 @@ fft_rows_kernel(const G<R>* __restrict__ in, int64_t in_batch_stride, int in_pit
   // stores, so the load latency is paid once per batch rather than once per element
   if (TIN) {
     // in[k][row0 + rr] (transposed input): consecutive threads take consecutive rows of one k
-    const G<R>* src = in + (int64_t)b * in_batch_stride + row0;
+    const GI* src = in + (int64_t)b * in_batch_stride + row0;
     const int rr = threadIdx.x & (rb - 1), step = blockDim.x >> lgrb;
     for (int c0 = threadIdx.x >> lgrb; c0 < len; c0 += step * FFT_LOAD_BATCH) {
       C<R> v[FFT_LOAD_BATCH];
 #pragma unroll
       for (int t = 0; t < FFT_LOAD_BATCH; ++t) {
         const int cc = c0 + t * step;
-        v[t] = (rr < nr && cc < cin) ? gload<R>(src[(int64_t)cc * in_pitch + rr]) : czero<R>();
+        v[t] = (rr < nr && cc < cin) ? FftIo<R, GI>::ld(src[(int64_t)cc * in_pitch + rr]) : czero<R>();
       }
 #pragma unroll
       for (int t = 0; t < FFT_LOAD_BATCH; ++t) {
@@ -202,7 +225,7 @@ fft_rows_kernel(const G<R>* __restrict__ in, int64_t in_batch_stride, int in_pit
       }
     }
   } else {
-    const G<R>* src = in + (int64_t)b * in_batch_stride + (int64_t)row0 * in_pitch;
+    const GI* src = in + (int64_t)b * in_batch_stride + (int64_t)row0 * in_pitch;
     const int total = rb << lg;
     for (int e0 = threadIdx.x; e0 < total; e0 += blockDim.x * FFT_LOAD_BATCH) {
       C<R> v[FFT_LOAD_BATCH];
@@ -210,7 +233,7 @@ fft_rows_kernel(const G<R>* __restrict__ in, int64_t in_batch_stride, int in_pit
       for (int t = 0; t < FFT_LOAD_BATCH; ++t) {
         const int e = e0 + t * (int)blockDim.x;
         const int rr = e >> lg, cc = e & (len - 1);
-        v[t] = (e < total && rr < nr && cc < cin) ? gload<R>(src[(int64_t)rr * in_pitch + cc]) : czero<R>();
+        v[t] = (e < total && rr < nr && cc < cin) ? FftIo<R, GI>::ld(src[(int64_t)rr * in_pitch + cc]) : czero<R>();
       }
 #pragma unroll
       for (int t = 0; t < FFT_LOAD_BATCH; ++t) {
@@ -222,16 +245,16 @@ fft_rows_kernel(const G<R>* __restrict__ in, int64_t in_batch_stride, int in_pit
   }
   __syncthreads();
   fft_smem_passes<R>(a, pitch, rb, lg, ws, dir);
-  G<R>* dst = out + (int64_t)b * out_batch_stride;
+  GO* dst = out + (int64_t)b * out_batch_stride;
   if (TOUT) {
     // out[k][row0 + rr]: consecutive threads take consecutive rows of one k
     const int rr = threadIdx.x & (rb - 1);
     for (int k = threadIdx.x >> lgrb; k < cout; k += blockDim.x >> lgrb)
-      if (rr < nr) dst[(int64_t)k * out_pitch + row0 + rr] = gstore<R>(a[rr * pitch + fpad(k)]);
+      if (rr < nr) dst[(int64_t)k * out_pitch + row0 + rr] = FftIo<R, GO>::st(a[rr * pitch + fpad(k)]);
   } else {
     for (int rr = 0; rr < nr; ++rr)
       for (int k = threadIdx.x; k < cout; k += blockDim.x)
-        dst[(int64_t)(row0 + rr) * out_pitch + k] = gstore<R>(a[rr * pitch + fpad(k)]);
+        dst[(int64_t)(row0 + rr) * out_pitch + k] = FftIo<R, GO>::st(a[rr * pitch + fpad(k)]);
   }
 }
 
@@ -239,22 +262,26 @@ fft_rows_kernel(const G<R>* __restrict__ in, int64_t in_batch_stride, int in_pit
 template <typename R> struct fft_compute { using t = R; };
 template <> struct fft_compute<double> { using t = DF; };
 
-template <typename R, bool TOUT, bool TIN = false>
+// IN_S / OUT_S: the input / output is in the transform's storage format (double-float pairs
+// for complex128 transforms; complex64 ones use float2 either way)
+template <typename R, bool TOUT, bool TIN = false, bool IN_S = false, bool OUT_S = false>
 static int fft_rows(tmat_ctx* ctx, const C<R>* in, int64_t in_bs, int in_pitch, int cin, int nrows, C<R>* out,
                     int64_t out_bs, int out_pitch, int cout, int len, int64_t nbatch, int dir, const double2* tw) {
   using CR = typename fft_compute<R>::t;
-  static_assert(sizeof(G<CR>) == sizeof(C<R>), "global element type");
+  using GI = std::conditional_t<IN_S, C<CR>, G<CR>>;
+  using GO = std::conditional_t<OUT_S, C<CR>, G<CR>>;
+  static_assert(sizeof(G<CR>) == sizeof(C<R>) && sizeof(C<CR>) == sizeof(C<R>), "global element type");
   const int lg = ilog2(len);
   int lgrb = ilog2(std::max(1, std::min((TOUT || TIN) ? 16 : 8, FFT_SMEM_POINTS / len)));
   const int rb = 1 << lgrb;
   const size_t smem = sizeof(C<CR>) * ((size_t)rb * (len + (len >> 4) + 1) + len);
-  auto kern = fft_rows_kernel<CR, TOUT, TIN>;
+  auto kern = fft_rows_kernel<CR, TOUT, TIN, GI, GO>;
   if (smem > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, smem));
   for (int64_t b0 = 0; b0 < nbatch; b0 += 65535) {
     const int nb = (int)std::min<int64_t>(65535, nbatch - b0);
     dim3 grid((unsigned)cdiv(nrows, rb), (unsigned)nb);
-    kern<<<grid, FFT_THREADS, smem, ctx->stream>>>((const G<CR>*)(in + b0 * in_bs), in_bs, in_pitch, cin, nrows,
-                                                   (G<CR>*)(out + b0 * out_bs), out_bs, out_pitch, cout, lg, lgrb, dir,
+    kern<<<grid, FFT_THREADS, smem, ctx->stream>>>((const GI*)(in + b0 * in_bs), in_bs, in_pitch, cin, nrows,
+                                                   (GO*)(out + b0 * out_bs), out_bs, out_pitch, cout, lg, lgrb, dir,
                                                    tw);
     TM_LAUNCHED(ctx);
   }
@@ -385,7 +412,7 @@ fft_mul_kernel(const C<R>* __restrict__ Bh, const C<R>* __restrict__ Xh, C<R>* _
     const int64_t num = ((int64_t)kx * CX * My + (int64_t)ky * CY * Mx) % F;
     double sn, cs;
     sincospi(2.0 * (double)num / (double)F, &sn, &cs);
-    ph = mk<R>((R)cs, (R)sn);
+    ph = cfrom64<R>(cs, sn);
   }
   const int* mir = mirror + c * L;
   for (int r0 = 0; r0 < R_; r0 += RC) {
@@ -395,12 +422,12 @@ fft_mul_kernel(const C<R>* __restrict__ Bh, const C<R>* __restrict__ Xh, C<R>* _
       for (int v = 0; v < L; ++v) {
         const bool live = r0 + q < R_;
         const int64_t row = (int64_t)(r0 + q) * P + c * L;
-        x1[(q * L + v) * TS] = live ? Xh[(row + v) * F + f1] : mk<R>((R)0, (R)0);
-        C<R> w = mk<R>((R)0, (R)0);
+        x1[(q * L + v) * TS] = live ? Xh[(row + v) * F + f1] : czero<R>();
+        C<R> w = czero<R>();
         if (live && pair) {
           const int m = mir[v];
           w = Xh[(row + (m & 0xffff)) * F + f2];
-          if (m >> 16) w = mk<R>(-w.x, -w.y);
+          if (m >> 16) w = cneg(w);
         }
         x2[(q * L + v) * TS] = w;
       }
@@ -416,7 +443,7 @@ fft_mul_kernel(const C<R>* __restrict__ Bh, const C<R>* __restrict__ Xh, C<R>* _
   {                                                                                          \
     __syncwarp(); /* the X^ columns are re-read per row, not hoisted into registers */       \
     C<R> acc1[RC], acc2[RC];                                                                 \
-    _Pragma("unroll") for (int q = 0; q < RC; ++q) acc1[q] = acc2[q] = mk<R>((R)0, (R)0);   \
+    _Pragma("unroll") for (int q = 0; q < RC; ++q) acc1[q] = acc2[q] = czero<R>();          \
     _Pragma("unroll") for (int v = 0; v < L; ++v) {                                          \
       _Pragma("unroll") for (int q = 0; q < RC; ++q) {                                       \
         cfma(acc1[q], G[v], x1[(q * L + v) * TS]);                                           \
@@ -424,14 +451,14 @@ fft_mul_kernel(const C<R>* __restrict__ Bh, const C<R>* __restrict__ Xh, C<R>* _
       }                                                                                      \
     }                                                                                        \
     const int m = mir[(U)];                                                                  \
-    const C<R> ph2 = ((m >> 16) != 0) != (msign < 0) ? mk<R>(-ph.x, -ph.y) : ph;           \
+    const C<R> ph2 = ((m >> 16) != 0) != (msign < 0) ? cneg(ph) : ph;                      \
     _Pragma("unroll") for (int q = 0; q < RC; ++q) if (r0 + q < R_) {                        \
       const int64_t row = (int64_t)(r0 + q) * P + c * L;                                     \
       Yh[(row + (U)) * F + f1] = cmul(acc1[q], ph);                                          \
       if (pair) Yh[(row + (m & 0xffff)) * F + f2] = cmul(acc2[q], ph2);                      \
     }                                                                                        \
   }
-    if constexpr (sizeof(R) == 4 && L <= 24) {
+    if constexpr (std::is_same_v<R, float> && L <= 24) {
       FFT_MUL_LOAD(0, gA)
 #pragma unroll 1
       for (int u = 0; u < L; u += 2) {
@@ -713,9 +740,11 @@ template <typename R>
 static int fft2_forward(tmat_ctx* ctx, const C<R>* grid, int nx, int ny, int Mx, int My, int64_t nb, C<R>* tmp,
                         C<R>* out, const double2* tw) {
   // F1: rows iy (ny of them), FFT along ix, write transposed tmp[b][kx][iy] (pitch ny)
-  TM_TRY((fft_rows<R, true>(ctx, grid, (int64_t)ny * nx, nx, nx, ny, tmp, (int64_t)Mx * ny, ny, Mx, Mx, nb, -1, tw)));
-  // F2: rows kx (Mx), FFT along iy zero-padded to My -> out[b][kx][ky]
-  TM_TRY((fft_rows<R, false>(ctx, tmp, (int64_t)Mx * ny, ny, ny, Mx, out, (int64_t)Mx * My, My, My, My, nb, -1, tw)));
+  TM_TRY((fft_rows<R, true, false, false, true>(ctx, grid, (int64_t)ny * nx, nx, nx, ny, tmp, (int64_t)Mx * ny, ny, Mx,
+                                                Mx, nb, -1, tw)));
+  // F2: rows kx (Mx), FFT along iy zero-padded to My -> out[b][kx][ky] (storage format)
+  TM_TRY((fft_rows<R, false, false, true, true>(ctx, tmp, (int64_t)Mx * ny, ny, ny, Mx, out, (int64_t)Mx * My, My, My,
+                                                My, nb, -1, tw)));
   return TMAT_OK;
 }
 
@@ -724,9 +753,11 @@ template <typename R>
 static int fft2_inverse(tmat_ctx* ctx, const C<R>* spec, int nx, int ny, int Mx, int My, int64_t nb, C<R>* tmp,
                         C<R>* out, const double2* tw) {
   // I2: rows kx, inverse along ky, keep iy < ny, transposed -> tmp[b][iy][kx] (pitch Mx)
-  TM_TRY((fft_rows<R, true>(ctx, spec, (int64_t)Mx * My, My, My, Mx, tmp, (int64_t)ny * Mx, Mx, ny, My, nb, +1, tw)));
+  TM_TRY((fft_rows<R, true, false, true, true>(ctx, spec, (int64_t)Mx * My, My, My, Mx, tmp, (int64_t)ny * Mx, Mx, ny,
+                                               My, nb, +1, tw)));
   // I1: rows iy, inverse along kx, keep ix < nx -> out[b][iy][ix]
-  TM_TRY((fft_rows<R, false>(ctx, tmp, (int64_t)ny * Mx, Mx, Mx, ny, out, (int64_t)ny * nx, nx, nx, Mx, nb, +1, tw)));
+  TM_TRY((fft_rows<R, false, false, true, false>(ctx, tmp, (int64_t)ny * Mx, Mx, Mx, ny, out, (int64_t)ny * nx, nx, nx,
+                                                 Mx, nb, +1, tw)));
   return TMAT_OK;
 }
 
@@ -836,16 +867,18 @@ static int fft_apply_t(tmat_ctx* ctx, const LatOp& a, const void* xv, void* yv, 
     }
   }
   if (!quad_done) {
+    // complex128 operators: the products in double-float on spectra stored as pairs
+    using CM = typename fft_compute<R>::t;
     constexpr int RC2 = (sizeof(R) == 4 && L <= 24) ? 2 : 1;
     const int RC = a.fft_bstride ? 1 : RC2;  // one RHS per pass when every RHS has its own spectra
-    const size_t msm = sizeof(C<R>) * 2 * (size_t)RC * L * FFT_MUL_THREADS;
-    auto kern = RC == 1 ? fft_mul_kernel<R, L, MODE, 1> : fft_mul_kernel<R, L, MODE, RC2>;
+    const size_t msm = sizeof(C<CM>) * 2 * (size_t)RC * L * FFT_MUL_THREADS;
+    auto kern = RC == 1 ? fft_mul_kernel<CM, L, MODE, 1> : fft_mul_kernel<CM, L, MODE, RC2>;
     if (msm > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, msm));
     const int64_t items = (int64_t)Mx * (My >= 2 ? My / 2 + 1 : 1);
     dim3 g((unsigned)cdiv(items, FFT_MUL_THREADS), 2);
     cudaEvent_t ev = timing_begin(ctx);
-    kern<<<g, FFT_MUL_THREADS, msm, ctx->stream>>>((const C<R>*)a.fft_Bhat, Xh, Yh, Mx, My, R_, a.CX, a.CY,
-                                                   a.fft_mirror, a.fft_mirror_sign, a.fft_bstride);
+    kern<<<g, FFT_MUL_THREADS, msm, ctx->stream>>>((const C<CM>*)a.fft_Bhat, (const C<CM>*)Xh, (C<CM>*)Yh, Mx, My, R_,
+                                                   a.CX, a.CY, a.fft_mirror, a.fft_mirror_sign, a.fft_bstride);
     TM_LAUNCHED(ctx);
     // the block spectra of one frequency per mirror pair, the RHS spectra in and out
     const double mul_bytes = (double)sizeof(C<R>) * (items * 2.0 * L * L * (a.fft_bstride ? R_ : 1) + 2.0 * nb * F);
