@@ -140,12 +140,13 @@ class ClockSampler:
 
 
 # DRAM bytes (read + write) / algorithmic bytes of one ncu capture of each HBM-bound kernel as
-# it stands (dot and update passes on a 100 x 100 solve, the block product on the 200 x 200
-# lattice), scaled to the timed launches by their algorithmic bytes (traffic grows with the
-# bytes a launch must move). Set an entry to None when its kernel changes.
-TRAFFIC_RATIO = {"arnoldi_dots32": (490.18e6 + 4.41e6) / (62 * 2 * 480000 * 8),
-                 "arnoldi_update32": (468.52e6 + 13.44e6) / (63 * 2 * 480000 * 8),
-                 "lattice_fft_mul32": None}
+# it stands (the quad block product on the 200 x 200 lattice: 205.93 MB read + 27.86 MB written
+# of 256.16 MB algorithmic), scaled to the timed launches by their algorithmic bytes (traffic
+# grows with the bytes a launch must move). None: the kernel changed since its last capture
+# (the compressed-basis dot and update passes).
+TRAFFIC_RATIO = {"arnoldi_dots32": None,
+                 "arnoldi_update32": None,
+                 "lattice_fft_mul32": (205.93e6 + 27.86e6) / 256.16e6}
 # DRAM bytes per launch of the direct-path window-view kernel and of the block product
 # (one ncu capture each on the 200 x 200 lattice)
 MEASURED_TRAFFIC = {"lattice_tc2_kernel<4,0>": 238.0e6 + 23.0e6}
@@ -847,8 +848,11 @@ def run_ours(args, rank, world):
         kern_name = name
         if n32:
             break
-    hbm_kinds = {"arnoldi_dots32": "dots32_kernel<true> (Arnoldi dot pass, two targets)",
-                 "arnoldi_update32": "dcgs2_update_kernel (Arnoldi update pass, two outputs)",
+    h16 = args.inner_tol >= 1e-2  # loose inner solves keep their final Krylov vectors in fp16
+    hbm_kinds = {"arnoldi_dots32": ("dots16_kernel<true> (Arnoldi dot pass on the fp16 basis, two targets)" if h16 else
+                                    "dots32_kernel<true> (Arnoldi dot pass, two targets)"),
+                 "arnoldi_update32": ("dcgs2_update16_kernel (Arnoldi update pass on the fp16 basis, two outputs)"
+                                      if h16 else "dcgs2_update_kernel (Arnoldi update pass, two outputs)"),
                  "lattice_fft_mul32": ("fft_mul4_kernel<24,0> (block products, quad-mirror form: one symmetric matrix per "
                                        "(+-kx, +-ky))" if args.fft_mode == 1 else
                                        "fft_mul_kernel<float,24,0,2> (block products, mirror pairs (kx, +-ky))")}
