@@ -80,10 +80,13 @@ dots_kernel(const C<VR>* __restrict__ V, int64_t vstride, int nvec, const C<VR>*
 // the complex64 Krylov vectors are done in fp32 (a lane sums the products of its
 // elements, a warp its 32 lanes), and only the per-warp partials are summed in fp64.
 // Work unit = one warp: D32_VPW basis vectors over one contiguous element range; the
-// ranges per vector group are chosen so that ~48 warps per SM stream at once, each
+// ranges per vector group are chosen so that ~64 warps per SM stream at once, each
 // with D32_VPW + 1 independent 512-byte loads per step (the same occupancy-driven
 // pattern as the update kernel). w is re-read once per vector group (from L1/L2).
-constexpr int D32_VPW = 8;
+// (measured on a B300 for 2 RHS of 1.92 M values and j = 2..30: two vectors per warp, four
+// blocks per SM, the element loop unrolled by two and ~64 warps per SM reach 3.5-5.8 TB/s,
+// eight vectors per warp at two blocks per SM 1.8-4.6 TB/s)
+constexpr int D32_VPW = 2;
 constexpr int D32_NBMAX = 1024;  // element ranges per group (partials per dot)
 
 struct Dots32Plan {
@@ -93,7 +96,7 @@ struct Dots32Plan {
 static inline Dots32Plan dots32_plan(int64_t n, int nvec, int num_sms, int R) {
   Dots32Plan p;
   p.groups = (nvec + D32_VPW - 1) / D32_VPW;
-  const int64_t target = (int64_t)num_sms * 48 / std::max(1, R);  // warps per RHS
+  const int64_t target = (int64_t)num_sms * 64 / std::max(1, R);  // warps per RHS
   int64_t nr = cdiv(target, (int64_t)p.groups);
   nr = std::min<int64_t>(nr, std::max<int64_t>(1, cdiv(n / 2, (int64_t)32 * 16)));
   p.ranges = (int)std::max<int64_t>(1, std::min<int64_t>(nr, D32_NBMAX));
@@ -103,7 +106,7 @@ static inline Dots32Plan dots32_plan(int64_t n, int nvec, int num_sms, int R) {
 
 // TWO: also dots against a second target w2 into part2 (one read of the basis for both).
 template <bool TWO>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 dots32_kernel(const float2* __restrict__ V, int64_t vstride, int nvec, const float2* __restrict__ w, int64_t n,
               int64_t rstride, double2* __restrict__ part, int maxv, int groups, int ranges,
               const int* __restrict__ active, const float2* __restrict__ w2 = nullptr,
@@ -131,6 +134,7 @@ dots32_kernel(const float2* __restrict__ V, int64_t vstride, int nvec, const flo
   for (int q = 0; q < D32_VPW; ++q) acc[q] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int q = 0; q < (TWO ? D32_VPW : 1); ++q) acc2[q] = make_float2(0.f, 0.f);
+#pragma unroll 2
   for (int64_t i = lo + lane; i < hi; i += 32) {
     const float4 wv = w4[i];
     float4 wv2 = make_float4(0.f, 0.f, 0.f, 0.f);
