@@ -484,7 +484,7 @@ def bench_sweep(ctx, torch, inner_tol=0.1):
                     "sub-region's iteration count is that of its batch"}
 
 
-def bench_cylinders(ctx, torch, steps=3):
+def bench_cylinders(ctx, torch, steps=3, inner_tol=0.2):
     """A metalens-like array of silicon-like cylinders (the paper's meta-atoms, App. I-B):
     200 x 200 upright cylinders on the 0.5-wavelength lattice, 8 radii from 0.08 to 0.15
     (height 0.3, index 3.5; every enclosing sphere inside its cell), nmax 4, cutoff 8 with the
@@ -503,7 +503,7 @@ def bench_cylinders(ctx, torch, steps=3):
     pol = torch.tensor([[1.0, 0.0, 0.0]], dtype=torch.complex128, device="cuda")
     radii = torch.from_numpy(np.sqrt(kinds[types] ** 2 + 0.15 ** 2)).cuda()
     opts = _lib.make_opts(tol=TOL, restart=300, max_iter=4000, cutoff=8.0, taper=8.0, precision=_lib.PREC_MIXED,
-                          inner_tol=0.2, path=_lib.PATH_LATTICE, lattice_nx=n, lattice_ny=n, lattice_pitch=PITCH,
+                          inner_tol=inner_tol, path=_lib.PATH_LATTICE, lattice_nx=n, lattice_ny=n, lattice_pitch=PITCH,
                           enclosing_radii=radii)
     rec = []
 
@@ -690,13 +690,14 @@ def fp64_plain(ctx, torch, step_inputs, opts_kw, s_mixed, steps=1):
                     "incident coefficients excluded); mixed_vs_fp64_rel_l2 = ||s_mixed - s_fp64|| / ||s_fp64||"}
 
 
-def bench_every_pair(ctx, torch, steps=2):
+def bench_every_pair(ctx, torch, steps=2, inner_tol=0.2):
     """The headline lattice with every pair coupled (the paper's operator, App. I-D; no cutoff):
     the same mixed solve through the FFT convolution on a 512 x 512 grid."""
     from paper_2107_09879_b300 import _lib
     wl, pos, atoms, dirs, pols, pts = study_inputs(200, torch)
     opts = _lib.make_opts(tol=TOL, restart=300, max_iter=4000, cutoff=0.0, taper=0.0, precision=_lib.PREC_MIXED,
-                          inner_tol=0.2, path=_lib.PATH_LATTICE, lattice_nx=200, lattice_ny=200, lattice_pitch=PITCH)
+                          inner_tol=inner_tol, path=_lib.PATH_LATTICE, lattice_nx=200, lattice_ny=200,
+                          lattice_pitch=PITCH)
     rec = []
 
     def one():
