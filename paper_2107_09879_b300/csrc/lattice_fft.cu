@@ -258,6 +258,104 @@ fft_rows_kernel(const GI* __restrict__ in, int64_t in_batch_stride, int in_pitch
   }
 }
 
+
+// ---- 256-point rows of the complex64 operators: four-step 16 x 16 ------------------------
+// X[k1 + 16 k2] = sum_a W256^(a k1) W16^(a k2) [sum_b x[a + 16 b] W16^(b k1)]: the 16 threads
+// of a row hold x[a + 16 b] (thread a, b = 0..15), take a 16-point DFT in registers,
+// multiply by W256^(a k1), exchange through shared memory within their half-warp and take
+// the second 16-point DFT; thread k1 ends with X[k1 + 16 k2]. One global load and one
+// store per value, no bit reversal, one shared-memory round trip (the generic kernel
+// makes three). 16 rows per block of 256 threads. W[m] = W256^m of the direction (forward
+// e^{-2 pi i m / 256}, inverse its conjugate).
+__device__ __forceinline__ void fft_dft4(float2& a, float2& b, float2& c, float2& d, int dir) {
+  const float2 t0 = cadd(a, c), t1 = csub(a, c), t2 = cadd(b, d), t3 = crot<float>(csub(b, d), dir);
+  a = cadd(t0, t2);
+  c = csub(t0, t2);
+  b = cadd(t1, t3);
+  d = csub(t1, t3);
+}
+// in-place 16-point DFT of v (index n in, index k out, natural order), W16^m = W[16 m]
+__device__ __forceinline__ void fft_dft16(float2 (&v)[16], const float2* W, int dir) {
+  // n = n1 + 4 n2: DFT4 over n2 for each n1 (outputs k' = 0..3 in place of n2)
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) fft_dft4(v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12], dir);
+  // twiddles W16^(n1 k')
+#pragma unroll
+  for (int n1 = 1; n1 < 4; ++n1)
+#pragma unroll
+    for (int kp = 1; kp < 4; ++kp) v[n1 + 4 * kp] = cmul(v[n1 + 4 * kp], W[16 * n1 * kp]);
+  // DFT4 over n1 for each k': X[k' + 4 k2] lands at position 4 k' + k2
+#pragma unroll
+  for (int kp = 0; kp < 4; ++kp) fft_dft4(v[4 * kp], v[4 * kp + 1], v[4 * kp + 2], v[4 * kp + 3], dir);
+  // reorder position 4 k' + k2 -> index k' + 4 k2 (a fixed permutation of registers)
+  float2 o[16];
+#pragma unroll
+  for (int kp = 0; kp < 4; ++kp)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) o[kp + 4 * k2] = v[4 * kp + k2];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = o[k];
+}
+
+constexpr int F256_RS = 16 * 17;  // exchange stride of a row (k1 blocks of 17)
+constexpr int F256_OS = 257;      // staging stride of a row for transposed stores
+
+template <bool TOUT>
+__global__ void __launch_bounds__(256, 4)
+fft256_rows_kernel(const float2* __restrict__ in, int64_t in_batch_stride, int in_pitch, int cin, int nrows,
+                   float2* __restrict__ out, int64_t out_batch_stride, int out_pitch, int cout, int dir,
+                   const double2* __restrict__ tw) {
+  __shared__ float2 W[256];
+  __shared__ float2 ex[16 * F256_RS];  // exchange, then (TOUT) the output staging [16][257]
+  static_assert(16 * F256_OS <= 16 * F256_RS, "staging fits the exchange buffer");
+  const int b = blockIdx.y;
+  const int row0 = blockIdx.x * 16;
+  const int rr = threadIdx.x >> 4, a = threadIdx.x & 15;
+  for (int m = threadIdx.x; m < 256; m += blockDim.x) {
+    // W256^m = tw[4 m] (m < 128), -tw[4 (m - 128)] (m >= 128), tw = e^{-2 pi i k / 1024}
+    const double2 t = tw[4 * (m & 127)];
+    const float sg = m < 128 ? 1.f : -1.f;
+    W[m] = make_float2(sg * (float)t.x, sg * (dir < 0 ? (float)t.y : -(float)t.y));
+  }
+  const int row = row0 + rr;
+  const bool live = row < nrows;
+  float2 v[16];
+  const float2* src = in + (int64_t)b * in_batch_stride + (int64_t)row * in_pitch;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int c = a + 16 * q;
+    v[q] = (live && c < cin) ? src[c] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();  // W
+  fft_dft16(v, W, dir);  // v[k1] = Y[a][k1]
+  float2* exr = ex + rr * F256_RS;
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) exr[k1 * 17 + a] = k1 ? cmul(v[k1], W[(a * k1) & 255]) : v[k1];
+  __syncwarp();
+  const int k1 = a;  // this thread now owns column k1: Y[a'][k1] for a' = 0..15
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = exr[k1 * 17 + q];
+  fft_dft16(v, W, dir);  // v[k2] = X[k1 + 16 k2]
+  float2* dst = out + (int64_t)b * out_batch_stride;
+  if (TOUT) {
+    __syncthreads();  // every row's exchange reads are done before the staging overwrites
+    float2* st = ex + rr * F256_OS;
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) st[k1 + 16 * k2] = v[k2];
+    __syncthreads();
+    // out[k][row0 + r]: consecutive threads take consecutive rows of one k
+    const int r = threadIdx.x & 15, nr = min(16, nrows - row0);
+    for (int k = threadIdx.x >> 4; k < cout; k += 16)
+      if (r < nr) dst[(int64_t)k * out_pitch + row0 + r] = ex[r * F256_OS + k];
+  } else if (live) {
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) {
+      const int k = k1 + 16 * k2;
+      if (k < cout) dst[(int64_t)row * out_pitch + k] = v[k2];
+    }
+  }
+}
+
 // complex64 transforms compute in fp32; complex128 ones in double-float (see above)
 template <typename R> struct fft_compute { using t = R; };
 template <> struct fft_compute<double> { using t = DF; };
@@ -271,6 +369,19 @@ static int fft_rows(tmat_ctx* ctx, const C<R>* in, int64_t in_bs, int in_pitch, 
   using GI = std::conditional_t<IN_S, C<CR>, G<CR>>;
   using GO = std::conditional_t<OUT_S, C<CR>, G<CR>>;
   static_assert(sizeof(G<CR>) == sizeof(C<R>) && sizeof(C<CR>) == sizeof(C<R>), "global element type");
+  if constexpr (std::is_same_v<R, float> && !TIN) {
+    if (len == 256) {  // the complex64 operators' rows: four-step kernel
+      for (int64_t b0 = 0; b0 < nbatch; b0 += 65535) {
+        const int nb = (int)std::min<int64_t>(65535, nbatch - b0);
+        dim3 grid((unsigned)cdiv(nrows, 16), (unsigned)nb);
+        fft256_rows_kernel<TOUT><<<grid, 256, 0, ctx->stream>>>((const float2*)(in + b0 * in_bs), in_bs, in_pitch, cin,
+                                                               nrows, (float2*)(out + b0 * out_bs), out_bs, out_pitch,
+                                                               cout, dir, tw);
+        TM_LAUNCHED(ctx);
+      }
+      return TMAT_OK;
+    }
+  }
   const int lg = ilog2(len);
   int lgrb = ilog2(std::max(1, std::min((TOUT || TIN) ? 16 : 8, FFT_SMEM_POINTS / len)));
   const int rb = 1 << lgrb;
