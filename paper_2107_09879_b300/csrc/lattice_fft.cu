@@ -356,6 +356,92 @@ fft256_rows_kernel(const float2* __restrict__ in, int64_t in_batch_stride, int i
   }
 }
 
+
+// ---- 256 x 256 complex64 transforms without transposes ------------------------------------
+// Every pass takes blocks of 16 consecutive components c of one right-hand side r and one
+// line: a row of the pass is (r, c, line) with elements at
+//   r rstride + c cstride + line lstride + col estride,
+// and its outputs go to the same form of the output array. Layouts whose components are
+// innermost (cstride 1: x, y and the intermediates [r][line][col][P]) are read and written
+// with consecutive threads on consecutive components; component-major ones (the spectra
+// [r P + c][kx][ky]) with consecutive threads along a row. The first forward pass reads x
+// (T x for the adjoint) in place and the last inverse pass writes y = x - T s (or x - s, s)
+// in place, so the operator needs no embed or extract kernels.
+struct F256Lay {
+  int64_t rstride, cstride, lstride, estride;
+};
+constexpr int F256_RS2 = 16 * 17 + 1;  // exchange stride of a row (odd: conflict-free in both mappings)
+
+// EMB: 0 plain input, 2 input times T (same layout, T's RHS stride tstride); EXT: -1 plain
+// output, 0 y = x - T s, 1 y = x - s, 2 y = s with s = scale * value (x, T in the output's layout)
+template <bool IN_CI, bool OUT_CI, int EMB, int EXT>
+__global__ void __launch_bounds__(256, 4)
+fft256_ci_kernel(const float2* __restrict__ in, F256Lay li, int cin, float2* __restrict__ out, F256Lay lo, int cout,
+                 int P, int dir, const double2* __restrict__ tw, const float2* __restrict__ T, int64_t tstride,
+                 const float2* __restrict__ xs, float scale) {
+  __shared__ float2 W[256];
+  __shared__ float2 ex[16 * F256_RS2];
+  const int line = blockIdx.x;
+  const int r = blockIdx.z;
+  const int c0 = blockIdx.y * 16;
+  for (int m = threadIdx.x; m < 256; m += blockDim.x) {
+    const double2 t = tw[4 * (m & 127)];
+    const float sg = m < 128 ? 1.f : -1.f;
+    W[m] = make_float2(sg * (float)t.x, sg * (dir < 0 ? (float)t.y : -(float)t.y));
+  }
+  // first half: thread (row rr, column a) holds x[a + 16 b]
+  {
+    const int rr = IN_CI ? (threadIdx.x & 15) : (threadIdx.x >> 4);
+    const int a = IN_CI ? (threadIdx.x >> 4) : (threadIdx.x & 15);
+    const int c = c0 + rr;
+    const bool live = c < P;
+    const int64_t base = (int64_t)r * li.rstride + (int64_t)c * li.cstride + (int64_t)line * li.lstride;
+    float2 v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int col = a + 16 * q;
+      float2 e = make_float2(0.f, 0.f);
+      if (live && col < cin) {
+        const int64_t o = base + (int64_t)col * li.estride;
+        e = in[o];
+        if (EMB == 2) e = cmul(T[(int64_t)r * tstride + o - (int64_t)r * li.rstride], e);
+      }
+      v[q] = e;
+    }
+    __syncthreads();  // W
+    fft_dft16(v, W, dir);
+    float2* exr = ex + rr * F256_RS2;
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) exr[k1 * 17 + a] = k1 ? cmul(v[k1], W[(a * k1) & 255]) : v[k1];
+  }
+  __syncthreads();
+  // second half: thread (row rr, k1) owns X[k1 + 16 k2]
+  const int rr = OUT_CI ? (threadIdx.x & 15) : (threadIdx.x >> 4);
+  const int k1 = OUT_CI ? (threadIdx.x >> 4) : (threadIdx.x & 15);
+  float2 v[16];
+  const float2* exr = ex + rr * F256_RS2;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = exr[k1 * 17 + q];
+  fft_dft16(v, W, dir);
+  const int c = c0 + rr;
+  if (c >= P) return;
+  const int64_t base = (int64_t)r * lo.rstride + (int64_t)c * lo.cstride + (int64_t)line * lo.lstride;
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) {
+    const int k = k1 + 16 * k2;
+    if (k >= cout) continue;
+    const int64_t o = base + (int64_t)k * lo.estride;
+    if (EXT < 0) {
+      out[o] = v[k2];
+    } else {
+      const float2 s = cscale(v[k2], scale);
+      if (EXT == 2) out[o] = s;
+      else if (EXT == 1) out[o] = csub(xs[o], s);
+      else out[o] = csub(xs[o], cmul(T[(int64_t)r * tstride + o - (int64_t)r * lo.rstride], s));
+    }
+  }
+}
+
 // complex64 transforms compute in fp32; complex128 ones in double-float (see above)
 template <typename R> struct fft_compute { using t = R; };
 template <> struct fft_compute<double> { using t = DF; };
@@ -950,9 +1036,35 @@ static int fft_apply_t(tmat_ctx* ctx, const LatOp& a, const void* xv, void* yv, 
   cudaEvent_t ev_all = timing_begin(ctx);
   dim3 tb(32, 8);
   dim3 tg((unsigned)cdiv(nx, 32), (unsigned)ny, (unsigned)(R_ * cdiv(P, 32)));
-  fft_embed_kernel<R, MODE == 1 ? 1 : 0><<<tg, tb, 0, ctx->stream>>>(x, T, nx, ny, P, R_, grid, a.t_stride);
-  TM_LAUNCHED(ctx);
-  TM_TRY(fft2_forward<R>(ctx, grid, nx, ny, Mx, My, nb, w1, Xh, tw));
+  // 256 x 256 complex64 grids: the passes read x and write y in place through the
+  // component-innermost intermediates T1 [r][kx][iy][P] and T2 [r][iy][kx][P] (w1)
+  const bool ci = std::is_same_v<R, float> && Mx == 256 && My == 256;
+  const int64_t Nsite = (int64_t)nx * ny;
+  const F256Lay lx{Nsite * P, 1, (int64_t)nx * P, P};                         // x, y: line iy, col ix
+  const F256Lay lspec{(int64_t)P * F, F, My, 1};                              // spectra: line kx, col ky
+  const F256Lay lt1_out{(int64_t)Mx * ny * P, 1, P, (int64_t)ny * P};         // T1 written: line iy, k kx
+  const F256Lay lt1_in{(int64_t)Mx * ny * P, 1, (int64_t)ny * P, P};          // T1 read: line kx, col iy
+  const F256Lay lt2_out{(int64_t)ny * Mx * P, 1, P, (int64_t)Mx * P};         // T2 written: line kx, k iy
+  const F256Lay lt2_in{(int64_t)ny * Mx * P, 1, (int64_t)Mx * P, P};          // T2 read: line iy, col kx
+  const dim3 gy((unsigned)ny, (unsigned)cdiv(P, 16), (unsigned)R_), gk((unsigned)Mx, (unsigned)cdiv(P, 16), (unsigned)R_);
+  if (ci) {
+    if constexpr (std::is_same_v<R, float>) {
+      if (MODE == 1)
+        fft256_ci_kernel<true, true, 2, -1><<<gy, 256, 0, ctx->stream>>>(x, lx, nx, w1, lt1_out, Mx, P, -1, tw, T,
+                                                                          a.t_stride, nullptr, 1.f);
+      else
+        fft256_ci_kernel<true, true, 0, -1><<<gy, 256, 0, ctx->stream>>>(x, lx, nx, w1, lt1_out, Mx, P, -1, tw, T,
+                                                                          a.t_stride, nullptr, 1.f);
+      TM_LAUNCHED(ctx);
+      fft256_ci_kernel<true, false, 0, -1><<<gk, 256, 0, ctx->stream>>>(w1, lt1_in, ny, Xh, lspec, My, P, -1, tw, T,
+                                                                         a.t_stride, nullptr, 1.f);
+      TM_LAUNCHED(ctx);
+    }
+  } else {
+    fft_embed_kernel<R, MODE == 1 ? 1 : 0><<<tg, tb, 0, ctx->stream>>>(x, T, nx, ny, P, R_, grid, a.t_stride);
+    TM_LAUNCHED(ctx);
+    TM_TRY(fft2_forward<R>(ctx, grid, nx, ny, Mx, My, nb, w1, Xh, tw));
+  }
   bool quad_done = false;
   if constexpr (sizeof(R) == 4) {
     if (a.fft_C) {
@@ -995,11 +1107,22 @@ static int fft_apply_t(tmat_ctx* ctx, const LatOp& a, const void* xv, void* yv, 
     const double mul_bytes = (double)sizeof(C<R>) * (items * 2.0 * L * L * (a.fft_bstride ? R_ : 1) + 2.0 * nb * F);
     timing_end(ctx, sizeof(R) == 4 ? "lattice_fft_mul32" : "lattice_fft_mul64", ev, mul_bytes);
   }
-  C<R>* Yc = Xh;  // X^ is no longer needed
-  TM_TRY(fft2_inverse<R>(ctx, Yh, nx, ny, Mx, My, nb, w1, Yc, tw));
-  fft_extract_kernel<R, MODE><<<tg, tb, 0, ctx->stream>>>(Yc, x, T, nx, ny, P, (R)(1.0 / (double)F), (C<R>*)yv,
-                                                          a.t_stride);
-  TM_LAUNCHED(ctx);
+  if (ci) {
+    if constexpr (std::is_same_v<R, float>) {
+      fft256_ci_kernel<false, true, 0, -1><<<gk, 256, 0, ctx->stream>>>(Yh, lspec, My, w1, lt2_out, ny, P, +1, tw, T,
+                                                                         a.t_stride, nullptr, 1.f);
+      TM_LAUNCHED(ctx);
+      fft256_ci_kernel<true, true, 0, MODE><<<gy, 256, 0, ctx->stream>>>(w1, lt2_in, Mx, (float2*)yv, lx, nx, P, +1, tw,
+                                                                          T, a.t_stride, x, (float)(1.0 / (double)F));
+      TM_LAUNCHED(ctx);
+    }
+  } else {
+    C<R>* Yc = Xh;  // X^ is no longer needed
+    TM_TRY(fft2_inverse<R>(ctx, Yh, nx, ny, Mx, My, nb, w1, Yc, tw));
+    fft_extract_kernel<R, MODE><<<tg, tb, 0, ctx->stream>>>(Yc, x, T, nx, ny, P, (R)(1.0 / (double)F), (C<R>*)yv,
+                                                            a.t_stride);
+    TM_LAUNCHED(ctx);
+  }
   timing_end(ctx, sizeof(R) == 4 ? "lattice_apply_fft32" : "lattice_apply_fft64", ev_all);
   return TMAT_OK;
 }

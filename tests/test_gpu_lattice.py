@@ -240,3 +240,23 @@ def test_fft_quad_product_matches_mirror_pair_product(nmax, nx, ny, cutoff, R, o
     assert rel_l2(yq, y64) <= C64_APPLY_TOL
     assert rel_l2(yp, y64) <= C64_APPLY_TOL
     assert rel_l2(yq, yp) <= 2 * C64_APPLY_TOL
+
+
+@pytest.mark.parametrize("nmax,n,cutoff,R", [(4, 130, 3.0, 2), (3, 125, 2.0, 3), (5, 129, 1.5, 1)])
+@pytest.mark.parametrize("op", [0, 1, 2])
+def test_fft_256_grid_passes_match_fp64_and_direct(nmax, n, cutoff, R, op):
+    """Lattices whose FFT grid is 256 x 256 take the four-step, transpose-free complex64 passes
+    (x read and y written in place; P = 30, 48, 70: full and partial component blocks; odd R)
+    against the complex128 FFT apply (the generic passes) and the direct tensor-core kernel."""
+    from paper_2107_09879_b300 import _lib
+    r = W.uniform_radii(n * n, 0.08, 0.24, 160 + nmax)
+    T = np.ascontiguousarray(np.array([mie.tmatrix_diag(nmax, K0, v, 2.0) for v in r]))
+    x = rand_c((R, n * n, T.shape[1]), 170 + nmax)
+    c = _lib.Context(0)
+    y32 = c.tmat_apply_lattice(op, 1, n, n, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
+    y64 = c.tmat_apply_lattice(op, 0, n, n, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
+    c.set_lattice_fft(False)
+    yd = c.tmat_apply_lattice(op, 1, n, n, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
+    c.close()
+    assert rel_l2(y32, y64) <= C64_APPLY_TOL
+    assert rel_l2(yd, y64) <= C64_APPLY_TOL
