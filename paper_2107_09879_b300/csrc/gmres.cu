@@ -329,6 +329,39 @@ norm32_kernel(const float2* __restrict__ v, int64_t n, int64_t rstride, double2*
   }
 }
 
+// ||v[r]||^2 block partials of complex128 vectors (fp64 throughout), as norm32_kernel: four
+// loads in flight per thread, a fixed summation order
+__global__ void __launch_bounds__(256)
+norm64_kernel(const double2* __restrict__ v, int64_t n, int64_t rstride, double2* __restrict__ part, int maxv,
+              const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  const double2* vr = v + r * rstride;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  double acc = 0.0;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    double2 a[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) a[t] = vr[i + t * stride];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) acc = fma(a[t].x, a[t].x, fma(a[t].y, a[t].y, acc));
+  }
+  for (; i < n; i += stride) {
+    const double2 a = vr[i];
+    acc = fma(a.x, a.x, fma(a.y, a.y, acc));
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  __shared__ double ws[8];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += ws[q];
+    part[(int64_t)r * maxv * gridDim.x + blockIdx.x] = make_double2(t, 0.0);  // slot k = 0
+  }
+}
+
 // out[r][i] += sign * sum_k V_k[r][i] coef[r][k]
 template <typename VR, typename XR>
 __global__ void update_kernel(const C<VR>* __restrict__ V, int64_t vstride, int nvec, const double2* __restrict__ coef,
@@ -985,6 +1018,16 @@ static int vec_norms(tmat_ctx* ctx, const C<VR>* v, int64_t n, int64_t rstride, 
       TM_LAUNCHED(ctx);
       return TMAT_OK;
     }
+  }
+  if constexpr (sizeof(VR) == 8) {
+    const int nbn = (int)std::max<int64_t>(1, std::min<int64_t>(nb, cdiv(n, 256 * 4)));
+    norm64_kernel<<<dim3(nbn, R), 256, 0, ctx->stream>>>(v, n, rstride, part, maxv, active);
+    TM_LAUNCHED(ctx);
+    launch_reduce(ctx, part, nbn, 1, maxv, tmp, active, R);
+    TM_LAUNCHED(ctx);
+    norm_from_dots_kernel<<<1, 32, 0, ctx->stream>>>(tmp, maxv, nrm, R, active);
+    TM_LAUNCHED(ctx);
+    return TMAT_OK;
   }
   dots_kernel<VR><<<dim3(nb, R), RED_THREADS, 0, ctx->stream>>>(v, 0, 1, v, n, rstride, part, maxv, active);
   TM_LAUNCHED(ctx);
