@@ -150,20 +150,32 @@ __global__ void pw_angular_kernel(const double* __restrict__ dirs, const double2
   coef[t] = make_double2(-4.0 * cl * v.x, -4.0 * cl * v.y);
 }
 
+// a0[r][i][f] = e^{i k.x_i} coef[r][f]: the phase of each (r, i) once per block (the block's
+// 256 values span at most 256 / P + 2 sites), shared by its P coefficients
 __global__ void pw_phase_kernel(const double* __restrict__ pos, int64_t N, double k, const double* __restrict__ dirs,
                                 const double2* __restrict__ coef, int R, int P, double2* __restrict__ a0) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)R * N * P) return;
-  int f = (int)(t % P);
-  int64_t i = (t / P) % N;
-  int r = (int)(t / ((int64_t)P * N));
-  double sb, cb, sa, ca;
-  sincos(dirs[2 * r], &sb, &cb);
-  sincos(dirs[2 * r + 1], &sa, &ca);
-  double ph = k * (sb * ca * pos[3 * i] + sb * sa * pos[3 * i + 1] + cb * pos[3 * i + 2]);
-  double s, c;
-  sincos(ph, &s, &c);
-  a0[t] = cmul(make_double2(c, s), coef[r * P + f]);
+  __shared__ double2 eph[258];
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x;
+  const int64_t tot = (int64_t)R * N * P;
+  const int64_t g0 = t0 / P;  // first (r, i) of the block, g = r N + i
+  const int64_t glast = (min(t0 + (int64_t)blockDim.x, tot) - 1) / P;
+  for (int64_t g = g0 + threadIdx.x; g <= glast; g += blockDim.x) {
+    const int r = (int)(g / N);
+    const int64_t i = g - (int64_t)r * N;
+    double sb, cb, sa, ca;
+    sincos(dirs[2 * r], &sb, &cb);
+    sincos(dirs[2 * r + 1], &sa, &ca);
+    const double ph = k * (sb * ca * pos[3 * i] + sb * sa * pos[3 * i + 1] + cb * pos[3 * i + 2]);
+    double s, c;
+    sincos(ph, &s, &c);
+    eph[g - g0] = make_double2(c, s);
+  }
+  __syncthreads();
+  const int64_t t = t0 + threadIdx.x;
+  if (t >= tot) return;
+  const int f = (int)(t % P);
+  const int r = (int)(t / ((int64_t)P * N));
+  a0[t] = cmul(eph[t / P - g0], coef[r * P + f]);
 }
 
 // xi(k d) for general displacements: one block per displacement.

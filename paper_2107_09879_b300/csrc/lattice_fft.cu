@@ -913,8 +913,22 @@ fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, fl
 // C[item][c][u][v] = ph(f1) Bs[(c L + u) L + J(v)][f1] (-1)^(m_v) from the stored spectra
 // (component-major, with the compact-grid shift phase, undone here); item = kx * hy + ky,
 // class blocks SC complex values apart (the padding is left zero).
-__global__ void fft_pack_quad_kernel(const float2* __restrict__ Bs, int Mx, int My, int L, int SC, int CX, int CY,
-                                     const int* __restrict__ sym, float2* __restrict__ Cq) {
+// the shift phase of every item, once (the pack kernel reads it for all 2 L^2 entries)
+__global__ void fft_quad_phase_kernel(int Mx, int My, int CX, int CY, float2* __restrict__ ph) {
+  const int hy = My >= 2 ? My / 2 + 1 : 1, hx = Mx >= 2 ? Mx / 2 + 1 : 1;
+  const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (item >= (int64_t)hx * hy) return;
+  const int kx = (int)(item / hy), ky = (int)(item % hy);
+  const int64_t F = (int64_t)Mx * My;
+  const int64_t num = ((int64_t)kx * CX * My + (int64_t)ky * CY * Mx) % F;
+  double sn, cs;
+  sincospi(2.0 * (double)num / (double)F, &sn, &cs);
+  ph[item] = make_float2((float)cs, (float)sn);
+}
+
+__global__ void fft_pack_quad_kernel(const float2* __restrict__ Bs, int Mx, int My, int L, int SC,
+                                     const float2* __restrict__ ph, const int* __restrict__ sym,
+                                     float2* __restrict__ Cq) {
   const int hy = My >= 2 ? My / 2 + 1 : 1, hx = Mx >= 2 ? Mx / 2 + 1 : 1;
   const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int e = blockIdx.y;  // (c, u, v)
@@ -922,12 +936,9 @@ __global__ void fft_pack_quad_kernel(const float2* __restrict__ Bs, int Mx, int 
   const int c = e / (L * L), u = (e / L) % L, v = e % L;
   const int kx = (int)(item / hy), ky = (int)(item % hy);
   const int64_t F = (int64_t)Mx * My, f1 = (int64_t)kx * My + ky;
-  const int64_t num = ((int64_t)kx * CX * My + (int64_t)ky * CY * Mx) % F;
-  double sn, cs;
-  sincospi(2.0 * (double)num / (double)F, &sn, &cs);
   const int sv = sym[c * L + v];
   const float2 b = Bs[((int64_t)(c * L + u) * L + (sv & 0xffff)) * F + f1];
-  float2 z = cmul(make_float2((float)cs, (float)sn), b);
+  float2 z = cmul(ph[item], b);
   if ((sv >> 16) & 1) z = make_float2(-z.x, -z.y);
   Cq[(item * 2 + c) * SC + u * L + v] = z;
 }
@@ -1000,8 +1011,12 @@ static int fft_prepare_t(tmat_ctx* ctx, LatOp* a, const char* name) {
     TM_TRY(scratch(ctx, "fft_quad_err", sizeof(int), (void**)&err));
     TM_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
     TM_CUDA(ctx, cudaMemsetAsync(Cq, 0, sizeof(float2) * items * 2 * SC, ctx->stream));
+    float2* qph;
+    TM_TRY(scratch(ctx, "fft_quad_ph", sizeof(float2) * items, (void**)&qph));
+    fft_quad_phase_kernel<<<(unsigned)cdiv(items, 128), 128, 0, ctx->stream>>>(Mx, My, a->CX, a->CY, qph);
+    TM_LAUNCHED(ctx);
     dim3 g((unsigned)cdiv(items, 128), (unsigned)(2 * L * L));
-    fft_pack_quad_kernel<<<g, 128, 0, ctx->stream>>>((const float2*)Bh, Mx, My, L, SC, a->CX, a->CY, a->fft_sym, Cq);
+    fft_pack_quad_kernel<<<g, 128, 0, ctx->stream>>>((const float2*)Bh, Mx, My, L, SC, qph, a->fft_sym, Cq);
     TM_LAUNCHED(ctx);
     a->fft_C = Cq;
     a->fft_err = err;
