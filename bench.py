@@ -1043,6 +1043,8 @@ def launch_summary(path):
         if len(r) <= vi or r[mi] != "gpu__time_duration.sum":
             continue
         name = r[ki].split("(")[0].replace("void ", "")
+        if "fma_peak_kernel" in name:  # the start-up FMA probe of bench.py, not the workload
+            continue
         agg[name][0] += 1
         agg[name][1] += float(r[vi].replace(",", "")) * scale[r[ui]]
     tot = sum(v[1] for v in agg.values())
