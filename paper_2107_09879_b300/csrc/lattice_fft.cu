@@ -374,16 +374,42 @@ constexpr int F256_RS2 = 16 * 17 + 1;  // exchange stride of a row (odd: conflic
 
 // EMB: 0 plain input, 2 input times T (same layout, T's RHS stride tstride); EXT: -1 plain
 // output, 0 y = x - T s, 1 y = x - s, 2 y = s with s = scale * value (x, T in the output's layout)
+// EXT 0 stages its x and T elements in shared memory with cp.async before the transform (x into
+// a dynamic buffer of 16 x 256 values at the start, T into the exchange buffer once it is
+// free), so the epilogue does not wait on global loads; slot k2 * 256 + thread of either buffer
+// is read by the thread that copied it.
+__device__ __forceinline__ void f256_cp8(float2* dst, const float2* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src) : "memory");
+}
+constexpr size_t F256_PF_SMEM = sizeof(float2) * 16 * 256;
+
 template <bool IN_CI, bool OUT_CI, int EMB, int EXT>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, EXT == 0 ? 3 : 4)
 fft256_ci_kernel(const float2* __restrict__ in, F256Lay li, int cin, float2* __restrict__ out, F256Lay lo, int cout,
                  int P, int dir, const double2* __restrict__ tw, const float2* __restrict__ T, int64_t tstride,
                  const float2* __restrict__ xs, float scale) {
+  static_assert(EXT != 0 || OUT_CI, "the staged epilogue assumes the component-innermost output mapping");
   __shared__ float2 W[256];
   __shared__ float2 ex[16 * F256_RS2];
+  extern __shared__ float2 f256_pf[];
   const int line = blockIdx.x;
   const int r = blockIdx.z;
   const int c0 = blockIdx.y * 16;
+  // output-side indexing of the second half (thread: row rr, column k1)
+  const int rr_o = OUT_CI ? (threadIdx.x & 15) : (threadIdx.x >> 4);
+  const int k1_o = OUT_CI ? (threadIdx.x >> 4) : (threadIdx.x & 15);
+  const int64_t obase =
+      (int64_t)r * lo.rstride + (int64_t)(c0 + rr_o) * lo.cstride + (int64_t)line * lo.lstride;
+  if constexpr (EXT == 0) {
+    if (c0 + rr_o < P) {
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) {
+        const int k = k1_o + 16 * k2;
+        if (k < cout) f256_cp8(f256_pf + k2 * 256 + threadIdx.x, xs + obase + (int64_t)k * lo.estride);
+      }
+    }
+  }
   for (int m = threadIdx.x; m < 256; m += blockDim.x) {
     const double2 t = tw[4 * (m & 127)];
     const float sg = m < 128 ? 1.f : -1.f;
@@ -416,28 +442,39 @@ fft256_ci_kernel(const float2* __restrict__ in, F256Lay li, int cin, float2* __r
   }
   __syncthreads();
   // second half: thread (row rr, k1) owns X[k1 + 16 k2]
-  const int rr = OUT_CI ? (threadIdx.x & 15) : (threadIdx.x >> 4);
-  const int k1 = OUT_CI ? (threadIdx.x >> 4) : (threadIdx.x & 15);
+  const int rr = rr_o;
+  const int k1 = k1_o;
   float2 v[16];
   const float2* exr = ex + rr * F256_RS2;
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = exr[k1 * 17 + q];
-  fft_dft16(v, W, dir);
   const int c = c0 + rr;
+  if constexpr (EXT == 0) {
+    __syncthreads();  // every row has left the exchange buffer
+    if (c < P) {
+      const float2* Tr = T + (int64_t)r * tstride - (int64_t)r * lo.rstride;
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) {
+        const int k = k1 + 16 * k2;
+        if (k < cout) f256_cp8(ex + k2 * 256 + threadIdx.x, Tr + obase + (int64_t)k * lo.estride);
+      }
+    }
+  }
+  fft_dft16(v, W, dir);
   if (c >= P) return;
-  const int64_t base = (int64_t)r * lo.rstride + (int64_t)c * lo.cstride + (int64_t)line * lo.lstride;
+  if constexpr (EXT == 0) asm volatile("cp.async.wait_all;\n" ::: "memory");
 #pragma unroll
   for (int k2 = 0; k2 < 16; ++k2) {
     const int k = k1 + 16 * k2;
     if (k >= cout) continue;
-    const int64_t o = base + (int64_t)k * lo.estride;
+    const int64_t o = obase + (int64_t)k * lo.estride;
     if (EXT < 0) {
       out[o] = v[k2];
     } else {
       const float2 s = cscale(v[k2], scale);
       if (EXT == 2) out[o] = s;
       else if (EXT == 1) out[o] = csub(xs[o], s);
-      else out[o] = csub(xs[o], cmul(T[(int64_t)r * tstride + o - (int64_t)r * lo.rstride], s));
+      else out[o] = csub(f256_pf[k2 * 256 + threadIdx.x], cmul(ex[k2 * 256 + threadIdx.x], s));
     }
   }
 }
@@ -1127,8 +1164,10 @@ static int fft_apply_t(tmat_ctx* ctx, const LatOp& a, const void* xv, void* yv, 
       fft256_ci_kernel<false, true, 0, -1><<<gk, 256, 0, ctx->stream>>>(Yh, lspec, My, w1, lt2_out, ny, P, +1, tw, T,
                                                                          a.t_stride, nullptr, 1.f);
       TM_LAUNCHED(ctx);
-      fft256_ci_kernel<true, true, 0, MODE><<<gy, 256, 0, ctx->stream>>>(w1, lt2_in, Mx, (float2*)yv, lx, nx, P, +1, tw,
-                                                                          T, a.t_stride, x, (float)(1.0 / (double)F));
+      const size_t pf = MODE == 0 ? F256_PF_SMEM : 0;
+      if (MODE == 0) TM_TRY(set_smem_limit(ctx, (const void*)fft256_ci_kernel<true, true, 0, MODE>, pf));
+      fft256_ci_kernel<true, true, 0, MODE><<<gy, 256, pf, ctx->stream>>>(w1, lt2_in, Mx, (float2*)yv, lx, nx, P, +1,
+                                                                           tw, T, a.t_stride, x, (float)(1.0 / (double)F));
       TM_LAUNCHED(ctx);
     }
   } else {
