@@ -169,6 +169,7 @@ extern "C" int tmat_ctx_destroy(tmat_ctx* ctx) {
   for (auto& kv : ctx->bufs) cudaFree(kv.second.p);
   for (auto& kv : ctx->tables) free_tables(kv.second);
   drop_events(ctx, true);
+  if (ctx->flag_event) cudaEventDestroy(ctx->flag_event);
   cudaFreeHost(ctx->pinned);
   delete ctx;
   return TMAT_OK;

@@ -1182,15 +1182,20 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
           TM_LAUNCHED(ctx);
           dcgs2_small_kernel<<<R, 256, gsm_bytes, ctx->stream>>>(s, j, m, maxv, R, final_only ? 1 : 0);
           TM_LAUNCHED(ctx);
-          bool any = true;
-          if (j >= 1 && (final_only || j % sync_every == 0)) {
-            int* ipin = (int*)ctx->pinned;
+          // The flags are copied out behind the small kernel and read while the update pass
+          // runs (it skips every RHS that has converged), so the device does not idle through
+          // the host's check before the next operator launch.
+          const bool check = j >= 1 && (final_only || j % sync_every == 0);
+          int* ipin = (int*)ctx->pinned;
+          if (check) {
+            if (!ctx->flag_event) TM_CUDA(ctx, cudaEventCreateWithFlags(&ctx->flag_event, cudaEventDisableTiming));
             TM_CUDA(ctx, cudaMemcpyAsync(ipin, s.active, sizeof(int) * R, cudaMemcpyDeviceToHost, ctx->stream));
-            TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-            any = false;
-            for (int r = 0; r < R; ++r) any = any || ipin[r];
+            TM_CUDA(ctx, cudaEventRecord(ctx->flag_event, ctx->stream));
           }
-          if (final_only || !any) break;
+          if (final_only) {
+            if (check) TM_CUDA(ctx, cudaEventSynchronize(ctx->flag_event));
+            break;
+          }
           cudaEvent_t ev_u = timing_begin(ctx);
           if (h16) {
             const unsigned gu = (unsigned)std::min<int64_t>(cdiv(n / 2, 256), (int64_t)ctx->num_sms * 16);
@@ -1205,6 +1210,12 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
           // the fp32 pending vector and w; writes fp16 slot j and w)
           timing_end(ctx, "arnoldi_update32", ev_u,
                      h16 ? 4.0 * R * n * (j + 1) + 8.0 * R * n * 3 : 8.0 * R * n * (j + 2 + (j > 0 ? 1 : 0) + 1));
+          if (check) {
+            TM_CUDA(ctx, cudaEventSynchronize(ctx->flag_event));
+            bool any = false;
+            for (int r = 0; r < R; ++r) any = any || ipin[r];
+            if (!any) break;
+          }
         }
         // columns 0..j-1 are final
       } else

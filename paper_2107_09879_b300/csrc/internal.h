@@ -90,6 +90,7 @@ struct tmat_ctx {
   bool fft_quad = true;      // complex64 FFT block products in the quad-mirror form
   bool field_mixed = false;  // near fields in fp32 with fp64 phases (tmat_ctx_set_field_precision)
   void* pinned = nullptr;  // small pinned host staging area (status words)
+  cudaEvent_t flag_event = nullptr;  // marks the copy of convergence flags into `pinned`
 };
 
 namespace tmat {
