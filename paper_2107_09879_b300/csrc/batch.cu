@@ -171,6 +171,7 @@ extern "C" int tmat_solve_batch(tmat_ctx* ctx, const tmat_batch_problem* probs, 
   bops.lat64.t_stride = Nc * P;
   bops.lat64.fft_Bhat = B64;
   bops.lat64.fft_bstride = s64;
+  bops.lat64.fft_C = nullptr;  // per-problem spectra: the mirror-pair product
   bops.A64.kind = 1;
   bops.A64.lat = &bops.lat64;
   if (mixed) {

@@ -267,18 +267,21 @@ fft_rows_kernel(const GI* __restrict__ in, int64_t in_batch_stride, int in_pitch
 // store per value, no bit reversal, one shared-memory round trip (the generic kernel
 // makes three). 16 rows per block of 256 threads. W[m] = W256^m of the direction (forward
 // e^{-2 pi i m / 256}, inverse its conjugate).
-__device__ __forceinline__ void fft_dft4(float2& a, float2& b, float2& c, float2& d, int dir) {
-  const float2 t0 = cadd(a, c), t1 = csub(a, c), t2 = cadd(b, d), t3 = crot<float>(csub(b, d), dir);
+// radix-4 butterfly and 16-point DFT in registers, for complex64 (CR = float) and
+// double-float (CR = DF) values
+template <typename CR>
+__device__ __forceinline__ void fft_dft4(C<CR>& a, C<CR>& b, C<CR>& c, C<CR>& d, int dir) {
+  const C<CR> t0 = cadd(a, c), t1 = csub(a, c), t2 = cadd(b, d), t3 = crot<CR>(csub(b, d), dir);
   a = cadd(t0, t2);
   c = csub(t0, t2);
   b = cadd(t1, t3);
   d = csub(t1, t3);
 }
-// in-place 16-point DFT of v (index n in, index k out, natural order), W16^m = W[16 m]
-__device__ __forceinline__ void fft_dft16(float2 (&v)[16], const float2* W, int dir) {
+template <typename CR>
+__device__ __forceinline__ void fft_dft16(C<CR> (&v)[16], const C<CR>* W, int dir) {
   // n = n1 + 4 n2: DFT4 over n2 for each n1 (outputs k' = 0..3 in place of n2)
 #pragma unroll
-  for (int n1 = 0; n1 < 4; ++n1) fft_dft4(v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12], dir);
+  for (int n1 = 0; n1 < 4; ++n1) fft_dft4<CR>(v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12], dir);
   // twiddles W16^(n1 k')
 #pragma unroll
   for (int n1 = 1; n1 < 4; ++n1)
@@ -286,9 +289,9 @@ __device__ __forceinline__ void fft_dft16(float2 (&v)[16], const float2* W, int 
     for (int kp = 1; kp < 4; ++kp) v[n1 + 4 * kp] = cmul(v[n1 + 4 * kp], W[16 * n1 * kp]);
   // DFT4 over n1 for each k': X[k' + 4 k2] lands at position 4 k' + k2
 #pragma unroll
-  for (int kp = 0; kp < 4; ++kp) fft_dft4(v[4 * kp], v[4 * kp + 1], v[4 * kp + 2], v[4 * kp + 3], dir);
+  for (int kp = 0; kp < 4; ++kp) fft_dft4<CR>(v[4 * kp], v[4 * kp + 1], v[4 * kp + 2], v[4 * kp + 3], dir);
   // reorder position 4 k' + k2 -> index k' + 4 k2 (a fixed permutation of registers)
-  float2 o[16];
+  C<CR> o[16];
 #pragma unroll
   for (int kp = 0; kp < 4; ++kp)
 #pragma unroll
@@ -296,6 +299,7 @@ __device__ __forceinline__ void fft_dft16(float2 (&v)[16], const float2* W, int 
 #pragma unroll
   for (int k = 0; k < 16; ++k) v[k] = o[k];
 }
+
 
 constexpr int F256_RS = 16 * 17;  // exchange stride of a row (k1 blocks of 17)
 constexpr int F256_OS = 257;      // staging stride of a row for transposed stores
@@ -327,7 +331,7 @@ fft256_rows_kernel(const float2* __restrict__ in, int64_t in_batch_stride, int i
     v[q] = (live && c < cin) ? src[c] : make_float2(0.f, 0.f);
   }
   __syncthreads();  // W
-  fft_dft16(v, W, dir);  // v[k1] = Y[a][k1]
+  fft_dft16<float>(v, W, dir);  // v[k1] = Y[a][k1]
   float2* exr = ex + rr * F256_RS;
 #pragma unroll
   for (int k1 = 0; k1 < 16; ++k1) exr[k1 * 17 + a] = k1 ? cmul(v[k1], W[(a * k1) & 255]) : v[k1];
@@ -335,7 +339,7 @@ fft256_rows_kernel(const float2* __restrict__ in, int64_t in_batch_stride, int i
   const int k1 = a;  // this thread now owns column k1: Y[a'][k1] for a' = 0..15
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = exr[k1 * 17 + q];
-  fft_dft16(v, W, dir);  // v[k2] = X[k1 + 16 k2]
+  fft_dft16<float>(v, W, dir);  // v[k2] = X[k1 + 16 k2]
   float2* dst = out + (int64_t)b * out_batch_stride;
   if (TOUT) {
     __syncthreads();  // every row's exchange reads are done before the staging overwrites
@@ -357,7 +361,7 @@ fft256_rows_kernel(const float2* __restrict__ in, int64_t in_batch_stride, int i
 }
 
 
-// ---- 256 x 256 complex64 transforms without transposes ------------------------------------
+// ---- 256 x 256 transforms without transposes -------------------------------------------
 // Every pass takes blocks of 16 consecutive components c of one right-hand side r and one
 // line: a row of the pass is (r, c, line) with elements at
 //   r rstride + c cstride + line lstride + col estride,
@@ -366,33 +370,48 @@ fft256_rows_kernel(const float2* __restrict__ in, int64_t in_batch_stride, int i
 // with consecutive threads on consecutive components; component-major ones (the spectra
 // [r P + c][kx][ky]) with consecutive threads along a row. The first forward pass reads x
 // (T x for the adjoint) in place and the last inverse pass writes y = x - T s (or x - s, s)
-// in place, so the operator needs no embed or extract kernels.
+// in place, so the operator needs no embed or extract kernels. CR = float: complex64
+// throughout; CR = DF: x, y and T complex128, the intermediates and spectra double-float
+// pairs (IN_S / OUT_S: the input / output is in that storage form), arithmetic in
+// double-float.
 struct F256Lay {
   int64_t rstride, cstride, lstride, estride;
 };
 constexpr int F256_RS2 = 16 * 17 + 1;  // exchange stride of a row (odd: conflict-free in both mappings)
 
-// EMB: 0 plain input, 2 input times T (same layout, T's RHS stride tstride); EXT: -1 plain
-// output, 0 y = x - T s, 1 y = x - s, 2 y = s with s = scale * value (x, T in the output's layout)
-// EXT 0 stages its x and T elements in shared memory with cp.async before the transform (x into
-// a dynamic buffer of 16 x 256 values at the start, T into the exchange buffer once it is
-// free), so the epilogue does not wait on global loads; slot k2 * 256 + thread of either buffer
-// is read by the thread that copied it.
+// The complex64 EXT 0 pass stages its x and T elements in shared memory with cp.async before
+// the transform (x into a buffer of 16 x 256 values at the start, T into the exchange buffer
+// once it is free), so the epilogue does not wait on global loads; slot k2 * 256 + thread of
+// either buffer is read by the thread that copied it.
 __device__ __forceinline__ void f256_cp8(float2* dst, const float2* src) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src) : "memory");
 }
-constexpr size_t F256_PF_SMEM = sizeof(float2) * 16 * 256;
+template <typename CR, int EXT> struct F256Smem {
+  static constexpr bool PF = EXT == 0 && std::is_same_v<CR, float>;
+  static constexpr size_t W_BYTES = 256 * sizeof(C<CR>);
+  static constexpr size_t EX_BYTES = 16 * F256_RS2 * sizeof(C<CR>);
+  static constexpr size_t BYTES = W_BYTES + EX_BYTES + (PF ? sizeof(float2) * 16 * 256 : 0);
+  static constexpr int MIN_BLOCKS = std::is_same_v<CR, float> ? (EXT == 0 ? 3 : 4) : 2;
+};
+template <typename CR> __device__ __forceinline__ C<CR> f256_scale(C<CR> v, float s) { return cscale(v, s); }
+template <> __device__ __forceinline__ dfc f256_scale<DF>(dfc v, float s) { return cscale_df(v, s, 0.f); }
 
-template <bool IN_CI, bool OUT_CI, int EMB, int EXT>
-__global__ void __launch_bounds__(256, EXT == 0 ? 3 : 4)
-fft256_ci_kernel(const float2* __restrict__ in, F256Lay li, int cin, float2* __restrict__ out, F256Lay lo, int cout,
-                 int P, int dir, const double2* __restrict__ tw, const float2* __restrict__ T, int64_t tstride,
-                 const float2* __restrict__ xs, float scale) {
+// EMB: 0 plain input, 2 input times T (same layout, T's RHS stride tstride); EXT: -1 plain
+// output, 0 y = x - T s, 1 y = x - s, 2 y = s with s = scale * value (x, T in the output's layout)
+template <typename CR, bool IN_CI, bool OUT_CI, int EMB, int EXT, bool IN_S, bool OUT_S>
+__global__ void __launch_bounds__(256, F256Smem<CR, EXT>::MIN_BLOCKS)
+fft256_ci_kernel(const std::conditional_t<IN_S, C<CR>, G<CR>>* __restrict__ in, F256Lay li, int cin,
+                 std::conditional_t<OUT_S, C<CR>, G<CR>>* __restrict__ out, F256Lay lo, int cout, int P, int dir,
+                 const double2* __restrict__ tw, const G<CR>* __restrict__ T, int64_t tstride,
+                 const G<CR>* __restrict__ xs, float scale) {
+  using CT = C<CR>;
+  using SM = F256Smem<CR, EXT>;
   static_assert(EXT != 0 || OUT_CI, "the staged epilogue assumes the component-innermost output mapping");
-  __shared__ float2 W[256];
-  __shared__ float2 ex[16 * F256_RS2];
-  extern __shared__ float2 f256_pf[];
+  extern __shared__ __align__(16) unsigned char f256_sm[];
+  CT* W = reinterpret_cast<CT*>(f256_sm);
+  CT* ex = reinterpret_cast<CT*>(f256_sm + SM::W_BYTES);
+  float2* pf = reinterpret_cast<float2*>(f256_sm + SM::W_BYTES + SM::EX_BYTES);  // x (staged pass)
   const int line = blockIdx.x;
   const int r = blockIdx.z;
   const int c0 = blockIdx.y * 16;
@@ -401,19 +420,25 @@ fft256_ci_kernel(const float2* __restrict__ in, F256Lay li, int cin, float2* __r
   const int k1_o = OUT_CI ? (threadIdx.x >> 4) : (threadIdx.x & 15);
   const int64_t obase =
       (int64_t)r * lo.rstride + (int64_t)(c0 + rr_o) * lo.cstride + (int64_t)line * lo.lstride;
-  if constexpr (EXT == 0) {
+  if constexpr (SM::PF) {
     if (c0 + rr_o < P) {
 #pragma unroll
       for (int k2 = 0; k2 < 16; ++k2) {
         const int k = k1_o + 16 * k2;
-        if (k < cout) f256_cp8(f256_pf + k2 * 256 + threadIdx.x, xs + obase + (int64_t)k * lo.estride);
+        if (k < cout)
+          f256_cp8(pf + k2 * 256 + threadIdx.x, reinterpret_cast<const float2*>(xs) + obase + (int64_t)k * lo.estride);
       }
     }
   }
   for (int m = threadIdx.x; m < 256; m += blockDim.x) {
     const double2 t = tw[4 * (m & 127)];
-    const float sg = m < 128 ? 1.f : -1.f;
-    W[m] = make_float2(sg * (float)t.x, sg * (dir < 0 ? (float)t.y : -(float)t.y));
+    if constexpr (std::is_same_v<CR, float>) {  // no fp64 arithmetic in the complex64 passes
+      const float sg = m < 128 ? 1.f : -1.f;
+      W[m] = make_float2(sg * (float)t.x, sg * (dir < 0 ? (float)t.y : -(float)t.y));
+    } else {
+      const C<CR> w = cfrom64<CR>(t.x, dir < 0 ? t.y : -t.y);  // exact negation below
+      W[m] = m < 128 ? w : cneg(w);
+    }
   }
   // first half: thread (row rr, column a) holds x[a + 16 b]
   {
@@ -422,21 +447,22 @@ fft256_ci_kernel(const float2* __restrict__ in, F256Lay li, int cin, float2* __r
     const int c = c0 + rr;
     const bool live = c < P;
     const int64_t base = (int64_t)r * li.rstride + (int64_t)c * li.cstride + (int64_t)line * li.lstride;
-    float2 v[16];
+    CT v[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int col = a + 16 * q;
-      float2 e = make_float2(0.f, 0.f);
+      CT e = czero<CR>();
       if (live && col < cin) {
         const int64_t o = base + (int64_t)col * li.estride;
-        e = in[o];
-        if (EMB == 2) e = cmul(T[(int64_t)r * tstride + o - (int64_t)r * li.rstride], e);
+        if constexpr (IN_S) e = in[o];
+        else e = gload<CR>(in[o]);
+        if (EMB == 2) e = cmul(gload<CR>(T[(int64_t)r * tstride + o - (int64_t)r * li.rstride]), e);
       }
       v[q] = e;
     }
     __syncthreads();  // W
-    fft_dft16(v, W, dir);
-    float2* exr = ex + rr * F256_RS2;
+    fft_dft16<CR>(v, W, dir);
+    CT* exr = ex + rr * F256_RS2;
 #pragma unroll
     for (int k1 = 0; k1 < 16; ++k1) exr[k1 * 17 + a] = k1 ? cmul(v[k1], W[(a * k1) & 255]) : v[k1];
   }
@@ -444,38 +470,49 @@ fft256_ci_kernel(const float2* __restrict__ in, F256Lay li, int cin, float2* __r
   // second half: thread (row rr, k1) owns X[k1 + 16 k2]
   const int rr = rr_o;
   const int k1 = k1_o;
-  float2 v[16];
-  const float2* exr = ex + rr * F256_RS2;
+  CT v[16];
+  const CT* exr = ex + rr * F256_RS2;
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = exr[k1 * 17 + q];
   const int c = c0 + rr;
-  if constexpr (EXT == 0) {
+  if constexpr (SM::PF) {
     __syncthreads();  // every row has left the exchange buffer
     if (c < P) {
-      const float2* Tr = T + (int64_t)r * tstride - (int64_t)r * lo.rstride;
+      const float2* Tr = reinterpret_cast<const float2*>(T) + (int64_t)r * tstride - (int64_t)r * lo.rstride;
+      float2* ts = reinterpret_cast<float2*>(ex);
 #pragma unroll
       for (int k2 = 0; k2 < 16; ++k2) {
         const int k = k1 + 16 * k2;
-        if (k < cout) f256_cp8(ex + k2 * 256 + threadIdx.x, Tr + obase + (int64_t)k * lo.estride);
+        if (k < cout) f256_cp8(ts + k2 * 256 + threadIdx.x, Tr + obase + (int64_t)k * lo.estride);
       }
     }
   }
-  fft_dft16(v, W, dir);
+  fft_dft16<CR>(v, W, dir);
   if (c >= P) return;
-  if constexpr (EXT == 0) asm volatile("cp.async.wait_all;\n" ::: "memory");
+  if constexpr (SM::PF) asm volatile("cp.async.wait_all;\n" ::: "memory");
 #pragma unroll
   for (int k2 = 0; k2 < 16; ++k2) {
     const int k = k1 + 16 * k2;
     if (k >= cout) continue;
     const int64_t o = obase + (int64_t)k * lo.estride;
-    if (EXT < 0) {
-      out[o] = v[k2];
+    CT res;
+    if constexpr (EXT < 0) {
+      res = v[k2];
     } else {
-      const float2 s = cscale(v[k2], scale);
-      if (EXT == 2) out[o] = s;
-      else if (EXT == 1) out[o] = csub(xs[o], s);
-      else out[o] = csub(f256_pf[k2 * 256 + threadIdx.x], cmul(ex[k2 * 256 + threadIdx.x], s));
+      const CT s = f256_scale<CR>(v[k2], scale);
+      if constexpr (EXT == 2) {
+        res = s;
+      } else if constexpr (EXT == 1) {
+        res = csub(gload<CR>(xs[o]), s);
+      } else if constexpr (SM::PF) {
+        const float2* ts = reinterpret_cast<const float2*>(ex);
+        res = csub(pf[k2 * 256 + threadIdx.x], cmul(ts[k2 * 256 + threadIdx.x], s));
+      } else {
+        res = csub(gload<CR>(xs[o]), cmul(gload<CR>(T[(int64_t)r * tstride + o - (int64_t)r * lo.rstride]), s));
+      }
     }
+    if constexpr (OUT_S) out[o] = res;
+    else out[o] = gstore<CR>(res);
   }
 }
 
@@ -735,7 +772,7 @@ fft_mul_kernel(const C<R>* __restrict__ Bh, const C<R>* __restrict__ Xh, C<R>* _
 // conflicts) and the column values by broadcast.
 constexpr uint32_t FFT4_WAIT_LIMIT = 1u << 22;  // polls of a bounded mbarrier wait
 
-template <int L, int RC_ = 2>
+template <int L, int RC_ = 2, typename CR = float>
 struct Fft4Cfg {
   static constexpr int NI = L <= 24 ? 4 : 2;  // items (consecutive ky) per tile
   static constexpr int THREADS = NI * 2 * L;
@@ -749,10 +786,11 @@ struct Fft4Cfg {
   // values past a multiple of 64 bytes, so the class-0 and class-1 lanes of a warp (two
   // broadcast addresses per 16-byte load) fall on different banks
   static constexpr int SW = L * NCOL + 2;
-  static constexpr size_t C_BYTES = (size_t)NI * 2 * SC * sizeof(float2);
-  static constexpr size_t W_BYTES = (size_t)NI * 2 * SW * sizeof(float2);
+  static constexpr size_t C_BYTES = (size_t)NI * 2 * SC * sizeof(C<CR>);
+  static constexpr size_t W_BYTES = (size_t)NI * 2 * SW * sizeof(C<CR>);
   static constexpr size_t SMEM = C_BYTES + W_BYTES + 16;
-  static constexpr int MIN_BLOCKS = L <= 24 ? 4 : 2;  // resident CTAs per SM the registers allow
+  // resident CTAs per SM the registers allow (double-float: shared memory allows two)
+  static constexpr int MIN_BLOCKS = std::is_same_v<CR, float> ? (L <= 24 ? 4 : 2) : (L <= 24 ? 2 : 1);
 };
 
 // sign selector: 0 none, 1 Dx = (-1)^(m+p), 2 Dy = (-1)^p, 3 Dm = (-1)^m
@@ -781,17 +819,20 @@ __device__ __forceinline__ int fft4_out_s(int k) { return k == 0 ? 0 : (k == 1 ?
 
 // cstride: complex values between the spectra of consecutive RHS (0: one operator for all
 // RHS; otherwise RC = 1 and every RHS pass stages its own C)
-template <int L, int MODE, int RC_>
-__global__ void __launch_bounds__(Fft4Cfg<L, RC_>::THREADS, Fft4Cfg<L, RC_>::MIN_BLOCKS)
-fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, float2* __restrict__ Yh, int Mx, int My,
+// CR = float: complex64 spectra and arithmetic; CR = DF: double-float pairs (the complex128
+// operators' fp64-accurate residuals), the same maps and staging.
+template <typename CR, int L, int MODE, int RC_>
+__global__ void __launch_bounds__(Fft4Cfg<L, RC_, CR>::THREADS, Fft4Cfg<L, RC_, CR>::MIN_BLOCKS)
+fft_mul4_kernel(const C<CR>* __restrict__ Cq, const C<CR>* __restrict__ Xh, C<CR>* __restrict__ Yh, int Mx, int My,
                 int R_, const int* __restrict__ sym, int* __restrict__ err, int64_t cstride) {
-  using Cfg = Fft4Cfg<L, RC_>;
+  using Cfg = Fft4Cfg<L, RC_, CR>;
+  using CT = C<CR>;
   constexpr int NI = Cfg::NI, RC = Cfg::RC, NCOL = Cfg::NCOL, P = 2 * L, SC = Cfg::SC, SW = Cfg::SW,
                 NT = Cfg::THREADS;
   constexpr int D = MODE == 1 ? 1 : 0;
   extern __shared__ __align__(128) unsigned char fsm4[];
-  float2* Cs = reinterpret_cast<float2*>(fsm4);                  // [NI][2][SC]
-  float2* Ws = reinterpret_cast<float2*>(fsm4 + Cfg::C_BYTES);   // [NI][2][SW >= L * NCOL]
+  CT* Cs = reinterpret_cast<CT*>(fsm4);                  // [NI][2][SC]
+  CT* Ws = reinterpret_cast<CT*>(fsm4 + Cfg::C_BYTES);   // [NI][2][SW >= L * NCOL]
   const uint32_t bar = (uint32_t)__cvta_generic_to_shared(fsm4 + Cfg::C_BYTES + Cfg::W_BYTES);
   const uint32_t cs_addr = (uint32_t)__cvta_generic_to_shared(Cs);
   const int t = threadIdx.x;
@@ -818,8 +859,8 @@ fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, fl
   auto issue_c = [&](int64_t tl, int r0) {
     int kx, ky0, ni;
     tile_of(tl, kx, ky0, ni);
-    const uint32_t bytes = (uint32_t)(ni * 2 * SC * sizeof(float2));
-    const float2* src = Cq + (int64_t)r0 * cstride + ((int64_t)kx * hy + ky0) * 2 * SC;
+    const uint32_t bytes = (uint32_t)(ni * 2 * SC * sizeof(CT));
+    const CT* src = Cq + (int64_t)r0 * cstride + ((int64_t)kx * hy + ky0) * 2 * SC;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
@@ -827,7 +868,7 @@ fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, fl
   };
   // load role: value e = t + j NT of the tile's transformed inputs, item fastest (the NI
   // items of a tile are consecutive frequencies: one 32-byte sector per plane for NI = 4)
-  float2 wv[NCOL];
+  CT wv[NCOL];
   auto load_w = [&](int64_t tl, int r0) {
     int kx, ky0, ni;
     tile_of(tl, kx, ky0, ni);
@@ -840,13 +881,13 @@ fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, fl
       const int cc = row / L, v = row % L, k = col / RC, q = col % RC;
       const int ky = ky0 + item, kym = (My - ky) % My;
       const bool ok = item < ni && r0 + q < R_ && ((k & 1) == 0 || kym != ky) && ((k & 2) == 0 || kxm != kx);
-      float2 w = make_float2(0.f, 0.f);
+      CT w = czero<CR>();
       if (ok) {
         const int sv = sym[cc * L + v];
         const int comp = fft4_in_j(D, k) ? (sv & 0xffff) : v;
         const int64_t f = (int64_t)((k & 2) ? kxm : kx) * My + ((k & 1) ? kym : ky);
         w = Xh[((int64_t)(r0 + q) * P + cc * L + comp) * F + f];
-        if (fft4_neg(fft4_in_s(k), (sv >> 16) & 1, (sv >> 17) & 1)) w = make_float2(-w.x, -w.y);
+        if (fft4_neg(fft4_in_s(k), (sv >> 16) & 1, (sv >> 17) & 1)) w = cneg(w);
       }
       wv[j] = w;
     }
@@ -885,32 +926,42 @@ fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, fl
         }
         return;
       }
-      float2 acc[NCOL];
+      CT acc[NCOL];
 #pragma unroll
-      for (int j = 0; j < NCOL; ++j) acc[j] = make_float2(0.f, 0.f);
-      const float2* Ci = Cs + (it * 2 + c) * SC + u;
-      const float4* Wi = reinterpret_cast<const float4*>(Ws + (it * 2 + c) * SW);
+      for (int j = 0; j < NCOL; ++j) acc[j] = czero<CR>();
+      const CT* Ci = Cs + (it * 2 + c) * SC + u;
+      if constexpr (std::is_same_v<CR, float>) {
+        const float4* Wi = reinterpret_cast<const float4*>(Ws + (it * 2 + c) * SW);
 #pragma unroll 4
-      for (int v = 0; v < L; ++v) {
-        const float2 g = Ci[v * L];
+        for (int v = 0; v < L; ++v) {
+          const float2 g = Ci[v * L];
 #pragma unroll
-        for (int j = 0; j < NCOL / 2; ++j) {
-          const float4 w2 = Wi[v * (NCOL / 2) + j];
-          cfma(acc[2 * j], g, make_float2(w2.x, w2.y));
-          cfma(acc[2 * j + 1], g, make_float2(w2.z, w2.w));
+          for (int j = 0; j < NCOL / 2; ++j) {
+            const float4 w2 = Wi[v * (NCOL / 2) + j];
+            cfma(acc[2 * j], g, make_float2(w2.x, w2.y));
+            cfma(acc[2 * j + 1], g, make_float2(w2.z, w2.w));
+          }
+        }
+      } else {
+        const CT* Wc = Ws + (it * 2 + c) * SW;
+#pragma unroll 2
+        for (int v = 0; v < L; ++v) {
+          const CT g = Ci[v * L];
+#pragma unroll
+          for (int j = 0; j < NCOL; ++j) cfma(acc[j], g, Wc[v * NCOL + j]);
         }
       }
       __syncthreads();  // every read of Cs and Ws of this stage is done
       // this thread's outputs, with their output signs, into the staging area (Ws); the
       // stores below take them item-fastest, so the NI items of a tile fill whole sectors
       {
-        float2* zrow = Ws + (it * 2 + c) * SW + u * NCOL;
+        CT* zrow = Ws + (it * 2 + c) * SW + u * NCOL;
 #pragma unroll
         for (int k = 0; k < 4; ++k)
 #pragma unroll
           for (int q = 0; q < RC; ++q) {
-            float2 z = acc[k * RC + q];
-            if (fft4_neg(fft4_out_s(k), mpar, pp)) z = make_float2(-z.x, -z.y);
+            CT z = acc[k * RC + q];
+            if (fft4_neg(fft4_out_s(k), mpar, pp)) z = cneg(z);
             zrow[k * RC + q] = z;
           }
       }
@@ -951,7 +1002,8 @@ fft_mul4_kernel(const float2* __restrict__ Cq, const float2* __restrict__ Xh, fl
 // (component-major, with the compact-grid shift phase, undone here); item = kx * hy + ky,
 // class blocks SC complex values apart (the padding is left zero).
 // the shift phase of every item, once (the pack kernel reads it for all 2 L^2 entries)
-__global__ void fft_quad_phase_kernel(int Mx, int My, int CX, int CY, float2* __restrict__ ph) {
+template <typename CR>
+__global__ void fft_quad_phase_kernel(int Mx, int My, int CX, int CY, C<CR>* __restrict__ ph) {
   const int hy = My >= 2 ? My / 2 + 1 : 1, hx = Mx >= 2 ? Mx / 2 + 1 : 1;
   const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (item >= (int64_t)hx * hy) return;
@@ -960,12 +1012,13 @@ __global__ void fft_quad_phase_kernel(int Mx, int My, int CX, int CY, float2* __
   const int64_t num = ((int64_t)kx * CX * My + (int64_t)ky * CY * Mx) % F;
   double sn, cs;
   sincospi(2.0 * (double)num / (double)F, &sn, &cs);
-  ph[item] = make_float2((float)cs, (float)sn);
+  ph[item] = cfrom64<CR>(cs, sn);
 }
 
-__global__ void fft_pack_quad_kernel(const float2* __restrict__ Bs, int Mx, int My, int L, int SC,
-                                     const float2* __restrict__ ph, const int* __restrict__ sym,
-                                     float2* __restrict__ Cq) {
+template <typename CR>
+__global__ void fft_pack_quad_kernel(const C<CR>* __restrict__ Bs, int Mx, int My, int L, int SC,
+                                     const C<CR>* __restrict__ ph, const int* __restrict__ sym,
+                                     C<CR>* __restrict__ Cq) {
   const int hy = My >= 2 ? My / 2 + 1 : 1, hx = Mx >= 2 ? Mx / 2 + 1 : 1;
   const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int e = blockIdx.y;  // (c, u, v)
@@ -974,9 +1027,9 @@ __global__ void fft_pack_quad_kernel(const float2* __restrict__ Bs, int Mx, int 
   const int kx = (int)(item / hy), ky = (int)(item % hy);
   const int64_t F = (int64_t)Mx * My, f1 = (int64_t)kx * My + ky;
   const int sv = sym[c * L + v];
-  const float2 b = Bs[((int64_t)(c * L + u) * L + (sv & 0xffff)) * F + f1];
-  float2 z = cmul(ph[item], b);
-  if ((sv >> 16) & 1) z = make_float2(-z.x, -z.y);
+  const C<CR> b = Bs[((int64_t)(c * L + u) * L + (sv & 0xffff)) * F + f1];
+  C<CR> z = cmul(ph[item], b);
+  if ((sv >> 16) & 1) z = cneg(z);
   Cq[(item * 2 + c) * SC + u * L + v] = z;
 }
 
@@ -1037,23 +1090,27 @@ static int fft_prepare_t(tmat_ctx* ctx, LatOp* a, const char* name) {
   a->fft_Bhat = Bh;
   a->use_fft = true;
   a->fft_C = nullptr;
-  if (sizeof(R) == 4 && a->fft_mirror_sign == 1 && a->fft_sym && ctx->fft_quad) {
+  // the quad-mirror form (complex64 operators, and the double-float pairs of complex128 ones)
+  if (a->fft_quad_ok && a->fft_mirror_sign == 1 && a->fft_sym && ctx->fft_quad) {
+    using CR = typename fft_compute<R>::t;
+    using CS = C<CR>;
     const int hx = Mx >= 2 ? Mx / 2 + 1 : 1, hy = My >= 2 ? My / 2 + 1 : 1;
     const int64_t items = (int64_t)hx * hy;
     const int SC = ((L * L + 7) / 16) * 16 + 8;  // Fft4Cfg<L>::SC
     std::string cn = std::string(name) + "_quad";
-    float2* Cq;
+    CS* Cq;
     int* err;
-    TM_TRY(scratch(ctx, cn.c_str(), sizeof(float2) * items * 2 * SC, (void**)&Cq));
+    TM_TRY(scratch(ctx, cn.c_str(), sizeof(CS) * items * 2 * SC, (void**)&Cq));
     TM_TRY(scratch(ctx, "fft_quad_err", sizeof(int), (void**)&err));
     TM_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
-    TM_CUDA(ctx, cudaMemsetAsync(Cq, 0, sizeof(float2) * items * 2 * SC, ctx->stream));
-    float2* qph;
-    TM_TRY(scratch(ctx, "fft_quad_ph", sizeof(float2) * items, (void**)&qph));
-    fft_quad_phase_kernel<<<(unsigned)cdiv(items, 128), 128, 0, ctx->stream>>>(Mx, My, a->CX, a->CY, qph);
+    TM_CUDA(ctx, cudaMemsetAsync(Cq, 0, sizeof(CS) * items * 2 * SC, ctx->stream));
+    CS* qph;
+    TM_TRY(scratch(ctx, "fft_quad_ph", sizeof(CS) * items, (void**)&qph));
+    fft_quad_phase_kernel<CR><<<(unsigned)cdiv(items, 128), 128, 0, ctx->stream>>>(Mx, My, a->CX, a->CY, qph);
     TM_LAUNCHED(ctx);
     dim3 g((unsigned)cdiv(items, 128), (unsigned)(2 * L * L));
-    fft_pack_quad_kernel<<<g, 128, 0, ctx->stream>>>((const float2*)Bh, Mx, My, L, SC, qph, a->fft_sym, Cq);
+    fft_pack_quad_kernel<CR><<<g, 128, 0, ctx->stream>>>(reinterpret_cast<const CS*>(Bh), Mx, My, L, SC, qph,
+                                                         a->fft_sym, Cq);
     TM_LAUNCHED(ctx);
     a->fft_C = Cq;
     a->fft_err = err;
@@ -1088,9 +1145,9 @@ static int fft_apply_t(tmat_ctx* ctx, const LatOp& a, const void* xv, void* yv, 
   cudaEvent_t ev_all = timing_begin(ctx);
   dim3 tb(32, 8);
   dim3 tg((unsigned)cdiv(nx, 32), (unsigned)ny, (unsigned)(R_ * cdiv(P, 32)));
-  // 256 x 256 complex64 grids: the passes read x and write y in place through the
-  // component-innermost intermediates T1 [r][kx][iy][P] and T2 [r][iy][kx][P] (w1)
-  const bool ci = std::is_same_v<R, float> && Mx == 256 && My == 256;
+  // 256 x 256 grids: the passes read x and write y in place through the component-innermost
+  // intermediates T1 [r][kx][iy][P] and T2 [r][iy][kx][P] (w1)
+  const bool ci = Mx == 256 && My == 256;
   const int64_t Nsite = (int64_t)nx * ny;
   const F256Lay lx{Nsite * P, 1, (int64_t)nx * P, P};                         // x, y: line iy, col ix
   const F256Lay lspec{(int64_t)P * F, F, My, 1};                              // spectra: line kx, col ky
@@ -1099,50 +1156,56 @@ static int fft_apply_t(tmat_ctx* ctx, const LatOp& a, const void* xv, void* yv, 
   const F256Lay lt2_out{(int64_t)ny * Mx * P, 1, P, (int64_t)Mx * P};         // T2 written: line kx, k iy
   const F256Lay lt2_in{(int64_t)ny * Mx * P, 1, (int64_t)Mx * P, P};          // T2 read: line iy, col kx
   const dim3 gy((unsigned)ny, (unsigned)cdiv(P, 16), (unsigned)R_), gk((unsigned)Mx, (unsigned)cdiv(P, 16), (unsigned)R_);
+  using CR = typename fft_compute<R>::t;
+  using CS = C<CR>;  // storage of the intermediates and spectra (double-float pairs for complex128)
   if (ci) {
-    if constexpr (std::is_same_v<R, float>) {
-      if (MODE == 1)
-        fft256_ci_kernel<true, true, 2, -1><<<gy, 256, 0, ctx->stream>>>(x, lx, nx, w1, lt1_out, Mx, P, -1, tw, T,
-                                                                          a.t_stride, nullptr, 1.f);
-      else
-        fft256_ci_kernel<true, true, 0, -1><<<gy, 256, 0, ctx->stream>>>(x, lx, nx, w1, lt1_out, Mx, P, -1, tw, T,
-                                                                          a.t_stride, nullptr, 1.f);
-      TM_LAUNCHED(ctx);
-      fft256_ci_kernel<true, false, 0, -1><<<gk, 256, 0, ctx->stream>>>(w1, lt1_in, ny, Xh, lspec, My, P, -1, tw, T,
-                                                                         a.t_stride, nullptr, 1.f);
-      TM_LAUNCHED(ctx);
+    const G<CR>* xg = reinterpret_cast<const G<CR>*>(x);
+    const G<CR>* Tg = reinterpret_cast<const G<CR>*>(T);
+    CS* w1s = reinterpret_cast<CS*>(w1);
+    auto k1 = MODE == 1 ? fft256_ci_kernel<CR, true, true, 2, -1, false, true>
+                        : fft256_ci_kernel<CR, true, true, 0, -1, false, true>;
+    auto k2 = fft256_ci_kernel<CR, true, false, 0, -1, true, true>;
+    const size_t sm = F256Smem<CR, -1>::BYTES;
+    if (sm > 48 * 1024) {
+      TM_TRY(set_smem_limit(ctx, (const void*)k1, sm));
+      TM_TRY(set_smem_limit(ctx, (const void*)k2, sm));
     }
+    k1<<<gy, 256, sm, ctx->stream>>>(xg, lx, nx, w1s, lt1_out, Mx, P, -1, tw, Tg, a.t_stride, nullptr, 1.f);
+    TM_LAUNCHED(ctx);
+    k2<<<gk, 256, sm, ctx->stream>>>(w1s, lt1_in, ny, reinterpret_cast<CS*>(Xh), lspec, My, P, -1, tw, Tg, a.t_stride,
+                                     nullptr, 1.f);
+    TM_LAUNCHED(ctx);
   } else {
     fft_embed_kernel<R, MODE == 1 ? 1 : 0><<<tg, tb, 0, ctx->stream>>>(x, T, nx, ny, P, R_, grid, a.t_stride);
     TM_LAUNCHED(ctx);
     TM_TRY(fft2_forward<R>(ctx, grid, nx, ny, Mx, My, nb, w1, Xh, tw));
   }
   bool quad_done = false;
-  if constexpr (sizeof(R) == 4) {
-    if (a.fft_C) {
-      // one RHS per pass when every RHS has its own operator
-      using Cfg = Fft4Cfg<L, 2>;
-      auto kern = a.fft_cstride ? fft_mul4_kernel<L, MODE == 1 ? 1 : 0, 1> : fft_mul4_kernel<L, MODE == 1 ? 1 : 0, 2>;
-      const size_t smem = a.fft_cstride ? Fft4Cfg<L, 1>::SMEM : Cfg::SMEM;
-      if (smem > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, smem));
-      const int hx = Mx >= 2 ? Mx / 2 + 1 : 1, hy = My >= 2 ? My / 2 + 1 : 1;
-      const int64_t ntiles = (int64_t)hx * cdiv(hy, Cfg::NI);
-      int per_sm = 0;
-      TM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::THREADS, smem));
-      const int64_t grid = std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * std::max(1, per_sm));
-      cudaEvent_t ev = timing_begin(ctx);
-      kern<<<(unsigned)grid, Cfg::THREADS, smem, ctx->stream>>>((const float2*)a.fft_C, (const float2*)Xh, (float2*)Yh,
-                                                                Mx, My, R_, a.fft_sym, a.fft_err, a.fft_cstride);
-      TM_LAUNCHED(ctx);
-      // the quad-form spectra once, the RHS spectra in and out
-      const double mul_bytes =
-          (double)sizeof(float2) * ((double)hx * hy * 2.0 * Cfg::SC * (a.fft_cstride ? R_ : 1) + 2.0 * nb * F);
-      timing_end(ctx, "lattice_fft_mul32", ev, mul_bytes);
-      quad_done = true;
-    }
+  if (a.fft_C) {
+    // one RHS per pass when every RHS has its own operator
+    using Cfg = Fft4Cfg<L, 2, CR>;
+    auto kern = a.fft_cstride ? fft_mul4_kernel<CR, L, MODE == 1 ? 1 : 0, 1> : fft_mul4_kernel<CR, L, MODE == 1 ? 1 : 0, 2>;
+    const size_t smem = a.fft_cstride ? Fft4Cfg<L, 1, CR>::SMEM : Cfg::SMEM;
+    if (smem > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, smem));
+    const int hx = Mx >= 2 ? Mx / 2 + 1 : 1, hy = My >= 2 ? My / 2 + 1 : 1;
+    const int64_t ntiles = (int64_t)hx * cdiv(hy, Cfg::NI);
+    int per_sm = 0;
+    TM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::THREADS, smem));
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * std::max(1, per_sm));
+    cudaEvent_t ev = timing_begin(ctx);
+    kern<<<(unsigned)grid, Cfg::THREADS, smem, ctx->stream>>>(reinterpret_cast<const CS*>(a.fft_C),
+                                                              reinterpret_cast<const CS*>(Xh), reinterpret_cast<CS*>(Yh),
+                                                              Mx, My, R_, a.fft_sym, a.fft_err, a.fft_cstride);
+    TM_LAUNCHED(ctx);
+    // the quad-form spectra once, the RHS spectra in and out
+    const double mul_bytes =
+        (double)sizeof(CS) * ((double)hx * hy * 2.0 * Cfg::SC * (a.fft_cstride ? R_ : 1) + 2.0 * nb * F);
+    timing_end(ctx, sizeof(R) == 4 ? "lattice_fft_mul32" : "lattice_fft_mul64", ev, mul_bytes);
+    quad_done = true;
   }
   if (!quad_done) {
-    // complex128 operators: the products in double-float on spectra stored as pairs
+    // the mirror-pair product (complex128 operators: in double-float on spectra stored as
+    // pairs), where the quad form is not built
     using CM = typename fft_compute<R>::t;
     constexpr int RC2 = (sizeof(R) == 4 && L <= 24) ? 2 : 1;
     const int RC = a.fft_bstride ? 1 : RC2;  // one RHS per pass when every RHS has its own spectra
@@ -1160,16 +1223,20 @@ static int fft_apply_t(tmat_ctx* ctx, const LatOp& a, const void* xv, void* yv, 
     timing_end(ctx, sizeof(R) == 4 ? "lattice_fft_mul32" : "lattice_fft_mul64", ev, mul_bytes);
   }
   if (ci) {
-    if constexpr (std::is_same_v<R, float>) {
-      fft256_ci_kernel<false, true, 0, -1><<<gk, 256, 0, ctx->stream>>>(Yh, lspec, My, w1, lt2_out, ny, P, +1, tw, T,
-                                                                         a.t_stride, nullptr, 1.f);
-      TM_LAUNCHED(ctx);
-      const size_t pf = MODE == 0 ? F256_PF_SMEM : 0;
-      if (MODE == 0) TM_TRY(set_smem_limit(ctx, (const void*)fft256_ci_kernel<true, true, 0, MODE>, pf));
-      fft256_ci_kernel<true, true, 0, MODE><<<gy, 256, pf, ctx->stream>>>(w1, lt2_in, Mx, (float2*)yv, lx, nx, P, +1,
-                                                                           tw, T, a.t_stride, x, (float)(1.0 / (double)F));
-      TM_LAUNCHED(ctx);
-    }
+    const G<CR>* xg = reinterpret_cast<const G<CR>*>(x);
+    const G<CR>* Tg = reinterpret_cast<const G<CR>*>(T);
+    CS* w1s = reinterpret_cast<CS*>(w1);
+    auto k3 = fft256_ci_kernel<CR, false, true, 0, -1, true, true>;
+    auto k4 = fft256_ci_kernel<CR, true, true, 0, MODE, true, false>;
+    const size_t sm3 = F256Smem<CR, -1>::BYTES, sm4 = F256Smem<CR, MODE>::BYTES;
+    if (sm3 > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)k3, sm3));
+    if (sm4 > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)k4, sm4));
+    k3<<<gk, 256, sm3, ctx->stream>>>(reinterpret_cast<const CS*>(Yh), lspec, My, w1s, lt2_out, ny, P, +1, tw, Tg,
+                                      a.t_stride, nullptr, 1.f);
+    TM_LAUNCHED(ctx);
+    k4<<<gy, 256, sm4, ctx->stream>>>(w1s, lt2_in, Mx, reinterpret_cast<G<CR>*>(yv), lx, nx, P, +1, tw, Tg, a.t_stride,
+                                      xg, (float)(1.0 / (double)F));
+    TM_LAUNCHED(ctx);
   } else {
     C<R>* Yc = Xh;  // X^ is no longer needed
     TM_TRY(fft2_inverse<R>(ctx, Yh, nx, ny, Mx, My, nb, w1, Yc, tw));

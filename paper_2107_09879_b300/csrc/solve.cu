@@ -838,6 +838,7 @@ extern "C" int tmat_position_gradient(tmat_ctx* ctx, const tmat_solution* sol, c
     d.use_tc = false;
     d.fp32 = false;
     d.fft_mirror_sign = q == 0 ? 1 : -1;
+    d.fft_quad_ok = false;  // dF/dd is odd under d -> -d: no quad form
     if (a.use_fft) TM_TRY(lattice_fft_prepare(ctx, &d, q == 0 ? "pg_Bh_x" : "pg_Bh_y"));
     TM_TRY(lattice_apply(ctx, d, TMAT_OP_COUPLE, sol->s, ys + q * N * P, 1));
     TM_TRY(lattice_apply(ctx, d, TMAT_OP_ADJOINT, tmu, yz + q * N * P, 1));

@@ -42,9 +42,13 @@ struct LatOp {
   int fft_mirror_sign = 1;
   // [2][L] per class member u: J(u) | (m mod 2) << 16 | p << 17 (quad-mirror block product)
   const int* fft_sym = nullptr;
-  // complex64 quad-mirror form of the spectra: per item (kx <= Mx/2, ky <= My/2) and class
-  // the symmetric matrix C = B^(kx, ky) S, S = J diag((-1)^m), item-major [items][2][L][L]
+  // quad-mirror form of the spectra (complex64, or double-float pairs for complex128
+  // operators): per item (kx <= Mx/2, ky <= My/2) and class the symmetric matrix
+  // C = B^(kx, ky) S, S = J diag((-1)^m), item-major [items][2][L][L]
   const void* fft_C = nullptr;
+  // the blocks obey reciprocity and inversion symmetry (the quad form needs both; the
+  // position-derivative blocks are odd under inversion)
+  bool fft_quad_ok = true;
   int* fft_err = nullptr;  // device counter of CTAs that gave up on a bounded wait
   // batched operators (one independent problem per RHS, FFT path): per-RHS strides, in
   // complex values, of T ([R][N][P]), of the block spectra and of the quad-form spectra;

@@ -245,9 +245,11 @@ def test_fft_quad_product_matches_mirror_pair_product(nmax, nx, ny, cutoff, R, o
 @pytest.mark.parametrize("nmax,n,cutoff,R", [(4, 130, 3.0, 2), (3, 125, 2.0, 3), (5, 129, 1.5, 1)])
 @pytest.mark.parametrize("op", [0, 1, 2])
 def test_fft_256_grid_passes_match_fp64_and_direct(nmax, n, cutoff, R, op):
-    """Lattices whose FFT grid is 256 x 256 take the four-step, transpose-free complex64 passes
-    (x read and y written in place; P = 30, 48, 70: full and partial component blocks; odd R)
-    against the complex128 FFT apply (the generic passes) and the direct tensor-core kernel."""
+    """Lattices whose FFT grid is 256 x 256 take the four-step, transpose-free passes (x read
+    and y written in place; P = 30, 48, 70: full and partial component blocks; odd R), in
+    complex64 and, for the complex128 operator, in double-float: the complex128 FFT apply
+    against the direct fp64 kernel to 1e-12, the complex64 one and the direct complex64
+    kernel against it to the complex64 tolerance."""
     from paper_2107_09879_b300 import _lib
     r = W.uniform_radii(n * n, 0.08, 0.24, 160 + nmax)
     T = np.ascontiguousarray(np.array([mie.tmatrix_diag(nmax, K0, v, 2.0) for v in r]))
@@ -257,6 +259,8 @@ def test_fft_256_grid_passes_match_fp64_and_direct(nmax, n, cutoff, R, op):
     y64 = c.tmat_apply_lattice(op, 0, n, n, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
     c.set_lattice_fft(False)
     yd = c.tmat_apply_lattice(op, 1, n, n, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
+    yd64 = c.tmat_apply_lattice(op, 0, n, n, 0.5, cutoff, K0, nmax, T, x, taper=cutoff)
     c.close()
+    assert rel_l2(y64, yd64) <= 1e-12
     assert rel_l2(y32, y64) <= C64_APPLY_TOL
     assert rel_l2(yd, y64) <= C64_APPLY_TOL
