@@ -10,6 +10,7 @@
 #include <cuda_fp16.h>
 
 #include "dev.cuh"
+#include "dfloat.cuh"
 #include "solver.h"
 
 namespace tmat {
@@ -87,7 +88,10 @@ dots_kernel(const C<VR>* __restrict__ V, int64_t vstride, int nvec, const C<VR>*
 // blocks per SM, the element loop unrolled by two and ~64 warps per SM reach 3.5-5.8 TB/s,
 // eight vectors per warp at two blocks per SM 1.8-4.6 TB/s)
 constexpr int D32_VPW = 2;
-constexpr int D32_NBMAX = 1024;  // element ranges per group (partials per dot)
+constexpr int D32_NBMAX = 1024;  // element ranges per group (a multiple of 8)
+// The ranges of a group come in blocks of eight (one per warp of a CTA): a CTA sums its
+// eight warp partials in a fixed order and writes one partial per dot, so a dot has
+// ranges / 8 partials, summed by the Hessenberg step in a fixed order.
 
 struct Dots32Plan {
   int groups, ranges, blocks;
@@ -99,8 +103,8 @@ static inline Dots32Plan dots32_plan(int64_t n, int nvec, int num_sms, int R) {
   const int64_t target = (int64_t)num_sms * 64 / std::max(1, R);  // warps per RHS
   int64_t nr = cdiv(target, (int64_t)p.groups);
   nr = std::min<int64_t>(nr, std::max<int64_t>(1, cdiv(n / 2, (int64_t)32 * 16)));
-  p.ranges = (int)std::max<int64_t>(1, std::min<int64_t>(nr, D32_NBMAX));
-  p.blocks = (int)cdiv((int64_t)p.groups * p.ranges, 8);
+  p.ranges = (int)(cdiv(std::max<int64_t>(1, std::min<int64_t>(nr, D32_NBMAX)), 8) * 8);
+  p.blocks = p.groups * (p.ranges / 8);
   return p;
 }
 
@@ -108,14 +112,18 @@ static inline Dots32Plan dots32_plan(int64_t n, int nvec, int num_sms, int R) {
 template <bool TWO>
 __global__ void __launch_bounds__(256, 4)
 dots32_kernel(const float2* __restrict__ V, int64_t vstride, int nvec, const float2* __restrict__ w, int64_t n,
-              int64_t rstride, double2* __restrict__ part, int maxv, int groups, int ranges,
+              int64_t rstride, float4* __restrict__ part, int maxv, int groups, int ranges,
               const int* __restrict__ active, const float2* __restrict__ w2 = nullptr,
-              double2* __restrict__ part2 = nullptr) {
+              float4* __restrict__ part2 = nullptr) {
   const int r = blockIdx.y;
   if (active && !active[r]) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t unit = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (unit >= (int64_t)groups * ranges) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if ((int64_t)blockIdx.x >= (int64_t)groups * (ranges / 8)) return;  // uniform over the CTA
+  __shared__ float2 bred[TWO ? 2 : 1][D32_VPW][8];  // warp sums; the last warp to finish adds them
+  __shared__ unsigned bdone;
+  if (threadIdx.x == 0) bdone = 0;
+  __syncthreads();
+  const int64_t unit = (int64_t)blockIdx.x * 8 + wid;
   const int g = (int)(unit / ranges), b = (int)(unit % ranges);
   const int kb = g * D32_VPW;
   const int64_t n2 = n >> 1;  // float4 = two complex values (n is even)
@@ -160,64 +168,39 @@ dots32_kernel(const float2* __restrict__ V, int64_t vstride, int nvec, const flo
       v.x += __shfl_down_sync(0xffffffffu, v.x, o);
       v.y += __shfl_down_sync(0xffffffffu, v.y, o);
     }
-    if (lane == 0 && kb + q < nvec) part[((int64_t)r * maxv + kb + q) * ranges + b] = make_double2(v.x, v.y);
+    if (lane == 0) bred[0][q][wid] = v;
     if (TWO) {
       float2 v2 = acc2[q];
       for (int o = 16; o > 0; o >>= 1) {
         v2.x += __shfl_down_sync(0xffffffffu, v2.x, o);
         v2.y += __shfl_down_sync(0xffffffffu, v2.y, o);
       }
-      if (lane == 0 && kb + q < nvec) part2[((int64_t)r * maxv + kb + q) * ranges + b] = make_double2(v2.x, v2.y);
+      if (lane == 0) bred[TWO ? 1 : 0][q][wid] = v2;
     }
   }
-}
-
-// w[r] += sign * sum_k V_k[r] coef[r][k] on complex64 vectors (fp32 arithmetic)
-__global__ void __launch_bounds__(256)
-update32_kernel(const float2* __restrict__ V, int64_t vstride, int nvec, const double2* __restrict__ coef, int maxv,
-                float sign, float2* __restrict__ out, int64_t n, int64_t rstride, const int* __restrict__ active,
-                const int* __restrict__ ncols) {
-  const int r = blockIdx.y;
-  if (active && !active[r]) return;
-  const int nv = ncols ? min(nvec, ncols[r]) : nvec;
-  extern __shared__ float2 cs[];  // coefficients of this RHS in fp32
-  for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-    double2 c = coef[r * maxv + k];
-    cs[k] = make_float2((float)(sign * c.x), (float)(sign * c.y));
+  // the last warp of the CTA (fence, then a shared counter) sums the eight warp sums in
+  // warp order and writes the CTA's partial; the others leave without waiting
+  unsigned prev = 0;
+  if (lane == 0) {
+    __threadfence_block();
+    prev = atomicAdd(&bdone, 1u);
   }
-  __syncthreads();
-  const int64_t n2 = n >> 1;
-  float4* o4 = reinterpret_cast<float4*>(out + r * rstride);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-    int k = 0;
-    for (; k + 4 <= nv; k += 4) {
-      float4 v[4];
+  prev = __shfl_sync(0xffffffffu, prev, 0);
+  if (prev != 7) return;
+  __threadfence_block();
+  if (lane < (TWO ? 2 : 1) * D32_VPW) {
+    const int tg = lane / D32_VPW, q = lane % D32_VPW;
+    if (kb + q < nvec) {
+      // double-float sum in warp order: (re hi, re lo, im hi, im lo)
+      float4 t = make_float4(bred[tg][q][0].x, 0.f, bred[tg][q][0].y, 0.f);
 #pragma unroll
-      for (int t = 0; t < 4; ++t) v[t] = reinterpret_cast<const float4*>(V + (int64_t)(k + t) * vstride + r * rstride)[i];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const float2 c = cs[k + t];
-        a.x = fmaf(v[t].x, c.x, fmaf(-v[t].y, c.y, a.x));
-        a.y = fmaf(v[t].x, c.y, fmaf(v[t].y, c.x, a.y));
-        a.z = fmaf(v[t].z, c.x, fmaf(-v[t].w, c.y, a.z));
-        a.w = fmaf(v[t].z, c.y, fmaf(v[t].w, c.x, a.w));
+      for (int w8 = 1; w8 < 8; ++w8) {
+        df_add(t.x, t.y, bred[tg][q][w8].x, 0.f, t.x, t.y);
+        df_add(t.z, t.w, bred[tg][q][w8].y, 0.f, t.z, t.w);
       }
+      const int RB = ranges / 8;
+      (tg ? part2 : part)[((int64_t)r * maxv + kb + q) * RB + (b >> 3)] = t;
     }
-    for (; k < nv; ++k) {
-      const float4 v = reinterpret_cast<const float4*>(V + (int64_t)k * vstride + r * rstride)[i];
-      const float2 c = cs[k];
-      a.x = fmaf(v.x, c.x, fmaf(-v.y, c.y, a.x));
-      a.y = fmaf(v.x, c.y, fmaf(v.y, c.x, a.y));
-      a.z = fmaf(v.z, c.x, fmaf(-v.w, c.y, a.z));
-      a.w = fmaf(v.z, c.y, fmaf(v.w, c.x, a.w));
-    }
-    float4 o = o4[i];
-    o.x += a.x;
-    o.y += a.y;
-    o.z += a.z;
-    o.w += a.w;
-    o4[i] = o;
   }
 }
 
@@ -259,39 +242,6 @@ reduce_kernel(const double2* __restrict__ part, int nb, int nvec, int maxv, doub
 static inline void launch_reduce(tmat_ctx* ctx, const double2* part, int nb, int nvec, int maxv, double2* out,
                                  const int* active, int R) {
   reduce_kernel<<<dim3(R, nvec), RED2_THREADS, 0, ctx->stream>>>(part, nb, nvec, maxv, out, active);
-}
-
-// both dot targets of a DCGS2 pass in one launch: blockIdx.z = 0 reduces part into out,
-// 1 part2 into out2 (the same fixed order as reduce_kernel)
-__global__ void __launch_bounds__(RED2_THREADS)
-reduce_pair_kernel(const double2* __restrict__ part, const double2* __restrict__ part2, int nb, int nvec, int maxv,
-                   double2* __restrict__ out, double2* __restrict__ out2, const int* __restrict__ active) {
-  const int r = blockIdx.x, k = blockIdx.y;
-  if (k >= nvec) return;
-  if (active && !active[r]) return;
-  const double2* pp = (blockIdx.z ? part2 : part) + ((int64_t)r * maxv + k) * nb;
-  double2 s = make_double2(0, 0);
-  for (int b = threadIdx.x; b < nb; b += RED2_THREADS) {
-    const double2 v = pp[b];
-    s.x += v.x;
-    s.y += v.y;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    const double2 t = shfl_down2(s, o);
-    s.x += t.x;
-    s.y += t.y;
-  }
-  __shared__ double2 w2[RED2_THREADS / 32];
-  if ((threadIdx.x & 31) == 0) w2[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double2 t = w2[0];
-    for (int q = 1; q < RED2_THREADS / 32; ++q) {
-      t.x += w2[q].x;
-      t.y += w2[q].y;
-    }
-    (blockIdx.z ? out2 : out)[r * maxv + k] = t;
-  }
 }
 
 // ||v[r]||^2 block partials of complex64 vectors into part[(r*maxv + 0)*nb + b] (as the
@@ -469,10 +419,9 @@ struct GState {
   double *nrm;           // [R] norm of the new vector / residual
   double *tol_abs;       // [R]
   int *active, *ncols, *flags;
-  // delayed CGS2 (complex64 vectors): unrotated Hessenberg [R][maxv][m], the dots of the
-  // basis against the pending vector (D1) and the new vector (D2) [R][maxv], and the
-  // update coefficients [R][maxv] with the self-scales [R]
-  double2 *Hu, *D1, *D2;
+  // delayed CGS2 (complex64 vectors): unrotated Hessenberg [R][maxv][m] and the update
+  // coefficients [R][maxv] with the self-scales [R]
+  double2 *Hu;
   float2 *cA, *cB;
   float *selfA, *selfB;
 };
@@ -578,22 +527,94 @@ __global__ void givens_kernel(GState s, int R, int j, int m, int maxv) {
 // the basis): two passes over the basis per iteration instead of four. The Hessenberg
 // columns are the classical Gram-Schmidt-twice ones; the reorthogonalisation of u_j uses the
 // vector actually stored, so rounding in forming it is corrected as in CGS2.
-__global__ void dcgs2_small_kernel(GState s, int j, int m, int maxv, int R, int final_only) {
+// The step runs as one block per RHS with its inputs staged in shared memory in one phase:
+// the dot partials of the pass (ranges / 8 double-float values per dot, summed here in a
+// fixed order), the rotations, column j-1 and, for short cycles, the Hessenberg block the
+// product H s needs, so the serial part waits on global memory once instead of once per
+// quantity. The fp64 work is kept on few lanes (the B300 issues fp64 at a small fraction of
+// its fp32 rate): the partial sums are double-float, the length-j vector steps run on one
+// warp with warp reductions, H s takes one thread per row.
+constexpr int DCGS2_HB = 48;  // Hessenberg blocks up to (48 + 1) x 48 are staged (j <= 48)
+constexpr int DCGS2_THREADS = 256;
+static inline size_t dcgs2_step_smem(int m, int maxv) {
+  return sizeof(double2) * (4 * (size_t)maxv + 2 * (size_t)m + (size_t)(DCGS2_HB + 1) * DCGS2_HB);
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(DCGS2_THREADS)
+dcgs2_step_kernel(GState s, const float4* __restrict__ part, const float4* __restrict__ part2, int RB, int j, int m,
+                  int maxv, int R, int final_only) {
   const int r = blockIdx.x;
   if (r >= R || !s.active[r]) return;
-  __shared__ double2 sv[1025];
-  __shared__ double red[2][32];
-  __shared__ double2 zeta_sh;
-  __shared__ double b1_sh, nu_sh, ib1_sh, inu_sh;
-  const double2* D1 = s.D1 + (int64_t)r * maxv;
-  const double2* D2 = s.D2 + (int64_t)r * maxv;
+  if (j == 0 && final_only) return;
+  extern __shared__ double2 dsm[];
+  double2* sD1 = dsm;              // [maxv] V^H u_j
+  double2* sD2 = sD1 + maxv;       // [maxv] V^H w
+  double2* sv = sD2 + maxv;        // [maxv] s = D1 / b1
+  double2* col = sv + maxv;        // [maxv] column j-1
+  double2* scs = col + maxv;       // [m] rotations
+  double2* ssn = scs + m;          // [m]
+  double2* Hb = ssn + m;           // [(j + 1) * j] rows 0..j of columns 0..j-1 (j <= DCGS2_HB)
+  __shared__ double2 g_sh, zeta_sh;
+  __shared__ double b1_sh, nu_sh;
+  __shared__ int act_sh;
+  const int tid = threadIdx.x, lane = tid & 31;
   double2* Hu = s.Hu + (int64_t)r * maxv * m;  // Hu[i * m + c]
   float2* cA = s.cA + (int64_t)r * maxv;
   float2* cB = s.cB + (int64_t)r * maxv;
-  const int tid = threadIdx.x;
+  const bool stage_h = j <= DCGS2_HB;
+  // ---- one phase of loads: dot partials, rotations, column j-1, the Hessenberg block ----
+  {
+    const int S = final_only ? j + 1 : 2 * (j + 1);  // sums: D1[0..j] (and D2[0..j])
+    int tps = 32;                                    // threads per sum (a power of two)
+    while (tps > 1 && tps * S > DCGS2_THREADS) tps >>= 1;
+    const int per_round = DCGS2_THREADS / tps;
+    for (int base = 0; base < S; base += per_round) {  // uniform trip count
+      const int si = base + tid / tps, li = tid % tps;
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);  // double-float (re hi, re lo, im hi, im lo)
+      if (si < S) {
+        const int k = si % (j + 1);
+        const float4* pp = (si <= j ? part : part2) + ((int64_t)r * maxv + k) * RB;
+#pragma unroll 4
+        for (int b = li; b < RB; b += tps) {
+          const float4 v = pp[b];
+          df_add(acc.x, acc.y, v.x, v.y, acc.x, acc.y);
+          df_add(acc.z, acc.w, v.z, v.w, acc.z, acc.w);
+        }
+      }
+      for (int o = tps >> 1; o > 0; o >>= 1) {
+        const float4 t = make_float4(__shfl_down_sync(0xffffffffu, acc.x, o, tps),
+                                     __shfl_down_sync(0xffffffffu, acc.y, o, tps),
+                                     __shfl_down_sync(0xffffffffu, acc.z, o, tps),
+                                     __shfl_down_sync(0xffffffffu, acc.w, o, tps));
+        df_add(acc.x, acc.y, t.x, t.y, acc.x, acc.y);
+        df_add(acc.z, acc.w, t.z, t.w, acc.z, acc.w);
+      }
+      if (si < S && li == 0)
+        (si <= j ? sD1 : sD2)[si % (j + 1)] =
+            make_double2((double)acc.x + (double)acc.y, (double)acc.z + (double)acc.w);
+    }
+    if (j > 0) {
+      for (int i = tid; i < j - 1; i += DCGS2_THREADS) {
+        scs[i] = s.cs[r * m + i];
+        ssn[i] = s.sn[r * m + i];
+      }
+      for (int k = tid; k < j; k += DCGS2_THREADS) col[k] = Hu[(int64_t)k * m + (j - 1)];
+      if (tid == 0) g_sh = s.g[r * maxv + j - 1];
+      if (stage_h && !final_only)
+        for (int e = tid; e < (j + 1) * j; e += DCGS2_THREADS) {
+          const int i = e / j, c = e % j;
+          if (c >= i - 1 && c != j - 1) Hb[e] = Hu[(int64_t)i * m + c];
+        }
+    }
+  }
+  __syncthreads();
   if (j == 0) {
     if (tid == 0) {
-      const double2 z0 = D2[0];
+      const double2 z0 = sD2[0];
       Hu[0] = z0;
       cB[0] = make_float2((float)z0.x, (float)z0.y);
       s.selfB[r] = 1.f;
@@ -601,111 +622,124 @@ __global__ void dcgs2_small_kernel(GState s, int j, int m, int maxv, int R, int 
     }
     return;
   }
-  if (tid == 0) {
-    b1_sh = sqrt(fmax(D1[j].x, 0.0));
-    ib1_sh = b1_sh > 0 ? 1.0 / b1_sh : 0.0;
-  }
-  __syncthreads();
-  const double b1 = b1_sh, ib1 = ib1_sh;  // divisions by b1 and nu as products with reciprocals
-  // s = D1 / b1 and |s|^2
-  double ss = 0.0;
-  for (int k = tid; k < j; k += blockDim.x) {
-    const double2 v = make_double2(D1[k].x * ib1, D1[k].y * ib1);
-    sv[k] = v;
-    ss += v.x * v.x + v.y * v.y;
-  }
-  for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
-  if ((tid & 31) == 0) red[0][tid >> 5] = ss;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[0][q];
-    nu_sh = b1 > 0 ? sqrt(fmax(1.0 - t, 1e-30)) : 1.0;
-    inu_sh = 1.0 / nu_sh;
-  }
-  __syncthreads();
-  const double nu = nu_sh, inu = inu_sh;
-  // finalise column j-1 and hand it to the Givens step (hA + hB, subdiagonal in nrm)
-  for (int k = tid; k < j; k += blockDim.x) {
-    double2 h = Hu[(int64_t)k * m + (j - 1)];
-    h.x += b1 * sv[k].x;
-    h.y += b1 * sv[k].y;
-    Hu[(int64_t)k * m + (j - 1)] = h;
-    s.hA[(int64_t)r * maxv + k] = h;
-    s.hB[(int64_t)r * maxv + k] = make_double2(0, 0);
-  }
-  if (tid == 0) {
-    Hu[(int64_t)j * m + (j - 1)] = make_double2(b1 * nu, 0.0);
-    s.nrm[r] = b1 * nu;
-  }
-  __syncthreads();
-  // rotations of column j-1 (residual estimate, convergence flag)
-  extern __shared__ double2 dsm[];
-  givens_block(s, r, j - 1, m, maxv, dsm);
-  if (final_only || !(b1 > 0) || !s.active[r]) return;
-  // zeta = (c - s^H z)/nu with z = D2/b1, c = D2[j]/b1^2
-  double zr = 0.0, zi = 0.0;
-  for (int k = tid; k < j; k += blockDim.x) {
-    const double2 z = make_double2(D2[k].x * ib1, D2[k].y * ib1);
-    zr += sv[k].x * z.x + sv[k].y * z.y;  // conj(s) z
-    zi += sv[k].x * z.y - sv[k].y * z.x;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    zr += __shfl_down_sync(0xffffffffu, zr, o);
-    zi += __shfl_down_sync(0xffffffffu, zi, o);
-  }
-  if ((tid & 31) == 0) {
-    red[0][tid >> 5] = zr;
-    red[1][tid >> 5] = zi;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double a = 0.0, bq = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
-      a += red[0][q];
-      bq += red[1][q];
+  const int J = j - 1;
+  if (tid < 32) {
+    // ---- b1 = ||u_j||, s = D1 / b1, nu = sqrt(1 - |s|^2) (warp 0) ----
+    const double b1 = sqrt(fmax(sD1[j].x, 0.0));
+    const double ib1 = b1 > 0 ? 1.0 / b1 : 0.0;  // divisions by b1 and nu as products with reciprocals
+    double ss = 0.0;
+    for (int k = lane; k < j; k += 32) {
+      const double2 v = make_double2(sD1[k].x * ib1, sD1[k].y * ib1);
+      sv[k] = v;
+      ss += v.x * v.x + v.y * v.y;
     }
-    const double ib2 = ib1 * ib1;
-    zeta_sh = make_double2((D2[j].x * ib2 - a) * inu, (D2[j].y * ib2 - bq) * inu);
+    ss = warp_sum_d(ss);
+    const double nu = b1 > 0 ? sqrt(fmax(1.0 - ss, 1e-30)) : 1.0;
+    // ---- column j-1 final: H[0..j-1][j-1] += b1 s, H[j][j-1] = b1 nu ----
+    for (int k = lane; k < j; k += 32) {
+      double2 h = col[k];
+      h.x += b1 * sv[k].x;
+      h.y += b1 * sv[k].y;
+      col[k] = h;
+      Hu[(int64_t)k * m + J] = h;
+      if (stage_h) Hb[k * j + J] = h;
+    }
+    const double hn = b1 * nu;  // subdiagonal H[j][j-1]
+    __syncwarp();
+    if (lane == 0) {
+      Hu[(int64_t)j * m + J] = make_double2(hn, 0.0);
+      if (stage_h) Hb[j * j + J] = make_double2(hn, 0.0);
+      s.nrm[r] = hn;
+      b1_sh = b1;
+      nu_sh = nu;
+      // ---- Givens step of column J (serial; G_i = [[conj(c_i), conj(s_i)], [-s_i, c_i]]) ----
+      double2 t0 = col[0];
+      for (int i = 0; i < J; ++i) {
+        const double2 c = scs[i], sn = ssn[i];
+        const double2 t1 = col[i + 1];
+        col[i] = make_double2(c.x * t0.x + c.y * t0.y + sn.x * t1.x + sn.y * t1.y,
+                              c.x * t0.y - c.y * t0.x + sn.x * t1.y - sn.y * t1.x);
+        t0 = make_double2(-(sn.x * t0.x - sn.y * t0.y) + (c.x * t1.x - c.y * t1.y),
+                          -(sn.x * t0.y + sn.y * t0.x) + (c.x * t1.y + c.y * t1.x));
+      }
+      const double2 hjj = t0;
+      const double den = sqrt(cabs2(hjj) + hn * hn);
+      double2 c = make_double2(1, 0), sn = make_double2(0, 0);
+      if (den > 0) {
+        const double iden = 1.0 / den;
+        c = make_double2(hjj.x * iden, hjj.y * iden);
+        sn = make_double2(hn * iden, 0.0);
+      }
+      s.cs[r * m + J] = c;
+      s.sn[r * m + J] = sn;
+      col[J] = make_double2(den, 0);
+      const double2 gj = g_sh;
+      const double2 gn = make_double2(-(sn.x * gj.x - sn.y * gj.y), -(sn.x * gj.y + sn.y * gj.x));
+      s.g[r * maxv + J + 1] = gn;
+      s.g[r * maxv + J] = make_double2(c.x * gj.x + c.y * gj.y, c.x * gj.y - c.y * gj.x);
+      s.ncols[r] = J + 1;
+      const double res = sqrt(cabs2(gn));
+      int act = 1;
+      if (!isfinite(res) || !isfinite(hn)) {
+        s.flags[r] |= 1;  // NaN / Inf
+        act = 0;
+      } else if (res <= s.tol_abs[r] || hn == 0.0) {
+        act = 0;
+      }
+      if (!act) s.active[r] = 0;
+      act_sh = act;
+    }
   }
   __syncthreads();
-  const double2 zeta = zeta_sh;
-  // column j: H[i][j] = ([z; zeta]_i - (H s)_i)/nu, H s over the final columns 0..j-1;
-  // one warp per row, the lanes split the row (H is upper Hessenberg: H[i][c] = 0 for c < i - 1)
   {
-    const int lane = tid & 31, nw = blockDim.x >> 5;
-    for (int i = tid >> 5; i <= j; i += nw) {
-      double tx = 0.0, ty = 0.0;
-      const int c0 = i > 0 ? i - 1 : 0;
-      for (int c = c0 + lane; c < j; c += 32) {
-        const double2 h = Hu[(int64_t)i * m + c];
-        tx += h.x * sv[c].x - h.y * sv[c].y;
-        ty += h.x * sv[c].y + h.y * sv[c].x;
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        tx += __shfl_down_sync(0xffffffffu, tx, o);
-        ty += __shfl_down_sync(0xffffffffu, ty, o);
-      }
-      if (lane == 0) {
-        const double2 zi2 = i < j ? make_double2(D2[i].x * ib1, D2[i].y * ib1) : zeta;
-        Hu[(int64_t)i * m + j] = make_double2((zi2.x - tx) * inu, (zi2.y - ty) * inu);
-      }
+    double2* hcol = s.H + (int64_t)r * maxv * m + J;  // rotated column J, element i at hcol[i * m]
+    for (int i = tid; i <= J; i += DCGS2_THREADS) hcol[(int64_t)i * m] = col[i];
+  }
+  const double b1 = b1_sh;
+  if (final_only || !(b1 > 0) || !act_sh) return;
+  const double ib1 = 1.0 / b1, inu = 1.0 / nu_sh;
+  if (tid < 32) {
+    // ---- zeta = (c - s^H z)/nu with z = D2/b1, c = D2[j]/b1^2 (warp 0) ----
+    double zr = 0.0, zi = 0.0;
+    for (int k = lane; k < j; k += 32) {
+      const double2 z = make_double2(sD2[k].x * ib1, sD2[k].y * ib1);
+      zr += sv[k].x * z.x + sv[k].y * z.y;  // conj(s) z
+      zi += sv[k].x * z.y - sv[k].y * z.x;
+    }
+    zr = warp_sum_d(zr);
+    zi = warp_sum_d(zi);
+    const double ib2 = ib1 * ib1;
+    const double2 zeta = make_double2((sD2[j].x * ib2 - zr) * inu, (sD2[j].y * ib2 - zi) * inu);
+    if (lane == 0) zeta_sh = zeta;
+    // ---- update coefficients ----
+    const double zn_r = zeta.x * inu, zn_i = zeta.y * inu;  // zeta / nu
+    for (int k = lane; k < j; k += 32) {
+      const double2 sk = sv[k];
+      const double2 z = make_double2(sD2[k].x * ib1, sD2[k].y * ib1);
+      cA[k] = make_float2((float)(sk.x * inu), (float)(sk.y * inu));
+      // (z - (zeta/nu) s)/nu
+      const double2 t = make_double2(z.x - (zn_r * sk.x - zn_i * sk.y), z.y - (zn_r * sk.y + zn_i * sk.x));
+      cB[k] = make_float2((float)(t.x * inu), (float)(t.y * inu));
+    }
+    if (lane == 0) {
+      cB[j] = make_float2((float)(zn_r * inu * ib1), (float)(zn_i * inu * ib1));  // zeta / (nu^2 b1)
+      s.selfA[r] = (float)(ib1 * inu);
+      s.selfB[r] = (float)(ib1 * inu);
     }
   }
-  // update coefficients
-  const double zn_r = zeta.x * inu, zn_i = zeta.y * inu;  // zeta / nu
-  for (int k = tid; k < j; k += blockDim.x) {
-    const double2 sk = sv[k];
-    const double2 z = make_double2(D2[k].x * ib1, D2[k].y * ib1);
-    cA[k] = make_float2((float)(sk.x * inu), (float)(sk.y * inu));
-    // (z - (zeta/nu) s)/nu
-    const double2 t = make_double2(z.x - (zn_r * sk.x - zn_i * sk.y), z.y - (zn_r * sk.y + zn_i * sk.x));
-    cB[k] = make_float2((float)(t.x * inu), (float)(t.y * inu));
-  }
-  if (tid == 0) {
-    cB[j] = make_float2((float)(zn_r * inu * ib1), (float)(zn_i * inu * ib1));  // zeta / (nu^2 b1)
-    s.selfA[r] = (float)(ib1 * inu);
-    s.selfB[r] = (float)(ib1 * inu);
+  __syncthreads();
+  // ---- column j: H[i][j] = ([z; zeta]_i - (H s)_i)/nu over the final columns 0..j-1, one
+  // thread per row (upper Hessenberg: H[i][c] = 0 for c < i - 1) ----
+  const double2 zeta = zeta_sh;
+  for (int i = tid; i <= j; i += DCGS2_THREADS) {
+    double tx = 0.0, ty = 0.0;
+    for (int c = i > 0 ? i - 1 : 0; c < j; ++c) {
+      const double2 h = stage_h ? Hb[i * j + c] : Hu[(int64_t)i * m + c];
+      tx += h.x * sv[c].x - h.y * sv[c].y;
+      ty += h.x * sv[c].y + h.y * sv[c].x;
+    }
+    const double2 zi2 = i < j ? make_double2(sD2[i].x * ib1, sD2[i].y * ib1) : zeta;
+    Hu[(int64_t)i * m + j] = make_double2((zi2.x - tx) * inu, (zi2.y - ty) * inu);
   }
 }
 
@@ -788,8 +822,8 @@ static inline Dots16Plan dots16_plan(int64_t n, int gh, int num_sms, int R) {
   const int64_t target = (int64_t)num_sms * 64 / std::max(1, R);  // warps per RHS
   int64_t nr = cdiv(target, (int64_t)gh + 1);
   nr = std::min<int64_t>(nr, std::max<int64_t>(1, cdiv(n / 2, (int64_t)32 * 16)));
-  p.ranges = (int)std::max<int64_t>(1, std::min<int64_t>(nr, D32_NBMAX));
-  p.blocks = (int)cdiv(((int64_t)gh + 1) * p.ranges, 8);
+  p.ranges = (int)(cdiv(std::max<int64_t>(1, std::min<int64_t>(nr, D32_NBMAX)), 8) * 8);
+  p.blocks = (gh + 1) * (p.ranges / 8);
   return p;
 }
 
@@ -799,13 +833,17 @@ static inline Dots16Plan dots16_plan(int64_t n, int gh, int num_sms, int R) {
 template <bool TWO>
 __global__ void __launch_bounds__(256, 4)
 dots16_kernel(const uint2* __restrict__ Vh, int64_t hstride, int nh, const float2* __restrict__ u, int64_t n,
-              int64_t rstride, double2* __restrict__ part, int maxv, int gh, int ranges, const int* __restrict__ active,
-              float inv_sc, const float2* __restrict__ w2 = nullptr, double2* __restrict__ part2 = nullptr) {
+              int64_t rstride, float4* __restrict__ part, int maxv, int gh, int ranges, const int* __restrict__ active,
+              float inv_sc, const float2* __restrict__ w2 = nullptr, float4* __restrict__ part2 = nullptr) {
   const int r = blockIdx.y;
   if (active && !active[r]) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t unit = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (unit >= (int64_t)(gh + 1) * ranges) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if ((int64_t)blockIdx.x >= (int64_t)(gh + 1) * (ranges / 8)) return;  // uniform over the CTA
+  __shared__ float2 bred[TWO ? 2 : 1][D16_VPW][8];  // warp sums; the last warp to finish adds them
+  __shared__ unsigned bdone;
+  if (threadIdx.x == 0) bdone = 0;
+  __syncthreads();
+  const int64_t unit = (int64_t)blockIdx.x * 8 + wid;
   const int g = (int)(unit / ranges), b = (int)(unit % ranges);
   const bool pend = g == gh;  // the pending fp32 vector
   const int kb = pend ? nh : g * D16_VPW;
@@ -858,14 +896,38 @@ dots16_kernel(const uint2* __restrict__ Vh, int64_t hstride, int nh, const float
       v.x += __shfl_down_sync(0xffffffffu, v.x, o);
       v.y += __shfl_down_sync(0xffffffffu, v.y, o);
     }
-    if (lane == 0 && q < nq) part[((int64_t)r * maxv + kb + q) * ranges + b] = make_double2(sc * v.x, sc * v.y);
+    if (lane == 0) bred[0][q][wid] = make_float2(sc * v.x, sc * v.y);
     if (TWO) {
       float2 v2 = acc2[q];
       for (int o = 16; o > 0; o >>= 1) {
         v2.x += __shfl_down_sync(0xffffffffu, v2.x, o);
         v2.y += __shfl_down_sync(0xffffffffu, v2.y, o);
       }
-      if (lane == 0 && q < nq) part2[((int64_t)r * maxv + kb + q) * ranges + b] = make_double2(sc * v2.x, sc * v2.y);
+      if (lane == 0) bred[TWO ? 1 : 0][q][wid] = make_float2(sc * v2.x, sc * v2.y);
+    }
+  }
+  // the last warp of the CTA (fence, then a shared counter) sums the eight warp sums in
+  // warp order and writes the CTA's partial; the others leave without waiting
+  unsigned prev = 0;
+  if (lane == 0) {
+    __threadfence_block();
+    prev = atomicAdd(&bdone, 1u);
+  }
+  prev = __shfl_sync(0xffffffffu, prev, 0);
+  if (prev != 7) return;
+  __threadfence_block();
+  if (lane < (TWO ? 2 : 1) * D16_VPW) {
+    const int tg = lane / D16_VPW, q = lane % D16_VPW;
+    if (q < nq) {
+      // double-float sum in warp order: (re hi, re lo, im hi, im lo)
+      float4 t = make_float4(bred[tg][q][0].x, 0.f, bred[tg][q][0].y, 0.f);
+#pragma unroll
+      for (int w8 = 1; w8 < 8; ++w8) {
+        df_add(t.x, t.y, bred[tg][q][w8].x, 0.f, t.x, t.y);
+        df_add(t.z, t.w, bred[tg][q][w8].y, 0.f, t.z, t.w);
+      }
+      const int RB = ranges / 8;
+      (tg ? part2 : part)[((int64_t)r * maxv + kb + q) * RB + (b >> 3)] = t;
     }
   }
 }
@@ -1091,8 +1153,6 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
     s.flags = (int*)take(sizeof(int) * R_);
     int* want = (int*)take(sizeof(int) * R_);
     s.Hu = (double2*)take(sizeof(double2) * R_ * maxv * m);
-    s.D1 = (double2*)take(sizeof(double2) * R_ * maxv);
-    s.D2 = (double2*)take(sizeof(double2) * R_ * maxv);
     s.cA = (float2*)take(sizeof(float2) * R_ * maxv);
     s.cB = (float2*)take(sizeof(float2) * R_ * maxv);
     s.selfA = (float*)take(sizeof(float) * R_);
@@ -1135,9 +1195,8 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
       if constexpr (sizeof(VR) == 4) {
         // delayed CGS2: the Hessenberg column of iteration j is finalised at iteration j + 1
         float2* V32 = reinterpret_cast<float2*>(V);
-        const size_t gsm_bytes = sizeof(double2) * (2 * (size_t)m + maxv);
-        if (gsm_bytes + 17 * 1024 > 48 * 1024)
-          TM_TRY(set_smem_limit(ctx, (const void*)dcgs2_small_kernel, gsm_bytes));
+        const size_t step_bytes = dcgs2_step_smem(m, maxv);
+        if (step_bytes > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)dcgs2_step_kernel, step_bytes));
         for (;; ++j) {
           const bool final_only = j == m || st->iterations >= p.max_iter;
           float2* vj = V32 + (int64_t)(h16 ? (j & 1) : j) * R * n;
@@ -1153,36 +1212,34 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
             dp.ranges = hp.ranges;
             dp.blocks = hp.blocks;
           }
+          float4* pf4 = reinterpret_cast<float4*>(part);  // double-float partials
+          float4* pf4b = reinterpret_cast<float4*>(part2);
           cudaEvent_t ev_d = timing_begin(ctx);
           if (h16) {
             if (final_only)
               dots16_kernel<false><<<dim3(dp.blocks, R), 256, 0, ctx->stream>>>(
-                  Vh, (int64_t)R * n, j, vj, n, rs, part, maxv, gh, dp.ranges, s.active, h16_inv);
+                  Vh, (int64_t)R * n, j, vj, n, rs, pf4, maxv, gh, dp.ranges, s.active, h16_inv);
             else
               dots16_kernel<true><<<dim3(dp.blocks, R), 256, 0, ctx->stream>>>(
-                  Vh, (int64_t)R * n, j, vj, n, rs, part, maxv, gh, dp.ranges, s.active, h16_inv, w, part2);
+                  Vh, (int64_t)R * n, j, vj, n, rs, pf4, maxv, gh, dp.ranges, s.active, h16_inv, w, pf4b);
           } else if (final_only) {
             dots32_kernel<false><<<dim3(dp.blocks, R), 256, 0, ctx->stream>>>(V32, (int64_t)R * n, j + 1, vj, n, rs,
-                                                                               part, maxv, dp.groups, dp.ranges, s.active);
+                                                                               pf4, maxv, dp.groups, dp.ranges, s.active);
           } else {
             dots32_kernel<true><<<dim3(dp.blocks, R), 256, 0, ctx->stream>>>(
-                V32, (int64_t)R * n, j + 1, vj, n, rs, part, maxv, dp.groups, dp.ranges, s.active, w, part2);
+                V32, (int64_t)R * n, j + 1, vj, n, rs, pf4, maxv, dp.groups, dp.ranges, s.active, w, pf4b);
           }
           TM_LAUNCHED(ctx);
           // reads the j + 1 basis slots (the pending vector is slot j) and w
           timing_end(ctx, "arnoldi_dots32", ev_d,
                      h16 ? 4.0 * R * n * j + 8.0 * R * n * (1 + (final_only ? 0 : 1))
                          : 8.0 * R * n * (j + 1 + (final_only ? 0 : 1)));
-          if (final_only) {
-            launch_reduce(ctx, part, dp.ranges, j + 1, maxv, s.D1, s.active, R);
-          } else {
-            reduce_pair_kernel<<<dim3(R, j + 1, 2), RED2_THREADS, 0, ctx->stream>>>(part, part2, dp.ranges, j + 1, maxv,
-                                                                                   s.D1, s.D2, s.active);
-          }
+          // the dot sums (ranges / 8 partials each), column j-1 final, its rotation, column j
+          // and the update coefficients
+          dcgs2_step_kernel<<<R, DCGS2_THREADS, step_bytes, ctx->stream>>>(s, pf4, pf4b, dp.ranges / 8, j, m, maxv, R,
+                                                                          final_only ? 1 : 0);
           TM_LAUNCHED(ctx);
-          dcgs2_small_kernel<<<R, 256, gsm_bytes, ctx->stream>>>(s, j, m, maxv, R, final_only ? 1 : 0);
-          TM_LAUNCHED(ctx);
-          // The flags are copied out behind the small kernel and read while the update pass
+          // The flags are copied out behind the step kernel and read while the update pass
           // runs (it skips every RHS that has converged), so the device does not idle through
           // the host's check before the next operator launch.
           const bool check = j >= 1 && (final_only || j % sync_every == 0);
@@ -1225,26 +1282,14 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
         TM_TRY(op_apply(ctx, A, mode, vj, w, R));
         for (int pass = 0; pass < 2; ++pass) {
           double2* hc = pass == 0 ? s.hA : s.hB;
-          int nbp = nb;
-          if constexpr (sizeof(VR) == 4) {
-            const Dots32Plan dp = dots32_plan(n, j + 1, ctx->num_sms, R);
-            nbp = dp.ranges;
-            dots32_kernel<false><<<dim3(dp.blocks, R), 256, 0, ctx->stream>>>(V, (int64_t)R * n, j + 1, w, n, rs, part,
-                                                                               maxv, dp.groups, dp.ranges, s.active);
-          } else {
-            dots_kernel<VR><<<dim3(nb, R), RED_THREADS, 0, ctx->stream>>>(V, (int64_t)R * n, j + 1, w, n, rs, part,
-                                                                           maxv, s.active);
-          }
+          // (complex128 vectors: complex64 ones take the delayed CGS2 above)
+          dots_kernel<VR><<<dim3(nb, R), RED_THREADS, 0, ctx->stream>>>(V, (int64_t)R * n, j + 1, w, n, rs, part, maxv,
+                                                                         s.active);
           TM_LAUNCHED(ctx);
-          launch_reduce(ctx, part, nbp, j + 1, maxv, hc, s.active, R);
+          launch_reduce(ctx, part, nb, j + 1, maxv, hc, s.active, R);
           TM_LAUNCHED(ctx);
-          if constexpr (sizeof(VR) == 4) {
-            update32_kernel<<<dim3(g1, R), 256, sizeof(float2) * (j + 1), ctx->stream>>>(
-                V, (int64_t)R * n, j + 1, hc, maxv, -1.0f, w, n, rs, s.active, nullptr);
-          } else {
-            update_kernel<VR, VR><<<dim3(g1, R), 256, 0, ctx->stream>>>(V, (int64_t)R * n, j + 1, hc, maxv, -1.0, w, n,
-                                                                        rs, s.active, nullptr);
-          }
+          update_kernel<VR, VR><<<dim3(g1, R), 256, 0, ctx->stream>>>(V, (int64_t)R * n, j + 1, hc, maxv, -1.0, w, n, rs,
+                                                                      s.active, nullptr);
           TM_LAUNCHED(ctx);
         }
         TM_TRY(vec_norms<VR>(ctx, w, n, rs, R, part, nb, s.y, maxv, s.nrm, s.active));
