@@ -371,12 +371,21 @@ __global__ void scale_kernel(const C<XR>* __restrict__ x, C<YR>* __restrict__ y,
   if (active && !active[r]) return;
   double s = norm ? norm[r] : 1.0;
   if (inv) s = (s > 0) ? 1.0 / s : 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    C<XR> v = x[r * rstride + i];
-    C<YR> o;
-    o.x = (YR)((double)v.x * s);
-    o.y = (YR)((double)v.y * s);
-    y[r * rstride + i] = o;
+  if constexpr (std::is_same_v<YR, float>) {
+    // a complex64 result: the product in fp32 (the B300's fp64 rate would bound this pass)
+    const float sf = (float)s;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+      const C<XR> v = x[r * rstride + i];
+      y[r * rstride + i] = make_float2((float)v.x * sf, (float)v.y * sf);
+    }
+  } else {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+      C<XR> v = x[r * rstride + i];
+      C<YR> o;
+      o.x = (YR)((double)v.x * s);
+      o.y = (YR)((double)v.y * s);
+      y[r * rstride + i] = o;
+    }
   }
 }
 
@@ -387,7 +396,10 @@ __global__ void residual_kernel(const C<BR>* __restrict__ b, const C<YR>* __rest
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     C<BR> bv = b[i];
     C<YR> yv = y[i];
-    out[i] = mk<BR>((BR)((double)bv.x - (double)yv.x), (BR)((double)bv.y - (double)yv.y));
+    if constexpr (std::is_same_v<BR, float> && std::is_same_v<YR, float>)
+      out[i] = make_float2(bv.x - yv.x, bv.y - yv.y);  // fp32 throughout: no fp64 round trip
+    else
+      out[i] = mk<BR>((BR)((double)bv.x - (double)yv.x), (BR)((double)bv.y - (double)yv.y));
   }
 }
 
@@ -1005,6 +1017,7 @@ xupdate16_kernel(const uint2* __restrict__ Vh, int64_t hstride, int nvec, const 
   const int64_t n2 = n >> 1;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
     for (int k = 0; k < nv; ++k) {
       const float4 v = h16_load2(Vh + ((int64_t)k * hstride + r * rstride) / 2, i);
       const float2 c = xcs[k];
@@ -1316,8 +1329,9 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
       lsq_kernel<<<R, 128, sizeof(double2) * maxv, ctx->stream>>>(s, R, m, maxv);
       TM_LAUNCHED(ctx);
       if constexpr (sizeof(VR) == 4) {
-        if (h16)
-          xupdate16_kernel<<<dim3(g1, R), 256, sizeof(float2) * std::max(j, 1), ctx->stream>>>(
+        if (h16)  // the update pass's grid (16 blocks per SM per RHS)
+          xupdate16_kernel<<<dim3((unsigned)std::min<int64_t>(cdiv(n / 2, 256), (int64_t)ctx->num_sms * 16), R), 256,
+                             sizeof(float2) * std::max(j, 1), ctx->stream>>>(
               Vh, (int64_t)R * n, j, s.y, maxv, x, n, rs, s.ncols, h16_inv);
         else
           xupdate32_kernel<<<dim3(g1, R), 256, sizeof(float2) * std::max(j, 1), ctx->stream>>>(
