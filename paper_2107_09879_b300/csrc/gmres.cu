@@ -551,6 +551,10 @@ constexpr int DCGS2_THREADS = 256;
 static inline size_t dcgs2_step_smem(int m, int maxv) {
   return sizeof(double2) * (4 * (size_t)maxv + 2 * (size_t)m + (size_t)(DCGS2_HB + 1) * DCGS2_HB);
 }
+__device__ __forceinline__ void dcgs2_cp16(void* dst, const void* src) {  // 16-byte cp.async
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
+}
 __device__ __forceinline__ double warp_sum_d(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -558,9 +562,9 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 __global__ void __launch_bounds__(DCGS2_THREADS)
 dcgs2_step_kernel(GState s, const float4* __restrict__ part, const float4* __restrict__ part2, int RB, int j, int m,
-                  int maxv, int R, int final_only) {
+                  int maxv, int R, int final_only, int stage_p) {
   const int r = blockIdx.x;
-  if (r >= R || !s.active[r]) return;
+  if (r >= R) return;
   if (j == 0 && final_only) return;
   extern __shared__ double2 dsm[];
   double2* sD1 = dsm;              // [maxv] V^H u_j
@@ -570,7 +574,9 @@ dcgs2_step_kernel(GState s, const float4* __restrict__ part, const float4* __res
   double2* scs = col + maxv;       // [m] rotations
   double2* ssn = scs + m;          // [m]
   double2* Hb = ssn + m;           // [(j + 1) * j] rows 0..j of columns 0..j-1 (j <= DCGS2_HB)
-  __shared__ double2 g_sh, zeta_sh;
+                                   // then (stage_p) the partials [S][RB] as double-float
+  __shared__ __align__(16) double2 g_sh;
+  __shared__ double2 zeta_sh;
   __shared__ double b1_sh, nu_sh;
   __shared__ int act_sh;
   const int tid = threadIdx.x, lane = tid & 31;
@@ -578,10 +584,34 @@ dcgs2_step_kernel(GState s, const float4* __restrict__ part, const float4* __res
   float2* cA = s.cA + (int64_t)r * maxv;
   float2* cB = s.cB + (int64_t)r * maxv;
   const bool stage_h = j <= DCGS2_HB;
-  // ---- one phase of loads: dot partials, rotations, column j-1, the Hessenberg block ----
+  // ---- one phase of copies: dot partials, rotations, column j-1, the Hessenberg block, all
+  // in flight at once (cp.async), then the sums from shared memory ----
   {
     const int S = final_only ? j + 1 : 2 * (j + 1);  // sums: D1[0..j] (and D2[0..j])
-    int tps = 32;                                    // threads per sum (a power of two)
+    float4* pst = reinterpret_cast<float4*>(Hb + (DCGS2_HB + 1) * DCGS2_HB);  // [S][RB] (stage_p)
+    if (stage_p)
+      for (int e = tid; e < S * RB; e += DCGS2_THREADS) {
+        const int si = e / RB, bq = e % RB, k = si % (j + 1);
+        dcgs2_cp16(pst + e, (si <= j ? part : part2) + ((int64_t)r * maxv + k) * RB + bq);
+      }
+    if (j > 0) {
+      for (int i = tid; i < j - 1; i += DCGS2_THREADS) {
+        dcgs2_cp16(scs + i, s.cs + r * m + i);
+        dcgs2_cp16(ssn + i, s.sn + r * m + i);
+      }
+      for (int k = tid; k < j; k += DCGS2_THREADS) dcgs2_cp16(col + k, Hu + (int64_t)k * m + (j - 1));
+      if (tid == 0) dcgs2_cp16(&g_sh, s.g + r * maxv + j - 1);
+      if (stage_h && !final_only)
+        for (int e = tid; e < (j + 1) * j; e += DCGS2_THREADS) {
+          const int i = e / j, c = e % j;
+          if (c >= i - 1 && c != j - 1) dcgs2_cp16(Hb + e, Hu + (int64_t)i * m + c);
+        }
+    }
+    const int act0 = s.active[r];  // read while the copies are in flight (an inactive RHS leaves)
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    if (!act0) return;
+    int tps = 32;  // threads per sum (a power of two)
     while (tps > 1 && tps * S > DCGS2_THREADS) tps >>= 1;
     const int per_round = DCGS2_THREADS / tps;
     for (int base = 0; base < S; base += per_round) {  // uniform trip count
@@ -589,10 +619,10 @@ dcgs2_step_kernel(GState s, const float4* __restrict__ part, const float4* __res
       float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);  // double-float (re hi, re lo, im hi, im lo)
       if (si < S) {
         const int k = si % (j + 1);
-        const float4* pp = (si <= j ? part : part2) + ((int64_t)r * maxv + k) * RB;
+        const float4* pp = stage_p ? pst + (int64_t)si * RB : (si <= j ? part : part2) + ((int64_t)r * maxv + k) * RB;
 #pragma unroll 4
-        for (int b = li; b < RB; b += tps) {
-          const float4 v = pp[b];
+        for (int bq = li; bq < RB; bq += tps) {
+          const float4 v = pp[bq];
           df_add(acc.x, acc.y, v.x, v.y, acc.x, acc.y);
           df_add(acc.z, acc.w, v.z, v.w, acc.z, acc.w);
         }
@@ -608,19 +638,6 @@ dcgs2_step_kernel(GState s, const float4* __restrict__ part, const float4* __res
       if (si < S && li == 0)
         (si <= j ? sD1 : sD2)[si % (j + 1)] =
             make_double2((double)acc.x + (double)acc.y, (double)acc.z + (double)acc.w);
-    }
-    if (j > 0) {
-      for (int i = tid; i < j - 1; i += DCGS2_THREADS) {
-        scs[i] = s.cs[r * m + i];
-        ssn[i] = s.sn[r * m + i];
-      }
-      for (int k = tid; k < j; k += DCGS2_THREADS) col[k] = Hu[(int64_t)k * m + (j - 1)];
-      if (tid == 0) g_sh = s.g[r * maxv + j - 1];
-      if (stage_h && !final_only)
-        for (int e = tid; e < (j + 1) * j; e += DCGS2_THREADS) {
-          const int i = e / j, c = e % j;
-          if (c >= i - 1 && c != j - 1) Hb[e] = Hu[(int64_t)i * m + c];
-        }
     }
   }
   __syncthreads();
@@ -1209,7 +1226,6 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
         // delayed CGS2: the Hessenberg column of iteration j is finalised at iteration j + 1
         float2* V32 = reinterpret_cast<float2*>(V);
         const size_t step_bytes = dcgs2_step_smem(m, maxv);
-        if (step_bytes > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)dcgs2_step_kernel, step_bytes));
         for (;; ++j) {
           const bool final_only = j == m || st->iterations >= p.max_iter;
           float2* vj = V32 + (int64_t)(h16 ? (j & 1) : j) * R * n;
@@ -1249,8 +1265,16 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
                          : 8.0 * R * n * (j + 1 + (final_only ? 0 : 1)));
           // the dot sums (ranges / 8 partials each), column j-1 final, its rotation, column j
           // and the update coefficients
-          dcgs2_step_kernel<<<R, DCGS2_THREADS, step_bytes, ctx->stream>>>(s, pf4, pf4b, dp.ranges / 8, j, m, maxv, R,
-                                                                          final_only ? 1 : 0);
+          {
+            // the partials go through shared memory with everything else when they fit
+            const int RB = dp.ranges / 8, S = final_only ? j + 1 : 2 * (j + 1);
+            const size_t pbytes = sizeof(float4) * (size_t)S * RB;
+            const int stage_p = step_bytes + pbytes <= 200 * 1024 ? 1 : 0;
+            const size_t sm = step_bytes + (stage_p ? pbytes : 0);
+            if (sm > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)dcgs2_step_kernel, sm));
+            dcgs2_step_kernel<<<R, DCGS2_THREADS, sm, ctx->stream>>>(s, pf4, pf4b, RB, j, m, maxv, R,
+                                                                    final_only ? 1 : 0, stage_p);
+          }
           TM_LAUNCHED(ctx);
           // The flags are copied out behind the step kernel and read while the update pass
           // runs (it skips every RHS that has converged), so the device does not idle through
