@@ -139,14 +139,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# kernel timing in the timed region: one Arnoldi iteration in TIMING_EVERY carries CUDA events
+TIMING_EVERY = 8
+
 # DRAM bytes (read + write) / algorithmic bytes of one ncu capture of each HBM-bound kernel as
-# it stands (the quad block product on the 200 x 200 lattice: 205.93 MB read + 27.86 MB written
+# it stands (the quad block product on the 200 x 200 lattice: 205.88 MB read + 27.22 MB written
 # of 256.16 MB algorithmic), scaled to the timed launches by their algorithmic bytes (traffic
 # grows with the bytes a launch must move). None: the kernel changed since its last capture
 # (the compressed-basis dot and update passes).
 TRAFFIC_RATIO = {"arnoldi_dots32": None,
                  "arnoldi_update32": None,
-                 "lattice_fft_mul32": (205.93e6 + 27.86e6) / 256.16e6}
+                 "lattice_fft_mul32": (205.88e6 + 27.22e6) / 256.16e6}
 # DRAM bytes per launch of the direct-path window-view kernel and of the block product
 # (one ncu capture each on the 200 x 200 lattice)
 MEASURED_TRAFFIC = {"lattice_tc2_kernel<4,0>": 238.0e6 + 23.0e6}
@@ -194,16 +197,18 @@ def fft_apply_work(nx, ny, c, L, R):
 
 
 def roofline_hbm(hbm, step_total_ms):
-    """The dominant kernel (largest summed time in the timed region) of the HBM-bound ones
-    the library counts algorithmic bytes for: achieved = its bytes / its time."""
-    kind, v = max(hbm.items(), key=lambda kv: kv[1]["total_ms"])
+    """The dominant kernel (largest time in the timed region: mean timed launch x calls) of
+    the HBM-bound ones the library counts algorithmic bytes for: achieved = the bytes of its
+    timed launches / their time."""
+    kind, v = max(hbm.items(), key=lambda kv: kv[1]["total_ms"] / kv[1]["launches"] * kv[1]["calls"])
     achieved = v["bytes"] / (v["total_ms"] * 1e-3) / 1e9
     ratio = TRAFFIC_RATIO.get(kind)
+    avg = v["total_ms"] / v["launches"]
     return {"kernel": v["kernel"], "bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
             "frac": achieved / HBM_PEAK_GBS,
             "traffic": (ratio * v["bytes"] / v["launches"]) if ratio else None,
-            "launches": v["launches"], "avg_launch_ms": v["total_ms"] / v["launches"],
-            "bytes_per_launch": v["bytes"] / v["launches"], "share_of_timed_region": v["total_ms"] / step_total_ms,
+            "launches": v["calls"], "timed_launches": v["launches"], "avg_launch_ms": avg,
+            "bytes_per_launch": v["bytes"] / v["launches"], "share_of_timed_region": avg * v["calls"] / step_total_ms,
             "peak_note": f"STREAM-style copy bandwidth ({PEAKS['note']})"}
 
 
@@ -822,7 +827,7 @@ def run_ours(args, rank, world):
         step(*dev_in)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
-    ctx.set_timing(True)
+    ctx.set_timing(TIMING_EVERY)
     launches0 = ctx.launches()
     infos.clear()
     clocks = ClockSampler(dev)
@@ -847,11 +852,12 @@ def run_ours(args, rank, world):
                    ("lattice_apply_tcv", "lattice_tc2_kernel<4,0> (tcgen05 3xTF32, window view)"),
                    ("lattice_apply_tc", "lattice_tc_kernel<4,2,0> (tcgen05 3xTF32, gather)"),
                    ("lattice_apply_fp32", "lattice_apply_kernel<float,4,2,0> (CUDA cores)")]
-    n32, ms32, kern_name = 0, 0.0, None
+    n32, ms32, kern_name, calls32 = 0, 0.0, None, 0
     for kind, name in apply_kinds:
         n32, ms32 = ctx.kernel_time(kind)
         kern_name = name
         if n32:
+            calls32 = ctx.kernel_calls(kind)
             break
     h16 = args.inner_tol >= 1e-2  # loose inner solves keep their final Krylov vectors in fp16
     hbm_kinds = {"arnoldi_dots32": ("dots16_kernel<true> (Arnoldi dot pass on the fp16 basis, two targets)" if h16 else
@@ -865,7 +871,9 @@ def run_ours(args, rank, world):
     for kind, name in hbm_kinds.items():
         nk, msk = ctx.kernel_time(kind)
         if nk:
-            hbm[kind] = {"kernel": name, "launches": nk, "total_ms": msk, "bytes": ctx.kernel_bytes(kind)}
+            calls = ctx.kernel_calls(kind)
+            hbm[kind] = {"kernel": name, "launches": nk, "calls": calls, "total_ms": msk, "bytes": ctx.kernel_bytes(kind),
+                         "ms_per_solve": msk / nk * calls / args.steps}
     res_kinds = [("lattice_apply_fft64", "FFT convolution, complex128 (lattice_fft.cu)"),
                  ("lattice_apply_oz", "lattice_oz_kernel<4,0> (tcgen05 bf16 slices, exact group sums, fp64-class)"),
                  ("lattice_apply_fp64", "lattice_apply_kernel<double,4,2,0> (FP64 CUDA cores)")]
@@ -919,7 +927,10 @@ def run_ours(args, rank, world):
                      roofline(kern_name, achieved, n32, avg32, flop_per_launch)),
         "hbm_kernels": {k: dict(v, achieved_gbs=v["bytes"] / (v["total_ms"] * 1e-3) / 1e9,
                                 frac=v["bytes"] / (v["total_ms"] * 1e-3) / 1e9 / HBM_PEAK_GBS) for k, v in hbm.items()},
-        "operator_apply": dict({"path": kern_name, "launches": n32, "avg_ms": avg32}, **(
+        "kernel_timing": f"CUDA events around the launches of the timed region; in the Arnoldi iterations one "
+                         f"iteration in {TIMING_EVERY} is timed (events at every launch cost ~3 ms per solve), "
+                         f"every other launch is timed; launches = all calls, timed_launches = the sample",
+        "operator_apply": dict({"path": kern_name, "launches": calls32, "timed_launches": n32, "avg_ms": avg32}, **(
             {"flop_per_apply": fft_work["flop_per_apply"], "achieved_tflops": fft_work["flop_per_apply"] / (avg32 * 1e-3) / 1e12,
              "fp32_peak_tflops": FMA_PEAKS.get("fp32_tflops"),
              "pass_bytes_per_apply": fft_work["pass_bytes"], "operand_bytes_per_apply": fft_work["operand_bytes"],

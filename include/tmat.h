@@ -141,8 +141,14 @@ int64_t tmat_ctx_launch_count(const tmat_ctx* ctx);
  * context stream around every operator-apply launch. tmat_ctx_kernel_time
  * synchronises and returns the launch count and summed duration of one kernel
  * kind since timing was (re)enabled: "lattice_apply_fp32", "lattice_apply_fp64",
- * "nbr_apply_fp32", "nbr_apply_fp64". Enabling again resets the record. */
+ * "nbr_apply_fp32", "nbr_apply_fp64". Enabling again resets the record.
+ * enable = 0 off, 1 every launch, n > 1: in the Arnoldi iterations of the complex64 inner
+ * solves only one iteration in n is timed (the events cost host and device time at every
+ * launch); launches outside those iterations are all timed. TMAT_EINVAL for enable < 0. */
 int tmat_ctx_set_timing(tmat_ctx* ctx, int enable);
+/* Calls of one kernel kind since timing was (re)enabled, timed or not (with enable = n > 1
+ * the timed launches of tmat_ctx_kernel_time are a sample of these). */
+int tmat_ctx_kernel_calls(tmat_ctx* ctx, const char* kind, int64_t* calls);
 /* Lattice operators (tmat_apply_lattice, the lattice path of tmat_solve, tmat_sweep)
  * are applied by FFT convolution when the grid fits (nx + max|dx| <= 1024 and
  * ny + max|dy| <= 1024): y_i = sum_o B_o x_{i+o} as a circular convolution on a

@@ -74,6 +74,7 @@ _SIGS = {
     "tmat_ctx_set_lattice_fft": [_vp, _int],
     "tmat_ctx_kernel_time": [_vp, ct.c_char_p, ct.POINTER(_i64), ct.POINTER(_d)],
     "tmat_ctx_kernel_bytes": [_vp, ct.c_char_p, ct.POINTER(_d)],
+    "tmat_ctx_kernel_calls": [_vp, ct.c_char_p, ct.POINTER(_i64)],
     "tmat_neighbors": [_vp, _vp, _i64, _d, _vp, _vp, ct.POINTER(_i64)],
     "tmat_subregions": [_vp, _i64, _i64, _i64, _i64, _i64, _vp, _vp, _vp, _vp, ct.POINTER(_i64), ct.POINTER(_i64)],
     "tmat_build": [_vp, _vp, _i64, _d, _d, _int, _vp, _vp],
@@ -197,7 +198,14 @@ class Context:
                                                 else (1 if on else 0)))
 
     def set_timing(self, on):
-        self.check(lib.tmat_ctx_set_timing(self.h, 1 if on else 0))
+        """True / False, or n > 1: one Arnoldi iteration in n of the complex64 inner solves timed."""
+        every = int(on) if not isinstance(on, bool) else (1 if on else 0)
+        self.check(lib.tmat_ctx_set_timing(self.h, every))
+
+    def kernel_calls(self, kind):
+        n = ct.c_int64()
+        self.check(lib.tmat_ctx_kernel_calls(self.h, kind.encode(), ct.byref(n)))
+        return n.value
 
     def kernel_time(self, kind):
         n, ms = ct.c_int64(), ct.c_double()

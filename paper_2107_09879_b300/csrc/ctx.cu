@@ -51,13 +51,15 @@ static cudaEvent_t pooled_event(tmat_ctx* ctx) {
 }
 
 cudaEvent_t timing_begin(tmat_ctx* ctx) {
-  if (!ctx->timing) return nullptr;
+  if (!ctx->timing || ctx->timing_skip) return nullptr;
   cudaEvent_t e = pooled_event(ctx);
   if (e) cudaEventRecord(e, ctx->stream);
   return e;
 }
 
 void timing_end(tmat_ctx* ctx, const char* kind, cudaEvent_t start, double bytes) {
+  if (!ctx->timing) return;
+  ctx->timed_calls[kind] += 1;
   if (!start) return;
   cudaEvent_t e = pooled_event(ctx);
   if (!e) return;
@@ -129,6 +131,7 @@ static void drop_events(tmat_ctx* ctx, bool destroy_all = false) {
     }
   ctx->timed.clear();
   ctx->timed_bytes.clear();
+  ctx->timed_calls.clear();
   if (destroy_all) {
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     ctx->event_pool.clear();
@@ -199,7 +202,18 @@ extern "C" int tmat_ctx_set_timing(tmat_ctx* ctx, int enable) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   drop_events(ctx);
+  if (enable < 0) return set_error(ctx, TMAT_EINVAL, "tmat_ctx_set_timing: enable must be >= 0");
   ctx->timing = enable != 0;
+  ctx->timing_every = enable > 1 ? enable : 1;
+  ctx->timing_skip = false;
+  ctx->timing_iter = 0;
+  return TMAT_OK;
+}
+
+extern "C" int tmat_ctx_kernel_calls(tmat_ctx* ctx, const char* kind, int64_t* calls) {
+  if (!ctx || !kind || !calls) return TMAT_EINVAL;
+  auto it = ctx->timed_calls.find(kind);
+  *calls = it == ctx->timed_calls.end() ? 0 : it->second;
   return TMAT_OK;
 }
 

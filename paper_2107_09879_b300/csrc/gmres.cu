@@ -1226,8 +1226,14 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
         // delayed CGS2: the Hessenberg column of iteration j is finalised at iteration j + 1
         float2* V32 = reinterpret_cast<float2*>(V);
         const size_t step_bytes = dcgs2_step_smem(m, maxv);
+        struct SkipReset {  // the sampling mark never outlives the loop (error returns included)
+          tmat_ctx* c;
+          ~SkipReset() { c->timing_skip = false; }
+        } skip_reset{ctx};
         for (;; ++j) {
           const bool final_only = j == m || st->iterations >= p.max_iter;
+          // sampled kernel timing: one iteration in timing_every is timed
+          ctx->timing_skip = ctx->timing_every > 1 && (ctx->timing_iter++ % ctx->timing_every) != 0;
           float2* vj = V32 + (int64_t)(h16 ? (j & 1) : j) * R * n;
           float2* w = final_only ? nullptr : V32 + (int64_t)(h16 ? ((j + 1) & 1) : j + 1) * R * n;
           if (!final_only) {

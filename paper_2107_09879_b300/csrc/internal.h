@@ -71,8 +71,14 @@ struct tmat_ctx {
   // mixed solves: inner solves with tolerance >= 1e-2 store the final Krylov vectors as
   // scaled fp16 (tmat_ctx_set_compressed_basis)
   bool compress_basis = true;
-  // kernel timing (off by default): event pairs recorded around operator launches
+  // kernel timing (off by default): event pairs recorded around operator launches; with
+  // timing_every = n > 1 only one Arnoldi iteration in n of the complex64 inner solves is
+  // timed (timing_skip marks the others), every call is still counted
   bool timing = false;
+  int timing_every = 1;
+  bool timing_skip = false;
+  int64_t timing_iter = 0;
+  std::map<std::string, int64_t> timed_calls;
   std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> timed;
   std::vector<cudaEvent_t> event_pool;          // recycled timing events
   std::map<std::string, double> timed_bytes;    // algorithmic bytes of the timed launches
