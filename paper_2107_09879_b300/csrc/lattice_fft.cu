@@ -1189,8 +1189,14 @@ static int fft_apply_t(tmat_ctx* ctx, const LatOp& a, const void* xv, void* yv, 
     if (smem > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, smem));
     const int hx = Mx >= 2 ? Mx / 2 + 1 : 1, hy = My >= 2 ? My / 2 + 1 : 1;
     const int64_t ntiles = (int64_t)hx * cdiv(hy, Cfg::NI);
-    int per_sm = 0;
-    TM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::THREADS, smem));
+    int per_sm = 0;  // queried once per kernel (its block size and shared memory are fixed)
+    auto occ = ctx->occupancy.find((const void*)kern);
+    if (occ != ctx->occupancy.end()) {
+      per_sm = occ->second;
+    } else {
+      TM_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::THREADS, smem));
+      ctx->occupancy[(const void*)kern] = per_sm;
+    }
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * std::max(1, per_sm));
     cudaEvent_t ev = timing_begin(ctx);
     kern<<<(unsigned)grid, Cfg::THREADS, smem, ctx->stream>>>(reinterpret_cast<const CS*>(a.fft_C),
