@@ -3,9 +3,34 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "../../include/tmat.h"
 
 namespace tmat {
+
+// Programmatic dependent launch: a kernel launched with launch_pdl (below) may become
+// resident while its predecessor in the stream drains; it waits here, before its first
+// global access, until the predecessor's writes are visible (a no-op for a plain launch).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch with programmatic stream serialisation (the kernel must begin with pdl_wait()):
+// the launch latency overlaps the predecessor's last wave instead of following it.
+template <typename... KArgs, typename... Args>
+static inline cudaError_t launch_pdl(cudaStream_t stream, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                     Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 template <typename R> struct cplx;
 template <> struct cplx<float> { using t = float2; };

@@ -115,6 +115,7 @@ dots32_kernel(const float2* __restrict__ V, int64_t vstride, int nvec, const flo
               int64_t rstride, float4* __restrict__ part, int maxv, int groups, int ranges,
               const int* __restrict__ active, const float2* __restrict__ w2 = nullptr,
               float4* __restrict__ part2 = nullptr) {
+  pdl_wait();
   const int r = blockIdx.y;
   if (active && !active[r]) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -563,6 +564,7 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 __global__ void __launch_bounds__(DCGS2_THREADS)
 dcgs2_step_kernel(GState s, const float4* __restrict__ part, const float4* __restrict__ part2, int RB, int j, int m,
                   int maxv, int R, int final_only, int stage_p) {
+  pdl_wait();
   const int r = blockIdx.x;
   if (r >= R) return;
   if (j == 0 && final_only) return;
@@ -777,6 +779,7 @@ dcgs2_step_kernel(GState s, const float4* __restrict__ part, const float4* __res
 __global__ void __launch_bounds__(256)
 dcgs2_update_kernel(float2* __restrict__ V, int64_t vstride, int j, GState s, int maxv, float2* __restrict__ w,
                     int64_t n, int64_t rstride) {
+  pdl_wait();
   const int r = blockIdx.y;
   if (!s.active[r]) return;
   extern __shared__ float2 dcs[];  // cA[0..j), cB[0..j]
@@ -864,6 +867,7 @@ __global__ void __launch_bounds__(256, 4)
 dots16_kernel(const uint2* __restrict__ Vh, int64_t hstride, int nh, const float2* __restrict__ u, int64_t n,
               int64_t rstride, float4* __restrict__ part, int maxv, int gh, int ranges, const int* __restrict__ active,
               float inv_sc, const float2* __restrict__ w2 = nullptr, float4* __restrict__ part2 = nullptr) {
+  pdl_wait();
   const int r = blockIdx.y;
   if (active && !active[r]) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -969,6 +973,7 @@ dots16_kernel(const uint2* __restrict__ Vh, int64_t hstride, int nh, const float
 __global__ void __launch_bounds__(256, 4)
 dcgs2_update16_kernel(uint2* __restrict__ Vh, int64_t hstride, int j, GState s, int maxv,
                       const float2* __restrict__ u, float2* __restrict__ w, int64_t n, int64_t rstride, float sc) {
+  pdl_wait();
   const int r = blockIdx.y;
   if (!s.active[r]) return;
   extern __shared__ float2 dcs[];  // cA[0..j) / sc, cB[0..j) / sc, cB[j]
@@ -1252,17 +1257,23 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
           cudaEvent_t ev_d = timing_begin(ctx);
           if (h16) {
             if (final_only)
-              dots16_kernel<false><<<dim3(dp.blocks, R), 256, 0, ctx->stream>>>(
-                  Vh, (int64_t)R * n, j, vj, n, rs, pf4, maxv, gh, dp.ranges, s.active, h16_inv);
+              TM_CUDA(ctx, launch_pdl(ctx->stream, dots16_kernel<false>, dim3(dp.blocks, R), dim3(256), 0,
+                                      (const uint2*)Vh, (int64_t)R * n, j, (const float2*)vj, n, rs, pf4, maxv, gh,
+                                      dp.ranges, (const int*)s.active, h16_inv, (const float2*)nullptr,
+                                      (float4*)nullptr));
             else
-              dots16_kernel<true><<<dim3(dp.blocks, R), 256, 0, ctx->stream>>>(
-                  Vh, (int64_t)R * n, j, vj, n, rs, pf4, maxv, gh, dp.ranges, s.active, h16_inv, w, pf4b);
+              TM_CUDA(ctx, launch_pdl(ctx->stream, dots16_kernel<true>, dim3(dp.blocks, R), dim3(256), 0,
+                                      (const uint2*)Vh, (int64_t)R * n, j, (const float2*)vj, n, rs, pf4, maxv, gh,
+                                      dp.ranges, (const int*)s.active, h16_inv, (const float2*)w, pf4b));
           } else if (final_only) {
-            dots32_kernel<false><<<dim3(dp.blocks, R), 256, 0, ctx->stream>>>(V32, (int64_t)R * n, j + 1, vj, n, rs,
-                                                                               pf4, maxv, dp.groups, dp.ranges, s.active);
+            TM_CUDA(ctx, launch_pdl(ctx->stream, dots32_kernel<false>, dim3(dp.blocks, R), dim3(256), 0,
+                                    (const float2*)V32, (int64_t)R * n, j + 1, (const float2*)vj, n, rs, pf4, maxv,
+                                    dp.groups, dp.ranges, (const int*)s.active, (const float2*)nullptr,
+                                    (float4*)nullptr));
           } else {
-            dots32_kernel<true><<<dim3(dp.blocks, R), 256, 0, ctx->stream>>>(
-                V32, (int64_t)R * n, j + 1, vj, n, rs, pf4, maxv, dp.groups, dp.ranges, s.active, w, pf4b);
+            TM_CUDA(ctx, launch_pdl(ctx->stream, dots32_kernel<true>, dim3(dp.blocks, R), dim3(256), 0,
+                                    (const float2*)V32, (int64_t)R * n, j + 1, (const float2*)vj, n, rs, pf4, maxv,
+                                    dp.groups, dp.ranges, (const int*)s.active, (const float2*)w, pf4b));
           }
           TM_LAUNCHED(ctx);
           // reads the j + 1 basis slots (the pending vector is slot j) and w
@@ -1278,8 +1289,9 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
             const int stage_p = step_bytes + pbytes <= 200 * 1024 ? 1 : 0;
             const size_t sm = step_bytes + (stage_p ? pbytes : 0);
             if (sm > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)dcgs2_step_kernel, sm));
-            dcgs2_step_kernel<<<R, DCGS2_THREADS, sm, ctx->stream>>>(s, pf4, pf4b, RB, j, m, maxv, R,
-                                                                    final_only ? 1 : 0, stage_p);
+            TM_CUDA(ctx, launch_pdl(ctx->stream, dcgs2_step_kernel, dim3(R), dim3(DCGS2_THREADS), sm, s,
+                                    (const float4*)pf4, (const float4*)pf4b, RB, j, m, maxv, R, final_only ? 1 : 0,
+                                    stage_p));
           }
           TM_LAUNCHED(ctx);
           // The flags are copied out behind the step kernel and read while the update pass

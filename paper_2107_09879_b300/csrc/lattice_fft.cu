@@ -405,6 +405,7 @@ fft256_ci_kernel(const std::conditional_t<IN_S, C<CR>, G<CR>>* __restrict__ in, 
                  std::conditional_t<OUT_S, C<CR>, G<CR>>* __restrict__ out, F256Lay lo, int cout, int P, int dir,
                  const double2* __restrict__ tw, const G<CR>* __restrict__ T, int64_t tstride,
                  const G<CR>* __restrict__ xs, float scale) {
+  pdl_wait();
   using CT = C<CR>;
   using SM = F256Smem<CR, EXT>;
   static_assert(EXT != 0 || OUT_CI, "the staged epilogue assumes the component-innermost output mapping");
@@ -825,6 +826,7 @@ template <typename CR, int L, int MODE, int RC_>
 __global__ void __launch_bounds__(Fft4Cfg<L, RC_, CR>::THREADS, Fft4Cfg<L, RC_, CR>::MIN_BLOCKS)
 fft_mul4_kernel(const C<CR>* __restrict__ Cq, const C<CR>* __restrict__ Xh, C<CR>* __restrict__ Yh, int Mx, int My,
                 int R_, const int* __restrict__ sym, int* __restrict__ err, int64_t cstride) {
+  pdl_wait();
   using Cfg = Fft4Cfg<L, RC_, CR>;
   using CT = C<CR>;
   constexpr int NI = Cfg::NI, RC = Cfg::RC, NCOL = Cfg::NCOL, P = 2 * L, SC = Cfg::SC, SW = Cfg::SW,
@@ -1170,10 +1172,11 @@ static int fft_apply_t(tmat_ctx* ctx, const LatOp& a, const void* xv, void* yv, 
       TM_TRY(set_smem_limit(ctx, (const void*)k1, sm));
       TM_TRY(set_smem_limit(ctx, (const void*)k2, sm));
     }
-    k1<<<gy, 256, sm, ctx->stream>>>(xg, lx, nx, w1s, lt1_out, Mx, P, -1, tw, Tg, a.t_stride, nullptr, 1.f);
+    TM_CUDA(ctx, launch_pdl(ctx->stream, k1, gy, dim3(256), sm, xg, lx, nx, w1s, lt1_out, Mx, P, -1, tw, Tg,
+                            a.t_stride, (const G<CR>*)nullptr, 1.f));
     TM_LAUNCHED(ctx);
-    k2<<<gk, 256, sm, ctx->stream>>>(w1s, lt1_in, ny, reinterpret_cast<CS*>(Xh), lspec, My, P, -1, tw, Tg, a.t_stride,
-                                     nullptr, 1.f);
+    TM_CUDA(ctx, launch_pdl(ctx->stream, k2, gk, dim3(256), sm, (const CS*)w1s, lt1_in, ny, reinterpret_cast<CS*>(Xh),
+                            lspec, My, P, -1, tw, Tg, a.t_stride, (const G<CR>*)nullptr, 1.f));
     TM_LAUNCHED(ctx);
   } else {
     fft_embed_kernel<R, MODE == 1 ? 1 : 0><<<tg, tb, 0, ctx->stream>>>(x, T, nx, ny, P, R_, grid, a.t_stride);
@@ -1199,9 +1202,9 @@ static int fft_apply_t(tmat_ctx* ctx, const LatOp& a, const void* xv, void* yv, 
     }
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * std::max(1, per_sm));
     cudaEvent_t ev = timing_begin(ctx);
-    kern<<<(unsigned)grid, Cfg::THREADS, smem, ctx->stream>>>(reinterpret_cast<const CS*>(a.fft_C),
-                                                              reinterpret_cast<const CS*>(Xh), reinterpret_cast<CS*>(Yh),
-                                                              Mx, My, R_, a.fft_sym, a.fft_err, a.fft_cstride);
+    TM_CUDA(ctx, launch_pdl(ctx->stream, kern, dim3((unsigned)grid), dim3(Cfg::THREADS), smem,
+                            reinterpret_cast<const CS*>(a.fft_C), reinterpret_cast<const CS*>(Xh),
+                            reinterpret_cast<CS*>(Yh), Mx, My, R_, a.fft_sym, a.fft_err, a.fft_cstride));
     TM_LAUNCHED(ctx);
     // the quad-form spectra once, the RHS spectra in and out
     const double mul_bytes =
@@ -1237,11 +1240,11 @@ static int fft_apply_t(tmat_ctx* ctx, const LatOp& a, const void* xv, void* yv, 
     const size_t sm3 = F256Smem<CR, -1>::BYTES, sm4 = F256Smem<CR, MODE>::BYTES;
     if (sm3 > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)k3, sm3));
     if (sm4 > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)k4, sm4));
-    k3<<<gk, 256, sm3, ctx->stream>>>(reinterpret_cast<const CS*>(Yh), lspec, My, w1s, lt2_out, ny, P, +1, tw, Tg,
-                                      a.t_stride, nullptr, 1.f);
+    TM_CUDA(ctx, launch_pdl(ctx->stream, k3, gk, dim3(256), sm3, reinterpret_cast<const CS*>(Yh), lspec, My, w1s,
+                            lt2_out, ny, P, +1, tw, Tg, a.t_stride, (const G<CR>*)nullptr, 1.f));
     TM_LAUNCHED(ctx);
-    k4<<<gy, 256, sm4, ctx->stream>>>(w1s, lt2_in, Mx, reinterpret_cast<G<CR>*>(yv), lx, nx, P, +1, tw, Tg, a.t_stride,
-                                      xg, (float)(1.0 / (double)F));
+    TM_CUDA(ctx, launch_pdl(ctx->stream, k4, gy, dim3(256), sm4, (const CS*)w1s, lt2_in, Mx, reinterpret_cast<G<CR>*>(yv),
+                            lx, nx, P, +1, tw, Tg, a.t_stride, xg, (float)(1.0 / (double)F)));
     TM_LAUNCHED(ctx);
   } else {
     C<R>* Yc = Xh;  // X^ is no longer needed
