@@ -173,6 +173,7 @@ extern "C" int tmat_ctx_destroy(tmat_ctx* ctx) {
   for (auto& kv : ctx->tables) free_tables(kv.second);
   drop_events(ctx, true);
   if (ctx->flag_event) cudaEventDestroy(ctx->flag_event);
+  if (ctx->flag_host) cudaFreeHost(ctx->flag_host);
   cudaFreeHost(ctx->pinned);
   delete ctx;
   return TMAT_OK;

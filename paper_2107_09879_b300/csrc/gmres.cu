@@ -4,7 +4,9 @@
 // classical Gram-Schmidt applied twice (CGS2) with fp64 dot products and fp64
 // Hessenberg / Givens / least-squares work; basis vectors are complex64 or
 // complex128. Reductions are two-stage with a fixed order (deterministic).
+#include <atomic>
 #include <chrono>
+#include <cstring>
 #include <cmath>
 
 #include <cuda_fp16.h>
@@ -556,6 +558,13 @@ __device__ __forceinline__ void dcgs2_cp16(void* dst, const void* src) {  // 16-
   const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
 }
+// the RHS's convergence flag to mapped host memory, then the step's tag (the host reads the
+// flag once it sees the tag)
+__device__ __forceinline__ void dcgs2_publish(int* hflag, int r, int act, int tag) {
+  reinterpret_cast<volatile int*>(hflag)[r] = act;
+  __threadfence_system();
+  reinterpret_cast<volatile int*>(hflag)[TMAT_MAX_RHS + r] = tag;
+}
 __device__ __forceinline__ double warp_sum_d(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -563,7 +572,7 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 __global__ void __launch_bounds__(DCGS2_THREADS)
 dcgs2_step_kernel(GState s, const float4* __restrict__ part, const float4* __restrict__ part2, int RB, int j, int m,
-                  int maxv, int R, int final_only, int stage_p) {
+                  int maxv, int R, int final_only, int stage_p, int* __restrict__ hflag, int tag) {
   pdl_wait();
   const int r = blockIdx.x;
   if (r >= R) return;
@@ -612,7 +621,10 @@ dcgs2_step_kernel(GState s, const float4* __restrict__ part, const float4* __res
     const int act0 = s.active[r];  // read while the copies are in flight (an inactive RHS leaves)
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
-    if (!act0) return;
+    if (!act0) {
+      if (tag && tid == 0) dcgs2_publish(hflag, r, 0, tag);
+      return;
+    }
     int tps = 32;  // threads per sum (a power of two)
     while (tps > 1 && tps * S > DCGS2_THREADS) tps >>= 1;
     const int per_round = DCGS2_THREADS / tps;
@@ -719,6 +731,7 @@ dcgs2_step_kernel(GState s, const float4* __restrict__ part, const float4* __res
       }
       if (!act) s.active[r] = 0;
       act_sh = act;
+      if (tag) dcgs2_publish(hflag, r, act, tag);
     }
   }
   __syncthreads();
@@ -1138,6 +1151,46 @@ static int vec_norms(tmat_ctx* ctx, const C<VR>* v, int64_t n, int64_t rstride, 
 // Restarted GMRES on vectors of type VR. b (VR, internal layout, R x n) and the
 // solution x (complex128, zero on entry) both device. Convergence when the true
 // residual ||b - K x|| <= tol ||b|| per RHS.
+// the mapped flag words (allocated once per context)
+static int flags_mapped(tmat_ctx* ctx) {
+  if (ctx->flag_host) return TMAT_OK;
+  void* h = nullptr;
+  TM_CUDA(ctx, cudaHostAlloc(&h, sizeof(int) * 2 * TMAT_MAX_RHS, cudaHostAllocMapped));
+  std::memset(h, 0, sizeof(int) * 2 * TMAT_MAX_RHS);
+  void* d = nullptr;
+  if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(h);
+    return set_error(ctx, TMAT_ECUDA, "gmres: no device mapping of the flag words");
+  }
+  ctx->flag_host = (int*)h;
+  ctx->flag_dev = (int*)d;
+  return TMAT_OK;
+}
+// Waits until every RHS's step has published `tag`, then reports whether any is active.
+// Bounded: past 10 s it synchronises the stream (which returns a kernel fault as an error)
+// and gives up if the tags are still missing.
+static int flags_wait(tmat_ctx* ctx, int R, int tag, bool* any) {
+  const volatile int* f = ctx->flag_host;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (uint64_t spin = 0;; ++spin) {
+    bool all = true;
+    for (int r = 0; r < R; ++r) all = all && f[TMAT_MAX_RHS + r] == tag;
+    if (all) break;
+    if ((spin & 1023) == 1023 && std::chrono::steady_clock::now() - t0 > std::chrono::seconds(10)) {
+      TM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      all = true;
+      for (int r = 0; r < R; ++r) all = all && f[TMAT_MAX_RHS + r] == tag;
+      if (!all) return set_error(ctx, TMAT_ECUDA, "gmres: convergence flags were not published");
+      break;
+    }
+  }
+  std::atomic_thread_fence(std::memory_order_acquire);
+  *any = false;
+  for (int r = 0; r < R; ++r) *any = *any || f[r] != 0;
+  return TMAT_OK;
+}
+
 template <typename VR>
 static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b, double2* x, int R, int64_t n,
                      const GmresParams& p, GmresStats* st) {
@@ -1281,7 +1334,18 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
                      h16 ? 4.0 * R * n * j + 8.0 * R * n * (1 + (final_only ? 0 : 1))
                          : 8.0 * R * n * (j + 1 + (final_only ? 0 : 1)));
           // the dot sums (ranges / 8 partials each), column j-1 final, its rotation, column j
-          // and the update coefficients
+          // and the update coefficients. The step publishes its convergence flags to mapped
+          // host memory (with a tag) and the host reads them while the update pass runs (it
+          // skips every RHS that has converged): no copy or event between the two kernels, so
+          // the update launch overlaps the step, and the device does not idle through the
+          // host's check before the next operator launch.
+          const bool check = j >= 1 && !final_only && j % sync_every == 0;
+          int tag = 0;
+          if (check) {
+            TM_TRY(flags_mapped(ctx));
+            if (++ctx->flag_tag <= 0) ctx->flag_tag = 1;
+            tag = ctx->flag_tag;
+          }
           {
             // the partials go through shared memory with everything else when they fit
             const int RB = dp.ranges / 8, S = final_only ? j + 1 : 2 * (j + 1);
@@ -1291,31 +1355,19 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
             if (sm > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)dcgs2_step_kernel, sm));
             TM_CUDA(ctx, launch_pdl(ctx->stream, dcgs2_step_kernel, dim3(R), dim3(DCGS2_THREADS), sm, s,
                                     (const float4*)pf4, (const float4*)pf4b, RB, j, m, maxv, R, final_only ? 1 : 0,
-                                    stage_p));
+                                    stage_p, ctx->flag_dev, tag));
           }
           TM_LAUNCHED(ctx);
-          // The flags are copied out behind the step kernel and read while the update pass
-          // runs (it skips every RHS that has converged), so the device does not idle through
-          // the host's check before the next operator launch.
-          const bool check = j >= 1 && (final_only || j % sync_every == 0);
-          int* ipin = (int*)ctx->pinned;
-          if (check) {
-            if (!ctx->flag_event) TM_CUDA(ctx, cudaEventCreateWithFlags(&ctx->flag_event, cudaEventDisableTiming));
-            TM_CUDA(ctx, cudaMemcpyAsync(ipin, s.active, sizeof(int) * R, cudaMemcpyDeviceToHost, ctx->stream));
-            TM_CUDA(ctx, cudaEventRecord(ctx->flag_event, ctx->stream));
-          }
-          if (final_only) {
-            if (check) TM_CUDA(ctx, cudaEventSynchronize(ctx->flag_event));
-            break;
-          }
+          if (final_only) break;
           cudaEvent_t ev_u = timing_begin(ctx);
           if (h16) {
             const unsigned gu = (unsigned)std::min<int64_t>(cdiv(n / 2, 256), (int64_t)ctx->num_sms * 16);
-            dcgs2_update16_kernel<<<dim3(gu, R), 256, sizeof(float2) * (2 * (size_t)j + 2), ctx->stream>>>(
-                Vh, (int64_t)R * n, j, s, maxv, vj, w, n, rs, h16_sc);
+            TM_CUDA(ctx, launch_pdl(ctx->stream, dcgs2_update16_kernel, dim3(gu, R), dim3(256),
+                                    sizeof(float2) * (2 * (size_t)j + 2), Vh, (int64_t)R * n, j, s, maxv,
+                                    (const float2*)vj, w, n, rs, h16_sc));
           } else {
-            dcgs2_update_kernel<<<dim3(g1, R), 256, sizeof(float2) * (2 * (size_t)j + 2), ctx->stream>>>(
-                V32, (int64_t)R * n, j, s, maxv, w, n, rs);
+            TM_CUDA(ctx, launch_pdl(ctx->stream, dcgs2_update_kernel, dim3(g1, R), dim3(256),
+                                    sizeof(float2) * (2 * (size_t)j + 2), V32, (int64_t)R * n, j, s, maxv, w, n, rs));
           }
           TM_LAUNCHED(ctx);
           // reads slots 0..j and w, writes slot j (j > 0) and w (compressed: fp16 slots 0..j-1,
@@ -1323,9 +1375,8 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
           timing_end(ctx, "arnoldi_update32", ev_u,
                      h16 ? 4.0 * R * n * (j + 1) + 8.0 * R * n * 3 : 8.0 * R * n * (j + 2 + (j > 0 ? 1 : 0) + 1));
           if (check) {
-            TM_CUDA(ctx, cudaEventSynchronize(ctx->flag_event));
             bool any = false;
-            for (int r = 0; r < R; ++r) any = any || ipin[r];
+            TM_TRY(flags_wait(ctx, R, tag, &any));
             if (!any) break;
           }
         }

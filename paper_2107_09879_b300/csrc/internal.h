@@ -98,6 +98,11 @@ struct tmat_ctx {
   bool field_mixed = false;  // near fields in fp32 with fp64 phases (tmat_ctx_set_field_precision)
   void* pinned = nullptr;  // small pinned host staging area (status words)
   cudaEvent_t flag_event = nullptr;  // marks the copy of convergence flags into `pinned`
+  // mapped pinned words the Arnoldi step kernel publishes its convergence flags to:
+  // [0, TMAT_MAX_RHS) active flags, [TMAT_MAX_RHS, 2 TMAT_MAX_RHS) the tag of the step
+  int* flag_host = nullptr;
+  int* flag_dev = nullptr;
+  int flag_tag = 0;
 };
 
 namespace tmat {
