@@ -140,7 +140,7 @@ class ClockSampler:
 
 
 # kernel timing in the timed region: one Arnoldi iteration in TIMING_EVERY carries CUDA events
-TIMING_EVERY = 16
+TIMING_EVERY = 32
 
 # DRAM bytes (read + write) / algorithmic bytes of one ncu capture of each HBM-bound kernel as
 # it stands (the quad block product on the 200 x 200 lattice: 205.88 MB read + 27.22 MB written

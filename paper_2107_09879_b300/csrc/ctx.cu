@@ -110,6 +110,12 @@ int stage_out(tmat_ctx* ctx, const char* name, void* user, size_t bytes, Staged*
   return scratch(ctx, name, bytes, &s->dev);
 }
 
+int aux_stream_ready(tmat_ctx* ctx) {
+  if (!ctx->aux_stream) TM_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
+  if (!ctx->aux_event) TM_CUDA(ctx, cudaEventCreateWithFlags(&ctx->aux_event, cudaEventDisableTiming));
+  return TMAT_OK;
+}
+
 int finish_out(tmat_ctx* ctx, Staged* s) {
   if (s->user && s->host && s->bytes) {
     TM_CUDA(ctx, cudaMemcpyAsync(const_cast<void*>(s->user), s->dev, s->bytes, cudaMemcpyDeviceToHost, ctx->stream));
@@ -174,6 +180,11 @@ extern "C" int tmat_ctx_destroy(tmat_ctx* ctx) {
   drop_events(ctx, true);
   if (ctx->flag_event) cudaEventDestroy(ctx->flag_event);
   if (ctx->flag_host) cudaFreeHost(ctx->flag_host);
+  if (ctx->aux_stream) {
+    cudaStreamSynchronize(ctx->aux_stream);
+    cudaStreamDestroy(ctx->aux_stream);
+  }
+  if (ctx->aux_event) cudaEventDestroy(ctx->aux_event);
   cudaFreeHost(ctx->pinned);
   delete ctx;
   return TMAT_OK;

@@ -38,12 +38,22 @@ extern "C" int tmat_forward(tmat_ctx* ctx, const double* pos, int64_t N, const t
   const int rc = tmat_solve(ctx, d_pos, N, wavelength, n_bg, nmax, (const tmat_c128*)T, (const tmat_c128*)a0, R, opts,
                             s, nullptr, info);
   if (rc != TMAT_OK && rc != TMAT_ENOCONV) return rc;
-  if (M > 0) {
-    for (int r = 0; r < R; ++r)
-      TM_TRY(tmat_field(ctx, d_pos, N, wavelength, n_bg, nmax, s + (int64_t)r * N * P, (const double*)spts.dev, M,
-                        (tmat_c128*)sE.dev + (int64_t)r * M * 3));
+  // a host solution buffer is filled on the side stream while the fields are computed
+  const bool s_aside = s_out && ss.host && M > 0;
+  if (s_aside) {
+    TM_TRY(aux_stream_ready(ctx));
+    TM_CUDA(ctx, cudaEventRecord(ctx->aux_event, ctx->stream));
+    TM_CUDA(ctx, cudaStreamWaitEvent(ctx->aux_stream, ctx->aux_event, 0));
+    TM_CUDA(ctx, cudaMemcpyAsync(s_out, ss.dev, ss.bytes, cudaMemcpyDeviceToHost, ctx->aux_stream));
   }
-  if (s_out) TM_TRY(finish_out(ctx, &ss));
-  TM_TRY(finish_out(ctx, &sE));
-  return rc;
+  int frc = TMAT_OK;
+  if (M > 0) {
+    for (int r = 0; r < R && frc == TMAT_OK; ++r)
+      frc = tmat_field(ctx, d_pos, N, wavelength, n_bg, nmax, s + (int64_t)r * N * P, (const double*)spts.dev, M,
+                       (tmat_c128*)sE.dev + (int64_t)r * M * 3);
+  }
+  if (frc == TMAT_OK && s_out && !s_aside) frc = finish_out(ctx, &ss);
+  if (frc == TMAT_OK) frc = finish_out(ctx, &sE);
+  if (s_aside) TM_CUDA(ctx, cudaStreamSynchronize(ctx->aux_stream));  // the copy ends before the scratch is reused
+  return frc != TMAT_OK ? frc : rc;
 }

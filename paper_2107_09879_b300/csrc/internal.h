@@ -103,6 +103,9 @@ struct tmat_ctx {
   int* flag_host = nullptr;
   int* flag_dev = nullptr;
   int flag_tag = 0;
+  // a second stream (created on first use) for copies that overlap work on `stream`
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t aux_event = nullptr;
 };
 
 namespace tmat {
@@ -157,6 +160,8 @@ struct Staged {
 int stage_in(tmat_ctx* ctx, const char* name, const void* user, size_t bytes, Staged* s);
 int stage_out(tmat_ctx* ctx, const char* name, void* user, size_t bytes, Staged* s);
 int finish_out(tmat_ctx* ctx, Staged* s);
+// The side stream and its event, created once per context.
+int aux_stream_ready(tmat_ctx* ctx);
 
 __host__ __device__ inline int num_coeffs(int nmax) { return 2 * nmax * (nmax + 2); }
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
