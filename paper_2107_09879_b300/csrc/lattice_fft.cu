@@ -304,13 +304,20 @@ __device__ __forceinline__ void fft_dft16(C<CR> (&v)[16], const C<CR>* W, int di
 constexpr int F256_RS = 16 * 17;  // exchange stride of a row (k1 blocks of 17)
 constexpr int F256_OS = 257;      // staging stride of a row for transposed stores
 
-template <bool TOUT>
-__global__ void __launch_bounds__(256, 4)
-fft256_rows_kernel(const float2* __restrict__ in, int64_t in_batch_stride, int in_pitch, int cin, int nrows,
-                   float2* __restrict__ out, int64_t out_batch_stride, int out_pitch, int cout, int dir,
-                   const double2* __restrict__ tw) {
-  __shared__ float2 W[256];
-  __shared__ float2 ex[16 * F256_RS];  // exchange, then (TOUT) the output staging [16][257]
+// CR = float: complex64; CR = DF: double-float arithmetic with complex128 (G) or double-float
+// storage (IN_S / OUT_S) in global memory, as in the passes below.
+template <typename CR> struct F256RowsSmem {
+  static constexpr size_t BYTES = sizeof(C<CR>) * (256 + 16 * F256_RS);
+};
+template <typename CR, bool TOUT, bool IN_S, bool OUT_S>
+__global__ void __launch_bounds__(256, std::is_same_v<CR, float> ? 4 : 2)
+fft256_rows_kernel(const std::conditional_t<IN_S, C<CR>, G<CR>>* __restrict__ in, int64_t in_batch_stride,
+                   int in_pitch, int cin, int nrows, std::conditional_t<OUT_S, C<CR>, G<CR>>* __restrict__ out,
+                   int64_t out_batch_stride, int out_pitch, int cout, int dir, const double2* __restrict__ tw) {
+  using CT = C<CR>;
+  extern __shared__ __align__(16) unsigned char f256r_sm[];
+  CT* W = reinterpret_cast<CT*>(f256r_sm);
+  CT* ex = W + 256;  // exchange, then (TOUT) the output staging [16][257]
   static_assert(16 * F256_OS <= 16 * F256_RS, "staging fits the exchange buffer");
   const int b = blockIdx.y;
   const int row0 = blockIdx.x * 16;
@@ -318,44 +325,58 @@ fft256_rows_kernel(const float2* __restrict__ in, int64_t in_batch_stride, int i
   for (int m = threadIdx.x; m < 256; m += blockDim.x) {
     // W256^m = tw[4 m] (m < 128), -tw[4 (m - 128)] (m >= 128), tw = e^{-2 pi i k / 1024}
     const double2 t = tw[4 * (m & 127)];
-    const float sg = m < 128 ? 1.f : -1.f;
-    W[m] = make_float2(sg * (float)t.x, sg * (dir < 0 ? (float)t.y : -(float)t.y));
+    if constexpr (std::is_same_v<CR, float>) {
+      const float sg = m < 128 ? 1.f : -1.f;
+      W[m] = make_float2(sg * (float)t.x, sg * (dir < 0 ? (float)t.y : -(float)t.y));
+    } else {
+      const CT w = cfrom64<CR>(t.x, dir < 0 ? t.y : -t.y);
+      W[m] = m < 128 ? w : cneg(w);
+    }
   }
   const int row = row0 + rr;
   const bool live = row < nrows;
-  float2 v[16];
-  const float2* src = in + (int64_t)b * in_batch_stride + (int64_t)row * in_pitch;
+  CT v[16];
+  const auto* src = in + (int64_t)b * in_batch_stride + (int64_t)row * in_pitch;
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
     const int c = a + 16 * q;
-    v[q] = (live && c < cin) ? src[c] : make_float2(0.f, 0.f);
+    if (live && c < cin) {
+      if constexpr (IN_S) v[q] = src[c];
+      else v[q] = gload<CR>(src[c]);
+    } else {
+      v[q] = czero<CR>();
+    }
   }
   __syncthreads();  // W
-  fft_dft16<float>(v, W, dir);  // v[k1] = Y[a][k1]
-  float2* exr = ex + rr * F256_RS;
+  fft_dft16<CR>(v, W, dir);  // v[k1] = Y[a][k1]
+  CT* exr = ex + rr * F256_RS;
 #pragma unroll
   for (int k1 = 0; k1 < 16; ++k1) exr[k1 * 17 + a] = k1 ? cmul(v[k1], W[(a * k1) & 255]) : v[k1];
   __syncwarp();
   const int k1 = a;  // this thread now owns column k1: Y[a'][k1] for a' = 0..15
 #pragma unroll
   for (int q = 0; q < 16; ++q) v[q] = exr[k1 * 17 + q];
-  fft_dft16<float>(v, W, dir);  // v[k2] = X[k1 + 16 k2]
-  float2* dst = out + (int64_t)b * out_batch_stride;
+  fft_dft16<CR>(v, W, dir);  // v[k2] = X[k1 + 16 k2]
+  auto* dst = out + (int64_t)b * out_batch_stride;
+  auto put = [&](int64_t o, const CT& z) {
+    if constexpr (OUT_S) dst[o] = z;
+    else dst[o] = gstore<CR>(z);
+  };
   if (TOUT) {
     __syncthreads();  // every row's exchange reads are done before the staging overwrites
-    float2* st = ex + rr * F256_OS;
+    CT* st = ex + rr * F256_OS;
 #pragma unroll
     for (int k2 = 0; k2 < 16; ++k2) st[k1 + 16 * k2] = v[k2];
     __syncthreads();
     // out[k][row0 + r]: consecutive threads take consecutive rows of one k
     const int r = threadIdx.x & 15, nr = min(16, nrows - row0);
     for (int k = threadIdx.x >> 4; k < cout; k += 16)
-      if (r < nr) dst[(int64_t)k * out_pitch + row0 + r] = ex[r * F256_OS + k];
+      if (r < nr) put((int64_t)k * out_pitch + row0 + r, ex[r * F256_OS + k]);
   } else if (live) {
 #pragma unroll
     for (int k2 = 0; k2 < 16; ++k2) {
       const int k = k1 + 16 * k2;
-      if (k < cout) dst[(int64_t)row * out_pitch + k] = v[k2];
+      if (k < cout) put((int64_t)row * out_pitch + k, v[k2]);
     }
   }
 }
@@ -530,14 +551,16 @@ static int fft_rows(tmat_ctx* ctx, const C<R>* in, int64_t in_bs, int in_pitch, 
   using GI = std::conditional_t<IN_S, C<CR>, G<CR>>;
   using GO = std::conditional_t<OUT_S, C<CR>, G<CR>>;
   static_assert(sizeof(G<CR>) == sizeof(C<R>) && sizeof(C<CR>) == sizeof(C<R>), "global element type");
-  if constexpr (std::is_same_v<R, float> && !TIN) {
-    if (len == 256) {  // the complex64 operators' rows: four-step kernel
+  if constexpr (!TIN) {
+    if (len == 256) {  // 256-point rows: the four-step kernel (complex64 or double-float)
+      auto kern = fft256_rows_kernel<CR, TOUT, IN_S, OUT_S>;
+      const size_t sm = F256RowsSmem<CR>::BYTES;
+      if (sm > 48 * 1024) TM_TRY(set_smem_limit(ctx, (const void*)kern, sm));
       for (int64_t b0 = 0; b0 < nbatch; b0 += 65535) {
         const int nb = (int)std::min<int64_t>(65535, nbatch - b0);
         dim3 grid((unsigned)cdiv(nrows, 16), (unsigned)nb);
-        fft256_rows_kernel<TOUT><<<grid, 256, 0, ctx->stream>>>((const float2*)(in + b0 * in_bs), in_bs, in_pitch, cin,
-                                                               nrows, (float2*)(out + b0 * out_bs), out_bs, out_pitch,
-                                                               cout, dir, tw);
+        kern<<<grid, 256, sm, ctx->stream>>>((const GI*)(in + b0 * in_bs), in_bs, in_pitch, cin, nrows,
+                                             (GO*)(out + b0 * out_bs), out_bs, out_pitch, cout, dir, tw);
         TM_LAUNCHED(ctx);
       }
       return TMAT_OK;
