@@ -1,5 +1,7 @@
 // Context, error reporting, scratch buffers and host/device staging.
 #include <cstring>
+#include <mutex>
+#include <utility>
 
 #include "internal.h"
 
@@ -17,7 +19,9 @@ int set_error(tmat_ctx* ctx, int code, const char* fmt, ...) {
 
 int cuda_fail(tmat_ctx* ctx, cudaError_t e, const char* what, const char* file, int line) {
   int code = (e == cudaErrorMemoryAllocation) ? TMAT_ENOMEM : TMAT_ECUDA;
-  if (e == cudaErrorMemoryAllocation) cudaGetLastError();  // not sticky: clear it
+  // a non-sticky error (allocation, launch configuration) is cleared so that the next launch
+  // check does not report it again; a sticky one stays whatever is done here
+  cudaGetLastError();
   return set_error(ctx, code, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
 }
 
@@ -68,11 +72,17 @@ void timing_end(tmat_ctx* ctx, const char* kind, cudaEvent_t start, double bytes
   ctx->timed_bytes[kind] += bytes;
 }
 
+// The limit is an attribute of the kernel (per device), shared by every context of the
+// process: the record is process-wide and the limit only grows, so that one context never
+// lowers it below what another has launched with.
 int set_smem_limit(tmat_ctx* ctx, const void* func, size_t bytes) {
-  auto it = ctx->smem_attr.find(func);
-  if (it != ctx->smem_attr.end() && it->second >= (int)bytes) return TMAT_OK;
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> limits;
+  std::lock_guard<std::mutex> lock(mu);
+  int& cur = limits[{ctx->device, func}];
+  if (cur >= (int)bytes) return TMAT_OK;
   TM_CUDA(ctx, cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  ctx->smem_attr[func] = (int)bytes;
+  cur = (int)bytes;
   return TMAT_OK;
 }
 

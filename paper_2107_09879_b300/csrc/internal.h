@@ -82,7 +82,6 @@ struct tmat_ctx {
   std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> timed;
   std::vector<cudaEvent_t> event_pool;          // recycled timing events
   std::map<std::string, double> timed_bytes;    // algorithmic bytes of the timed launches
-  std::map<const void*, int> smem_attr;         // dynamic shared memory limit set per kernel
   std::map<const void*, int> occupancy;         // resident CTAs per SM queried per kernel (fixed shapes)
   int device = 0;
   cudaStream_t stream = nullptr;
