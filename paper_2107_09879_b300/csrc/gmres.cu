@@ -214,6 +214,7 @@ constexpr int RED2_THREADS = 64;
 __global__ void __launch_bounds__(RED2_THREADS)
 reduce_kernel(const double2* __restrict__ part, int nb, int nvec, int maxv, double2* __restrict__ out,
               const int* __restrict__ active) {
+  pdl_wait();
   const int r = blockIdx.x, k = blockIdx.y;
   if (k >= nvec) return;
   if (active && !active[r]) return;
@@ -244,7 +245,8 @@ reduce_kernel(const double2* __restrict__ part, int nb, int nvec, int maxv, doub
 
 static inline void launch_reduce(tmat_ctx* ctx, const double2* part, int nb, int nvec, int maxv, double2* out,
                                  const int* active, int R) {
-  reduce_kernel<<<dim3(R, nvec), RED2_THREADS, 0, ctx->stream>>>(part, nb, nvec, maxv, out, active);
+  // launched behind its producer's last wave (the launch's result is checked by the caller)
+  launch_pdl(ctx->stream, reduce_kernel, dim3(R, nvec), dim3(RED2_THREADS), 0, part, nb, nvec, maxv, out, active);
 }
 
 // ||v[r]||^2 block partials of complex64 vectors into part[(r*maxv + 0)*nb + b] (as the
@@ -252,6 +254,7 @@ static inline void launch_reduce(tmat_ctx* ctx, const double2* part, int nb, int
 __global__ void __launch_bounds__(256)
 norm32_kernel(const float2* __restrict__ v, int64_t n, int64_t rstride, double2* __restrict__ part, int maxv,
               const int* __restrict__ active) {
+  pdl_wait();
   const int r = blockIdx.y;
   if (active && !active[r]) return;
   const int64_t n2 = n >> 1;
@@ -287,6 +290,7 @@ norm32_kernel(const float2* __restrict__ v, int64_t n, int64_t rstride, double2*
 __global__ void __launch_bounds__(256)
 norm64_kernel(const double2* __restrict__ v, int64_t n, int64_t rstride, double2* __restrict__ part, int maxv,
               const int* __restrict__ active) {
+  pdl_wait();
   const int r = blockIdx.y;
   if (active && !active[r]) return;
   const double2* vr = v + r * rstride;
@@ -370,6 +374,7 @@ xupdate32_kernel(const float2* __restrict__ V, int64_t vstride, int nvec, const 
 template <typename XR, typename YR>
 __global__ void scale_kernel(const C<XR>* __restrict__ x, C<YR>* __restrict__ y, int64_t n, int64_t rstride,
                              const double* __restrict__ norm, int inv, const int* __restrict__ active) {
+  pdl_wait();
   const int r = blockIdx.y;
   if (active && !active[r]) return;
   double s = norm ? norm[r] : 1.0;
@@ -396,6 +401,7 @@ __global__ void scale_kernel(const C<XR>* __restrict__ x, C<YR>* __restrict__ y,
 template <typename BR, typename YR>
 __global__ void residual_kernel(const C<BR>* __restrict__ b, const C<YR>* __restrict__ y, C<BR>* __restrict__ out,
                                 int64_t total) {
+  pdl_wait();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     C<BR> bv = b[i];
     C<YR> yv = y[i];
@@ -408,6 +414,7 @@ __global__ void residual_kernel(const C<BR>* __restrict__ b, const C<YR>* __rest
 
 template <typename XR, typename YR>
 __global__ void convert_kernel(const C<XR>* __restrict__ x, C<YR>* __restrict__ y, int64_t total) {
+  pdl_wait();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = mk<YR>((YR)x[i].x, (YR)x[i].y);
 }
@@ -415,6 +422,7 @@ __global__ void convert_kernel(const C<XR>* __restrict__ x, C<YR>* __restrict__ 
 // x[r] += alpha[r] * d[r]
 __global__ void axpy_scaled_kernel(double2* __restrict__ x, const double2* __restrict__ d, const double* __restrict__ alpha,
                                    int64_t n, int64_t rstride) {
+  pdl_wait();
   const int r = blockIdx.y;
   const double a = alpha[r];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -442,6 +450,7 @@ struct GState {
 };
 
 __global__ void cycle_init_kernel(GState s, int R, int maxv, const double* __restrict__ rnorm, const int* __restrict__ want) {
+  pdl_wait();
   int r = threadIdx.x;
   if (r >= R) return;
   for (int k = 0; k < maxv; ++k) s.g[r * maxv + k] = make_double2(0, 0);
@@ -453,6 +462,7 @@ __global__ void cycle_init_kernel(GState s, int R, int maxv, const double* __res
 
 __global__ void norm_from_dots_kernel(const double2* __restrict__ d, int maxv, double* __restrict__ nrm, int R,
                                       const int* __restrict__ active) {
+  pdl_wait();
   int r = threadIdx.x;
   if (r >= R) return;
   if (active && !active[r]) return;
@@ -1041,6 +1051,7 @@ dcgs2_update16_kernel(uint2* __restrict__ Vh, int64_t hstride, int j, GState s, 
 __global__ void __launch_bounds__(256)
 xupdate16_kernel(const uint2* __restrict__ Vh, int64_t hstride, int nvec, const double2* __restrict__ coef, int maxv,
                  double2* __restrict__ x, int64_t n, int64_t rstride, const int* __restrict__ ncols, float inv_sc) {
+  pdl_wait();
   const int r = blockIdx.y;
   const int nv = ncols ? min(nvec, ncols[r]) : nvec;
   extern __shared__ float2 xcs[];
@@ -1074,6 +1085,7 @@ xupdate16_kernel(const uint2* __restrict__ Vh, int64_t hstride, int nvec, const 
 
 // back substitution y = H^{-1} g over the first ncols columns
 __global__ void lsq_kernel(GState s, int R, int m, int maxv) {
+  pdl_wait();
   // one block per RHS, column-oriented back substitution: y_k = b_k / H_kk, then
   // b_i -= H_ik y_k for i < k in parallel
   const int r = blockIdx.x;
@@ -1120,22 +1132,26 @@ static int vec_norms(tmat_ctx* ctx, const C<VR>* v, int64_t n, int64_t rstride, 
   if constexpr (sizeof(VR) == 4) {
     if ((n & 1) == 0) {
       const int nbn = (int)std::max<int64_t>(1, std::min<int64_t>(nb, cdiv(n / 2, 256 * 8)));
-      norm32_kernel<<<dim3(nbn, R), 256, 0, ctx->stream>>>(v, n, rstride, part, maxv, active);
+      TM_CUDA(ctx, launch_pdl(ctx->stream, norm32_kernel, dim3(nbn, R), dim3(256), 0, (const float2*)v, n, rstride,
+                              part, maxv, active));
       TM_LAUNCHED(ctx);
       launch_reduce(ctx, part, nbn, 1, maxv, tmp, active, R);
       TM_LAUNCHED(ctx);
-      norm_from_dots_kernel<<<1, 32, 0, ctx->stream>>>(tmp, maxv, nrm, R, active);
+      TM_CUDA(ctx, launch_pdl(ctx->stream, norm_from_dots_kernel, dim3(1), dim3(32), 0, (const double2*)tmp, maxv, nrm,
+                              R, active));
       TM_LAUNCHED(ctx);
       return TMAT_OK;
     }
   }
   if constexpr (sizeof(VR) == 8) {
     const int nbn = (int)std::max<int64_t>(1, std::min<int64_t>(nb, cdiv(n, 256 * 4)));
-    norm64_kernel<<<dim3(nbn, R), 256, 0, ctx->stream>>>(v, n, rstride, part, maxv, active);
+    TM_CUDA(ctx, launch_pdl(ctx->stream, norm64_kernel, dim3(nbn, R), dim3(256), 0, (const double2*)v, n, rstride, part,
+                            maxv, active));
     TM_LAUNCHED(ctx);
     launch_reduce(ctx, part, nbn, 1, maxv, tmp, active, R);
     TM_LAUNCHED(ctx);
-    norm_from_dots_kernel<<<1, 32, 0, ctx->stream>>>(tmp, maxv, nrm, R, active);
+    TM_CUDA(ctx, launch_pdl(ctx->stream, norm_from_dots_kernel, dim3(1), dim3(32), 0, (const double2*)tmp, maxv, nrm, R,
+                            active));
     TM_LAUNCHED(ctx);
     return TMAT_OK;
   }
@@ -1277,7 +1293,8 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
       TM_CUDA(ctx, cudaMemcpyAsync(want, hwant, sizeof(int) * R, cudaMemcpyHostToDevice, ctx->stream));
       cycle_init_kernel<<<1, 32, 0, ctx->stream>>>(s, R, maxv, rnorm, want);
       TM_LAUNCHED(ctx);
-      scale_kernel<VR, VR><<<dim3(g1, R), 256, 0, ctx->stream>>>(rsrc, V, n, rs, rnorm, 1, nullptr);
+      TM_CUDA(ctx, launch_pdl(ctx->stream, scale_kernel<VR, VR>, dim3(g1, R), dim3(256), 0, rsrc, V, n, rs,
+                              (const double*)rnorm, 1, (const int*)nullptr));
       TM_LAUNCHED(ctx);
       int j = 0;
       if constexpr (sizeof(VR) == 4) {
@@ -1419,13 +1436,14 @@ static int gmres_run(tmat_ctx* ctx, const Operator& A, int mode, const C<VR>* b,
         }
       }
       // x += V y over the columns each RHS built in this cycle (ncols[r] <= j)
-      lsq_kernel<<<R, 128, sizeof(double2) * maxv, ctx->stream>>>(s, R, m, maxv);
+      TM_CUDA(ctx, launch_pdl(ctx->stream, lsq_kernel, dim3(R), dim3(128), sizeof(double2) * maxv, s, R, m, maxv));
       TM_LAUNCHED(ctx);
       if constexpr (sizeof(VR) == 4) {
         if (h16)  // the update pass's grid (16 blocks per SM per RHS)
-          xupdate16_kernel<<<dim3((unsigned)std::min<int64_t>(cdiv(n / 2, 256), (int64_t)ctx->num_sms * 16), R), 256,
-                             sizeof(float2) * std::max(j, 1), ctx->stream>>>(
-              Vh, (int64_t)R * n, j, s.y, maxv, x, n, rs, s.ncols, h16_inv);
+          TM_CUDA(ctx, launch_pdl(ctx->stream, xupdate16_kernel,
+                                  dim3((unsigned)std::min<int64_t>(cdiv(n / 2, 256), (int64_t)ctx->num_sms * 16), R),
+                                  dim3(256), sizeof(float2) * std::max(j, 1), (const uint2*)Vh, (int64_t)R * n, j,
+                                  (const double2*)s.y, maxv, x, n, rs, (const int*)s.ncols, h16_inv));
         else
           xupdate32_kernel<<<dim3(g1, R), 256, sizeof(float2) * std::max(j, 1), ctx->stream>>>(
               reinterpret_cast<const float2*>(V), (int64_t)R * n, j, s.y, maxv, x, n, rs, s.ncols);
@@ -1549,7 +1567,8 @@ int solve_system(tmat_ctx* ctx, const Operator& A64, const Operator* A32, int mo
     TM_TRY(gmres_run<float>(ctx, *A32, mode, r32, d64, R, n, ip, &gs));
     st->iterations += gs.iterations;
     // x += ||r|| d
-    axpy_scaled_kernel<<<dim3(g1, R), 256, 0, ctx->stream>>>(x, d64, alpha, n, n);
+    TM_CUDA(ctx, launch_pdl(ctx->stream, axpy_scaled_kernel, dim3(g1, R), dim3(256), 0, x, (const double2*)d64,
+                            (const double*)alpha, n, n));
     TM_LAUNCHED(ctx);
     // Fast check first while the residual is large: r = b - K x with K applied in
     // complex64 to x rounded to complex64 has an absolute error of about
@@ -1564,10 +1583,12 @@ int solve_system(tmat_ctx* ctx, const Operator& A64, const Operator* A32, int mo
     for (int r = 0; r < R; ++r)
       if (hb[r] != 0 && halpha[r] != 0.0) try_fast = try_fast && ip.tol * hr[r] > 10.0 * fast_thr * hb[r];
     if (try_fast) {
-      convert_kernel<double, float><<<g1, 256, 0, ctx->stream>>>(x, r32, (int64_t)R * n);
+      TM_CUDA(ctx, launch_pdl(ctx->stream, convert_kernel<double, float>, dim3(g1), dim3(256), 0, (const double2*)x,
+                              r32, (int64_t)R * n));
       TM_LAUNCHED(ctx);
       TM_TRY(op_apply(ctx, *A32, mode, r32, y32, R));
-      residual_kernel<double, float><<<g1, 256, 0, ctx->stream>>>(b, y32, r64, (int64_t)R * n);
+      TM_CUDA(ctx, launch_pdl(ctx->stream, residual_kernel<double, float>, dim3(g1), dim3(256), 0, (const double2*)b,
+                              (const float2*)y32, r64, (int64_t)R * n));
       TM_LAUNCHED(ctx);
       TM_TRY(vec_norms<double>(ctx, r64, n, n, R, part, nb, tmp, 1, rn, nullptr));
       TM_CUDA(ctx, cudaMemcpyAsync(pin, rn, sizeof(double) * R, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1587,7 +1608,8 @@ int solve_system(tmat_ctx* ctx, const Operator& A64, const Operator* A32, int mo
     }
     // r = b - K x, fp64-accurate
     TM_TRY(op_apply(ctx, Ares, mode, x, y64, R));
-    residual_kernel<double, double><<<g1, 256, 0, ctx->stream>>>(b, y64, r64, (int64_t)R * n);
+    TM_CUDA(ctx, launch_pdl(ctx->stream, residual_kernel<double, double>, dim3(g1), dim3(256), 0, (const double2*)b,
+                            (const double2*)y64, r64, (int64_t)R * n));
     TM_LAUNCHED(ctx);
     TM_TRY(vec_norms<double>(ctx, r64, n, n, R, part, nb, tmp, 1, rn, nullptr));
     TM_CUDA(ctx, cudaMemcpyAsync(pin, rn, sizeof(double) * R, cudaMemcpyDeviceToHost, ctx->stream));
