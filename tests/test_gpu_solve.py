@@ -252,3 +252,36 @@ def test_compressed_basis_solve_matches_the_complex64_basis_and_fp64():
     assert rc == 0
     assert rel_l2(s16, s64) <= 1e-6 and rel_l2(s32, s64) <= 1e-6
     assert i16.iterations <= 1.3 * i32.iterations + 10
+
+
+def test_sampled_kernel_timing_counts_every_call():
+    """tmat_ctx_set_timing(ctx, n): every launch of a timed kind is counted, one Arnoldi
+    iteration in n of the complex64 inner solves carries the events (the dot pass is launched
+    once per iteration), n = 1 times them all, and a negative n is rejected."""
+    from paper_2107_09879_b300 import _lib
+    nmax, cut, n = 4, 3.0, 24
+    pos = W.lattice_positions(n, n)
+    r = W.uniform_radii(n * n, 0.08, 0.24, 93)
+    T = ctx().tmat_build(atoms(r), 1.0, 1.0, nmax)
+    a0 = ctx().tmat_incident_planewave(pos, 1.0, 1.0, nmax, np.array([[0.0, 0.0]]), np.array([[1, 0, 0]], complex))
+    opts = _lib.make_opts(tol=1e-7, restart=200, max_iter=4000, cutoff=cut, taper=cut, precision=_lib.PREC_MIXED,
+                          inner_tol=0.2, path=_lib.PATH_LATTICE, lattice_nx=n, lattice_ny=n, lattice_pitch=0.5)
+    c = _lib.Context(0)
+    try:
+        counts = {}
+        for every in (1, 4):
+            c.set_timing(every)
+            s, info, _, rc = c.tmat_solve(pos, 1.0, 1.0, nmax, T, a0, opts)
+            assert rc == 0 and info.converged
+            timed, ms = c.kernel_time("arnoldi_dots32")
+            calls = c.kernel_calls("arnoldi_dots32")
+            assert calls >= info.iterations >= 1 and ms > 0
+            counts[every] = (timed, calls)
+        assert counts[1][0] == counts[1][1]
+        timed, calls = counts[4]
+        assert abs(timed - math.ceil(calls / 4)) <= 1
+        with pytest.raises(_lib.TMatError) as e:
+            c.set_timing(-1)
+        assert e.value.code == _lib.EINVAL
+    finally:
+        c.close()
