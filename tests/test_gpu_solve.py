@@ -285,3 +285,29 @@ def test_sampled_kernel_timing_counts_every_call():
         assert e.value.code == _lib.EINVAL
     finally:
         c.close()
+
+
+def test_contexts_share_the_kernels_shared_memory_limits():
+    """The dynamic shared-memory limit is an attribute of a kernel, not of a context: a context
+    that launches the DCGS2 step with a shorter restart length (above 48 KB of shared memory,
+    so it sets a limit too) must not lower the limit another context relies on (restart 1000
+    needs ~134 KB)."""
+    from paper_2107_09879_b300 import _lib
+    nmax, cut, n = 3, 2.0, 12
+    pos = W.lattice_positions(n, n)
+    r = W.uniform_radii(n * n, 0.08, 0.24, 95)
+    T = ctx().tmat_build(atoms(r), 1.0, 1.0, nmax)
+    a0 = ctx().tmat_incident_planewave(pos, 1.0, 1.0, nmax, np.array([[0.0, 0.0]]), np.array([[1, 0, 0]], complex))
+    kw = dict(tol=1e-7, max_iter=4000, cutoff=cut, taper=cut, precision=_lib.PREC_MIXED, inner_tol=1e-4,
+              path=_lib.PATH_LATTICE, lattice_nx=n, lattice_ny=n, lattice_pitch=0.5)
+    ca, cb = _lib.Context(0), _lib.Context(0)
+    try:
+        sa, ia, _, rc = ca.tmat_solve(pos, 1.0, 1.0, nmax, T, a0, _lib.make_opts(restart=1000, **kw))
+        assert rc == 0 and ia.converged
+        _, ib, _, rc = cb.tmat_solve(pos, 1.0, 1.0, nmax, T, a0, _lib.make_opts(restart=200, **kw))
+        assert rc == 0 and ib.converged
+        sa2, ia2, _, rc = ca.tmat_solve(pos, 1.0, 1.0, nmax, T, a0, _lib.make_opts(restart=1000, **kw))
+        assert rc == 0 and ia2.converged and rel_l2(sa2, sa) <= 1e-12
+    finally:
+        ca.close()
+        cb.close()
